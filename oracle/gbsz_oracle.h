@@ -1,0 +1,118 @@
+/*
+ * gbsz_oracle.h -- plain CPU oracle of the cuSZ dual-quantization + Huffman
+ * path (Tian et al., "cuSZ: An Efficient GPU-Based Error-Bounded Lossy
+ * Compression Framework for Scientific Data", PACT 2020).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library exists so that tests, the smoke
+ * check and the CPU-baseline leg of the benchmark can check the CUDA library
+ * against an independent, slow, obviously correct restatement of the paper.
+ * The product path never links, loads or calls it.  It shares no code, header
+ * or constant with the CUDA library: the archive layout below is written out
+ * here a second time on purpose.
+ *
+ * Every function takes HOST pointers.  Return value 0 = success; otherwise one
+ * of the REF_ERR_* codes.  Numeric values of the status codes equal the CUDA
+ * library's so the tests can compare them, but they are defined here anew.
+ */
+#ifndef GBSZ_ORACLE_H
+#define GBSZ_ORACLE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+    REF_OK = 0,
+    REF_ERR_INVALID_ARG = 1,
+    REF_ERR_CAPACITY = 2,
+    REF_ERR_CORRUPT = 3,
+    REF_ERR_OOM = 4
+};
+
+enum { REF_EB_ABS = 0, REF_EB_REL = 1 };
+
+typedef struct {
+    uint32_t ndim;    /* 1, 2 or 3 */
+    uint64_t dims[3]; /* dims[0] varies fastest; unused dims are 1 */
+    double eb;        /* absolute bound, or value-range-relative bound */
+    uint32_t eb_mode; /* REF_EB_ABS or REF_EB_REL */
+    uint32_t radius;  /* R: in-cap residuals satisfy |delta| < R; 2R bins */
+    uint32_t chunk;   /* Huffman chunk in symbols, power of two 64..65536 */
+} gbsz_ref_params;
+
+/* S0 -- error bound scalars (value-range-relative bound, footnote of Sec.
+ * 3.2.2).  out[0] = eb, out[1] = 2*eb, out[2] = 1/(2*eb), all FP32. */
+int gbsz_ref_error_bound(const float *x, uint64_t n, uint32_t eb_mode,
+                         double eb, float out[3]);
+
+/* S1 -- prequantization of one value (Sec. 3.1.2, Eq. for D-circle) with the
+ * watchdog of Algorithm 1.  Returns 1 if the value becomes a verbatim
+ * exception, 0 otherwise; *q receives the integer. */
+int gbsz_ref_prequant_one(float x, const float sc[3], int32_t *q);
+
+/* S2 -- Lorenzo residual delta = q - l(q) of order `order` (Sec. 3.1.2,
+ * "Lorenzo Predictor with Binomial Coefficients"), zero outside the field,
+ * arithmetic modulo 2^32. */
+int gbsz_ref_lorenzo_delta(const int32_t *q, uint32_t ndim,
+                           const uint64_t dims[3], uint32_t order,
+                           int32_t *delta);
+
+/* S1+S2 -- dual-quantization of a whole field (Algorithm 2, compression
+ * loop).  codes[n]; outliers (idx, delta) and exceptions (idx, raw bits) in
+ * ascending idx.  Capacities are in entries; *m and *e get the counts.  q may
+ * be NULL; if not, it receives the prequantized integers. */
+int gbsz_ref_dualquant(const float *x, uint32_t ndim, const uint64_t dims[3],
+                       const float sc[3], uint32_t radius, uint16_t *codes,
+                       uint32_t *out_idx, int32_t *out_delta, uint64_t *m,
+                       uint32_t *exc_idx, uint32_t *exc_raw, uint64_t *e,
+                       int32_t *q);
+
+/* S3 -- histogram of quant codes (Sec. 3.2.1). */
+int gbsz_ref_histogram(const uint16_t *codes, uint64_t n, uint32_t nbins,
+                       uint32_t *hist);
+
+/* S4a -- Huffman code lengths by the two-queue construction with the
+ * (frequency, symbol) tie rule (Sec. 3.2.2).  len[nbins]; *maxlen. */
+int gbsz_ref_huffman_lengths(const uint32_t *hist, uint32_t nbins,
+                             uint8_t *len, uint32_t *maxlen);
+
+/* S4b -- canonical codewords from lengths (Sec. 3.2.3). code[nbins]. */
+int gbsz_ref_canonical_codes(const uint8_t *len, uint32_t nbins,
+                             uint64_t *code);
+
+/* S5 -- chunked encode + deflate (Sec. 3.2.4).  bits[nchunk]; stream words
+ * are written MSB-first, each chunk starting on a word.  *words = total. */
+int gbsz_ref_deflate(const uint16_t *codes, uint64_t n, uint32_t chunk,
+                     const uint8_t *len, const uint64_t *code,
+                     uint32_t *bits, uint32_t *stream, uint64_t stream_cap,
+                     uint64_t *words);
+
+/* S7 -- inflate (Sec. 3.3): canonical decode of every chunk. */
+int gbsz_ref_inflate(const uint32_t *stream, uint64_t words,
+                     const uint32_t *bits, uint64_t n, uint32_t chunk,
+                     const uint8_t *len, uint32_t nbins, uint16_t *codes);
+
+/* S8 -- reversed dual-quantization (Algorithm 2, decompression loop). */
+int gbsz_ref_reconstruct(const uint16_t *codes, uint32_t ndim,
+                         const uint64_t dims[3], uint32_t radius,
+                         const uint32_t *out_idx, const int32_t *out_delta,
+                         uint64_t m, const uint32_t *exc_idx,
+                         const uint32_t *exc_raw, uint64_t e, float ebx2,
+                         float *xr);
+
+/* Whole path: archive bytes and back. */
+size_t gbsz_ref_compress_bound(const gbsz_ref_params *p);
+int gbsz_ref_compress(const float *x, const gbsz_ref_params *p, void *archive,
+                      size_t capacity, size_t *out_bytes);
+int gbsz_ref_decompress(const void *archive, size_t bytes, float *x,
+                        uint64_t capacity_elems);
+int gbsz_ref_archive_info(const void *archive, size_t bytes,
+                          gbsz_ref_params *p, uint64_t *n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
