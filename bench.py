@@ -1,0 +1,308 @@
+"""Benchmark: compress + decompress throughput of one FP32 field on GB300.
+
+Workload (default): the 1D random walk of 2^28 values (1 GiB) with 1% spikes,
+value-range-relative error bound 1e-4, radius 512 (1024 bins), Huffman
+chunk 4096.  One step = one compress and one decompress of the resident
+field through the C ABI.  `value` = input bytes of all ranks / (max over
+ranks of the timed K steps), in GB/s (1e9 bytes/s).
+
+Under torchrun every rank compresses its own field (seed + rank): the
+problems are independent, so there is no data-path collective (weak
+scaling); only the timing is reduced (max over ranks).
+
+--impl reference times the CPU oracle on the host cores instead, on a
+bounded prefix of the same workload.
+"""
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "compress+decompress GB/s (input FP32 bytes)"
+PEAKS = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--log2n", type=int, default=28, help="field size 2^k (default: the 2^28 workload)")
+    ap.add_argument("--rel", type=float, default=1e-4)
+    ap.add_argument("--radius", type=int, default=512)
+    ap.add_argument("--chunk", type=int, default=0, help="0 = automatic (4096 at 2^28)")
+    ap.add_argument("--skip-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--cpu-sample-log2", type=int, default=26)
+    return ap.parse_args()
+
+
+def workload_config(a, n, chunk):
+    return {"workload": f"1D random walk 2^{a.log2n} FP32 (1% spikes), rel eb {a.rel:g}, radius {a.radius}, "
+                        f"chunk {chunk}", "n": n, "eb_mode": "rel", "eb": a.rel, "radius": a.radius,
+            "chunk": chunk, "l2": "inputs larger than L2 (1 GiB field vs 129 MB L2)" if n * 4 > (256 << 20)
+            else "input smaller than L2; no flush", "parallelism": "replicas (one field per rank)"}
+
+
+def read_peaks():
+    try:
+        with open(PEAKS) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples during the timed region (clock, throttle reasons)."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        sm, smax, reasons = [], [], set()
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "samples": len(sm), "reasons": sorted(reasons)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def cpu_oracle_time(x, a, chunk, omp=False):
+    from oracle import ref
+    t0 = time.perf_counter()
+    arc = ref.compress(x, a.rel, ref.EB_REL, a.radius, chunk, omp=omp)
+    t1 = time.perf_counter()
+    ref.decompress(arc, omp=omp)
+    t2 = time.perf_counter()
+    return t1 - t0, t2 - t1, arc.size
+
+
+def run_reference(a):
+    """The oracle on the host cores, on a bounded prefix of the workload."""
+    from paper_2007_09625_gb300 import workloads
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    n_full = 1 << a.log2n
+    ns = min(n_full, 1 << a.cpu_sample_log2)
+    x = workloads.random_walk_1d(n_full, seed=1002)[:ns].copy()
+    chunk = a.chunk or 4096
+    for _ in range(a.warmup):
+        cpu_oracle_time(x, a, chunk)
+    ts = []
+    for _ in range(a.steps):
+        tc, td, nb = cpu_oracle_time(x, a, chunk)
+        ts.append(tc + td)
+    t = float(np.mean(ts))
+    gbs = 4 * ns / t / 1e9
+    line = {"metric": METRIC, "value": gbs, "unit": "GB/s", "n_gpus": a.gpus, "steps": a.steps,
+            "warmup": a.warmup, "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "impl": "reference",
+            "config": workload_config(a, n_full, chunk),
+            "cpu_baseline": {"value": gbs, "unit": "GB/s", "cores": 1, "kind": "oracle",
+                             "sample": f"first 2^{a.cpu_sample_log2} values of the workload, "
+                                       f"compress+decompress per step"},
+            "e2e": {"value": gbs, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import torch
+
+    from paper_2007_09625_gb300 import gbsz, workloads
+
+    ws, rank, local = dist_env()
+    dist = ws > 1
+    if dist:
+        import torch.distributed as tdist
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    n = 1 << a.log2n
+    x_host = workloads.random_walk_1d(n, seed=1002 + rank)
+    x = torch.from_numpy(x_host).to(dev)
+    ctx = gbsz.Context(local)
+    chunk = a.chunk or gbsz.auto_chunk([n], a.radius)
+    bound = gbsz.compress_bound([n], a.rel, gbsz.EB_REL, a.radius, chunk)
+    arc = torch.empty(bound, dtype=torch.uint8, device=dev)
+    y = torch.empty_like(x)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        _, nb = ctx.compress(x, a.rel, gbsz.EB_REL, a.radius, chunk, out=arc)
+        ctx.decompress(arc, nb, out=y)
+        return nb
+
+    for _ in range(max(a.warmup, 0)):
+        nb = step()
+    torch.cuda.synchronize(dev)
+    # correctness of the timed configuration: error bound on every element
+    err = (x.double() - y.double()).abs()
+    ebf = float(ctx.debug_copy(gbsz.DEBUG_SCALARS, 3, np.float32)[0])
+    fin = torch.isfinite(x)
+    assert float(err[fin].max()) <= ebf, "error bound violated"
+
+    ctx.profile_read()  # reset counters
+    ctx.profile_enable(True)
+    sampler = ClockSampler(local)
+    if dist:
+        tdist.barrier()
+    torch.cuda.synchronize(dev)
+    sampler.start()
+    time.sleep(0.3)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(a.steps):
+        nb = step()
+    e1.record(stream)
+    torch.cuda.synchronize(dev)
+    clocks = sampler.stop()
+    if dist:
+        tdist.barrier()
+    ms_total = e0.elapsed_time(e1)
+    stage_ms, stage_calls, launches = ctx.profile_read()
+    ctx.profile_enable(False)
+    if dist:
+        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms_total = float(t.item())
+    ms_step = ms_total / a.steps
+    value = 4.0 * n * ws / (ms_step / 1e3) / 1e9
+
+    # compress-only and decompress-only times from the stage events
+    comp_ms = sum(stage_ms[0:4]) / a.steps
+    dec_ms = sum(stage_ms[4:7]) / a.steps
+    cr = 4.0 * n / nb
+
+    # roofline of the dominant stage (algorithmic bytes)
+    peaks, peak_kind = read_peaks()
+    hbm = float(peaks.get("hbm_gbs", 6800.0))
+    m_out = int(np.frombuffer(arc[80:88].cpu().numpy().tobytes(), np.uint64)[0])
+    w_words = int(np.frombuffer(arc[96:104].cpu().numpy().tobytes(), np.uint64)[0])
+    f = m_out / n
+    alg = {  # bytes per launch of each stage
+        0: 4.0 * n,
+        1: 6.0 * n + 4.0 * m_out,
+        3: 2.0 * n + 16.0 * m_out + 4.0 * w_words + 4.0 * (n // chunk),
+        5: 4.0 * w_words + 4.0 * (n // chunk) + 2.0 * n,
+        6: 2.0 * n + 2.0 * n + 4.0 * n + 12.0 * m_out,
+    }
+    dom = max(alg, key=lambda s: stage_ms[s])
+    dom_ms = stage_ms[dom] / max(stage_calls[dom], 1)
+    achieved = alg[dom] / (dom_ms / 1e3) / 1e9
+    stage_names = gbsz.STAGES
+    roofline = {"bound": "hbm", "kernel": stage_names[dom], "achieved": achieved, "peak": hbm,
+                "unit": "GB/s", "frac": achieved / hbm, "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
+                "traffic": None,
+                "alg_bytes_per_launch": alg[dom]}
+
+    e2e = None
+    if not a.skip_e2e:
+        # through the host-buffer entry points: H2D field, compress, D2H
+        # archive, H2D archive, decompress, D2H field -- every step
+        hx = torch.from_numpy(x_host).pin_memory()
+        harc = torch.empty(bound, dtype=torch.uint8).pin_memory()
+        hy = torch.empty_like(hx).pin_memory()
+        for _ in range(2):
+            _, hnb = ctx.compress_host(hx, a.rel, gbsz.EB_REL, a.radius, chunk, out=harc)
+            ctx.decompress_host(harc, hnb, hy)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        ke = max(1, min(a.steps, 5))
+        for _ in range(ke):
+            _, hnb = ctx.compress_host(hx, a.rel, gbsz.EB_REL, a.radius, chunk, out=harc)
+            ctx.decompress_host(harc, hnb, hy)
+        torch.cuda.synchronize(dev)
+        te = (time.perf_counter() - t0) / ke
+        if dist:
+            t = torch.tensor([te], device=dev, dtype=torch.float64)
+            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+            te = float(t.item())
+        assert torch.equal(hy.view(torch.int32), y.cpu().view(torch.int32))
+        e2e = {"value": 4.0 * n * ws / te / 1e9, "unit": "GB/s", "h2d_bytes_per_step": 4 * n + hnb,
+               "d2h_bytes_per_step": hnb + 4 * n, "ms_per_step": te * 1e3}
+
+    cpu = None
+    if rank == 0 and not a.skip_cpu_baseline:
+        ns = min(n, 1 << a.cpu_sample_log2)
+        xs = x_host[:ns].copy()
+        tc, td, _ = cpu_oracle_time(xs, a, chunk)
+        cpu = {"value": 4 * ns / (tc + td) / 1e9, "unit": "GB/s", "cores": 1, "kind": "oracle",
+               "sample": f"first 2^{a.cpu_sample_log2} values of the workload, one compress+decompress",
+               "compress_gbs": 4 * ns / tc / 1e9, "decompress_gbs": 4 * ns / td / 1e9}
+        try:
+            tco, tdo, _ = cpu_oracle_time(xs, a, chunk, omp=True)
+            cpu["omp"] = {"value": 4 * ns / (tco + tdo) / 1e9, "cores": os.cpu_count()}
+        except Exception as ex:  # pragma: no cover
+            cpu["omp"] = {"error": str(ex)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "GB/s", "n_gpus": ws, "steps": a.steps,
+                "warmup": a.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": workload_config(a, n, chunk),
+                "compress_gbs": 4.0 * n / (comp_ms / 1e3) / 1e9 if comp_ms else None,
+                "decompress_gbs": 4.0 * n / (dec_ms / 1e3) / 1e9 if dec_ms else None,
+                "compression_ratio": cr, "outlier_frac": f,
+                "stage_ms_per_step": {nm: stage_ms[i] / a.steps for i, nm in enumerate(stage_names)},
+                "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "clocks": clocks}
+        print(json.dumps(line), flush=True)
+    if dist:
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,162 @@
+/*
+ * gbsz.h -- C ABI of the GB300 (sm_103a) error-bounded lossy compressor for
+ * FP32 fields that implements the dual-quantization + Huffman path of cuSZ
+ * (Tian et al., PACT 2020, arXiv 2007.09625).
+ *
+ * Pipeline (paper section in brackets):
+ *   compress   : error bound from the value range [Sec. 3.2.2 footnote]
+ *                -> prequant + Lorenzo + postquant, outliers [Sec. 3.1, Alg. 2]
+ *                -> histogram [Sec. 3.2.1] -> Huffman lengths and canonical
+ *                codebook [Sec. 3.2.2-3.2.3] -> chunked encode + deflate
+ *                [Sec. 3.2.4] -> archive bytes
+ *   decompress : inflate [Sec. 3.3] -> reversed dual-quantization as a
+ *                d-dimensional integer prefix sum [Alg. 2, Sec. 3.3]
+ *
+ * Conventions shared by every entry point:
+ *   - Pointers named d_* are CUDA device pointers on the context's device;
+ *     h_* are host pointers.  The caller owns every buffer it passes; the
+ *     library never frees, keeps or aliases them beyond the call (stream-
+ *     ordered work on them may still be pending when an async call returns).
+ *   - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ *   - Fields are FP32, row-major with dims[0] varying fastest.
+ *   - Errors are return codes; no call aborts the process or throws.  Device
+ *     side errors (corrupt archive, exhausted capacity, bounded waits that
+ *     ran out) are recorded in a device status word and reported by the call
+ *     that synchronises.
+ *   - A context is not thread-safe; use one context per host thread.
+ */
+#ifndef GBSZ_H
+#define GBSZ_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct gbsz_ctx gbsz_ctx;
+
+typedef enum {
+    GBSZ_OK = 0,
+    GBSZ_ERR_INVALID_ARG = 1, /* bad pointer, size, dims, eb, radius or chunk */
+    GBSZ_ERR_CAPACITY = 2,    /* output buffer too small; needed size reported */
+    GBSZ_ERR_CORRUPT = 3,     /* archive fails a consistency check */
+    GBSZ_ERR_OOM = 4,         /* device or pinned allocation failed */
+    GBSZ_ERR_CUDA = 5,        /* a CUDA runtime call failed */
+    GBSZ_ERR_TIMEOUT = 6,     /* a bounded device wait ran out */
+    GBSZ_ERR_UNSUPPORTED = 7  /* device is not sm_103 or feature absent */
+} gbsz_status;
+
+typedef enum { GBSZ_EB_ABS = 0, GBSZ_EB_REL = 1 } gbsz_eb_mode;
+
+/* Compression parameters.
+ *   ndim     1, 2 or 3 (Lorenzo predictor dimensionality, Sec. 3.1.2)
+ *   dims     extents, dims[0] fastest; entries >= ndim must be 1;
+ *            product n in [1, 2^32)
+ *   eb       error bound: absolute (GBSZ_EB_ABS) or relative to the value
+ *            range max-min over finite values (GBSZ_EB_REL, the paper's
+ *            "valrel"); every reconstructed value satisfies |d - d'| <= eb
+ *            as FP32 eb, non-finite values are kept verbatim
+ *   radius   R in [2, 32768]: residuals with |delta| < R get code delta+R,
+ *            others are outliers with code 0; 2R Huffman symbols
+ *            (Sec. 3.1.2 "cap"; 512 = the paper's 1024 bins)
+ *   chunk    Huffman chunk in symbols, power of two in [64, 65536]
+ *            (Sec. 3.2.4); 0 = choose automatically from n */
+typedef struct {
+    uint32_t ndim;
+    uint64_t dims[3];
+    double eb;
+    uint32_t eb_mode;
+    uint32_t radius;
+    uint32_t chunk;
+} gbsz_params;
+
+/* Creates a context on CUDA device `device` (must be compute capability
+ * 10.3, GB300).  The context owns device scratch (grown on demand and kept
+ * across calls), pinned staging and CUDA events.
+ * Errors: INVALID_ARG (out NULL), UNSUPPORTED (wrong device), CUDA, OOM. */
+gbsz_status gbsz_create(gbsz_ctx **out, int device);
+
+/* Frees everything the context owns.  Waits for its pending work.  NULL ok. */
+void gbsz_destroy(gbsz_ctx *ctx);
+
+/* Worst-case archive size in bytes for these parameters (0 if invalid).
+ * Host-only, no device work. */
+size_t gbsz_compress_bound(const gbsz_params *p);
+
+/* Chunk size that chunk = 0 resolves to for these parameters. */
+uint32_t gbsz_auto_chunk(const gbsz_params *p);
+
+/* Compresses n = prod(dims) floats at d_field into the archive at d_archive
+ * (device memory, 16-byte aligned, `capacity` bytes).  Stages: S0 error
+ * bound, S1-S3 dual-quant + histogram, S4 codebook, S5 encode/deflate and
+ * archive assembly, all as sm_103a kernels on `stream`.  Synchronises the
+ * stream once to return the archive size in *out_bytes (host).
+ * Errors: INVALID_ARG, CAPACITY (*out_bytes = bytes needed; archive
+ * contents unspecified), OOM, CUDA, TIMEOUT. */
+gbsz_status gbsz_compress(gbsz_ctx *ctx, const float *d_field,
+                          const gbsz_params *p, void *d_archive,
+                          size_t capacity, size_t *out_bytes, void *stream);
+
+/* Decompresses the archive at d_archive (`bytes` bytes, device memory,
+ * 16-byte aligned) into d_field (room for capacity_elems floats, 16-byte
+ * aligned).  Stages: S7 decode, S8 outlier scatter + prefix-sum
+ * reconstruction + exception patch.  Reads the 128-byte header to the host
+ * first and synchronises at the end to report device-side checks.
+ * Errors: INVALID_ARG, CORRUPT, CAPACITY (field larger than capacity),
+ * OOM, CUDA, TIMEOUT. */
+gbsz_status gbsz_decompress(gbsz_ctx *ctx, const void *d_archive, size_t bytes,
+                            float *d_field, uint64_t capacity_elems,
+                            void *stream);
+
+/* Host-buffer variants: the field (or archive) is copied from host memory to
+ * context-owned device staging, processed, and the result copied back to
+ * host memory, all inside the call (pinned host buffers copy fastest).
+ * Same errors as the device variants. */
+gbsz_status gbsz_compress_host(gbsz_ctx *ctx, const float *h_field,
+                               const gbsz_params *p, void *h_archive,
+                               size_t capacity, size_t *out_bytes,
+                               void *stream);
+gbsz_status gbsz_decompress_host(gbsz_ctx *ctx, const void *h_archive,
+                                 size_t bytes, float *h_field,
+                                 uint64_t capacity_elems, void *stream);
+
+/* Parses a host copy of an archive header (at least 128 bytes; `bytes` is
+ * the archive's full size, used for the size check).  Fills *out and *n.
+ * Host-only.  Errors: INVALID_ARG (NULL), CORRUPT. */
+gbsz_status gbsz_archive_info(const void *h_archive, size_t bytes,
+                              gbsz_params *out, uint64_t *n);
+
+/* Static description of a status code. */
+const char *gbsz_status_str(gbsz_status s);
+
+/* Copies an internal buffer of the last compress/decompress on this context
+ * to host memory, for stage-by-stage checks.  `which`:
+ *   0 quant codes of the last compress (uint16[n])
+ *   1 histogram of the last compress (uint32[2R])
+ *   2 error-bound scalars of the last compress (float[3]: eb, 2eb, 1/(2eb))
+ *   3 quant codes decoded by the last decompress (uint16[n])
+ *   4 canonical codewords of the last compress (uint64[2R]: code, no length)
+ * `bytes` must equal the buffer's size.  Synchronises the context's last
+ * stream.  Errors: INVALID_ARG, CUDA. */
+gbsz_status gbsz_debug_copy(gbsz_ctx *ctx, int which, void *h_dst,
+                            size_t bytes);
+
+/* Stage timing.  While enabled, every compress/decompress records CUDA
+ * events around each stage on its stream.  gbsz_profile_read synchronises,
+ * adds up the stage durations recorded since the last read, and returns
+ * them with the count of kernel launches.  Stage indices:
+ *   0 error bound, 1 dual-quant+histogram, 2 codebook, 3 encode+deflate,
+ *   4 decode tables, 5 decode, 6 reconstruct (scatter+scan+patch),
+ *   7 other (header/aux)
+ * ms[nstage], calls[nstage] may be NULL.  Errors: INVALID_ARG, CUDA. */
+#define GBSZ_NSTAGE 8
+gbsz_status gbsz_profile_enable(gbsz_ctx *ctx, int enable);
+gbsz_status gbsz_profile_read(gbsz_ctx *ctx, double *ms, uint64_t *calls,
+                              uint64_t *kernel_launches);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,353 @@
+// common.cuh -- definitions shared by the sm_103a kernels of the compressor.
+//
+// Archive format (version 1), little-endian, sections 16-byte aligned:
+//   [0,128)          header (field offsets below)
+//   len[2R]          Huffman code length per quant code (uint8)
+//   bits[nchunk]     deflated bits per chunk (uint32)
+//   outliers[M]      {uint32 idx, int32 delta}, ascending idx
+//   exceptions[E]    {uint32 idx, uint32 raw float bits}, ascending idx
+//   stream[W]        uint32 words; each chunk starts on a word, MSB first
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace gbsz {
+
+constexpr uint32_t kMagic = 0x5A534247u;  // "GBSZ"
+constexpr uint16_t kVersion = 1;
+constexpr uint32_t kHeaderBytes = 128;
+// Deepest possible Huffman leaf for n < 2^32 symbols: a leaf at depth d needs
+// a total weight >= Fibonacci(d + 2), and Fibonacci(48) > 2^32.
+constexpr uint32_t kMaxLen = 45;
+constexpr uint32_t kMaxBins = 65536;
+
+// header byte offsets
+enum : uint32_t {
+    H_MAGIC = 0, H_VERSION = 4, H_HDRBYTES = 6, H_NDIM = 8, H_EBMODE = 12,
+    H_DIMS = 16, H_N = 40, H_EB = 48, H_EBF = 56, H_EBX2 = 60, H_INV2EB = 64,
+    H_RADIUS = 68, H_CHUNK = 72, H_NCHUNK = 76, H_M = 80, H_E = 88, H_W = 96,
+    H_MAXLEN = 104, H_LBLOCK = 108, H_TOTAL = 112
+};
+
+__host__ __device__ inline uint64_t align16(uint64_t v) { return (v + 15) & ~uint64_t(15); }
+
+struct Layout {
+    uint64_t len, bits, outl, exc, stream, total;
+};
+
+__host__ __device__ inline Layout make_layout(uint32_t radius, uint64_t nchunk, uint64_t m,
+                                              uint64_t e, uint64_t w)
+{
+    Layout L;
+    L.len = kHeaderBytes;
+    L.bits = align16(L.len + 2ull * radius);
+    L.outl = align16(L.bits + 4 * nchunk);
+    L.exc = L.outl + 8 * m;
+    L.stream = align16(L.exc + 8 * e);
+    L.total = L.stream + 4 * w;
+    return L;
+}
+
+// device status bits (Control::error)
+enum : uint32_t {
+    DERR_CAPACITY = 1u, DERR_CORRUPT = 2u, DERR_TIMEOUT = 4u, DERR_EB = 8u, DERR_INTERNAL = 16u
+};
+
+// Per-call device control block.  Zeroed by one memset at the start of each
+// compress / decompress.
+struct Control {
+    uint32_t max_key;      // S0: max ordered key over finite values (0 = none)
+    uint32_t min_key_inv;  // S0: max of ~key, i.e. the min (0 = none)
+    uint32_t s0_done;      // S0: finished blocks
+    uint32_t error;        // DERR_* bits
+    float eb, ebx2, inv2eb;
+    uint32_t maxlen;
+    unsigned long long n_out;  // outliers (code 0), counted by the dual-quant kernel
+    unsigned long long n_exc;  // verbatim exceptions
+    uint32_t ticket;           // encode: next work unit
+    uint32_t nsym;             // codebook: symbols with nonzero frequency
+    unsigned long long words;  // encode: total stream words
+    unsigned long long total;  // encode: archive bytes
+    unsigned long long zeros;  // decode: code-0 symbols decoded
+    unsigned long long out_chk; // encode: outliers emitted (check)
+    unsigned long long exc_chk; // encode: exceptions emitted (check)
+};
+
+struct EbScalars {
+    float eb, ebx2, inv2eb;
+};
+
+// ---------------------------------------------------------------------------
+// Prequantization (Sec. 3.1.2): d° = round(d / 2eb) as t = fl(d * 1/(2eb)),
+// round half to even, accepted only if the value the decompressor rebuilds,
+// fl(2eb * fl(q)), is within eb of d (the watchdog of Algorithm 1); else
+// q +- 1; else the value is kept verbatim (exception).
+
+__device__ __forceinline__ float recon_value(int32_t q, float ebx2)
+{
+    return __fmul_rn(ebx2, __int2float_rn(q));
+}
+
+// |d - r| <= eb, decided exactly.  The rounded difference decides unless it
+// equals eb; then Knuth's TwoSum gives the exact residual of the subtraction.
+__device__ __forceinline__ bool within_bound(float d, float r, float eb)
+{
+    const float s = __fsub_rn(d, r);
+    const float a = fabsf(s);
+    if (a < eb) return true;
+    if (!(a == eb)) return false;
+    const float nr = -r;
+    const float bp = __fsub_rn(s, d);
+    const float ap = __fsub_rn(s, bp);
+    const float e = __fadd_rn(__fsub_rn(d, ap), __fsub_rn(nr, bp));
+    return s > 0.0f ? e <= 0.0f : e >= 0.0f;
+}
+
+__device__ __forceinline__ int32_t prequant(float d, const EbScalars &s, bool &exc)
+{
+    if ((__float_as_uint(d) & 0x7F800000u) == 0x7F800000u) {  // NaN or Inf
+        exc = true;
+        return 0;
+    }
+    const float t = __fmul_rn(d, s.inv2eb);
+    if (!(fabsf(t) < 1073741824.0f)) {
+        exc = true;
+        return t > 0.0f ? (1 << 30) : -(1 << 30);
+    }
+    const int32_t q = __float2int_rn(t);
+    const float r = recon_value(q, s.ebx2);
+    if (within_bound(d, r, s.eb)) {
+        exc = false;
+        return q;
+    }
+    const int32_t q2 = d > r ? q + 1 : q - 1;
+    if (within_bound(d, recon_value(q2, s.ebx2), s.eb)) {
+        exc = false;
+        return q2;
+    }
+    exc = true;
+    return q;
+}
+
+__device__ __forceinline__ EbScalars load_scalars(const Control *ctl)
+{
+    EbScalars s;
+    s.eb = ctl->eb;
+    s.ebx2 = ctl->ebx2;
+    s.inv2eb = ctl->inv2eb;
+    return s;
+}
+
+// code for residual delta (postquant, Algorithm 2): delta + R if in cap and
+// not an exception, else 0 (outlier marker)
+__device__ __forceinline__ uint32_t postquant(uint32_t delta, bool exc, int32_t R)
+{
+    const int32_t dl = (int32_t)delta;
+    return (!exc && dl > -R && dl < R) ? (uint32_t)(dl + R) : 0u;
+}
+
+// ---------------------------------------------------------------------------
+// small warp / block helpers
+
+__device__ __forceinline__ uint32_t warp_incl_scan(uint32_t v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_incl_scan64(unsigned long long v)
+{
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    return v;
+}
+
+// Block-wide exclusive scan of one uint32 per thread; `sh` needs
+// blockDim.x/32 + 1 entries.  Returns the exclusive prefix; *total gets the
+// block total.  Contains __syncthreads; all threads must call.
+__device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *sh, uint32_t *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t inc = warp_incl_scan(v);
+    if (lane == 31) sh[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < nw ? sh[lane] : 0;
+        uint32_t wi = warp_incl_scan(w);
+        if (lane < nw) sh[lane] = wi - w;
+        if (lane == nw - 1) sh[nw] = wi;
+    }
+    __syncthreads();
+    uint32_t r = sh[warp] + inc - v;
+    *total = sh[nw];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ unsigned long long block_excl_scan64(unsigned long long v,
+                                                                unsigned long long *sh,
+                                                                unsigned long long *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    unsigned long long inc = warp_incl_scan64(v);
+    if (lane == 31) sh[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        unsigned long long w = lane < nw ? sh[lane] : 0;
+        unsigned long long wi = warp_incl_scan64(w);
+        if (lane < nw) sh[lane] = wi - w;
+        if (lane == nw - 1) sh[nw] = wi;
+    }
+    __syncthreads();
+    unsigned long long r = sh[warp] + inc - v;
+    *total = sh[nw];
+    __syncthreads();
+    return r;
+}
+
+__device__ __forceinline__ uint32_t block_max(uint32_t v, uint32_t *sh)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (lane == 0) sh[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < nw ? sh[lane] : 0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w = max(w, __shfl_xor_sync(0xffffffffu, w, o));
+        if (lane == 0) sh[nw] = w;
+    }
+    __syncthreads();
+    uint32_t r = sh[nw];
+    __syncthreads();
+    return r;
+}
+
+// Bounded spin on a flag written by another CTA.  Returns the flag value, or
+// 0 after `limit` polls (the caller records DERR_TIMEOUT).
+__device__ __forceinline__ uint32_t spin_until_nonzero_epoch(const uint32_t *flag, uint32_t epoch,
+                                                             uint32_t limit)
+{
+    for (uint32_t it = 0; it < limit; it++) {
+        uint32_t f = *(const volatile uint32_t *)flag;
+        if ((f >> 2) == epoch && (f & 3u)) return f;
+        __nanosleep(64);
+    }
+    return 0;
+}
+
+constexpr uint32_t kSpinLimit = 1u << 24;  // ~1 s of polling at 64 ns
+
+// ---------------------------------------------------------------------------
+// launch wrappers implemented in the kernel translation units
+
+struct QuantArgs {
+    const float *x;
+    uint64_t dims[3];
+    uint32_t ndim;
+    uint32_t radius;
+    uint16_t *codes;
+    int32_t *dscr;   // residual of every code-0 point, indexed by point
+    uint32_t *hist;  // 2R bins, zeroed by the caller
+    Control *ctl;
+    int num_sms;
+};
+
+void launch_minmax_eb(const float *x, uint64_t n, Control *ctl, double eb, uint32_t mode,
+                      int num_sms, cudaStream_t st);
+void launch_dualquant(const QuantArgs &a, cudaStream_t st);
+
+struct CodebookArgs {
+    const uint32_t *hist;  // for compress; NULL for the decode-table build
+    const uint8_t *len_in; // for decode: lengths from the archive
+    uint32_t nbins;
+    uint8_t *len_out;      // compress: lengths (written into the archive)
+    uint64_t *cw64;        // (len << 56) | code
+    uint32_t *cw32;        // (len << 24) | code, valid when maxlen <= 24
+    uint64_t *codes_only;  // plain codewords (debug copy)
+    // decode tables
+    uint32_t *lut;         // 1 << kLutBits entries: (sym << 8) | len, 0 = long code
+    unsigned long long *first;   // [kMaxLen + 2] first canonical code per length
+    uint32_t *count;       // [kMaxLen + 2]
+    uint32_t *start;       // [kMaxLen + 2]
+    uint16_t *sorted;      // symbols in (len, sym) order
+    uint32_t expect_maxlen;  // decode: header's maxlen
+    // scratch (global, kMaxBins-sized or 2x)
+    unsigned long long *keyA, *keyB;
+    uint32_t *nodef, *parent, *distA, *distB, *parA, *parB;
+    Control *ctl;
+};
+constexpr int kLutBits = 12;
+
+void launch_codebook(const CodebookArgs &a, cudaStream_t st);
+void launch_decode_tables(const CodebookArgs &a, cudaStream_t st);
+
+struct EncodeArgs {
+    const uint16_t *codes;
+    const float *x;
+    const int32_t *dscr;
+    uint64_t n;
+    uint32_t chunk, radius, nbins;
+    const uint64_t *cw64;
+    const uint32_t *cw32;
+    uint8_t *archive;
+    uint64_t capacity;
+    uint32_t *lb_flag;
+    ulonglong2 *lb_agg, *lb_inc;
+    uint32_t epoch;
+    Control *ctl;
+    // header fields
+    uint32_t ndim, eb_mode;
+    uint64_t dims[3];
+    double eb;
+    int num_sms;
+};
+void launch_encode(const EncodeArgs &a, cudaStream_t st);
+
+struct DecodeArgs {
+    const uint8_t *archive;
+    uint64_t n;
+    uint32_t chunk, nchunk, radius, maxlen;
+    uint64_t words;
+    uint64_t off_bits, off_stream;
+    const uint32_t *lut;
+    const unsigned long long *first;
+    const uint32_t *count, *start;
+    const uint16_t *sorted;
+    unsigned long long *chunk_off;  // scratch nchunk
+    uint16_t *codes;
+    Control *ctl;
+};
+void launch_decode(const DecodeArgs &a, cudaStream_t st);
+
+struct ReconArgs {
+    const uint16_t *codes;
+    const uint8_t *archive;
+    uint64_t off_outl, off_exc;
+    uint64_t m, e;
+    uint32_t ndim;
+    uint64_t dims[3];
+    uint32_t radius;
+    float ebx2;
+    int32_t *dscr;
+    uint32_t *faces;      // carry scratch
+    uint64_t faces_cap;   // entries
+    float *out;
+    Control *ctl;
+    int num_sms;
+};
+uint64_t recon_faces_entries(uint32_t ndim, const uint64_t dims[3]);
+void launch_reconstruct(const ReconArgs &a, cudaStream_t st, int *launches);
+
+}  // namespace gbsz

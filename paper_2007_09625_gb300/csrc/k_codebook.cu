@@ -1,0 +1,384 @@
+// k_codebook.cu -- S4: Huffman code lengths, canonical codebook and the
+// decoder's reverse codebook, each built by one CTA on the device so no
+// frequency table or codebook crosses PCIe (Sec. 3.2.2, 3.2.3).
+//
+// Tree: leaves sorted by (frequency, symbol); the two-queue merge takes the
+// leaf on equal frequency.  The paper builds the tree with one GPU thread;
+// here the merge runs in phases: with a, b the two smallest available nodes,
+// every available node of frequency <= a + b is consumed before any node not
+// yet created (those are all >= a + b and lose ties), so that whole prefix is
+// paired at once, pair j creating internal node j of the phase.  This yields
+// exactly the serial merge's tree.  Depths by pointer jumping (depth <= 45).
+//
+// Canonization (Sec. 3.2.3): symbols in (length, symbol) order, first code 0,
+// next = (prev + 1) << (len - prevlen).  Codeword tables hold (len, code) as
+// len << 24 | code in 32 bits when the longest code fits 24 bits, and
+// len << 56 | code in 64 bits always (the paper's adaptive representation).
+#include "common.cuh"
+
+namespace gbsz {
+
+namespace {
+
+constexpr int kCbThreads = 1024;
+constexpr uint32_t kRankSortMax = 2048;
+
+// Stable sort of n unique 64-bit keys by bits [bit_lo, bit_hi); the keys are
+// already ordered by the bits below bit_lo.  Returns the buffer holding the
+// result (a or b).  s_cnt: 16 * blockDim.x words of shared memory.
+__device__ unsigned long long *cta_sort(unsigned long long *a, unsigned long long *b, uint32_t n,
+                                        int bit_lo, int bit_hi, uint32_t *s_cnt)
+{
+    const uint32_t T = blockDim.x, t = threadIdx.x;
+    if (n <= 1 || bit_lo >= bit_hi) return a;
+    if (n <= kRankSortMax) {
+        // rank sort through shared memory: rank = number of smaller keys
+        unsigned long long *sk = reinterpret_cast<unsigned long long *>(s_cnt);
+        const unsigned long long mask =
+            (bit_hi >= 64 ? ~0ull : ((1ull << bit_hi) - 1)) & ~((1ull << bit_lo) - 1);
+        for (uint32_t i = t; i < n; i += T) sk[i] = a[i];
+        __syncthreads();
+        for (uint32_t i = t; i < n; i += T) {
+            const unsigned long long ki = sk[i];
+            const unsigned long long mi = ki & mask;
+            uint32_t r = 0;
+            for (uint32_t j = 0; j < n; j++) {
+                const unsigned long long mj = sk[j] & mask;
+                r += (mj < mi) || (mj == mi && j < i);
+            }
+            b[r] = ki;
+        }
+        __syncthreads();
+        return b;
+    }
+    const uint32_t per = (n + T - 1) / T;
+    const uint32_t lo = min(n, t * per), hi = min(n, lo + per);
+    __shared__ uint32_t s_scan[33];
+    for (int bit = bit_lo; bit < bit_hi; bit += 4) {
+        for (int d = 0; d < 16; d++) s_cnt[d * T + t] = 0;
+        for (uint32_t i = lo; i < hi; i++) s_cnt[((a[i] >> bit) & 15u) * T + t]++;
+        __syncthreads();
+        // exclusive scan of the digit-major count matrix
+        uint32_t loc = 0;
+        for (int j = 0; j < 16; j++) loc += s_cnt[16 * t + j];
+        uint32_t tot;
+        uint32_t run = block_excl_scan(loc, s_scan, &tot);
+        for (int j = 0; j < 16; j++) {
+            const uint32_t c = s_cnt[16 * t + j];
+            s_cnt[16 * t + j] = run;
+            run += c;
+        }
+        __syncthreads();
+        for (uint32_t i = lo; i < hi; i++) {
+            const unsigned long long k = a[i];
+            const uint32_t d = (uint32_t)((k >> bit) & 15u);
+            b[s_cnt[d * T + t]++] = k;
+        }
+        __syncthreads();
+        unsigned long long *tmp = a;
+        a = b;
+        b = tmp;
+    }
+    return a;
+}
+
+struct Canon {
+    unsigned long long first[kMaxLen + 2];
+    uint32_t count[kMaxLen + 2];
+    uint32_t start[kMaxLen + 2];
+};
+
+// Canonical codes from lengths (all threads).  Fills sh (tables), writes
+// sorted symbols (if non-NULL) and per-symbol codewords (if non-NULL).
+__device__ void canonicalize(const uint8_t *len, uint32_t nbins, unsigned long long *keyA,
+                             unsigned long long *keyB, uint32_t *s_cnt, Canon &sh, uint16_t *sorted,
+                             uint64_t *cw64, uint32_t *cw32, uint64_t *codes_only, uint32_t maxlen)
+{
+    const uint32_t T = blockDim.x, t = threadIdx.x;
+    __shared__ uint32_t s_scan[33];
+    // compaction of used symbols in ascending order
+    const uint32_t per = (nbins + T - 1) / T;
+    const uint32_t lo = min(nbins, t * per), hi = min(nbins, lo + per);
+    uint32_t c = 0;
+    for (uint32_t s = lo; s < hi; s++) c += len[s] > 0;
+    uint32_t k;
+    uint32_t pos = block_excl_scan(c, s_scan, &k);
+    for (uint32_t s = lo; s < hi; s++)
+        if (len[s]) keyA[pos++] = ((unsigned long long)len[s] << 16) | s;
+    for (uint32_t l = t; l < kMaxLen + 2; l += T) sh.count[l] = 0;
+    __syncthreads();
+    unsigned long long *srt = cta_sort(keyA, keyB, k, 16, 24, s_cnt);
+    for (uint32_t p = t; p < k; p += T) atomicAdd(&sh.count[srt[p] >> 16], 1u);
+    __syncthreads();
+    if (t == 0) {
+        uint32_t st = 0;
+        unsigned long long f = 0;
+        for (uint32_t l = 0; l < kMaxLen + 2; l++) {
+            sh.start[l] = st;
+            sh.first[l] = f;
+            if (l >= 1) {
+                st += sh.count[l];
+                f = (f + sh.count[l]) << 1;
+            }
+        }
+        sh.start[0] = 0;
+        sh.first[0] = 0;
+    }
+    __syncthreads();
+    for (uint32_t p = t; p < k; p += T) {
+        const unsigned long long key = srt[p];
+        const uint32_t l = (uint32_t)(key >> 16), s = (uint32_t)(key & 0xFFFFu);
+        const unsigned long long code = sh.first[l] + (p - sh.start[l]);
+        if (sorted) sorted[p] = (uint16_t)s;
+        if (cw64) cw64[s] = ((unsigned long long)l << 56) | code;
+        if (cw32) cw32[s] = maxlen <= 24 ? ((l << 24) | (uint32_t)code) : 0u;
+        if (codes_only) codes_only[s] = code;
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kCbThreads, 1) k_codebook(CodebookArgs a)
+{
+    extern __shared__ uint32_t s_cnt[];  // 16 * kCbThreads words
+    __shared__ Canon canon;
+    __shared__ uint32_t s_scan[33];
+    __shared__ uint32_t s_lh, s_ih, s_ni, s_cl, s_ci, s_np;
+    const uint32_t T = blockDim.x, t = threadIdx.x, nbins = a.nbins;
+
+    // symbols with nonzero frequency, keys (freq << 16 | sym) in symbol order
+    const uint32_t per = (nbins + T - 1) / T;
+    const uint32_t lo = min(nbins, t * per), hi = min(nbins, lo + per);
+    uint32_t c = 0, fmax = 0;
+    for (uint32_t s = lo; s < hi; s++) {
+        const uint32_t f = a.hist[s];
+        c += f > 0;
+        fmax = max(fmax, f);
+    }
+    uint32_t k;
+    uint32_t pos = block_excl_scan(c, s_scan, &k);
+    fmax = block_max(fmax, s_scan);
+    for (uint32_t s = lo; s < hi; s++) {
+        const uint32_t f = a.hist[s];
+        if (f) a.keyA[pos++] = ((unsigned long long)f << 16) | s;
+        a.len_out[s] = 0;
+        a.cw64[s] = 0;
+        a.cw32[s] = 0;
+        a.codes_only[s] = 0;
+    }
+    __syncthreads();
+    if (k == 0) {
+        if (t == 0) atomicOr(&a.ctl->error, DERR_INTERNAL);
+        return;
+    }
+    const int fbits = 32 - __clz(fmax);
+    unsigned long long *K = cta_sort(a.keyA, a.keyB, k, 16, 16 + ((fbits + 3) & ~3), s_cnt);
+    unsigned long long *spare = K == a.keyA ? a.keyB : a.keyA;
+    uint32_t maxlen = 1;
+    if (k == 1) {
+        if (t == 0) a.len_out[K[0] & 0xFFFFu] = 1;
+    } else {
+        // phase-parallel two-queue merge
+        uint32_t *F = a.nodef;    // internal node frequencies, creation order
+        uint32_t *P = a.parent;   // parent of every node (leaves 0..k-1, internal k..)
+        auto LF = [&](uint32_t i) -> uint32_t { return (uint32_t)(K[i] >> 16); };
+        if (t == 0) {
+            s_lh = 0;
+            s_ih = 0;
+            s_ni = 0;
+        }
+        __syncthreads();
+        for (;;) {
+            if (t == 0) {
+                const uint32_t lh = s_lh, ih = s_ih, ni = s_ni;
+                if ((k - lh) + (ni - ih) <= 1) {
+                    s_np = 0;
+                } else {
+                    uint32_t x = lh, y = ih;
+                    unsigned long long f2 = 0;
+                    for (int r = 0; r < 2; r++) {
+                        if (x < k && (y >= ni || LF(x) <= F[y])) f2 += LF(x++);
+                        else f2 += F[y++];
+                    }
+                    // counts of available nodes with frequency <= f2
+                    uint32_t l0 = lh, l1 = k;
+                    while (l0 < l1) {
+                        const uint32_t m = (l0 + l1) >> 1;
+                        if ((unsigned long long)LF(m) <= f2) l0 = m + 1;
+                        else l1 = m;
+                    }
+                    uint32_t i0 = ih, i1 = ni;
+                    while (i0 < i1) {
+                        const uint32_t m = (i0 + i1) >> 1;
+                        if ((unsigned long long)F[m] <= f2) i0 = m + 1;
+                        else i1 = m;
+                    }
+                    s_cl = l0 - lh;
+                    s_ci = i0 - ih;
+                    s_np = (s_cl + s_ci) >> 1;
+                }
+            }
+            __syncthreads();
+            const uint32_t np = s_np;
+            if (np == 0) break;
+            const uint32_t lh = s_lh, ih = s_ih, ni = s_ni, cl = s_cl, ci = s_ci;
+            // merge-path split: number of leaves among the first d merged nodes
+            auto split = [&](uint32_t d) -> uint32_t {
+                uint32_t l0 = d > ci ? d - ci : 0, l1 = min(d, cl);
+                while (l0 < l1) {
+                    const uint32_t m = (l0 + l1) >> 1, b = d - m;
+                    if (b == 0 || m == cl || F[ih + b - 1] < LF(lh + m)) l1 = m;
+                    else l0 = m + 1;
+                }
+                return l0;
+            };
+            for (uint32_t p = t; p < np; p += T) {
+                uint32_t x = split(2 * p), y = 2 * p - x;
+                uint32_t f = 0;
+                for (int r = 0; r < 2; r++) {
+                    if (x < cl && (y >= ci || LF(lh + x) <= F[ih + y])) {
+                        f += LF(lh + x);
+                        P[lh + x] = k + ni + p;
+                        x++;
+                    } else {
+                        f += F[ih + y];
+                        P[k + ih + y] = k + ni + p;
+                        y++;
+                    }
+                }
+                F[ni + p] = f;
+            }
+            __syncthreads();
+            if (t == 0) {
+                const uint32_t x = split(2 * np);
+                s_lh = lh + x;
+                s_ih = ih + (2 * np - x);
+                s_ni = ni + np;
+            }
+            __syncthreads();
+        }
+        if (t == 0 && s_ni != k - 1) atomicOr(&a.ctl->error, DERR_INTERNAL);
+        // depths by pointer jumping over 2k-1 nodes; root = 2k-2
+        const uint32_t N = 2 * k - 1, root = N - 1;
+        uint32_t *pa = a.parA, *da = a.distA, *pb = a.parB, *db = a.distB;
+        for (uint32_t i = t; i < N; i += T) {
+            pa[i] = i == root ? root : P[i];
+            da[i] = i == root ? 0u : 1u;
+        }
+        __syncthreads();
+        for (int r = 0; r < 6; r++) {
+            for (uint32_t i = t; i < N; i += T) {
+                const uint32_t p = pa[i];
+                db[i] = da[i] + da[p];
+                pb[i] = pa[p];
+            }
+            __syncthreads();
+            uint32_t *tp = pa; pa = pb; pb = tp;
+            tp = da; da = db; db = tp;
+        }
+        uint32_t ml = 0;
+        for (uint32_t i = t; i < k; i += T) {
+            const uint32_t d = da[i];
+            ml = max(ml, d);
+            a.len_out[K[i] & 0xFFFFu] = (uint8_t)min(d, 255u);
+        }
+        maxlen = block_max(ml, s_scan);
+        if (t == 0 && maxlen > kMaxLen) atomicOr(&a.ctl->error, DERR_INTERNAL);
+    }
+    __syncthreads();
+    if (t == 0) {
+        a.ctl->maxlen = maxlen;
+        a.ctl->nsym = k;
+    }
+    if (maxlen > kMaxLen) return;
+    canonicalize(a.len_out, nbins, spare, K, s_cnt, canon, nullptr, a.cw64, a.cw32, a.codes_only, maxlen);
+}
+
+// Reverse codebook for decoding: validates the length table (every length
+// <= 45, the header's maximum matches, Kraft sum <= 1), then builds the
+// canonical tables and a 2^12-entry lookup of (symbol, length) for codes of
+// at most 12 bits.
+__global__ void __launch_bounds__(kCbThreads, 1) k_decode_tables(CodebookArgs a)
+{
+    extern __shared__ uint32_t s_cnt[];
+    __shared__ Canon canon;
+    __shared__ uint32_t s_scan[33];
+    __shared__ unsigned long long s_kraft;
+    __shared__ uint32_t s_bad;
+    const uint32_t T = blockDim.x, t = threadIdx.x, nbins = a.nbins;
+    if (t == 0) {
+        s_kraft = 0;
+        s_bad = 0;
+    }
+    __syncthreads();
+    uint32_t ml = 0;
+    unsigned long long kr = 0;
+    for (uint32_t s = t; s < nbins; s += T) {
+        const uint32_t l = a.len_in[s];
+        if (l > kMaxLen) atomicOr(&s_bad, 1u);
+        ml = max(ml, l);
+    }
+    ml = block_max(ml, s_scan);
+    if (ml == 0 || ml != a.expect_maxlen) atomicOr(&s_bad, 1u);
+    __syncthreads();
+    if (s_bad) {
+        if (t == 0) atomicOr(&a.ctl->error, DERR_CORRUPT);
+        return;
+    }
+    for (uint32_t s = t; s < nbins; s += T) {
+        const uint32_t l = a.len_in[s];
+        if (l) kr += 1ull << (ml - l);
+    }
+    atomicAdd(&s_kraft, kr);
+    __syncthreads();
+    if (s_kraft > (1ull << ml)) {
+        if (t == 0) atomicOr(&a.ctl->error, DERR_CORRUPT);
+        return;
+    }
+    canonicalize(a.len_in, nbins, a.keyA, a.keyB, s_cnt, canon, a.sorted, nullptr, nullptr, nullptr, ml);
+    for (uint32_t l = t; l < kMaxLen + 2; l += T) {
+        a.first[l] = canon.first[l];
+        a.count[l] = canon.count[l];
+        a.start[l] = canon.start[l];
+    }
+    // lookup table: canonical decode of every 12-bit prefix
+    for (uint32_t v = t; v < (1u << kLutBits); v += T) {
+        uint32_t e = 0;
+        for (uint32_t l = 1; l <= (uint32_t)kLutBits && l <= ml; l++) {
+            const unsigned long long code = v >> (kLutBits - l);
+            const unsigned long long off = code - canon.first[l];
+            if (off < canon.count[l]) {
+                e = ((uint32_t)a.sorted[canon.start[l] + off] << 8) | l;
+                break;
+            }
+        }
+        a.lut[v] = e;
+    }
+}
+
+}  // namespace
+
+void launch_codebook(const CodebookArgs &a, cudaStream_t st)
+{
+    const size_t smem = 16 * kCbThreads * sizeof(uint32_t);
+    static bool init = false;
+    if (!init) {
+        cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_decode_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        init = true;
+    }
+    k_codebook<<<1, kCbThreads, smem, st>>>(a);
+}
+
+void launch_decode_tables(const CodebookArgs &a, cudaStream_t st)
+{
+    const size_t smem = 16 * kCbThreads * sizeof(uint32_t);
+    static bool init = false;
+    if (!init) {
+        cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        cudaFuncSetAttribute(k_decode_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        init = true;
+    }
+    k_decode_tables<<<1, kCbThreads, smem, st>>>(a);
+}
+
+}  // namespace gbsz

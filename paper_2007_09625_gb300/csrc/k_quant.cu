@@ -1,0 +1,507 @@
+// k_quant.cu -- S0 (error bound from the value range) and S1-S3 (prequant,
+// Lorenzo prediction, postquant with outliers, fused code histogram).
+//
+// Paper: Sec. 3.1 (chunking, dual-quantization, Algorithm 2), Lorenzo
+// predictor with binomial coefficients (order 1), Sec. 3.2.1 (histogram),
+// valrel footnote of Sec. 3.2.2.
+//
+// Unlike the paper's per-block zero padding, one predictor covers the whole
+// field: every tile computes the prequantized integers of a one-point halo on
+// its low side itself, so tiles are independent and the output does not
+// depend on the tile shape.
+#include "common.cuh"
+
+#include <algorithm>
+
+namespace gbsz {
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// S0
+
+__device__ __forceinline__ uint32_t ordered_key(float f)
+{
+    const uint32_t b = __float_as_uint(f);
+    return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+__device__ __forceinline__ float key_to_float(uint32_t k)
+{
+    return __uint_as_float((k & 0x80000000u) ? (k & 0x7FFFFFFFu) : ~k);
+}
+
+// eb = rel * (max - min) over finite values (valrel), or the absolute bound;
+// 2eb as a float product; 1/(2eb) rounded from double.
+__device__ void finalize_eb(Control *ctl, double eb, uint32_t mode, uint32_t kmax, uint32_t kmin_inv)
+{
+    float e;
+    if (mode == 1 && kmax != 0) {
+        const float hi = key_to_float(kmax), lo = key_to_float(~kmin_inv);
+        const double range = __dsub_rn((double)hi, (double)lo);
+        e = range == 0.0 ? __double2float_rn(eb) : __double2float_rn(__dmul_rn(eb, range));
+    } else {
+        e = __double2float_rn(eb);
+    }
+    const float e2 = __fmul_rn(e, 2.0f);
+    const float inv = __double2float_rn(__ddiv_rn(1.0, (double)e2));
+    const bool ok = e > 0.0f && isfinite(e) && isfinite(e2) && isfinite(inv) && inv > 0.0f;
+    ctl->eb = e;
+    ctl->ebx2 = e2;
+    ctl->inv2eb = inv;
+    if (!ok) atomicOr(&ctl->error, DERR_EB);
+}
+
+__device__ __forceinline__ void mm_update(float v, uint32_t &kmax, uint32_t &kmin)
+{
+    if ((__float_as_uint(v) & 0x7F800000u) != 0x7F800000u) {
+        const uint32_t k = ordered_key(v);
+        kmax = max(kmax, k);
+        kmin = max(kmin, ~k);
+    }
+}
+
+template <bool VEC>
+__global__ void __launch_bounds__(256) k_minmax(const float *__restrict__ x, uint64_t n, Control *ctl,
+                                                double eb, uint32_t mode)
+{
+    uint32_t kmax = 0, kmin = 0;
+    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    if (VEC) {
+        const float4 *x4 = reinterpret_cast<const float4 *>(x);
+        const uint64_t n4 = n / 4;
+        uint64_t i = tid;
+        for (; i + 3 * stride < n4; i += 4 * stride) {
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; u++) v[u] = x4[i + u * stride];
+#pragma unroll
+            for (int u = 0; u < 4; u++) {
+                mm_update(v[u].x, kmax, kmin);
+                mm_update(v[u].y, kmax, kmin);
+                mm_update(v[u].z, kmax, kmin);
+                mm_update(v[u].w, kmax, kmin);
+            }
+        }
+        for (; i < n4; i += stride) {
+            const float4 v = x4[i];
+            mm_update(v.x, kmax, kmin);
+            mm_update(v.y, kmax, kmin);
+            mm_update(v.z, kmax, kmin);
+            mm_update(v.w, kmax, kmin);
+        }
+        for (uint64_t j = n4 * 4 + tid; j < n; j += stride) mm_update(x[j], kmax, kmin);
+    } else {
+        for (uint64_t j = tid; j < n; j += stride) mm_update(x[j], kmax, kmin);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
+        kmin = max(kmin, __shfl_xor_sync(0xffffffffu, kmin, o));
+    }
+    __shared__ uint32_t s_max[8], s_min[8];
+    __shared__ bool s_last;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    if (lane == 0) {
+        s_max[warp] = kmax;
+        s_min[warp] = kmin;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); w++) {
+            kmax = max(kmax, s_max[w]);
+            kmin = max(kmin, s_min[w]);
+        }
+        if (kmax) atomicMax(&ctl->max_key, kmax);
+        if (kmin) atomicMax(&ctl->min_key_inv, kmin);
+        __threadfence();
+        s_last = atomicAdd(&ctl->s0_done, 1u) == gridDim.x - 1;
+    }
+    __syncthreads();
+    if (s_last && threadIdx.x == 0) {
+        __threadfence();
+        const uint32_t km = atomicAdd(&ctl->max_key, 0u);
+        const uint32_t kn = atomicAdd(&ctl->min_key_inv, 0u);
+        finalize_eb(ctl, eb, mode, km, kn);
+    }
+}
+
+__global__ void k_eb_abs(Control *ctl, double eb) { finalize_eb(ctl, eb, 0, 0, 0); }
+
+// ---------------------------------------------------------------------------
+// S1-S3 shared pieces
+
+// Histogram: full 2R bins in shared memory when 2R <= kWinBins, else a
+// window of kWinBins bins centred on R with global atomics outside it.  The
+// three central codes R-1, R, R+1 are counted in registers first.
+constexpr uint32_t kWinBins = 8192;
+
+struct HistState {
+    uint32_t *sh;   // shared bins
+    uint32_t lo;    // first bin held in shared memory
+    uint32_t nsh;   // bins held in shared memory
+    uint32_t R;
+    uint32_t c_lo, c_mid, c_hi;
+    uint32_t n_out, n_exc;
+};
+
+__device__ __forceinline__ void hist_add(HistState &h, uint32_t code, uint32_t *ghist)
+{
+    if (code == h.R) {
+        h.c_mid++;
+    } else if (code == h.R - 1) {
+        h.c_lo++;
+    } else if (code == h.R + 1) {
+        h.c_hi++;
+    } else {
+        const uint32_t b = code - h.lo;
+        if (b < h.nsh) atomicAdd(&h.sh[b], 1u);
+        else atomicAdd(&ghist[code], 1u);
+    }
+}
+
+__device__ __forceinline__ void hist_init(HistState &h, uint32_t *sh, uint32_t R)
+{
+    h.sh = sh;
+    h.R = R;
+    const uint32_t nbins = 2 * R;
+    if (nbins <= kWinBins) {
+        h.lo = 0;
+        h.nsh = nbins;
+    } else {
+        h.lo = R - kWinBins / 2;
+        h.nsh = kWinBins;
+    }
+    h.c_lo = h.c_mid = h.c_hi = 0;
+    h.n_out = h.n_exc = 0;
+    for (uint32_t i = threadIdx.x; i < h.nsh; i += blockDim.x) sh[i] = 0;
+}
+
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+__device__ void hist_flush(HistState &h, uint32_t *ghist, Control *ctl)
+{
+    const uint32_t lo = warp_sum(h.c_lo), mid = warp_sum(h.c_mid), hi = warp_sum(h.c_hi);
+    const uint32_t no = warp_sum(h.n_out), ne = warp_sum(h.n_exc);
+    __syncthreads();  // every shared atomic of the block has landed
+    if ((threadIdx.x & 31) == 0) {
+        if (lo) atomicAdd(&h.sh[h.R - 1 - h.lo], lo);
+        if (mid) atomicAdd(&h.sh[h.R - h.lo], mid);
+        if (hi) atomicAdd(&h.sh[h.R + 1 - h.lo], hi);
+        if (no) atomicAdd(&ctl->n_out, (unsigned long long)no);
+        if (ne) atomicAdd(&ctl->n_exc, (unsigned long long)ne);
+    }
+    __syncthreads();
+    for (uint32_t i = threadIdx.x; i < h.nsh; i += blockDim.x) {
+        const uint32_t v = h.sh[i];
+        if (v) atomicAdd(&ghist[h.lo + i], v);
+    }
+}
+
+// emit one point: code, outlier residual, histogram
+__device__ __forceinline__ uint32_t emit_point(HistState &h, const QuantArgs &a, uint64_t idx,
+                                               uint32_t delta, bool exc)
+{
+    const uint32_t code = postquant(delta, exc, (int32_t)h.R);
+    if (code == 0) {
+        a.dscr[idx] = (int32_t)delta;
+        h.n_out++;
+    }
+    h.n_exc += exc;
+    hist_add(h, code, a.hist);
+    return code;
+}
+
+// ---------------------------------------------------------------------------
+// 1D: 256 threads, tile of 2048 points as two block-strided groups of 4
+// consecutive points per thread (float4 loads, 8-byte code stores).  The left
+// neighbour of a group comes from the previous lane; lane 0 recomputes it.
+
+constexpr int kQ1Threads = 256;
+constexpr int kQ1Tile = 2048;
+
+template <bool VEC>
+__global__ void __launch_bounds__(kQ1Threads) k_dualquant_1d(QuantArgs a, uint64_t ntiles)
+{
+    extern __shared__ uint32_t sh_hist[];
+    HistState h;
+    hist_init(h, sh_hist, a.radius);
+    __syncthreads();
+    if (a.ctl->error & DERR_EB) return;
+    const EbScalars sc = load_scalars(a.ctl);
+    const uint64_t n = a.dims[0];
+    const int lane = threadIdx.x & 31;
+    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint64_t base = tile * kQ1Tile;
+#pragma unroll
+        for (int g = 0; g < 2; g++) {
+            const uint64_t e0 = base + (uint64_t)g * (kQ1Tile / 2) + threadIdx.x * 4u;
+            float v[4];
+            const bool full = e0 + 3 < n;
+            if (VEC && full) {
+                const float4 f = *reinterpret_cast<const float4 *>(a.x + e0);
+                v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; j++) v[j] = e0 + j < n ? a.x[e0 + j] : 0.0f;
+            }
+            int32_t q[4];
+            bool ex[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) q[j] = prequant(v[j], sc, ex[j]);
+            int32_t qp = __shfl_up_sync(0xffffffffu, q[3], 1);
+            if (lane == 0) {
+                if (e0 == 0 || e0 > n) {
+                    qp = 0;
+                } else {
+                    bool dummy;
+                    qp = prequant(a.x[e0 - 1], sc, dummy);
+                }
+            }
+            uint32_t code[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint32_t d = (uint32_t)q[j] - (uint32_t)(j ? q[j - 1] : qp);
+                code[j] = 0;
+                if (e0 + j < n) code[j] = emit_point(h, a, e0 + j, d, ex[j]);
+            }
+            if (full) {
+                uint2 w;
+                w.x = code[0] | (code[1] << 16);
+                w.y = code[2] | (code[3] << 16);
+                *reinterpret_cast<uint2 *>(a.codes + e0) = w;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    if (e0 + j < n) a.codes[e0 + j] = (uint16_t)code[j];
+            }
+        }
+    }
+    hist_flush(h, a.hist, a.ctl);
+}
+
+// ---------------------------------------------------------------------------
+// 2D: 128 threads; tile 512 (x) x 32 (y) swept row by row.  Each thread holds
+// 4 points of a row (x = x0 + tid + 128 j).  Three row buffers of prequantized
+// integers in shared memory (slot 0 = the halo column x0 - 1); the next row's
+// floats are prefetched into registers while the current row is processed.
+
+constexpr int kQ2Threads = 128;
+constexpr int kQ2TX = 512;
+constexpr int kQ2TY = 32;
+
+__global__ void __launch_bounds__(kQ2Threads) k_dualquant_2d(QuantArgs a, uint32_t ntx, uint32_t nty)
+{
+    extern __shared__ uint32_t sh_hist[];
+    __shared__ int32_t rows[3][kQ2TX + 1];
+    HistState h;
+    hist_init(h, sh_hist, a.radius);
+    __syncthreads();
+    if (a.ctl->error & DERR_EB) return;
+    const EbScalars sc = load_scalars(a.ctl);
+    const uint64_t nx = a.dims[0], ny = a.dims[1];
+    const uint32_t ntiles = ntx * nty;
+    int buf = 0;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint64_t x0 = (uint64_t)(tile % ntx) * kQ2TX;
+        const int64_t y0 = (int64_t)(tile / ntx) * kQ2TY;
+        const int64_t y1 = min((int64_t)ny, y0 + kQ2TY);
+        float cur[4], nxt[4], hcur = 0.0f, hnxt = 0.0f;
+        auto load_row = [&](int64_t y, float *v, float &hv) {
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint64_t x = x0 + threadIdx.x + 128u * j;
+                v[j] = (y >= 0 && x < nx) ? a.x[(uint64_t)y * nx + x] : 0.0f;
+            }
+            if (threadIdx.x == 0) hv = (y >= 0 && x0 > 0) ? a.x[(uint64_t)y * nx + x0 - 1] : 0.0f;
+        };
+        load_row(y0 - 1, cur, hcur);
+        for (int64_t y = y0 - 1; y < y1; y++) {
+            if (y + 1 < y1) load_row(y + 1, nxt, hnxt);
+            int32_t q[4];
+            bool ex[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const uint64_t x = x0 + threadIdx.x + 128u * j;
+                q[j] = 0;
+                ex[j] = false;
+                if (y >= 0 && x < nx) q[j] = prequant(cur[j], sc, ex[j]);
+                rows[buf][1 + threadIdx.x + 128 * j] = q[j];
+            }
+            if (threadIdx.x == 0) {
+                bool dummy;
+                rows[buf][0] = (y >= 0 && x0 > 0) ? prequant(hcur, sc, dummy) : 0;
+            }
+            __syncthreads();
+            if (y >= y0) {
+                const int prev = buf == 0 ? 2 : buf - 1;
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const uint32_t lx = threadIdx.x + 128u * j;
+                    const uint64_t x = x0 + lx;
+                    if (x < nx) {
+                        const uint32_t d = (uint32_t)q[j] - (uint32_t)rows[buf][lx] -
+                                           (uint32_t)rows[prev][lx + 1] + (uint32_t)rows[prev][lx];
+                        const uint64_t idx = (uint64_t)y * nx + x;
+                        a.codes[idx] = (uint16_t)emit_point(h, a, idx, d, ex[j]);
+                    }
+                }
+            }
+            buf = buf == 2 ? 0 : buf + 1;
+#pragma unroll
+            for (int j = 0; j < 4; j++) cur[j] = nxt[j];
+            hcur = hnxt;
+        }
+    }
+    hist_flush(h, a.hist, a.ctl);
+}
+
+// ---------------------------------------------------------------------------
+// 3D: 256 threads; tile 32 (x) x 32 (y) swept along z over tz planes.  Thread
+// (lx = tid % 32, ly = tid / 32 + 8 j) holds 4 points of a plane.  Threads
+// 0..64 also prequantize one halo point each: the column x0 - 1 for
+// y0-1..y0+31 and the row y0 - 1 for x0..x0+31.  Three plane buffers.
+
+constexpr int kQ3Threads = 256;
+constexpr int kQ3T = 32;
+
+__global__ void __launch_bounds__(kQ3Threads) k_dualquant_3d(QuantArgs a, uint32_t ntx, uint32_t nty,
+                                                             uint32_t ntz, uint32_t tz)
+{
+    extern __shared__ uint32_t sh_hist[];
+    __shared__ int32_t pl[3][kQ3T + 1][kQ3T + 1];
+    HistState h;
+    hist_init(h, sh_hist, a.radius);
+    __syncthreads();
+    if (a.ctl->error & DERR_EB) return;
+    const EbScalars sc = load_scalars(a.ctl);
+    const int64_t nx = a.dims[0], ny = a.dims[1], nz = a.dims[2];
+    const uint32_t ntiles = ntx * nty * ntz;
+    const int lx = threadIdx.x & 31, ly0 = threadIdx.x >> 5;
+    // halo point of this thread (if any), as plane-local coordinates (+1 offset)
+    int hx = -2, hy = -2;
+    if (threadIdx.x < 33) {
+        hx = -1;
+        hy = (int)threadIdx.x - 1;
+    } else if (threadIdx.x < 65) {
+        hx = (int)threadIdx.x - 33;
+        hy = -1;
+    }
+    int buf = 0;
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const int64_t x0 = (int64_t)(tile % ntx) * kQ3T;
+        const int64_t y0 = (int64_t)((tile / ntx) % nty) * kQ3T;
+        const int64_t z0 = (int64_t)(tile / (ntx * nty)) * tz;
+        const int64_t z1 = min(nz, z0 + (int64_t)tz);
+        const int64_t gx = x0 + lx;
+        const int64_t ghx = x0 + hx, ghy = y0 + hy;
+        const bool has_halo = hx > -2;
+        const bool halo_in = has_halo && ghx >= 0 && ghy >= 0 && ghx < nx && ghy < ny;
+        float cur[4], nxt[4], hcur = 0.0f, hnxt = 0.0f;
+        auto load_plane = [&](int64_t z, float *v, float &hv) {
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int64_t gy = y0 + ly0 + 8 * j;
+                v[j] = (z >= 0 && gx < nx && gy < ny) ? a.x[((uint64_t)z * ny + gy) * nx + gx] : 0.0f;
+            }
+            hv = (z >= 0 && halo_in) ? a.x[((uint64_t)z * ny + ghy) * nx + ghx] : 0.0f;
+        };
+        load_plane(z0 - 1, cur, hcur);
+        for (int64_t z = z0 - 1; z < z1; z++) {
+            if (z + 1 < z1) load_plane(z + 1, nxt, hnxt);
+            int32_t q[4];
+            bool ex[4];
+#pragma unroll
+            for (int j = 0; j < 4; j++) {
+                const int64_t gy = y0 + ly0 + 8 * j;
+                q[j] = 0;
+                ex[j] = false;
+                if (z >= 0 && gx < nx && gy < ny) q[j] = prequant(cur[j], sc, ex[j]);
+                pl[buf][ly0 + 8 * j + 1][lx + 1] = q[j];
+            }
+            if (has_halo) {
+                bool dummy;
+                pl[buf][hy + 1][hx + 1] = (z >= 0 && halo_in) ? prequant(hcur, sc, dummy) : 0;
+            }
+            __syncthreads();
+            if (z >= z0) {
+                const int prev = buf == 0 ? 2 : buf - 1;
+                const int X = lx + 1;
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    const int Y = ly0 + 8 * j + 1;
+                    const int64_t gy = y0 + Y - 1;
+                    if (gx < nx && gy < ny) {
+                        const uint32_t(*c)[kQ3T + 1] = (const uint32_t(*)[kQ3T + 1])pl[buf];
+                        const uint32_t(*p)[kQ3T + 1] = (const uint32_t(*)[kQ3T + 1])pl[prev];
+                        const uint32_t d = c[Y][X] - c[Y][X - 1] - c[Y - 1][X] - p[Y][X] +
+                                           c[Y - 1][X - 1] + p[Y][X - 1] + p[Y - 1][X] - p[Y - 1][X - 1];
+                        const uint64_t idx = ((uint64_t)z * ny + gy) * nx + gx;
+                        a.codes[idx] = (uint16_t)emit_point(h, a, idx, d, ex[j]);
+                    }
+                }
+            }
+            buf = buf == 2 ? 0 : buf + 1;
+#pragma unroll
+            for (int j = 0; j < 4; j++) cur[j] = nxt[j];
+            hcur = hnxt;
+        }
+    }
+    hist_flush(h, a.hist, a.ctl);
+}
+
+}  // namespace
+
+void launch_minmax_eb(const float *x, uint64_t n, Control *ctl, double eb, uint32_t mode, int num_sms,
+                      cudaStream_t st)
+{
+    if (mode == 0) {
+        k_eb_abs<<<1, 1, 0, st>>>(ctl, eb);
+        return;
+    }
+    const uint64_t need = (n / 4 + 255) / 256;
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)num_sms * 8));
+    if ((reinterpret_cast<uintptr_t>(x) & 15) == 0)
+        k_minmax<true><<<grid, 256, 0, st>>>(x, n, ctl, eb, mode);
+    else
+        k_minmax<false><<<grid, 256, 0, st>>>(x, n, ctl, eb, mode);
+}
+
+void launch_dualquant(const QuantArgs &a, cudaStream_t st)
+{
+    const uint32_t nbins = 2 * a.radius;
+    const size_t hist_bytes = sizeof(uint32_t) * std::min<uint32_t>(nbins, kWinBins);
+    if (a.ndim == 1) {
+        const uint64_t n = a.dims[0];
+        const uint64_t ntiles = (n + kQ1Tile - 1) / kQ1Tile;
+        const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)a.num_sms * 8);
+        if ((reinterpret_cast<uintptr_t>(a.x) & 15) == 0)
+            k_dualquant_1d<true><<<grid, kQ1Threads, hist_bytes, st>>>(a, ntiles);
+        else
+            k_dualquant_1d<false><<<grid, kQ1Threads, hist_bytes, st>>>(a, ntiles);
+    } else if (a.ndim == 2) {
+        const uint32_t ntx = (uint32_t)((a.dims[0] + kQ2TX - 1) / kQ2TX);
+        const uint32_t nty = (uint32_t)((a.dims[1] + kQ2TY - 1) / kQ2TY);
+        const uint64_t ntiles = (uint64_t)ntx * nty;
+        const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)a.num_sms * 12);
+        k_dualquant_2d<<<grid, kQ2Threads, hist_bytes, st>>>(a, ntx, nty);
+    } else {
+        const uint32_t ntx = (uint32_t)((a.dims[0] + kQ3T - 1) / kQ3T);
+        const uint32_t nty = (uint32_t)((a.dims[1] + kQ3T - 1) / kQ3T);
+        const uint64_t nz = a.dims[2];
+        uint64_t tz = nz;
+        while (tz > 4 && (uint64_t)ntx * nty * ((nz + tz - 1) / tz) < (uint64_t)a.num_sms * 8) tz = (tz + 1) / 2;
+        const uint32_t ntz = (uint32_t)((nz + tz - 1) / tz);
+        const uint64_t ntiles = (uint64_t)ntx * nty * ntz;
+        const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)a.num_sms * 8);
+        k_dualquant_3d<<<grid, kQ3Threads, hist_bytes, st>>>(a, ntx, nty, ntz, (uint32_t)tz);
+    }
+}
+
+}  // namespace gbsz

@@ -1,0 +1,418 @@
+// k_recon.cu -- S8: reversed dual-quantization (Algorithm 2, decompression;
+// Sec. 3.3).
+//
+// The paper reconstructs cascadingly per chunk.  Since the order-1 Lorenzo
+// residual is the d-dimensional first difference of the prequantized
+// integers, reconstruction is the d-dimensional inclusive prefix sum of the
+// residuals (modulo 2^32), computed here without any inter-CTA waiting:
+//   1. outlier scatter: the residual of every code-0 point goes to a per-point
+//      scratch array (indices checked: ascending, in range, code 0);
+//   2. faces: each tile computes its local prefix sum L and publishes, for
+//      every non-empty subset A of the dimensions, L taken at the tile's last
+//      coordinate along A as a function of the other coordinates (1D: the
+//      tile total; 2D: last column, last row, total; 3D: 3 faces, 3 edges,
+//      total);
+//   3. carries: inclusive scans of each published array along the tile grid
+//      dimensions in A;
+//   4. values: S = L + sum over A of the scanned array of the tile that
+//      precedes this one along every dimension of A, at this point's other
+//      coordinates; d' = fl(2eb * fl((float)S)); then verbatim exceptions.
+#include "common.cuh"
+
+#include <algorithm>
+
+namespace gbsz {
+
+namespace {
+
+struct Geo {
+    uint32_t ndim;
+    uint64_t n[3];      // field extents
+    uint32_t T[3];      // tile extents
+    uint32_t nt[3];     // tiles per dimension
+    uint64_t ntiles;
+    uint64_t size[8];   // entries per tile of the array of subset A
+    uint64_t off[8];    // start of the array of subset A in the carry scratch
+};
+
+constexpr int k1Threads = 256;
+constexpr int k1PerThread = 16;
+constexpr int k1Tile = k1Threads * k1PerThread;  // 4096
+constexpr int k2TX = 128, k2TY = 32, k2Threads = 256;
+constexpr int k3TX = 32, k3TY = 16, k3TZ = 16, k3Threads = 512;
+
+Geo make_geo(uint32_t ndim, const uint64_t dims[3])
+{
+    Geo g{};
+    g.ndim = ndim;
+    for (int d = 0; d < 3; d++) g.n[d] = d < (int)ndim ? dims[d] : 1;
+    if (ndim == 1) {
+        g.T[0] = k1Tile; g.T[1] = 1; g.T[2] = 1;
+    } else if (ndim == 2) {
+        g.T[0] = k2TX; g.T[1] = k2TY; g.T[2] = 1;
+    } else {
+        g.T[0] = k3TX; g.T[1] = k3TY; g.T[2] = k3TZ;
+    }
+    g.ntiles = 1;
+    for (int d = 0; d < 3; d++) {
+        g.nt[d] = (uint32_t)((g.n[d] + g.T[d] - 1) / g.T[d]);
+        g.ntiles *= g.nt[d];
+    }
+    uint64_t off = 0;
+    for (int A = 1; A < 8; A++) {
+        bool used = true;
+        for (int d = 0; d < 3; d++)
+            if ((A >> d) & 1) used &= d < (int)ndim;
+        uint64_t s = 1;
+        for (int d = 0; d < (int)ndim; d++)
+            if (!((A >> d) & 1)) s *= g.T[d];
+        g.size[A] = used ? s : 0;
+        g.off[A] = off;
+        off += used ? s * g.ntiles : 0;
+    }
+    g.off[0] = off;  // total entries
+    return g;
+}
+
+__device__ __forceinline__ uint32_t delta_of(const ReconArgs &a, uint64_t i)
+{
+    const uint32_t c = a.codes[i];
+    return c ? c - a.radius : (uint32_t)a.dscr[i];
+}
+
+// ---------------------------------------------------------------------------
+// 1. outliers
+
+__global__ void k_scatter_outliers(ReconArgs a, uint64_t n)
+{
+    const uint8_t *o = a.archive + a.off_outl;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.m;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t idx = *reinterpret_cast<const uint32_t *>(o + 8 * t);
+        const int32_t d = *reinterpret_cast<const int32_t *>(o + 8 * t + 4);
+        bool ok = idx < n;
+        if (t > 0) ok &= idx > *reinterpret_cast<const uint32_t *>(o + 8 * (t - 1));
+        if (ok) ok &= a.codes[idx] == 0;
+        if (ok) a.dscr[idx] = d;
+        else atomicOr(&a.ctl->error, DERR_CORRUPT);
+    }
+}
+
+__global__ void k_patch_exceptions(ReconArgs a, uint64_t n)
+{
+    const uint8_t *e = a.archive + a.off_exc;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.e;
+         t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t idx = *reinterpret_cast<const uint32_t *>(e + 8 * t);
+        const uint32_t raw = *reinterpret_cast<const uint32_t *>(e + 8 * t + 4);
+        bool ok = idx < n;
+        if (t > 0) ok &= idx > *reinterpret_cast<const uint32_t *>(e + 8 * (t - 1));
+        if (ok) ok &= a.codes[idx] == 0;
+        if (ok) reinterpret_cast<uint32_t *>(a.out)[idx] = raw;
+        else atomicOr(&a.ctl->error, DERR_CORRUPT);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 1D tiles: 4096 points, 16 consecutive per thread, block scan of totals
+
+__device__ __forceinline__ void load16_delta(const ReconArgs &a, uint64_t n, uint64_t s0, uint32_t *d)
+{
+    if (s0 + 16 <= n) {
+        const uint4 *p = reinterpret_cast<const uint4 *>(a.codes + s0);
+        const uint4 w0 = p[0], w1 = p[1];
+        const uint32_t w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            const uint32_t c = (w[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu;
+            d[j] = c ? c - a.radius : (uint32_t)a.dscr[s0 + j];
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < 16; j++) d[j] = s0 + j < n ? delta_of(a, s0 + j) : 0u;
+    }
+}
+
+__global__ void __launch_bounds__(k1Threads) k_faces_1d(ReconArgs a, Geo g, uint32_t *F)
+{
+    __shared__ uint32_t sh[33];
+    if (a.ctl->error & DERR_CORRUPT) return;
+    const uint64_t n = g.n[0];
+    for (uint64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+        uint32_t d[16];
+        load16_delta(a, n, tile * k1Tile + (uint64_t)threadIdx.x * 16, d);
+        uint32_t s = 0;
+#pragma unroll
+        for (int j = 0; j < 16; j++) s += d[j];
+        uint32_t tot;
+        block_excl_scan(s, sh, &tot);
+        if (threadIdx.x == 0) F[g.off[1] + tile] = tot;
+    }
+}
+
+__global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, const uint32_t *F)
+{
+    __shared__ uint32_t sh[33];
+    if (a.ctl->error & DERR_CORRUPT) return;
+    const uint64_t n = g.n[0];
+    const float ebx2 = a.ebx2;
+    for (uint64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+        const uint64_t s0 = tile * k1Tile + (uint64_t)threadIdx.x * 16;
+        uint32_t d[16];
+        load16_delta(a, n, s0, d);
+        uint32_t s = 0;
+#pragma unroll
+        for (int j = 0; j < 16; j++) {
+            s += d[j];
+            d[j] = s;
+        }
+        uint32_t tot;
+        uint32_t pre = block_excl_scan(s, sh, &tot);
+        pre += tile ? F[g.off[1] + tile - 1] : 0u;
+        float v[16];
+#pragma unroll
+        for (int j = 0; j < 16; j++) v[j] = recon_value((int32_t)(d[j] + pre), ebx2);
+        if (s0 + 16 <= n) {
+            float4 *o = reinterpret_cast<float4 *>(a.out + s0);
+#pragma unroll
+            for (int j = 0; j < 4; j++) o[j] = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; j++)
+                if (s0 + j < n) a.out[s0 + j] = v[j];
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 2D / 3D tiles through shared memory
+
+template <int TX, int TY, int TZ, int NT>
+__device__ void tile_prefix(const ReconArgs &a, const Geo &g, uint64_t tile, uint32_t *sm)
+{
+    constexpr int NE = TX * TY * TZ;
+    const uint64_t tx = tile % g.nt[0], ty = (tile / g.nt[0]) % g.nt[1], tz = tile / ((uint64_t)g.nt[0] * g.nt[1]);
+    const uint64_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
+    for (int l = threadIdx.x; l < NE; l += NT) {
+        const int x = l % TX, y = (l / TX) % TY, z = l / (TX * TY);
+        const uint64_t gx = x0 + x, gy = y0 + y, gz = z0 + z;
+        uint32_t v = 0;
+        if (gx < g.n[0] && gy < g.n[1] && gz < g.n[2]) v = delta_of(a, (gz * g.n[1] + gy) * g.n[0] + gx);
+        sm[l] = v;
+    }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int line = warp; line < TY * TZ; line += NT / 32) {
+        uint32_t carry = 0;
+        for (int seg = 0; seg < TX / 32; seg++) {
+            const int idx = line * TX + seg * 32 + lane;
+            const uint32_t v = warp_incl_scan(sm[idx]) + carry;
+            sm[idx] = v;
+            carry = __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+    __syncthreads();
+    if (TY > 1) {
+        for (int line = threadIdx.x; line < TX * TZ; line += NT) {
+            const int x = line % TX, z = line / TX;
+            uint32_t run = 0;
+            for (int y = 0; y < TY; y++) {
+                const int idx = (z * TY + y) * TX + x;
+                run += sm[idx];
+                sm[idx] = run;
+            }
+        }
+        __syncthreads();
+    }
+    if (TZ > 1) {
+        for (int line = threadIdx.x; line < TX * TY; line += NT) {
+            uint32_t run = 0;
+            for (int z = 0; z < TZ; z++) {
+                const int idx = z * TX * TY + line;
+                run += sm[idx];
+                sm[idx] = run;
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// local index, inside the array of subset A, of the point (x, y, z)
+template <int TX, int TY, int TZ>
+__device__ __forceinline__ int comp_index(int A, int x, int y, int z)
+{
+    int ci = 0, mul = 1;
+    if (!(A & 1)) { ci += x * mul; mul *= TX; }
+    if (!(A & 2)) { ci += y * mul; mul *= TY; }
+    if (!(A & 4)) { ci += z * mul; }
+    return ci;
+}
+
+template <int TX, int TY, int TZ, int NT>
+__global__ void __launch_bounds__(NT) k_faces(ReconArgs a, Geo g, uint32_t *F)
+{
+    __shared__ uint32_t sm[TX * TY * TZ];
+    if (a.ctl->error & DERR_CORRUPT) return;
+    const int nA = g.ndim == 2 ? 3 : 7;
+    for (uint64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+        tile_prefix<TX, TY, TZ, NT>(a, g, tile, sm);
+        for (int A = 1; A <= nA; A++) {
+            const uint64_t sz = g.size[A];
+            uint32_t *dst = F + g.off[A] + tile * sz;
+            for (int ci = threadIdx.x; ci < (int)sz; ci += NT) {
+                // complement coordinates from ci, A coordinates at the last index
+                int r = ci, x = TX - 1, y = TY - 1, z = TZ - 1;
+                if (!(A & 1)) { x = r % TX; r /= TX; }
+                if (!(A & 2)) { y = r % TY; r /= TY; }
+                if (!(A & 4)) { z = r; }
+                dst[ci] = sm[(z * TY + y) * TX + x];
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <int TX, int TY, int TZ, int NT>
+__global__ void __launch_bounds__(NT) k_values(ReconArgs a, Geo g, const uint32_t *F)
+{
+    __shared__ uint32_t sm[TX * TY * TZ];
+    __shared__ uint32_t carry[TX * TY + TX * TZ + TY * TZ + TX + TY + TZ + 1];
+    if (a.ctl->error & DERR_CORRUPT) return;
+    const int nA = g.ndim == 2 ? 3 : 7;
+    const float ebx2 = a.ebx2;
+    for (uint64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+        const uint64_t tc[3] = {tile % g.nt[0], (tile / g.nt[0]) % g.nt[1], tile / ((uint64_t)g.nt[0] * g.nt[1])};
+        // stage the carries of every subset
+        int cbase[8];
+        int cb = 0;
+        for (int A = 1; A <= nA; A++) {
+            const int sz = (int)g.size[A];
+            cbase[A] = cb;
+            bool has = true;
+            uint64_t pt[3];
+            for (int d = 0; d < 3; d++) {
+                pt[d] = tc[d];
+                if ((A >> d) & 1) {
+                    has &= tc[d] > 0;
+                    pt[d] = tc[d] - 1;
+                }
+            }
+            const uint64_t ptile = (pt[2] * g.nt[1] + pt[1]) * g.nt[0] + pt[0];
+            const uint32_t *src = F + g.off[A] + ptile * (uint64_t)sz;
+            for (int ci = threadIdx.x; ci < sz; ci += NT) carry[cb + ci] = has ? src[ci] : 0u;
+            cb += sz;
+        }
+        tile_prefix<TX, TY, TZ, NT>(a, g, tile, sm);
+        const uint64_t x0 = tc[0] * TX, y0 = tc[1] * TY, z0 = tc[2] * TZ;
+        for (int l = threadIdx.x; l < TX * TY * TZ; l += NT) {
+            const int x = l % TX, y = (l / TX) % TY, z = l / (TX * TY);
+            const uint64_t gx = x0 + x, gy = y0 + y, gz = z0 + z;
+            if (gx < g.n[0] && gy < g.n[1] && gz < g.n[2]) {
+                uint32_t s = sm[l];
+                for (int A = 1; A <= nA; A++) s += carry[cbase[A] + comp_index<TX, TY, TZ>(A, x, y, z)];
+                a.out[(gz * g.n[1] + gy) * g.n[0] + gx] = recon_value((int32_t)s, ebx2);
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// ---------------------------------------------------------------------------
+// 3. inclusive scans of a subset's array along one tile-grid dimension
+
+__device__ __forceinline__ uint64_t line_base(const Geo &g, int A, int d, uint64_t line, uint64_t &stride)
+{
+    const uint64_t sz = g.size[A];
+    const uint64_t ci = line % sz;
+    uint64_t r = line / sz;
+    uint64_t c[3] = {0, 0, 0};
+    for (int e = 0; e < 3; e++) {
+        if (e == d) continue;
+        c[e] = r % g.nt[e];
+        r /= g.nt[e];
+    }
+    const uint64_t tile = (c[2] * g.nt[1] + c[1]) * g.nt[0] + c[0];
+    stride = sz * (d == 0 ? 1 : d == 1 ? g.nt[0] : (uint64_t)g.nt[0] * g.nt[1]);
+    return g.off[A] + tile * sz + ci;
+}
+
+__global__ void k_scan_lines(Geo g, int A, int d, uint64_t nlines, uint32_t *F)
+{
+    const uint64_t line = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (line >= nlines) return;
+    uint64_t stride;
+    uint64_t p = line_base(g, A, d, line, stride);
+    uint32_t run = 0;
+    for (uint32_t i = 0; i < g.nt[d]; i++, p += stride) {
+        run += F[p];
+        F[p] = run;
+    }
+}
+
+// one CTA per long line
+__global__ void __launch_bounds__(1024) k_scan_lines_cta(Geo g, int A, int d, uint32_t *F)
+{
+    __shared__ uint32_t sh[33];
+    uint64_t stride;
+    const uint64_t p0 = line_base(g, A, d, blockIdx.x, stride);
+    const uint32_t len = g.nt[d], T = blockDim.x, t = threadIdx.x;
+    const uint32_t per = (len + T - 1) / T;
+    const uint32_t lo = min(len, t * per), hi = min(len, lo + per);
+    uint32_t s = 0;
+    for (uint32_t i = lo; i < hi; i++) s += F[p0 + i * stride];
+    uint32_t tot;
+    uint32_t run = block_excl_scan(s, sh, &tot);
+    for (uint32_t i = lo; i < hi; i++) {
+        run += F[p0 + i * stride];
+        F[p0 + i * stride] = run;
+    }
+}
+
+}  // namespace
+
+uint64_t recon_faces_entries(uint32_t ndim, const uint64_t dims[3])
+{
+    return make_geo(ndim, dims).off[0];
+}
+
+void launch_reconstruct(const ReconArgs &a, cudaStream_t st, int *launches)
+{
+    const Geo g = make_geo(a.ndim, a.dims);
+    const uint64_t n = g.n[0] * g.n[1] * g.n[2];
+    int nl = 0;
+    if (a.m) {
+        const int grid = (int)std::min<uint64_t>((a.m + 255) / 256, (uint64_t)a.num_sms * 16);
+        k_scatter_outliers<<<grid, 256, 0, st>>>(a, n);
+        nl++;
+    }
+    const int gridt = (int)std::min<uint64_t>(g.ntiles, (uint64_t)a.num_sms * 8);
+    if (g.ndim == 1) k_faces_1d<<<gridt, k1Threads, 0, st>>>(a, g, a.faces);
+    else if (g.ndim == 2) k_faces<k2TX, k2TY, 1, k2Threads><<<gridt, k2Threads, 0, st>>>(a, g, a.faces);
+    else k_faces<k3TX, k3TY, k3TZ, k3Threads><<<gridt, k3Threads, 0, st>>>(a, g, a.faces);
+    nl++;
+    for (int A = 1; A < 8; A++) {
+        if (!g.size[A]) continue;
+        for (int d = 0; d < (int)g.ndim; d++) {
+            if (!((A >> d) & 1) || g.nt[d] < 2) continue;
+            const uint64_t nlines = g.size[A] * (g.ntiles / g.nt[d]);
+            if (g.nt[d] > 2048) {
+                k_scan_lines_cta<<<(unsigned)nlines, 1024, 0, st>>>(g, A, d, a.faces);
+            } else {
+                k_scan_lines<<<(unsigned)((nlines + 255) / 256), 256, 0, st>>>(g, A, d, nlines, a.faces);
+            }
+            nl++;
+        }
+    }
+    if (g.ndim == 1) k_values_1d<<<gridt, k1Threads, 0, st>>>(a, g, a.faces);
+    else if (g.ndim == 2) k_values<k2TX, k2TY, 1, k2Threads><<<gridt, k2Threads, 0, st>>>(a, g, a.faces);
+    else k_values<k3TX, k3TY, k3TZ, k3Threads><<<gridt, k3Threads, 0, st>>>(a, g, a.faces);
+    nl++;
+    if (a.e) {
+        const int grid = (int)std::min<uint64_t>((a.e + 255) / 256, (uint64_t)a.num_sms * 16);
+        k_patch_exceptions<<<grid, 256, 0, st>>>(a, n);
+        nl++;
+    }
+    if (launches) *launches += nl;
+}
+
+}  // namespace gbsz

@@ -1,0 +1,245 @@
+"""Python binding of the C ABI in include/gbsz.h (argument marshalling only).
+
+Every step of compression and decompression runs in the CUDA kernels of
+libgbsz.so; this module only passes torch device pointers, sizes and the
+current CUDA stream.  There is no CPU fallback: if the library is missing
+or cannot load, every call raises.
+"""
+import ctypes as C
+import os
+
+import torch
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libgbsz.so")
+
+OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CORRUPT, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(8)
+EB_ABS, EB_REL = 0, 1
+NSTAGE = 8
+STAGES = ["error_bound", "dualquant_hist", "codebook", "encode_deflate", "decode_tables", "decode",
+          "reconstruct", "other"]
+DEBUG_CODES, DEBUG_HIST, DEBUG_SCALARS, DEBUG_DECODED, DEBUG_CODEWORDS = range(5)
+
+# every entry point of include/gbsz.h with its ctypes signature
+_P = C.c_void_p
+SIGNATURES = {
+    "gbsz_create": ([C.POINTER(C.c_void_p), C.c_int], C.c_int),
+    "gbsz_destroy": ([_P], None),
+    "gbsz_compress_bound": ([_P], C.c_size_t),
+    "gbsz_auto_chunk": ([_P], C.c_uint32),
+    "gbsz_compress": ([_P, _P, _P, _P, C.c_size_t, C.POINTER(C.c_size_t), _P], C.c_int),
+    "gbsz_decompress": ([_P, _P, C.c_size_t, _P, C.c_uint64, _P], C.c_int),
+    "gbsz_compress_host": ([_P, _P, _P, _P, C.c_size_t, C.POINTER(C.c_size_t), _P], C.c_int),
+    "gbsz_decompress_host": ([_P, _P, C.c_size_t, _P, C.c_uint64, _P], C.c_int),
+    "gbsz_archive_info": ([_P, C.c_size_t, _P, C.POINTER(C.c_uint64)], C.c_int),
+    "gbsz_status_str": ([C.c_int], C.c_char_p),
+    "gbsz_debug_copy": ([_P, C.c_int, _P, C.c_size_t], C.c_int),
+    "gbsz_profile_enable": ([_P, C.c_int], C.c_int),
+    "gbsz_profile_read": ([_P, _P, _P, C.POINTER(C.c_uint64)], C.c_int),
+}
+
+
+class GbszError(RuntimeError):
+    def __init__(self, status, what):
+        msg = status_str(status) if _lib is not None else str(status)
+        super().__init__(f"{what}: {msg} ({status})")
+        self.status = status
+
+
+class Params(C.Structure):
+    _fields_ = [("ndim", C.c_uint32), ("dims", C.c_uint64 * 3), ("eb", C.c_double),
+                ("eb_mode", C.c_uint32), ("radius", C.c_uint32), ("chunk", C.c_uint32)]
+
+
+_lib = None
+
+
+def load():
+    """Load libgbsz.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library {LIB_PATH} is not built; run __graft_entry__.build()")
+        L = C.CDLL(LIB_PATH)
+        for name, (args, res) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.argtypes = args
+            f.restype = res
+        _lib = L
+    return _lib
+
+
+def status_str(s):
+    return load().gbsz_status_str(int(s)).decode()
+
+
+def make_params(dims, eb, eb_mode=EB_REL, radius=512, chunk=0):
+    """dims: extents with the fastest-varying first (x, y, z)."""
+    dims = [int(d) for d in dims]
+    p = Params()
+    p.ndim = len(dims)
+    for i in range(3):
+        p.dims[i] = dims[i] if i < len(dims) else 1
+    p.eb, p.eb_mode, p.radius, p.chunk = float(eb), int(eb_mode), int(radius), int(chunk)
+    return p
+
+
+def field_dims(t):
+    """Extents of a C-ordered tensor, fastest first."""
+    return list(t.shape)[::-1]
+
+
+def compress_bound(dims, eb=1e-4, eb_mode=EB_REL, radius=512, chunk=0):
+    return load().gbsz_compress_bound(C.byref(make_params(dims, eb, eb_mode, radius, chunk)))
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+class Context:
+    """A device context; owns resident scratch (see gbsz_create)."""
+
+    def __init__(self, device=0):
+        L = load()
+        self.device = int(device)
+        h = C.c_void_p()
+        st = L.gbsz_create(C.byref(h), self.device)
+        if st != OK:
+            raise GbszError(st, "gbsz_create")
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            load().gbsz_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- device-buffer API -------------------------------------------------
+    def compress(self, field, eb, eb_mode=EB_REL, radius=512, chunk=0, out=None, stream=None):
+        """field: contiguous float32 CUDA tensor (C order, last axis fastest).
+        Returns (archive uint8 tensor on the device, nbytes)."""
+        assert field.is_cuda and field.dtype == torch.float32 and field.is_contiguous()
+        p = make_params(field_dims(field), eb, eb_mode, radius, chunk)
+        cap = load().gbsz_compress_bound(C.byref(p))
+        if cap == 0:
+            raise GbszError(ERR_INVALID_ARG, "compress_bound")
+        if out is None:
+            out = torch.empty(cap, dtype=torch.uint8, device=field.device)
+        nbytes = C.c_size_t()
+        st = load().gbsz_compress(self.h, C.c_void_p(field.data_ptr()), C.byref(p),
+                                  C.c_void_p(out.data_ptr()), out.numel(), C.byref(nbytes), _stream(stream))
+        if st != OK:
+            raise GbszError(st, "gbsz_compress")
+        return out, nbytes.value
+
+    def compress_status(self, field, params, out, stream=None):
+        """Raw status call: returns (status, nbytes) without raising."""
+        nbytes = C.c_size_t()
+        st = load().gbsz_compress(self.h, C.c_void_p(field.data_ptr()), C.byref(params),
+                                  C.c_void_p(out.data_ptr()), out.numel(), C.byref(nbytes), _stream(stream))
+        return st, nbytes.value
+
+    def decompress(self, archive, nbytes=None, out=None, stream=None):
+        """archive: uint8 CUDA tensor.  Returns the float32 field tensor."""
+        nbytes = archive.numel() if nbytes is None else int(nbytes)
+        hdr = archive[:128].cpu().numpy()
+        p, n = archive_info(hdr, nbytes)
+        shape = [int(p.dims[i]) for i in range(p.ndim)][::-1]
+        if out is None:
+            out = torch.empty(shape, dtype=torch.float32, device=archive.device)
+        st = load().gbsz_decompress(self.h, C.c_void_p(archive.data_ptr()), nbytes,
+                                    C.c_void_p(out.data_ptr()), out.numel(), _stream(stream))
+        if st != OK:
+            raise GbszError(st, "gbsz_decompress")
+        return out
+
+    def decompress_status(self, archive, nbytes, out, stream=None):
+        return load().gbsz_decompress(self.h, C.c_void_p(archive.data_ptr()), int(nbytes),
+                                      C.c_void_p(out.data_ptr()), out.numel(), _stream(stream))
+
+    # -- host-buffer API ---------------------------------------------------
+    def compress_host(self, field_np, eb, eb_mode=EB_REL, radius=512, chunk=0, out=None, stream=None):
+        """field_np: contiguous float32 numpy array (or pinned CPU tensor)."""
+        import numpy as np
+        ptr, shape = _host_ptr(field_np)
+        p = make_params(shape[::-1], eb, eb_mode, radius, chunk)
+        cap = load().gbsz_compress_bound(C.byref(p))
+        if out is None:
+            out = np.empty(cap, dtype=np.uint8)
+        optr, _ = _host_ptr(out)
+        nbytes = C.c_size_t()
+        st = load().gbsz_compress_host(self.h, ptr, C.byref(p), optr, _nbytes(out), C.byref(nbytes),
+                                       _stream(stream))
+        if st != OK:
+            raise GbszError(st, "gbsz_compress_host")
+        return out, nbytes.value
+
+    def decompress_host(self, archive, nbytes, out, stream=None):
+        aptr, _ = _host_ptr(archive)
+        optr, _ = _host_ptr(out)
+        st = load().gbsz_decompress_host(self.h, aptr, int(nbytes), optr, _numel(out), _stream(stream))
+        if st != OK:
+            raise GbszError(st, "gbsz_decompress_host")
+        return out
+
+    # -- introspection -----------------------------------------------------
+    def debug_copy(self, which, count, dtype):
+        import numpy as np
+        a = np.zeros(count, dtype=dtype)
+        st = load().gbsz_debug_copy(self.h, int(which), C.c_void_p(a.ctypes.data), a.nbytes)
+        if st != OK:
+            raise GbszError(st, "gbsz_debug_copy")
+        return a
+
+    def profile_enable(self, on=True):
+        load().gbsz_profile_enable(self.h, 1 if on else 0)
+
+    def profile_read(self):
+        """Returns (stage_ms[8], stage_calls[8], kernel_launches)."""
+        ms = (C.c_double * NSTAGE)()
+        calls = (C.c_uint64 * NSTAGE)()
+        kl = C.c_uint64()
+        st = load().gbsz_profile_read(self.h, C.cast(ms, C.c_void_p), C.cast(calls, C.c_void_p), C.byref(kl))
+        if st != OK:
+            raise GbszError(st, "gbsz_profile_read")
+        return list(ms), list(calls), kl.value
+
+
+def _host_ptr(a):
+    if isinstance(a, torch.Tensor):
+        assert not a.is_cuda and a.is_contiguous()
+        return C.c_void_p(a.data_ptr()), list(a.shape)
+    assert a.flags["C_CONTIGUOUS"]
+    return C.c_void_p(a.ctypes.data), list(a.shape)
+
+
+def _nbytes(a):
+    return a.numel() * a.element_size() if isinstance(a, torch.Tensor) else a.nbytes
+
+
+def _numel(a):
+    return a.numel() if isinstance(a, torch.Tensor) else a.size
+
+
+def archive_info(header_bytes, nbytes=None):
+    """Parse a host copy of the archive header (numpy uint8).  Returns (Params, n)."""
+    import numpy as np
+    h = np.ascontiguousarray(header_bytes, dtype=np.uint8)
+    nb = int(nbytes) if nbytes is not None else h.size
+    p = Params()
+    n = C.c_uint64()
+    st = load().gbsz_archive_info(C.c_void_p(h.ctypes.data), nb, C.byref(p), C.byref(n))
+    if st != OK:
+        raise GbszError(st, "gbsz_archive_info")
+    return p, n.value
+
+
+def auto_chunk(dims, radius=512):
+    return load().gbsz_auto_chunk(C.byref(make_params(dims, 1e-4, EB_REL, radius, 0)))

@@ -1,0 +1,177 @@
+"""GPU vs oracle parity, stage by stage, through the C ABI.
+
+Tolerance: the whole path is integer and bit-exact, so every stage is
+compared for equality -- error-bound scalars, quant codes, histogram, code
+lengths, codewords, chunk bit counts, outliers, exceptions, bitstream, the
+archive bytes, and the reconstructed floats (0 ulp).  Inputs are seeded
+synthetic fields at sizes that span several tiles and a ragged tail.
+"""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ref
+from paper_2007_09625_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx(gb):
+    c = gb.Context(0)
+    yield c
+    c.close()
+
+
+def compare_stages(gb, ctx, x, eb, eb_mode, R, C):
+    """Compress on the GPU and with the oracle; assert each stage equal.
+    Returns (gpu archive tensor, nbytes, oracle archive)."""
+    xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    arc, nb = ctx.compress(xt, eb, eb_mode, R, C)
+    torch.cuda.synchronize()
+    ga = arc[:nb].cpu().numpy()
+    n = x.size
+    sc = ref.error_bound(x, eb, eb_mode)
+    gsc = ctx.debug_copy(gb.DEBUG_SCALARS, 3, np.float32)
+    assert np.array_equal(gsc.view(np.uint32), sc.view(np.uint32)), (gsc, sc)
+    dq = ref.dualquant(x, sc, R)
+    gcodes = ctx.debug_copy(gb.DEBUG_CODES, n, np.uint16)
+    if not np.array_equal(gcodes, dq["codes"]):
+        bad = np.flatnonzero(gcodes != dq["codes"])
+        raise AssertionError(f"codes differ at {bad.size} points, first {bad[:8]}: "
+                             f"gpu {gcodes[bad[:8]]} oracle {dq['codes'][bad[:8]]}")
+    hist = ref.histogram(dq["codes"], 2 * R)
+    ghist = ctx.debug_copy(gb.DEBUG_HIST, 2 * R, np.uint32)
+    assert np.array_equal(ghist, hist)
+    ln, mx = ref.huffman_lengths(hist)
+    cw = ref.canonical_codes(ln)
+    gcw = ctx.debug_copy(gb.DEBUG_CODEWORDS, 2 * R, np.uint64)
+    gs = ref.sections(ga)
+    assert np.array_equal(gs["len"], ln), "code lengths differ"
+    assert np.array_equal(gcw, cw), "canonical codewords differ"
+    oa = ref.compress(x, eb, eb_mode, radius=R, chunk=C)
+    os_ = ref.sections(oa)
+    for key in ("maxlen", "m", "e", "words", "nchunk"):
+        assert gs[key] == os_[key], (key, gs[key], os_[key])
+    assert np.array_equal(gs["bits"], os_["bits"]), "chunk bit counts differ"
+    assert np.array_equal(gs["out_idx"], os_["out_idx"]) and np.array_equal(gs["out_delta"], os_["out_delta"])
+    assert np.array_equal(gs["exc_idx"], os_["exc_idx"]) and np.array_equal(gs["exc_raw"], os_["exc_raw"])
+    if not np.array_equal(gs["stream"], os_["stream"]):
+        bad = np.flatnonzero(gs["stream"] != os_["stream"])
+        raise AssertionError(f"bitstream differs in {bad.size} words, first {bad[:8]}")
+    assert nb == oa.size and np.array_equal(ga, oa), "archive bytes differ"
+    return arc, nb, oa
+
+
+def check_decompress(gb, ctx, arc, nb, oa, x, eb, eb_mode):
+    y = ctx.decompress(arc, nb)
+    torch.cuda.synchronize()
+    y = y.cpu().numpy()
+    yo = ref.decompress(oa)
+    assert y.shape == x.shape
+    if not np.array_equal(y.view(np.uint32), yo.view(np.uint32)):
+        bad = np.flatnonzero(y.view(np.uint32).ravel() != yo.view(np.uint32).ravel())
+        raise AssertionError(f"reconstruction differs at {bad.size} points, first {bad[:8]}")
+    dcodes = ctx.debug_copy(gb.DEBUG_DECODED, x.size, np.uint16)
+    assert np.array_equal(dcodes, ref.dualquant(x, ref.error_bound(x, eb, eb_mode), ref.sections(oa)["radius"])["codes"])
+    sc = ref.error_bound(x, eb, eb_mode)
+    fin = np.isfinite(x)
+    err = np.abs(x[fin].astype(np.float64) - y[fin].astype(np.float64))
+    assert err.size == 0 or err.max() <= float(sc[0])
+    assert np.array_equal(x[~fin].view(np.uint32), y[~fin].view(np.uint32))
+
+
+CASES = [
+    # kind, shape (numpy order), eb, mode, R, C
+    ("walk", (100003,), 1e-4, ref.EB_REL, 512, 4096),
+    ("walk", (100003,), 1e-4, ref.EB_REL, 512, 64),
+    ("walk", (100003,), 1e-4, ref.EB_REL, 512, 8192),
+    ("walk", (9000,), 1e-5, ref.EB_REL, 512, 65536),
+    ("sinus", (181, 1037), 1e-4, ref.EB_REL, 512, 1024),
+    ("grf", (181, 1037), 1e-3, ref.EB_REL, 512, 4096),
+    ("grf", (600, 700), 1e-4, ref.EB_REL, 32768, 4096),
+    ("sinus", (37, 41, 67), 1e-4, ref.EB_REL, 512, 4096),
+    ("lognormal", (37, 41, 67), 1e-3, ref.EB_REL, 512, 256),
+    ("lognormal", (40, 40, 40), 1e-5, ref.EB_REL, 32768, 4096),
+    ("sinus", (64, 64, 64), 1e-4, ref.EB_REL, 512, 4096),
+]
+
+
+@pytest.mark.parametrize("kind,shape,eb,mode,R,C", CASES, ids=[f"{c[0]}{'x'.join(map(str, c[1]))}-eb{c[2]}-R{c[4]}-C{c[5]}" for c in CASES])
+def test_parity(gb, ctx, kind, shape, eb, mode, R, C):
+    x = workloads.field_for(kind, shape, seed=sum(shape) + R + C)
+    arc, nb, oa = compare_stages(gb, ctx, x, eb, mode, R, C)
+    check_decompress(gb, ctx, arc, nb, oa, x, eb, mode)
+
+
+EDGE = {
+    "n1": np.array([3.25], np.float32),
+    "n2": np.array([3.25, -1.0], np.float32),
+    "tiny_1d": np.linspace(-1, 1, 37).astype(np.float32),
+    "tiny_2d": np.arange(6, dtype=np.float32).reshape(2, 3),
+    "tiny_3d": np.random.default_rng(0).normal(size=(2, 3, 5)).astype(np.float32),
+    "thin_3d": np.random.default_rng(1).normal(size=(70, 1, 33)).astype(np.float32),
+    "col_2d": np.random.default_rng(2).normal(size=(3000, 1)).astype(np.float32),
+    "constant_2d": np.full((50, 70), 7.5, np.float32),
+    "zeros_3d": np.zeros((9, 10, 11), np.float32),
+    "nonfinite": np.where(np.random.default_rng(3).random(5000) < 0.05, np.nan,
+                          np.cumsum(np.random.default_rng(4).normal(size=5000))).astype(np.float32),
+    "inf_and_huge": np.concatenate([np.cumsum(np.random.default_rng(5).normal(size=3000)),
+                                    [np.inf, -np.inf, 3e38, -3e38, 1e-45]]).astype(np.float32),
+    "noise_all_outliers": np.random.default_rng(6).normal(size=(20, 30, 40)).astype(np.float32),
+}
+
+
+@pytest.mark.parametrize("name", sorted(EDGE))
+@pytest.mark.parametrize("R", [2, 512])
+def test_edge_cases(gb, ctx, name, R):
+    x = EDGE[name]
+    eb, mode = (1e-6, ref.EB_REL) if name == "noise_all_outliers" else (1e-3, ref.EB_REL)
+    arc, nb, oa = compare_stages(gb, ctx, x, eb, mode, R, 64)
+    check_decompress(gb, ctx, arc, nb, oa, x, eb, mode)
+
+
+def test_absolute_eb_mode(gb, ctx):
+    x = workloads.field_for("grf", (90, 130), seed=7) * np.float32(100)
+    arc, nb, oa = compare_stages(gb, ctx, x, 0.05, ref.EB_ABS, 512, 512)
+    check_decompress(gb, ctx, arc, nb, oa, x, 0.05, ref.EB_ABS)
+
+
+def test_determinism_and_repeat_calls(gb, ctx):
+    x = workloads.field_for("walk", (50000,), seed=9)
+    xt = torch.from_numpy(x).cuda()
+    a1, n1 = ctx.compress(xt, 1e-4)
+    b1 = a1[:n1].cpu().numpy()
+    for _ in range(3):
+        a2, n2 = ctx.compress(xt, 1e-4)
+        assert n2 == n1 and np.array_equal(a2[:n2].cpu().numpy(), b1)
+
+
+def test_capacity_error_reports_needed_size(gb, ctx):
+    x = workloads.field_for("walk", (20000,), seed=11)
+    xt = torch.from_numpy(x).cuda()
+    arc, nb = ctx.compress(xt, 1e-4)
+    small = torch.empty(nb - 16, dtype=torch.uint8, device="cuda")
+    p = gb.make_params([x.size], 1e-4, gb.EB_REL, 512, 0)
+    st, need = ctx.compress_status(xt, p, small)
+    assert st == gb.ERR_CAPACITY and need == nb
+    out = torch.empty(x.size - 1, dtype=torch.float32, device="cuda")
+    assert ctx.decompress_status(arc, nb, out) == gb.ERR_CAPACITY
+
+
+def test_host_buffer_api(gb, ctx):
+    x = workloads.field_for("sinus", (33, 45, 29), seed=12)
+    a, nb = ctx.compress_host(x, 1e-4)
+    oa = ref.compress(x, 1e-4, ref.EB_REL, 512, gb.auto_chunk(list(x.shape)[::-1]))
+    assert nb == oa.size and np.array_equal(a[:nb], oa)
+    y = np.empty_like(x)
+    ctx.decompress_host(a[:nb], nb, y)
+    assert np.array_equal(y.view(np.uint32), ref.decompress(oa).view(np.uint32))
+
+
+def test_gpu_decodes_oracle_archives(gb, ctx):
+    x = workloads.field_for("lognormal", (21, 30, 50), seed=13)
+    oa = ref.compress(x, 1e-4, ref.EB_REL, radius=1024, chunk=128)
+    at = torch.from_numpy(oa).cuda()
+    y = ctx.decompress(at, oa.size).cpu().numpy()
+    assert np.array_equal(y.view(np.uint32), ref.decompress(oa).view(np.uint32))
