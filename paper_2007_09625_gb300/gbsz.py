@@ -149,10 +149,10 @@ class Context:
     def decompress(self, archive, nbytes=None, out=None, stream=None):
         """archive: uint8 CUDA tensor.  Returns the float32 field tensor."""
         nbytes = archive.numel() if nbytes is None else int(nbytes)
-        hdr = archive[:128].cpu().numpy()
-        p, n = archive_info(hdr, nbytes)
-        shape = [int(p.dims[i]) for i in range(p.ndim)][::-1]
         if out is None:
+            hdr = archive[:128].cpu().numpy()
+            p, n = archive_info(hdr, nbytes)
+            shape = [int(p.dims[i]) for i in range(p.ndim)][::-1]
             out = torch.empty(shape, dtype=torch.float32, device=archive.device)
         st = load().gbsz_decompress(self.h, C.c_void_p(archive.data_ptr()), nbytes,
                                     C.c_void_p(out.data_ptr()), out.numel(), _stream(stream))
