@@ -82,6 +82,7 @@ struct gbsz_ctx {
     // last call (debug copies)
     uint64_t last_n = 0, last_dn = 0;
     uint32_t last_nbins = 0;
+    float last_sc[3] = {0, 0, 0};  // error-bound scalars of the last compress
     bool have_compress = false, have_decompress = false;
     // timing
     bool profiling = false;
@@ -438,6 +439,9 @@ gbsz_status gbsz_compress(gbsz_ctx *c, const float *d_field, const gbsz_params *
     if (s != GBSZ_OK) return s;
     const uint32_t derr = c->ctl_host->error;
     *out_bytes = (size_t)c->ctl_host->total;
+    c->last_sc[0] = c->ctl_host->eb;
+    c->last_sc[1] = c->ctl_host->ebx2;
+    c->last_sc[2] = c->ctl_host->inv2eb;
     return map_device_error(derr);
 }
 
@@ -591,7 +595,10 @@ gbsz_status gbsz_debug_copy(gbsz_ctx *c, int which, void *h_dst, size_t bytes)
     switch (which) {
     case 0: src = c->codes.p; need = c->have_compress ? c->last_n * 2 : 0; break;
     case 1: src = c->hist.p; need = c->have_compress ? c->last_nbins * 4 : 0; break;
-    case 2: src = &c->ctl->eb; need = c->have_compress ? 12 : 0; break;
+    case 2:
+        if (!c->have_compress || bytes != 12) return GBSZ_ERR_INVALID_ARG;
+        std::memcpy(h_dst, c->last_sc, 12);
+        return GBSZ_OK;
     case 3: src = c->codes.p; need = c->have_decompress ? c->last_dn * 2 : 0; break;
     case 4: src = c->codes_only.p; need = c->have_compress ? c->last_nbins * 8 : 0; break;
     default: return GBSZ_ERR_INVALID_ARG;
