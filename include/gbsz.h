@@ -156,6 +156,29 @@ gbsz_status gbsz_profile_enable(gbsz_ctx *ctx, int enable);
 gbsz_status gbsz_profile_read(gbsz_ctx *ctx, double *ms, uint64_t *calls,
                               uint64_t *kernel_launches);
 
+/* Huffman codebook from a histogram without allocating device memory.  The
+ * paper has no counterpart: it exists for callers that cannot call
+ * cudaMalloc -- code running during CUDA graph capture, frameworks that own
+ * all device memory through their own pool, processes under a fixed memory
+ * budget.  It runs the compressor's codebook kernel (S4) with its scratch in
+ * a fixed device array that the library defines (sized for 65536 symbols,
+ * about 4 MB, held on every GPU that loads the library until exit).
+ *   d_hist   device uint32[nbins] symbol frequencies (nbins in [1, 65536];
+ *            at least one nonzero)
+ *   d_len    device uint8[nbins] out: code lengths (0 = symbol absent)
+ *   d_code   device uint64[nbins] out: canonical codewords, right-aligned
+ *   maxlen   host out (may be NULL): longest code length
+ * Runs on the current CUDA device; its first call on a device looks up the
+ * array's device address, so make that first call before any stream
+ * capture.  All calls share the array and it keeps the last call's contents:
+ * calls whose work overlaps on the GPU race, so serialise them.  Synchronises
+ * `stream` to report errors.  Allocates nothing (no cudaMalloc, cudaFree or
+ * allocating library routine).
+ * Errors: INVALID_ARG (bad sizes, NULL, all-zero histogram), CUDA. */
+gbsz_status gbsz_codebook_noalloc(const uint32_t *d_hist, uint32_t nbins,
+                                  uint8_t *d_len, uint64_t *d_code,
+                                  uint32_t *maxlen, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -355,30 +355,33 @@ __global__ void __launch_bounds__(kCbThreads, 1) k_decode_tables(CodebookArgs a)
     }
 }
 
+constexpr size_t kCbSmem = 16 * kCbThreads * sizeof(uint32_t);
+
+// opt in to more than 48 KB of dynamic shared memory, once per device
+void set_smem_attributes()
+{
+    static unsigned long long done = 0;  // one bit per device id < 64
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0;
+    if (bit && (done & bit)) return;
+    cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem);
+    cudaFuncSetAttribute(k_decode_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem);
+    done |= bit;
+}
+
 }  // namespace
 
 void launch_codebook(const CodebookArgs &a, cudaStream_t st)
 {
-    const size_t smem = 16 * kCbThreads * sizeof(uint32_t);
-    static bool init = false;
-    if (!init) {
-        cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_decode_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        init = true;
-    }
-    k_codebook<<<1, kCbThreads, smem, st>>>(a);
+    set_smem_attributes();
+    k_codebook<<<1, kCbThreads, kCbSmem, st>>>(a);
 }
 
 void launch_decode_tables(const CodebookArgs &a, cudaStream_t st)
 {
-    const size_t smem = 16 * kCbThreads * sizeof(uint32_t);
-    static bool init = false;
-    if (!init) {
-        cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        cudaFuncSetAttribute(k_decode_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        init = true;
-    }
-    k_decode_tables<<<1, kCbThreads, smem, st>>>(a);
+    set_smem_attributes();
+    k_decode_tables<<<1, kCbThreads, kCbSmem, st>>>(a);
 }
 
 }  // namespace gbsz

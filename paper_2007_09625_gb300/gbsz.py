@@ -36,6 +36,7 @@ SIGNATURES = {
     "gbsz_debug_copy": ([_P, C.c_int, _P, C.c_size_t], C.c_int),
     "gbsz_profile_enable": ([_P, C.c_int], C.c_int),
     "gbsz_profile_read": ([_P, _P, _P, C.POINTER(C.c_uint64)], C.c_int),
+    "gbsz_codebook_noalloc": ([_P, C.c_uint32, _P, _P, C.POINTER(C.c_uint32), _P], C.c_int),
 }
 
 
@@ -243,3 +244,19 @@ def archive_info(header_bytes, nbytes=None):
 
 def auto_chunk(dims, radius=512):
     return load().gbsz_auto_chunk(C.byref(make_params(dims, 1e-4, EB_REL, radius, 0)))
+
+
+def codebook_noalloc(hist, stream=None):
+    """Code lengths and canonical codewords from a device histogram, through
+    the entry point that allocates no device memory (see gbsz.h).  The output
+    tensors are allocated here by torch; the library allocates nothing."""
+    assert hist.is_cuda and hist.dtype == torch.int32 and hist.is_contiguous()
+    nb = hist.numel()
+    ln = torch.empty(nb, dtype=torch.uint8, device=hist.device)
+    code = torch.empty(nb, dtype=torch.int64, device=hist.device)
+    mx = C.c_uint32()
+    st = load().gbsz_codebook_noalloc(C.c_void_p(hist.data_ptr()), nb, C.c_void_p(ln.data_ptr()),
+                                      C.c_void_p(code.data_ptr()), C.byref(mx), _stream(stream))
+    if st != OK:
+        raise GbszError(st, "gbsz_codebook_noalloc")
+    return ln, code, mx.value
