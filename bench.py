@@ -43,7 +43,52 @@ def parse():
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--cpu-sample-log2", type=int, default=26)
+    ap.add_argument("--skip-batch", action="store_true",
+                    help="skip the batched vs per-field measurement (16 x 1800x3600 fields)")
     return ap.parse_args()
+
+
+def batch_vs_per_field(ctx, gbsz, workloads, dev, steps=5):
+    """16 fields of 1800x3600 (power-law -3 fields, four of them with masked
+    constant regions) at rel eb 1e-4: one compress+decompress per field in a
+    loop, versus one compress_batch + decompress_batch over all 16."""
+    import torch
+    fields = [torch.from_numpy(f).to(dev) for f in workloads.grf_2d_batch(16, seed=1003)]
+    n_all = sum(f.numel() for f in fields)
+    params = [gbsz.make_params(gbsz.field_dims(f), 1e-4) for f in fields]
+    arcs = [torch.empty(gbsz.compress_bound(gbsz.field_dims(f), 1e-4), dtype=torch.uint8, device=dev)
+            for f in fields]
+    outs = [torch.empty_like(f) for f in fields]
+    stream = torch.cuda.current_stream(dev)
+
+    def per_field():
+        for f, a, o in zip(fields, arcs, outs):
+            _, nb = ctx.compress(f, 1e-4, out=a)
+            ctx.decompress(a, nb, out=o)
+
+    def batched():
+        _, nbs, _ = ctx.compress_batch(fields, None, outs=arcs, params=params)
+        ctx.decompress_batch(arcs, nbs, outs)
+
+    res = {}
+    for name, fn in (("per_field", per_field), ("batched", batched)):
+        for _ in range(2):
+            fn()
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        res[name] = 4.0 * n_all / (e0.elapsed_time(e1) / steps / 1e3) / 1e9
+    # batched results are the single-field results
+    single, nb1 = ctx.compress(fields[5], 1e-4)
+    _, nbs, _ = ctx.compress_batch(fields, None, outs=arcs, params=params)
+    assert nbs[5] == nb1 and torch.equal(arcs[5][:nb1], single[:nb1])
+    return {"workload": "16 x 1800x3600 FP32 power-law fields, rel eb 1e-4, radius 512",
+            "per_field_gbs": res["per_field"], "batched_gbs": res["batched"],
+            "speedup": res["batched"] / res["per_field"], "steps": steps}
 
 
 def workload_config(a, n, chunk):
@@ -114,6 +159,20 @@ def dist_env():
     return ws, rank, local
 
 
+def rank_seed(rank):
+    """Every rank compresses its own field: workload seed 1002 + rank."""
+    return 1002 + rank
+
+
+def reduce_max(value, device):
+    """Max over ranks of a timing (the only collective of the benchmark)."""
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor([float(value)], device=device, dtype=torch.float64)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def cpu_oracle_time(x, a, chunk, omp=False):
     from oracle import ref
     t0 = time.perf_counter()
@@ -170,7 +229,7 @@ def main():
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     n = 1 << a.log2n
-    x_host = workloads.random_walk_1d(n, seed=1002 + rank)
+    x_host = workloads.random_walk_1d(n, seed=rank_seed(rank))
     x = torch.from_numpy(x_host).to(dev)
     ctx = gbsz.Context(local)
     chunk = a.chunk or gbsz.auto_chunk([n], a.radius)
@@ -215,9 +274,7 @@ def main():
     stage_ms, stage_calls, launches = ctx.profile_read()
     ctx.profile_enable(False)
     if dist:
-        t = torch.tensor([ms_total], device=dev, dtype=torch.float64)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms_total = float(t.item())
+        ms_total = reduce_max(ms_total, dev)
     ms_step = ms_total / a.steps
     value = 4.0 * n * ws / (ms_step / 1e3) / 1e9
 
@@ -232,12 +289,13 @@ def main():
     m_out = int(np.frombuffer(arc[80:88].cpu().numpy().tobytes(), np.uint64)[0])
     w_words = int(np.frombuffer(arc[96:104].cpu().numpy().tobytes(), np.uint64)[0])
     f = m_out / n
-    alg = {  # bytes per launch of each stage
-        0: 4.0 * n,
-        1: 6.0 * n + 4.0 * m_out,
-        3: 2.0 * n + 16.0 * m_out + 4.0 * w_words + 4.0 * (n // chunk),
-        5: 4.0 * w_words + 4.0 * (n // chunk) + 2.0 * n,
-        6: 2.0 * n + 2.0 * n + 4.0 * n + 12.0 * m_out,
+    nc = (n + chunk - 1) // chunk
+    alg = {  # algorithmic bytes per call of each stage
+        0: 4.0 * n,                                               # read the field
+        1: 6.0 * n + 8.0 * m_out,                                 # field in, codes out, outlier residuals
+        3: 2.0 * n + 16.0 * m_out + 4.0 * w_words + 4.0 * nc,     # codes + residuals in; stream, outliers, bits out
+        5: 4.0 * w_words + 12.0 * nc + 2.0 * n,                   # stream, bits, offsets in; codes out
+        6: 6.0 * n + 16.0 * m_out,                                # codes in, field out; outlier scatter
     }
     dom = max(alg, key=lambda s: stage_ms[s])
     dom_ms = stage_ms[dom] / max(stage_calls[dom], 1)
@@ -267,12 +325,14 @@ def main():
         torch.cuda.synchronize(dev)
         te = (time.perf_counter() - t0) / ke
         if dist:
-            t = torch.tensor([te], device=dev, dtype=torch.float64)
-            tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-            te = float(t.item())
+            te = reduce_max(te, dev)
         assert torch.equal(hy.view(torch.int32), y.cpu().view(torch.int32))
         e2e = {"value": 4.0 * n * ws / te / 1e9, "unit": "GB/s", "h2d_bytes_per_step": 4 * n + hnb,
                "d2h_bytes_per_step": hnb + 4 * n, "ms_per_step": te * 1e3}
+
+    batch = None
+    if not a.skip_batch:
+        batch = batch_vs_per_field(ctx, gbsz, workloads, dev)
 
     cpu = None
     if rank == 0 and not a.skip_cpu_baseline:
@@ -298,6 +358,7 @@ def main():
                 "compression_ratio": cr, "outlier_frac": f,
                 "stage_ms_per_step": {nm: stage_ms[i] / a.steps for i, nm in enumerate(stage_names)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
+                "batch_vs_per_field": batch,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist:

@@ -44,7 +44,7 @@ typedef enum {
     GBSZ_ERR_CORRUPT = 3,     /* archive fails a consistency check */
     GBSZ_ERR_OOM = 4,         /* device or pinned allocation failed */
     GBSZ_ERR_CUDA = 5,        /* a CUDA runtime call failed */
-    GBSZ_ERR_TIMEOUT = 6,     /* a bounded device wait ran out */
+    GBSZ_ERR_TIMEOUT = 6,     /* reserved: a bounded device wait ran out (no kernel waits today) */
     GBSZ_ERR_UNSUPPORTED = 7  /* device is not sm_103 or feature absent */
 } gbsz_status;
 
@@ -109,6 +109,31 @@ gbsz_status gbsz_compress(gbsz_ctx *ctx, const float *d_field,
 gbsz_status gbsz_decompress(gbsz_ctx *ctx, const void *d_archive, size_t bytes,
                             float *d_field, uint64_t capacity_elems,
                             void *stream);
+
+/* Batched compression of `count` independent fields (host arrays of
+ * length count: device pointers, parameters, capacities; outputs out_bytes
+ * and per-field statuses).  The fields' stages are spread over up to eight
+ * internal streams forked from `stream` and joined back into it, so small
+ * fields' kernels overlap on the GPU; the call synchronises once at the end.
+ * Every archive is byte-identical to what gbsz_compress gives for that field
+ * alone.  Returns GBSZ_OK if every field succeeded, else the first field's
+ * error (see statuses[]).  This is the batching the paper's block-by-block
+ * processing of many fields (Sec. 4.1) calls for, done concurrently. */
+gbsz_status gbsz_compress_batch(gbsz_ctx *ctx, uint32_t count,
+                                const float *const *d_fields,
+                                const gbsz_params *params,
+                                void *const *d_archives,
+                                const size_t *capacities, size_t *out_bytes,
+                                gbsz_status *statuses, void *stream);
+
+/* Batched decompression; the counterpart of gbsz_compress_batch.  Reads all
+ * headers to the host with one synchronisation, then decodes every field
+ * concurrently as above.  Per-field statuses as for gbsz_decompress. */
+gbsz_status gbsz_decompress_batch(gbsz_ctx *ctx, uint32_t count,
+                                  const void *const *d_archives,
+                                  const size_t *bytes, float *const *d_fields,
+                                  const uint64_t *capacities,
+                                  gbsz_status *statuses, void *stream);
 
 /* Host-buffer variants: the field (or archive) is copied from host memory to
  * context-owned device staging, processed, and the result copied back to

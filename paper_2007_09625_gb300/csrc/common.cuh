@@ -65,7 +65,7 @@ struct Control {
     uint32_t maxlen;
     unsigned long long n_out;  // outliers (code 0), counted by the dual-quant kernel
     unsigned long long n_exc;  // verbatim exceptions
-    uint32_t ticket;           // encode: next work unit
+    uint32_t ticket;           // unused (kept for layout stability)
     uint32_t nsym;             // codebook: symbols with nonzero frequency
     unsigned long long words;  // encode: total stream words
     unsigned long long total;  // encode: archive bytes
@@ -104,7 +104,7 @@ __device__ __forceinline__ bool within_bound(float d, float r, float eb)
     return s > 0.0f ? e <= 0.0f : e >= 0.0f;
 }
 
-__device__ __forceinline__ int32_t prequant(float d, const EbScalars &s, bool &exc)
+__device__ __forceinline__ int32_t prequant_full(float d, const EbScalars &s, bool &exc)
 {
     if ((__float_as_uint(d) & 0x7F800000u) == 0x7F800000u) {  // NaN or Inf
         exc = true;
@@ -128,6 +128,28 @@ __device__ __forceinline__ int32_t prequant(float d, const EbScalars &s, bool &e
     }
     exc = true;
     return q;
+}
+
+// Common case of prequant_full without int/float conversions: for |t| < 2^22,
+// t + 1.5*2^23 lands in [2^23, 2^24) where floats are the integers, so the
+// one rounding of that addition is round-half-even of t (1.5*2^23 is even);
+// subtracting it back is exact, and the integer is the float's bit pattern
+// minus that of 1.5*2^23 offset by 2^22.  Accepted only when the rounded
+// |d - fl(2eb * q)| is strictly below eb (then the exact value is too);
+// every other case (NaN, Inf, large |t|, near-ties) takes the full path,
+// which gives the same q for the cases accepted here.
+__device__ __forceinline__ int32_t prequant(float d, const EbScalars &s, bool &exc)
+{
+    const float t = __fmul_rn(d, s.inv2eb);
+    if (fabsf(t) < 4194304.0f) {
+        const float tm = __fadd_rn(t, 12582912.0f);
+        const float r = __fmul_rn(s.ebx2, __fsub_rn(tm, 12582912.0f));
+        if (fabsf(__fsub_rn(d, r)) < s.eb) {
+            exc = false;
+            return __float_as_int(tm) - 0x4B400000;
+        }
+    }
+    return prequant_full(d, s, exc);
 }
 
 __device__ __forceinline__ EbScalars load_scalars(const Control *ctl)
@@ -234,20 +256,6 @@ __device__ __forceinline__ uint32_t block_max(uint32_t v, uint32_t *sh)
     return r;
 }
 
-// Bounded spin on a flag written by another CTA.  Returns the flag value, or
-// 0 after `limit` polls (the caller records DERR_TIMEOUT).
-__device__ __forceinline__ uint32_t spin_until_nonzero_epoch(const uint32_t *flag, uint32_t epoch,
-                                                             uint32_t limit)
-{
-    for (uint32_t it = 0; it < limit; it++) {
-        uint32_t f = *(const volatile uint32_t *)flag;
-        if ((f >> 2) == epoch && (f & 3u)) return f;
-        __nanosleep(64);
-    }
-    return 0;
-}
-
-constexpr uint32_t kSpinLimit = 1u << 24;  // ~1 s of polling at 64 ns
 
 // ---------------------------------------------------------------------------
 // launch wrappers implemented in the kernel translation units
@@ -258,7 +266,7 @@ struct QuantArgs {
     uint32_t ndim;
     uint32_t radius;
     uint16_t *codes;
-    int32_t *dscr;   // residual of every code-0 point, indexed by point
+    int2 *dscr;      // {residual, is exception} of every code-0 point, by point
     uint32_t *hist;  // 2R bins, zeroed by the caller
     Control *ctl;
     int num_sms;
@@ -296,16 +304,17 @@ void launch_decode_tables(const CodebookArgs &a, cudaStream_t st);
 struct EncodeArgs {
     const uint16_t *codes;
     const float *x;
-    const int32_t *dscr;
+    const int2 *dscr;
     uint64_t n;
     uint32_t chunk, radius, nbins;
     const uint64_t *cw64;
     const uint32_t *cw32;
     uint8_t *archive;
     uint64_t capacity;
-    uint32_t *lb_flag;
-    ulonglong2 *lb_agg, *lb_inc;
-    uint32_t epoch;
+    uint32_t *lane_bits;    // bits of every lane (S symbols) of every round
+    ulonglong2 *unit_tot;   // per unit: {words, outliers | exceptions << 32}
+    ulonglong2 *unit_off;   // their exclusive prefix sums
+    ulonglong2 *scan_part;  // scan scratch
     Control *ctl;
     // header fields
     uint32_t ndim, eb_mode;
@@ -313,7 +322,8 @@ struct EncodeArgs {
     double eb;
     int num_sms;
 };
-void launch_encode(const EncodeArgs &a, cudaStream_t st);
+int launch_encode(const EncodeArgs &a, cudaStream_t st);  // returns kernels launched
+uint64_t encode_units(uint64_t n, uint32_t chunk);        // units (per-unit totals) of the encoder
 
 struct DecodeArgs {
     const uint8_t *archive;
@@ -326,10 +336,13 @@ struct DecodeArgs {
     const uint32_t *count, *start;
     const uint16_t *sorted;
     unsigned long long *chunk_off;  // scratch nchunk
+    unsigned long long *scan_partial;  // scratch for the offset scan
+    uint32_t *tile_sums;  // 1D: residual sum per 4096-point tile (zeroed), else NULL
     uint16_t *codes;
     Control *ctl;
 };
-void launch_decode(const DecodeArgs &a, cudaStream_t st);
+constexpr uint32_t kRecon1DTile = 4096;  // 1D reconstruction tile (points)
+int launch_decode(const DecodeArgs &a, cudaStream_t st);
 
 struct ReconArgs {
     const uint16_t *codes;
@@ -341,8 +354,9 @@ struct ReconArgs {
     uint32_t radius;
     float ebx2;
     int32_t *dscr;
-    uint32_t *faces;      // carry scratch
+    uint32_t *faces;      // carry scratch; 1D: the tile sums left by the decoder
     uint64_t faces_cap;   // entries
+    uint32_t *scan_partial;  // scratch for the 1D carry scan
     float *out;
     Control *ctl;
     int num_sms;

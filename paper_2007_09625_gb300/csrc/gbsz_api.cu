@@ -1,8 +1,18 @@
 // gbsz_api.cu -- host side of the C ABI declared in include/gbsz.h:
-// context with resident device scratch, argument validation, archive header
-// parsing, stage orchestration on the caller's stream, stage timing.
+// contexts with resident device scratch, argument validation, archive header
+// parsing, stage orchestration, batches, stage timing.
+//
+// A context owns "slots": each slot is one complete set of per-call device
+// scratch (control block, quant codes, outlier residuals, encoder unit totals,
+// codebook and decode tables, carry arrays) plus a stream of its own.  A
+// single-field call runs on slot 0 in the caller's stream.  A batch call
+// forks the caller's stream into up to kMaxSlots slot streams, gives field i
+// to slot i mod K, lets every field run without host synchronisation (the
+// fields' kernels overlap on the GPU), joins back into the caller's stream
+// and synchronises once.  Results never depend on the slot a field ran on.
 #include "../../include/gbsz.h"
 #include "common.cuh"
+#include "scan.cuh"
 
 #include <algorithm>
 #include <cmath>
@@ -13,6 +23,8 @@
 using namespace gbsz;
 
 namespace {
+
+constexpr int kMaxSlots = 8;
 
 struct DevGuard {
     int prev = -1;
@@ -56,9 +68,80 @@ struct Buf {
     template <typename T> T *as() const { return static_cast<T *>(p); }
 };
 
+// pinned host array, grown on demand
+template <typename T> struct HostBuf {
+    T *p = nullptr;
+    size_t cap = 0;
+    bool ensure(size_t count)
+    {
+        if (count <= cap && p) return true;
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+        if (cudaMallocHost(&p, std::max<size_t>(count, 1) * sizeof(T)) != cudaSuccess) {
+            cudaGetLastError();
+            p = nullptr;
+            return false;
+        }
+        cap = std::max<size_t>(count, 1);
+        return true;
+    }
+    void release()
+    {
+        if (p) cudaFreeHost(p);
+        p = nullptr;
+        cap = 0;
+    }
+};
+
 struct StageRec {
     int stage;
     cudaEvent_t a, b;
+};
+
+struct Slot {
+    Control *ctl = nullptr;
+    // per-field scratch (grown on demand)
+    Buf codes, dscr, unit_tot, unit_off, unit_part, lane_bits, chunk_off, faces, scan_part;
+    // fixed-size scratch
+    Buf hist, cw64, cw32, codes_only, keyA, keyB, nodef, parent, distA, distB, parA, parB;
+    Buf lut, first, count, start, sorted;
+    cudaStream_t stream = nullptr;  // used by batch calls
+    cudaEvent_t done = nullptr;
+
+    bool init()
+    {
+        const size_t B = kMaxBins;
+        if (cudaMalloc(&ctl, sizeof(Control)) != cudaSuccess) {
+            cudaGetLastError();
+            ctl = nullptr;
+            return false;
+        }
+        if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            return false;
+        }
+        return hist.ensure(B * 4) && cw64.ensure(B * 8) && cw32.ensure(B * 4) && codes_only.ensure(B * 8) &&
+               keyA.ensure(B * 8) && keyB.ensure(B * 8) && nodef.ensure(B * 4) && parent.ensure(2 * B * 4) &&
+               distA.ensure(2 * B * 4) && distB.ensure(2 * B * 4) && parA.ensure(2 * B * 4) &&
+               parB.ensure(2 * B * 4) && lut.ensure((1u << kLutBits) * 4) && first.ensure((kMaxLen + 2) * 8) &&
+               count.ensure((kMaxLen + 2) * 4) && start.ensure((kMaxLen + 2) * 4) && sorted.ensure(B * 2);
+    }
+    void release()
+    {
+        for (Buf *b : {&codes, &dscr, &unit_tot, &unit_off, &unit_part, &lane_bits, &chunk_off, &faces, &scan_part,
+                       &hist, &cw64,
+                       &cw32, &codes_only, &keyA, &keyB, &nodef, &parent, &distA, &distB, &parA, &parB, &lut,
+                       &first, &count, &start, &sorted})
+            b->release();
+        if (ctl) cudaFree(ctl);
+        ctl = nullptr;
+        if (stream) cudaStreamDestroy(stream);
+        stream = nullptr;
+        if (done) cudaEventDestroy(done);
+        done = nullptr;
+    }
 };
 
 }  // namespace
@@ -67,18 +150,12 @@ struct gbsz_ctx {
     int device = 0;
     int num_sms = 152;
     cudaStream_t last_stream = nullptr;
-    Control *ctl = nullptr;
-    Control *ctl_host = nullptr;  // pinned
-    uint8_t *h_header = nullptr;  // pinned, kHeaderBytes
-    // per-field scratch (grown on demand)
-    Buf codes, dscr, lb_flag, lb_agg, lb_inc, chunk_off, faces;
-    // fixed-size scratch
-    Buf hist, cw64, cw32, codes_only, keyA, keyB, nodef, parent, distA, distB, parA, parB;
-    Buf lut, first, count, start, sorted;
+    std::vector<Slot *> slots;       // slot 0 always exists
+    HostBuf<Control> ctl_host;       // one control block per field of the last call
+    HostBuf<uint8_t> h_header;       // kHeaderBytes per field of the last call
+    cudaEvent_t fork = nullptr;
     // staging of the host-buffer API
     Buf stage_field, stage_archive;
-    uint32_t epoch = 0;
-    size_t lb_units = 0;
     // last call (debug copies)
     uint64_t last_n = 0, last_dn = 0;
     uint32_t last_nbins = 0;
@@ -101,11 +178,24 @@ struct gbsz_ctx {
         cudaEventCreate(&e);
         return e;
     }
+
+    bool ensure_slots(int k)
+    {
+        while ((int)slots.size() < k) {
+            Slot *s = new (std::nothrow) Slot();
+            if (!s) return false;
+            if (!s->init()) {
+                s->release();
+                delete s;
+                return false;
+            }
+            slots.push_back(s);
+        }
+        return true;
+    }
 };
 
 namespace {
-
-constexpr uint32_t kUnitSymbols = 4096;  // encoder work unit (symbols)
 
 bool valid_params(const gbsz_params *p, uint64_t *n_out)
 {
@@ -128,8 +218,10 @@ bool valid_params(const gbsz_params *p, uint64_t *n_out)
 
 uint32_t auto_chunk(uint64_t n)
 {
-    // about 128 chunks per SM of a 152-SM GB300, between 64 and 4096 symbols
-    uint64_t target = n / (152ull * 128ull);
+    // Decoding is sequential inside a chunk, one thread per chunk: aim for
+    // about 1024 chunks per SM of a 152-SM GB300, between 64 and 4096 symbols.
+    // Depends on n only, so equal inputs always give equal archives.
+    uint64_t target = n / (152ull * 1024ull);
     uint32_t c = 64;
     while (c < 4096 && (uint64_t)c * 2 <= target) c *= 2;
     return c;
@@ -161,37 +253,26 @@ void stage_end(gbsz_ctx *c, cudaStream_t st, int stage, cudaEvent_t a)
     c->recs.push_back({stage, a, b});
 }
 
-bool ensure_fixed(gbsz_ctx *c)
-{
-    const size_t B = kMaxBins;
-    return c->hist.ensure(B * 4) && c->cw64.ensure(B * 8) && c->cw32.ensure(B * 4) &&
-           c->codes_only.ensure(B * 8) && c->keyA.ensure(B * 8) && c->keyB.ensure(B * 8) &&
-           c->nodef.ensure(B * 4) && c->parent.ensure(2 * B * 4) && c->distA.ensure(2 * B * 4) &&
-           c->distB.ensure(2 * B * 4) && c->parA.ensure(2 * B * 4) && c->parB.ensure(2 * B * 4) &&
-           c->lut.ensure((1u << kLutBits) * 4) && c->first.ensure((kMaxLen + 2) * 8) &&
-           c->count.ensure((kMaxLen + 2) * 4) && c->start.ensure((kMaxLen + 2) * 4) && c->sorted.ensure(B * 2);
-}
-
-CodebookArgs codebook_args(gbsz_ctx *c)
+CodebookArgs codebook_args(Slot *s)
 {
     CodebookArgs a{};
-    a.cw64 = c->cw64.as<uint64_t>();
-    a.cw32 = c->cw32.as<uint32_t>();
-    a.codes_only = c->codes_only.as<uint64_t>();
-    a.lut = c->lut.as<uint32_t>();
-    a.first = c->first.as<unsigned long long>();
-    a.count = c->count.as<uint32_t>();
-    a.start = c->start.as<uint32_t>();
-    a.sorted = c->sorted.as<uint16_t>();
-    a.keyA = c->keyA.as<unsigned long long>();
-    a.keyB = c->keyB.as<unsigned long long>();
-    a.nodef = c->nodef.as<uint32_t>();
-    a.parent = c->parent.as<uint32_t>();
-    a.distA = c->distA.as<uint32_t>();
-    a.distB = c->distB.as<uint32_t>();
-    a.parA = c->parA.as<uint32_t>();
-    a.parB = c->parB.as<uint32_t>();
-    a.ctl = c->ctl;
+    a.cw64 = s->cw64.as<uint64_t>();
+    a.cw32 = s->cw32.as<uint32_t>();
+    a.codes_only = s->codes_only.as<uint64_t>();
+    a.lut = s->lut.as<uint32_t>();
+    a.first = s->first.as<unsigned long long>();
+    a.count = s->count.as<uint32_t>();
+    a.start = s->start.as<uint32_t>();
+    a.sorted = s->sorted.as<uint16_t>();
+    a.keyA = s->keyA.as<unsigned long long>();
+    a.keyB = s->keyB.as<unsigned long long>();
+    a.nodef = s->nodef.as<uint32_t>();
+    a.parent = s->parent.as<uint32_t>();
+    a.distA = s->distA.as<uint32_t>();
+    a.distB = s->distB.as<uint32_t>();
+    a.parA = s->parA.as<uint32_t>();
+    a.parB = s->parB.as<uint32_t>();
+    a.ctl = s->ctl;
     return a;
 }
 
@@ -247,12 +328,169 @@ gbsz_status parse_header(const uint8_t *b, size_t bytes, Header *h)
     return GBSZ_OK;
 }
 
-gbsz_status finish(gbsz_ctx *c, cudaStream_t st)
+// Host-side checks of one compress request; resolves chunk = 0.
+gbsz_status check_compress(const float *d_field, const gbsz_params *pin, const void *d_archive, size_t capacity,
+                           gbsz_params *p, uint64_t *n, size_t *need)
 {
-    if (cudaMemcpyAsync(c->ctl_host, c->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st) != cudaSuccess)
-        return GBSZ_ERR_CUDA;
-    if (cudaStreamSynchronize(st) != cudaSuccess) return GBSZ_ERR_CUDA;
-    if (cudaGetLastError() != cudaSuccess) return GBSZ_ERR_CUDA;
+    if (!d_field || !d_archive || !valid_params(pin, n)) return GBSZ_ERR_INVALID_ARG;
+    if (reinterpret_cast<uintptr_t>(d_archive) & 15) return GBSZ_ERR_INVALID_ARG;
+    *p = *pin;
+    if (p->chunk == 0) p->chunk = auto_chunk(*n);
+    const uint64_t nchunk = (*n + p->chunk - 1) / p->chunk;
+    const Layout Lmin = make_layout(p->radius, nchunk, 0, 0, 0);
+    if (capacity < Lmin.stream) {
+        *need = Lmin.stream;
+        return GBSZ_ERR_CAPACITY;
+    }
+    return GBSZ_OK;
+}
+
+// Enqueues S0-S6 of one field on stream st using slot s; no synchronisation.
+gbsz_status enqueue_compress(gbsz_ctx *c, Slot *s, const float *d_field, const gbsz_params &p, uint64_t n,
+                             void *d_archive, size_t capacity, cudaStream_t st)
+{
+    const uint32_t nbins = 2 * p.radius;
+    const uint64_t nunits = encode_units(n, p.chunk);
+    if (!s->codes.ensure(n * 2 + 64) || !s->dscr.ensure(n * 8 + 64) || !s->unit_tot.ensure(nunits * 16) ||
+        !s->lane_bits.ensure((n / 64 + 64) * 4) ||
+        !s->unit_off.ensure(nunits * 16) || !s->unit_part.ensure(scan_partials(nunits) * 16 + 64))
+        return GBSZ_ERR_OOM;
+    cudaMemsetAsync(s->ctl, 0, sizeof(Control), st);
+    cudaMemsetAsync(s->hist.p, 0, nbins * 4, st);
+
+    cudaEvent_t e0;
+    stage_begin(c, st, &e0);
+    launch_minmax_eb(d_field, n, s->ctl, p.eb, p.eb_mode, c->num_sms, st);
+    stage_end(c, st, 0, e0);
+
+    QuantArgs q{};
+    q.x = d_field;
+    for (int i = 0; i < 3; i++) q.dims[i] = p.dims[i];
+    q.ndim = p.ndim;
+    q.radius = p.radius;
+    q.codes = s->codes.as<uint16_t>();
+    q.dscr = s->dscr.as<int2>();
+    q.hist = s->hist.as<uint32_t>();
+    q.ctl = s->ctl;
+    q.num_sms = c->num_sms;
+    stage_begin(c, st, &e0);
+    launch_dualquant(q, st);
+    stage_end(c, st, 1, e0);
+
+    CodebookArgs cb = codebook_args(s);
+    cb.hist = s->hist.as<uint32_t>();
+    cb.nbins = nbins;
+    cb.len_out = static_cast<uint8_t *>(d_archive) + kHeaderBytes;
+    stage_begin(c, st, &e0);
+    launch_codebook(cb, st);
+    stage_end(c, st, 2, e0);
+
+    EncodeArgs en{};
+    en.codes = q.codes;
+    en.x = d_field;
+    en.dscr = q.dscr;
+    en.n = n;
+    en.chunk = p.chunk;
+    en.radius = p.radius;
+    en.nbins = nbins;
+    en.cw64 = cb.cw64;
+    en.cw32 = cb.cw32;
+    en.archive = static_cast<uint8_t *>(d_archive);
+    en.capacity = capacity;
+    en.lane_bits = s->lane_bits.as<uint32_t>();
+    en.unit_tot = s->unit_tot.as<ulonglong2>();
+    en.unit_off = s->unit_off.as<ulonglong2>();
+    en.scan_part = s->unit_part.as<ulonglong2>();
+    en.ctl = s->ctl;
+    en.ndim = p.ndim;
+    en.eb_mode = p.eb_mode;
+    for (int i = 0; i < 3; i++) en.dims[i] = p.dims[i];
+    en.eb = p.eb;
+    en.num_sms = c->num_sms;
+    stage_begin(c, st, &e0);
+    const int nenc = launch_encode(en, st);
+    stage_end(c, st, 3, e0);
+    c->launches += 3 + nenc;
+    return GBSZ_OK;
+}
+
+// Enqueues S7-S8 of one parsed archive on stream st using slot s.
+gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void *d_archive, float *d_field,
+                               cudaStream_t st)
+{
+    const uint64_t n = h.n;
+    const uint64_t nfaces = recon_faces_entries(h.p.ndim, h.p.dims);
+    const uint64_t nscan = std::max<uint64_t>(h.nchunk, nfaces);
+    if (!s->codes.ensure(n * 2 + 64) || !s->dscr.ensure(n * 8 + 64) || !s->chunk_off.ensure(h.nchunk * 8 + 8) ||
+        !s->faces.ensure(nfaces * 4 + 16) || !s->scan_part.ensure(scan_partials(nscan) * 8 + 64))
+        return GBSZ_ERR_OOM;
+    cudaMemsetAsync(s->ctl, 0, sizeof(Control), st);
+    if (h.p.ndim == 1) cudaMemsetAsync(s->faces.p, 0, nfaces * 4, st);  // tile sums
+    const uint8_t *arc = static_cast<const uint8_t *>(d_archive);
+
+    CodebookArgs cb = codebook_args(s);
+    cb.len_in = arc + kHeaderBytes;
+    cb.nbins = 2 * h.p.radius;
+    cb.expect_maxlen = h.maxlen;
+    cudaEvent_t e0;
+    stage_begin(c, st, &e0);
+    launch_decode_tables(cb, st);
+    stage_end(c, st, 4, e0);
+
+    DecodeArgs d{};
+    d.archive = arc;
+    d.n = n;
+    d.chunk = h.p.chunk;
+    d.nchunk = (uint32_t)h.nchunk;
+    d.radius = h.p.radius;
+    d.maxlen = h.maxlen;
+    d.words = h.w;
+    d.off_bits = h.L.bits;
+    d.off_stream = h.L.stream;
+    d.lut = cb.lut;
+    d.first = cb.first;
+    d.count = cb.count;
+    d.start = cb.start;
+    d.sorted = cb.sorted;
+    d.chunk_off = s->chunk_off.as<unsigned long long>();
+    d.scan_partial = s->scan_part.as<unsigned long long>();
+    d.tile_sums = h.p.ndim == 1 ? s->faces.as<uint32_t>() : nullptr;
+    d.codes = s->codes.as<uint16_t>();
+    d.ctl = s->ctl;
+    stage_begin(c, st, &e0);
+    const int ndec = launch_decode(d, st);
+    stage_end(c, st, 5, e0);
+
+    ReconArgs r{};
+    r.codes = d.codes;
+    r.archive = arc;
+    r.off_outl = h.L.outl;
+    r.off_exc = h.L.exc;
+    r.m = h.m;
+    r.e = h.e;
+    r.ndim = h.p.ndim;
+    for (int i = 0; i < 3; i++) r.dims[i] = h.p.dims[i];
+    r.radius = h.p.radius;
+    r.ebx2 = h.ebx2;
+    r.dscr = s->dscr.as<int32_t>();
+    r.faces = s->faces.as<uint32_t>();
+    r.faces_cap = nfaces;
+    r.scan_partial = s->scan_part.as<uint32_t>();
+    r.out = d_field;
+    r.ctl = s->ctl;
+    r.num_sms = c->num_sms;
+    int nl = 0;
+    stage_begin(c, st, &e0);
+    launch_reconstruct(r, st, &nl);
+    stage_end(c, st, 6, e0);
+    c->launches += 1 + ndec + nl;
+    return GBSZ_OK;
+}
+
+gbsz_status decompress_status(const Control &ctl, const Header &h)
+{
+    if (ctl.error) return map_device_error(ctl.error);
+    if (ctl.zeros != h.m) return GBSZ_ERR_CORRUPT;
     return GBSZ_OK;
 }
 
@@ -292,9 +530,8 @@ gbsz_status gbsz_create(gbsz_ctx **out, int device)
     if (!c) return GBSZ_ERR_OOM;
     c->device = device;
     c->num_sms = prop.multiProcessorCount;
-    if (cudaMalloc(&c->ctl, sizeof(Control)) != cudaSuccess ||
-        cudaMallocHost(&c->ctl_host, sizeof(Control)) != cudaSuccess ||
-        cudaMallocHost(&c->h_header, kHeaderBytes) != cudaSuccess || !ensure_fixed(c)) {
+    if (!c->ensure_slots(1) || !c->ctl_host.ensure(1) || !c->h_header.ensure(kHeaderBytes) ||
+        cudaEventCreateWithFlags(&c->fork, cudaEventDisableTiming) != cudaSuccess) {
         gbsz_destroy(c);
         cudaGetLastError();
         return GBSZ_ERR_OOM;
@@ -308,19 +545,21 @@ void gbsz_destroy(gbsz_ctx *c)
     if (!c) return;
     DevGuard g(c->device);
     cudaDeviceSynchronize();
-    for (Buf *b : {&c->codes, &c->dscr, &c->lb_flag, &c->lb_agg, &c->lb_inc, &c->chunk_off, &c->faces, &c->hist,
-                   &c->cw64, &c->cw32, &c->codes_only, &c->keyA, &c->keyB, &c->nodef, &c->parent, &c->distA,
-                   &c->distB, &c->parA, &c->parB, &c->lut, &c->first, &c->count, &c->start, &c->sorted,
-                   &c->stage_field, &c->stage_archive})
-        b->release();
+    for (Slot *s : c->slots) {
+        s->release();
+        delete s;
+    }
+    c->slots.clear();
+    c->stage_field.release();
+    c->stage_archive.release();
+    c->ctl_host.release();
+    c->h_header.release();
     for (auto &r : c->recs) {
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
     for (auto e : c->pool) cudaEventDestroy(e);
-    if (c->ctl) cudaFree(c->ctl);
-    if (c->ctl_host) cudaFreeHost(c->ctl_host);
-    if (c->h_header) cudaFreeHost(c->h_header);
+    if (c->fork) cudaEventDestroy(c->fork);
     delete c;
 }
 
@@ -344,105 +583,34 @@ size_t gbsz_compress_bound(const gbsz_params *p)
 gbsz_status gbsz_compress(gbsz_ctx *c, const float *d_field, const gbsz_params *pin, void *d_archive,
                           size_t capacity, size_t *out_bytes, void *stream)
 {
-    uint64_t n;
-    if (!c || !d_field || !d_archive || !out_bytes || !valid_params(pin, &n)) return GBSZ_ERR_INVALID_ARG;
-    if (reinterpret_cast<uintptr_t>(d_archive) & 15) return GBSZ_ERR_INVALID_ARG;
-    gbsz_params p = *pin;
-    if (p.chunk == 0) p.chunk = auto_chunk(n);
+    if (!c || !out_bytes) return GBSZ_ERR_INVALID_ARG;
     *out_bytes = 0;
+    gbsz_params p;
+    uint64_t n;
+    size_t need = 0;
+    gbsz_status s = check_compress(d_field, pin, d_archive, capacity, &p, &n, &need);
+    if (s != GBSZ_OK) {
+        *out_bytes = need;
+        return s;
+    }
     DevGuard g(c->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     c->last_stream = st;
-    const uint32_t nbins = 2 * p.radius;
-    const uint64_t nchunk = (n + p.chunk - 1) / p.chunk;
-    const Layout Lmin = make_layout(p.radius, nchunk, 0, 0, 0);
-    if (capacity < Lmin.stream) {
-        *out_bytes = Lmin.stream;
-        return GBSZ_ERR_CAPACITY;
-    }
-    const uint64_t U = p.chunk > kUnitSymbols ? p.chunk : kUnitSymbols;
-    const uint64_t nunits = (n + U - 1) / U;
-    if (!c->codes.ensure(n * 2 + 64) || !c->dscr.ensure(n * 4 + 64)) return GBSZ_ERR_OOM;
-    if (nunits > c->lb_units) {
-        if (!c->lb_flag.ensure(nunits * 4) || !c->lb_agg.ensure(nunits * 16) || !c->lb_inc.ensure(nunits * 16))
-            return GBSZ_ERR_OOM;
-        cudaMemsetAsync(c->lb_flag.p, 0, c->lb_flag.cap, st);
-        // capacity in units is that of the smallest of the three arrays
-        c->lb_units = std::min(c->lb_flag.cap / 4, std::min(c->lb_agg.cap, c->lb_inc.cap) / 16);
-        c->epoch = 0;
-    }
-    if (++c->epoch >= (1u << 29)) {
-        cudaMemsetAsync(c->lb_flag.p, 0, c->lb_flag.cap, st);
-        c->epoch = 1;
-    }
-    cudaMemsetAsync(c->ctl, 0, sizeof(Control), st);
-    cudaMemsetAsync(c->hist.p, 0, nbins * 4, st);
-
-    cudaEvent_t e0;
-    stage_begin(c, st, &e0);
-    launch_minmax_eb(d_field, n, c->ctl, p.eb, p.eb_mode, c->num_sms, st);
-    stage_end(c, st, 0, e0);
-
-    QuantArgs q{};
-    q.x = d_field;
-    for (int i = 0; i < 3; i++) q.dims[i] = p.dims[i];
-    q.ndim = p.ndim;
-    q.radius = p.radius;
-    q.codes = c->codes.as<uint16_t>();
-    q.dscr = c->dscr.as<int32_t>();
-    q.hist = c->hist.as<uint32_t>();
-    q.ctl = c->ctl;
-    q.num_sms = c->num_sms;
-    stage_begin(c, st, &e0);
-    launch_dualquant(q, st);
-    stage_end(c, st, 1, e0);
-
-    CodebookArgs cb = codebook_args(c);
-    cb.hist = c->hist.as<uint32_t>();
-    cb.nbins = nbins;
-    cb.len_out = static_cast<uint8_t *>(d_archive) + kHeaderBytes;
-    stage_begin(c, st, &e0);
-    launch_codebook(cb, st);
-    stage_end(c, st, 2, e0);
-
-    EncodeArgs en{};
-    en.codes = q.codes;
-    en.x = d_field;
-    en.dscr = q.dscr;
-    en.n = n;
-    en.chunk = p.chunk;
-    en.radius = p.radius;
-    en.nbins = nbins;
-    en.cw64 = cb.cw64;
-    en.cw32 = cb.cw32;
-    en.archive = static_cast<uint8_t *>(d_archive);
-    en.capacity = capacity;
-    en.lb_flag = c->lb_flag.as<uint32_t>();
-    en.lb_agg = c->lb_agg.as<ulonglong2>();
-    en.lb_inc = c->lb_inc.as<ulonglong2>();
-    en.epoch = c->epoch;
-    en.ctl = c->ctl;
-    en.ndim = p.ndim;
-    en.eb_mode = p.eb_mode;
-    for (int i = 0; i < 3; i++) en.dims[i] = p.dims[i];
-    en.eb = p.eb;
-    en.num_sms = c->num_sms;
-    stage_begin(c, st, &e0);
-    launch_encode(en, st);
-    stage_end(c, st, 3, e0);
-    c->launches += 4;
-
-    c->last_n = n;
-    c->last_nbins = nbins;
-    c->have_compress = true;
-    gbsz_status s = finish(c, st);
+    Slot *sl = c->slots[0];
+    s = enqueue_compress(c, sl, d_field, p, n, d_archive, capacity, st);
     if (s != GBSZ_OK) return s;
-    const uint32_t derr = c->ctl_host->error;
-    *out_bytes = (size_t)c->ctl_host->total;
-    c->last_sc[0] = c->ctl_host->eb;
-    c->last_sc[1] = c->ctl_host->ebx2;
-    c->last_sc[2] = c->ctl_host->inv2eb;
-    return map_device_error(derr);
+    c->last_n = n;
+    c->last_nbins = 2 * p.radius;
+    c->have_compress = true;
+    if (cudaMemcpyAsync(c->ctl_host.p, sl->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        return GBSZ_ERR_CUDA;
+    const Control &ch = c->ctl_host.p[0];
+    *out_bytes = (size_t)ch.total;
+    c->last_sc[0] = ch.eb;
+    c->last_sc[1] = ch.ebx2;
+    c->last_sc[2] = ch.inv2eb;
+    return map_device_error(ch.error);
 }
 
 gbsz_status gbsz_archive_info(const void *h_archive, size_t bytes, gbsz_params *out, uint64_t *n)
@@ -466,83 +634,122 @@ gbsz_status gbsz_decompress(gbsz_ctx *c, const void *d_archive, size_t bytes, fl
     DevGuard g(c->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     c->last_stream = st;
-    if (cudaMemcpyAsync(c->h_header, d_archive, kHeaderBytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+    if (cudaMemcpyAsync(c->h_header.p, d_archive, kHeaderBytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return GBSZ_ERR_CUDA;
     Header h;
-    gbsz_status s = parse_header(c->h_header, bytes, &h);
+    gbsz_status s = parse_header(c->h_header.p, bytes, &h);
     if (s != GBSZ_OK) return s;
     if (h.n > capacity_elems) return GBSZ_ERR_CAPACITY;
-    const uint64_t n = h.n;
-    const uint64_t nfaces = recon_faces_entries(h.p.ndim, h.p.dims);
-    if (!c->codes.ensure(n * 2 + 64) || !c->dscr.ensure(n * 4 + 64) || !c->chunk_off.ensure(h.nchunk * 8 + 8) ||
-        !c->faces.ensure(nfaces * 4 + 16))
-        return GBSZ_ERR_OOM;
-    cudaMemsetAsync(c->ctl, 0, sizeof(Control), st);
-    const uint8_t *arc = static_cast<const uint8_t *>(d_archive);
-
-    CodebookArgs cb = codebook_args(c);
-    cb.len_in = arc + kHeaderBytes;
-    cb.nbins = 2 * h.p.radius;
-    cb.expect_maxlen = h.maxlen;
-    cudaEvent_t e0;
-    stage_begin(c, st, &e0);
-    launch_decode_tables(cb, st);
-    stage_end(c, st, 4, e0);
-
-    DecodeArgs d{};
-    d.archive = arc;
-    d.n = n;
-    d.chunk = h.p.chunk;
-    d.nchunk = (uint32_t)h.nchunk;
-    d.radius = h.p.radius;
-    d.maxlen = h.maxlen;
-    d.words = h.w;
-    d.off_bits = h.L.bits;
-    d.off_stream = h.L.stream;
-    d.lut = cb.lut;
-    d.first = cb.first;
-    d.count = cb.count;
-    d.start = cb.start;
-    d.sorted = cb.sorted;
-    d.chunk_off = c->chunk_off.as<unsigned long long>();
-    d.codes = c->codes.as<uint16_t>();
-    d.ctl = c->ctl;
-    stage_begin(c, st, &e0);
-    launch_decode(d, st);
-    stage_end(c, st, 5, e0);
-
-    ReconArgs r{};
-    r.codes = d.codes;
-    r.archive = arc;
-    r.off_outl = h.L.outl;
-    r.off_exc = h.L.exc;
-    r.m = h.m;
-    r.e = h.e;
-    r.ndim = h.p.ndim;
-    for (int i = 0; i < 3; i++) r.dims[i] = h.p.dims[i];
-    r.radius = h.p.radius;
-    r.ebx2 = h.ebx2;
-    r.dscr = c->dscr.as<int32_t>();
-    r.faces = c->faces.as<uint32_t>();
-    r.faces_cap = nfaces;
-    r.out = d_field;
-    r.ctl = c->ctl;
-    r.num_sms = c->num_sms;
-    int nl = 0;
-    stage_begin(c, st, &e0);
-    launch_reconstruct(r, st, &nl);
-    stage_end(c, st, 6, e0);
-    c->launches += 3 + nl;
-
-    c->last_dn = n;
-    c->have_decompress = true;
-    s = finish(c, st);
+    Slot *sl = c->slots[0];
+    s = enqueue_decompress(c, sl, h, d_archive, d_field, st);
     if (s != GBSZ_OK) return s;
-    const uint32_t derr = c->ctl_host->error;
-    if (derr) return map_device_error(derr);
-    if (c->ctl_host->zeros != h.m) return GBSZ_ERR_CORRUPT;
-    return GBSZ_OK;
+    c->last_dn = h.n;
+    c->have_decompress = true;
+    if (cudaMemcpyAsync(c->ctl_host.p, sl->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
+        return GBSZ_ERR_CUDA;
+    return decompress_status(c->ctl_host.p[0], h);
+}
+
+gbsz_status gbsz_compress_batch(gbsz_ctx *c, uint32_t count, const float *const *d_fields,
+                                const gbsz_params *params, void *const *d_archives, const size_t *capacities,
+                                size_t *out_bytes, gbsz_status *statuses, void *stream)
+{
+    if (!c || !d_fields || !params || !d_archives || !capacities || !out_bytes || !statuses)
+        return GBSZ_ERR_INVALID_ARG;
+    if (count == 0) return GBSZ_OK;
+    DevGuard g(c->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    const int K = (int)std::min<uint32_t>(count, kMaxSlots);
+    if (!c->ensure_slots(K) || !c->ctl_host.ensure(count)) return GBSZ_ERR_OOM;
+    std::vector<gbsz_params> rp(count);
+    std::vector<uint64_t> rn(count);
+    for (uint32_t i = 0; i < count; i++) {
+        size_t need = 0;
+        out_bytes[i] = 0;
+        statuses[i] = check_compress(d_fields[i], &params[i], d_archives[i], capacities[i], &rp[i], &rn[i], &need);
+        if (statuses[i] == GBSZ_ERR_CAPACITY) out_bytes[i] = need;
+    }
+    cudaEventRecord(c->fork, st);
+    for (int k = 0; k < K; k++) cudaStreamWaitEvent(c->slots[k]->stream, c->fork, 0);
+    for (uint32_t i = 0; i < count; i++) {
+        if (statuses[i] != GBSZ_OK) continue;
+        Slot *sl = c->slots[i % K];
+        statuses[i] = enqueue_compress(c, sl, d_fields[i], rp[i], rn[i], d_archives[i], capacities[i], sl->stream);
+        if (statuses[i] == GBSZ_OK)
+            cudaMemcpyAsync(&c->ctl_host.p[i], sl->ctl, sizeof(Control), cudaMemcpyDeviceToHost, sl->stream);
+    }
+    for (int k = 0; k < K; k++) {
+        cudaEventRecord(c->slots[k]->done, c->slots[k]->stream);
+        cudaStreamWaitEvent(st, c->slots[k]->done, 0);
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GBSZ_ERR_CUDA;
+    gbsz_status first = GBSZ_OK;
+    for (uint32_t i = 0; i < count; i++) {
+        if (statuses[i] == GBSZ_OK) {
+            out_bytes[i] = (size_t)c->ctl_host.p[i].total;
+            statuses[i] = map_device_error(c->ctl_host.p[i].error);
+        }
+        if (first == GBSZ_OK) first = statuses[i];
+    }
+    return first;
+}
+
+gbsz_status gbsz_decompress_batch(gbsz_ctx *c, uint32_t count, const void *const *d_archives, const size_t *bytes,
+                                  float *const *d_fields, const uint64_t *capacities, gbsz_status *statuses,
+                                  void *stream)
+{
+    if (!c || !d_archives || !bytes || !d_fields || !capacities || !statuses) return GBSZ_ERR_INVALID_ARG;
+    if (count == 0) return GBSZ_OK;
+    DevGuard g(c->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    c->last_stream = st;
+    const int K = (int)std::min<uint32_t>(count, kMaxSlots);
+    if (!c->ensure_slots(K) || !c->ctl_host.ensure(count) || !c->h_header.ensure((size_t)count * kHeaderBytes))
+        return GBSZ_ERR_OOM;
+    for (uint32_t i = 0; i < count; i++) {
+        statuses[i] = GBSZ_OK;
+        if (!d_archives[i] || !d_fields[i] || (reinterpret_cast<uintptr_t>(d_archives[i]) & 15) ||
+            (reinterpret_cast<uintptr_t>(d_fields[i]) & 15)) {
+            statuses[i] = GBSZ_ERR_INVALID_ARG;
+            continue;
+        }
+        if (bytes[i] < kHeaderBytes) {
+            statuses[i] = GBSZ_ERR_CORRUPT;
+            continue;
+        }
+        cudaMemcpyAsync(c->h_header.p + (size_t)i * kHeaderBytes, d_archives[i], kHeaderBytes,
+                        cudaMemcpyDeviceToHost, st);
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess) return GBSZ_ERR_CUDA;
+    std::vector<Header> hs(count);
+    for (uint32_t i = 0; i < count; i++) {
+        if (statuses[i] != GBSZ_OK) continue;
+        statuses[i] = parse_header(c->h_header.p + (size_t)i * kHeaderBytes, bytes[i], &hs[i]);
+        if (statuses[i] == GBSZ_OK && hs[i].n > capacities[i]) statuses[i] = GBSZ_ERR_CAPACITY;
+    }
+    cudaEventRecord(c->fork, st);
+    for (int k = 0; k < K; k++) cudaStreamWaitEvent(c->slots[k]->stream, c->fork, 0);
+    for (uint32_t i = 0; i < count; i++) {
+        if (statuses[i] != GBSZ_OK) continue;
+        Slot *sl = c->slots[i % K];
+        statuses[i] = enqueue_decompress(c, sl, hs[i], d_archives[i], d_fields[i], sl->stream);
+        if (statuses[i] == GBSZ_OK)
+            cudaMemcpyAsync(&c->ctl_host.p[i], sl->ctl, sizeof(Control), cudaMemcpyDeviceToHost, sl->stream);
+    }
+    for (int k = 0; k < K; k++) {
+        cudaEventRecord(c->slots[k]->done, c->slots[k]->stream);
+        cudaStreamWaitEvent(st, c->slots[k]->done, 0);
+    }
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GBSZ_ERR_CUDA;
+    gbsz_status first = GBSZ_OK;
+    for (uint32_t i = 0; i < count; i++) {
+        if (statuses[i] == GBSZ_OK) statuses[i] = decompress_status(c->ctl_host.p[i], hs[i]);
+        if (first == GBSZ_OK) first = statuses[i];
+    }
+    return first;
 }
 
 gbsz_status gbsz_compress_host(gbsz_ctx *c, const float *h_field, const gbsz_params *p, void *h_archive,
@@ -590,17 +797,18 @@ gbsz_status gbsz_debug_copy(gbsz_ctx *c, int which, void *h_dst, size_t bytes)
 {
     if (!c || !h_dst) return GBSZ_ERR_INVALID_ARG;
     DevGuard g(c->device);
+    Slot *sl = c->slots[0];
     const void *src = nullptr;
     size_t need = 0;
     switch (which) {
-    case 0: src = c->codes.p; need = c->have_compress ? c->last_n * 2 : 0; break;
-    case 1: src = c->hist.p; need = c->have_compress ? c->last_nbins * 4 : 0; break;
+    case 0: src = sl->codes.p; need = c->have_compress ? c->last_n * 2 : 0; break;
+    case 1: src = sl->hist.p; need = c->have_compress ? c->last_nbins * 4 : 0; break;
     case 2:
         if (!c->have_compress || bytes != 12) return GBSZ_ERR_INVALID_ARG;
         std::memcpy(h_dst, c->last_sc, 12);
         return GBSZ_OK;
-    case 3: src = c->codes.p; need = c->have_decompress ? c->last_dn * 2 : 0; break;
-    case 4: src = c->codes_only.p; need = c->have_compress ? c->last_nbins * 8 : 0; break;
+    case 3: src = sl->codes.p; need = c->have_decompress ? c->last_dn * 2 : 0; break;
+    case 4: src = sl->codes_only.p; need = c->have_compress ? c->last_nbins * 8 : 0; break;
     default: return GBSZ_ERR_INVALID_ARG;
     }
     if (need == 0 || bytes != need) return GBSZ_ERR_INVALID_ARG;

@@ -21,7 +21,12 @@ namespace gbsz {
 namespace {
 
 constexpr int kCbThreads = 1024;
-constexpr uint32_t kRankSortMax = 2048;
+constexpr uint32_t kRankSortMax = 0;     // rank sort unused; bitonic covers small n
+constexpr uint32_t kBitonicMax = 8192;    // 8192 keys = 64 KB of shared memory
+// merge state (4k words) in shared memory up to this many used symbols, and
+// the pointer-jumping buffers too (12k words in all) up to kDepthSmemMax
+constexpr uint32_t kMergeSmemMax = 4096;
+constexpr uint32_t kDepthSmemMax = 1024;
 
 // Stable sort of n unique 64-bit keys by bits [bit_lo, bit_hi); the keys are
 // already ordered by the bits below bit_lo.  Returns the buffer holding the
@@ -31,6 +36,36 @@ __device__ unsigned long long *cta_sort(unsigned long long *a, unsigned long lon
 {
     const uint32_t T = blockDim.x, t = threadIdx.x;
     if (n <= 1 || bit_lo >= bit_hi) return a;
+    if (n <= kBitonicMax) {
+        // bitonic sort in shared memory of the full (unique) keys, padded to a
+        // power of two with all-ones keys; the order of unique keys is the
+        // order by the selected bits with ties in their original order,
+        // because every caller's low bits (the symbol) ascend in input order
+        unsigned long long *sk = reinterpret_cast<unsigned long long *>(s_cnt);
+        uint32_t m = 1;
+        while (m < n) m <<= 1;
+        const unsigned long long hmask = bit_hi >= 64 ? ~0ull : ((1ull << bit_hi) - 1);
+        for (uint32_t i = t; i < m; i += T) sk[i] = i < n ? (a[i] & hmask) : ~0ull;
+        __syncthreads();
+        for (uint32_t size = 2; size <= m; size <<= 1) {
+            for (uint32_t stride = size >> 1; stride > 0; stride >>= 1) {
+                for (uint32_t p = t; p < m / 2; p += T) {
+                    const uint32_t i = 2 * p - (p & (stride - 1));  // lower index of the pair
+                    const uint32_t j = i + stride;
+                    const bool up = (i & size) == 0;
+                    const unsigned long long x = sk[i], y = sk[j];
+                    if ((x > y) == up) {
+                        sk[i] = y;
+                        sk[j] = x;
+                    }
+                }
+                __syncthreads();
+            }
+        }
+        for (uint32_t i = t; i < n; i += T) b[i] = sk[i];
+        __syncthreads();
+        return b;
+    }
     if (n <= kRankSortMax) {
         // rank sort through shared memory: rank = number of smaller keys
         unsigned long long *sk = reinterpret_cast<unsigned long long *>(s_cnt);
@@ -137,12 +172,100 @@ __device__ void canonicalize(const uint8_t *len, uint32_t nbins, unsigned long l
     __syncthreads();
 }
 
+// Two-queue Huffman merge in phases (all threads).  LF: leaf frequencies in
+// (frequency, symbol) order; F: internal frequencies in creation order; P:
+// parent of every node (leaves 0..k-1, internal node i has id k+i).  With a,
+// b the two smallest available nodes, every available node of frequency
+// <= a + b is consumed, in merge order (leaf first on equal frequency),
+// before any node not yet created, so the phase pairs that whole prefix.
+__device__ void phase_merge(const uint32_t *LF, uint32_t *F, uint32_t *P, uint32_t k, Control *ctl)
+{
+    __shared__ uint32_t s_lh, s_ih, s_ni, s_cl, s_ci, s_np;
+    const uint32_t t = threadIdx.x, T = blockDim.x;
+    if (t == 0) {
+        s_lh = 0;
+        s_ih = 0;
+        s_ni = 0;
+    }
+    __syncthreads();
+    for (;;) {
+        if (t == 0) {
+            const uint32_t lh = s_lh, ih = s_ih, ni = s_ni;
+            if ((k - lh) + (ni - ih) <= 1) {
+                s_np = 0;
+            } else {
+                uint32_t x = lh, y = ih;
+                unsigned long long f2 = 0;
+                for (int r = 0; r < 2; r++) {
+                    if (x < k && (y >= ni || LF[x] <= F[y])) f2 += LF[x++];
+                    else f2 += F[y++];
+                }
+                // counts of available nodes with frequency <= f2
+                uint32_t l0 = lh, l1 = k;
+                while (l0 < l1) {
+                    const uint32_t m = (l0 + l1) >> 1;
+                    if ((unsigned long long)LF[m] <= f2) l0 = m + 1;
+                    else l1 = m;
+                }
+                uint32_t i0 = ih, i1 = ni;
+                while (i0 < i1) {
+                    const uint32_t m = (i0 + i1) >> 1;
+                    if ((unsigned long long)F[m] <= f2) i0 = m + 1;
+                    else i1 = m;
+                }
+                s_cl = l0 - lh;
+                s_ci = i0 - ih;
+                s_np = (s_cl + s_ci) >> 1;
+            }
+        }
+        __syncthreads();
+        const uint32_t np = s_np;
+        if (np == 0) break;
+        const uint32_t lh = s_lh, ih = s_ih, ni = s_ni, cl = s_cl, ci = s_ci;
+        // merge-path split: number of leaves among the first d merged nodes
+        auto split = [&](uint32_t d) -> uint32_t {
+            uint32_t l0 = d > ci ? d - ci : 0, l1 = min(d, cl);
+            while (l0 < l1) {
+                const uint32_t m = (l0 + l1) >> 1, b = d - m;
+                if (b == 0 || m == cl || F[ih + b - 1] < LF[lh + m]) l1 = m;
+                else l0 = m + 1;
+            }
+            return l0;
+        };
+        for (uint32_t p = t; p < np; p += T) {
+            uint32_t x = split(2 * p), y = 2 * p - x;
+            uint32_t f = 0;
+            for (int r = 0; r < 2; r++) {
+                if (x < cl && (y >= ci || LF[lh + x] <= F[ih + y])) {
+                    f += LF[lh + x];
+                    P[lh + x] = k + ni + p;
+                    x++;
+                } else {
+                    f += F[ih + y];
+                    P[k + ih + y] = k + ni + p;
+                    y++;
+                }
+            }
+            F[ni + p] = f;
+        }
+        __syncthreads();
+        if (t == 0) {
+            const uint32_t x = split(2 * np);
+            s_lh = lh + x;
+            s_ih = ih + (2 * np - x);
+            s_ni = ni + np;
+        }
+        __syncthreads();
+    }
+    if (t == 0 && s_ni != k - 1) atomicOr(&ctl->error, DERR_INTERNAL);
+    __syncthreads();
+}
+
 __global__ void __launch_bounds__(kCbThreads, 1) k_codebook(CodebookArgs a)
 {
     extern __shared__ uint32_t s_cnt[];  // 16 * kCbThreads words
     __shared__ Canon canon;
     __shared__ uint32_t s_scan[33];
-    __shared__ uint32_t s_lh, s_ih, s_ni, s_cl, s_ci, s_np;
     const uint32_t T = blockDim.x, t = threadIdx.x, nbins = a.nbins;
 
     // symbols with nonzero frequency, keys (freq << 16 | sym) in symbol order
@@ -177,89 +300,20 @@ __global__ void __launch_bounds__(kCbThreads, 1) k_codebook(CodebookArgs a)
     if (k == 1) {
         if (t == 0) a.len_out[K[0] & 0xFFFFu] = 1;
     } else {
-        // phase-parallel two-queue merge
-        uint32_t *F = a.nodef;    // internal node frequencies, creation order
-        uint32_t *P = a.parent;   // parent of every node (leaves 0..k-1, internal k..)
-        auto LF = [&](uint32_t i) -> uint32_t { return (uint32_t)(K[i] >> 16); };
-        if (t == 0) {
-            s_lh = 0;
-            s_ih = 0;
-            s_ni = 0;
-        }
+        // leaf frequencies, internal frequencies and parents: in shared memory
+        // (the sort's buffer, free now) up to kMergeSmemMax used symbols
+        const bool sm_merge = k <= kMergeSmemMax;
+        uint32_t *LF = sm_merge ? s_cnt : a.distB;
+        uint32_t *F = sm_merge ? LF + k : a.nodef;
+        uint32_t *P = sm_merge ? F + k : a.parent;
+        for (uint32_t i = t; i < k; i += T) LF[i] = (uint32_t)(K[i] >> 16);
         __syncthreads();
-        for (;;) {
-            if (t == 0) {
-                const uint32_t lh = s_lh, ih = s_ih, ni = s_ni;
-                if ((k - lh) + (ni - ih) <= 1) {
-                    s_np = 0;
-                } else {
-                    uint32_t x = lh, y = ih;
-                    unsigned long long f2 = 0;
-                    for (int r = 0; r < 2; r++) {
-                        if (x < k && (y >= ni || LF(x) <= F[y])) f2 += LF(x++);
-                        else f2 += F[y++];
-                    }
-                    // counts of available nodes with frequency <= f2
-                    uint32_t l0 = lh, l1 = k;
-                    while (l0 < l1) {
-                        const uint32_t m = (l0 + l1) >> 1;
-                        if ((unsigned long long)LF(m) <= f2) l0 = m + 1;
-                        else l1 = m;
-                    }
-                    uint32_t i0 = ih, i1 = ni;
-                    while (i0 < i1) {
-                        const uint32_t m = (i0 + i1) >> 1;
-                        if ((unsigned long long)F[m] <= f2) i0 = m + 1;
-                        else i1 = m;
-                    }
-                    s_cl = l0 - lh;
-                    s_ci = i0 - ih;
-                    s_np = (s_cl + s_ci) >> 1;
-                }
-            }
-            __syncthreads();
-            const uint32_t np = s_np;
-            if (np == 0) break;
-            const uint32_t lh = s_lh, ih = s_ih, ni = s_ni, cl = s_cl, ci = s_ci;
-            // merge-path split: number of leaves among the first d merged nodes
-            auto split = [&](uint32_t d) -> uint32_t {
-                uint32_t l0 = d > ci ? d - ci : 0, l1 = min(d, cl);
-                while (l0 < l1) {
-                    const uint32_t m = (l0 + l1) >> 1, b = d - m;
-                    if (b == 0 || m == cl || F[ih + b - 1] < LF(lh + m)) l1 = m;
-                    else l0 = m + 1;
-                }
-                return l0;
-            };
-            for (uint32_t p = t; p < np; p += T) {
-                uint32_t x = split(2 * p), y = 2 * p - x;
-                uint32_t f = 0;
-                for (int r = 0; r < 2; r++) {
-                    if (x < cl && (y >= ci || LF(lh + x) <= F[ih + y])) {
-                        f += LF(lh + x);
-                        P[lh + x] = k + ni + p;
-                        x++;
-                    } else {
-                        f += F[ih + y];
-                        P[k + ih + y] = k + ni + p;
-                        y++;
-                    }
-                }
-                F[ni + p] = f;
-            }
-            __syncthreads();
-            if (t == 0) {
-                const uint32_t x = split(2 * np);
-                s_lh = lh + x;
-                s_ih = ih + (2 * np - x);
-                s_ni = ni + np;
-            }
-            __syncthreads();
-        }
-        if (t == 0 && s_ni != k - 1) atomicOr(&a.ctl->error, DERR_INTERNAL);
-        // depths by pointer jumping over 2k-1 nodes; root = 2k-2
+        phase_merge(LF, F, P, k, a.ctl);
+        // depths by pointer jumping over 2k-1 nodes; root = 2k-2; depth <= 45
+        const bool sm_depth = k <= kDepthSmemMax;
         const uint32_t N = 2 * k - 1, root = N - 1;
-        uint32_t *pa = a.parA, *da = a.distA, *pb = a.parB, *db = a.distB;
+        uint32_t *pa = sm_depth ? P + 2 * k : a.parA, *da = sm_depth ? pa + 2 * k : a.distA;
+        uint32_t *pb = sm_depth ? da + 2 * k : a.parB, *db = sm_depth ? pb + 2 * k : a.distB;
         for (uint32_t i = t; i < N; i += T) {
             pa[i] = i == root ? root : P[i];
             da[i] = i == root ? 0u : 1u;
@@ -302,13 +356,10 @@ __global__ void __launch_bounds__(kCbThreads, 1) k_decode_tables(CodebookArgs a)
     extern __shared__ uint32_t s_cnt[];
     __shared__ Canon canon;
     __shared__ uint32_t s_scan[33];
-    __shared__ unsigned long long s_kraft;
+    __shared__ unsigned long long s_scan64[33];
     __shared__ uint32_t s_bad;
     const uint32_t T = blockDim.x, t = threadIdx.x, nbins = a.nbins;
-    if (t == 0) {
-        s_kraft = 0;
-        s_bad = 0;
-    }
+    if (t == 0) s_bad = 0;
     __syncthreads();
     uint32_t ml = 0;
     unsigned long long kr = 0;
@@ -328,9 +379,9 @@ __global__ void __launch_bounds__(kCbThreads, 1) k_decode_tables(CodebookArgs a)
         const uint32_t l = a.len_in[s];
         if (l) kr += 1ull << (ml - l);
     }
-    atomicAdd(&s_kraft, kr);
-    __syncthreads();
-    if (s_kraft > (1ull << ml)) {
+    unsigned long long ktot;
+    block_excl_scan64(kr, s_scan64, &ktot);
+    if (ktot > (1ull << ml)) {
         if (t == 0) atomicOr(&a.ctl->error, DERR_CORRUPT);
         return;
     }

@@ -1,21 +1,29 @@
 // k_encode.cu -- S5: Huffman encode + deflate (Sec. 3.2.4) and S6 archive
 // assembly.
 //
-// The paper deflates one chunk per thread.  Here a CTA of 128 threads works
-// on a unit of 4096 symbols (32 per thread; a unit holds 4096/C chunks when
-// C <= 4096, or is one C-symbol chunk of C/4096 tiles otherwise):
-//   pass 1  code lengths -> per-thread bit counts, block scans give each
-//           chunk's bits and the unit's words, outliers and exceptions;
-//   look-back  a decoupled look-back over units (bounded waits) turns unit
-//           totals into global word / outlier / exception offsets;
-//   pass 2  each thread packs its codewords MSB-first into a shared-memory
-//           copy of the unit's words, which is written out with 16-byte
-//           stores; outliers (idx, delta) and exceptions (idx, raw bits) are
-//           emitted in index order at their global offsets.
-// Outlier residuals were parked per point by the dual-quant kernel; whether a
-// code-0 point is a verbatim exception is recomputed from the input value
-// with the same prequantization function.
+// The paper deflates one chunk per thread.  Here one warp deflates one work
+// unit with warp-level scans and shuffles only, in three fully parallel
+// phases with no waiting between CTAs:
+//   lanes     each lane owns S = min(128, C) consecutive symbols, so chunk
+//             boundaries fall on lane boundaries; a unit is 32*S symbols
+//             (4096/C chunks) or, for C > 4096, one whole chunk in rounds of
+//             4096 symbols;
+//   count     code lengths -> bits per lane -> chunk bits (segmented warp
+//             sums, written to the archive's chunk table) -> the unit's
+//             words, outliers and exceptions;
+//   scan      exclusive prefix sums of the unit totals give every unit's
+//             global word / outlier / exception offsets;
+//   pack      each lane packs its codewords MSB-first into 32-bit words and
+//             stores the words it owns; the word it shares with the previous
+//             lane of the same chunk is handed to that lane by a shuffle and
+//             stored once, merged; outliers (idx, delta) and exceptions (idx,
+//             raw bits) are written in index order at their global offsets;
+//             the last unit writes the header.
+// The dual-quant kernel parked {residual, is-exception} for every code-0
+// point; it is read only where there are outliers (exception flags only when
+// the field has exceptions at all), and the field only for exceptions.
 #include "common.cuh"
+#include "scan.cuh"
 
 #include <algorithm>
 
@@ -23,169 +31,125 @@ namespace gbsz {
 
 namespace {
 
-constexpr int kEncThreads = 128;
-constexpr int kSPT = 32;
-constexpr int kTile = kEncThreads * kSPT;
-constexpr int kMaxTileWords = kTile * kMaxLen / 32 + 4;
-
-struct Entry {
-    uint32_t len;
-    unsigned long long code;
-};
+constexpr int kEncThreads = 256;
+constexpr int kWarps = kEncThreads / 32;
+constexpr uint32_t kLaneMax = 128;  // symbols per lane
+constexpr uint32_t kRound = 32 * kLaneMax;
 
 template <bool CW32>
 struct Table {
     const void *tab;
-    __device__ __forceinline__ Entry get(uint32_t sym) const
+    __device__ __forceinline__ void get(uint32_t sym, uint32_t &len, unsigned long long &code) const
     {
-        Entry e;
         if (CW32) {
             const uint32_t v = static_cast<const uint32_t *>(tab)[sym];
-            e.len = v >> 24;
-            e.code = v & 0xFFFFFFu;
+            len = v >> 24;
+            code = v & 0xFFFFFFu;
         } else {
             const unsigned long long v = static_cast<const unsigned long long *>(tab)[sym];
-            e.len = (uint32_t)(v >> 56);
-            e.code = v & ((1ull << 56) - 1);
+            len = (uint32_t)(v >> 56);
+            code = v & ((1ull << 56) - 1);
         }
-        return e;
+    }
+    __device__ __forceinline__ uint32_t len_of(uint32_t sym) const
+    {
+        if (CW32) return static_cast<const uint32_t *>(tab)[sym] >> 24;
+        return (uint32_t)(static_cast<const unsigned long long *>(tab)[sym] >> 56);
     }
 };
 
-// bit writer into shared-memory words; the first word starts `skip` bits in
-__device__ __forceinline__ void put_bits(unsigned long long &acc, uint32_t &nacc, uint32_t &widx,
-                                         uint32_t *sw, unsigned long long code, uint32_t len)
+__device__ __forceinline__ uint32_t warp_sum(uint32_t v)
 {
-    if (len > 32) {
-        const uint32_t hl = len - 32;
-        acc = (acc << hl) | (code >> 32);
-        nacc += hl;
-        if (nacc >= 32) {
-            atomicOr(&sw[widx++], (uint32_t)(acc >> (nacc - 32)));
-            nacc -= 32;
-            acc &= (1ull << nacc) - 1;
-        }
-        code &= 0xFFFFFFFFull;
-        len = 32;
-    }
-    acc = (acc << len) | code;
-    nacc += len;
-    if (nacc >= 32) {
-        atomicOr(&sw[widx++], (uint32_t)(acc >> (nacc - 32)));
-        nacc -= 32;
-        acc &= (1ull << nacc) - 1;
-    }
-}
-
-__device__ __forceinline__ void flush_bits(unsigned long long acc, uint32_t nacc, uint32_t widx, uint32_t *sw)
-{
-    if (nacc) atomicOr(&sw[widx], (uint32_t)(acc << (32 - nacc)));
-}
-
-struct Smem {
-    uint32_t words[kMaxTileWords];
-    uint32_t e[kEncThreads + 1];
-    uint32_t wo[kEncThreads + 1];
-    uint32_t scan[33];
-    unsigned long long scan64[33];
-    uint32_t unit;
-    unsigned long long excl_w, excl_oe;
-    uint32_t carry;
-};
-
-__device__ __forceinline__ void load_codes(const uint16_t *codes, uint64_t n, uint64_t s0, uint32_t *cr)
-{
-    if (s0 + kSPT <= n) {
-        const uint4 *p = reinterpret_cast<const uint4 *>(codes + s0);
 #pragma unroll
-        for (int v = 0; v < 4; v++) {
-            const uint4 w = p[v];
-            cr[4 * v + 0] = w.x;
-            cr[4 * v + 1] = w.y;
-            cr[4 * v + 2] = w.z;
-            cr[4 * v + 3] = w.w;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// sum over aligned groups of g lanes (g a power of two)
+__device__ __forceinline__ uint32_t group_sum(uint32_t v, uint32_t g)
+{
+    for (uint32_t o = 1; o < g; o <<= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// exclusive scan inside aligned groups of g lanes
+__device__ __forceinline__ uint32_t group_excl_scan(uint32_t v, uint32_t g)
+{
+    const uint32_t lane = threadIdx.x & 31, gl = lane & (g - 1);
+    uint32_t inc = v;
+    for (uint32_t o = 1; o < g; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (gl >= o) inc += t;
+    }
+    return inc - v;
+}
+
+// A lane's symbols, 8 at a time.  When the whole 32*S-symbol round lies in
+// the field, the warp first copies it into its shared-memory slot with one
+// burst of coalesced 16-byte loads (16 per lane, all independent), stored
+// swizzled so that lanes reading "their" 16 bytes hit different banks; a
+// partial last round is read from global memory directly.
+struct Lane {
+    const uint16_t *g;  // global codes of this lane (s0)
+    const uint4 *sm;    // this warp's shared slot, or nullptr
+    uint32_t lane, nv;  // nv = S / 8 vectors per lane
+    uint32_t cnt;       // symbols of this lane (0..S)
+    __device__ __forceinline__ uint4 vec(uint32_t j) const
+    {
+        return sm[lane * nv + ((j + lane) & (nv - 1))];
+    }
+};
+
+__device__ __forceinline__ void stage_round(const uint16_t *codes, uint64_t r0, uint32_t S, uint4 *slot)
+{
+    const uint32_t lane = threadIdx.x & 31, nv = S / 8;
+    const uint4 *src = reinterpret_cast<const uint4 *>(codes + r0);
+    for (uint32_t k = 0; k < nv; k++) {
+        const uint32_t gidx = k * 32 + lane, L = gidx / nv, j = gidx % nv;
+        const uint32_t dst = (uint32_t)__cvta_generic_to_shared(slot + L * nv + ((j + L) & (nv - 1)));
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst), "l"(src + gidx) : "memory");
+    }
+    asm volatile("cp.async.commit_group;\n\tcp.async.wait_group 0;" ::: "memory");
+    __syncwarp();
+}
+
+template <typename F>
+__device__ __forceinline__ void for_symbols(const Lane &ln, F f)
+{
+    if (ln.sm) {
+        for (uint32_t j = 0; j < ln.nv; j++) {
+            const uint4 w = ln.vec(j);
+            const uint32_t v[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+            for (int k = 0; k < 8; k++) f(8 * j + k, (v[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu);
         }
     } else {
-#pragma unroll
-        for (int j = 0; j < kSPT / 2; j++) {
-            const uint32_t a = s0 + 2 * j < n ? codes[s0 + 2 * j] : 0u;
-            const uint32_t b = s0 + 2 * j + 1 < n ? codes[s0 + 2 * j + 1] : 0u;
-            cr[j] = a | (b << 16);
-        }
+        for (uint32_t j = 0; j < ln.cnt; j++) f(j, (uint32_t)ln.g[j]);
     }
 }
 
-__device__ __forceinline__ uint32_t sym_of(const uint32_t *cr, int j) { return (cr[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu; }
+struct LaneStats {
+    uint32_t bits, out, exc;
+};
 
-// Decoupled look-back (warp 0).  Publishes the unit's aggregate, gathers the
-// exclusive prefix of (words, outliers | exceptions << 32) and publishes the
-// inclusive value.
-__device__ void look_back(const EncodeArgs &a, uint32_t u, unsigned long long agg_w,
-                          unsigned long long agg_oe, unsigned long long &ex_w, unsigned long long &ex_oe)
+template <bool CW32>
+__device__ __forceinline__ LaneStats lane_stats(const EncodeArgs &a, const Table<CW32> &tab, const Lane &ln,
+                                                uint64_t s0, bool any_exc)
 {
-    const int lane = threadIdx.x & 31;
-    const uint32_t tag = a.epoch << 2;
-    if (u == 0) {
-        ex_w = 0;
-        ex_oe = 0;
-        if (lane == 0) {
-            __stcg(&a.lb_inc[0], make_ulonglong2(agg_w, agg_oe));
-            __threadfence();
-            atomicExch(&a.lb_flag[0], tag | 2u);
+    LaneStats st{0, 0, 0};
+    for_symbols(ln, [&](uint32_t j, uint32_t c) {
+        st.bits += tab.len_of(c);
+        if (c == 0) {
+            st.out++;
+            if (any_exc) st.exc += a.dscr[s0 + j].y != 0;
         }
-        return;
-    }
-    if (lane == 0) {
-        __stcg(&a.lb_agg[u], make_ulonglong2(agg_w, agg_oe));
-        __threadfence();
-        atomicExch(&a.lb_flag[u], tag | 1u);
-    }
-    unsigned long long sw = 0, soe = 0;
-    int64_t j = (int64_t)u - 1;
-    for (;;) {
-        const int64_t jj = j - lane;
-        unsigned long long vw = 0, voe = 0;
-        bool inc = true;
-        if (jj >= 0) {
-            const uint32_t f = spin_until_nonzero_epoch(&a.lb_flag[jj], a.epoch, kSpinLimit);
-            if (f == 0) {
-                atomicOr(&a.ctl->error, DERR_TIMEOUT);
-            } else {
-                __threadfence();
-                inc = (f & 3u) == 2u;
-                const ulonglong2 v = inc ? __ldcg(&a.lb_inc[jj]) : __ldcg(&a.lb_agg[jj]);
-                vw = v.x;
-                voe = v.y;
-            }
-        }
-        const uint32_t m = __ballot_sync(0xffffffffu, inc);
-        const int first = m ? __ffs(m) - 1 : 32;
-        if (lane > first) {
-            vw = 0;
-            voe = 0;
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-            vw += __shfl_xor_sync(0xffffffffu, vw, o);
-            voe += __shfl_xor_sync(0xffffffffu, voe, o);
-        }
-        sw += vw;
-        soe += voe;
-        if (m) break;
-        j -= 32;
-    }
-    ex_w = sw;
-    ex_oe = soe;
-    if (lane == 0) {
-        __stcg(&a.lb_inc[u], make_ulonglong2(sw + agg_w, soe + agg_oe));
-        __threadfence();
-        atomicExch(&a.lb_flag[u], tag | 2u);
-    }
+    });
+    return st;
 }
 
 __device__ __forceinline__ void put_u32(uint8_t *p, uint32_t v) { *reinterpret_cast<uint32_t *>(p) = v; }
 
-// archive header and the zero bytes between sections (last unit's CTA)
+// archive header and the zero bytes between sections (last unit's warp)
 __device__ void write_header(const EncodeArgs &a, const Layout &L, uint64_t nchunk, uint64_t m, uint64_t e,
                              uint64_t w, uint32_t maxlen)
 {
@@ -222,288 +186,413 @@ __device__ void write_header(const EncodeArgs &a, const Layout &L, uint64_t nchu
     for (uint64_t b = L.exc + 8 * e; b < L.stream; b++) a.archive[b] = 0;
 }
 
-template <bool MULTI, bool CW32>
-__device__ __forceinline__ void encode_body(const EncodeArgs &a, uint64_t nunits, uint32_t use_smem_table,
-                                            Smem &s, unsigned long long *s_tab)
-{
-    const uint32_t t = threadIdx.x;
-    const uint32_t nbins = a.nbins;
-    Table<CW32> tab;
-    if (use_smem_table) {
-        if (CW32) {
-            uint32_t *st = reinterpret_cast<uint32_t *>(s_tab);
-            for (uint32_t i = t; i < nbins; i += kEncThreads) st[i] = a.cw32[i];
-        } else {
-            for (uint32_t i = t; i < nbins; i += kEncThreads) s_tab[i] = a.cw64[i];
-        }
-        tab.tab = s_tab;
-    } else {
-        tab.tab = CW32 ? (const void *)a.cw32 : (const void *)a.cw64;
+struct UnitGeom {
+    uint32_t S;       // symbols per lane
+    bool multi;       // a unit is one chunk of several 4096-symbol rounds
+    uint32_t G;       // lanes per chunk inside a round
+    uint64_t U;       // symbols per unit
+    __device__ __forceinline__ explicit UnitGeom(uint32_t C)
+    {
+        S = C < kLaneMax ? C : kLaneMax;
+        multi = C > kRound;
+        G = multi ? 32u : C / S;
+        U = multi ? C : 32ull * S;
     }
+};
+
+// Phase 1: per-unit totals, per-lane bit counts and the archive's chunk bit
+// counts.  Codes are read with coalesced 16-byte loads (lane l holds symbols
+// 256k + 8l .. +7 of step k); the sums of each S-symbol segment (one "lane"
+// of the packing phase) are formed by reductions over the S/8 lanes that
+// hold it, so no staging is needed here.
+template <bool CW32>
+__device__ void count_units(const EncodeArgs &a, uint64_t nunits, const Table<CW32> &tab)
+{
+    const uint32_t lane = threadIdx.x & 31;
     const uint64_t n = a.n;
     const uint32_t C = a.chunk;
+    const UnitGeom ug(C);
+    const uint32_t S = ug.S, per = S / 8;  // lanes holding one segment in a step
+    const uint32_t segs = 32 / per;        // segments per 256-symbol step
+    const uint64_t nchunk = (n + C - 1) / C;
+    const Layout L0 = make_layout(a.radius, nchunk, a.ctl->n_out, a.ctl->n_exc, 0);
+    const bool any_exc = a.ctl->n_exc != 0;
+    const bool first_of_chunk = (lane & (ug.G - 1)) == 0;
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t u = gw; u < nunits; u += nw) {
+        const uint64_t ubase = u * ug.U;
+        const uint64_t ulen = n - ubase < ug.U ? n - ubase : ug.U;
+        const uint32_t rounds = ug.multi ? (uint32_t)((ulen + kRound - 1) / kRound) : 1u;
+        uint32_t unit_words = 0, unit_out = 0, unit_exc = 0;
+        unsigned long long chunk_bits = 0;
+        for (uint32_t r = 0; r < rounds; r++) {
+            const uint64_t r0 = ubase + (uint64_t)r * 32 * S;
+            // segment sums: after step k, lane k*segs + (lane / per) owns one
+            uint32_t sb = 0, so = 0, se = 0;
+            const uint32_t steps = S / 8;  // 256-symbol steps per round (= 32*S/256)
+            for (uint32_t k = 0; k < steps; k++) {
+                const uint64_t p = r0 + 256ull * k + 8ull * lane;
+                uint32_t b = 0, o = 0, e = 0;
+                if (p + 8 <= n) {
+                    const uint4 w = *reinterpret_cast<const uint4 *>(a.codes + p);
+                    const uint32_t v[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+                    for (int q = 0; q < 8; q++) {
+                        const uint32_t c = (v[q >> 1] >> ((q & 1) * 16)) & 0xFFFFu;
+                        b += tab.len_of(c);
+                        o += c == 0;
+                        if (any_exc && c == 0) e += a.dscr[p + q].y != 0;
+                    }
+                } else {
+                    for (uint32_t q = 0; q < 8 && p + q < n; q++) {
+                        const uint32_t c = a.codes[p + q];
+                        b += tab.len_of(c);
+                        o += c == 0;
+                        if (any_exc && c == 0) e += a.dscr[p + q].y != 0;
+                    }
+                }
+                for (uint32_t x = 1; x < per; x <<= 1) {
+                    b += __shfl_xor_sync(0xffffffffu, b, x);
+                    o += __shfl_xor_sync(0xffffffffu, o, x);
+                    e += __shfl_xor_sync(0xffffffffu, e, x);
+                }
+                // segment k*segs + g is held (reduced) by lanes g*per .. g*per+per-1
+                const uint32_t owner = lane - k * segs;  // valid when lane is one of this step's segments
+                const uint32_t srcl = (owner < segs ? owner : 0u) * per;
+                const uint32_t tb = __shfl_sync(0xffffffffu, b, srcl);
+                const uint32_t to = __shfl_sync(0xffffffffu, o, srcl);
+                const uint32_t te = __shfl_sync(0xffffffffu, e, srcl);
+                if (owner < segs) {
+                    sb = tb;
+                    so = to;
+                    se = te;
+                }
+            }
+            const uint64_t s0 = r0 + (uint64_t)lane * S;
+            const uint32_t cnt = s0 < n ? (uint32_t)(n - s0 < S ? n - s0 : S) : 0u;
+            if (cnt) a.lane_bits[r0 / S + lane] = sb;
+            if (ug.multi) {
+                chunk_bits += warp_sum(sb);
+            } else {
+                const uint32_t cb = group_sum(sb, ug.G);
+                uint32_t cw = 0;
+                if (first_of_chunk && cnt) {
+                    cw = (cb + 31) / 32;
+                    put_u32(a.archive + L0.bits + 4 * (s0 / C), cb);
+                }
+                unit_words += warp_sum(cw);
+            }
+            unit_out += warp_sum(so);
+            unit_exc += warp_sum(se);
+        }
+        if (ug.multi) {
+            unit_words = (uint32_t)((chunk_bits + 31) / 32);
+            if (lane == 0) put_u32(a.archive + L0.bits + 4 * u, (uint32_t)chunk_bits);
+        }
+        if (lane == 0)
+            a.unit_tot[u] = make_ulonglong2(unit_words, (unsigned long long)unit_out | ((unsigned long long)unit_exc << 32));
+    }
+}
+
+// appends one codeword to the bit accumulator; returns true when a full word
+// (acc >> nacc, low 32 bits) is ready.  Codes of at most 24 bits (CW32) need
+// no masking: bits above the 32 still pending just shift out of the 64-bit
+// accumulator.
+template <bool CW32>
+__device__ __forceinline__ void append(unsigned long long &acc, uint32_t &nacc, unsigned long long code, uint32_t len,
+                                       uint32_t *w, uint32_t &nw)
+{
+    nw = 0;
+    if (!CW32 && len > 32) {
+        const uint32_t hl = len - 32;
+        acc = (acc << hl) | (code >> 32);
+        nacc += hl;
+        if (nacc >= 32) {
+            nacc -= 32;
+            w[nw++] = (uint32_t)(acc >> nacc);
+        }
+        code &= 0xFFFFFFFFull;
+        len = 32;
+    }
+    acc = (acc << len) | code;
+    nacc += len;
+    if (nacc >= 32) {
+        nacc -= 32;
+        w[nw++] = (uint32_t)(acc >> nacc);
+    }
+}
+
+// Phase 3: pack every unit at its offsets; the last unit writes the header.
+template <bool CW32>
+__device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW32> &tab, uint4 *slot)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t n = a.n;
+    const uint32_t C = a.chunk;
+    const UnitGeom ug(C);
+    const uint32_t S = ug.S, G = ug.G, nv = S / 8;
+    const bool multi = ug.multi;
     const uint64_t nchunk = (n + C - 1) / C;
     const uint64_t M = a.ctl->n_out, E = a.ctl->n_exc;
+    const bool any_exc = E != 0;
     const Layout L0 = make_layout(a.radius, nchunk, M, E, 0);
-    const EbScalars sc = load_scalars(a.ctl);
-    const uint64_t U = MULTI ? C : kTile;
-
-    for (;;) {
-        if (t == 0) s.unit = atomicAdd(&a.ctl->ticket, 1u);
-        __syncthreads();
-        const uint32_t u = s.unit;
-        __syncthreads();
-        if (u >= nunits) break;
-        const uint64_t ubase = (uint64_t)u * U;
-        const uint64_t ulen = n - ubase < U ? n - ubase : U;
-        const uint32_t ntile = MULTI ? (uint32_t)((ulen + kTile - 1) / kTile) : 1;
-
-        // ---- pass 1
-        uint32_t cr[kSPT / 2];
-        uint32_t excmask = 0;
-        uint32_t my_bits = 0, my_out = 0, my_exc = 0;
-        unsigned long long unit_words = 0, unit_out = 0, unit_exc = 0;
-        unsigned long long chunk_bits = 0;
-        uint32_t seg_bit = 0, seg_word = 0;  // single-tile: bit offset in chunk, chunk word offset in unit
-        for (uint32_t tj = 0; tj < ntile; tj++) {
-            const uint64_t s0 = ubase + (uint64_t)tj * kTile + (uint64_t)t * kSPT;
-            load_codes(a.codes, n, s0, cr);
-            uint32_t b = 0, o = 0, ex = 0;
-            excmask = 0;
+    uint32_t *stream = reinterpret_cast<uint32_t *>(a.archive + L0.stream);
+    const uint64_t stream_cap = a.capacity > L0.stream ? (a.capacity - L0.stream) / 4 : 0;
+    const bool first_of_chunk = (lane & (G - 1)) == 0;
+    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    bool cap_err = false;
+    for (uint64_t u = gw; u < nunits; u += nwarps) {
+        const uint64_t ubase = u * ug.U;
+        const uint64_t ulen = n - ubase < ug.U ? n - ubase : ug.U;
+        const uint32_t rounds = multi ? (uint32_t)((ulen + kRound - 1) / kRound) : 1u;
+        const ulonglong2 off = a.unit_off[u];
+        const unsigned long long W0 = off.x, O0 = off.y & 0xFFFFFFFFull, E0 = off.y >> 32;
+        if (u == nunits - 1 && lane == 0) {
+            const ulonglong2 tot = a.unit_tot[u];
+            const unsigned long long W = W0 + tot.x;
+            const Layout L = make_layout(a.radius, nchunk, M, E, W);
+            if (O0 + (tot.y & 0xFFFFFFFFull) != M || E0 + (tot.y >> 32) != E) atomicOr(&a.ctl->error, DERR_INTERNAL);
+            a.ctl->words = W;
+            a.ctl->total = L.total;
+            if (L.total > a.capacity) atomicOr(&a.ctl->error, DERR_CAPACITY);
+            if (L.stream <= a.capacity) write_header(a, L, nchunk, M, E, W, a.ctl->maxlen);
+        }
+        unsigned long long round_bits = 0;  // multi: bits of earlier rounds of the chunk
+        uint32_t o_run = 0, e_run = 0;
+        uint32_t carry = 0;                 // multi: partial last word of the previous round
+        for (uint32_t r = 0; r < rounds; r++) {
+            const uint64_t r0 = ubase + (uint64_t)r * 32 * S, s0 = r0 + (uint64_t)lane * S;
+            const uint32_t cnt = s0 < n ? (uint32_t)(n - s0 < S ? n - s0 : S) : 0u;
+            const bool full = r0 + 32ull * S <= n;
+            const uint32_t bits = cnt ? a.lane_bits[r0 / S + lane] : 0u;
+            __syncwarp();
+            if (full) stage_round(a.codes, r0, S, slot);
+            const Lane ln{a.codes + s0, full ? slot : nullptr, lane, nv, cnt};
+            unsigned long long gbit;  // global bit position of this lane's first bit
+            uint32_t rtot = 0;
+            if (multi) {
+                const uint32_t inc = warp_incl_scan(bits);
+                rtot = __shfl_sync(0xffffffffu, inc, 31);
+                gbit = W0 * 32 + round_bits + (inc - bits);
+            } else {
+                const uint32_t cb = group_sum(bits, G);
+                const uint32_t cw = first_of_chunk && cnt ? (cb + 31) / 32 : 0u;
+                const uint32_t bin = group_excl_scan(bits, G);
+                const uint32_t winc = warp_incl_scan(cw);
+                const uint32_t woff = __shfl_sync(0xffffffffu, winc - cw, lane & ~(G - 1));
+                gbit = (W0 + woff) * 32 + bin;
+            }
+            // pack: words wholly owned are stored at once; the first word is
+            // the "head" when this lane starts inside it (owned by the
+            // previous lane), the last partial one is the "tail"
+            const bool starts_mid = (gbit & 31u) != 0 && cnt > 0;
+            unsigned long long acc = 0;
+            uint32_t nacc = (uint32_t)(gbit & 31u);
+            uint64_t widx = gbit >> 5;
+            const uint64_t hidx = starts_mid ? widx : ~0ull;  // the head's word index
+            if ((gbit + bits + 31) / 32 > stream_cap) cap_err = true;
+            uint32_t *out = cap_err ? nullptr : stream;
+            uint32_t head = 0;
+            unsigned long long zlo = 0, zhi = 0;  // code-0 positions of this lane
+            auto put = [&](uint32_t w) {
+                if (widx == hidx) head = w;
+                else if (out) out[widx] = w;
+                widx++;
+            };
+            if (ln.sm) {
+                for (uint32_t j = 0; j < ln.nv; j++) {
+                    const uint4 q4 = ln.vec(j);
+                    const uint32_t v[4] = {q4.x, q4.y, q4.z, q4.w};
+                    // zero symbols of these 8, as bits 8j.. of the lane's mask
+                    const uint32_t z = ((__vcmpeq2(v[0], 0) & 0x00010001u) * 1u) |
+                                       ((__vcmpeq2(v[1], 0) & 0x00010001u) << 2) |
+                                       ((__vcmpeq2(v[2], 0) & 0x00010001u) << 4) |
+                                       ((__vcmpeq2(v[3], 0) & 0x00010001u) << 6);
+                    const uint32_t z8 = (z | (z >> 15)) & 0xFFu;
+                    if (z8) {
+                        if (j < 8) zlo |= (unsigned long long)z8 << (8 * j);
+                        else zhi |= (unsigned long long)z8 << (8 * (j - 8));
+                    }
 #pragma unroll
-            for (int j = 0; j < kSPT; j++) {
-                const uint64_t i = s0 + j;
-                if (i < n) {
-                    const uint32_t c = sym_of(cr, j);
-                    b += tab.get(c).len;
+                    for (int k = 0; k < 8; k++) {
+                        uint32_t len;
+                        unsigned long long code;
+                        tab.get((v[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu, len, code);
+                        uint32_t w[2], nw;
+                        append<CW32>(acc, nacc, code, len, w, nw);
+                        if (nw) {
+                            put(w[0]);
+                            if (!CW32 && nw > 1) put(w[1]);
+                        }
+                    }
+                }
+            } else {
+                for (uint32_t j = 0; j < cnt; j++) {
+                    const uint32_t c = ln.g[j];
+                    uint32_t len;
+                    unsigned long long code;
+                    tab.get(c, len, code);
+                    uint32_t w[2], nw;
+                    append<CW32>(acc, nacc, code, len, w, nw);
+                    for (uint32_t q = 0; q < nw; q++) put(w[q]);
                     if (c == 0) {
-                        o++;
-                        bool e;
-                        prequant(a.x[i], sc, e);
-                        if (e) {
-                            ex++;
-                            excmask |= 1u << j;
-                        }
+                        if (j < 64) zlo |= 1ull << j;
+                        else zhi |= 1ull << (j - 64);
                     }
                 }
             }
-            my_bits = b;
-            my_out = o;
-            my_exc = ex;
-            uint32_t tot;
-            const uint32_t eb_ = block_excl_scan(b, s.scan, &tot);
-            if (MULTI) {
-                chunk_bits += tot;
-                uint32_t to, te;
-                block_excl_scan(o, s.scan, &to);
-                block_excl_scan(ex, s.scan, &te);
-                unit_out += to;
-                unit_exc += te;
-            } else {
-                // chunks of C/32 threads inside the 4096-symbol unit
-                const uint32_t tpc = C / kSPT;
-                const uint32_t cs = t - t % tpc;
-                s.e[t] = eb_;
-                if (t == 0) s.e[kEncThreads] = tot;
-                __syncthreads();
-                seg_bit = eb_ - s.e[cs];
-                const bool first = t == cs;
-                const uint64_t cstart = ubase + (uint64_t)cs * kSPT;
-                uint32_t wc = 0;
-                if (first && cstart < n) {
-                    const uint32_t cb = s.e[min(cs + tpc, (uint32_t)kEncThreads)] - s.e[cs];
-                    wc = (cb + 31) / 32;
-                    const uint64_t c = cstart / C;
-                    put_u32(a.archive + L0.bits + 4 * c, cb);
-                }
-                uint32_t tw;
-                const uint32_t wo = block_excl_scan(wc, s.scan, &tw);
-                if (first) s.wo[cs] = wo;
-                unit_words = tw;
-                uint32_t to, te;
-                block_excl_scan(o, s.scan, &to);
-                block_excl_scan(ex, s.scan, &te);
-                unit_out = to;
-                unit_exc = te;
-                __syncthreads();
-                seg_word = s.wo[cs];
-            }
-        }
-        if (MULTI) {
-            unit_words = (chunk_bits + 31) / 32;
-            if (t == 0) put_u32(a.archive + L0.bits + 4 * (uint64_t)u, (uint32_t)chunk_bits);
-        }
-
-        // ---- look-back
-        if (t < 32) {
-            unsigned long long xw, xoe;
-            look_back(a, u, unit_words, unit_out | (unit_exc << 32), xw, xoe);
-            if (t == 0) {
-                s.excl_w = xw;
-                s.excl_oe = xoe;
-                if (u == nunits - 1) {
-                    const unsigned long long W = xw + unit_words;
-                    const unsigned long long Mt = (xoe & 0xFFFFFFFFull) + unit_out;
-                    const unsigned long long Et = (xoe >> 32) + unit_exc;
-                    if (Mt != M || Et != E) atomicOr(&a.ctl->error, DERR_INTERNAL);
-                    const Layout L = make_layout(a.radius, nchunk, M, E, W);
-                    a.ctl->words = W;
-                    a.ctl->total = L.total;
-                    if (L.stream > a.capacity) atomicOr(&a.ctl->error, DERR_CAPACITY);
-                    else write_header(a, L, nchunk, M, E, W, a.ctl->maxlen);
-                }
-            }
-        }
-        __syncthreads();
-        const unsigned long long W0 = s.excl_w;
-        const unsigned long long O0 = s.excl_oe & 0xFFFFFFFFull, E0 = s.excl_oe >> 32;
-
-        // ---- pass 2
-        unsigned long long run_bits = 0, run_out = 0, run_exc = 0;
-        if (MULTI && t == 0) s.carry = 0;
-        for (uint32_t tj = 0; tj < ntile; tj++) {
-            const uint64_t s0 = ubase + (uint64_t)tj * kTile + (uint64_t)t * kSPT;
-            uint32_t pbit, o_off, e_off, nw, wbase_rel;
-            bool keep_last = false;
-            if (MULTI) {
-                load_codes(a.codes, n, s0, cr);
-                uint32_t b = 0, o = 0, ex = 0;
-                excmask = 0;
-#pragma unroll
-                for (int j = 0; j < kSPT; j++) {
-                    const uint64_t i = s0 + j;
-                    if (i < n) {
-                        const uint32_t c = sym_of(cr, j);
-                        b += tab.get(c).len;
-                        if (c == 0) {
-                            o++;
-                            bool e;
-                            prequant(a.x[i], sc, e);
-                            if (e) {
-                                ex++;
-                                excmask |= 1u << j;
-                            }
-                        }
-                    }
-                }
-                uint32_t tb, to, te;
-                const uint32_t be = block_excl_scan(b, s.scan, &tb);
-                o_off = block_excl_scan(o, s.scan, &to);
-                e_off = block_excl_scan(ex, s.scan, &te);
-                o_off += (uint32_t)run_out;
-                e_off += (uint32_t)run_exc;
-                const unsigned long long tstart = run_bits, tend = run_bits + tb;
-                wbase_rel = (uint32_t)(tstart / 32);
-                pbit = (uint32_t)(tstart - 32ull * wbase_rel) + be;
-                nw = (uint32_t)((tend + 31) / 32 - wbase_rel);
-                keep_last = (tj + 1 < ntile) && (tend % 32 != 0);
-                run_bits = tend;
-                run_out += to;
-                run_exc += te;
-                for (uint32_t i = t; i < nw; i += kEncThreads) s.words[i] = 0;
-                __syncthreads();
-                if (t == 0 && (tstart % 32)) s.words[0] = s.carry;
-                __syncthreads();
-            } else {
-                uint32_t to, te;
-                o_off = block_excl_scan(my_out, s.scan, &to);
-                e_off = block_excl_scan(my_exc, s.scan, &te);
-                wbase_rel = 0;
-                pbit = seg_word * 32 + seg_bit;
-                nw = (uint32_t)unit_words;
-                for (uint32_t i = t; i < nw; i += kEncThreads) s.words[i] = 0;
-                __syncthreads();
-            }
-            // pack codewords
-            {
-                unsigned long long acc = 0;
-                uint32_t nacc = pbit % 32, widx = pbit / 32;
-#pragma unroll
-                for (int j = 0; j < kSPT; j++) {
-                    if (s0 + j < n) {
-                        const Entry en = tab.get(sym_of(cr, j));
-                        put_bits(acc, nacc, widx, s.words, en.code, en.len);
-                    }
-                }
-                flush_bits(acc, nacc, widx, s.words);
-            }
-            // outliers and exceptions in index order
-            {
-                uint32_t ko = 0, ke = 0;
-                const uint64_t oe_base = L0.outl + 8 * (O0 + o_off);
-                for (int j = 0; j < kSPT; j++) {
-                    const uint64_t i = s0 + j;
-                    if (i < n && sym_of(cr, j) == 0) {
-                        const uint64_t off = oe_base + 8ull * ko++;
-                        if (off + 8 <= a.capacity) {
-                            put_u32(a.archive + off, (uint32_t)i);
-                            put_u32(a.archive + off + 4, (uint32_t)a.dscr[i]);
-                        } else {
-                            atomicOr(&a.ctl->error, DERR_CAPACITY);
-                        }
-                        if (excmask & (1u << j)) {
-                            const uint64_t eo = L0.outl + 8 * M + 8 * (E0 + e_off + ke++);
-                            if (eo + 8 <= a.capacity) {
-                                put_u32(a.archive + eo, (uint32_t)i);
-                                put_u32(a.archive + eo + 4, __float_as_uint(a.x[i]));
-                            } else {
-                                atomicOr(&a.ctl->error, DERR_CAPACITY);
-                            }
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-            // write the staged words: global word index W0 + wbase_rel + i
-            {
-                const uint32_t nflush = keep_last ? nw - 1 : nw;
-                const unsigned long long gw0 = W0 + wbase_rel;
-                const Layout L = make_layout(a.radius, nchunk, M, E, 0);
-                if (L.stream + 4 * (gw0 + nflush) > a.capacity) {
-                    if (t == 0 && nflush) atomicOr(&a.ctl->error, DERR_CAPACITY);
+            uint32_t tail = 0;
+            bool has_tail = false;
+            if (nacc > 0 && cnt > 0) {
+                const uint32_t w = (uint32_t)(acc << (32 - nacc));
+                if (widx == hidx) {  // the whole lane fits inside its first word
+                    head = w;
                 } else {
-                    uint32_t *dst = reinterpret_cast<uint32_t *>(a.archive + L.stream) + gw0;
-                    const uint32_t head = min((uint32_t)((4 - (gw0 & 3)) & 3), nflush);
-                    if (t < head) dst[t] = s.words[t];
-                    const uint32_t nvec = (nflush - head) / 4;
-                    uint4 *dv = reinterpret_cast<uint4 *>(dst + head);
-                    for (uint32_t v = t; v < nvec; v += kEncThreads) {
-                        const uint32_t b = head + 4 * v;
-                        dv[v] = make_uint4(s.words[b], s.words[b + 1], s.words[b + 2], s.words[b + 3]);
-                    }
-                    for (uint32_t i = head + 4 * nvec + t; i < nflush; i += kEncThreads) dst[i] = s.words[i];
+                    tail = w;
+                    has_tail = true;
                 }
-                if (MULTI && t == 0) s.carry = keep_last ? s.words[nw - 1] : 0u;
             }
-            __syncthreads();
+            const uint64_t tail_idx = widx;
+            // hand heads to the previous lane of the same chunk
+            const uint32_t next_head = __shfl_down_sync(0xffffffffu, head, 1);
+            const bool next_starts_mid = __shfl_down_sync(0xffffffffu, starts_mid ? 1u : 0u, 1) != 0;
+            const bool next_same_chunk = lane < 31 && ((lane + 1) & (G - 1)) != 0;
+            const uint32_t prev_carry = __shfl_sync(0xffffffffu, carry, 31);
+            if (has_tail) {
+                uint32_t v = tail;
+                if (next_same_chunk && next_starts_mid) v |= next_head;
+                if (multi && lane == 31 && r + 1 < rounds) {
+                    carry = v;  // the next round's lane 0 finishes this word
+                } else if (out) {
+                    out[tail_idx] = v;
+                }
+            }
+            if (multi && lane == 0 && r > 0 && starts_mid && out) out[hidx] = head | prev_carry;
+            if (multi && !(lane == 31 && has_tail)) carry = 0;
+            // outliers and exceptions in index order
+            const uint32_t nz = __popcll(zlo) + __popcll(zhi);
+            uint32_t ne = 0;
+            if (any_exc) {
+                for (unsigned long long m = zlo; m; m &= m - 1) ne += a.dscr[s0 + __ffsll(m) - 1].y != 0;
+                for (unsigned long long m = zhi; m; m &= m - 1) ne += a.dscr[s0 + 63 + __ffsll(m)].y != 0;
+            }
+            const uint32_t oinc = warp_incl_scan(nz), einc = warp_incl_scan(ne);
+            uint64_t oi = O0 + o_run + (oinc - nz), ei = E0 + e_run + (einc - ne);
+            auto emit_outlier = [&](uint64_t idx) {
+                const int2 dv = a.dscr[idx];
+                const uint64_t o8 = L0.outl + 8 * oi++;
+                if (o8 + 8 <= a.capacity) {
+                    put_u32(a.archive + o8, (uint32_t)idx);
+                    put_u32(a.archive + o8 + 4, (uint32_t)dv.x);
+                } else {
+                    cap_err = true;
+                }
+                if (dv.y) {
+                    const uint64_t e8 = L0.exc + 8 * ei++;
+                    if (e8 + 8 <= a.capacity) {
+                        put_u32(a.archive + e8, (uint32_t)idx);
+                        put_u32(a.archive + e8 + 4, __float_as_uint(a.x[idx]));
+                    } else {
+                        cap_err = true;
+                    }
+                }
+            };
+            for (unsigned long long m = zlo; m; m &= m - 1) emit_outlier(s0 + __ffsll(m) - 1);
+            for (unsigned long long m = zhi; m; m &= m - 1) emit_outlier(s0 + 63 + __ffsll(m));
+            o_run += __shfl_sync(0xffffffffu, oinc, 31);
+            e_run += __shfl_sync(0xffffffffu, einc, 31);
+            round_bits += rtot;
         }
     }
+    if (cap_err) atomicOr(&a.ctl->error, DERR_CAPACITY);
 }
 
 // The codeword width is chosen on the device from the longest code length
 // the codebook kernel found: 32-bit entries when it is at most 24 bits.
-template <bool MULTI>
-__global__ void __launch_bounds__(kEncThreads) k_encode(EncodeArgs a, uint64_t nunits, uint32_t use_smem_table)
+__device__ __forceinline__ const void *load_table(const EncodeArgs &a, uint32_t use_smem, unsigned long long *s_tab,
+                                                  bool w32)
 {
-    __shared__ Smem s;
-    extern __shared__ unsigned long long s_tab[];
+    if (!use_smem) return w32 ? (const void *)a.cw32 : (const void *)a.cw64;
+    if (w32) {
+        uint32_t *st = reinterpret_cast<uint32_t *>(s_tab);
+        for (uint32_t i = threadIdx.x; i < a.nbins; i += blockDim.x) st[i] = a.cw32[i];
+    } else {
+        for (uint32_t i = threadIdx.x; i < a.nbins; i += blockDim.x) s_tab[i] = a.cw64[i];
+    }
+    __syncthreads();
+    return s_tab;
+}
+
+__global__ void __launch_bounds__(kEncThreads, 4) k_encode_count(EncodeArgs a, uint64_t nunits, uint32_t use_smem)
+{
+    extern __shared__ unsigned long long s_tabc[];
     if (a.ctl->error & (DERR_EB | DERR_INTERNAL)) return;
-    if (a.ctl->maxlen <= 24) encode_body<MULTI, true>(a, nunits, use_smem_table, s, s_tab);
-    else encode_body<MULTI, false>(a, nunits, use_smem_table, s, s_tab);
+    const bool w32 = a.ctl->maxlen <= 24;
+    const void *tab = load_table(a, use_smem, s_tabc, w32);
+    if (w32) count_units<true>(a, nunits, Table<true>{tab});
+    else count_units<false>(a, nunits, Table<false>{tab});
+}
+
+__global__ void __launch_bounds__(kEncThreads, 3) k_encode_pack(EncodeArgs a, uint64_t nunits, uint32_t use_smem)
+{
+    extern __shared__ uint4 s_dyn[];
+    uint4 *slot = s_dyn + (threadIdx.x >> 5) * (kRound / 8);  // 8 KB per warp
+    unsigned long long *s_tab = reinterpret_cast<unsigned long long *>(s_dyn + kWarps * (kRound / 8));
+    if (a.ctl->error & (DERR_EB | DERR_INTERNAL)) return;
+    const bool w32 = a.ctl->maxlen <= 24;
+    const void *tab = load_table(a, use_smem, s_tab, w32);
+    if (w32) pack_units<true>(a, nunits, Table<true>{tab}, slot);
+    else pack_units<false>(a, nunits, Table<false>{tab}, slot);
+}
+
+// exclusive scan of the unit totals (words, outliers | exceptions << 32)
+struct UnitOp {
+    using T = ulonglong2;
+    const ulonglong2 *tot;
+    ulonglong2 *off;
+    __device__ T load(uint64_t i) const { return tot[i]; }
+    __device__ void store(uint64_t i, T v) const { off[i] = v; }
+    __device__ void total(T) const {}
+};
+
+// opt in to the dynamic shared memory the packing kernel needs, once per device
+void set_encode_smem()
+{
+    static unsigned long long done = 0;  // one bit per device id < 64
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0;
+    if (bit && (done & bit)) return;
+    const size_t most = (size_t)kWarps * kRound * 2 + 4096 * 8;
+    cudaFuncSetAttribute(k_encode_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+    done |= bit;
 }
 
 }  // namespace
 
-void launch_encode(const EncodeArgs &a, cudaStream_t st)
+uint64_t encode_units(uint64_t n, uint32_t chunk)
 {
-    const bool multi = a.chunk > (uint32_t)kTile;
-    const uint64_t U = multi ? a.chunk : kTile;
-    const uint64_t nunits = (a.n + U - 1) / U;
+    const uint32_t S = chunk < kLaneMax ? chunk : kLaneMax;
+    const uint64_t U = chunk > kRound ? chunk : 32ull * S;
+    return (n + U - 1) / U;
+}
+
+int launch_encode(const EncodeArgs &a, cudaStream_t st)
+{
+    const uint64_t nunits = encode_units(a.n, a.chunk);
     const uint32_t use_smem = a.nbins <= 4096 ? 1u : 0u;
-    const size_t tab_bytes = use_smem ? (size_t)a.nbins * 8 : 0;
-    const int grid = (int)std::min<uint64_t>(nunits, (uint64_t)a.num_sms * 12);
-    if (multi) k_encode<true><<<grid, kEncThreads, tab_bytes, st>>>(a, nunits, use_smem);
-    else k_encode<false><<<grid, kEncThreads, tab_bytes, st>>>(a, nunits, use_smem);
+    const size_t tab = use_smem ? (size_t)a.nbins * 8 : 0;
+    const size_t pack_smem = (size_t)kWarps * kRound * 2 + tab;
+    set_encode_smem();
+    const uint64_t want = (nunits + kWarps - 1) / kWarps;
+    const int grid_c = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)a.num_sms * 4));
+    const int grid_p = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)a.num_sms * 3));
+    k_encode_count<<<grid_c, kEncThreads, tab, st>>>(a, nunits, use_smem);
+    const int ns = launch_scan(UnitOp{a.unit_tot, a.unit_off}, nunits, a.scan_part, st);
+    k_encode_pack<<<grid_p, kEncThreads, pack_smem, st>>>(a, nunits, use_smem);
+    return 2 + ns;
 }
 
 }  // namespace gbsz

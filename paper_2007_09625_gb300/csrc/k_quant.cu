@@ -210,7 +210,7 @@ __device__ __forceinline__ uint32_t emit_point(HistState &h, const QuantArgs &a,
 {
     const uint32_t code = postquant(delta, exc, (int32_t)h.R);
     if (code == 0) {
-        a.dscr[idx] = (int32_t)delta;
+        a.dscr[idx] = make_int2((int32_t)delta, exc ? 1 : 0);
         h.n_out++;
     }
     h.n_exc += exc;
@@ -219,15 +219,42 @@ __device__ __forceinline__ uint32_t emit_point(HistState &h, const QuantArgs &a,
 }
 
 // ---------------------------------------------------------------------------
-// 1D: 256 threads, tile of 2048 points as two block-strided groups of 4
-// consecutive points per thread (float4 loads, 8-byte code stores).  The left
-// neighbour of a group comes from the previous lane; lane 0 recomputes it.
+// 1D: 256 threads, tile of 4096 points, 16 consecutive points per thread
+// (four 16-byte loads issued together, two 16-byte code stores).  Each lane
+// prequantizes the point before its run itself (one extra point per 16) so
+// no lane waits on another.  Point indices fit in 32 bits (n < 2^32).
 
 constexpr int kQ1Threads = 256;
-constexpr int kQ1Tile = 2048;
+constexpr int kQ1Per = 16;
+constexpr int kQ1Tile = kQ1Threads * kQ1Per;
+
+// code for residual d; in cap iff -R < d < R, tested as one unsigned compare
+__device__ __forceinline__ uint32_t code_of(uint32_t d, bool exc, uint32_t R)
+{
+    return (!exc && d + (R - 1) < 2 * R - 1) ? d + R : 0u;
+}
+
+__device__ __forceinline__ void point_1d(HistState &h, const QuantArgs &a, uint32_t idx, uint32_t d, bool exc,
+                                         uint32_t &code)
+{
+    code = code_of(d, exc, h.R);
+    h.c_mid += code == h.R;
+    h.c_lo += code == h.R - 1;
+    h.c_hi += code == h.R + 1;
+    if (code + 1 < h.R || code > h.R + 1) {  // not one of the three central codes
+        if (code == 0) {
+            a.dscr[idx] = make_int2((int32_t)d, exc ? 1 : 0);
+            h.n_out++;
+            h.n_exc += exc;
+        }
+        const uint32_t b = code - h.lo;
+        if (b < h.nsh) atomicAdd(&h.sh[b], 1u);
+        else atomicAdd(&a.hist[code], 1u);
+    }
+}
 
 template <bool VEC>
-__global__ void __launch_bounds__(kQ1Threads) k_dualquant_1d(QuantArgs a, uint64_t ntiles)
+__global__ void __launch_bounds__(kQ1Threads) k_dualquant_1d(QuantArgs a, uint32_t ntiles)
 {
     extern __shared__ uint32_t sh_hist[];
     HistState h;
@@ -235,52 +262,48 @@ __global__ void __launch_bounds__(kQ1Threads) k_dualquant_1d(QuantArgs a, uint64
     __syncthreads();
     if (a.ctl->error & DERR_EB) return;
     const EbScalars sc = load_scalars(a.ctl);
-    const uint64_t n = a.dims[0];
-    const int lane = threadIdx.x & 31;
-    for (uint64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint64_t base = tile * kQ1Tile;
+    const uint32_t n = (uint32_t)a.dims[0];
+    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        const uint32_t e0 = tile * kQ1Tile + threadIdx.x * kQ1Per;
+        float v[kQ1Per];
+        float vp = 0.0f;
+        const bool full = VEC && (uint64_t)e0 + kQ1Per <= n;
+        if (full) {
+            const float4 *p = reinterpret_cast<const float4 *>(a.x + e0);
 #pragma unroll
-        for (int g = 0; g < 2; g++) {
-            const uint64_t e0 = base + (uint64_t)g * (kQ1Tile / 2) + threadIdx.x * 4u;
-            float v[4];
-            const bool full = e0 + 3 < n;
-            if (VEC && full) {
-                const float4 f = *reinterpret_cast<const float4 *>(a.x + e0);
-                v[0] = f.x; v[1] = f.y; v[2] = f.z; v[3] = f.w;
-            } else {
-#pragma unroll
-                for (int j = 0; j < 4; j++) v[j] = e0 + j < n ? a.x[e0 + j] : 0.0f;
+            for (int j = 0; j < kQ1Per / 4; j++) {
+                const float4 f = p[j];
+                v[4 * j] = f.x;
+                v[4 * j + 1] = f.y;
+                v[4 * j + 2] = f.z;
+                v[4 * j + 3] = f.w;
             }
-            int32_t q[4];
-            bool ex[4];
+        } else {
 #pragma unroll
-            for (int j = 0; j < 4; j++) q[j] = prequant(v[j], sc, ex[j]);
-            int32_t qp = __shfl_up_sync(0xffffffffu, q[3], 1);
-            if (lane == 0) {
-                if (e0 == 0 || e0 > n) {
-                    qp = 0;
-                } else {
-                    bool dummy;
-                    qp = prequant(a.x[e0 - 1], sc, dummy);
-                }
-            }
-            uint32_t code[4];
+            for (int j = 0; j < kQ1Per; j++) v[j] = e0 + j < n ? a.x[e0 + j] : 0.0f;
+        }
+        if (e0 > 0 && e0 <= n) vp = a.x[e0 - 1];
+        bool dummy;
+        uint32_t qprev = (e0 > 0 && e0 <= n) ? (uint32_t)prequant(vp, sc, dummy) : 0u;
+        uint32_t code[kQ1Per];
 #pragma unroll
-            for (int j = 0; j < 4; j++) {
-                const uint32_t d = (uint32_t)q[j] - (uint32_t)(j ? q[j - 1] : qp);
-                code[j] = 0;
-                if (e0 + j < n) code[j] = emit_point(h, a, e0 + j, d, ex[j]);
-            }
-            if (full) {
-                uint2 w;
-                w.x = code[0] | (code[1] << 16);
-                w.y = code[2] | (code[3] << 16);
-                *reinterpret_cast<uint2 *>(a.codes + e0) = w;
-            } else {
+        for (int j = 0; j < kQ1Per; j++) {
+            bool exc;
+            const uint32_t q = (uint32_t)prequant(v[j], sc, exc);
+            code[j] = 0;
+            if (full || e0 + j < n) point_1d(h, a, e0 + j, q - qprev, exc, code[j]);
+            qprev = q;
+        }
+        if (full) {
+            uint4 *o = reinterpret_cast<uint4 *>(a.codes + e0);
+            o[0] = make_uint4(code[0] | (code[1] << 16), code[2] | (code[3] << 16), code[4] | (code[5] << 16),
+                              code[6] | (code[7] << 16));
+            o[1] = make_uint4(code[8] | (code[9] << 16), code[10] | (code[11] << 16), code[12] | (code[13] << 16),
+                              code[14] | (code[15] << 16));
+        } else {
 #pragma unroll
-                for (int j = 0; j < 4; j++)
-                    if (e0 + j < n) a.codes[e0 + j] = (uint16_t)code[j];
-            }
+            for (int j = 0; j < kQ1Per; j++)
+                if (e0 + j < n) a.codes[e0 + j] = (uint16_t)code[j];
         }
     }
     hist_flush(h, a.hist, a.ctl);
@@ -479,7 +502,7 @@ void launch_dualquant(const QuantArgs &a, cudaStream_t st)
     const size_t hist_bytes = sizeof(uint32_t) * std::min<uint32_t>(nbins, kWinBins);
     if (a.ndim == 1) {
         const uint64_t n = a.dims[0];
-        const uint64_t ntiles = (n + kQ1Tile - 1) / kQ1Tile;
+        const uint32_t ntiles = (uint32_t)((n + kQ1Tile - 1) / kQ1Tile);
         const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)a.num_sms * 8);
         if ((reinterpret_cast<uintptr_t>(a.x) & 15) == 0)
             k_dualquant_1d<true><<<grid, kQ1Threads, hist_bytes, st>>>(a, ntiles);

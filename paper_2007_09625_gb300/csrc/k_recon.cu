@@ -18,6 +18,7 @@
 //      precedes this one along every dimension of A, at this point's other
 //      coordinates; d' = fl(2eb * fl((float)S)); then verbatim exceptions.
 #include "common.cuh"
+#include "scan.cuh"
 
 #include <algorithm>
 
@@ -38,6 +39,7 @@ struct Geo {
 constexpr int k1Threads = 256;
 constexpr int k1PerThread = 16;
 constexpr int k1Tile = k1Threads * k1PerThread;  // 4096
+static_assert(k1Tile == (int)kRecon1DTile, "decoder tile sums and 1D tiles must agree");
 constexpr int k2TX = 128, k2TY = 32, k2Threads = 256;
 constexpr int k3TX = 32, k3TY = 16, k3TZ = 16, k3Threads = 512;
 
@@ -93,8 +95,12 @@ __global__ void k_scatter_outliers(ReconArgs a, uint64_t n)
         bool ok = idx < n;
         if (t > 0) ok &= idx > *reinterpret_cast<const uint32_t *>(o + 8 * (t - 1));
         if (ok) ok &= a.codes[idx] == 0;
-        if (ok) a.dscr[idx] = d;
-        else atomicOr(&a.ctl->error, DERR_CORRUPT);
+        if (ok) {
+            a.dscr[idx] = d;
+            if (a.ndim == 1) atomicAdd(&a.faces[idx / kRecon1DTile], (uint32_t)d);
+        } else {
+            atomicOr(&a.ctl->error, DERR_CORRUPT);
+        }
     }
 }
 
@@ -133,23 +139,6 @@ __device__ __forceinline__ void load16_delta(const ReconArgs &a, uint64_t n, uin
     }
 }
 
-__global__ void __launch_bounds__(k1Threads) k_faces_1d(ReconArgs a, Geo g, uint32_t *F)
-{
-    __shared__ uint32_t sh[33];
-    if (a.ctl->error & DERR_CORRUPT) return;
-    const uint64_t n = g.n[0];
-    for (uint64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
-        uint32_t d[16];
-        load16_delta(a, n, tile * k1Tile + (uint64_t)threadIdx.x * 16, d);
-        uint32_t s = 0;
-#pragma unroll
-        for (int j = 0; j < 16; j++) s += d[j];
-        uint32_t tot;
-        block_excl_scan(s, sh, &tot);
-        if (threadIdx.x == 0) F[g.off[1] + tile] = tot;
-    }
-}
-
 __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, const uint32_t *F)
 {
     __shared__ uint32_t sh[33];
@@ -168,7 +157,7 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
         }
         uint32_t tot;
         uint32_t pre = block_excl_scan(s, sh, &tot);
-        pre += tile ? F[g.off[1] + tile - 1] : 0u;
+        pre += F[tile];  // exclusive prefix of the tile sums
         float v[16];
 #pragma unroll
         for (int j = 0; j < 16; j++) v[j] = recon_value((int32_t)(d[j] + pre), ebx2);
@@ -368,6 +357,15 @@ __global__ void __launch_bounds__(1024) k_scan_lines_cta(Geo g, int A, int d, ui
     }
 }
 
+// in-place exclusive scan of the 1D tile sums (modulo 2^32)
+struct TileOp {
+    using T = uint32_t;
+    uint32_t *v;
+    __device__ T load(uint64_t i) const { return v[i]; }
+    __device__ void store(uint64_t i, T x) const { v[i] = x; }
+    __device__ void total(T) const {}
+};
+
 }  // namespace
 
 uint64_t recon_faces_entries(uint32_t ndim, const uint64_t dims[3])
@@ -386,11 +384,17 @@ void launch_reconstruct(const ReconArgs &a, cudaStream_t st, int *launches)
         nl++;
     }
     const int gridt = (int)std::min<uint64_t>(g.ntiles, (uint64_t)a.num_sms * 8);
-    if (g.ndim == 1) k_faces_1d<<<gridt, k1Threads, 0, st>>>(a, g, a.faces);
-    else if (g.ndim == 2) k_faces<k2TX, k2TY, 1, k2Threads><<<gridt, k2Threads, 0, st>>>(a, g, a.faces);
-    else k_faces<k3TX, k3TY, k3TZ, k3Threads><<<gridt, k3Threads, 0, st>>>(a, g, a.faces);
-    nl++;
-    for (int A = 1; A < 8; A++) {
+    if (g.ndim == 1) {
+        // tile sums were accumulated by the decoder and the outlier scatter
+        nl += launch_scan(TileOp{a.faces}, g.ntiles, a.scan_partial, st);
+    } else if (g.ndim == 2) {
+        k_faces<k2TX, k2TY, 1, k2Threads><<<gridt, k2Threads, 0, st>>>(a, g, a.faces);
+        nl++;
+    } else {
+        k_faces<k3TX, k3TY, k3TZ, k3Threads><<<gridt, k3Threads, 0, st>>>(a, g, a.faces);
+        nl++;
+    }
+    for (int A = 1; A < 8 && g.ndim > 1; A++) {
         if (!g.size[A]) continue;
         for (int d = 0; d < (int)g.ndim; d++) {
             if (!((A >> d) & 1) || g.nt[d] < 2) continue;

@@ -37,6 +37,8 @@ SIGNATURES = {
     "gbsz_profile_enable": ([_P, C.c_int], C.c_int),
     "gbsz_profile_read": ([_P, _P, _P, C.POINTER(C.c_uint64)], C.c_int),
     "gbsz_codebook_noalloc": ([_P, C.c_uint32, _P, _P, C.POINTER(C.c_uint32), _P], C.c_int),
+    "gbsz_compress_batch": ([_P, C.c_uint32, _P, _P, _P, _P, _P, _P, _P], C.c_int),
+    "gbsz_decompress_batch": ([_P, C.c_uint32, _P, _P, _P, _P, _P, _P], C.c_int),
 }
 
 
@@ -164,6 +166,44 @@ class Context:
     def decompress_status(self, archive, nbytes, out, stream=None):
         return load().gbsz_decompress(self.h, C.c_void_p(archive.data_ptr()), int(nbytes),
                                       C.c_void_p(out.data_ptr()), out.numel(), _stream(stream))
+
+    # -- batches -------------------------------------------------------------
+    def compress_batch(self, fields, eb, eb_mode=EB_REL, radius=512, chunk=0, outs=None, stream=None,
+                       params=None):
+        """fields: list of contiguous float32 CUDA tensors.  eb/radius/chunk
+        may be scalars or per-field lists.  Returns (list of archive tensors,
+        list of nbytes, list of statuses); raises if any field failed."""
+        k = len(fields)
+        per = lambda v: list(v) if isinstance(v, (list, tuple)) else [v] * k
+        ebs, rads, chunks, modes = per(eb), per(radius), per(chunk), per(eb_mode)
+        if params is None:
+            params = [make_params(field_dims(f), e, m, r, c) for f, e, m, r, c in zip(fields, ebs, modes, rads, chunks)]
+        P = (Params * k)(*params)
+        if outs is None:
+            outs = [torch.empty(load().gbsz_compress_bound(C.byref(p)), dtype=torch.uint8, device=f.device)
+                    for p, f in zip(params, fields)]
+        fp = (C.c_void_p * k)(*[f.data_ptr() for f in fields])
+        ap = (C.c_void_p * k)(*[o.data_ptr() for o in outs])
+        caps = (C.c_size_t * k)(*[o.numel() for o in outs])
+        nb = (C.c_size_t * k)()
+        sts = (C.c_int * k)()
+        st = load().gbsz_compress_batch(self.h, k, fp, P, ap, caps, nb, sts, _stream(stream))
+        if st != OK:
+            raise GbszError(st, "gbsz_compress_batch")
+        return outs, list(nb), list(sts)
+
+    def decompress_batch(self, archives, nbytes, outs, stream=None):
+        """archives: list of uint8 CUDA tensors; outs: float32 CUDA tensors."""
+        k = len(archives)
+        ap = (C.c_void_p * k)(*[a.data_ptr() for a in archives])
+        bs = (C.c_size_t * k)(*[int(b) for b in nbytes])
+        op = (C.c_void_p * k)(*[o.data_ptr() for o in outs])
+        caps = (C.c_uint64 * k)(*[o.numel() for o in outs])
+        sts = (C.c_int * k)()
+        st = load().gbsz_decompress_batch(self.h, k, ap, bs, op, caps, sts, _stream(stream))
+        if st != OK:
+            raise GbszError(st, "gbsz_decompress_batch")
+        return outs, list(sts)
 
     # -- host-buffer API ---------------------------------------------------
     def compress_host(self, field_np, eb, eb_mode=EB_REL, radius=512, chunk=0, out=None, stream=None):

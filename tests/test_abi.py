@@ -54,9 +54,11 @@ def test_compress_bound_and_invalid_params(lib):
 
 
 def test_auto_chunk_rule(lib):
-    assert gbsz.auto_chunk([1 << 28]) == 4096
+    assert gbsz.auto_chunk([1 << 28]) == 1024
+    assert gbsz.auto_chunk([1 << 30]) == 4096
     assert gbsz.auto_chunk([64, 64, 64]) == 64
-    assert gbsz.auto_chunk([3600, 1800]) == 256
+    assert gbsz.auto_chunk([512, 512, 512]) == 512
+    assert gbsz.auto_chunk([3600, 1800]) == 64
 
 
 def test_null_context_and_pointers_rejected(lib):

@@ -1,0 +1,86 @@
+"""Batched compress/decompress: every field of a batch gives exactly the
+bytes (archive) and floats (reconstruction) that a single-field call gives,
+and the oracle too; fields run on several internal streams, so this also
+checks that no state leaks between concurrently running fields."""
+import numpy as np
+import pytest
+import torch
+
+from oracle import ref
+from paper_2007_09625_gb300 import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def mixed_fields(count, seed):
+    rng = np.random.default_rng(seed)
+    kinds = [("walk", 1), ("sinus", 2), ("grf", 2), ("lognormal", 3), ("sinus", 3)]
+    out = []
+    for i in range(count):
+        kind, rank = kinds[i % len(kinds)]
+        if rank == 1:
+            shape = (int(rng.integers(1000, 300000)),)
+        elif rank == 2:
+            shape = (int(rng.integers(20, 400)), int(rng.integers(20, 700)))
+        else:
+            shape = tuple(int(v) for v in rng.integers(5, 60, 3))
+        if kind == "grf" and rank == 3:
+            kind = "lognormal"
+        out.append(workloads.field_for(kind, shape, seed=seed + i))
+    return out
+
+
+@pytest.fixture(scope="module")
+def ctx(gb):
+    c = gb.Context(0)
+    yield c
+    c.close()
+
+
+def test_batch_matches_single_calls_and_oracle(gb, ctx):
+    fields = mixed_fields(13, seed=300)  # more fields than internal streams
+    ebs = [1e-4, 1e-3, 1e-5] * 5
+    rads = [512, 512, 32768, 64] * 4
+    ts = [torch.from_numpy(f).cuda() for f in fields]
+    arcs, nbs, sts = ctx.compress_batch(ts, ebs[:13], gb.EB_REL, rads[:13], 0)
+    torch.cuda.synchronize()
+    assert all(s == gb.OK for s in sts)
+    for i, f in enumerate(fields):
+        single, nb1 = ctx.compress(ts[i], ebs[i], gb.EB_REL, rads[i], 0)
+        a_b = arcs[i][:nbs[i]].cpu().numpy()
+        assert nbs[i] == nb1 and np.array_equal(a_b, single[:nb1].cpu().numpy()), i
+        chunk = gb.auto_chunk(list(f.shape)[::-1], rads[i])
+        oa = ref.compress(f, ebs[i], ref.EB_REL, rads[i], chunk)
+        assert np.array_equal(a_b, oa), i
+    outs = [torch.empty_like(t) for t in ts]
+    outs, dsts = ctx.decompress_batch(arcs, nbs, outs)
+    torch.cuda.synchronize()
+    assert all(s == gb.OK for s in dsts)
+    for i, f in enumerate(fields):
+        yo = ref.decompress(arcs[i][:nbs[i]].cpu().numpy())
+        assert np.array_equal(outs[i].cpu().numpy().view(np.uint32), yo.view(np.uint32)), i
+
+
+def test_batch_reports_per_field_errors(gb, ctx):
+    fields = mixed_fields(4, seed=400)
+    ts = [torch.from_numpy(f).cuda() for f in fields]
+    params = [gb.make_params(gb.field_dims(t), 1e-4) for t in ts]
+    outs = [torch.empty(gb.load().gbsz_compress_bound(__import__("ctypes").byref(p)), dtype=torch.uint8,
+                        device="cuda") for p in params]
+    outs[2] = torch.empty(64, dtype=torch.uint8, device="cuda")  # far too small
+    with pytest.raises(gb.GbszError):
+        ctx.compress_batch(ts, 1e-4, outs=outs, params=params)
+    # the other fields still complete correctly
+    import ctypes as C
+    k = len(ts)
+    P = (gb.Params * k)(*params)
+    fp = (C.c_void_p * k)(*[t.data_ptr() for t in ts])
+    ap = (C.c_void_p * k)(*[o.data_ptr() for o in outs])
+    caps = (C.c_size_t * k)(*[o.numel() for o in outs])
+    nb = (C.c_size_t * k)()
+    sts = (C.c_int * k)()
+    st = gb.load().gbsz_compress_batch(ctx.h, k, fp, P, ap, caps, nb, sts, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    assert st == gb.ERR_CAPACITY and list(sts) == [0, 0, gb.ERR_CAPACITY, 0] and nb[2] > 64
+    for i in (0, 1, 3):
+        single, n1 = ctx.compress(ts[i], 1e-4)
+        assert nb[i] == n1 and torch.equal(outs[i][:n1], single[:n1])

@@ -1,0 +1,64 @@
+"""The serving loop on the GPU: a stream of mixed compress / decompress
+requests arriving while others run gives, for every request, exactly the
+bytes (archives) and floats (reconstructions) that the same request gives
+alone.  Integer / bit-exact results, so the tolerance is equality."""
+import time
+
+import numpy as np
+import pytest
+import torch
+
+from paper_2007_09625_gb300 import serve, workloads
+
+pytestmark = pytest.mark.gpu
+
+
+def test_mixed_stream_matches_alone(gb):
+    rng = np.random.default_rng(77)
+    kinds = ["walk", "sinus", "grf", "lognormal"]
+    fields = []
+    for i in range(24):
+        rank = int(rng.integers(1, 4))
+        nbytes = float(np.exp(rng.uniform(np.log(64 << 10), np.log(4 << 20))))
+        n = max(64, int(nbytes // 4))
+        if rank == 1:
+            shape = (n,)
+        elif rank == 2:
+            a = int(np.sqrt(n))
+            shape = (max(2, n // a), a)
+        else:
+            a = int(round(n ** (1 / 3)))
+            shape = (max(2, n // (a * a)), a, a)
+        kind = kinds[i % 4] if rank > 1 or kinds[i % 4] == "walk" else "walk"
+        fields.append(workloads.field_for(kind, shape, seed=500 + i))
+    rels = [1e-2, 1e-3, 1e-4]
+    alone = gb.Context(0)
+    ref_arcs, ref_out = [], []
+    for i, f in enumerate(fields):
+        a, nb = alone.compress(torch.from_numpy(f).cuda(), rels[i % 3])
+        ref_arcs.append((a[:nb].clone(), nb))
+        ref_out.append(alone.decompress(a, nb).cpu().numpy())
+    torch.cuda.synchronize()
+
+    srv = serve.Server(workers=2, max_batch=4, mem_budget=2 << 30).start()
+    reqs = []
+    for i, f in enumerate(fields):
+        x = torch.from_numpy(f).cuda()
+        if i % 2 == 0:
+            reqs.append(("c", i, srv.submit(serve.COMPRESS, x, eb=rels[i % 3])))
+        else:
+            a, nb = ref_arcs[i]
+            reqs.append(("d", i, srv.submit(serve.DECOMPRESS, a, nbytes=nb)))
+        time.sleep(float(rng.exponential(1 / 200.0)))
+    for kind, i, r in reqs:
+        out = r.wait(120)
+        assert r.status == gb.OK
+        if kind == "c":
+            arc, nb = out
+            assert nb == ref_arcs[i][1] and torch.equal(arc[:nb], ref_arcs[i][0]), i
+        else:
+            assert np.array_equal(out.cpu().numpy().view(np.uint32), ref_out[i].view(np.uint32)), i
+    st = srv.stats()
+    srv.stop()
+    alone.close()
+    assert st["requests"] == len(fields) and st["p99_ms"] >= st["p50_ms"]
