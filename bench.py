@@ -248,7 +248,9 @@ def main():
     torch.cuda.synchronize(dev)
     # correctness of the timed configuration: error bound on every element
     err = (x.double() - y.double()).abs()
-    ebf = float(np.frombuffer(arc[56:60].cpu().numpy().tobytes(), np.float32)[0])  # header: eb
+    hdr = arc[:128].cpu().numpy()
+    ebf = float(np.frombuffer(hdr[56:60].tobytes(), np.float32)[0])  # header: eb
+    maxlen = int(np.frombuffer(hdr[104:108].tobytes(), np.uint32)[0])  # header: longest code
     fin = torch.isfinite(x)
     assert float(err[fin].max()) <= ebf, "error bound violated"
 
@@ -279,8 +281,8 @@ def main():
     value = 4.0 * n * ws / (ms_step / 1e3) / 1e9
 
     # compress-only and decompress-only times from the stage events
-    comp_ms = sum(stage_ms[0:4]) / a.steps
-    dec_ms = sum(stage_ms[4:7]) / a.steps
+    comp_ms = sum(stage_ms[0:6]) / a.steps
+    dec_ms = sum(stage_ms[6:10]) / a.steps
     cr = 4.0 * n / nb
 
     # roofline of the dominant stage (algorithmic bytes)
@@ -290,12 +292,12 @@ def main():
     w_words = int(np.frombuffer(arc[96:104].cpu().numpy().tobytes(), np.uint64)[0])
     f = m_out / n
     nc = (n + chunk - 1) // chunk
-    alg = {  # algorithmic bytes per call of each stage
-        0: 4.0 * n,                                               # read the field
-        1: 6.0 * n + 8.0 * m_out,                                 # field in, codes out, outlier residuals
-        3: 2.0 * n + 16.0 * m_out + 4.0 * w_words + 4.0 * nc,     # codes + residuals in; stream, outliers, bits out
-        5: 4.0 * w_words + 12.0 * nc + 2.0 * n,                   # stream, bits, offsets in; codes out
-        6: 6.0 * n + 16.0 * m_out,                                # codes in, field out; outlier scatter
+    alg = {  # algorithmic bytes per launch of each single-kernel stage
+        0: 4.0 * n,                                               # minmax: read the field
+        1: 6.0 * n + 8.0 * m_out,                                 # dual-quant: field in, codes out, residuals
+        3: 2.0 * n + n / 32.0 + 4.0 * nc,                         # count: codes in; lane bits, chunk bits out
+        5: 2.0 * n + n / 32.0 + 16.0 * m_out + 4.0 * w_words,     # pack: codes, lane bits, residuals in; stream, outliers out
+        8: 4.0 * w_words + 12.0 * nc + 2.0 * n,                   # decode: stream, bits, offsets in; codes out
     }
     dom = max(alg, key=lambda s: stage_ms[s])
     dom_ms = stage_ms[dom] / max(stage_calls[dom], 1)
@@ -355,7 +357,7 @@ def main():
                 "config": workload_config(a, n, chunk),
                 "compress_gbs": 4.0 * n / (comp_ms / 1e3) / 1e9 if comp_ms else None,
                 "decompress_gbs": 4.0 * n / (dec_ms / 1e3) / 1e9 if dec_ms else None,
-                "compression_ratio": cr, "outlier_frac": f,
+                "compression_ratio": cr, "outlier_frac": f, "max_code_len": maxlen,
                 "stage_ms_per_step": {nm: stage_ms[i] / a.steps for i, nm in enumerate(stage_names)},
                 "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "batch_vs_per_field": batch,

@@ -172,11 +172,12 @@ gbsz_status gbsz_debug_copy(gbsz_ctx *ctx, int which, void *h_dst,
  * events around each stage on its stream.  gbsz_profile_read synchronises,
  * adds up the stage durations recorded since the last read, and returns
  * them with the count of kernel launches.  Stage indices:
- *   0 error bound, 1 dual-quant+histogram, 2 codebook, 3 encode+deflate,
- *   4 decode tables, 5 decode, 6 reconstruct (scatter+scan+patch),
- *   7 other (header/aux)
+ *   0 error bound, 1 dual-quant+histogram, 2 codebook,
+ *   3 encode: bit counts, 4 encode: offset scan, 5 encode: pack (deflate),
+ *   6 decode tables, 7 decode: chunk offset scan, 8 decode: symbols,
+ *   9 reconstruct (scatter+scan+patch), 10 other (reserved)
  * ms[nstage], calls[nstage] may be NULL.  Errors: INVALID_ARG, CUDA. */
-#define GBSZ_NSTAGE 8
+#define GBSZ_NSTAGE 11
 gbsz_status gbsz_profile_enable(gbsz_ctx *ctx, int enable);
 gbsz_status gbsz_profile_read(gbsz_ctx *ctx, double *ms, uint64_t *calls,
                               uint64_t *kernel_launches);

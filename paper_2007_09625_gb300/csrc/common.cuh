@@ -141,13 +141,13 @@ __device__ __forceinline__ int32_t prequant_full(float d, const EbScalars &s, bo
 __device__ __forceinline__ int32_t prequant(float d, const EbScalars &s, bool &exc)
 {
     const float t = __fmul_rn(d, s.inv2eb);
-    if (fabsf(t) < 4194304.0f) {
-        const float tm = __fadd_rn(t, 12582912.0f);
-        const float r = __fmul_rn(s.ebx2, __fsub_rn(tm, 12582912.0f));
-        if (fabsf(__fsub_rn(d, r)) < s.eb) {
-            exc = false;
-            return __float_as_int(tm) - 0x4B400000;
-        }
+    const float tm = __fadd_rn(t, 12582912.0f);
+    const float r = __fmul_rn(s.ebx2, __fsub_rn(tm, 12582912.0f));
+    // one predicate for both tests (NaN and Inf fail the first)
+    const bool ok = (fabsf(t) < 4194304.0f) & (fabsf(__fsub_rn(d, r)) < s.eb);
+    if (ok) {
+        exc = false;
+        return __float_as_int(tm) - 0x4B400000;
     }
     return prequant_full(d, s, exc);
 }
@@ -290,6 +290,9 @@ struct CodebookArgs {
     uint32_t *count;       // [kMaxLen + 2]
     uint32_t *start;       // [kMaxLen + 2]
     uint16_t *sorted;      // symbols in (len, sym) order
+    void *lutf;            // complete table over fast_bits-bit prefixes (see kFastLutMax)
+    uint32_t fast_bits;    // 0: no complete table
+    uint32_t fast_pair;    // the table resolves two codes per entry
     uint32_t expect_maxlen;  // decode: header's maxlen
     // scratch (global, kMaxBins-sized or 2x)
     unsigned long long *keyA, *keyB;
@@ -297,6 +300,19 @@ struct CodebookArgs {
     Control *ctl;
 };
 constexpr int kLutBits = 12;
+// When every code is at most kFastLutMax bits and symbols fit 12 bits, the
+// decoder uses one complete table indexed by B = maxlen bits.  Up to
+// kPairLutMax bits an entry resolves the first code of its prefix and, when
+// it also fits, the second: 32-bit entries len1 | len2 << 4 | sym1 << 8 |
+// sym2 << 20 (len2 = 0: the second code is longer than the bits left).
+// Above that, 16-bit entries (sym << 4) | len.  Length 0: no code matches.
+constexpr uint32_t kFastLutMax = 15;
+constexpr uint32_t kPairLutMax = 14;
+constexpr size_t kFastLutBytes = 4u << kPairLutMax;  // also 2 << kFastLutMax
+__host__ __device__ inline uint32_t fast_lut_bits(uint32_t maxlen, uint32_t nbins)
+{
+    return (maxlen >= 1 && maxlen <= kFastLutMax && nbins <= 4096) ? maxlen : 0u;
+}
 
 void launch_codebook(const CodebookArgs &a, cudaStream_t st);
 void launch_decode_tables(const CodebookArgs &a, cudaStream_t st);
@@ -322,7 +338,8 @@ struct EncodeArgs {
     double eb;
     int num_sms;
 };
-int launch_encode(const EncodeArgs &a, cudaStream_t st);  // returns kernels launched
+// phase 0: count, 1: scan of the unit totals, 2: pack; returns kernels launched
+int launch_encode(const EncodeArgs &a, cudaStream_t st, int phase);
 uint64_t encode_units(uint64_t n, uint32_t chunk);        // units (per-unit totals) of the encoder
 
 struct DecodeArgs {
@@ -335,6 +352,8 @@ struct DecodeArgs {
     const unsigned long long *first;
     const uint32_t *count, *start;
     const uint16_t *sorted;
+    const void *lutf;          // complete table when fast_bits != 0
+    uint32_t fast_bits, fast_pair, num_sms;
     unsigned long long *chunk_off;  // scratch nchunk
     unsigned long long *scan_partial;  // scratch for the offset scan
     uint32_t *tile_sums;  // 1D: residual sum per 4096-point tile (zeroed), else NULL
@@ -342,7 +361,8 @@ struct DecodeArgs {
     Control *ctl;
 };
 constexpr uint32_t kRecon1DTile = 4096;  // 1D reconstruction tile (points)
-int launch_decode(const DecodeArgs &a, cudaStream_t st);
+// phase 0: chunk word offsets (scan), 1: symbols; returns kernels launched
+int launch_decode(const DecodeArgs &a, cudaStream_t st, int phase);
 
 struct ReconArgs {
     const uint16_t *codes;

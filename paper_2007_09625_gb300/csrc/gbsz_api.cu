@@ -105,7 +105,7 @@ struct Slot {
     Buf codes, dscr, unit_tot, unit_off, unit_part, lane_bits, chunk_off, faces, scan_part;
     // fixed-size scratch
     Buf hist, cw64, cw32, codes_only, keyA, keyB, nodef, parent, distA, distB, parA, parB;
-    Buf lut, first, count, start, sorted;
+    Buf lut, lutf, first, count, start, sorted;
     cudaStream_t stream = nullptr;  // used by batch calls
     cudaEvent_t done = nullptr;
 
@@ -125,14 +125,14 @@ struct Slot {
         return hist.ensure(B * 4) && cw64.ensure(B * 8) && cw32.ensure(B * 4) && codes_only.ensure(B * 8) &&
                keyA.ensure(B * 8) && keyB.ensure(B * 8) && nodef.ensure(B * 4) && parent.ensure(2 * B * 4) &&
                distA.ensure(2 * B * 4) && distB.ensure(2 * B * 4) && parA.ensure(2 * B * 4) &&
-               parB.ensure(2 * B * 4) && lut.ensure((1u << kLutBits) * 4) && first.ensure((kMaxLen + 2) * 8) &&
+               parB.ensure(2 * B * 4) && lut.ensure((1u << kLutBits) * 4) && lutf.ensure(kFastLutBytes) && first.ensure((kMaxLen + 2) * 8) &&
                count.ensure((kMaxLen + 2) * 4) && start.ensure((kMaxLen + 2) * 4) && sorted.ensure(B * 2);
     }
     void release()
     {
         for (Buf *b : {&codes, &dscr, &unit_tot, &unit_off, &unit_part, &lane_bits, &chunk_off, &faces, &scan_part,
                        &hist, &cw64,
-                       &cw32, &codes_only, &keyA, &keyB, &nodef, &parent, &distA, &distB, &parA, &parB, &lut,
+                       &cw32, &codes_only, &keyA, &keyB, &nodef, &parent, &distA, &distB, &parA, &parB, &lut, &lutf,
                        &first, &count, &start, &sorted})
             b->release();
         if (ctl) cudaFree(ctl);
@@ -260,6 +260,7 @@ CodebookArgs codebook_args(Slot *s)
     a.cw32 = s->cw32.as<uint32_t>();
     a.codes_only = s->codes_only.as<uint64_t>();
     a.lut = s->lut.as<uint32_t>();
+    a.lutf = s->lutf.p;
     a.first = s->first.as<unsigned long long>();
     a.count = s->count.as<uint32_t>();
     a.start = s->start.as<uint32_t>();
@@ -407,9 +408,12 @@ gbsz_status enqueue_compress(gbsz_ctx *c, Slot *s, const float *d_field, const g
     for (int i = 0; i < 3; i++) en.dims[i] = p.dims[i];
     en.eb = p.eb;
     en.num_sms = c->num_sms;
-    stage_begin(c, st, &e0);
-    const int nenc = launch_encode(en, st);
-    stage_end(c, st, 3, e0);
+    int nenc = 0;
+    for (int ph = 0; ph < 3; ph++) {
+        stage_begin(c, st, &e0);
+        nenc += launch_encode(en, st, ph);
+        stage_end(c, st, 3 + ph, e0);
+    }
     c->launches += 3 + nenc;
     return GBSZ_OK;
 }
@@ -432,10 +436,12 @@ gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void
     cb.len_in = arc + kHeaderBytes;
     cb.nbins = 2 * h.p.radius;
     cb.expect_maxlen = h.maxlen;
+    cb.fast_bits = fast_lut_bits(h.maxlen, cb.nbins);
+    cb.fast_pair = cb.fast_bits && cb.fast_bits <= kPairLutMax ? 1u : 0u;
     cudaEvent_t e0;
     stage_begin(c, st, &e0);
     launch_decode_tables(cb, st);
-    stage_end(c, st, 4, e0);
+    stage_end(c, st, 6, e0);
 
     DecodeArgs d{};
     d.archive = arc;
@@ -452,14 +458,21 @@ gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void
     d.count = cb.count;
     d.start = cb.start;
     d.sorted = cb.sorted;
+    d.lutf = cb.lutf;
+    d.fast_bits = cb.fast_bits;
+    d.fast_pair = cb.fast_pair;
+    d.num_sms = c->num_sms;
     d.chunk_off = s->chunk_off.as<unsigned long long>();
     d.scan_partial = s->scan_part.as<unsigned long long>();
     d.tile_sums = h.p.ndim == 1 ? s->faces.as<uint32_t>() : nullptr;
     d.codes = s->codes.as<uint16_t>();
     d.ctl = s->ctl;
-    stage_begin(c, st, &e0);
-    const int ndec = launch_decode(d, st);
-    stage_end(c, st, 5, e0);
+    int ndec = 0;
+    for (int ph = 0; ph < 2; ph++) {
+        stage_begin(c, st, &e0);
+        ndec += launch_decode(d, st, ph);
+        stage_end(c, st, 7 + ph, e0);
+    }
 
     ReconArgs r{};
     r.codes = d.codes;
@@ -482,7 +495,7 @@ gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void
     int nl = 0;
     stage_begin(c, st, &e0);
     launch_reconstruct(r, st, &nl);
-    stage_end(c, st, 6, e0);
+    stage_end(c, st, 9, e0);
     c->launches += 1 + ndec + nl;
     return GBSZ_OK;
 }

@@ -404,6 +404,33 @@ __global__ void __launch_bounds__(kCbThreads, 1) k_decode_tables(CodebookArgs a)
         }
         a.lut[v] = e;
     }
+    // complete table over fast_bits-bit prefixes (every code fits)
+    const uint32_t B = a.fast_bits;
+    auto code_at = [&](uint32_t bits, uint32_t nb, uint32_t &len) -> uint32_t {
+        // the code that starts the nb-bit string `bits` (MSB first), if any
+        for (uint32_t l = 1; l <= nb; l++) {
+            const unsigned long long off = (unsigned long long)(bits >> (nb - l)) - canon.first[l];
+            if (off < canon.count[l]) {
+                len = l;
+                return a.sorted[canon.start[l] + off];
+            }
+        }
+        len = 0;
+        return 0;
+    };
+    for (uint32_t v = t; B && v < (1u << B); v += T) {
+        uint32_t l1, l2 = 0, s2 = 0;
+        const uint32_t s1 = code_at(v, B, l1);
+        if (!a.fast_pair) {
+            static_cast<uint16_t *>(a.lutf)[v] = (uint16_t)(l1 ? (s1 << 4) | l1 : 0u);
+            continue;
+        }
+        if (l1 && l1 < B) {
+            s2 = code_at(v & ((1u << (B - l1)) - 1), B - l1, l2);
+            if (!l2) s2 = 0;
+        }
+        static_cast<uint32_t *>(a.lutf)[v] = l1 ? (l1 | (l2 << 4) | (s1 << 8) | (s2 << 20)) : 0u;
+    }
 }
 
 constexpr size_t kCbSmem = 16 * kCbThreads * sizeof(uint32_t);

@@ -51,6 +51,7 @@ struct Table {
             code = v & ((1ull << 56) - 1);
         }
     }
+    __device__ __forceinline__ uint32_t raw32(uint32_t sym) const { return static_cast<const uint32_t *>(tab)[sym]; }
     __device__ __forceinline__ uint32_t len_of(uint32_t sym) const
     {
         if (CW32) return static_cast<const uint32_t *>(tab)[sym] >> 24;
@@ -113,40 +114,6 @@ __device__ __forceinline__ void stage_round(const uint16_t *codes, uint64_t r0, 
     __syncwarp();
 }
 
-template <typename F>
-__device__ __forceinline__ void for_symbols(const Lane &ln, F f)
-{
-    if (ln.sm) {
-        for (uint32_t j = 0; j < ln.nv; j++) {
-            const uint4 w = ln.vec(j);
-            const uint32_t v[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-            for (int k = 0; k < 8; k++) f(8 * j + k, (v[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu);
-        }
-    } else {
-        for (uint32_t j = 0; j < ln.cnt; j++) f(j, (uint32_t)ln.g[j]);
-    }
-}
-
-struct LaneStats {
-    uint32_t bits, out, exc;
-};
-
-template <bool CW32>
-__device__ __forceinline__ LaneStats lane_stats(const EncodeArgs &a, const Table<CW32> &tab, const Lane &ln,
-                                                uint64_t s0, bool any_exc)
-{
-    LaneStats st{0, 0, 0};
-    for_symbols(ln, [&](uint32_t j, uint32_t c) {
-        st.bits += tab.len_of(c);
-        if (c == 0) {
-            st.out++;
-            if (any_exc) st.exc += a.dscr[s0 + j].y != 0;
-        }
-    });
-    return st;
-}
-
 __device__ __forceinline__ void put_u32(uint8_t *p, uint32_t v) { *reinterpret_cast<uint32_t *>(p) = v; }
 
 // archive header and the zero bytes between sections (last unit's warp)
@@ -201,23 +168,83 @@ struct UnitGeom {
 };
 
 // Phase 1: per-unit totals, per-lane bit counts and the archive's chunk bit
-// counts.  Codes are read with coalesced 16-byte loads (lane l holds symbols
-// 256k + 8l .. +7 of step k); the sums of each S-symbol segment (one "lane"
-// of the packing phase) are formed by reductions over the S/8 lanes that
-// hold it, so no staging is needed here.
+// counts.  Codes are read with coalesced 16-byte loads, four in flight per
+// lane (lane l holds symbols 256k + 8l .. +7 of step k).  A "count entry" per
+// symbol packs its code length (bits 0-15) with a code-0 flag (bit 16), so one
+// add per symbol accumulates both; exceptions add 1 << 24.  Each lane parks
+// the packed sum of its 8 symbols in a padded per-warp shared array, and lane
+// l then sums the S / 8 partials of its S-symbol segment (the segment lane l
+// packs in phase 3).
+struct CountSmem {
+    const uint32_t *t;
+    __device__ __forceinline__ uint32_t operator()(uint32_t c) const { return t[c]; }
+};
 template <bool CW32>
-__device__ void count_units(const EncodeArgs &a, uint64_t nunits, const Table<CW32> &tab)
+struct CountGlobal {
+    Table<CW32> tab;
+    __device__ __forceinline__ uint32_t operator()(uint32_t c) const
+    {
+        return tab.len_of(c) | (c == 0 ? 0x10000u : 0u);
+    }
+};
+
+constexpr uint32_t kPartStride = 33;  // padded row of per-lane partials
+
+// one 128-bit read-only load
+__device__ __forceinline__ uint4 ldg_nc16(const void *p)
+{
+    uint4 v;
+    asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
+}
+
+// ANY_EXC is a template argument so that fields without exceptions carry no
+// (predicated) residual loads at all
+template <bool ANY_EXC, typename CT>
+__device__ __forceinline__ uint32_t count8(const EncodeArgs &a, const CT &ct, uint4 w, uint64_t p)
+{
+    const uint32_t v[4] = {w.x, w.y, w.z, w.w};
+    uint32_t s = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) s += ct(v[q] & 0xFFFFu) + ct(v[q] >> 16);
+    if (ANY_EXC && (s & 0xFF0000u)) {
+#pragma unroll
+        for (int q = 0; q < 8; q++) {
+            const uint32_t c = (v[q >> 1] >> ((q & 1) * 16)) & 0xFFFFu;
+            if (c == 0 && a.dscr[p + q].y != 0) s += 1u << 24;
+        }
+    }
+    return s;
+}
+
+template <bool ANY_EXC, typename CT>
+__device__ __forceinline__ uint32_t count_tail(const EncodeArgs &a, const CT &ct, uint64_t p, uint64_t n)
+{
+    uint32_t s = 0;
+    for (uint32_t q = 0; q < 8 && p + q < n; q++) {
+        const uint32_t c = a.codes[p + q];
+        s += ct(c);
+        if (ANY_EXC && c == 0 && a.dscr[p + q].y != 0) s += 1u << 24;
+    }
+    return s;
+}
+
+template <bool ANY_EXC, typename CT>
+__device__ __forceinline__ void count_units(const EncodeArgs &a, uint64_t nunits, const CT &ct, uint32_t *part)
 {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t n = a.n;
     const uint32_t C = a.chunk;
     const UnitGeom ug(C);
-    const uint32_t S = ug.S, per = S / 8;  // lanes holding one segment in a step
+    const uint32_t S = ug.S, per = S / 8;  // partials per segment
     const uint32_t segs = 32 / per;        // segments per 256-symbol step
+    const uint32_t steps = S / 8;          // 256-symbol steps per round, a multiple of 4
     const uint64_t nchunk = (n + C - 1) / C;
     const Layout L0 = make_layout(a.radius, nchunk, a.ctl->n_out, a.ctl->n_exc, 0);
-    const bool any_exc = a.ctl->n_exc != 0;
     const bool first_of_chunk = (lane & (ug.G - 1)) == 0;
+    const uint32_t *myseg = part + (lane / segs) * kPartStride + (lane % segs) * per;
     const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     for (uint64_t u = gw; u < nunits; u += nw) {
@@ -228,47 +255,32 @@ __device__ void count_units(const EncodeArgs &a, uint64_t nunits, const Table<CW
         unsigned long long chunk_bits = 0;
         for (uint32_t r = 0; r < rounds; r++) {
             const uint64_t r0 = ubase + (uint64_t)r * 32 * S;
-            // segment sums: after step k, lane k*segs + (lane / per) owns one
-            uint32_t sb = 0, so = 0, se = 0;
-            const uint32_t steps = S / 8;  // 256-symbol steps per round (= 32*S/256)
-            for (uint32_t k = 0; k < steps; k++) {
-                const uint64_t p = r0 + 256ull * k + 8ull * lane;
-                uint32_t b = 0, o = 0, e = 0;
-                if (p + 8 <= n) {
-                    const uint4 w = *reinterpret_cast<const uint4 *>(a.codes + p);
-                    const uint32_t v[4] = {w.x, w.y, w.z, w.w};
+            const bool full = r0 + 32ull * S <= n;
+            const uint4 *src = reinterpret_cast<const uint4 *>(a.codes + r0) + lane;
+            __syncwarp();  // the previous round's partials have been read
+            for (uint32_t k = 0; k < steps; k += 4) {
+                uint32_t s4[4];
+                if (full) {
+                    uint4 w[4];
 #pragma unroll
-                    for (int q = 0; q < 8; q++) {
-                        const uint32_t c = (v[q >> 1] >> ((q & 1) * 16)) & 0xFFFFu;
-                        b += tab.len_of(c);
-                        o += c == 0;
-                        if (any_exc && c == 0) e += a.dscr[p + q].y != 0;
-                    }
+                    for (int i = 0; i < 4; i++) w[i] = ldg_nc16(src + 32 * (k + i));
+#pragma unroll
+                    for (int i = 0; i < 4; i++) s4[i] = count8<ANY_EXC>(a, ct, w[i], r0 + 256ull * (k + i) + 8 * lane);
                 } else {
-                    for (uint32_t q = 0; q < 8 && p + q < n; q++) {
-                        const uint32_t c = a.codes[p + q];
-                        b += tab.len_of(c);
-                        o += c == 0;
-                        if (any_exc && c == 0) e += a.dscr[p + q].y != 0;
+#pragma unroll
+                    for (int i = 0; i < 4; i++) {
+                        const uint64_t p = r0 + 256ull * (k + i) + 8ull * lane;
+                        s4[i] = p + 8 <= n ? count8<ANY_EXC>(a, ct, src[32 * (k + i)], p)
+                                           : count_tail<ANY_EXC>(a, ct, p, n);
                     }
                 }
-                for (uint32_t x = 1; x < per; x <<= 1) {
-                    b += __shfl_xor_sync(0xffffffffu, b, x);
-                    o += __shfl_xor_sync(0xffffffffu, o, x);
-                    e += __shfl_xor_sync(0xffffffffu, e, x);
-                }
-                // segment k*segs + g is held (reduced) by lanes g*per .. g*per+per-1
-                const uint32_t owner = lane - k * segs;  // valid when lane is one of this step's segments
-                const uint32_t srcl = (owner < segs ? owner : 0u) * per;
-                const uint32_t tb = __shfl_sync(0xffffffffu, b, srcl);
-                const uint32_t to = __shfl_sync(0xffffffffu, o, srcl);
-                const uint32_t te = __shfl_sync(0xffffffffu, e, srcl);
-                if (owner < segs) {
-                    sb = tb;
-                    so = to;
-                    se = te;
-                }
+#pragma unroll
+                for (int i = 0; i < 4; i++) part[(k + i) * kPartStride + lane] = s4[i];
             }
+            __syncwarp();
+            uint32_t seg = 0;
+            for (uint32_t t = 0; t < per; t++) seg += myseg[t];
+            const uint32_t sb = seg & 0xFFFFu, so = (seg >> 16) & 0xFFu, se = seg >> 24;
             const uint64_t s0 = r0 + (uint64_t)lane * S;
             const uint32_t cnt = s0 < n ? (uint32_t)(n - s0 < S ? n - s0 : S) : 0u;
             if (cnt) a.lane_bits[r0 / S + lane] = sb;
@@ -283,9 +295,11 @@ __device__ void count_units(const EncodeArgs &a, uint64_t nunits, const Table<CW
                 }
                 unit_words += warp_sum(cw);
             }
-            unit_out += warp_sum(so);
-            unit_exc += warp_sum(se);
+            unit_out += so;
+            unit_exc += se;
         }
+        unit_out = warp_sum(unit_out);
+        unit_exc = warp_sum(unit_exc);
         if (ug.multi) {
             unit_words = (uint32_t)((chunk_bits + 31) / 32);
             if (lane == 0) put_u32(a.archive + L0.bits + 4 * u, (uint32_t)chunk_bits);
@@ -384,23 +398,24 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
                 const uint32_t woff = __shfl_sync(0xffffffffu, winc - cw, lane & ~(G - 1));
                 gbit = (W0 + woff) * 32 + bin;
             }
-            // pack: words wholly owned are stored at once; the first word is
-            // the "head" when this lane starts inside it (owned by the
-            // previous lane), the last partial one is the "tail"
+            // pack: every completed word is stored as soon as it is full,
+            // with no branch (the store is predicated).  The accumulator
+            // starts with (gbit & 31) zero bits, so a lane that starts inside
+            // a word (the "head", shared with the previous lane of its chunk)
+            // stores that word with only its own bits; after the loop the
+            // head is read back and handed to the previous lane, which stores
+            // its last partial word (the "tail") merged with it.  Every full
+            // lane holds at least S >= 64 bits, so it always completes its
+            // head word inside the loop; only a short last lane can end inside
+            // it, and then its bits are handed over without being stored.
             const bool starts_mid = (gbit & 31u) != 0 && cnt > 0;
+            if ((gbit + bits + 31) / 32 > stream_cap) cap_err = true;
+            const bool ok = !cap_err;
+            uint32_t *lout = stream + (gbit >> 5);
             unsigned long long acc = 0;
             uint32_t nacc = (uint32_t)(gbit & 31u);
-            uint64_t widx = gbit >> 5;
-            const uint64_t hidx = starts_mid ? widx : ~0ull;  // the head's word index
-            if ((gbit + bits + 31) / 32 > stream_cap) cap_err = true;
-            uint32_t *out = cap_err ? nullptr : stream;
-            uint32_t head = 0;
+            uint32_t nw32 = 0;  // words completed by this lane
             unsigned long long zlo = 0, zhi = 0;  // code-0 positions of this lane
-            auto put = [&](uint32_t w) {
-                if (widx == hidx) head = w;
-                else if (out) out[widx] = w;
-                widx++;
-            };
             if (ln.sm) {
                 for (uint32_t j = 0; j < ln.nv; j++) {
                     const uint4 q4 = ln.vec(j);
@@ -417,14 +432,26 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
                     }
 #pragma unroll
                     for (int k = 0; k < 8; k++) {
-                        uint32_t len;
-                        unsigned long long code;
-                        tab.get((v[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu, len, code);
-                        uint32_t w[2], nw;
-                        append<CW32>(acc, nacc, code, len, w, nw);
-                        if (nw) {
-                            put(w[0]);
-                            if (!CW32 && nw > 1) put(w[1]);
+                        const uint32_t c = (v[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
+                        if (CW32) {
+                            const uint32_t e = tab.raw32(c);
+                            const uint32_t len = e >> 24;
+                            acc = (acc << len) | (e & 0xFFFFFFu);
+                            nacc += len;
+                            const bool full_w = nacc >= 32;
+                            nacc -= full_w ? 32u : 0u;
+                            if (full_w && ok) lout[nw32] = (uint32_t)(acc >> nacc);
+                            nw32 += full_w ? 1u : 0u;
+                        } else {
+                            uint32_t len;
+                            unsigned long long code;
+                            tab.get(c, len, code);
+                            uint32_t w[2], nw;
+                            append<CW32>(acc, nacc, code, len, w, nw);
+                            for (uint32_t q = 0; q < nw; q++) {
+                                if (ok) lout[nw32] = w[q];
+                                nw32++;
+                            }
                         }
                     }
                 }
@@ -436,40 +463,37 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
                     tab.get(c, len, code);
                     uint32_t w[2], nw;
                     append<CW32>(acc, nacc, code, len, w, nw);
-                    for (uint32_t q = 0; q < nw; q++) put(w[q]);
+                    for (uint32_t q = 0; q < nw; q++) {
+                        if (ok) lout[nw32] = w[q];
+                        nw32++;
+                    }
                     if (c == 0) {
                         if (j < 64) zlo |= 1ull << j;
                         else zhi |= 1ull << (j - 64);
                     }
                 }
             }
-            uint32_t tail = 0;
-            bool has_tail = false;
-            if (nacc > 0 && cnt > 0) {
-                const uint32_t w = (uint32_t)(acc << (32 - nacc));
-                if (widx == hidx) {  // the whole lane fits inside its first word
-                    head = w;
-                } else {
-                    tail = w;
-                    has_tail = true;
-                }
-            }
-            const uint64_t tail_idx = widx;
+            __syncwarp();  // in-loop head stores land before the previous lane's merged store
+            const uint32_t last = nacc > 0 ? (uint32_t)(acc << (32 - nacc)) : 0u;
+            const bool inside_head = starts_mid && nw32 == 0;  // short last lane
+            uint32_t head = 0;
+            if (starts_mid && ok) head = inside_head ? last : lout[0];
+            const bool has_tail = nacc > 0 && cnt > 0 && !inside_head;
             // hand heads to the previous lane of the same chunk
             const uint32_t next_head = __shfl_down_sync(0xffffffffu, head, 1);
             const bool next_starts_mid = __shfl_down_sync(0xffffffffu, starts_mid ? 1u : 0u, 1) != 0;
             const bool next_same_chunk = lane < 31 && ((lane + 1) & (G - 1)) != 0;
             const uint32_t prev_carry = __shfl_sync(0xffffffffu, carry, 31);
             if (has_tail) {
-                uint32_t v = tail;
+                uint32_t v = last;
                 if (next_same_chunk && next_starts_mid) v |= next_head;
                 if (multi && lane == 31 && r + 1 < rounds) {
                     carry = v;  // the next round's lane 0 finishes this word
-                } else if (out) {
-                    out[tail_idx] = v;
+                } else if (ok) {
+                    lout[nw32] = v;
                 }
             }
-            if (multi && lane == 0 && r > 0 && starts_mid && out) out[hidx] = head | prev_carry;
+            if (multi && lane == 0 && r > 0 && starts_mid && ok) lout[0] = head | prev_carry;
             if (multi && !(lane == 31 && has_tail)) carry = 0;
             // outliers and exceptions in index order
             const uint32_t nz = __popcll(zlo) + __popcll(zhi);
@@ -525,14 +549,34 @@ __device__ __forceinline__ const void *load_table(const EncodeArgs &a, uint32_t 
     return s_tab;
 }
 
-__global__ void __launch_bounds__(kEncThreads, 4) k_encode_count(EncodeArgs a, uint64_t nunits, uint32_t use_smem)
+constexpr uint32_t kCountSmemBins = 8192;
+constexpr uint32_t kPartWords = 16 * kPartStride;  // per warp, S <= 128
+
+template <bool ANY_EXC>
+__device__ __forceinline__ void count_dispatch(const EncodeArgs &a, uint64_t nunits, uint32_t *part, uint32_t *tab,
+                                               bool w32)
 {
-    extern __shared__ unsigned long long s_tabc[];
+    if (a.nbins <= kCountSmemBins) count_units<ANY_EXC>(a, nunits, CountSmem{tab}, part);
+    else if (w32) count_units<ANY_EXC>(a, nunits, CountGlobal<true>{Table<true>{a.cw32}}, part);
+    else count_units<ANY_EXC>(a, nunits, CountGlobal<false>{Table<false>{a.cw64}}, part);
+}
+
+__global__ void __launch_bounds__(kEncThreads, 4) k_encode_count(EncodeArgs a, uint64_t nunits)
+{
+    extern __shared__ uint32_t s_cnt[];
+    uint32_t *part = s_cnt + (threadIdx.x >> 5) * kPartWords;
+    uint32_t *tab = s_cnt + kWarps * kPartWords;
     if (a.ctl->error & (DERR_EB | DERR_INTERNAL)) return;
     const bool w32 = a.ctl->maxlen <= 24;
-    const void *tab = load_table(a, use_smem, s_tabc, w32);
-    if (w32) count_units<true>(a, nunits, Table<true>{tab});
-    else count_units<false>(a, nunits, Table<false>{tab});
+    if (a.nbins <= kCountSmemBins) {
+        for (uint32_t i = threadIdx.x; i < a.nbins; i += blockDim.x) {
+            const uint32_t len = w32 ? a.cw32[i] >> 24 : (uint32_t)(a.cw64[i] >> 56);
+            tab[i] = len | (i == 0 ? 0x10000u : 0u);
+        }
+        __syncthreads();
+    }
+    if (a.ctl->n_exc != 0) count_dispatch<true>(a, nunits, part, tab, w32);
+    else count_dispatch<false>(a, nunits, part, tab, w32);
 }
 
 __global__ void __launch_bounds__(kEncThreads, 3) k_encode_pack(EncodeArgs a, uint64_t nunits, uint32_t use_smem)
@@ -542,9 +586,16 @@ __global__ void __launch_bounds__(kEncThreads, 3) k_encode_pack(EncodeArgs a, ui
     unsigned long long *s_tab = reinterpret_cast<unsigned long long *>(s_dyn + kWarps * (kRound / 8));
     if (a.ctl->error & (DERR_EB | DERR_INTERNAL)) return;
     const bool w32 = a.ctl->maxlen <= 24;
-    const void *tab = load_table(a, use_smem, s_tab, w32);
-    if (w32) pack_units<true>(a, nunits, Table<true>{tab}, slot);
-    else pack_units<false>(a, nunits, Table<false>{tab}, slot);
+    // each call sees where its table lives, so shared-memory tables are read
+    // with shared loads
+    if (use_smem) {
+        load_table(a, 1, s_tab, w32);
+        if (w32) pack_units<true>(a, nunits, Table<true>{s_tab}, slot);
+        else pack_units<false>(a, nunits, Table<false>{s_tab}, slot);
+    } else {
+        if (w32) pack_units<true>(a, nunits, Table<true>{a.cw32}, slot);
+        else pack_units<false>(a, nunits, Table<false>{a.cw64}, slot);
+    }
 }
 
 // exclusive scan of the unit totals (words, outliers | exceptions << 32)
@@ -557,7 +608,7 @@ struct UnitOp {
     __device__ void total(T) const {}
 };
 
-// opt in to the dynamic shared memory the packing kernel needs, once per device
+// opt in to the dynamic shared memory the kernels need, once per device
 void set_encode_smem()
 {
     static unsigned long long done = 0;  // one bit per device id < 64
@@ -567,6 +618,8 @@ void set_encode_smem()
     if (bit && (done & bit)) return;
     const size_t most = (size_t)kWarps * kRound * 2 + 4096 * 8;
     cudaFuncSetAttribute(k_encode_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+    cudaFuncSetAttribute(k_encode_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)((kWarps * kPartWords + kCountSmemBins) * 4));
     done |= bit;
 }
 
@@ -579,20 +632,23 @@ uint64_t encode_units(uint64_t n, uint32_t chunk)
     return (n + U - 1) / U;
 }
 
-int launch_encode(const EncodeArgs &a, cudaStream_t st)
+int launch_encode(const EncodeArgs &a, cudaStream_t st, int phase)
 {
     const uint64_t nunits = encode_units(a.n, a.chunk);
     const uint32_t use_smem = a.nbins <= 4096 ? 1u : 0u;
     const size_t tab = use_smem ? (size_t)a.nbins * 8 : 0;
-    const size_t pack_smem = (size_t)kWarps * kRound * 2 + tab;
     set_encode_smem();
     const uint64_t want = (nunits + kWarps - 1) / kWarps;
-    const int grid_c = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)a.num_sms * 4));
-    const int grid_p = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)a.num_sms * 3));
-    k_encode_count<<<grid_c, kEncThreads, tab, st>>>(a, nunits, use_smem);
-    const int ns = launch_scan(UnitOp{a.unit_tot, a.unit_off}, nunits, a.scan_part, st);
-    k_encode_pack<<<grid_p, kEncThreads, pack_smem, st>>>(a, nunits, use_smem);
-    return 2 + ns;
+    if (phase == 0) {
+        const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)a.num_sms * 4));
+        const size_t smem = (kWarps * kPartWords + (a.nbins <= kCountSmemBins ? a.nbins : 0)) * 4;
+        k_encode_count<<<grid, kEncThreads, smem, st>>>(a, nunits);
+        return 1;
+    }
+    if (phase == 1) return launch_scan(UnitOp{a.unit_tot, a.unit_off}, nunits, a.scan_part, st);
+    const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)a.num_sms * 3));
+    k_encode_pack<<<grid, kEncThreads, (size_t)kWarps * kRound * 2 + tab, st>>>(a, nunits, use_smem);
+    return 1;
 }
 
 }  // namespace gbsz

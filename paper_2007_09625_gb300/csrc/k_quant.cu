@@ -185,7 +185,9 @@ __device__ __forceinline__ uint32_t warp_sum(uint32_t v)
     return v;
 }
 
-__device__ void hist_flush(HistState &h, uint32_t *ghist, Control *ctl)
+// out_from_bin0: the block's outliers are its shared bin-0 count (every bin
+// in shared memory) rather than the per-thread n_out
+__device__ void hist_flush(HistState &h, uint32_t *ghist, Control *ctl, bool out_from_bin0 = false)
 {
     const uint32_t lo = warp_sum(h.c_lo), mid = warp_sum(h.c_mid), hi = warp_sum(h.c_hi);
     const uint32_t no = warp_sum(h.n_out), ne = warp_sum(h.n_exc);
@@ -198,6 +200,7 @@ __device__ void hist_flush(HistState &h, uint32_t *ghist, Control *ctl)
         if (ne) atomicAdd(&ctl->n_exc, (unsigned long long)ne);
     }
     __syncthreads();
+    if (out_from_bin0 && threadIdx.x == 0 && h.sh[0]) atomicAdd(&ctl->n_out, (unsigned long long)h.sh[0]);
     for (uint32_t i = threadIdx.x; i < h.nsh; i += blockDim.x) {
         const uint32_t v = h.sh[i];
         if (v) atomicAdd(&ghist[h.lo + i], v);
@@ -234,26 +237,41 @@ __device__ __forceinline__ uint32_t code_of(uint32_t d, bool exc, uint32_t R)
     return (!exc && d + (R - 1) < 2 * R - 1) ? d + R : 0u;
 }
 
-__device__ __forceinline__ void point_1d(HistState &h, const QuantArgs &a, uint32_t idx, uint32_t d, bool exc,
-                                         uint32_t &code)
+// One point of the 1D kernel, without branches.  The three central codes
+// are counted in a packed register (8-bit fields, emptied every tile);
+// other codes go to the shared bins with a predicated atomic.  With every bin
+// in shared memory (WIN), the block's outlier count is its bin-0 count, so
+// it is not counted here.
+template <bool WIN>
+__device__ __forceinline__ uint32_t point_1d(HistState &h, const QuantArgs &a, uint32_t idx, uint32_t d, bool exc,
+                                             uint32_t &pk)
 {
-    code = code_of(d, exc, h.R);
-    h.c_mid += code == h.R;
-    h.c_lo += code == h.R - 1;
-    h.c_hi += code == h.R + 1;
-    if (code + 1 < h.R || code > h.R + 1) {  // not one of the three central codes
-        if (code == 0) {
-            a.dscr[idx] = make_int2((int32_t)d, exc ? 1 : 0);
-            h.n_out++;
-            h.n_exc += exc;
-        }
+    const uint32_t code = code_of(d, exc, h.R);
+    const uint32_t k = code + 1 - h.R;  // 0, 1, 2 for R-1, R, R+1
+    const bool central = k < 3;
+    pk += central ? 1u << (k << 3) : 0u;
+    if (WIN) {
+        if (!central) atomicAdd(&h.sh[code], 1u);
+    } else if (!central) {
         const uint32_t b = code - h.lo;
         if (b < h.nsh) atomicAdd(&h.sh[b], 1u);
         else atomicAdd(&a.hist[code], 1u);
+        h.n_out += code == 0;
     }
+    if (code == 0) a.dscr[idx] = make_int2((int32_t)d, exc ? 1 : 0);
+    h.n_exc += exc;
+    return code;
 }
 
-template <bool VEC>
+__device__ __forceinline__ void unpack_central(HistState &h, uint32_t &pk)
+{
+    h.c_lo += pk & 0xFFu;
+    h.c_mid += (pk >> 8) & 0xFFu;
+    h.c_hi += pk >> 16;
+    pk = 0;
+}
+
+template <bool VEC, bool WIN>
 __global__ void __launch_bounds__(kQ1Threads) k_dualquant_1d(QuantArgs a, uint32_t ntiles)
 {
     extern __shared__ uint32_t sh_hist[];
@@ -286,15 +304,15 @@ __global__ void __launch_bounds__(kQ1Threads) k_dualquant_1d(QuantArgs a, uint32
         bool dummy;
         uint32_t qprev = (e0 > 0 && e0 <= n) ? (uint32_t)prequant(vp, sc, dummy) : 0u;
         uint32_t code[kQ1Per];
-#pragma unroll
-        for (int j = 0; j < kQ1Per; j++) {
-            bool exc;
-            const uint32_t q = (uint32_t)prequant(v[j], sc, exc);
-            code[j] = 0;
-            if (full || e0 + j < n) point_1d(h, a, e0 + j, q - qprev, exc, code[j]);
-            qprev = q;
-        }
+        uint32_t pk = 0;
         if (full) {
+#pragma unroll
+            for (int j = 0; j < kQ1Per; j++) {
+                bool exc;
+                const uint32_t q = (uint32_t)prequant(v[j], sc, exc);
+                code[j] = point_1d<WIN>(h, a, e0 + j, q - qprev, exc, pk);
+                qprev = q;
+            }
             uint4 *o = reinterpret_cast<uint4 *>(a.codes + e0);
             o[0] = make_uint4(code[0] | (code[1] << 16), code[2] | (code[3] << 16), code[4] | (code[5] << 16),
                               code[6] | (code[7] << 16));
@@ -302,11 +320,17 @@ __global__ void __launch_bounds__(kQ1Threads) k_dualquant_1d(QuantArgs a, uint32
                               code[14] | (code[15] << 16));
         } else {
 #pragma unroll
-            for (int j = 0; j < kQ1Per; j++)
-                if (e0 + j < n) a.codes[e0 + j] = (uint16_t)code[j];
+            for (int j = 0; j < kQ1Per; j++) {
+                bool exc;
+                const uint32_t q = (uint32_t)prequant(v[j], sc, exc);
+                if (e0 + j < n) a.codes[e0 + j] = (uint16_t)point_1d<WIN>(h, a, e0 + j, q - qprev, exc, pk);
+                qprev = q;
+            }
         }
+        unpack_central(h, pk);
     }
-    hist_flush(h, a.hist, a.ctl);
+    if (WIN) h.n_out = 0;  // taken from bin 0 below
+    hist_flush(h, a.hist, a.ctl, WIN);
 }
 
 // ---------------------------------------------------------------------------
@@ -504,10 +528,11 @@ void launch_dualquant(const QuantArgs &a, cudaStream_t st)
         const uint64_t n = a.dims[0];
         const uint32_t ntiles = (uint32_t)((n + kQ1Tile - 1) / kQ1Tile);
         const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)a.num_sms * 8);
-        if ((reinterpret_cast<uintptr_t>(a.x) & 15) == 0)
-            k_dualquant_1d<true><<<grid, kQ1Threads, hist_bytes, st>>>(a, ntiles);
-        else
-            k_dualquant_1d<false><<<grid, kQ1Threads, hist_bytes, st>>>(a, ntiles);
+        const bool vec = (reinterpret_cast<uintptr_t>(a.x) & 15) == 0, win = nbins <= kWinBins;
+        if (vec && win) k_dualquant_1d<true, true><<<grid, kQ1Threads, hist_bytes, st>>>(a, ntiles);
+        else if (vec) k_dualquant_1d<true, false><<<grid, kQ1Threads, hist_bytes, st>>>(a, ntiles);
+        else if (win) k_dualquant_1d<false, true><<<grid, kQ1Threads, hist_bytes, st>>>(a, ntiles);
+        else k_dualquant_1d<false, false><<<grid, kQ1Threads, hist_bytes, st>>>(a, ntiles);
     } else if (a.ndim == 2) {
         const uint32_t ntx = (uint32_t)((a.dims[0] + kQ2TX - 1) / kQ2TX);
         const uint32_t nty = (uint32_t)((a.dims[1] + kQ2TY - 1) / kQ2TY);

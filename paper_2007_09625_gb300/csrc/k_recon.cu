@@ -104,6 +104,62 @@ __global__ void k_scatter_outliers(ReconArgs a, uint64_t n)
     }
 }
 
+// 1D: the outlier residuals go to the tile sums (added to the in-cap sums
+// the decoder left there), and every 512-point group g learns where its
+// outliers start in the index-ordered list: start[g] = first outlier with
+// idx >= 512 g, for g = 0 .. ngroups (start[ngroups] = m).  Consecutive
+// outliers mostly share a tile, so a warp adds each run of equal tiles with
+// one atomic.
+constexpr uint32_t kGroup1D = 512;  // points per warp in the 1D value kernel
+
+__global__ void k_outlier_tiles_1d(ReconArgs a, uint64_t n, uint64_t ngroups, uint32_t *start)
+{
+    const uint8_t *o = a.archive + a.off_outl;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    // whole warps stay in the loop so the shuffles see every lane
+    const uint64_t tmax = (a.m + 31) & ~31ull;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tmax; t += stride) {
+        const bool live = t < a.m;
+        uint32_t idx = 0, d = 0;
+        bool ok = true;
+        int64_t gprev = -1;
+        if (live) {
+            idx = *reinterpret_cast<const uint32_t *>(o + 8 * t);
+            d = *reinterpret_cast<const uint32_t *>(o + 8 * t + 4);
+            ok = idx < n;
+            if (t > 0) {
+                const uint32_t pidx = *reinterpret_cast<const uint32_t *>(o + 8 * (t - 1));
+                ok &= idx > pidx;
+                gprev = (int64_t)(pidx / kGroup1D);
+            }
+        }
+        const uint64_t T = ok ? idx / kRecon1DTile : 0;
+        if (live && !ok) atomicOr(&a.ctl->error, DERR_CORRUPT);
+        // runs of equal tiles inside the warp (the list is sorted)
+        const uint64_t key = live && ok ? T : ~0ull;
+        const uint64_t kprev = __shfl_up_sync(0xffffffffu, key, 1);
+        const bool head = lane == 0 || kprev != key;
+        uint32_t sum = live && ok ? d : 0u;
+        const unsigned heads = __ballot_sync(0xffffffffu, head);
+        const unsigned below = heads & (0xffffffffu >> (31 - lane));
+        const uint32_t seg0 = 31 - __clz(below);  // first lane of this lane's run
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            const uint32_t v = __shfl_up_sync(0xffffffffu, sum, off);
+            if (lane >= (uint32_t)off && lane - off >= seg0) sum += v;
+        }
+        const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u) || t + 1 >= a.m;
+        if (live && ok && tail) atomicAdd(&a.faces[T], sum);
+        if (live && ok) {
+            const uint64_t G = idx / kGroup1D;
+            for (int64_t u = gprev + 1; u <= (int64_t)G; u++) start[u] = (uint32_t)t;
+            if (t + 1 == a.m)
+                for (uint64_t u = G + 1; u <= ngroups; u++) start[u] = (uint32_t)a.m;
+        }
+    }
+}
+
 __global__ void k_patch_exceptions(ReconArgs a, uint64_t n)
 {
     const uint8_t *e = a.archive + a.off_exc;
@@ -122,45 +178,105 @@ __global__ void k_patch_exceptions(ReconArgs a, uint64_t n)
 // ---------------------------------------------------------------------------
 // 1D tiles: 4096 points, 16 consecutive per thread, block scan of totals
 
-__device__ __forceinline__ void load16_delta(const ReconArgs &a, uint64_t n, uint64_t s0, uint32_t *d)
+// One 4096-point tile per block iteration; warp w of the block covers the
+// tile's 512-point group w.  A warp's outliers are the run start[g] ..
+// start[g+1] of the index-ordered list; a warp scan of the lanes' code-0
+// counts gives each lane its first entry, and its code-0 points, in order,
+// take the next entries, whose indices must be theirs (and the counts must
+// match the run).  Residuals are code - R, or the outlier's residual for
+// code 0; their sum within the tile comes from a thread run and one block
+// scan; the tile's carry F[tile] completes the prefix.  The next tile's codes
+// and group bounds are loaded while this one is processed.
+__device__ __forceinline__ uint4 ldg_nc16(const void *p)
 {
-    if (s0 + 16 <= n) {
-        const uint4 *p = reinterpret_cast<const uint4 *>(a.codes + s0);
-        const uint4 w0 = p[0], w1 = p[1];
-        const uint32_t w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
-#pragma unroll
-        for (int j = 0; j < 16; j++) {
-            const uint32_t c = (w[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu;
-            d[j] = c ? c - a.radius : (uint32_t)a.dscr[s0 + j];
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < 16; j++) d[j] = s0 + j < n ? delta_of(a, s0 + j) : 0u;
-    }
+    uint4 v;
+    asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
+                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+                 : "l"(p));
+    return v;
 }
 
-__global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, const uint32_t *F)
+__global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, const uint32_t *F, const uint32_t *start)
 {
     __shared__ uint32_t sh[33];
+    __shared__ uint32_t s_od[k1Threads * 17];  // outlier residuals by (thread, point); stride 17 spreads banks
     if (a.ctl->error & DERR_CORRUPT) return;
     const uint64_t n = g.n[0];
     const float ebx2 = a.ebx2;
+    const uint32_t R = a.radius;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint2 *ol = reinterpret_cast<const uint2 *>(a.archive + a.off_outl);
+    uint32_t *od = s_od + threadIdx.x * 17;
+    bool bad = false;
+    // loads of one tile: this thread's codes and its warp's group bounds
+    auto fetch = [&](uint64_t tile, uint4 &w0, uint4 &w1, uint32_t &ga, uint32_t &gb) {
+        const uint64_t s0 = tile * k1Tile + (uint64_t)threadIdx.x * 16;
+        if (s0 + 16 <= n) {
+            w0 = ldg_nc16(a.codes + s0);
+            w1 = ldg_nc16(a.codes + s0 + 8);
+        }
+        ga = gb = 0;
+        if (a.m) {
+            const uint64_t gi = tile * (k1Tile / kGroup1D) + warp;
+            ga = start[gi];
+            gb = start[gi + 1];
+        }
+    };
+    uint4 w0 = make_uint4(0, 0, 0, 0), w1 = w0;
+    uint32_t ga = 0, gb = 0;
+    if (blockIdx.x < g.ntiles) fetch(blockIdx.x, w0, w1, ga, gb);
     for (uint64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
         const uint64_t s0 = tile * k1Tile + (uint64_t)threadIdx.x * 16;
-        uint32_t d[16];
-        load16_delta(a, n, s0, d);
-        uint32_t s = 0;
+        uint32_t c[16];
+        if (s0 + 16 <= n) {
+            const uint32_t w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
+#pragma unroll
+            for (int j = 0; j < 16; j++) c[j] = (w[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu;
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; j++) c[j] = s0 + j < n ? a.codes[s0 + j] : R;  // past the end: residual 0
+        }
+        const uint32_t lo = ga, hi = gb;
+        if (tile + gridDim.x < g.ntiles) fetch(tile + gridDim.x, w0, w1, ga, gb);
+        uint32_t d[16], zm = 0;
 #pragma unroll
         for (int j = 0; j < 16; j++) {
-            s += d[j];
-            d[j] = s;
+            d[j] = c[j] - R;
+            zm |= (c[j] == 0 ? 1u : 0u) << j;
         }
+        const uint32_t zc = __popc(zm);
+        const uint32_t zinc = warp_incl_scan(zc);
+        if (lane == 31 && (uint64_t)lo + zinc != hi) bad = true;  // a group holds exactly its outliers
+        uint64_t e = (uint64_t)lo + (zinc - zc);
+        for (uint32_t m = zm; m; m &= m - 1) {  // this thread's code-0 points, in order
+            const uint32_t j = __ffs(m) - 1;
+            uint32_t dv = 0;
+            if (e < hi) {
+                const uint2 en = ol[e];
+                if (en.x == s0 + j) dv = en.y;
+                else bad = true;
+            } else {
+                bad = true;
+            }
+            od[j] = dv;
+            e++;
+        }
+        if (zm) {
+#pragma unroll
+            for (int j = 0; j < 16; j++)
+                if (c[j] == 0) d[j] = od[j];
+        }
+        uint32_t s = 0;
+#pragma unroll
+        for (int j = 0; j < 16; j++) s += d[j];
         uint32_t tot;
-        uint32_t pre = block_excl_scan(s, sh, &tot);
-        pre += F[tile];  // exclusive prefix of the tile sums
+        uint32_t run = block_excl_scan(s, sh, &tot) + F[tile];
         float v[16];
 #pragma unroll
-        for (int j = 0; j < 16; j++) v[j] = recon_value((int32_t)(d[j] + pre), ebx2);
+        for (int j = 0; j < 16; j++) {
+            run += d[j];
+            v[j] = recon_value((int32_t)run, ebx2);
+        }
         if (s0 + 16 <= n) {
             float4 *o = reinterpret_cast<float4 *>(a.out + s0);
 #pragma unroll
@@ -170,7 +286,9 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
             for (int j = 0; j < 16; j++)
                 if (s0 + j < n) a.out[s0 + j] = v[j];
         }
+        __syncthreads();  // sh is reused by the next tile
     }
+    if (bad) atomicOr(&a.ctl->error, DERR_CORRUPT);
 }
 
 // ---------------------------------------------------------------------------
@@ -378,9 +496,12 @@ void launch_reconstruct(const ReconArgs &a, cudaStream_t st, int *launches)
     const Geo g = make_geo(a.ndim, a.dims);
     const uint64_t n = g.n[0] * g.n[1] * g.n[2];
     int nl = 0;
+    uint32_t *start1d = reinterpret_cast<uint32_t *>(a.dscr);  // 1D: per-group outlier starts
+    const uint64_t ngroups = g.ntiles * (k1Tile / kGroup1D);
     if (a.m) {
         const int grid = (int)std::min<uint64_t>((a.m + 255) / 256, (uint64_t)a.num_sms * 16);
-        k_scatter_outliers<<<grid, 256, 0, st>>>(a, n);
+        if (g.ndim == 1) k_outlier_tiles_1d<<<grid, 256, 0, st>>>(a, n, ngroups, start1d);
+        else k_scatter_outliers<<<grid, 256, 0, st>>>(a, n);
         nl++;
     }
     const int gridt = (int)std::min<uint64_t>(g.ntiles, (uint64_t)a.num_sms * 8);
@@ -407,7 +528,7 @@ void launch_reconstruct(const ReconArgs &a, cudaStream_t st, int *launches)
             nl++;
         }
     }
-    if (g.ndim == 1) k_values_1d<<<gridt, k1Threads, 0, st>>>(a, g, a.faces);
+    if (g.ndim == 1) k_values_1d<<<gridt, k1Threads, 0, st>>>(a, g, a.faces, start1d);
     else if (g.ndim == 2) k_values<k2TX, k2TY, 1, k2Threads><<<gridt, k2Threads, 0, st>>>(a, g, a.faces);
     else k_values<k3TX, k3TY, k3TZ, k3Threads><<<gridt, k3Threads, 0, st>>>(a, g, a.faces);
     nl++;

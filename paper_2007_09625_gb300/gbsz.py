@@ -15,9 +15,9 @@ LIB_PATH = os.path.join(_HERE, "libgbsz.so")
 
 OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CORRUPT, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(8)
 EB_ABS, EB_REL = 0, 1
-NSTAGE = 8
-STAGES = ["error_bound", "dualquant_hist", "codebook", "encode_deflate", "decode_tables", "decode",
-          "reconstruct", "other"]
+NSTAGE = 11
+STAGES = ["error_bound", "dualquant_hist", "codebook", "encode_count", "encode_scan", "encode_pack",
+          "decode_tables", "decode_offsets", "decode", "reconstruct", "other"]
 DEBUG_CODES, DEBUG_HIST, DEBUG_SCALARS, DEBUG_DECODED, DEBUG_CODEWORDS = range(5)
 
 # every entry point of include/gbsz.h with its ctypes signature

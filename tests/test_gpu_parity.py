@@ -175,3 +175,50 @@ def test_gpu_decodes_oracle_archives(gb, ctx):
     at = torch.from_numpy(oa).cuda()
     y = ctx.decompress(at, oa.size).cpu().numpy()
     assert np.array_equal(y.view(np.uint32), ref.decompress(oa).view(np.uint32))
+
+
+def fibonacci_walk(levels, seed):
+    """1D integer-valued walk whose Lorenzo residuals take `levels` distinct
+    values with Fibonacci counts 1, 1, 2, 3, 5, ...: the Huffman tree is a
+    chain, so the longest code has levels - 1 bits.  With absolute eb 0.5
+    (2eb = 1) every value is its own prequantized integer.  The most frequent
+    residual is 0; the others are +-1, +-2, ... with signs chosen (largest
+    count first) to keep the drift of the walk small, so every value stays an
+    exact float32 integer."""
+    F = [1, 1]
+    while len(F) < levels:
+        F.append(F[-1] + F[-2])
+    counts = F[:levels][::-1]  # largest first
+    vals, drift = [0], 0
+    for k in range(1, levels, 2):
+        m = (k + 1) // 2
+        ca = counts[k]
+        cb = counts[k + 1] if k + 1 < levels else 0
+        s = 1 if abs(drift + m * (ca - cb)) <= abs(drift - m * (ca - cb)) else -1
+        vals += [s * m, -s * m][: levels - k]
+        drift += s * m * (ca - cb)
+    rng = np.random.default_rng(seed)
+    v = np.repeat(np.array(vals, np.int64), counts)
+    rng.shuffle(v)
+    x = np.cumsum(v)
+    assert np.abs(x).max() < 2 ** 24
+    return x.astype(np.float32)
+
+
+@pytest.mark.parametrize("levels,C", [(12, 64), (16, 4096), (17, 256), (22, 1024), (27, 8192)])
+def test_long_codes(gb, ctx, levels, C):
+    """Code lengths up to and past the decoder's complete table (15 bits),
+    past the encoder's 24-bit codeword form, through both 1D tile-sum paths."""
+    x = fibonacci_walk(levels, seed=levels)
+    arc, nb, oa = compare_stages(gb, ctx, x, 0.5, ref.EB_ABS, 512, C)
+    assert ref.sections(oa)["maxlen"] == levels - 1
+    check_decompress(gb, ctx, arc, nb, oa, x, 0.5, ref.EB_ABS)
+
+
+def test_codes_longer_than_a_word(gb, ctx):
+    """A 34-bit longest code (24M symbols): codewords that span two stream
+    words and a decoder window that advances twice for one code."""
+    x = fibonacci_walk(35, seed=35)
+    arc, nb, oa = compare_stages(gb, ctx, x, 0.5, ref.EB_ABS, 512, 4096)
+    assert ref.sections(oa)["maxlen"] == 34
+    check_decompress(gb, ctx, arc, nb, oa, x, 0.5, ref.EB_ABS)
