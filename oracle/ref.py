@@ -253,7 +253,8 @@ def sections(archive):
     off_str = al(off_exc + 8 * e)
     d = dict(radius=R, nchunk=nc, m=m, e=e, words=w, maxlen=u32(104), chunk=u32(72),
              total=u64(112), n=u64(40),
-             sc=np.frombuffer(b[56:68], dtype=np.float32).copy())
+             sc=np.frombuffer(b[56:68], dtype=np.float32).copy(),
+             off_len=off_len, off_bits=off_bits, off_out=off_out, off_exc=off_exc, off_str=off_str)
     d["len"] = a[off_len:off_len + 2 * R].copy()
     d["bits"] = np.frombuffer(b[off_bits:off_bits + 4 * nc], np.uint32).copy()
     o = np.frombuffer(b[off_out:off_out + 8 * m], np.uint32).reshape(-1, 2)

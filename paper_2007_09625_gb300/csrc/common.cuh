@@ -216,6 +216,25 @@ __device__ __forceinline__ uint32_t block_excl_scan(uint32_t v, uint32_t *sh, ui
     return r;
 }
 
+// The same without the closing barrier: sh may be written again only after
+// every thread has passed another barrier (callers alternate two arrays).
+__device__ __forceinline__ uint32_t block_excl_scan_nb(uint32_t v, uint32_t *sh, uint32_t *total)
+{
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    uint32_t inc = warp_incl_scan(v);
+    if (lane == 31) sh[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t w = lane < nw ? sh[lane] : 0;
+        uint32_t wi = warp_incl_scan(w);
+        if (lane < nw) sh[lane] = wi - w;
+        if (lane == nw - 1) sh[nw] = wi;
+    }
+    __syncthreads();
+    *total = sh[nw];
+    return sh[warp] + inc - v;
+}
+
 __device__ __forceinline__ unsigned long long block_excl_scan64(unsigned long long v,
                                                                 unsigned long long *sh,
                                                                 unsigned long long *total)
@@ -268,6 +287,8 @@ struct QuantArgs {
     uint16_t *codes;
     int2 *dscr;      // {residual, is exception} of every code-0 point, by point
     uint32_t *hist;  // 2R bins, zeroed by the caller
+    uint32_t *unit_exc;   // exceptions per encoder unit (zeroed by the caller)
+    uint32_t unit_shift;  // log2 of the encoder unit in points
     Control *ctl;
     int num_sms;
 };
@@ -328,6 +349,7 @@ struct EncodeArgs {
     uint8_t *archive;
     uint64_t capacity;
     uint32_t *lane_bits;    // bits of every lane (S symbols) of every round
+    const uint32_t *unit_exc;  // exceptions per unit, counted by the dual-quant kernels
     ulonglong2 *unit_tot;   // per unit: {words, outliers | exceptions << 32}
     ulonglong2 *unit_off;   // their exclusive prefix sums
     ulonglong2 *scan_part;  // scan scratch
@@ -341,6 +363,7 @@ struct EncodeArgs {
 // phase 0: count, 1: scan of the unit totals, 2: pack; returns kernels launched
 int launch_encode(const EncodeArgs &a, cudaStream_t st, int phase);
 uint64_t encode_units(uint64_t n, uint32_t chunk);        // units (per-unit totals) of the encoder
+uint32_t encode_unit_shift(uint32_t chunk);                // log2 of the encoder unit in points
 
 struct DecodeArgs {
     const uint8_t *archive;

@@ -102,7 +102,7 @@ struct StageRec {
 struct Slot {
     Control *ctl = nullptr;
     // per-field scratch (grown on demand)
-    Buf codes, dscr, unit_tot, unit_off, unit_part, lane_bits, chunk_off, faces, scan_part;
+    Buf codes, dscr, unit_tot, unit_off, unit_part, unit_exc, lane_bits, chunk_off, faces, scan_part;
     // fixed-size scratch
     Buf hist, cw64, cw32, codes_only, keyA, keyB, nodef, parent, distA, distB, parA, parB;
     Buf lut, lutf, first, count, start, sorted;
@@ -130,7 +130,7 @@ struct Slot {
     }
     void release()
     {
-        for (Buf *b : {&codes, &dscr, &unit_tot, &unit_off, &unit_part, &lane_bits, &chunk_off, &faces, &scan_part,
+        for (Buf *b : {&codes, &dscr, &unit_tot, &unit_off, &unit_part, &unit_exc, &lane_bits, &chunk_off, &faces, &scan_part,
                        &hist, &cw64,
                        &cw32, &codes_only, &keyA, &keyB, &nodef, &parent, &distA, &distB, &parA, &parB, &lut, &lutf,
                        &first, &count, &start, &sorted})
@@ -354,10 +354,12 @@ gbsz_status enqueue_compress(gbsz_ctx *c, Slot *s, const float *d_field, const g
     const uint64_t nunits = encode_units(n, p.chunk);
     if (!s->codes.ensure(n * 2 + 64) || !s->dscr.ensure(n * 8 + 64) || !s->unit_tot.ensure(nunits * 16) ||
         !s->lane_bits.ensure((n / 64 + 64) * 4) ||
-        !s->unit_off.ensure(nunits * 16) || !s->unit_part.ensure(scan_partials(nunits) * 16 + 64))
+        !s->unit_off.ensure(nunits * 16) || !s->unit_part.ensure(scan_partials(nunits) * 16 + 64) ||
+        !s->unit_exc.ensure(nunits * 4))
         return GBSZ_ERR_OOM;
     cudaMemsetAsync(s->ctl, 0, sizeof(Control), st);
     cudaMemsetAsync(s->hist.p, 0, nbins * 4, st);
+    cudaMemsetAsync(s->unit_exc.p, 0, nunits * 4, st);
 
     cudaEvent_t e0;
     stage_begin(c, st, &e0);
@@ -372,6 +374,8 @@ gbsz_status enqueue_compress(gbsz_ctx *c, Slot *s, const float *d_field, const g
     q.codes = s->codes.as<uint16_t>();
     q.dscr = s->dscr.as<int2>();
     q.hist = s->hist.as<uint32_t>();
+    q.unit_exc = s->unit_exc.as<uint32_t>();
+    q.unit_shift = encode_unit_shift(p.chunk);
     q.ctl = s->ctl;
     q.num_sms = c->num_sms;
     stage_begin(c, st, &e0);
@@ -399,6 +403,7 @@ gbsz_status enqueue_compress(gbsz_ctx *c, Slot *s, const float *d_field, const g
     en.archive = static_cast<uint8_t *>(d_archive);
     en.capacity = capacity;
     en.lane_bits = s->lane_bits.as<uint32_t>();
+    en.unit_exc = s->unit_exc.as<uint32_t>();
     en.unit_tot = s->unit_tot.as<ulonglong2>();
     en.unit_off = s->unit_off.as<ulonglong2>();
     en.scan_part = s->unit_part.as<ulonglong2>();
@@ -437,7 +442,7 @@ gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void
     cb.nbins = 2 * h.p.radius;
     cb.expect_maxlen = h.maxlen;
     cb.fast_bits = fast_lut_bits(h.maxlen, cb.nbins);
-    cb.fast_pair = cb.fast_bits && cb.fast_bits <= kPairLutMax ? 1u : 0u;
+    cb.fast_pair = 0;  // the decoder builds its own first level from the complete table
     cudaEvent_t e0;
     stage_begin(c, st, &e0);
     launch_decode_tables(cb, st);

@@ -269,109 +269,125 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeArgs a, uint32_t s
     if (zeros) atomicAdd(&a.ctl->zeros, (unsigned long long)zeros);
 }
 
-// One code from the 16-bit complete table: no long-code path, no branch.  A
-// pattern that matches no code has entry 0 (length 0); the smallest length
-// seen is checked after the chunk.
-__device__ __forceinline__ uint32_t decode_single(Window &w, const Ring<kRingFast> &rg, const uint16_t *lut,
-                                                  uint32_t shift, uint32_t &minlen)
+// Two-level decode for archives whose codes all fit the complete table
+// (at most kFastLutMax bits).  Level 1 resolves every code of at most 8 bits
+// from the window's top byte; it is replicated once per lane with lane l's
+// copy in bank l (entry i of lane l at word 32 i + l), so the 32 lookups of a
+// warp never conflict.  Longer codes take the complete table (16-bit
+// entries (sym << 4) | len over B = maxlen bits) under a warp-uniform branch.
+// A pattern that matches no code has length 0; the smallest length seen is
+// checked after the chunk.
+constexpr uint32_t kL1Bits = 8;
+
+// complete-table entry from global memory (read-only path; the rarely used
+// part of the table stays in L1)
+__device__ __forceinline__ uint32_t ld_ft_pred(bool p, const uint16_t *addr, uint32_t keep)
 {
-    const uint32_t nxt = rg.at(w.v + 4);
-    const uint32_t cur = __funnelshift_l(w.lo, w.hi, w.bo);
-    const uint32_t e = lut[cur >> shift];
-    const uint32_t len = e & 15u;
-    minlen = min(minlen, len);
-    step(w, nxt, len);
-    return e >> 4;
+    uint32_t v = keep;
+    asm volatile(
+        "{\n\t.reg .pred q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "@q ld.global.nc.u16 %0, [%2];\n\t}"
+        : "+r"(v)
+        : "r"((uint32_t)p), "l"(addr));
+    return v;
 }
 
-// Two codes from the pair table: the entry of the first B bits gives the
-// first code and, when it fits in those B bits, the second; otherwise the
-// second comes from a lookup of the B bits after the first code (a
-// predicated load, so lanes that need none leave the banks alone).
-__device__ __forceinline__ void decode_pair(Window &w, const Ring<kRingFast> &rg, const uint32_t *lut,
-                                            uint32_t shift, uint32_t &minlen, uint32_t &s1, uint32_t &s2)
+// Two codes per step.  The level-1 entry of the window's top byte holds the
+// first code and, when it fits in the same byte, the second:
+// len1 | len2 << 4 | sym1 << 8 | sym2 << 20 (len1 = 0: the first code is
+// longer than 8 bits; len2 = 0: the second is not in the byte).  Missing
+// codes come from a second level-1 lookup after the first code and, for codes
+// longer than 8 bits, from the complete table in global memory; each of these
+// runs only when some lane of the warp needs it.  act1 / act2 = false (lanes past the end
+// of a short chunk, kept in step for the warp votes): that code consumes no
+// bits and its length is not checked.
+__device__ __forceinline__ uint32_t ld_shared_pred32(bool p, const void *addr, uint32_t keep)
+{
+    uint32_t v = keep;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(addr);
+    asm volatile(
+        "{\n\t.reg .pred q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "@q ld.shared.u32 %0, [%2];\n\t}"
+        : "+r"(v)
+        : "r"((uint32_t)p), "r"(a));
+    return v;
+}
+
+__device__ __forceinline__ void decode_two(Window &w, const Ring<kRingFast> &rg, const uint32_t *l1,
+                                           const uint16_t *ft, uint32_t shift, uint32_t &minlen, bool act1,
+                                           bool act2, uint32_t &s1, uint32_t &s2)
 {
     const uint32_t nxt = rg.at(w.v + 4);
     const uint32_t c0 = __funnelshift_l(w.lo, w.hi, w.bo);
     const uint32_t c1 = __funnelshift_l(w.q0, w.lo, w.bo);
-    const uint32_t e = lut[c0 >> shift];
-    const uint32_t l1 = e & 15u;
-    const uint32_t cur2 = __funnelshift_l(c1, c0, l1);  // the 32 bits after the first code (l1 < 16)
-    uint32_t e2 = e >> 4;                                // len2 | sym1 << 4 | sym2 << 16 as a fallback shape
-    const uint32_t saddr = (uint32_t)__cvta_generic_to_shared(lut) + ((cur2 >> shift) << 2);
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "setp.eq.u32 p, %1, 0;\n\t"
-        "@p ld.shared.u32 %0, [%2];\n\t}"
-        : "+r"(e2)
-        : "r"((e >> 4) & 15u), "r"(saddr));
-    // e2 is either the original entry shifted right by 4 (second code
-    // present: its length in bits 0-3, symbol in bits 16-27) or a fresh
-    // entry (first code of the later lookup: length bits 0-3, symbol 8-19)
-    const bool second_inline = ((e >> 4) & 15u) != 0;
-    const uint32_t l2 = e2 & 15u;
+    uint32_t e = l1[(c0 >> (32 - kL1Bits)) * 32];
+    uint32_t l1n = e & 15u, l2n = (e >> 4) & 15u;
     s1 = (e >> 8) & 0xFFFu;
-    s2 = second_inline ? (e2 >> 16) : ((e2 >> 8) & 0xFFFu);
-    minlen = min(minlen, min(l1, l2));
-    step(w, nxt, l1 + l2);
+    s2 = e >> 20;
+    const bool long1 = l1n == 0;
+    if (__any_sync(0xffffffffu, long1)) {
+        const uint32_t f = ld_ft_pred(long1, ft + (c0 >> shift), 0u);
+        if (long1) {
+            l1n = f & 15u;
+            s1 = f >> 4;
+            l2n = 0;
+        }
+    }
+    const bool need2 = l2n == 0;
+    if (__any_sync(0xffffffffu, need2)) {
+        const uint32_t cur2 = __funnelshift_l(c1, c0, l1n);  // the bits after the first code (l1n < 16)
+        const uint32_t e2 = ld_shared_pred32(need2, l1 + (cur2 >> (32 - kL1Bits)) * 32, 0u);
+        uint32_t l2b = e2 & 15u, s2b = (e2 >> 8) & 0xFFFu;
+        const bool long2 = need2 && l2b == 0;
+        if (__any_sync(0xffffffffu, long2)) {
+            const uint32_t f = ld_ft_pred(long2, ft + (cur2 >> shift), 0u);
+            if (long2) {
+                l2b = f & 15u;
+                s2b = f >> 4;
+            }
+        }
+        if (need2) {
+            l2n = l2b;
+            s2 = s2b;
+        }
+    }
+    l1n = act1 ? l1n : 0u;
+    l2n = act2 ? l2n : 0u;
+    minlen = min(minlen, min(act1 ? l1n : 15u, act2 ? l2n : 15u));
+    step(w, nxt, l1n + l2n);
 }
 
-// Persistent decoder for archives whose codes all fit the complete table
-// (at most kFastLutMax bits): each thread decodes chunks c, c + grid, ...
-template <bool MULTI_TILE, bool PAIR>
-__global__ void __launch_bounds__(kDecFastThreads, 2) k_decode_fast(DecodeArgs a)
+// single code (the odd last symbol of a chunk)
+__device__ __forceinline__ uint32_t decode_two_level(Window &w, const Ring<kRingFast> &rg, const uint32_t *l1,
+                                                     const uint16_t *ft, uint32_t shift, uint32_t &minlen,
+                                                     bool active)
 {
-    extern __shared__ uint32_t s_dyn[];  // rings, then the table
-    uint32_t *tab = s_dyn + kDecFastThreads * kRingFast;
-    const uint32_t B = a.fast_bits, shift = 32 - B;
-    const uint32_t tab_words = PAIR ? (1u << B) : ((1u << B) + 1) / 2;
-    for (uint32_t i = threadIdx.x; i < tab_words; i += blockDim.x) tab[i] = static_cast<const uint32_t *>(a.lutf)[i];
-    __syncthreads();
-    if (a.ctl->error & DERR_CORRUPT) return;
-    const uint32_t *stream = reinterpret_cast<const uint32_t *>(a.archive + a.off_stream);
-    const uint32_t *bits_tab = reinterpret_cast<const uint32_t *>(a.archive + a.off_bits);
+    uint32_t s1, s2;
+    decode_two(w, rg, l1, ft, shift, minlen, active, false, s1, s2);
+    return s1;
+}
+
+// One chunk of cnt symbols; the warp runs kend >= cnt symbol steps (GUARD:
+// some lane's chunk is shorter than the warp's longest).
+template <bool MULTI_TILE, bool GUARD>
+__device__ __forceinline__ void decode_chunk(const DecodeArgs &a, Ring<kRingFast> &rg, Window &w, const uint32_t *l1,
+                                             const uint16_t *ft, uint32_t shift, uint64_t s0, uint32_t cnt,
+                                             uint32_t kend, unsigned long long &zeros, uint32_t &minlen)
+{
     const uint32_t R = a.radius;
-    uint32_t *warp_ring = s_dyn + (threadIdx.x >> 5) * kRingFast * 32;
-    const uint32_t lane = threadIdx.x & 31;
-    unsigned long long zeros = 0;
-    bool bad = false;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-    uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    uint32_t nbits = 0;
-    uint64_t coff = 0;
-    if (c < a.nchunk) {
-        nbits = bits_tab[c];
-        coff = a.chunk_off[c];
-    }
-    for (; c < a.nchunk; c += stride) {
-        // the next chunk's bit count and offset are fetched while this one decodes
-        const uint64_t cn = c + stride;
-        uint32_t nbits_n = 0;
-        uint64_t coff_n = 0;
-        if (cn < a.nchunk) {
-            nbits_n = bits_tab[cn];
-            coff_n = a.chunk_off[cn];
-        }
-        const uint64_t s0 = c * a.chunk;
-        const uint32_t cnt = (uint32_t)(a.n - s0 < a.chunk ? a.n - s0 : a.chunk);
-        Ring<kRingFast> rg;
-        rg.start(warp_ring, lane, stream + coff, coff < a.words ? a.words - coff : 0);
-        Window w{0, 0, rg.at(0), rg.at(1), rg.at(2), rg.at(3)};
-        uint32_t ssum = 0, tz = 0, tstart = 0, minlen = 15;
-        uint16_t *out = a.codes + s0;
-        const uint32_t full = cnt & ~(kBatch - 1);
-        for (uint32_t k = 0; k < full; k += kBatch) {
-            rg.refill(w.v);
-            uint32_t sy[kBatch];
-            if (PAIR) {
+    uint32_t ssum = 0, tz = 0, tstart = 0;
+    uint16_t *out = a.codes + s0;
+    const uint32_t full = kend & ~(kBatch - 1);
+    for (uint32_t k = 0; k < full; k += kBatch) {
+        rg.refill(w.v);
+        uint32_t sy[kBatch];
 #pragma unroll
-                for (int j = 0; j < (int)kBatch; j += 2)
-                    decode_pair(w, rg, tab, shift, minlen, sy[j], sy[j + 1]);
-            } else {
-#pragma unroll
-                for (int j = 0; j < (int)kBatch; j++)
-                    sy[j] = decode_single(w, rg, reinterpret_cast<const uint16_t *>(tab), shift, minlen);
-            }
+        for (int j = 0; j < (int)kBatch; j += 2)
+            decode_two(w, rg, l1, ft, shift, minlen, !GUARD || k + j < cnt, !GUARD || k + j + 1 < cnt, sy[j],
+                       sy[j + 1]);
+        if (!GUARD || k + kBatch <= cnt) {
             const uint4 o = make_uint4(sy[0] | (sy[1] << 16), sy[2] | (sy[3] << 16), sy[4] | (sy[5] << 16),
                                        sy[6] | (sy[7] << 16));
             // symbols are below 4096 here, so the halves of the word sum cannot carry
@@ -379,45 +395,104 @@ __global__ void __launch_bounds__(kDecFastThreads, 2) k_decode_fast(DecodeArgs a
             ssum += (t4 & 0xFFFFu) + (t4 >> 16);
             *reinterpret_cast<uint4 *>(out + k) = o;
             tz += zeros_in(o.x) + zeros_in(o.y) + zeros_in(o.z) + zeros_in(o.w);
-            if (MULTI_TILE && a.tile_sums && ((s0 + k + kBatch) & (kRecon1DTile - 1)) == 0) {
-                // residual sum of the tile's in-cap codes: sum(code) - R * (#nonzero), mod 2^32
-                const uint32_t m = k + kBatch - tstart;
-                atomicAdd(&a.tile_sums[(s0 + k) / kRecon1DTile], ssum - R * (m - tz));
-                zeros += tz;
-                ssum = tz = 0;
-                tstart = k + kBatch;
-            }
-        }
-        if (full < cnt) {
-            rg.refill(w.v);
-            for (uint32_t k = full; k < cnt; k++) {
-                const uint32_t sym =
-                    PAIR ? 0u : decode_single(w, rg, reinterpret_cast<const uint16_t *>(tab), shift, minlen);
-                uint32_t s = sym;
-                if (PAIR) {
-                    // one code: the first half of a pair entry
-                    const uint32_t nxt = rg.at(w.v + 4);
-                    const uint32_t cur = __funnelshift_l(w.lo, w.hi, w.bo);
-                    const uint32_t e = tab[cur >> shift];
-                    const uint32_t l1 = e & 15u;
-                    minlen = min(minlen, l1);
-                    step(w, nxt, l1);
-                    s = (e >> 8) & 0xFFFu;
+        } else {
+#pragma unroll
+            for (int j = 0; j < (int)kBatch; j++) {
+                if (k + j < cnt) {
+                    ssum += sy[j];
+                    tz += sy[j] == 0;
+                    out[k + j] = (uint16_t)sy[j];
                 }
-                ssum += s;
-                tz += s == 0;
-                out[k] = (uint16_t)s;
             }
         }
-        zeros += tz;
-        if (a.tile_sums && cnt > tstart) {
-            const uint32_t tsum = ssum - R * (cnt - tstart - tz);
-            if (tsum) atomicAdd(&a.tile_sums[(s0 + cnt - 1) / kRecon1DTile], tsum);
+        if (MULTI_TILE && a.tile_sums && (!GUARD || k + kBatch <= cnt) &&
+            ((s0 + k + kBatch) & (kRecon1DTile - 1)) == 0) {
+            // residual sum of the tile's in-cap codes: sum(code) - R * (#nonzero), mod 2^32
+            const uint32_t m = k + kBatch - tstart;
+            atomicAdd(&a.tile_sums[(s0 + k) / kRecon1DTile], ssum - R * (m - tz));
+            zeros += tz;
+            ssum = tz = 0;
+            tstart = k + kBatch;
+        }
+    }
+    if (full < kend) {
+        rg.refill(w.v);
+        for (uint32_t k = full; k < kend; k++) {
+            const uint32_t sym = decode_two_level(w, rg, l1, ft, shift, minlen, !GUARD || k < cnt);
+            if (!GUARD || k < cnt) {
+                ssum += sym;
+                tz += sym == 0;
+                out[k] = (uint16_t)sym;
+            }
+        }
+    }
+    zeros += tz;
+    if (a.tile_sums && cnt > tstart) {
+        const uint32_t tsum = ssum - R * (cnt - tstart - tz);
+        if (tsum) atomicAdd(&a.tile_sums[(s0 + cnt - 1) / kRecon1DTile], tsum);
+    }
+}
+
+template <bool MULTI_TILE>
+__global__ void __launch_bounds__(kDecFastThreads, 2) k_decode_fast(DecodeArgs a)
+{
+    extern __shared__ uint32_t s_dyn[];  // rings, level-1 table (lane-replicated)
+    uint32_t *l1tab = s_dyn + kDecFastThreads * kRingFast;
+    const uint32_t B = a.fast_bits, shift = 32 - B;
+    const uint16_t *gft = static_cast<const uint16_t *>(a.lutf);
+    const uint16_t *ft = gft;
+    // level 1 from the complete table: the code at the start of each byte if
+    // it has at most 8 bits, and the code after it if that fits in the byte
+    auto ft_at = [&](uint32_t byte) -> uint32_t {  // complete-table entry of an 8-bit prefix
+        return B >= kL1Bits ? gft[byte << (B - kL1Bits)] : gft[byte >> (kL1Bits - B)];
+    };
+    for (uint32_t k = threadIdx.x; k < (32u << kL1Bits); k += blockDim.x) {
+        const uint32_t i = k >> 5;
+        const uint32_t f = ft_at(i);
+        const uint32_t la = f & 15u;
+        uint32_t e = 0;
+        if (la >= 1 && la <= kL1Bits) {
+            e = la | ((f >> 4) << 8);
+            if (la < kL1Bits) {
+                const uint32_t g2 = ft_at((i << la) & 0xFFu);
+                const uint32_t lb = g2 & 15u;
+                if (lb >= 1 && lb <= kL1Bits - la) e |= (lb << 4) | ((g2 >> 4) << 20);
+            }
+        }
+        l1tab[k] = e;
+    }
+    __syncthreads();
+    if (a.ctl->error & DERR_CORRUPT) return;
+    const uint32_t *stream = reinterpret_cast<const uint32_t *>(a.archive + a.off_stream);
+    const uint32_t *bits_tab = reinterpret_cast<const uint32_t *>(a.archive + a.off_bits);
+    uint32_t *warp_ring = s_dyn + (threadIdx.x >> 5) * kRingFast * 32;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint32_t *l1 = l1tab + lane;
+    unsigned long long zeros = 0;
+    bool bad = false;
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    // whole warps iterate together (the level-1 fallback votes across the
+    // warp); lanes past the last chunk decode nothing
+    for (uint64_t cw = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; cw < a.nchunk; cw += stride) {
+        const uint64_t c = cw + lane;
+        const bool live = c < a.nchunk;
+        const uint32_t nbits = live ? bits_tab[c] : 0u;
+        const uint64_t coff = live ? a.chunk_off[c] : 0u;
+        const uint64_t s0 = live ? c * a.chunk : 0u;
+        const uint32_t cnt = live ? (uint32_t)(a.n - s0 < a.chunk ? a.n - s0 : a.chunk) : 0u;
+        Ring<kRingFast> rg;
+        rg.start(warp_ring, lane, stream + coff, coff < a.words ? a.words - coff : 0);
+        Window w{0, 0, rg.at(0), rg.at(1), rg.at(2), rg.at(3)};
+        uint32_t minlen = 15;
+        if (__all_sync(0xffffffffu, cnt == a.chunk)) {
+            decode_chunk<MULTI_TILE, false>(a, rg, w, l1, ft, shift, s0, cnt, cnt, zeros, minlen);
+        } else {
+            const uint32_t cmax = __reduce_max_sync(0xffffffffu, cnt);
+            decode_chunk<MULTI_TILE, true>(a, rg, w, l1, ft, shift, s0, cnt, cmax, zeros, minlen);
         }
         cp_async_wait<0>();  // the ring is reused by the next chunk
-        bad |= minlen == 0 || (uint64_t)w.v * 32 + w.bo != nbits;
-        nbits = nbits_n;
-        coff = coff_n;
+        if (live) bad |= minlen == 0 || (uint64_t)w.v * 32 + w.bo != nbits;
+        __syncwarp();
     }
     if (bad) atomicOr(&a.ctl->error, DERR_CORRUPT);
     if (zeros) atomicAdd(&a.ctl->zeros, zeros);
@@ -446,26 +521,19 @@ int launch_decode(const DecodeArgs &a, cudaStream_t st, int phase)
         const int most = (int)(kDecThreads * kRing * 4 + kSortedSmemMax * sizeof(uint16_t));
         cudaFuncSetAttribute(k_decode<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         cudaFuncSetAttribute(k_decode<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-        const int most_fast = (int)(kDecFastThreads * kRingFast * 4 + kFastLutBytes);
-        cudaFuncSetAttribute(k_decode_fast<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
-        cudaFuncSetAttribute(k_decode_fast<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
-        cudaFuncSetAttribute(k_decode_fast<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
-        cudaFuncSetAttribute(k_decode_fast<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
+        const int most_fast = (int)(kDecFastThreads * kRingFast * 4 + (4u << (5 + kL1Bits)));
+        cudaFuncSetAttribute(k_decode_fast<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
+        cudaFuncSetAttribute(k_decode_fast<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
         attr_done |= bit;
     }
     const bool multi = a.chunk > kRecon1DTile;
     if (a.fast_bits) {
-        const size_t tab = a.fast_pair ? (4u << a.fast_bits) : (((2u << a.fast_bits) + 3) & ~3u);
-        const size_t dyn_fast = (size_t)kDecFastThreads * kRingFast * 4 + tab;
+        const size_t dyn_fast = (size_t)kDecFastThreads * kRingFast * 4 + (4u << (5 + kL1Bits));
         const uint64_t want = (a.nchunk + kDecFastThreads - 1) / kDecFastThreads;
-        const unsigned g = (unsigned)std::min<uint64_t>(want, (uint64_t)(a.num_sms ? a.num_sms : 1) * 2);
-        if (a.fast_pair) {
-            if (multi) k_decode_fast<true, true><<<g, kDecFastThreads, dyn_fast, st>>>(a);
-            else k_decode_fast<false, true><<<g, kDecFastThreads, dyn_fast, st>>>(a);
-        } else {
-            if (multi) k_decode_fast<true, false><<<g, kDecFastThreads, dyn_fast, st>>>(a);
-            else k_decode_fast<false, false><<<g, kDecFastThreads, dyn_fast, st>>>(a);
-        }
+        const int per_sm = 2;
+        const unsigned g = (unsigned)std::min<uint64_t>(want, (uint64_t)(a.num_sms ? a.num_sms : 1) * per_sm);
+        if (multi) k_decode_fast<true><<<g, kDecFastThreads, dyn_fast, st>>>(a);
+        else k_decode_fast<false><<<g, kDecFastThreads, dyn_fast, st>>>(a);
     } else if (multi) {
         k_decode<true><<<(unsigned)grid, kDecThreads, dyn, st>>>(a, in_smem);
     } else {

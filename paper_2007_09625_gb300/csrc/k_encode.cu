@@ -10,7 +10,8 @@
 //             4096 symbols;
 //   count     code lengths -> bits per lane -> chunk bits (segmented warp
 //             sums, written to the archive's chunk table) -> the unit's
-//             words, outliers and exceptions;
+//             words and outliers (its exceptions were counted by the
+//             dual-quant kernels);
 //   scan      exclusive prefix sums of the unit totals give every unit's
 //             global word / outlier / exception offsets;
 //   pack      each lane packs its codewords MSB-first into 32-bit words and
@@ -171,7 +172,8 @@ struct UnitGeom {
 // counts.  Codes are read with coalesced 16-byte loads, four in flight per
 // lane (lane l holds symbols 256k + 8l .. +7 of step k).  A "count entry" per
 // symbol packs its code length (bits 0-15) with a code-0 flag (bit 16), so one
-// add per symbol accumulates both; exceptions add 1 << 24.  Each lane parks
+// add per symbol accumulates both; a unit's exceptions were counted by the
+// dual-quant kernels, so no residual is read here.  Each lane parks
 // the packed sum of its 8 symbols in a padded per-warp shared array, and lane
 // l then sums the S / 8 partials of its S-symbol segment (the segment lane l
 // packs in phase 3).
@@ -190,7 +192,7 @@ struct CountGlobal {
 
 constexpr uint32_t kPartStride = 33;  // padded row of per-lane partials
 
-// one 128-bit read-only load
+// one 128-bit read-only load (codes do not change while the encoder runs)
 __device__ __forceinline__ uint4 ldg_nc16(const void *p)
 {
     uint4 v;
@@ -200,38 +202,30 @@ __device__ __forceinline__ uint4 ldg_nc16(const void *p)
     return v;
 }
 
-// ANY_EXC is a template argument so that fields without exceptions carry no
-// (predicated) residual loads at all
-template <bool ANY_EXC, typename CT>
-__device__ __forceinline__ uint32_t count8(const EncodeArgs &a, const CT &ct, uint4 w, uint64_t p)
+__device__ __forceinline__ uint32_t count8(const CountSmem &ct, uint4 w)
+{
+    return ct(w.x & 0xFFFFu) + ct(w.x >> 16) + ct(w.y & 0xFFFFu) + ct(w.y >> 16) + ct(w.z & 0xFFFFu) +
+           ct(w.z >> 16) + ct(w.w & 0xFFFFu) + ct(w.w >> 16);
+}
+template <typename CT>
+__device__ __forceinline__ uint32_t count8(const CT &ct, uint4 w)
 {
     const uint32_t v[4] = {w.x, w.y, w.z, w.w};
     uint32_t s = 0;
 #pragma unroll
     for (int q = 0; q < 4; q++) s += ct(v[q] & 0xFFFFu) + ct(v[q] >> 16);
-    if (ANY_EXC && (s & 0xFF0000u)) {
-#pragma unroll
-        for (int q = 0; q < 8; q++) {
-            const uint32_t c = (v[q >> 1] >> ((q & 1) * 16)) & 0xFFFFu;
-            if (c == 0 && a.dscr[p + q].y != 0) s += 1u << 24;
-        }
-    }
     return s;
 }
 
-template <bool ANY_EXC, typename CT>
+template <typename CT>
 __device__ __forceinline__ uint32_t count_tail(const EncodeArgs &a, const CT &ct, uint64_t p, uint64_t n)
 {
     uint32_t s = 0;
-    for (uint32_t q = 0; q < 8 && p + q < n; q++) {
-        const uint32_t c = a.codes[p + q];
-        s += ct(c);
-        if (ANY_EXC && c == 0 && a.dscr[p + q].y != 0) s += 1u << 24;
-    }
+    for (uint32_t q = 0; q < 8 && p + q < n; q++) s += ct(a.codes[p + q]);
     return s;
 }
 
-template <bool ANY_EXC, typename CT>
+template <typename CT>
 __device__ __forceinline__ void count_units(const EncodeArgs &a, uint64_t nunits, const CT &ct, uint32_t *part)
 {
     const uint32_t lane = threadIdx.x & 31;
@@ -240,7 +234,7 @@ __device__ __forceinline__ void count_units(const EncodeArgs &a, uint64_t nunits
     const UnitGeom ug(C);
     const uint32_t S = ug.S, per = S / 8;  // partials per segment
     const uint32_t segs = 32 / per;        // segments per 256-symbol step
-    const uint32_t steps = S / 8;          // 256-symbol steps per round, a multiple of 4
+    const uint32_t steps = S / 8;          // 256-symbol steps per round: 8 or 16
     const uint64_t nchunk = (n + C - 1) / C;
     const Layout L0 = make_layout(a.radius, nchunk, a.ctl->n_out, a.ctl->n_exc, 0);
     const bool first_of_chunk = (lane & (ug.G - 1)) == 0;
@@ -251,36 +245,36 @@ __device__ __forceinline__ void count_units(const EncodeArgs &a, uint64_t nunits
         const uint64_t ubase = u * ug.U;
         const uint64_t ulen = n - ubase < ug.U ? n - ubase : ug.U;
         const uint32_t rounds = ug.multi ? (uint32_t)((ulen + kRound - 1) / kRound) : 1u;
-        uint32_t unit_words = 0, unit_out = 0, unit_exc = 0;
+        uint32_t unit_words = 0, unit_out = 0;
         unsigned long long chunk_bits = 0;
         for (uint32_t r = 0; r < rounds; r++) {
             const uint64_t r0 = ubase + (uint64_t)r * 32 * S;
             const bool full = r0 + 32ull * S <= n;
             const uint4 *src = reinterpret_cast<const uint4 *>(a.codes + r0) + lane;
             __syncwarp();  // the previous round's partials have been read
-            for (uint32_t k = 0; k < steps; k += 4) {
-                uint32_t s4[4];
+            // eight 16-byte loads in flight per lane (steps is 8 or 16)
+            for (uint32_t k = 0; k < steps; k += 8) {
+                uint32_t s8[8];
                 if (full) {
-                    uint4 w[4];
+                    uint4 w[8];
 #pragma unroll
-                    for (int i = 0; i < 4; i++) w[i] = ldg_nc16(src + 32 * (k + i));
+                    for (int i = 0; i < 8; i++) w[i] = ldg_nc16(src + 32 * (k + i));
 #pragma unroll
-                    for (int i = 0; i < 4; i++) s4[i] = count8<ANY_EXC>(a, ct, w[i], r0 + 256ull * (k + i) + 8 * lane);
+                    for (int i = 0; i < 8; i++) s8[i] = count8(ct, w[i]);
                 } else {
 #pragma unroll
-                    for (int i = 0; i < 4; i++) {
+                    for (int i = 0; i < 8; i++) {
                         const uint64_t p = r0 + 256ull * (k + i) + 8ull * lane;
-                        s4[i] = p + 8 <= n ? count8<ANY_EXC>(a, ct, src[32 * (k + i)], p)
-                                           : count_tail<ANY_EXC>(a, ct, p, n);
+                        s8[i] = p + 8 <= n ? count8(ct, src[32 * (k + i)]) : count_tail(a, ct, p, n);
                     }
                 }
 #pragma unroll
-                for (int i = 0; i < 4; i++) part[(k + i) * kPartStride + lane] = s4[i];
+                for (int i = 0; i < 8; i++) part[(k + i) * kPartStride + lane] = s8[i];
             }
             __syncwarp();
             uint32_t seg = 0;
             for (uint32_t t = 0; t < per; t++) seg += myseg[t];
-            const uint32_t sb = seg & 0xFFFFu, so = (seg >> 16) & 0xFFu, se = seg >> 24;
+            const uint32_t sb = seg & 0xFFFFu, so = seg >> 16;
             const uint64_t s0 = r0 + (uint64_t)lane * S;
             const uint32_t cnt = s0 < n ? (uint32_t)(n - s0 < S ? n - s0 : S) : 0u;
             if (cnt) a.lane_bits[r0 / S + lane] = sb;
@@ -296,10 +290,9 @@ __device__ __forceinline__ void count_units(const EncodeArgs &a, uint64_t nunits
                 unit_words += warp_sum(cw);
             }
             unit_out += so;
-            unit_exc += se;
         }
         unit_out = warp_sum(unit_out);
-        unit_exc = warp_sum(unit_exc);
+        const uint32_t unit_exc = a.unit_exc[u];
         if (ug.multi) {
             unit_words = (uint32_t)((chunk_bits + 31) / 32);
             if (lane == 0) put_u32(a.archive + L0.bits + 4 * u, (uint32_t)chunk_bits);
@@ -338,7 +331,10 @@ __device__ __forceinline__ void append(unsigned long long &acc, uint32_t &nacc, 
 }
 
 // Phase 3: pack every unit at its offsets; the last unit writes the header.
-template <bool CW32>
+// PAIR (longest code at most 16 bits): two codewords are joined into one of
+// at most 32 bits before they enter the accumulator, so each pair needs one
+// shift-in and one full-word test.
+template <bool CW32, bool PAIR>
 __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW32> &tab, uint4 *slot)
 {
     const uint32_t lane = threadIdx.x & 31;
@@ -430,27 +426,42 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
                         if (j < 8) zlo |= (unsigned long long)z8 << (8 * j);
                         else zhi |= (unsigned long long)z8 << (8 * (j - 8));
                     }
+                    if (CW32 && PAIR) {
 #pragma unroll
-                    for (int k = 0; k < 8; k++) {
-                        const uint32_t c = (v[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
-                        if (CW32) {
-                            const uint32_t e = tab.raw32(c);
-                            const uint32_t len = e >> 24;
-                            acc = (acc << len) | (e & 0xFFFFFFu);
+                        for (int k = 0; k < 4; k++) {
+                            const uint32_t e0 = tab.raw32(v[k] & 0xFFFFu), e1 = tab.raw32(v[k] >> 16);
+                            const uint32_t l1 = e1 >> 24;
+                            const uint32_t len = (e0 >> 24) + l1;
+                            acc = (acc << len) | (((e0 & 0xFFFFFFu) << l1) | (e1 & 0xFFFFFFu));
                             nacc += len;
                             const bool full_w = nacc >= 32;
                             nacc -= full_w ? 32u : 0u;
                             if (full_w && ok) lout[nw32] = (uint32_t)(acc >> nacc);
                             nw32 += full_w ? 1u : 0u;
-                        } else {
-                            uint32_t len;
-                            unsigned long long code;
-                            tab.get(c, len, code);
-                            uint32_t w[2], nw;
-                            append<CW32>(acc, nacc, code, len, w, nw);
-                            for (uint32_t q = 0; q < nw; q++) {
-                                if (ok) lout[nw32] = w[q];
-                                nw32++;
+                        }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 8; k++) {
+                            const uint32_t c = (v[k >> 1] >> ((k & 1) * 16)) & 0xFFFFu;
+                            if (CW32) {
+                                const uint32_t e = tab.raw32(c);
+                                const uint32_t len = e >> 24;
+                                acc = (acc << len) | (e & 0xFFFFFFu);
+                                nacc += len;
+                                const bool full_w = nacc >= 32;
+                                nacc -= full_w ? 32u : 0u;
+                                if (full_w && ok) lout[nw32] = (uint32_t)(acc >> nacc);
+                                nw32 += full_w ? 1u : 0u;
+                            } else {
+                                uint32_t len;
+                                unsigned long long code;
+                                tab.get(c, len, code);
+                                uint32_t w[2], nw;
+                                append<CW32>(acc, nacc, code, len, w, nw);
+                                for (uint32_t q = 0; q < nw; q++) {
+                                    if (ok) lout[nw32] = w[q];
+                                    nw32++;
+                                }
                             }
                         }
                     }
@@ -552,13 +563,12 @@ __device__ __forceinline__ const void *load_table(const EncodeArgs &a, uint32_t 
 constexpr uint32_t kCountSmemBins = 8192;
 constexpr uint32_t kPartWords = 16 * kPartStride;  // per warp, S <= 128
 
-template <bool ANY_EXC>
 __device__ __forceinline__ void count_dispatch(const EncodeArgs &a, uint64_t nunits, uint32_t *part, uint32_t *tab,
                                                bool w32)
 {
-    if (a.nbins <= kCountSmemBins) count_units<ANY_EXC>(a, nunits, CountSmem{tab}, part);
-    else if (w32) count_units<ANY_EXC>(a, nunits, CountGlobal<true>{Table<true>{a.cw32}}, part);
-    else count_units<ANY_EXC>(a, nunits, CountGlobal<false>{Table<false>{a.cw64}}, part);
+    if (a.nbins <= kCountSmemBins) count_units(a, nunits, CountSmem{tab}, part);
+    else if (w32) count_units(a, nunits, CountGlobal<true>{Table<true>{a.cw32}}, part);
+    else count_units(a, nunits, CountGlobal<false>{Table<false>{a.cw64}}, part);
 }
 
 __global__ void __launch_bounds__(kEncThreads, 4) k_encode_count(EncodeArgs a, uint64_t nunits)
@@ -575,8 +585,7 @@ __global__ void __launch_bounds__(kEncThreads, 4) k_encode_count(EncodeArgs a, u
         }
         __syncthreads();
     }
-    if (a.ctl->n_exc != 0) count_dispatch<true>(a, nunits, part, tab, w32);
-    else count_dispatch<false>(a, nunits, part, tab, w32);
+    count_dispatch(a, nunits, part, tab, w32);
 }
 
 __global__ void __launch_bounds__(kEncThreads, 3) k_encode_pack(EncodeArgs a, uint64_t nunits, uint32_t use_smem)
@@ -588,13 +597,15 @@ __global__ void __launch_bounds__(kEncThreads, 3) k_encode_pack(EncodeArgs a, ui
     const bool w32 = a.ctl->maxlen <= 24;
     // each call sees where its table lives, so shared-memory tables are read
     // with shared loads
+    const bool pair = a.ctl->maxlen <= 16;
     if (use_smem) {
         load_table(a, 1, s_tab, w32);
-        if (w32) pack_units<true>(a, nunits, Table<true>{s_tab}, slot);
-        else pack_units<false>(a, nunits, Table<false>{s_tab}, slot);
+        if (pair) pack_units<true, true>(a, nunits, Table<true>{s_tab}, slot);
+        else if (w32) pack_units<true, false>(a, nunits, Table<true>{s_tab}, slot);
+        else pack_units<false, false>(a, nunits, Table<false>{s_tab}, slot);
     } else {
-        if (w32) pack_units<true>(a, nunits, Table<true>{a.cw32}, slot);
-        else pack_units<false>(a, nunits, Table<false>{a.cw64}, slot);
+        if (w32) pack_units<true, false>(a, nunits, Table<true>{a.cw32}, slot);
+        else pack_units<false, false>(a, nunits, Table<false>{a.cw64}, slot);
     }
 }
 
@@ -624,6 +635,15 @@ void set_encode_smem()
 }
 
 }  // namespace
+
+uint32_t encode_unit_shift(uint32_t chunk)
+{
+    const uint32_t S = chunk < kLaneMax ? chunk : kLaneMax;
+    const uint64_t U = chunk > kRound ? chunk : 32ull * S;
+    uint32_t sh = 0;
+    while ((1ull << sh) < U) sh++;
+    return sh;
+}
 
 uint64_t encode_units(uint64_t n, uint32_t chunk)
 {

@@ -216,6 +216,7 @@ __device__ __forceinline__ uint32_t emit_point(HistState &h, const QuantArgs &a,
         a.dscr[idx] = make_int2((int32_t)delta, exc ? 1 : 0);
         h.n_out++;
     }
+    if (exc) atomicAdd(&a.unit_exc[idx >> a.unit_shift], 1u);
     h.n_exc += exc;
     hist_add(h, code, a.hist);
     return code;
@@ -305,6 +306,7 @@ __global__ void __launch_bounds__(kQ1Threads) k_dualquant_1d(QuantArgs a, uint32
         uint32_t qprev = (e0 > 0 && e0 <= n) ? (uint32_t)prequant(vp, sc, dummy) : 0u;
         uint32_t code[kQ1Per];
         uint32_t pk = 0;
+        const uint32_t exc0 = h.n_exc;  // this run's exceptions go to its encoder unit below
         if (full) {
 #pragma unroll
             for (int j = 0; j < kQ1Per; j++) {
@@ -328,6 +330,8 @@ __global__ void __launch_bounds__(kQ1Threads) k_dualquant_1d(QuantArgs a, uint32
             }
         }
         unpack_central(h, pk);
+        // the 16 points of a run lie in one encoder unit (units are 2^k >= 2048 points)
+        if (h.n_exc != exc0) atomicAdd(&a.unit_exc[e0 >> a.unit_shift], h.n_exc - exc0);
     }
     if (WIN) h.n_out = 0;  // taken from bin 0 below
     hist_flush(h, a.hist, a.ctl, WIN);

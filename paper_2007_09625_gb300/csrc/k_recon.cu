@@ -179,14 +179,16 @@ __global__ void k_patch_exceptions(ReconArgs a, uint64_t n)
 // 1D tiles: 4096 points, 16 consecutive per thread, block scan of totals
 
 // One 4096-point tile per block iteration; warp w of the block covers the
-// tile's 512-point group w.  A warp's outliers are the run start[g] ..
-// start[g+1] of the index-ordered list; a warp scan of the lanes' code-0
-// counts gives each lane its first entry, and its code-0 points, in order,
-// take the next entries, whose indices must be theirs (and the counts must
-// match the run).  Residuals are code - R, or the outlier's residual for
-// code 0; their sum within the tile comes from a thread run and one block
-// scan; the tile's carry F[tile] completes the prefix.  The next tile's codes
-// and group bounds are loaded while this one is processed.
+// tile's 512-point group g.  A warp's outliers are the run start[g] ..
+// start[g+1] of the index-ordered list; the first 32 of them are loaded one
+// per lane, and a warp scan of the lanes' code-0 counts tells each lane which
+// entries its code-0 points take, in order (fetched by shuffles; runs longer
+// than 32 read the rest from global memory).  Every entry's index must be
+// its point's and the counts must match the run.  Residuals are code - R, or
+// the outlier's residual for code 0; their sum within the tile comes from a
+// thread run and one block scan; the tile's carry F[tile] completes the
+// prefix.  All loads of the next tile (codes, its outlier entries) and the
+// run bounds of the tile after it are issued before this tile is processed.
 __device__ __forceinline__ uint4 ldg_nc16(const void *p)
 {
     uint4 v;
@@ -198,7 +200,7 @@ __device__ __forceinline__ uint4 ldg_nc16(const void *p)
 
 __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, const uint32_t *F, const uint32_t *start)
 {
-    __shared__ uint32_t sh[33];
+    __shared__ uint32_t sh2[2][33];  // scan scratch, alternating between tiles
     __shared__ uint32_t s_od[k1Threads * 17];  // outlier residuals by (thread, point); stride 17 spreads banks
     if (a.ctl->error & DERR_CORRUPT) return;
     const uint64_t n = g.n[0];
@@ -207,25 +209,37 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
     const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const uint2 *ol = reinterpret_cast<const uint2 *>(a.archive + a.off_outl);
     uint32_t *od = s_od + threadIdx.x * 17;
+    constexpr uint32_t kGroups = k1Tile / kGroup1D;
     bool bad = false;
-    // loads of one tile: this thread's codes and its warp's group bounds
-    auto fetch = [&](uint64_t tile, uint4 &w0, uint4 &w1, uint32_t &ga, uint32_t &gb) {
+    auto bounds = [&](uint64_t tile, uint32_t &lo, uint32_t &hi) {
+        lo = hi = 0;
+        if (a.m && tile < g.ntiles) {
+            lo = start[tile * kGroups + warp];
+            hi = start[tile * kGroups + warp + 1];
+        }
+    };
+    auto codes = [&](uint64_t tile, uint4 &w0, uint4 &w1) {
         const uint64_t s0 = tile * k1Tile + (uint64_t)threadIdx.x * 16;
-        if (s0 + 16 <= n) {
+        if (tile < g.ntiles && s0 + 16 <= n) {
             w0 = ldg_nc16(a.codes + s0);
             w1 = ldg_nc16(a.codes + s0 + 8);
         }
-        ga = gb = 0;
-        if (a.m) {
-            const uint64_t gi = tile * (k1Tile / kGroup1D) + warp;
-            ga = start[gi];
-            gb = start[gi + 1];
-        }
     };
+    auto entry = [&](uint32_t lo, uint32_t hi) {
+        uint2 en = make_uint2(0xFFFFFFFFu, 0u);
+        if (lo + lane < hi) en = ol[lo + lane];
+        return en;
+    };
+    uint64_t tile = blockIdx.x;
     uint4 w0 = make_uint4(0, 0, 0, 0), w1 = w0;
-    uint32_t ga = 0, gb = 0;
-    if (blockIdx.x < g.ntiles) fetch(blockIdx.x, w0, w1, ga, gb);
-    for (uint64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+    uint32_t lo, hi, lo1, hi1;
+    bounds(tile, lo, hi);
+    bounds(tile + gridDim.x, lo1, hi1);
+    codes(tile, w0, w1);
+    uint2 en = entry(lo, hi);
+    uint32_t carry = tile < g.ntiles ? F[tile] : 0u;
+    uint32_t par = 0;
+    for (; tile < g.ntiles; tile += gridDim.x, par ^= 1) {
         const uint64_t s0 = tile * k1Tile + (uint64_t)threadIdx.x * 16;
         uint32_t c[16];
         if (s0 + 16 <= n) {
@@ -236,8 +250,17 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
 #pragma unroll
             for (int j = 0; j < 16; j++) c[j] = s0 + j < n ? a.codes[s0 + j] : R;  // past the end: residual 0
         }
-        const uint32_t lo = ga, hi = gb;
-        if (tile + gridDim.x < g.ntiles) fetch(tile + gridDim.x, w0, w1, ga, gb);
+        const uint32_t clo = lo, chi = hi, ccarry = carry;
+        const uint2 cen = en;
+        // next tile's loads
+        const uint64_t tn = tile + gridDim.x;
+        codes(tn, w0, w1);
+        en = entry(lo1, hi1);
+        lo = lo1;
+        hi = hi1;
+        bounds(tn + gridDim.x, lo1, hi1);
+        if (tn < g.ntiles) carry = F[tn];
+
         uint32_t d[16], zm = 0;
 #pragma unroll
         for (int j = 0; j < 16; j++) {
@@ -246,20 +269,21 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
         }
         const uint32_t zc = __popc(zm);
         const uint32_t zinc = warp_incl_scan(zc);
-        if (lane == 31 && (uint64_t)lo + zinc != hi) bad = true;  // a group holds exactly its outliers
-        uint64_t e = (uint64_t)lo + (zinc - zc);
-        for (uint32_t m = zm; m; m &= m - 1) {  // this thread's code-0 points, in order
-            const uint32_t j = __ffs(m) - 1;
-            uint32_t dv = 0;
-            if (e < hi) {
-                const uint2 en = ol[e];
-                if (en.x == s0 + j) dv = en.y;
-                else bad = true;
-            } else {
-                bad = true;
+        if (lane == 31 && (uint64_t)clo + zinc != chi) bad = true;  // a group holds exactly its outliers
+        const uint32_t kmax = __reduce_max_sync(0xffffffffu, zc);
+        uint32_t r = zinc - zc;  // this lane's first entry within the run
+        uint32_t m = zm;
+        for (uint32_t k = 0; k < kmax; k++, r++) {
+            const uint32_t ix = __shfl_sync(0xffffffffu, cen.x, r & 31);
+            const uint32_t dv = __shfl_sync(0xffffffffu, cen.y, r & 31);
+            if (k < zc) {
+                const uint32_t j = __ffs(m) - 1;
+                m &= m - 1;
+                uint2 e = make_uint2(ix, dv);
+                if (r >= 32) e = (uint64_t)clo + r < chi ? ol[clo + r] : make_uint2(0xFFFFFFFFu, 0u);
+                if (e.x != s0 + j) bad = true;
+                od[j] = e.x == s0 + j ? e.y : 0u;
             }
-            od[j] = dv;
-            e++;
         }
         if (zm) {
 #pragma unroll
@@ -269,8 +293,10 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
         uint32_t s = 0;
 #pragma unroll
         for (int j = 0; j < 16; j++) s += d[j];
+        // the scan's scratch alternates between two arrays, so the next tile's
+        // scan cannot overwrite one that a slow warp of this tile still reads
         uint32_t tot;
-        uint32_t run = block_excl_scan(s, sh, &tot) + F[tile];
+        uint32_t run = block_excl_scan_nb(s, sh2[par], &tot) + ccarry;
         float v[16];
 #pragma unroll
         for (int j = 0; j < 16; j++) {
@@ -286,7 +312,6 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
             for (int j = 0; j < 16; j++)
                 if (s0 + j < n) a.out[s0 + j] = v[j];
         }
-        __syncthreads();  // sh is reused by the next tile
     }
     if (bad) atomicOr(&a.ctl->error, DERR_CORRUPT);
 }
@@ -528,8 +553,13 @@ void launch_reconstruct(const ReconArgs &a, cudaStream_t st, int *launches)
             nl++;
         }
     }
-    if (g.ndim == 1) k_values_1d<<<gridt, k1Threads, 0, st>>>(a, g, a.faces, start1d);
-    else if (g.ndim == 2) k_values<k2TX, k2TY, 1, k2Threads><<<gridt, k2Threads, 0, st>>>(a, g, a.faces);
+    if (g.ndim == 1) {
+        // persistent: as many blocks as fit at once (57 registers -> 4 per SM)
+        const int grid1 = (int)std::min<uint64_t>(g.ntiles, (uint64_t)a.num_sms * 4);
+        k_values_1d<<<grid1, k1Threads, 0, st>>>(a, g, a.faces, start1d);
+    }
+    else if (g.ndim == 2)
+        k_values<k2TX, k2TY, 1, k2Threads><<<gridt, k2Threads, 0, st>>>(a, g, a.faces);
     else k_values<k3TX, k3TY, k3TZ, k3Threads><<<gridt, k3Threads, 0, st>>>(a, g, a.faces);
     nl++;
     if (a.e) {
