@@ -138,16 +138,25 @@ __device__ __forceinline__ int32_t prequant_full(float d, const EbScalars &s, bo
 // |d - fl(2eb * q)| is strictly below eb (then the exact value is too);
 // every other case (NaN, Inf, large |t|, near-ties) takes the full path,
 // which gives the same q for the cases accepted here.
-__device__ __forceinline__ int32_t prequant(float d, const EbScalars &s, bool &exc)
+// The fast path alone: ok = false when it cannot decide (then the value must
+// go through prequant_full).
+__device__ __forceinline__ int32_t prequant_fast(float d, const EbScalars &s, bool &ok)
 {
     const float t = __fmul_rn(d, s.inv2eb);
     const float tm = __fadd_rn(t, 12582912.0f);
     const float r = __fmul_rn(s.ebx2, __fsub_rn(tm, 12582912.0f));
     // one predicate for both tests (NaN and Inf fail the first)
-    const bool ok = (fabsf(t) < 4194304.0f) & (fabsf(__fsub_rn(d, r)) < s.eb);
+    ok = (fabsf(t) < 4194304.0f) & (fabsf(__fsub_rn(d, r)) < s.eb);
+    return __float_as_int(tm) - 0x4B400000;
+}
+
+__device__ __forceinline__ int32_t prequant(float d, const EbScalars &s, bool &exc)
+{
+    bool ok;
+    const int32_t q = prequant_fast(d, s, ok);
     if (ok) {
         exc = false;
-        return __float_as_int(tm) - 0x4B400000;
+        return q;
     }
     return prequant_full(d, s, exc);
 }

@@ -252,7 +252,14 @@ __device__ __forceinline__ uint32_t point_1d(HistState &h, const QuantArgs &a, u
     const bool central = k < 3;
     pk += central ? 1u << (k << 3) : 0u;
     if (WIN) {
-        if (!central) atomicAdd(&h.sh[code], 1u);
+        // predicated shared-memory add: no branch around it
+        const uint32_t addr = (uint32_t)__cvta_generic_to_shared(h.sh + code);
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "setp.ne.u32 p, %0, 0;\n\t"
+            "@p red.shared.add.u32 [%1], 1;\n\t}" ::"r"((uint32_t)!central),
+            "r"(addr)
+            : "memory");
     } else if (!central) {
         const uint32_t b = code - h.lo;
         if (b < h.nsh) atomicAdd(&h.sh[b], 1u);
@@ -308,12 +315,30 @@ __global__ void __launch_bounds__(kQ1Threads) k_dualquant_1d(QuantArgs a, uint32
         uint32_t pk = 0;
         const uint32_t exc0 = h.n_exc;  // this run's exceptions go to its encoder unit below
         if (full) {
+            // the prequant fast path for all 16 points; the few it cannot
+            // decide (near a rounding tie, huge, non-finite) are redone with
+            // the full watchdog in a branch the warp rarely takes
+            uint32_t q[kQ1Per], slow = 0, excm = 0;
 #pragma unroll
             for (int j = 0; j < kQ1Per; j++) {
-                bool exc;
-                const uint32_t q = (uint32_t)prequant(v[j], sc, exc);
-                code[j] = point_1d<WIN>(h, a, e0 + j, q - qprev, exc, pk);
-                qprev = q;
+                bool ok;
+                q[j] = (uint32_t)prequant_fast(v[j], sc, ok);
+                slow |= (ok ? 0u : 1u) << j;
+            }
+            if (slow) {
+#pragma unroll
+                for (int j = 0; j < kQ1Per; j++) {
+                    if (slow & (1u << j)) {
+                        bool exc;
+                        q[j] = (uint32_t)prequant_full(v[j], sc, exc);
+                        excm |= (exc ? 1u : 0u) << j;
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < kQ1Per; j++) {
+                code[j] = point_1d<WIN>(h, a, e0 + j, q[j] - qprev, (excm >> j) & 1u, pk);
+                qprev = q[j];
             }
             uint4 *o = reinterpret_cast<uint4 *>(a.codes + e0);
             o[0] = make_uint4(code[0] | (code[1] << 16), code[2] | (code[3] << 16), code[4] | (code[5] << 16),
