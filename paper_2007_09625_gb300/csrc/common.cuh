@@ -392,7 +392,7 @@ struct DecodeArgs {
     uint16_t *codes;
     Control *ctl;
 };
-constexpr uint32_t kRecon1DTile = 4096;  // 1D reconstruction tile (points)
+constexpr uint32_t kRecon1DTile = 512;  // 1D reconstruction tile (points): one warp of the value kernel
 // phase 0: chunk word offsets (scan), 1: symbols; returns kernels launched
 int launch_decode(const DecodeArgs &a, cudaStream_t st, int phase);
 

@@ -36,9 +36,9 @@ struct Geo {
     uint64_t off[8];    // start of the array of subset A in the carry scratch
 };
 
-constexpr int k1Threads = 256;
+constexpr int k1Threads = 256;                // 8 warps, each on its own tiles
 constexpr int k1PerThread = 16;
-constexpr int k1Tile = k1Threads * k1PerThread;  // 4096
+constexpr int k1Tile = 32 * k1PerThread;      // 512 points: one warp
 static_assert(k1Tile == (int)kRecon1DTile, "decoder tile sums and 1D tiles must agree");
 constexpr int k2TX = 128, k2TY = 32, k2Threads = 256;
 constexpr int k3TX = 32, k3TY = 16, k3TZ = 16, k3Threads = 512;
@@ -105,12 +105,12 @@ __global__ void k_scatter_outliers(ReconArgs a, uint64_t n)
 }
 
 // 1D: the outlier residuals go to the tile sums (added to the in-cap sums
-// the decoder left there), and every 512-point group g learns where its
+// the decoder left there), and every 512-point tile g learns where its
 // outliers start in the index-ordered list: start[g] = first outlier with
-// idx >= 512 g, for g = 0 .. ngroups (start[ngroups] = m).  Consecutive
+// idx >= 512 g, for g = 0 .. ntiles (start[ntiles] = m).  Consecutive
 // outliers mostly share a tile, so a warp adds each run of equal tiles with
 // one atomic.
-constexpr uint32_t kGroup1D = 512;  // points per warp in the 1D value kernel
+constexpr uint32_t kGroup1D = kRecon1DTile;
 
 __global__ void k_outlier_tiles_1d(ReconArgs a, uint64_t n, uint64_t ngroups, uint32_t *start)
 {
@@ -178,17 +178,17 @@ __global__ void k_patch_exceptions(ReconArgs a, uint64_t n)
 // ---------------------------------------------------------------------------
 // 1D tiles: 4096 points, 16 consecutive per thread, block scan of totals
 
-// One 4096-point tile per block iteration; warp w of the block covers the
-// tile's 512-point group g.  A warp's outliers are the run start[g] ..
-// start[g+1] of the index-ordered list; the first 32 of them are loaded one
-// per lane, and a warp scan of the lanes' code-0 counts tells each lane which
-// entries its code-0 points take, in order (fetched by shuffles; runs longer
-// than 32 read the rest from global memory).  Every entry's index must be
-// its point's and the counts must match the run.  Residuals are code - R, or
-// the outlier's residual for code 0; their sum within the tile comes from a
-// thread run and one block scan; the tile's carry F[tile] completes the
-// prefix.  All loads of the next tile (codes, its outlier entries) and the
-// run bounds of the tile after it are issued before this tile is processed.
+// One 512-point tile per warp iteration, with no block-level synchronisation.
+// A tile's outliers are the run start[t] .. start[t+1] of the index-ordered
+// list; the first 32 of them are loaded one per lane, and a warp scan of the
+// lanes' code-0 counts tells each lane which entries its code-0 points take,
+// in order (fetched by shuffles; runs longer than 32 read the rest from
+// global memory).  Every entry's index must be its point's and the counts
+// must match the run.  Residuals are code - R, or the outlier's residual for
+// code 0; their sum within the tile is a thread run plus a warp scan, and the
+// tile's carry F[t] completes the prefix.  The next tile's codes, outlier
+// entries and carry, and the run bounds of the tile after it, are loaded
+// before this tile is processed.
 __device__ __forceinline__ uint4 ldg_nc16(const void *p)
 {
     uint4 v;
@@ -200,27 +200,26 @@ __device__ __forceinline__ uint4 ldg_nc16(const void *p)
 
 __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, const uint32_t *F, const uint32_t *start)
 {
-    __shared__ uint32_t sh2[2][33];  // scan scratch, alternating between tiles
     __shared__ uint32_t s_od[k1Threads * 17];  // outlier residuals by (thread, point); stride 17 spreads banks
     if (a.ctl->error & DERR_CORRUPT) return;
     const uint64_t n = g.n[0];
     const float ebx2 = a.ebx2;
     const uint32_t R = a.radius;
-    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const uint32_t lane = threadIdx.x & 31;
     const uint2 *ol = reinterpret_cast<const uint2 *>(a.archive + a.off_outl);
     uint32_t *od = s_od + threadIdx.x * 17;
-    constexpr uint32_t kGroups = k1Tile / kGroup1D;
+    const uint64_t nwarps = (uint64_t)gridDim.x * (k1Threads / 32);
     bool bad = false;
-    auto bounds = [&](uint64_t tile, uint32_t &lo, uint32_t &hi) {
+    auto bounds = [&](uint64_t t, uint32_t &lo, uint32_t &hi) {
         lo = hi = 0;
-        if (a.m && tile < g.ntiles) {
-            lo = start[tile * kGroups + warp];
-            hi = start[tile * kGroups + warp + 1];
+        if (a.m && t < g.ntiles) {
+            lo = start[t];
+            hi = start[t + 1];
         }
     };
-    auto codes = [&](uint64_t tile, uint4 &w0, uint4 &w1) {
-        const uint64_t s0 = tile * k1Tile + (uint64_t)threadIdx.x * 16;
-        if (tile < g.ntiles && s0 + 16 <= n) {
+    auto codes = [&](uint64_t t, uint4 &w0, uint4 &w1) {
+        const uint64_t s0 = t * k1Tile + (uint64_t)lane * 16;
+        if (t < g.ntiles && s0 + 16 <= n) {
             w0 = ldg_nc16(a.codes + s0);
             w1 = ldg_nc16(a.codes + s0 + 8);
         }
@@ -230,17 +229,16 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
         if (lo + lane < hi) en = ol[lo + lane];
         return en;
     };
-    uint64_t tile = blockIdx.x;
+    uint64_t tile = (uint64_t)blockIdx.x * (k1Threads / 32) + (threadIdx.x >> 5);
     uint4 w0 = make_uint4(0, 0, 0, 0), w1 = w0;
     uint32_t lo, hi, lo1, hi1;
     bounds(tile, lo, hi);
-    bounds(tile + gridDim.x, lo1, hi1);
+    bounds(tile + nwarps, lo1, hi1);
     codes(tile, w0, w1);
     uint2 en = entry(lo, hi);
     uint32_t carry = tile < g.ntiles ? F[tile] : 0u;
-    uint32_t par = 0;
-    for (; tile < g.ntiles; tile += gridDim.x, par ^= 1) {
-        const uint64_t s0 = tile * k1Tile + (uint64_t)threadIdx.x * 16;
+    for (; tile < g.ntiles; tile += nwarps) {
+        const uint64_t s0 = tile * k1Tile + (uint64_t)lane * 16;
         uint32_t c[16];
         if (s0 + 16 <= n) {
             const uint32_t w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
@@ -253,12 +251,12 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
         const uint32_t clo = lo, chi = hi, ccarry = carry;
         const uint2 cen = en;
         // next tile's loads
-        const uint64_t tn = tile + gridDim.x;
+        const uint64_t tn = tile + nwarps;
         codes(tn, w0, w1);
         en = entry(lo1, hi1);
         lo = lo1;
         hi = hi1;
-        bounds(tn + gridDim.x, lo1, hi1);
+        bounds(tn + nwarps, lo1, hi1);
         if (tn < g.ntiles) carry = F[tn];
 
         uint32_t d[16], zm = 0;
@@ -269,7 +267,7 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
         }
         const uint32_t zc = __popc(zm);
         const uint32_t zinc = warp_incl_scan(zc);
-        if (lane == 31 && (uint64_t)clo + zinc != chi) bad = true;  // a group holds exactly its outliers
+        if (lane == 31 && (uint64_t)clo + zinc != chi) bad = true;  // a tile holds exactly its outliers
         const uint32_t kmax = __reduce_max_sync(0xffffffffu, zc);
         uint32_t r = zinc - zc;  // this lane's first entry within the run
         uint32_t m = zm;
@@ -293,10 +291,7 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
         uint32_t s = 0;
 #pragma unroll
         for (int j = 0; j < 16; j++) s += d[j];
-        // the scan's scratch alternates between two arrays, so the next tile's
-        // scan cannot overwrite one that a slow warp of this tile still reads
-        uint32_t tot;
-        uint32_t run = block_excl_scan_nb(s, sh2[par], &tot) + ccarry;
+        uint32_t run = ccarry + warp_incl_scan(s) - s;
         float v[16];
 #pragma unroll
         for (int j = 0; j < 16; j++) {
@@ -521,8 +516,8 @@ void launch_reconstruct(const ReconArgs &a, cudaStream_t st, int *launches)
     const Geo g = make_geo(a.ndim, a.dims);
     const uint64_t n = g.n[0] * g.n[1] * g.n[2];
     int nl = 0;
-    uint32_t *start1d = reinterpret_cast<uint32_t *>(a.dscr);  // 1D: per-group outlier starts
-    const uint64_t ngroups = g.ntiles * (k1Tile / kGroup1D);
+    uint32_t *start1d = reinterpret_cast<uint32_t *>(a.dscr);  // 1D: per-tile outlier starts
+    const uint64_t ngroups = g.ntiles;
     if (a.m) {
         const int grid = (int)std::min<uint64_t>((a.m + 255) / 256, (uint64_t)a.num_sms * 16);
         if (g.ndim == 1) k_outlier_tiles_1d<<<grid, 256, 0, st>>>(a, n, ngroups, start1d);
@@ -554,8 +549,9 @@ void launch_reconstruct(const ReconArgs &a, cudaStream_t st, int *launches)
         }
     }
     if (g.ndim == 1) {
-        // persistent: as many blocks as fit at once (57 registers -> 4 per SM)
-        const int grid1 = (int)std::min<uint64_t>(g.ntiles, (uint64_t)a.num_sms * 4);
+        // persistent: as many blocks as fit at once
+        const uint64_t blocks = (g.ntiles + k1Threads / 32 - 1) / (k1Threads / 32);
+        const int grid1 = (int)std::min<uint64_t>(blocks, (uint64_t)a.num_sms * 4);
         k_values_1d<<<grid1, k1Threads, 0, st>>>(a, g, a.faces, start1d);
     }
     else if (g.ndim == 2)
