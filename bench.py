@@ -282,7 +282,13 @@ def main():
     ebf = float(np.frombuffer(hdr[56:60].tobytes(), np.float32)[0])  # header: eb
     maxlen = int(np.frombuffer(hdr[104:108].tobytes(), np.uint32)[0])  # header: longest code
     fin = torch.isfinite(x)
-    assert float(err[fin].max()) <= ebf, "error bound violated"
+    max_err = float(err[fin].max())
+    assert max_err <= ebf, "error bound violated"
+    xf = x[fin].double()
+    vrange = float(xf.max() - xf.min())
+    mse = float((err[fin] ** 2).mean())
+    psnr = 20 * np.log10(vrange) - 10 * np.log10(mse) if mse > 0 and vrange > 0 else float("inf")
+    del err, xf
 
     ctx.profile_read()  # reset counters
     ctx.profile_enable(True)
@@ -337,6 +343,11 @@ def main():
                 "unit": "GB/s", "frac": achieved / hbm, "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
                 "traffic": measured_traffic(stage_names[dom], (a.log2n, a.rel, a.radius, chunk)),
                 "alg_bytes_per_launch": alg[dom]}
+    # the whole compress+decompress step: 12 + 8f + 4/CR (compress, relative eb)
+    # plus 8 + 8f + 4/CR (decompress) bytes per point
+    step_bytes = n * (20.0 + 16.0 * f + 8.0 / cr)
+    pipe_gbs = step_bytes / (ms_step / 1e3) / 1e9
+    pipe = {"alg_bytes_per_step": step_bytes, "achieved_gbs": pipe_gbs, "peak": hbm, "frac": pipe_gbs / hbm}
     # every single-kernel stage against the same peak
     per_kernel = {}
     for st_i, by in alg.items():
@@ -396,6 +407,8 @@ def main():
                 "compress_gbs": 4.0 * n / (comp_ms / 1e3) / 1e9 if comp_ms else None,
                 "decompress_gbs": 4.0 * n / (dec_ms / 1e3) / 1e9 if dec_ms else None,
                 "compression_ratio": cr, "outlier_frac": f, "max_code_len": maxlen,
+                "psnr_db": psnr, "max_err_over_eb": max_err / ebf,
+                "pipeline_roofline": pipe,
                 "stage_ms_per_step": {nm: stage_ms[i] / a.steps for i, nm in enumerate(stage_names)},
                 "roofline": roofline, "kernels": per_kernel, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "batch_vs_per_field": batch,
