@@ -96,6 +96,7 @@ static int check_params(const gbsz_ref_params *p, uint64_t *n_out)
     if (p->radius < 2 || p->radius > 32768) return REF_ERR_INVALID_ARG;
     if (p->chunk < 64 || p->chunk > 65536 || (p->chunk & (p->chunk - 1)))
         return REF_ERR_INVALID_ARG;
+    if (p->lorenzo_block > 1) return REF_ERR_INVALID_ARG;
     *n_out = n;
     return REF_OK;
 }
@@ -189,11 +190,24 @@ static uint64_t binom(uint32_t n, uint32_t k)
     return r;
 }
 
-int gbsz_ref_lorenzo_delta(const int32_t *q, uint32_t ndim,
-                           const uint64_t dims[3], uint32_t order,
-                           int32_t *delta)
+uint32_t gbsz_ref_lorenzo_block_extent(uint32_t ndim)
 {
-    if (ndim < 1 || ndim > 3 || order < 1 || order > 4) return REF_ERR_INVALID_ARG;
+    return ndim == 1 ? 32u : ndim == 2 ? 16u : 8u;
+}
+
+/* Position of coordinate c inside its block: c itself over the whole field,
+ * c mod the block extent in the per-block mode.  A neighbour k steps back
+ * exists (is not padding) iff k <= that position. */
+static uint64_t in_block(uint64_t c, uint32_t ndim, uint32_t lblock)
+{
+    return lblock ? c % gbsz_ref_lorenzo_block_extent(ndim) : c;
+}
+
+int gbsz_ref_lorenzo_delta_blocked(const int32_t *q, uint32_t ndim,
+                                   const uint64_t dims[3], uint32_t order,
+                                   uint32_t lblock, int32_t *delta)
+{
+    if (ndim < 1 || ndim > 3 || order < 1 || order > 4 || lblock > 1) return REF_ERR_INVALID_ARG;
     uint64_t d[3] = {1, 1, 1};
     for (uint32_t i = 0; i < ndim; i++) d[i] = dims[i];
     const uint32_t kz_max = ndim >= 3 ? order : 0;
@@ -204,12 +218,14 @@ int gbsz_ref_lorenzo_delta(const int32_t *q, uint32_t ndim,
         for (uint64_t y = 0; y < d[1]; y++) {
             for (uint64_t x = 0; x < d[0]; x++) {
                 uint32_t p = 0; /* prediction, modulo 2^32 */
+                const uint64_t bx = in_block(x, ndim, lblock), by = in_block(y, ndim, lblock),
+                               bz = in_block(z, ndim, lblock);
                 for (uint32_t kz = 0; kz <= kz_max; kz++)
                     for (uint32_t ky = 0; ky <= ky_max; ky++)
                         for (uint32_t kx = 0; kx <= order; kx++) {
                             if (kx == 0 && ky == 0 && kz == 0) continue;
-                            /* points outside the field are zero */
-                            if (kx > x || ky > y || kz > z) continue;
+                            /* points outside the field (or the block) are zero */
+                            if (kx > bx || ky > by || kz > bz) continue;
                             uint64_t j = (x - kx) + d[0] * ((y - ky) + d[1] * (z - kz));
                             uint64_t c = binom(order, kx) * binom(order, ky) * binom(order, kz);
                             /* sign (-1)^(kx+ky+kz+1) */
@@ -225,16 +241,25 @@ int gbsz_ref_lorenzo_delta(const int32_t *q, uint32_t ndim,
     return REF_OK;
 }
 
+int gbsz_ref_lorenzo_delta(const int32_t *q, uint32_t ndim,
+                           const uint64_t dims[3], uint32_t order,
+                           int32_t *delta)
+{
+    return gbsz_ref_lorenzo_delta_blocked(q, ndim, dims, order, 0, delta);
+}
+
 /* ------------------------------------------------------------------------ */
 /* S1 + S2: dual-quantization of the field (Algorithm 2, compression)         */
 
-int gbsz_ref_dualquant(const float *x, uint32_t ndim, const uint64_t dims[3],
-                       const float sc[3], uint32_t radius, uint16_t *codes,
-                       uint32_t *out_idx, int32_t *out_delta, uint64_t *m,
-                       uint32_t *exc_idx, uint32_t *exc_raw, uint64_t *e,
-                       int32_t *q_keep)
+int gbsz_ref_dualquant_blocked(const float *x, uint32_t ndim,
+                               const uint64_t dims[3], const float sc[3],
+                               uint32_t radius, uint32_t lblock,
+                               uint16_t *codes, uint32_t *out_idx,
+                               int32_t *out_delta, uint64_t *m,
+                               uint32_t *exc_idx, uint32_t *exc_raw,
+                               uint64_t *e, int32_t *q_keep)
 {
-    if (ndim < 1 || ndim > 3 || radius < 2 || radius > 32768) return REF_ERR_INVALID_ARG;
+    if (ndim < 1 || ndim > 3 || radius < 2 || radius > 32768 || lblock > 1) return REF_ERR_INVALID_ARG;
     uint64_t n = field_size(ndim, dims);
     int32_t *q = (int32_t *)malloc(n * sizeof(int32_t) + 1);
     int32_t *delta = (int32_t *)malloc(n * sizeof(int32_t) + 1);
@@ -247,7 +272,7 @@ int gbsz_ref_dualquant(const float *x, uint32_t ndim, const uint64_t dims[3],
 #pragma omp parallel for
     for (int64_t i = 0; i < (int64_t)n; i++) exc[i] = (uint8_t)gbsz_ref_prequant_one(x[i], sc, &q[i]);
     /* prediction on the prequantized integers, then postquant */
-    gbsz_ref_lorenzo_delta(q, ndim, dims, 1, delta);
+    gbsz_ref_lorenzo_delta_blocked(q, ndim, dims, 1, lblock, delta);
     uint64_t nm = 0, ne = 0;
     for (uint64_t i = 0; i < n; i++) {
         int32_t dl = delta[i];
@@ -273,6 +298,16 @@ int gbsz_ref_dualquant(const float *x, uint32_t ndim, const uint64_t dims[3],
     if (q_keep) memcpy(q_keep, q, n * sizeof(int32_t));
     free(q); free(delta); free(exc);
     return REF_OK;
+}
+
+int gbsz_ref_dualquant(const float *x, uint32_t ndim, const uint64_t dims[3],
+                       const float sc[3], uint32_t radius, uint16_t *codes,
+                       uint32_t *out_idx, int32_t *out_delta, uint64_t *m,
+                       uint32_t *exc_idx, uint32_t *exc_raw, uint64_t *e,
+                       int32_t *q_keep)
+{
+    return gbsz_ref_dualquant_blocked(x, ndim, dims, sc, radius, 0, codes, out_idx, out_delta, m,
+                                      exc_idx, exc_raw, e, q_keep);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -494,14 +529,15 @@ int gbsz_ref_inflate(const uint32_t *stream, uint64_t words,
 /* ------------------------------------------------------------------------ */
 /* S8: reversed dual-quantization, reconstructed cascadingly (Algorithm 2)   */
 
-int gbsz_ref_reconstruct(const uint16_t *codes, uint32_t ndim,
-                         const uint64_t dims[3], uint32_t radius,
-                         const uint32_t *out_idx, const int32_t *out_delta,
-                         uint64_t m, const uint32_t *exc_idx,
-                         const uint32_t *exc_raw, uint64_t e, float ebx2,
-                         float *xr)
+int gbsz_ref_reconstruct_blocked(const uint16_t *codes, uint32_t ndim,
+                                 const uint64_t dims[3], uint32_t radius,
+                                 uint32_t lblock, const uint32_t *out_idx,
+                                 const int32_t *out_delta, uint64_t m,
+                                 const uint32_t *exc_idx,
+                                 const uint32_t *exc_raw, uint64_t e,
+                                 float ebx2, float *xr)
 {
-    if (ndim < 1 || ndim > 3) return REF_ERR_INVALID_ARG;
+    if (ndim < 1 || ndim > 3 || lblock > 1) return REF_ERR_INVALID_ARG;
     uint64_t d[3] = {1, 1, 1};
     for (uint32_t i = 0; i < ndim; i++) d[i] = dims[i];
     uint64_t n = d[0] * d[1] * d[2];
@@ -520,11 +556,14 @@ int gbsz_ref_reconstruct(const uint16_t *codes, uint32_t ndim,
                     if (j >= m || out_idx[j] != i) { free(q); return REF_ERR_CORRUPT; }
                     dl = out_delta[j++];
                 }
-                /* p = l(q of reconstructed neighbours), order 1, zero outside */
+                /* p = l(q of reconstructed neighbours), order 1, zero outside
+                   the field (and outside the block in the per-block mode) */
                 uint32_t p = 0;
+                const uint64_t bx = in_block(x, ndim, lblock), by = in_block(y, ndim, lblock),
+                               bz = in_block(z, ndim, lblock);
                 for (uint32_t k = 1; k < (1u << ndim); k++) {
                     uint32_t kx = k & 1u, ky = (k >> 1) & 1u, kz = (k >> 2) & 1u;
-                    if (kx > x || ky > y || kz > z) continue;
+                    if (kx > bx || ky > by || kz > bz) continue;
                     uint32_t v = (uint32_t)q[(x - kx) + d[0] * ((y - ky) + d[1] * (z - kz))];
                     p = ((kx + ky + kz) % 2 == 1) ? p + v : p - v;
                 }
@@ -539,6 +578,17 @@ int gbsz_ref_reconstruct(const uint16_t *codes, uint32_t ndim,
     }
     free(q);
     return REF_OK;
+}
+
+int gbsz_ref_reconstruct(const uint16_t *codes, uint32_t ndim,
+                         const uint64_t dims[3], uint32_t radius,
+                         const uint32_t *out_idx, const int32_t *out_delta,
+                         uint64_t m, const uint32_t *exc_idx,
+                         const uint32_t *exc_raw, uint64_t e, float ebx2,
+                         float *xr)
+{
+    return gbsz_ref_reconstruct_blocked(codes, ndim, dims, radius, 0, out_idx, out_delta, m,
+                                        exc_idx, exc_raw, e, ebx2, xr);
 }
 
 /* ------------------------------------------------------------------------ */
@@ -584,7 +634,8 @@ int gbsz_ref_compress(const float *x, const gbsz_ref_params *p, void *archive,
         st = REF_ERR_OOM;
         goto done;
     }
-    st = gbsz_ref_dualquant(x, p->ndim, dims, sc, R, codes, oidx, odel, &m, eidx, eraw, &e, NULL);
+    st = gbsz_ref_dualquant_blocked(x, p->ndim, dims, sc, R, p->lorenzo_block, codes, oidx, odel, &m,
+                                    eidx, eraw, &e, NULL);
     if (st) goto done;
     st = gbsz_ref_histogram(codes, n, nbins, hist);
     if (st) goto done;
@@ -625,7 +676,7 @@ int gbsz_ref_compress(const float *x, const gbsz_ref_params *p, void *archive,
         put_u64(a, 88, e);
         put_u64(a, 96, w);
         put_u32(a, 104, maxlen);
-        put_u32(a, 108, 0); /* Lorenzo over the whole field, no blocks */
+        put_u32(a, 108, p->lorenzo_block); /* 0: one predictor; 1: per block */
         put_u64(a, 112, total);
         memcpy(a + off_len, len, nbins);
         for (uint64_t c = 0; c < nc; c++) put_u32(a, off_bits + 4 * c, bits[c]);
@@ -679,7 +730,8 @@ static int parse_header(const uint8_t *a, size_t bytes, hdr_t *h)
     if (check_params(&h->p, &n) || n != h->n) return REF_ERR_CORRUPT;
     for (uint32_t i = h->p.ndim; i < 3; i++)
         if (h->p.dims[i] != 1) return REF_ERR_CORRUPT;
-    if (get_u32(a, 108) != 0) return REF_ERR_CORRUPT;
+    h->p.lorenzo_block = get_u32(a, 108);
+    if (h->p.lorenzo_block > 1) return REF_ERR_CORRUPT;
     if (h->nc != nchunks(n, h->p.chunk)) return REF_ERR_CORRUPT;
     if (!(h->sc[0] > 0.0f) || !isfinite(h->sc[0]) || h->sc[1] != h->sc[0] * 2.0f ||
         !isfinite(h->sc[1]))
@@ -750,7 +802,7 @@ int gbsz_ref_decompress(const void *archive, size_t bytes, float *x,
     }
     st = gbsz_ref_inflate(stream, h.w, bits, h.n, h.p.chunk, len, nbins, codes);
     if (st) goto done;
-    st = gbsz_ref_reconstruct(codes, h.p.ndim, h.p.dims, h.p.radius, oidx, odel, h.m,
+    st = gbsz_ref_reconstruct_blocked(codes, h.p.ndim, h.p.dims, h.p.radius, h.p.lorenzo_block, oidx, odel, h.m,
                               eidx, eraw, h.e, h.sc[1], x);
 done:
     free(bits); free(stream); free(oidx); free(odel); free(eidx); free(eraw); free(codes);

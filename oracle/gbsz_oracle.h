@@ -41,7 +41,14 @@ typedef struct {
     uint32_t eb_mode; /* REF_EB_ABS or REF_EB_REL */
     uint32_t radius;  /* R: in-cap residuals satisfy |delta| < R; 2R bins */
     uint32_t chunk;   /* Huffman chunk in symbols, power of two 64..65536 */
+    uint32_t lorenzo_block; /* 0: one predictor over the whole field; 1: the
+                               paper's blocks (Sec. 3.1.1, 32 / 16x16 / 8x8x8)
+                               with a zero padding layer around each block */
 } gbsz_ref_params;
+
+/* Block extent of the per-block Lorenzo mode along every dimension
+ * (Sec. 3.1.1, "Chunking and Padding"): 32 in 1D, 16 in 2D, 8 in 3D. */
+uint32_t gbsz_ref_lorenzo_block_extent(uint32_t ndim);
 
 /* S0 -- error bound scalars (value-range-relative bound, footnote of Sec.
  * 3.2.2).  out[0] = eb, out[1] = 2*eb, out[2] = 1/(2*eb), all FP32. */
@@ -60,6 +67,12 @@ int gbsz_ref_lorenzo_delta(const int32_t *q, uint32_t ndim,
                            const uint64_t dims[3], uint32_t order,
                            int32_t *delta);
 
+/* The same inside the paper's blocks when lblock = 1: a neighbour outside the
+ * point's block counts as zero (the zero padding layer of Sec. 3.1.1). */
+int gbsz_ref_lorenzo_delta_blocked(const int32_t *q, uint32_t ndim,
+                                   const uint64_t dims[3], uint32_t order,
+                                   uint32_t lblock, int32_t *delta);
+
 /* S1+S2 -- dual-quantization of a whole field (Algorithm 2, compression
  * loop).  codes[n]; outliers (idx, delta) and exceptions (idx, raw bits) in
  * ascending idx.  Capacities are in entries; *m and *e get the counts.  q may
@@ -69,6 +82,13 @@ int gbsz_ref_dualquant(const float *x, uint32_t ndim, const uint64_t dims[3],
                        uint32_t *out_idx, int32_t *out_delta, uint64_t *m,
                        uint32_t *exc_idx, uint32_t *exc_raw, uint64_t *e,
                        int32_t *q);
+int gbsz_ref_dualquant_blocked(const float *x, uint32_t ndim,
+                               const uint64_t dims[3], const float sc[3],
+                               uint32_t radius, uint32_t lblock,
+                               uint16_t *codes, uint32_t *out_idx,
+                               int32_t *out_delta, uint64_t *m,
+                               uint32_t *exc_idx, uint32_t *exc_raw,
+                               uint64_t *e, int32_t *q);
 
 /* S3 -- histogram of quant codes (Sec. 3.2.1). */
 int gbsz_ref_histogram(const uint16_t *codes, uint64_t n, uint32_t nbins,
@@ -102,6 +122,13 @@ int gbsz_ref_reconstruct(const uint16_t *codes, uint32_t ndim,
                          uint64_t m, const uint32_t *exc_idx,
                          const uint32_t *exc_raw, uint64_t e, float ebx2,
                          float *xr);
+int gbsz_ref_reconstruct_blocked(const uint16_t *codes, uint32_t ndim,
+                                 const uint64_t dims[3], uint32_t radius,
+                                 uint32_t lblock, const uint32_t *out_idx,
+                                 const int32_t *out_delta, uint64_t m,
+                                 const uint32_t *exc_idx,
+                                 const uint32_t *exc_raw, uint64_t e,
+                                 float ebx2, float *xr);
 
 /* Whole path: archive bytes and back. */
 size_t gbsz_ref_compress_bound(const gbsz_ref_params *p);

@@ -481,3 +481,68 @@ def test_corrupt_archives_report_errors_without_crashing():
         bad[pos] ^= np.uint8(1 << int(rng.integers(0, 8)))
         st = ref.decompress_status(bad)
         assert st in (ref.OK, ref.ERR_CORRUPT)
+
+
+# ---------------------------------------------------------------------------
+# Per-block Lorenzo (Sec. 3.1.1, chunking with a zero padding layer)
+
+def test_block_extents_follow_the_paper():
+    # 32 for 1D, 16x16 for 2D, 8x8x8 for 3D (Sec. 3.1.1)
+    assert [ref.lorenzo_block_extent(d) for d in (1, 2, 3)] == [32, 16, 8]
+
+
+@pytest.mark.parametrize("shape", [(70,), (37, 20), (17, 9, 10), (5, 33), (3, 3, 40)])
+def test_block_lorenzo_is_the_global_predictor_of_each_block(shape):
+    """Zero padding around every block means each block is predicted as if it
+    were a field of its own: cut the field into blocks, run the (separately
+    pinned) whole-field predictor on each, and the residuals must agree."""
+    rng = np.random.default_rng(sum(shape))
+    q = rng.integers(-2**31, 2**31, size=shape, dtype=np.int64).astype(np.int32)
+    B = ref.lorenzo_block_extent(len(shape))
+    got = ref.lorenzo_delta(q, 1, lblock=1)
+    want = np.zeros_like(q)
+    import itertools
+    for starts in itertools.product(*[range(0, s, B) for s in shape]):
+        sl = tuple(slice(a, min(a + B, s)) for a, s in zip(starts, shape))
+        want[sl] = ref.lorenzo_delta(np.ascontiguousarray(q[sl]), 1)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("shape", [(32,), (16, 16), (8, 8, 8), (7, 5), (3, 4, 2)])
+def test_block_lorenzo_equals_global_inside_one_block(shape):
+    rng = np.random.default_rng(7)
+    q = rng.integers(-1000, 1000, size=shape).astype(np.int32)
+    assert np.array_equal(ref.lorenzo_delta(q, 1, lblock=1), ref.lorenzo_delta(q, 1))
+
+
+def test_block_lorenzo_constant_field_1d():
+    # a constant c: every block restarts from the zero padding, so the
+    # residual is c at each block start and 0 elsewhere
+    q = np.full(100, 41, np.int32)
+    d = ref.lorenzo_delta(q, 1, lblock=1)
+    want = np.where(np.arange(100) % 32 == 0, 41, 0).astype(np.int32)
+    assert np.array_equal(d, want)
+
+
+@pytest.mark.parametrize("shape,eb", [((3000,), 1e-3), ((50, 61), 1e-4), ((13, 17, 19), 1e-3)])
+def test_block_archive_roundtrip_and_header(shape, eb):
+    rng = np.random.default_rng(len(shape))
+    x = np.cumsum(rng.normal(0, 1, shape), axis=-1).astype(np.float32)
+    a = ref.compress(x, eb, ref.EB_REL, radius=64, chunk=256, lblock=1)
+    s = ref.sections(a)
+    assert s["lblock"] == 1
+    y = ref.decompress(a)
+    sc = ref.error_bound(x, eb, ref.EB_REL)
+    assert np.all(np.abs(x.astype(np.float64) - y) <= float(sc[0]))
+    # the quant codes of the archive are those of the per-block dual-quant
+    dq = ref.dualquant(x, sc, 64, lblock=1)
+    assert np.array_equal(ref.inflate(s["stream"], s["bits"], x.size, 256, s["len"]), dq["codes"])
+
+
+def test_block_mode_inside_one_block_changes_only_the_flag():
+    rng = np.random.default_rng(3)
+    x = rng.normal(0, 1, (16, 16)).astype(np.float32)
+    a0 = ref.compress(x, 1e-3, ref.EB_REL, radius=512, chunk=64)
+    a1 = ref.compress(x, 1e-3, ref.EB_REL, radius=512, chunk=64, lblock=1)
+    diff = np.flatnonzero(a0 != a1)
+    assert a0.size == a1.size and np.all((diff >= 108) & (diff < 112))
