@@ -62,7 +62,12 @@ typedef enum { GBSZ_EB_ABS = 0, GBSZ_EB_REL = 1 } gbsz_eb_mode;
  *            others are outliers with code 0; 2R Huffman symbols
  *            (Sec. 3.1.2 "cap"; 512 = the paper's 1024 bins)
  *   chunk    Huffman chunk in symbols, power of two in [64, 65536]
- *            (Sec. 3.2.4); 0 = choose automatically from n */
+ *            (Sec. 3.2.4); 0 = choose automatically from n
+ *   lorenzo_block  0: one Lorenzo predictor over the whole field (values
+ *            outside the field are 0); 1: the paper's blocks (Sec. 3.1.1,
+ *            "Chunking and Padding": 32 in 1D, 16x16 in 2D, 8x8x8 in 3D),
+ *            each surrounded by a padding layer of zeros, so every block is
+ *            predicted and reconstructed on its own.  Stored in the archive. */
 typedef struct {
     uint32_t ndim;
     uint64_t dims[3];
@@ -70,6 +75,7 @@ typedef struct {
     uint32_t eb_mode;
     uint32_t radius;
     uint32_t chunk;
+    uint32_t lorenzo_block;
 } gbsz_params;
 
 /* Creates a context on CUDA device `device` (must be compute capability

@@ -298,9 +298,15 @@ struct QuantArgs {
     uint32_t *hist;  // 2R bins, zeroed by the caller
     uint32_t *unit_exc;   // exceptions per encoder unit (zeroed by the caller)
     uint32_t unit_shift;  // log2 of the encoder unit in points
+    uint32_t lblock;      // 1: Lorenzo inside the paper's blocks (zero padding layer)
     Control *ctl;
     int num_sms;
 };
+// block extent of the per-block Lorenzo mode (Sec. 3.1.1): 32, 16x16, 8x8x8
+__host__ __device__ constexpr uint32_t lorenzo_block_extent(uint32_t ndim)
+{
+    return ndim == 1 ? 32u : ndim == 2 ? 16u : 8u;
+}
 
 void launch_minmax_eb(const float *x, uint64_t n, Control *ctl, double eb, uint32_t mode,
                       int num_sms, cudaStream_t st);
@@ -364,7 +370,7 @@ struct EncodeArgs {
     ulonglong2 *scan_part;  // scan scratch
     Control *ctl;
     // header fields
-    uint32_t ndim, eb_mode;
+    uint32_t ndim, eb_mode, lblock;
     uint64_t dims[3];
     double eb;
     int num_sms;
@@ -406,6 +412,7 @@ struct ReconArgs {
     uint32_t radius;
     float ebx2;
     int32_t *dscr;
+    uint32_t lblock;      // 1: block-local reconstruction (the paper's blocks)
     uint32_t *faces;      // carry scratch; 1D: the tile sums left by the decoder
     uint64_t faces_cap;   // entries
     uint32_t *scan_partial;  // scratch for the 1D carry scan

@@ -212,6 +212,7 @@ bool valid_params(const gbsz_params *p, uint64_t *n_out)
     if (p->eb_mode != GBSZ_EB_ABS && p->eb_mode != GBSZ_EB_REL) return false;
     if (p->radius < 2 || p->radius > 32768) return false;
     if (p->chunk != 0 && (p->chunk < 64 || p->chunk > 65536 || (p->chunk & (p->chunk - 1)))) return false;
+    if (p->lorenzo_block > 1) return false;
     *n_out = n;
     return true;
 }
@@ -305,9 +306,10 @@ gbsz_status parse_header(const uint8_t *b, size_t bytes, Header *h)
     p.eb = rd<double>(b, H_EB);
     p.radius = rd<uint32_t>(b, H_RADIUS);
     p.chunk = rd<uint32_t>(b, H_CHUNK);
+    p.lorenzo_block = rd<uint32_t>(b, H_LBLOCK);  // validated with the other parameters
     uint64_t n;
     if (!valid_params(&p, &n) || p.chunk == 0) return GBSZ_ERR_CORRUPT;
-    if (rd<uint64_t>(b, H_N) != n || rd<uint32_t>(b, H_LBLOCK) != 0) return GBSZ_ERR_CORRUPT;
+    if (rd<uint64_t>(b, H_N) != n) return GBSZ_ERR_CORRUPT;
     h->p = p;
     h->n = n;
     h->nchunk = rd<uint32_t>(b, H_NCHUNK);
@@ -376,6 +378,7 @@ gbsz_status enqueue_compress(gbsz_ctx *c, Slot *s, const float *d_field, const g
     q.hist = s->hist.as<uint32_t>();
     q.unit_exc = s->unit_exc.as<uint32_t>();
     q.unit_shift = encode_unit_shift(p.chunk);
+    q.lblock = p.lorenzo_block;
     q.ctl = s->ctl;
     q.num_sms = c->num_sms;
     stage_begin(c, st, &e0);
@@ -410,6 +413,7 @@ gbsz_status enqueue_compress(gbsz_ctx *c, Slot *s, const float *d_field, const g
     en.ctl = s->ctl;
     en.ndim = p.ndim;
     en.eb_mode = p.eb_mode;
+    en.lblock = p.lorenzo_block;
     for (int i = 0; i < 3; i++) en.dims[i] = p.dims[i];
     en.eb = p.eb;
     en.num_sms = c->num_sms;
@@ -469,7 +473,7 @@ gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void
     d.num_sms = c->num_sms;
     d.chunk_off = s->chunk_off.as<unsigned long long>();
     d.scan_partial = s->scan_part.as<unsigned long long>();
-    d.tile_sums = h.p.ndim == 1 ? s->faces.as<uint32_t>() : nullptr;
+    d.tile_sums = h.p.ndim == 1 && !h.p.lorenzo_block ? s->faces.as<uint32_t>() : nullptr;
     d.codes = s->codes.as<uint16_t>();
     d.ctl = s->ctl;
     int ndec = 0;
@@ -491,6 +495,7 @@ gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void
     r.radius = h.p.radius;
     r.ebx2 = h.ebx2;
     r.dscr = s->dscr.as<int32_t>();
+    r.lblock = h.p.lorenzo_block;
     r.faces = s->faces.as<uint32_t>();
     r.faces_cap = nfaces;
     r.scan_partial = s->scan_part.as<uint32_t>();

@@ -146,7 +146,7 @@ __device__ void write_header(const EncodeArgs &a, const Layout &L, uint64_t nchu
     set64(H_E, e);
     set64(H_W, w);
     h[H_MAXLEN / 4] = maxlen;
-    h[H_LBLOCK / 4] = 0;
+    h[H_LBLOCK / 4] = a.lblock;
     set64(H_TOTAL, L.total);
     for (int i = 0; i < (int)(kHeaderBytes / 4); i++) put_u32(a.archive + 4 * i, h[i]);
     for (uint64_t b = L.len + a.nbins; b < L.bits; b++) a.archive[b] = 0;

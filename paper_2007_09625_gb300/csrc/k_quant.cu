@@ -308,9 +308,12 @@ __global__ void __launch_bounds__(kQ1Threads) k_dualquant_1d(QuantArgs a, uint32
 #pragma unroll
             for (int j = 0; j < kQ1Per; j++) v[j] = e0 + j < n ? a.x[e0 + j] : 0.0f;
         }
-        if (e0 > 0 && e0 <= n) vp = a.x[e0 - 1];
+        // the point before the run predicts its first point, unless that one
+        // starts a block of the per-block mode (its neighbour is padding)
+        const bool has_prev = e0 > 0 && e0 <= n && !(a.lblock && e0 % lorenzo_block_extent(1) == 0);
+        if (has_prev) vp = a.x[e0 - 1];
         bool dummy;
-        uint32_t qprev = (e0 > 0 && e0 <= n) ? (uint32_t)prequant(vp, sc, dummy) : 0u;
+        uint32_t qprev = has_prev ? (uint32_t)prequant(vp, sc, dummy) : 0u;
         uint32_t code[kQ1Per];
         uint32_t pk = 0;
         const uint32_t exc0 = h.n_exc;  // this run's exceptions go to its encoder unit below
@@ -422,8 +425,12 @@ __global__ void __launch_bounds__(kQ2Threads) k_dualquant_2d(QuantArgs a, uint32
                     const uint32_t lx = threadIdx.x + 128u * j;
                     const uint64_t x = x0 + lx;
                     if (x < nx) {
-                        const uint32_t d = (uint32_t)q[j] - (uint32_t)rows[buf][lx] -
-                                           (uint32_t)rows[prev][lx + 1] + (uint32_t)rows[prev][lx];
+                        // per-block mode: neighbours across a block edge are padding (0)
+                        const uint32_t mL = (a.lblock && x % lorenzo_block_extent(2) == 0) ? 0u : ~0u;
+                        const uint32_t mU = (a.lblock && (uint64_t)y % lorenzo_block_extent(2) == 0) ? 0u : ~0u;
+                        const uint32_t d = (uint32_t)q[j] - ((uint32_t)rows[buf][lx] & mL) -
+                                           ((uint32_t)rows[prev][lx + 1] & mU) +
+                                           ((uint32_t)rows[prev][lx] & mL & mU);
                         const uint64_t idx = (uint64_t)y * nx + x;
                         a.codes[idx] = (uint16_t)emit_point(h, a, idx, d, ex[j]);
                     }
@@ -516,8 +523,14 @@ __global__ void __launch_bounds__(kQ3Threads) k_dualquant_3d(QuantArgs a, uint32
                     if (gx < nx && gy < ny) {
                         const uint32_t(*c)[kQ3T + 1] = (const uint32_t(*)[kQ3T + 1])pl[buf];
                         const uint32_t(*p)[kQ3T + 1] = (const uint32_t(*)[kQ3T + 1])pl[prev];
-                        const uint32_t d = c[Y][X] - c[Y][X - 1] - c[Y - 1][X] - p[Y][X] +
-                                           c[Y - 1][X - 1] + p[Y][X - 1] + p[Y - 1][X] - p[Y - 1][X - 1];
+                        // per-block mode: neighbours across a block face are padding (0)
+                        const uint32_t B3 = lorenzo_block_extent(3);
+                        const uint32_t mL = (a.lblock && gx % B3 == 0) ? 0u : ~0u;
+                        const uint32_t mU = (a.lblock && gy % B3 == 0) ? 0u : ~0u;
+                        const uint32_t mB = (a.lblock && z % B3 == 0) ? 0u : ~0u;
+                        const uint32_t d = c[Y][X] - (c[Y][X - 1] & mL) - (c[Y - 1][X] & mU) - (p[Y][X] & mB) +
+                                           (c[Y - 1][X - 1] & mL & mU) + (p[Y][X - 1] & mL & mB) +
+                                           (p[Y - 1][X] & mU & mB) - (p[Y - 1][X - 1] & mL & mU & mB);
                         const uint64_t idx = ((uint64_t)z * ny + gy) * nx + gx;
                         a.codes[idx] = (uint16_t)emit_point(h, a, idx, d, ex[j]);
                     }

@@ -236,7 +236,9 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
     bounds(tile + nwarps, lo1, hi1);
     codes(tile, w0, w1);
     uint2 en = entry(lo, hi);
-    uint32_t carry = tile < g.ntiles ? F[tile] : 0u;
+    // per-block mode: no carries (every 32-point block restarts from 0)
+    const bool blocked = a.lblock != 0;
+    uint32_t carry = tile < g.ntiles && !blocked ? F[tile] : 0u;
     for (; tile < g.ntiles; tile += nwarps) {
         const uint64_t s0 = tile * k1Tile + (uint64_t)lane * 16;
         uint32_t c[16];
@@ -257,7 +259,7 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
         lo = lo1;
         hi = hi1;
         bounds(tn + nwarps, lo1, hi1);
-        if (tn < g.ntiles) carry = F[tn];
+        if (tn < g.ntiles && !blocked) carry = F[tn];
 
         uint32_t d[16], zm = 0;
 #pragma unroll
@@ -291,7 +293,14 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
         uint32_t s = 0;
 #pragma unroll
         for (int j = 0; j < 16; j++) s += d[j];
-        uint32_t run = ccarry + warp_incl_scan(s) - s;
+        uint32_t run;
+        if (blocked) {
+            // a 32-point block is two lanes: the odd lane continues the even one
+            const uint32_t sprev = __shfl_up_sync(0xffffffffu, s, 1);
+            run = (lane & 1u) ? sprev : 0u;
+        } else {
+            run = ccarry + warp_incl_scan(s) - s;
+        }
         float v[16];
 #pragma unroll
         for (int j = 0; j < 16; j++) {
@@ -309,6 +318,48 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
         }
     }
     if (bad) atomicOr(&a.ctl->error, DERR_CORRUPT);
+}
+
+// ---------------------------------------------------------------------------
+// Per-block mode, 2D / 3D: every B^D block is reconstructed on its own as a
+// d-dimensional inclusive prefix sum of its residuals (zero padding around
+// the block), one thread per point, sums along x, then y, then z in shared
+// memory.
+
+template <int D>
+__global__ void __launch_bounds__(D == 2 ? 256 : 512) k_values_blocked(ReconArgs a, Geo g)
+{
+    constexpr uint32_t B = lorenzo_block_extent(D);
+    constexpr uint32_t NB = D == 2 ? B * B : B * B * B;
+    __shared__ uint32_t s0[NB], s1[NB];
+    if (a.ctl->error & DERR_CORRUPT) return;
+    const uint32_t t = threadIdx.x;
+    const uint32_t lx = t % B, ly = (t / B) % B, lz = D == 3 ? t / (B * B) : 0u;
+    const uint64_t nbx = (g.n[0] + B - 1) / B, nby = (g.n[1] + B - 1) / B;
+    const uint64_t nbz = D == 3 ? (g.n[2] + B - 1) / B : 1;
+    const uint64_t nblocks = nbx * nby * nbz;
+    for (uint64_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
+        const uint64_t gx = (blk % nbx) * B + lx, gy = ((blk / nbx) % nby) * B + ly;
+        const uint64_t gz = D == 3 ? (blk / (nbx * nby)) * B + lz : 0;
+        const bool in = gx < g.n[0] && gy < g.n[1] && gz < g.n[2];
+        const uint64_t idx = (gz * g.n[1] + gy) * g.n[0] + gx;
+        s0[t] = in ? delta_of(a, idx) : 0u;
+        __syncthreads();
+        uint32_t v = 0;  // along x
+        for (uint32_t k = 0; k <= lx; k++) v += s0[t - lx + k];
+        s1[t] = v;
+        __syncthreads();
+        v = 0;  // along y
+        for (uint32_t k = 0; k <= ly; k++) v += s1[t - (ly - k) * B];
+        if (D == 3) {
+            s0[t] = v;
+            __syncthreads();
+            v = 0;  // along z
+            for (uint32_t k = 0; k <= lz; k++) v += s0[t - (lz - k) * B * B];
+        }
+        if (in) a.out[idx] = recon_value((int32_t)v, a.ebx2);
+        __syncthreads();  // s0 / s1 are reused by the next block
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -525,39 +576,51 @@ void launch_reconstruct(const ReconArgs &a, cudaStream_t st, int *launches)
         nl++;
     }
     const int gridt = (int)std::min<uint64_t>(g.ntiles, (uint64_t)a.num_sms * 8);
-    if (g.ndim == 1) {
-        // tile sums were accumulated by the decoder and the outlier scatter
-        nl += launch_scan(TileOp{a.faces}, g.ntiles, a.scan_partial, st);
-    } else if (g.ndim == 2) {
-        k_faces<k2TX, k2TY, 1, k2Threads><<<gridt, k2Threads, 0, st>>>(a, g, a.faces);
+    if (a.lblock && g.ndim > 1) {
+        // per-block mode: block-local prefix sums, no carries
+        const uint32_t B = lorenzo_block_extent(g.ndim);
+        uint64_t nb = 1;
+        for (uint32_t d = 0; d < g.ndim; d++) nb *= (g.n[d] + B - 1) / B;
+        const int gridb = (int)std::min<uint64_t>(nb, (uint64_t)a.num_sms * 8);
+        if (g.ndim == 2) k_values_blocked<2><<<gridb, 256, 0, st>>>(a, g);
+        else k_values_blocked<3><<<gridb, 512, 0, st>>>(a, g);
         nl++;
     } else {
-        k_faces<k3TX, k3TY, k3TZ, k3Threads><<<gridt, k3Threads, 0, st>>>(a, g, a.faces);
-        nl++;
-    }
-    for (int A = 1; A < 8 && g.ndim > 1; A++) {
-        if (!g.size[A]) continue;
-        for (int d = 0; d < (int)g.ndim; d++) {
-            if (!((A >> d) & 1) || g.nt[d] < 2) continue;
-            const uint64_t nlines = g.size[A] * (g.ntiles / g.nt[d]);
-            if (g.nt[d] > 2048) {
-                k_scan_lines_cta<<<(unsigned)nlines, 1024, 0, st>>>(g, A, d, a.faces);
-            } else {
-                k_scan_lines<<<(unsigned)((nlines + 255) / 256), 256, 0, st>>>(g, A, d, nlines, a.faces);
-            }
+        if (g.ndim == 1) {
+            // tile sums were accumulated by the decoder and the outlier pass
+            if (!a.lblock) nl += launch_scan(TileOp{a.faces}, g.ntiles, a.scan_partial, st);
+        } else if (g.ndim == 2) {
+            k_faces<k2TX, k2TY, 1, k2Threads><<<gridt, k2Threads, 0, st>>>(a, g, a.faces);
+            nl++;
+        } else {
+            k_faces<k3TX, k3TY, k3TZ, k3Threads><<<gridt, k3Threads, 0, st>>>(a, g, a.faces);
             nl++;
         }
+        for (int A = 1; A < 8 && g.ndim > 1; A++) {
+            if (!g.size[A]) continue;
+            for (int d = 0; d < (int)g.ndim; d++) {
+                if (!((A >> d) & 1) || g.nt[d] < 2) continue;
+                const uint64_t nlines = g.size[A] * (g.ntiles / g.nt[d]);
+                if (g.nt[d] > 2048) {
+                    k_scan_lines_cta<<<(unsigned)nlines, 1024, 0, st>>>(g, A, d, a.faces);
+                } else {
+                    k_scan_lines<<<(unsigned)((nlines + 255) / 256), 256, 0, st>>>(g, A, d, nlines, a.faces);
+                }
+                nl++;
+            }
+        }
+        if (g.ndim == 1) {
+            // persistent: as many blocks as fit at once
+            const uint64_t blocks = (g.ntiles + k1Threads / 32 - 1) / (k1Threads / 32);
+            const int grid1 = (int)std::min<uint64_t>(blocks, (uint64_t)a.num_sms * 4);
+            k_values_1d<<<grid1, k1Threads, 0, st>>>(a, g, a.faces, start1d);
+        } else if (g.ndim == 2) {
+            k_values<k2TX, k2TY, 1, k2Threads><<<gridt, k2Threads, 0, st>>>(a, g, a.faces);
+        } else {
+            k_values<k3TX, k3TY, k3TZ, k3Threads><<<gridt, k3Threads, 0, st>>>(a, g, a.faces);
+        }
+        nl++;
     }
-    if (g.ndim == 1) {
-        // persistent: as many blocks as fit at once
-        const uint64_t blocks = (g.ntiles + k1Threads / 32 - 1) / (k1Threads / 32);
-        const int grid1 = (int)std::min<uint64_t>(blocks, (uint64_t)a.num_sms * 4);
-        k_values_1d<<<grid1, k1Threads, 0, st>>>(a, g, a.faces, start1d);
-    }
-    else if (g.ndim == 2)
-        k_values<k2TX, k2TY, 1, k2Threads><<<gridt, k2Threads, 0, st>>>(a, g, a.faces);
-    else k_values<k3TX, k3TY, k3TZ, k3Threads><<<gridt, k3Threads, 0, st>>>(a, g, a.faces);
-    nl++;
     if (a.e) {
         const int grid = (int)std::min<uint64_t>((a.e + 255) / 256, (uint64_t)a.num_sms * 16);
         k_patch_exceptions<<<grid, 256, 0, st>>>(a, n);

@@ -51,7 +51,8 @@ class GbszError(RuntimeError):
 
 class Params(C.Structure):
     _fields_ = [("ndim", C.c_uint32), ("dims", C.c_uint64 * 3), ("eb", C.c_double),
-                ("eb_mode", C.c_uint32), ("radius", C.c_uint32), ("chunk", C.c_uint32)]
+                ("eb_mode", C.c_uint32), ("radius", C.c_uint32), ("chunk", C.c_uint32),
+                ("lorenzo_block", C.c_uint32)]
 
 
 _lib = None
@@ -76,14 +77,16 @@ def status_str(s):
     return load().gbsz_status_str(int(s)).decode()
 
 
-def make_params(dims, eb, eb_mode=EB_REL, radius=512, chunk=0):
-    """dims: extents with the fastest-varying first (x, y, z)."""
+def make_params(dims, eb, eb_mode=EB_REL, radius=512, chunk=0, lblock=0):
+    """dims: extents with the fastest-varying first (x, y, z).  lblock = 1:
+    Lorenzo inside the paper's blocks (see gbsz_params.lorenzo_block)."""
     dims = [int(d) for d in dims]
     p = Params()
     p.ndim = len(dims)
     for i in range(3):
         p.dims[i] = dims[i] if i < len(dims) else 1
     p.eb, p.eb_mode, p.radius, p.chunk = float(eb), int(eb_mode), int(radius), int(chunk)
+    p.lorenzo_block = int(lblock)
     return p
 
 
@@ -92,8 +95,8 @@ def field_dims(t):
     return list(t.shape)[::-1]
 
 
-def compress_bound(dims, eb=1e-4, eb_mode=EB_REL, radius=512, chunk=0):
-    return load().gbsz_compress_bound(C.byref(make_params(dims, eb, eb_mode, radius, chunk)))
+def compress_bound(dims, eb=1e-4, eb_mode=EB_REL, radius=512, chunk=0, lblock=0):
+    return load().gbsz_compress_bound(C.byref(make_params(dims, eb, eb_mode, radius, chunk, lblock)))
 
 
 def _stream(stream=None):
@@ -125,11 +128,11 @@ class Context:
             pass
 
     # -- device-buffer API -------------------------------------------------
-    def compress(self, field, eb, eb_mode=EB_REL, radius=512, chunk=0, out=None, stream=None):
+    def compress(self, field, eb, eb_mode=EB_REL, radius=512, chunk=0, out=None, stream=None, lblock=0):
         """field: contiguous float32 CUDA tensor (C order, last axis fastest).
         Returns (archive uint8 tensor on the device, nbytes)."""
         assert field.is_cuda and field.dtype == torch.float32 and field.is_contiguous()
-        p = make_params(field_dims(field), eb, eb_mode, radius, chunk)
+        p = make_params(field_dims(field), eb, eb_mode, radius, chunk, lblock)
         cap = load().gbsz_compress_bound(C.byref(p))
         if cap == 0:
             raise GbszError(ERR_INVALID_ARG, "compress_bound")
@@ -206,11 +209,12 @@ class Context:
         return outs, list(sts)
 
     # -- host-buffer API ---------------------------------------------------
-    def compress_host(self, field_np, eb, eb_mode=EB_REL, radius=512, chunk=0, out=None, stream=None):
+    def compress_host(self, field_np, eb, eb_mode=EB_REL, radius=512, chunk=0, out=None, stream=None,
+                      lblock=0):
         """field_np: contiguous float32 numpy array (or pinned CPU tensor)."""
         import numpy as np
         ptr, shape = _host_ptr(field_np)
-        p = make_params(shape[::-1], eb, eb_mode, radius, chunk)
+        p = make_params(shape[::-1], eb, eb_mode, radius, chunk, lblock)
         cap = load().gbsz_compress_bound(C.byref(p))
         if out is None:
             out = np.empty(cap, dtype=np.uint8)

@@ -23,18 +23,18 @@ def ctx(gb):
     c.close()
 
 
-def compare_stages(gb, ctx, x, eb, eb_mode, R, C):
+def compare_stages(gb, ctx, x, eb, eb_mode, R, C, lblock=0):
     """Compress on the GPU and with the oracle; assert each stage equal.
     Returns (gpu archive tensor, nbytes, oracle archive)."""
     xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
-    arc, nb = ctx.compress(xt, eb, eb_mode, R, C)
+    arc, nb = ctx.compress(xt, eb, eb_mode, R, C, lblock=lblock)
     torch.cuda.synchronize()
     ga = arc[:nb].cpu().numpy()
     n = x.size
     sc = ref.error_bound(x, eb, eb_mode)
     gsc = ctx.debug_copy(gb.DEBUG_SCALARS, 3, np.float32)
     assert np.array_equal(gsc.view(np.uint32), sc.view(np.uint32)), (gsc, sc)
-    dq = ref.dualquant(x, sc, R)
+    dq = ref.dualquant(x, sc, R, lblock=lblock)
     gcodes = ctx.debug_copy(gb.DEBUG_CODES, n, np.uint16)
     if not np.array_equal(gcodes, dq["codes"]):
         bad = np.flatnonzero(gcodes != dq["codes"])
@@ -49,7 +49,7 @@ def compare_stages(gb, ctx, x, eb, eb_mode, R, C):
     gs = ref.sections(ga)
     assert np.array_equal(gs["len"], ln), "code lengths differ"
     assert np.array_equal(gcw, cw), "canonical codewords differ"
-    oa = ref.compress(x, eb, eb_mode, radius=R, chunk=C)
+    oa = ref.compress(x, eb, eb_mode, radius=R, chunk=C, lblock=lblock)
     os_ = ref.sections(oa)
     for key in ("maxlen", "m", "e", "words", "nchunk"):
         assert gs[key] == os_[key], (key, gs[key], os_[key])
@@ -73,7 +73,9 @@ def check_decompress(gb, ctx, arc, nb, oa, x, eb, eb_mode):
         bad = np.flatnonzero(y.view(np.uint32).ravel() != yo.view(np.uint32).ravel())
         raise AssertionError(f"reconstruction differs at {bad.size} points, first {bad[:8]}")
     dcodes = ctx.debug_copy(gb.DEBUG_DECODED, x.size, np.uint16)
-    assert np.array_equal(dcodes, ref.dualquant(x, ref.error_bound(x, eb, eb_mode), ref.sections(oa)["radius"])["codes"])
+    s_ = ref.sections(oa)
+    assert np.array_equal(dcodes, ref.dualquant(x, ref.error_bound(x, eb, eb_mode), s_["radius"],
+                                                lblock=s_["lblock"])["codes"])
     sc = ref.error_bound(x, eb, eb_mode)
     fin = np.isfinite(x)
     err = np.abs(x[fin].astype(np.float64) - y[fin].astype(np.float64))
@@ -222,3 +224,23 @@ def test_codes_longer_than_a_word(gb, ctx):
     arc, nb, oa = compare_stages(gb, ctx, x, 0.5, ref.EB_ABS, 512, 4096)
     assert ref.sections(oa)["maxlen"] == 34
     check_decompress(gb, ctx, arc, nb, oa, x, 0.5, ref.EB_ABS)
+
+
+BLOCK_CASES = [
+    # the paper's per-block Lorenzo (Sec. 3.1.1): 32 / 16x16 / 8x8x8 blocks with zero padding
+    ("walk", (100003,), 1e-4, ref.EB_REL, 512, 4096),
+    ("walk", (70001,), 1e-4, ref.EB_REL, 16, 1024),
+    ("sinus", (181, 1037), 1e-4, ref.EB_REL, 512, 1024),
+    ("grf", (150, 170), 1e-5, ref.EB_REL, 64, 256),
+    ("lognormal", (37, 41, 67), 1e-3, ref.EB_REL, 512, 256),
+    ("sinus", (20, 9, 33), 1e-4, ref.EB_REL, 64, 64),
+]
+
+
+@pytest.mark.parametrize("kind,shape,eb,mode,R,C", BLOCK_CASES,
+                         ids=[f"blk-{c[0]}{'x'.join(map(str, c[1]))}-R{c[4]}" for c in BLOCK_CASES])
+def test_parity_per_block_lorenzo(gb, ctx, kind, shape, eb, mode, R, C):
+    x = workloads.field_for(kind, shape, seed=sum(shape) + 3 * R)
+    arc, nb, oa = compare_stages(gb, ctx, x, eb, mode, R, C, lblock=1)
+    assert ref.sections(oa)["lblock"] == 1
+    check_decompress(gb, ctx, arc, nb, oa, x, eb, mode)
