@@ -59,18 +59,22 @@ def batch_vs_per_field(ctx, gbsz, workloads, dev, steps=5):
     arcs = [torch.empty(gbsz.compress_bound(gbsz.field_dims(f), 1e-4), dtype=torch.uint8, device=dev)
             for f in fields]
     outs = [torch.empty_like(f) for f in fields]
-    stream = torch.cuda.current_stream(dev)
+    # a stream of its own: batch calls on it are captured once as CUDA graphs
+    # and replayed (the legacy default stream cannot be captured)
+    stream = torch.cuda.Stream(dev)
+    stream.wait_stream(torch.cuda.current_stream(dev))
 
     def per_field():
         for f, a, o in zip(fields, arcs, outs):
-            _, nb = ctx.compress(f, 1e-4, out=a)
-            ctx.decompress(a, nb, out=o)
+            _, nb = ctx.compress(f, 1e-4, out=a, stream=stream)
+            ctx.decompress(a, nb, out=o, stream=stream)
 
     def batched():
-        _, nbs, _ = ctx.compress_batch(fields, None, outs=arcs, params=params)
-        ctx.decompress_batch(arcs, nbs, outs)
+        _, nbs, _ = ctx.compress_batch(fields, None, outs=arcs, params=params, stream=stream)
+        ctx.decompress_batch(arcs, nbs, outs, stream=stream)
 
     res = {}
+    g0 = ctx.debug_copy(gbsz.DEBUG_GRAPHS, 4, np.uint64)
     for name, fn in (("per_field", per_field), ("batched", batched)):
         for _ in range(2):
             fn()
@@ -82,13 +86,20 @@ def batch_vs_per_field(ctx, gbsz, workloads, dev, steps=5):
         e1.record(stream)
         torch.cuda.synchronize(dev)
         res[name] = 4.0 * n_all / (e0.elapsed_time(e1) / steps / 1e3) / 1e9
-    # batched results are the single-field results
-    single, nb1 = ctx.compress(fields[5], 1e-4)
-    _, nbs, _ = ctx.compress_batch(fields, None, outs=arcs, params=params)
+    # batched (graph-replayed) results are the single-field results
+    single, nb1 = ctx.compress(fields[5], 1e-4, stream=stream)
+    _, nbs, _ = ctx.compress_batch(fields, None, outs=arcs, params=params, stream=stream)
+    stream.synchronize()
     assert nbs[5] == nb1 and torch.equal(arcs[5][:nb1], single[:nb1])
+    y5 = ctx.decompress(arcs[5], nbs[5], stream=stream)
+    ctx.decompress_batch(arcs, nbs, outs, stream=stream)
+    stream.synchronize()
+    assert torch.equal(outs[5].view(torch.int32), y5.view(torch.int32))
+    g1 = ctx.debug_copy(gbsz.DEBUG_GRAPHS, 4, np.uint64)
     return {"workload": "16 x 1800x3600 FP32 power-law fields, rel eb 1e-4, radius 512",
             "per_field_gbs": res["per_field"], "batched_gbs": res["batched"],
-            "speedup": res["batched"] / res["per_field"], "steps": steps}
+            "speedup": res["batched"] / res["per_field"], "steps": steps,
+            "graph_replays": int(g1[1] - g0[1] + g1[3] - g0[3])}
 
 
 def workload_config(a, n, chunk):

@@ -91,8 +91,22 @@ void gbsz_destroy(gbsz_ctx *ctx);
  * Host-only, no device work. */
 size_t gbsz_compress_bound(const gbsz_params *p);
 
-/* Chunk size that chunk = 0 resolves to for these parameters. */
+/* Chunk size that chunk = 0 resolves to for these parameters (a fixed rule
+ * of n: about 1024 chunks per SM of a GB300, 64..4096 symbols). */
 uint32_t gbsz_auto_chunk(const gbsz_params *p);
+
+/* Measured choice of the Huffman chunk (Sec. 3.2.4; the paper tunes it by
+ * hand, Sec. 4.2).  Times compress + decompress of the field at d_field for
+ * chunk sizes 256..4096 and the rule's choice on `stream` (CUDA events, best
+ * of two runs each), and writes *out = *p with the fastest chunk.  The choice
+ * is remembered per context for the key (ndim, dims, radius, lorenzo_block):
+ * later calls with the same key return it without measuring, so every
+ * single or batched call given *out produces the same archive.  *ms (may be
+ * NULL) gets the measured time of the chosen chunk (0 when remembered).
+ * Allocates scratch for one archive and one field.  Errors: INVALID_ARG,
+ * OOM, CUDA, and any error of the compress/decompress calls it makes. */
+gbsz_status gbsz_autotune(gbsz_ctx *ctx, const float *d_field, const gbsz_params *p,
+                          gbsz_params *out, float *ms, void *stream);
 
 /* Compresses n = prod(dims) floats at d_field into the archive at d_archive
  * (device memory, 16-byte aligned, `capacity` bytes).  Stages: S0 error
@@ -169,6 +183,8 @@ const char *gbsz_status_str(gbsz_status s);
  *   2 error-bound scalars of the last compress (float[3]: eb, 2eb, 1/(2eb))
  *   3 quant codes decoded by the last decompress (uint16[n])
  *   4 canonical codewords of the last compress (uint64[2R]: code, no length)
+ *   5 batch graph counters (uint64[4]: compress captures, compress replays,
+ *     decompress captures, decompress replays)
  * `bytes` must equal the buffer's size.  Synchronises the context's last
  * stream.  Errors: INVALID_ARG, CUDA. */
 gbsz_status gbsz_debug_copy(gbsz_ctx *ctx, int which, void *h_dst,

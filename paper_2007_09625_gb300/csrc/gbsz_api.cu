@@ -15,6 +15,7 @@
 #include "scan.cuh"
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <cstring>
 #include <new>
@@ -41,12 +42,17 @@ struct DevGuard {
     }
 };
 
+// Bumped whenever any scratch buffer of any context is allocated or freed:
+// a captured batch graph is replayed only if nothing it points into moved.
+std::atomic<uint64_t> g_alloc_gen{1};
+
 struct Buf {
     void *p = nullptr;
     size_t cap = 0;
     bool ensure(size_t bytes)
     {
         if (bytes <= cap && p) return true;
+        g_alloc_gen.fetch_add(1);
         if (p) cudaFree(p);
         p = nullptr;
         cap = 0;
@@ -61,7 +67,10 @@ struct Buf {
     }
     void release()
     {
-        if (p) cudaFree(p);
+        if (p) {
+            g_alloc_gen.fetch_add(1);
+            cudaFree(p);
+        }
         p = nullptr;
         cap = 0;
     }
@@ -75,6 +84,7 @@ template <typename T> struct HostBuf {
     bool ensure(size_t count)
     {
         if (count <= cap && p) return true;
+        g_alloc_gen.fetch_add(1);
         if (p) cudaFreeHost(p);
         p = nullptr;
         cap = 0;
@@ -88,9 +98,31 @@ template <typename T> struct HostBuf {
     }
     void release()
     {
-        if (p) cudaFreeHost(p);
+        if (p) {
+            g_alloc_gen.fetch_add(1);
+            cudaFreeHost(p);
+        }
         p = nullptr;
         cap = 0;
+    }
+};
+
+// A batch call recorded as a CUDA graph.  The key is every input of the
+// call that shapes its launches (pointers, parameters, parsed headers) plus
+// the allocation generation; the first call with a key runs eagerly, the
+// second is captured, later ones replay the graph (one launch instead of
+// about a dozen kernels, copies and memsets per field).
+struct BatchGraph {
+    std::vector<uint64_t> key;   // key of the captured graph
+    std::vector<uint64_t> seen;  // key of the last eager call
+    cudaGraphExec_t exec = nullptr;
+    uint64_t launches = 0;       // kernels in one replay
+    uint64_t captures = 0, replays = 0;
+    void drop()
+    {
+        if (exec) cudaGraphExecDestroy(exec);
+        exec = nullptr;
+        key.clear();
     }
 };
 
@@ -161,6 +193,11 @@ struct gbsz_ctx {
     uint32_t last_nbins = 0;
     float last_sc[3] = {0, 0, 0};  // error-bound scalars of the last compress
     bool have_compress = false, have_decompress = false;
+    // captured batch calls
+    BatchGraph gcomp, gdecomp;
+    // autotuned chunks, keyed by (ndim, dims, radius, lorenzo_block)
+    std::vector<std::pair<std::vector<uint64_t>, uint32_t>> tuned;
+    Buf tune_arc, tune_out;
     // timing
     bool profiling = false;
     std::vector<StageRec> recs;
@@ -348,17 +385,31 @@ gbsz_status check_compress(const float *d_field, const gbsz_params *pin, const v
     return GBSZ_OK;
 }
 
+// Sizes a slot's scratch for one field (allocates only when it grows).
+bool reserve_compress(Slot *s, const gbsz_params &p, uint64_t n)
+{
+    const uint64_t nunits = encode_units(n, p.chunk);
+    return s->codes.ensure(n * 2 + 64) && s->dscr.ensure(n * 8 + 64) && s->unit_tot.ensure(nunits * 16) &&
+           s->lane_bits.ensure((n / 64 + 64) * 4) && s->unit_off.ensure(nunits * 16) &&
+           s->unit_part.ensure(scan_partials(nunits) * 16 + 64) && s->unit_exc.ensure(nunits * 4);
+}
+
+bool reserve_decompress(Slot *s, const Header &h)
+{
+    const uint64_t n = h.n;
+    const uint64_t nfaces = recon_faces_entries(h.p.ndim, h.p.dims);
+    const uint64_t nscan = std::max<uint64_t>(h.nchunk, nfaces);
+    return s->codes.ensure(n * 2 + 64) && s->dscr.ensure(n * 8 + 64) && s->chunk_off.ensure(h.nchunk * 8 + 8) &&
+           s->faces.ensure(nfaces * 4 + 16) && s->scan_part.ensure(scan_partials(nscan) * 8 + 64);
+}
+
 // Enqueues S0-S6 of one field on stream st using slot s; no synchronisation.
 gbsz_status enqueue_compress(gbsz_ctx *c, Slot *s, const float *d_field, const gbsz_params &p, uint64_t n,
                              void *d_archive, size_t capacity, cudaStream_t st)
 {
     const uint32_t nbins = 2 * p.radius;
     const uint64_t nunits = encode_units(n, p.chunk);
-    if (!s->codes.ensure(n * 2 + 64) || !s->dscr.ensure(n * 8 + 64) || !s->unit_tot.ensure(nunits * 16) ||
-        !s->lane_bits.ensure((n / 64 + 64) * 4) ||
-        !s->unit_off.ensure(nunits * 16) || !s->unit_part.ensure(scan_partials(nunits) * 16 + 64) ||
-        !s->unit_exc.ensure(nunits * 4))
-        return GBSZ_ERR_OOM;
+    if (!reserve_compress(s, p, n)) return GBSZ_ERR_OOM;
     cudaMemsetAsync(s->ctl, 0, sizeof(Control), st);
     cudaMemsetAsync(s->hist.p, 0, nbins * 4, st);
     cudaMemsetAsync(s->unit_exc.p, 0, nunits * 4, st);
@@ -433,10 +484,7 @@ gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void
 {
     const uint64_t n = h.n;
     const uint64_t nfaces = recon_faces_entries(h.p.ndim, h.p.dims);
-    const uint64_t nscan = std::max<uint64_t>(h.nchunk, nfaces);
-    if (!s->codes.ensure(n * 2 + 64) || !s->dscr.ensure(n * 8 + 64) || !s->chunk_off.ensure(h.nchunk * 8 + 8) ||
-        !s->faces.ensure(nfaces * 4 + 16) || !s->scan_part.ensure(scan_partials(nscan) * 8 + 64))
-        return GBSZ_ERR_OOM;
+    if (!reserve_decompress(s, h)) return GBSZ_ERR_OOM;
     cudaMemsetAsync(s->ctl, 0, sizeof(Control), st);
     if (h.p.ndim == 1) cudaMemsetAsync(s->faces.p, 0, nfaces * 4, st);  // tile sums
     const uint8_t *arc = static_cast<const uint8_t *>(d_archive);
@@ -519,6 +567,60 @@ gbsz_status decompress_status(const Control &ctl, const Header &h)
 
 }  // namespace
 
+namespace {
+
+// Runs `enqueue` (which forks the caller's stream st to the slot streams and
+// joins them back) either eagerly, or through the context's graph for this
+// kind of batch: replayed if `key` matches the captured one, captured if it
+// matches the previous eager call's.  Profiling always runs eagerly (its
+// events are recorded at enqueue time).
+template <typename F>
+gbsz_status run_batch(gbsz_ctx *c, BatchGraph &bg, std::vector<uint64_t> &key, cudaStream_t st, F enqueue)
+{
+    key.push_back(g_alloc_gen.load());
+    if (!c->profiling && bg.exec && key == bg.key) {
+        c->launches += bg.launches;
+        bg.replays++;
+        return cudaGraphLaunch(bg.exec, st) == cudaSuccess ? GBSZ_OK : GBSZ_ERR_CUDA;
+    }
+    if (!c->profiling && key == bg.seen) {
+        bg.drop();
+        const uint64_t l0 = c->launches;
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            const gbsz_status es = enqueue();
+            const cudaError_t ce = cudaStreamEndCapture(st, &graph);
+            if (es == GBSZ_OK && ce == cudaSuccess && graph &&
+                cudaGraphInstantiate(&bg.exec, graph, 0) == cudaSuccess && key.back() == g_alloc_gen.load()) {
+                cudaGraphDestroy(graph);
+                bg.key = key;
+                bg.launches = c->launches - l0;
+                bg.captures++;
+                return cudaGraphLaunch(bg.exec, st) == cudaSuccess ? GBSZ_OK : GBSZ_ERR_CUDA;
+            }
+            if (graph) cudaGraphDestroy(graph);
+            bg.drop();
+        }
+        cudaGetLastError();  // a failed capture leaves nothing behind; run eagerly
+        c->launches = l0;
+    }
+    const gbsz_status es = enqueue();
+    bg.seen = key;
+    return es;
+}
+
+inline void key_add(std::vector<uint64_t> &k, const void *p, size_t bytes)
+{
+    const uint8_t *b = static_cast<const uint8_t *>(p);
+    for (size_t i = 0; i < bytes; i += 8) {
+        uint64_t v = 0;
+        std::memcpy(&v, b + i, std::min<size_t>(8, bytes - i));
+        k.push_back(v);
+    }
+}
+
+}  // namespace
+
 extern "C" {
 
 const char *gbsz_status_str(gbsz_status s)
@@ -573,6 +675,10 @@ void gbsz_destroy(gbsz_ctx *c)
         delete s;
     }
     c->slots.clear();
+    c->gcomp.drop();
+    c->gdecomp.drop();
+    c->tune_arc.release();
+    c->tune_out.release();
     c->stage_field.release();
     c->stage_archive.release();
     c->ctl_host.release();
@@ -591,6 +697,64 @@ uint32_t gbsz_auto_chunk(const gbsz_params *p)
     uint64_t n;
     if (!valid_params(p, &n)) return 0;
     return p->chunk ? p->chunk : auto_chunk(n);
+}
+
+gbsz_status gbsz_autotune(gbsz_ctx *c, const float *d_field, const gbsz_params *p, gbsz_params *out, float *ms,
+                          void *stream)
+{
+    uint64_t n;
+    if (!c || !d_field || !p || !out || !valid_params(p, &n)) return GBSZ_ERR_INVALID_ARG;
+    DevGuard g(c->device);
+    const std::vector<uint64_t> key{p->ndim, p->dims[0], p->dims[1], p->dims[2], p->radius, p->lorenzo_block};
+    *out = *p;
+    if (ms) *ms = 0.0f;
+    for (const auto &t : c->tuned)
+        if (t.first == key) {
+            out->chunk = t.second;
+            return GBSZ_OK;
+        }
+    std::vector<uint32_t> cand{256, 512, 1024, 2048, 4096};
+    const uint32_t rule = auto_chunk(n);
+    if (std::find(cand.begin(), cand.end(), rule) == cand.end()) cand.push_back(rule);
+    gbsz_params q = *p;
+    size_t cap = 0;
+    for (uint32_t C : cand) {
+        q.chunk = C;
+        cap = std::max(cap, gbsz_compress_bound(&q));
+    }
+    if (!c->tune_arc.ensure(cap) || !c->tune_out.ensure(n * 4)) return GBSZ_ERR_OOM;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = c->ev(), e1 = c->ev();
+    float best = -1.0f;
+    uint32_t best_c = rule;
+    gbsz_status status = GBSZ_OK;
+    for (uint32_t C : cand) {
+        q.chunk = C;
+        float tmin = -1.0f;
+        for (int rep = 0; rep < 3 && status == GBSZ_OK; rep++) {  // the first run is a warm-up
+            size_t nb = 0;
+            cudaEventRecord(e0, st);
+            status = gbsz_compress(c, d_field, &q, c->tune_arc.p, cap, &nb, stream);
+            if (status == GBSZ_OK) status = gbsz_decompress(c, c->tune_arc.p, nb, c->tune_out.as<float>(), n, stream);
+            cudaEventRecord(e1, st);
+            if (cudaEventSynchronize(e1) != cudaSuccess) status = GBSZ_ERR_CUDA;
+            float t = 0.0f;
+            cudaEventElapsedTime(&t, e0, e1);
+            if (rep > 0 && (tmin < 0.0f || t < tmin)) tmin = t;
+        }
+        if (status != GBSZ_OK) break;
+        if (best < 0.0f || tmin < best) {
+            best = tmin;
+            best_c = C;
+        }
+    }
+    c->pool.push_back(e0);
+    c->pool.push_back(e1);
+    if (status != GBSZ_OK) return status;
+    c->tuned.push_back({key, best_c});
+    out->chunk = best_c;
+    if (ms) *ms = best;
+    return GBSZ_OK;
 }
 
 size_t gbsz_compress_bound(const gbsz_params *p)
@@ -695,19 +859,38 @@ gbsz_status gbsz_compress_batch(gbsz_ctx *c, uint32_t count, const float *const 
         statuses[i] = check_compress(d_fields[i], &params[i], d_archives[i], capacities[i], &rp[i], &rn[i], &need);
         if (statuses[i] == GBSZ_ERR_CAPACITY) out_bytes[i] = need;
     }
-    cudaEventRecord(c->fork, st);
-    for (int k = 0; k < K; k++) cudaStreamWaitEvent(c->slots[k]->stream, c->fork, 0);
+    // slot scratch is sized before any capture (a graph must not allocate)
+    for (uint32_t i = 0; i < count; i++)
+        if (statuses[i] == GBSZ_OK && !reserve_compress(c->slots[i % K], rp[i], rn[i])) statuses[i] = GBSZ_ERR_OOM;
+    std::vector<uint64_t> key{0xC0u, count, (uint64_t)K, (uint64_t)(uintptr_t)c->ctl_host.p};
     for (uint32_t i = 0; i < count; i++) {
-        if (statuses[i] != GBSZ_OK) continue;
-        Slot *sl = c->slots[i % K];
-        statuses[i] = enqueue_compress(c, sl, d_fields[i], rp[i], rn[i], d_archives[i], capacities[i], sl->stream);
-        if (statuses[i] == GBSZ_OK)
-            cudaMemcpyAsync(&c->ctl_host.p[i], sl->ctl, sizeof(Control), cudaMemcpyDeviceToHost, sl->stream);
+        key_add(key, &d_fields[i], sizeof(void *));
+        key_add(key, &d_archives[i], sizeof(void *));
+        key_add(key, &capacities[i], sizeof(size_t));
+        key.insert(key.end(), {rp[i].ndim, rp[i].dims[0], rp[i].dims[1], rp[i].dims[2], rp[i].eb_mode,
+                               rp[i].radius, rp[i].chunk, rp[i].lorenzo_block});
+        key_add(key, &rp[i].eb, sizeof(double));
+        key.push_back((uint64_t)statuses[i]);
     }
-    for (int k = 0; k < K; k++) {
-        cudaEventRecord(c->slots[k]->done, c->slots[k]->stream);
-        cudaStreamWaitEvent(st, c->slots[k]->done, 0);
-    }
+    auto enqueue = [&]() -> gbsz_status {
+        cudaEventRecord(c->fork, st);
+        for (int k = 0; k < K; k++) cudaStreamWaitEvent(c->slots[k]->stream, c->fork, 0);
+        gbsz_status es = GBSZ_OK;
+        for (uint32_t i = 0; i < count && es == GBSZ_OK; i++) {
+            if (statuses[i] != GBSZ_OK) continue;
+            Slot *sl = c->slots[i % K];
+            es = enqueue_compress(c, sl, d_fields[i], rp[i], rn[i], d_archives[i], capacities[i], sl->stream);
+            if (es == GBSZ_OK)
+                cudaMemcpyAsync(&c->ctl_host.p[i], sl->ctl, sizeof(Control), cudaMemcpyDeviceToHost, sl->stream);
+        }
+        for (int k = 0; k < K; k++) {  // always joined, so a capture can end cleanly
+            cudaEventRecord(c->slots[k]->done, c->slots[k]->stream);
+            cudaStreamWaitEvent(st, c->slots[k]->done, 0);
+        }
+        return es;
+    };
+    const gbsz_status es = run_batch(c, c->gcomp, key, st, enqueue);
+    if (es != GBSZ_OK) return es;
     if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GBSZ_ERR_CUDA;
     gbsz_status first = GBSZ_OK;
     for (uint32_t i = 0; i < count; i++) {
@@ -753,19 +936,35 @@ gbsz_status gbsz_decompress_batch(gbsz_ctx *c, uint32_t count, const void *const
         statuses[i] = parse_header(c->h_header.p + (size_t)i * kHeaderBytes, bytes[i], &hs[i]);
         if (statuses[i] == GBSZ_OK && hs[i].n > capacities[i]) statuses[i] = GBSZ_ERR_CAPACITY;
     }
-    cudaEventRecord(c->fork, st);
-    for (int k = 0; k < K; k++) cudaStreamWaitEvent(c->slots[k]->stream, c->fork, 0);
+    for (uint32_t i = 0; i < count; i++)
+        if (statuses[i] == GBSZ_OK && !reserve_decompress(c->slots[i % K], hs[i])) statuses[i] = GBSZ_ERR_OOM;
+    std::vector<uint64_t> key{0xDEu, count, (uint64_t)K, (uint64_t)(uintptr_t)c->ctl_host.p};
     for (uint32_t i = 0; i < count; i++) {
-        if (statuses[i] != GBSZ_OK) continue;
-        Slot *sl = c->slots[i % K];
-        statuses[i] = enqueue_decompress(c, sl, hs[i], d_archives[i], d_fields[i], sl->stream);
-        if (statuses[i] == GBSZ_OK)
-            cudaMemcpyAsync(&c->ctl_host.p[i], sl->ctl, sizeof(Control), cudaMemcpyDeviceToHost, sl->stream);
+        key_add(key, &d_archives[i], sizeof(void *));
+        key_add(key, &d_fields[i], sizeof(void *));
+        key_add(key, &bytes[i], sizeof(size_t));
+        key.push_back((uint64_t)statuses[i]);
+        if (statuses[i] == GBSZ_OK) key_add(key, c->h_header.p + (size_t)i * kHeaderBytes, kHeaderBytes);
     }
-    for (int k = 0; k < K; k++) {
-        cudaEventRecord(c->slots[k]->done, c->slots[k]->stream);
-        cudaStreamWaitEvent(st, c->slots[k]->done, 0);
-    }
+    auto enqueue = [&]() -> gbsz_status {
+        cudaEventRecord(c->fork, st);
+        for (int k = 0; k < K; k++) cudaStreamWaitEvent(c->slots[k]->stream, c->fork, 0);
+        gbsz_status es = GBSZ_OK;
+        for (uint32_t i = 0; i < count && es == GBSZ_OK; i++) {
+            if (statuses[i] != GBSZ_OK) continue;
+            Slot *sl = c->slots[i % K];
+            es = enqueue_decompress(c, sl, hs[i], d_archives[i], d_fields[i], sl->stream);
+            if (es == GBSZ_OK)
+                cudaMemcpyAsync(&c->ctl_host.p[i], sl->ctl, sizeof(Control), cudaMemcpyDeviceToHost, sl->stream);
+        }
+        for (int k = 0; k < K; k++) {  // always joined, so a capture can end cleanly
+            cudaEventRecord(c->slots[k]->done, c->slots[k]->stream);
+            cudaStreamWaitEvent(st, c->slots[k]->done, 0);
+        }
+        return es;
+    };
+    const gbsz_status es = run_batch(c, c->gdecomp, key, st, enqueue);
+    if (es != GBSZ_OK) return es;
     if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GBSZ_ERR_CUDA;
     gbsz_status first = GBSZ_OK;
     for (uint32_t i = 0; i < count; i++) {
@@ -832,6 +1031,12 @@ gbsz_status gbsz_debug_copy(gbsz_ctx *c, int which, void *h_dst, size_t bytes)
         return GBSZ_OK;
     case 3: src = sl->codes.p; need = c->have_decompress ? c->last_dn * 2 : 0; break;
     case 4: src = sl->codes_only.p; need = c->have_compress ? c->last_nbins * 8 : 0; break;
+    case 5: {
+        if (bytes != 32) return GBSZ_ERR_INVALID_ARG;
+        const uint64_t v[4] = {c->gcomp.captures, c->gcomp.replays, c->gdecomp.captures, c->gdecomp.replays};
+        std::memcpy(h_dst, v, 32);
+        return GBSZ_OK;
+    }
     default: return GBSZ_ERR_INVALID_ARG;
     }
     if (need == 0 || bytes != need) return GBSZ_ERR_INVALID_ARG;

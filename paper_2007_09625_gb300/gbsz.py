@@ -18,7 +18,7 @@ EB_ABS, EB_REL = 0, 1
 NSTAGE = 11
 STAGES = ["error_bound", "dualquant_hist", "codebook", "encode_count", "encode_scan", "encode_pack",
           "decode_tables", "decode_offsets", "decode", "reconstruct", "other"]
-DEBUG_CODES, DEBUG_HIST, DEBUG_SCALARS, DEBUG_DECODED, DEBUG_CODEWORDS = range(5)
+DEBUG_CODES, DEBUG_HIST, DEBUG_SCALARS, DEBUG_DECODED, DEBUG_CODEWORDS, DEBUG_GRAPHS = range(6)
 
 # every entry point of include/gbsz.h with its ctypes signature
 _P = C.c_void_p
@@ -39,6 +39,7 @@ SIGNATURES = {
     "gbsz_codebook_noalloc": ([_P, C.c_uint32, _P, _P, C.POINTER(C.c_uint32), _P], C.c_int),
     "gbsz_compress_batch": ([_P, C.c_uint32, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "gbsz_decompress_batch": ([_P, C.c_uint32, _P, _P, _P, _P, _P, _P], C.c_int),
+    "gbsz_autotune": ([_P, _P, _P, _P, C.POINTER(C.c_float), _P], C.c_int),
 }
 
 
@@ -144,6 +145,28 @@ class Context:
         if st != OK:
             raise GbszError(st, "gbsz_compress")
         return out, nbytes.value
+
+    def autotune(self, field, eb, eb_mode=EB_REL, radius=512, lblock=0, stream=None):
+        """Measured chunk choice for this field's (rank, dims, radius) (see
+        gbsz_autotune).  Returns (Params with the chosen chunk, ms)."""
+        p = make_params(field_dims(field), eb, eb_mode, radius, 0, lblock)
+        out = Params()
+        ms = C.c_float()
+        st = load().gbsz_autotune(self.h, C.c_void_p(field.data_ptr()), C.byref(p), C.byref(out), C.byref(ms),
+                                  _stream(stream))
+        if st != OK:
+            raise GbszError(st, "gbsz_autotune")
+        return out, ms.value
+
+    def compress_params(self, field, params, out=None, stream=None):
+        """Compress with an explicit Params (e.g. from autotune)."""
+        cap = load().gbsz_compress_bound(C.byref(params))
+        if out is None:
+            out = torch.empty(cap, dtype=torch.uint8, device=field.device)
+        st, nb = self.compress_status(field, params, out, stream)
+        if st != OK:
+            raise GbszError(st, "gbsz_compress")
+        return out, nb
 
     def compress_status(self, field, params, out, stream=None):
         """Raw status call: returns (status, nbytes) without raising."""

@@ -84,3 +84,66 @@ def test_batch_reports_per_field_errors(gb, ctx):
     for i in (0, 1, 3):
         single, n1 = ctx.compress(ts[i], 1e-4)
         assert nb[i] == n1 and torch.equal(outs[i][:n1], single[:n1])
+
+
+def test_batch_graph_replay_follows_new_data(gb, ctx):
+    """On a stream of its own, the second identical batch call is captured as
+    a CUDA graph and later ones replay it: replays must read the fields'
+    current contents, and a changed parameter or header must not replay."""
+    s = torch.cuda.Stream()
+    fields = mixed_fields(5, seed=600)
+    ts = [torch.from_numpy(f).cuda() for f in fields]
+    params = [gb.make_params(gb.field_dims(t), 1e-4) for t in ts]
+    arcs = [torch.empty(gb.load().gbsz_compress_bound(__import__("ctypes").byref(p)), dtype=torch.uint8,
+                        device="cuda") for p in params]
+    outs = [torch.empty_like(t) for t in ts]
+    torch.cuda.synchronize()
+
+    def run():
+        _, nbs, sts = ctx.compress_batch(ts, None, outs=arcs, params=params, stream=s)
+        ctx.decompress_batch(arcs, nbs, outs, stream=s)
+        s.synchronize()
+        return list(nbs)
+
+    def check(nbs):
+        for i, f in enumerate(fields):
+            oa = ref.compress(f, 1e-4, ref.EB_REL, 512, gb.auto_chunk(list(f.shape)[::-1], 512))
+            assert nbs[i] == oa.size and np.array_equal(arcs[i][:nbs[i]].cpu().numpy(), oa), i
+            assert np.array_equal(outs[i].cpu().numpy().view(np.uint32), ref.decompress(oa).view(np.uint32)), i
+
+    g0 = ctx.debug_copy(gb.DEBUG_GRAPHS, 4, np.uint64)
+    for _ in range(4):  # eager (allocates), eager or captured, then replayed
+        check(run())
+    g1 = ctx.debug_copy(gb.DEBUG_GRAPHS, 4, np.uint64)
+    assert all(int(v) >= 1 for v in g1 - g0), (g0, g1)  # each kind captured and replayed
+    # same pointers and parameters, new contents: the replay must see them
+    rng = np.random.default_rng(9)
+    for i, f in enumerate(fields):
+        f += np.float32(0.5) * rng.standard_normal(f.shape).astype(np.float32)
+        ts[i].copy_(torch.from_numpy(f))
+    torch.cuda.synchronize()
+    for _ in range(2):
+        check(run())
+    # a different parameter is a different batch
+    params[2] = gb.make_params(gb.field_dims(ts[2]), 1e-3)
+    nbs = run()
+    oa = ref.compress(fields[2], 1e-3, ref.EB_REL, 512, gb.auto_chunk(list(fields[2].shape)[::-1], 512))
+    assert nbs[2] == oa.size and np.array_equal(arcs[2][:nbs[2]].cpu().numpy(), oa)
+
+
+def test_autotune_choice_is_remembered_and_reproducible(gb, ctx):
+    """The tuner picks one of its candidates, remembers it per (rank, dims,
+    radius), and single and batched calls with its parameters give the
+    oracle's archive for that chunk."""
+    f = workloads.field_for("grf", (300, 700), seed=11)
+    t = torch.from_numpy(f).cuda()
+    p, ms = ctx.autotune(t, 1e-4)
+    assert p.chunk in (256, 512, 1024, 2048, 4096, gb.auto_chunk([700, 300], 512)) and ms > 0
+    p2, ms2 = ctx.autotune(t, 1e-4)
+    assert p2.chunk == p.chunk and ms2 == 0.0
+    arc, nb = ctx.compress_params(t, p)
+    oa = ref.compress(f, 1e-4, ref.EB_REL, 512, p.chunk)
+    assert nb == oa.size and np.array_equal(arc[:nb].cpu().numpy(), oa)
+    arcs, nbs, _ = ctx.compress_batch([t, t], None, params=[p, p])
+    torch.cuda.synchronize()
+    assert all(n_ == oa.size and np.array_equal(a[:n_].cpu().numpy(), oa) for a, n_ in zip(arcs, nbs))
