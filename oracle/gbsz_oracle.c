@@ -83,9 +83,9 @@ static uint64_t field_size(uint32_t ndim, const uint64_t dims[3])
 
 static int check_params(const gbsz_ref_params *p, uint64_t *n_out)
 {
-    if (!p || p->ndim < 1 || p->ndim > 3) return REF_ERR_INVALID_ARG;
+    if (!p || p->ndim < 1 || p->ndim > 4) return REF_ERR_INVALID_ARG;
     uint64_t n = 1;
-    for (uint32_t i = 0; i < 3; i++) {
+    for (uint32_t i = 0; i < 4; i++) {
         uint64_t d = i < p->ndim ? p->dims[i] : 1;
         if (d == 0 || d >= (1ull << 32)) return REF_ERR_INVALID_ARG;
         n *= d;
@@ -96,9 +96,25 @@ static int check_params(const gbsz_ref_params *p, uint64_t *n_out)
     if (p->radius < 2 || p->radius > 32768) return REF_ERR_INVALID_ARG;
     if (p->chunk < 64 || p->chunk > 65536 || (p->chunk & (p->chunk - 1)))
         return REF_ERR_INVALID_ARG;
-    if (p->lorenzo_block > 1) return REF_ERR_INVALID_ARG;
+    if (p->lorenzo_block > 1 || p->lorenzo_order > 3) return REF_ERR_INVALID_ARG;
+    if (p->lorenzo_block && p->lorenzo_order > 1) return REF_ERR_INVALID_ARG;
     *n_out = n;
     return REF_OK;
+}
+
+/* The predictor's geometry: a 4D field is predicted as 3D with its two
+ * slowest extents folded into one (dims[2] * dims[3]). */
+static uint32_t lorenzo_geometry(const gbsz_ref_params *p, uint64_t d[3])
+{
+    d[0] = d[1] = d[2] = 1;
+    for (uint32_t i = 0; i < p->ndim && i < 3; i++) d[i] = p->dims[i];
+    if (p->ndim == 4) d[2] *= p->dims[3];
+    return p->ndim == 4 ? 3u : p->ndim;
+}
+
+static uint32_t lorenzo_order(const gbsz_ref_params *p)
+{
+    return p->lorenzo_order ? p->lorenzo_order : 1u;
 }
 
 /* ------------------------------------------------------------------------ */
@@ -203,6 +219,39 @@ static uint64_t in_block(uint64_t c, uint32_t ndim, uint32_t lblock)
     return lblock ? c % gbsz_ref_lorenzo_block_extent(ndim) : c;
 }
 
+/* The order-n prediction of point (x, y, z) from q (Sec. 3.1.2, "Lorenzo
+ * Predictor with Binomial Coefficients"): the sum over every offset k != 0
+ * with 0 <= k_j <= n of c(k) q[x - k], where c(k) is the product of the
+ * binomials C(n, k_j) times (-1)^(k_x + k_y + k_z + 1).  This is the
+ * coefficient of the shift by k in 1 - prod_j (1 - S_j)^n, so the residual
+ * q - p is the n-th difference along every dimension and the coefficients
+ * sum to 1.  (The printed formula puts one factor (-1)^(k_j + 1) per
+ * dimension; for an even number of dimensions that flips every sign, which
+ * contradicts its own 2D example and unit weight.)  Points outside the field,
+ * or outside the point's block in the per-block mode, count as zero.
+ * Arithmetic modulo 2^32. */
+static uint32_t lorenzo_predict(const int32_t *q, const uint64_t d[3], uint32_t ndim, uint32_t order,
+                                uint32_t lblock, uint64_t x, uint64_t y, uint64_t z)
+{
+    const uint32_t kz_max = ndim >= 3 ? order : 0;
+    const uint32_t ky_max = ndim >= 2 ? order : 0;
+    const uint64_t bx = in_block(x, ndim, lblock), by = in_block(y, ndim, lblock),
+                   bz = in_block(z, ndim, lblock);
+    uint32_t p = 0;
+    for (uint32_t kz = 0; kz <= kz_max; kz++)
+        for (uint32_t ky = 0; ky <= ky_max; ky++)
+            for (uint32_t kx = 0; kx <= order; kx++) {
+                if (kx == 0 && ky == 0 && kz == 0) continue;
+                if (kx > bx || ky > by || kz > bz) continue;
+                uint64_t j = (x - kx) + d[0] * ((y - ky) + d[1] * (z - kz));
+                uint64_t c = binom(order, kx) * binom(order, ky) * binom(order, kz);
+                int neg = ((kx + ky + kz) % 2) == 0;
+                uint32_t term = (uint32_t)c * (uint32_t)q[j];
+                p = neg ? p - term : p + term;
+            }
+    return p;
+}
+
 int gbsz_ref_lorenzo_delta_blocked(const int32_t *q, uint32_t ndim,
                                    const uint64_t dims[3], uint32_t order,
                                    uint32_t lblock, int32_t *delta)
@@ -210,33 +259,14 @@ int gbsz_ref_lorenzo_delta_blocked(const int32_t *q, uint32_t ndim,
     if (ndim < 1 || ndim > 3 || order < 1 || order > 4 || lblock > 1) return REF_ERR_INVALID_ARG;
     uint64_t d[3] = {1, 1, 1};
     for (uint32_t i = 0; i < ndim; i++) d[i] = dims[i];
-    const uint32_t kz_max = ndim >= 3 ? order : 0;
-    const uint32_t ky_max = ndim >= 2 ? order : 0;
 #pragma omp parallel for
     for (int64_t zz = 0; zz < (int64_t)d[2]; zz++) {
         uint64_t z = (uint64_t)zz;
-        for (uint64_t y = 0; y < d[1]; y++) {
+        for (uint64_t y = 0; y < d[1]; y++)
             for (uint64_t x = 0; x < d[0]; x++) {
-                uint32_t p = 0; /* prediction, modulo 2^32 */
-                const uint64_t bx = in_block(x, ndim, lblock), by = in_block(y, ndim, lblock),
-                               bz = in_block(z, ndim, lblock);
-                for (uint32_t kz = 0; kz <= kz_max; kz++)
-                    for (uint32_t ky = 0; ky <= ky_max; ky++)
-                        for (uint32_t kx = 0; kx <= order; kx++) {
-                            if (kx == 0 && ky == 0 && kz == 0) continue;
-                            /* points outside the field (or the block) are zero */
-                            if (kx > bx || ky > by || kz > bz) continue;
-                            uint64_t j = (x - kx) + d[0] * ((y - ky) + d[1] * (z - kz));
-                            uint64_t c = binom(order, kx) * binom(order, ky) * binom(order, kz);
-                            /* sign (-1)^(kx+ky+kz+1) */
-                            int neg = ((kx + ky + kz) % 2) == 0;
-                            uint32_t term = (uint32_t)c * (uint32_t)q[j];
-                            p = neg ? p - term : p + term;
-                        }
                 uint64_t i = x + d[0] * (y + d[1] * z);
-                delta[i] = (int32_t)((uint32_t)q[i] - p);
+                delta[i] = (int32_t)((uint32_t)q[i] - lorenzo_predict(q, d, ndim, order, lblock, x, y, z));
             }
-        }
     }
     return REF_OK;
 }
@@ -251,15 +281,16 @@ int gbsz_ref_lorenzo_delta(const int32_t *q, uint32_t ndim,
 /* ------------------------------------------------------------------------ */
 /* S1 + S2: dual-quantization of the field (Algorithm 2, compression)         */
 
-int gbsz_ref_dualquant_blocked(const float *x, uint32_t ndim,
-                               const uint64_t dims[3], const float sc[3],
-                               uint32_t radius, uint32_t lblock,
-                               uint16_t *codes, uint32_t *out_idx,
-                               int32_t *out_delta, uint64_t *m,
-                               uint32_t *exc_idx, uint32_t *exc_raw,
-                               uint64_t *e, int32_t *q_keep)
+int gbsz_ref_dualquant_ex(const float *x, uint32_t ndim,
+                          const uint64_t dims[3], const float sc[3],
+                          uint32_t radius, uint32_t lblock, uint32_t order,
+                          uint16_t *codes, uint32_t *out_idx,
+                          int32_t *out_delta, uint64_t *m,
+                          uint32_t *exc_idx, uint32_t *exc_raw,
+                          uint64_t *e, int32_t *q_keep)
 {
     if (ndim < 1 || ndim > 3 || radius < 2 || radius > 32768 || lblock > 1) return REF_ERR_INVALID_ARG;
+    if (order < 1 || order > 3 || (lblock && order > 1)) return REF_ERR_INVALID_ARG;
     uint64_t n = field_size(ndim, dims);
     int32_t *q = (int32_t *)malloc(n * sizeof(int32_t) + 1);
     int32_t *delta = (int32_t *)malloc(n * sizeof(int32_t) + 1);
@@ -272,7 +303,7 @@ int gbsz_ref_dualquant_blocked(const float *x, uint32_t ndim,
 #pragma omp parallel for
     for (int64_t i = 0; i < (int64_t)n; i++) exc[i] = (uint8_t)gbsz_ref_prequant_one(x[i], sc, &q[i]);
     /* prediction on the prequantized integers, then postquant */
-    gbsz_ref_lorenzo_delta_blocked(q, ndim, dims, 1, lblock, delta);
+    gbsz_ref_lorenzo_delta_blocked(q, ndim, dims, order, lblock, delta);
     uint64_t nm = 0, ne = 0;
     for (uint64_t i = 0; i < n; i++) {
         int32_t dl = delta[i];
@@ -306,7 +337,7 @@ int gbsz_ref_dualquant(const float *x, uint32_t ndim, const uint64_t dims[3],
                        uint32_t *exc_idx, uint32_t *exc_raw, uint64_t *e,
                        int32_t *q_keep)
 {
-    return gbsz_ref_dualquant_blocked(x, ndim, dims, sc, radius, 0, codes, out_idx, out_delta, m,
+    return gbsz_ref_dualquant_ex(x, ndim, dims, sc, radius, 0, 1, codes, out_idx, out_delta, m,
                                       exc_idx, exc_raw, e, q_keep);
 }
 
@@ -529,15 +560,17 @@ int gbsz_ref_inflate(const uint32_t *stream, uint64_t words,
 /* ------------------------------------------------------------------------ */
 /* S8: reversed dual-quantization, reconstructed cascadingly (Algorithm 2)   */
 
-int gbsz_ref_reconstruct_blocked(const uint16_t *codes, uint32_t ndim,
-                                 const uint64_t dims[3], uint32_t radius,
-                                 uint32_t lblock, const uint32_t *out_idx,
-                                 const int32_t *out_delta, uint64_t m,
-                                 const uint32_t *exc_idx,
-                                 const uint32_t *exc_raw, uint64_t e,
-                                 float ebx2, float *xr)
+int gbsz_ref_reconstruct_ex(const uint16_t *codes, uint32_t ndim,
+                            const uint64_t dims[3], uint32_t radius,
+                            uint32_t lblock, uint32_t order,
+                            const uint32_t *out_idx,
+                            const int32_t *out_delta, uint64_t m,
+                            const uint32_t *exc_idx,
+                            const uint32_t *exc_raw, uint64_t e,
+                            float ebx2, float *xr)
 {
     if (ndim < 1 || ndim > 3 || lblock > 1) return REF_ERR_INVALID_ARG;
+    if (order < 1 || order > 3 || (lblock && order > 1)) return REF_ERR_INVALID_ARG;
     uint64_t d[3] = {1, 1, 1};
     for (uint32_t i = 0; i < ndim; i++) d[i] = dims[i];
     uint64_t n = d[0] * d[1] * d[2];
@@ -556,17 +589,8 @@ int gbsz_ref_reconstruct_blocked(const uint16_t *codes, uint32_t ndim,
                     if (j >= m || out_idx[j] != i) { free(q); return REF_ERR_CORRUPT; }
                     dl = out_delta[j++];
                 }
-                /* p = l(q of reconstructed neighbours), order 1, zero outside
-                   the field (and outside the block in the per-block mode) */
-                uint32_t p = 0;
-                const uint64_t bx = in_block(x, ndim, lblock), by = in_block(y, ndim, lblock),
-                               bz = in_block(z, ndim, lblock);
-                for (uint32_t k = 1; k < (1u << ndim); k++) {
-                    uint32_t kx = k & 1u, ky = (k >> 1) & 1u, kz = (k >> 2) & 1u;
-                    if (kx > bx || ky > by || kz > bz) continue;
-                    uint32_t v = (uint32_t)q[(x - kx) + d[0] * ((y - ky) + d[1] * (z - kz))];
-                    p = ((kx + ky + kz) % 2 == 1) ? p + v : p - v;
-                }
+                /* p = l(q of the reconstructed points before this one) */
+                const uint32_t p = lorenzo_predict(q, d, ndim, order, lblock, x, y, z);
                 q[i] = (int32_t)(p + (uint32_t)dl);
             }
     if (j != m) { free(q); return REF_ERR_CORRUPT; }
@@ -587,7 +611,7 @@ int gbsz_ref_reconstruct(const uint16_t *codes, uint32_t ndim,
                          const uint32_t *exc_raw, uint64_t e, float ebx2,
                          float *xr)
 {
-    return gbsz_ref_reconstruct_blocked(codes, ndim, dims, radius, 0, out_idx, out_delta, m,
+    return gbsz_ref_reconstruct_ex(codes, ndim, dims, radius, 0, 1, out_idx, out_delta, m,
                                         exc_idx, exc_raw, e, ebx2, xr);
 }
 
@@ -614,8 +638,8 @@ int gbsz_ref_compress(const float *x, const gbsz_ref_params *p, void *archive,
     if (st) return st;
     const uint32_t R = p->radius, nbins = 2 * R, C = p->chunk;
     const uint64_t nc = nchunks(n, C);
-    uint64_t dims[3] = {1, 1, 1};
-    for (uint32_t i = 0; i < p->ndim; i++) dims[i] = p->dims[i];
+    uint64_t dims[3];
+    const uint32_t gnd = lorenzo_geometry(p, dims);
 
     uint16_t *codes = (uint16_t *)malloc(n * 2 + 2);
     uint32_t *oidx = (uint32_t *)malloc(n * 4 + 4);
@@ -634,8 +658,8 @@ int gbsz_ref_compress(const float *x, const gbsz_ref_params *p, void *archive,
         st = REF_ERR_OOM;
         goto done;
     }
-    st = gbsz_ref_dualquant_blocked(x, p->ndim, dims, sc, R, p->lorenzo_block, codes, oidx, odel, &m,
-                                    eidx, eraw, &e, NULL);
+    st = gbsz_ref_dualquant_ex(x, gnd, dims, sc, R, p->lorenzo_block, lorenzo_order(p), codes, oidx, odel,
+                               &m, eidx, eraw, &e, NULL);
     if (st) goto done;
     st = gbsz_ref_histogram(codes, n, nbins, hist);
     if (st) goto done;
@@ -661,9 +685,9 @@ int gbsz_ref_compress(const float *x, const gbsz_ref_params *p, void *archive,
         put_u16(a, 6, (uint16_t)A_HEADER);
         put_u32(a, 8, p->ndim);
         put_u32(a, 12, p->eb_mode);
-        put_u64(a, 16, dims[0]);
-        put_u64(a, 24, dims[1]);
-        put_u64(a, 32, dims[2]);
+        put_u64(a, 16, p->dims[0]);
+        put_u64(a, 24, p->ndim >= 2 ? p->dims[1] : 1);
+        put_u64(a, 32, p->ndim >= 3 ? p->dims[2] : 1);
         put_u64(a, 40, n);
         put_f64(a, 48, p->eb);
         put_f32(a, 56, sc[0]);
@@ -678,6 +702,8 @@ int gbsz_ref_compress(const float *x, const gbsz_ref_params *p, void *archive,
         put_u32(a, 104, maxlen);
         put_u32(a, 108, p->lorenzo_block); /* 0: one predictor; 1: per block */
         put_u64(a, 112, total);
+        put_u32(a, 120, lorenzo_order(p));
+        put_u32(a, 124, p->ndim == 4 ? (uint32_t)p->dims[3] : 1u); /* below 2^32 as n is */
         memcpy(a + off_len, len, nbins);
         for (uint64_t c = 0; c < nc; c++) put_u32(a, off_bits + 4 * c, bits[c]);
         for (uint64_t t = 0; t < m; t++) {
@@ -713,6 +739,9 @@ static int parse_header(const uint8_t *a, size_t bytes, hdr_t *h)
     h->p.ndim = get_u32(a, 8);
     h->p.eb_mode = get_u32(a, 12);
     for (int i = 0; i < 3; i++) h->p.dims[i] = get_u64(a, 16 + 8 * i);
+    h->p.dims[3] = get_u32(a, 124);
+    h->p.lorenzo_order = get_u32(a, 120);
+    h->p.lorenzo_block = get_u32(a, 108);
     h->n = get_u64(a, 40);
     h->p.eb = get_f64(a, 48);
     h->sc[0] = get_f32(a, 56);
@@ -728,10 +757,9 @@ static int parse_header(const uint8_t *a, size_t bytes, hdr_t *h)
     h->total = get_u64(a, 112);
     uint64_t n;
     if (check_params(&h->p, &n) || n != h->n) return REF_ERR_CORRUPT;
-    for (uint32_t i = h->p.ndim; i < 3; i++)
+    for (uint32_t i = h->p.ndim; i < 4; i++)
         if (h->p.dims[i] != 1) return REF_ERR_CORRUPT;
-    h->p.lorenzo_block = get_u32(a, 108);
-    if (h->p.lorenzo_block > 1) return REF_ERR_CORRUPT;
+    if (h->p.lorenzo_order < 1) return REF_ERR_CORRUPT; /* written as 1..3 */
     if (h->nc != nchunks(n, h->p.chunk)) return REF_ERR_CORRUPT;
     if (!(h->sc[0] > 0.0f) || !isfinite(h->sc[0]) || h->sc[1] != h->sc[0] * 2.0f ||
         !isfinite(h->sc[1]))
@@ -802,8 +830,12 @@ int gbsz_ref_decompress(const void *archive, size_t bytes, float *x,
     }
     st = gbsz_ref_inflate(stream, h.w, bits, h.n, h.p.chunk, len, nbins, codes);
     if (st) goto done;
-    st = gbsz_ref_reconstruct_blocked(codes, h.p.ndim, h.p.dims, h.p.radius, h.p.lorenzo_block, oidx, odel, h.m,
-                              eidx, eraw, h.e, h.sc[1], x);
+    {
+        uint64_t dims[3];
+        const uint32_t gnd = lorenzo_geometry(&h.p, dims);
+        st = gbsz_ref_reconstruct_ex(codes, gnd, dims, h.p.radius, h.p.lorenzo_block, h.p.lorenzo_order, oidx,
+                                     odel, h.m, eidx, eraw, h.e, h.sc[1], x);
+    }
 done:
     free(bits); free(stream); free(oidx); free(odel); free(eidx); free(eraw); free(codes);
     return st;

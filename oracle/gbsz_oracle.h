@@ -35,8 +35,10 @@ enum {
 enum { REF_EB_ABS = 0, REF_EB_REL = 1 };
 
 typedef struct {
-    uint32_t ndim;    /* 1, 2 or 3 */
-    uint64_t dims[3]; /* dims[0] varies fastest; unused dims are 1 */
+    uint32_t ndim;    /* 1, 2, 3, or 4 (predicted as 3D over dims[0],
+                         dims[1] and dims[2]*dims[3]: the two slowest extents
+                         folded into one) */
+    uint64_t dims[4]; /* dims[0] varies fastest; unused dims are 1 */
     double eb;        /* absolute bound, or value-range-relative bound */
     uint32_t eb_mode; /* REF_EB_ABS or REF_EB_REL */
     uint32_t radius;  /* R: in-cap residuals satisfy |delta| < R; 2R bins */
@@ -44,6 +46,10 @@ typedef struct {
     uint32_t lorenzo_block; /* 0: one predictor over the whole field; 1: the
                                paper's blocks (Sec. 3.1.1, 32 / 16x16 / 8x8x8)
                                with a zero padding layer around each block */
+    uint32_t lorenzo_order; /* n of the Lorenzo predictor with binomial
+                               coefficients (Sec. 3.1.2): 0 or 1 = first
+                               order, 2, 3; orders above 1 need
+                               lorenzo_block = 0 */
 } gbsz_ref_params;
 
 /* Block extent of the per-block Lorenzo mode along every dimension
@@ -82,13 +88,15 @@ int gbsz_ref_dualquant(const float *x, uint32_t ndim, const uint64_t dims[3],
                        uint32_t *out_idx, int32_t *out_delta, uint64_t *m,
                        uint32_t *exc_idx, uint32_t *exc_raw, uint64_t *e,
                        int32_t *q);
-int gbsz_ref_dualquant_blocked(const float *x, uint32_t ndim,
-                               const uint64_t dims[3], const float sc[3],
-                               uint32_t radius, uint32_t lblock,
-                               uint16_t *codes, uint32_t *out_idx,
-                               int32_t *out_delta, uint64_t *m,
-                               uint32_t *exc_idx, uint32_t *exc_raw,
-                               uint64_t *e, int32_t *q);
+/* The same with the per-block mode (lblock = 1) and a Lorenzo predictor of
+ * order `order` (1..3; above 1 only with lblock = 0). */
+int gbsz_ref_dualquant_ex(const float *x, uint32_t ndim,
+                          const uint64_t dims[3], const float sc[3],
+                          uint32_t radius, uint32_t lblock, uint32_t order,
+                          uint16_t *codes, uint32_t *out_idx,
+                          int32_t *out_delta, uint64_t *m,
+                          uint32_t *exc_idx, uint32_t *exc_raw,
+                          uint64_t *e, int32_t *q);
 
 /* S3 -- histogram of quant codes (Sec. 3.2.1). */
 int gbsz_ref_histogram(const uint16_t *codes, uint64_t n, uint32_t nbins,
@@ -115,20 +123,22 @@ int gbsz_ref_inflate(const uint32_t *stream, uint64_t words,
                      const uint32_t *bits, uint64_t n, uint32_t chunk,
                      const uint8_t *len, uint32_t nbins, uint16_t *codes);
 
-/* S8 -- reversed dual-quantization (Algorithm 2, decompression loop). */
+/* S8 -- reversed dual-quantization (Algorithm 2, decompression loop): every
+ * point is predicted from the already reconstructed points before it. */
 int gbsz_ref_reconstruct(const uint16_t *codes, uint32_t ndim,
                          const uint64_t dims[3], uint32_t radius,
                          const uint32_t *out_idx, const int32_t *out_delta,
                          uint64_t m, const uint32_t *exc_idx,
                          const uint32_t *exc_raw, uint64_t e, float ebx2,
                          float *xr);
-int gbsz_ref_reconstruct_blocked(const uint16_t *codes, uint32_t ndim,
-                                 const uint64_t dims[3], uint32_t radius,
-                                 uint32_t lblock, const uint32_t *out_idx,
-                                 const int32_t *out_delta, uint64_t m,
-                                 const uint32_t *exc_idx,
-                                 const uint32_t *exc_raw, uint64_t e,
-                                 float ebx2, float *xr);
+int gbsz_ref_reconstruct_ex(const uint16_t *codes, uint32_t ndim,
+                            const uint64_t dims[3], uint32_t radius,
+                            uint32_t lblock, uint32_t order,
+                            const uint32_t *out_idx,
+                            const int32_t *out_delta, uint64_t m,
+                            const uint32_t *exc_idx,
+                            const uint32_t *exc_raw, uint64_t e,
+                            float ebx2, float *xr);
 
 /* Whole path: archive bytes and back. */
 size_t gbsz_ref_compress_bound(const gbsz_ref_params *p);

@@ -21,19 +21,20 @@ class OracleError(RuntimeError):
 
 
 class Params(C.Structure):
-    _fields_ = [("ndim", C.c_uint32), ("dims", C.c_uint64 * 3), ("eb", C.c_double),
+    _fields_ = [("ndim", C.c_uint32), ("dims", C.c_uint64 * 4), ("eb", C.c_double),
                 ("eb_mode", C.c_uint32), ("radius", C.c_uint32), ("chunk", C.c_uint32),
-                ("lorenzo_block", C.c_uint32)]
+                ("lorenzo_block", C.c_uint32), ("lorenzo_order", C.c_uint32)]
 
 
-def make_params(dims, eb, eb_mode=EB_REL, radius=512, chunk=4096, lblock=0):
+def make_params(dims, eb, eb_mode=EB_REL, radius=512, chunk=4096, lblock=0, order=1):
     dims = tuple(int(d) for d in dims)
     p = Params()
     p.ndim = len(dims)
-    for i in range(3):
+    for i in range(4):
         p.dims[i] = dims[i] if i < len(dims) else 1
     p.eb, p.eb_mode, p.radius, p.chunk = float(eb), int(eb_mode), int(radius), int(chunk)
     p.lorenzo_block = int(lblock)
+    p.lorenzo_order = int(order)
     return p
 
 
@@ -53,14 +54,14 @@ def lib(omp=False):
             "gbsz_ref_lorenzo_delta": [P, u32, P, u32, P],
             "gbsz_ref_lorenzo_delta_blocked": [P, u32, P, u32, u32, P],
             "gbsz_ref_dualquant": [P, u32, P, P, u32, P, P, P, P, P, P, P, P],
-            "gbsz_ref_dualquant_blocked": [P, u32, P, P, u32, u32, P, P, P, P, P, P, P, P],
+            "gbsz_ref_dualquant_ex": [P, u32, P, P, u32, u32, u32, P, P, P, P, P, P, P, P],
             "gbsz_ref_histogram": [P, u64, u32, P],
             "gbsz_ref_huffman_lengths": [P, u32, P, P],
             "gbsz_ref_canonical_codes": [P, u32, P],
             "gbsz_ref_deflate": [P, u64, u32, P, P, P, P, u64, P],
             "gbsz_ref_inflate": [P, u64, P, u64, u32, P, u32, P],
             "gbsz_ref_reconstruct": [P, u32, P, u32, P, P, u64, P, P, u64, C.c_float, P],
-            "gbsz_ref_reconstruct_blocked": [P, u32, P, u32, u32, P, P, u64, P, P, u64, C.c_float, P],
+            "gbsz_ref_reconstruct_ex": [P, u32, P, u32, u32, u32, P, P, u64, P, P, u64, C.c_float, P],
             "gbsz_ref_compress": [P, P, P, C.c_size_t, P],
             "gbsz_ref_decompress": [P, C.c_size_t, P, u64],
             "gbsz_ref_archive_info": [P, C.c_size_t, P, P],
@@ -122,7 +123,7 @@ def lorenzo_block_extent(ndim):
     return int(lib().gbsz_ref_lorenzo_block_extent(ndim))
 
 
-def dualquant(x, sc, radius, lblock=0):
+def dualquant(x, sc, radius, lblock=0, order=1):
     """Returns dict(codes, out_idx, out_delta, exc_idx, exc_raw, q)."""
     x = np.ascontiguousarray(x, dtype=np.float32)
     dims = x.shape[::-1]
@@ -133,9 +134,9 @@ def dualquant(x, sc, radius, lblock=0):
     ei, er = np.zeros(n, np.uint32), np.zeros(n, np.uint32)
     q = np.zeros(n, np.int32)
     m, e = C.c_uint64(), C.c_uint64()
-    _check(lib().gbsz_ref_dualquant_blocked(_p(x), len(dims), _p(_dims3(dims)), _p(sc), radius, lblock,
-                                            _p(codes), _p(oi), _p(od), C.byref(m), _p(ei), _p(er),
-                                            C.byref(e), _p(q)), "dualquant")
+    _check(lib().gbsz_ref_dualquant_ex(_p(x), len(dims), _p(_dims3(dims)), _p(sc), radius, lblock, order,
+                                       _p(codes), _p(oi), _p(od), C.byref(m), _p(ei), _p(er),
+                                       C.byref(e), _p(q)), "dualquant")
     m, e = m.value, e.value
     return dict(codes=codes, out_idx=oi[:m].copy(), out_delta=od[:m].copy(),
                 exc_idx=ei[:e].copy(), exc_raw=er[:e].copy(), q=q)
@@ -189,7 +190,7 @@ def inflate(stream, bits, n, chunk, lengths):
     return codes
 
 
-def reconstruct(codes, dims, radius, out_idx, out_delta, exc_idx, exc_raw, ebx2, lblock=0):
+def reconstruct(codes, dims, radius, out_idx, out_delta, exc_idx, exc_raw, ebx2, lblock=0, order=1):
     """dims in numpy order (slowest first); returns float32 array of that shape."""
     codes = np.ascontiguousarray(codes, dtype=np.uint16).ravel()
     fd = tuple(dims)[::-1]
@@ -198,22 +199,24 @@ def reconstruct(codes, dims, radius, out_idx, out_delta, exc_idx, exc_raw, ebx2,
     ei = np.ascontiguousarray(exc_idx, dtype=np.uint32)
     er = np.ascontiguousarray(exc_raw, dtype=np.uint32)
     x = np.zeros(codes.size, np.float32)
-    _check(lib().gbsz_ref_reconstruct_blocked(_p(codes), len(fd), _p(_dims3(fd)), radius, lblock, _p(oi),
-                                              _p(od), oi.size, _p(ei), _p(er), ei.size, C.c_float(ebx2), _p(x)),
+    _check(lib().gbsz_ref_reconstruct_ex(_p(codes), len(fd), _p(_dims3(fd)), radius, lblock, order, _p(oi),
+                                         _p(od), oi.size, _p(ei), _p(er), ei.size, C.c_float(ebx2), _p(x)),
            "reconstruct")
     return x.reshape(dims)
 
 
-def compress_bound(shape, eb, eb_mode=EB_REL, radius=512, chunk=4096, lblock=0):
-    p = make_params(tuple(shape)[::-1], eb, eb_mode, radius, chunk, lblock)
+def compress_bound(shape, eb, eb_mode=EB_REL, radius=512, chunk=4096, lblock=0, order=1):
+    p = make_params(tuple(shape)[::-1], eb, eb_mode, radius, chunk, lblock, order)
     return lib().gbsz_ref_compress_bound(C.byref(p))
 
 
-def compress(x, eb, eb_mode=EB_REL, radius=512, chunk=4096, omp=False, lblock=0):
-    """x: numpy float32 array, C order (last axis fastest).  Returns bytes array.
-    lblock = 1: Lorenzo inside the paper's blocks (zero padding layer)."""
+def compress(x, eb, eb_mode=EB_REL, radius=512, chunk=4096, omp=False, lblock=0, order=1):
+    """x: numpy float32 array, C order (last axis fastest; up to 4 axes, a 4D
+    field being predicted as 3D with its two slowest axes folded).  Returns
+    bytes array.  lblock = 1: Lorenzo inside the paper's blocks (zero padding
+    layer); order: Lorenzo order n (1..3)."""
     x = np.ascontiguousarray(x, dtype=np.float32)
-    p = make_params(x.shape[::-1], eb, eb_mode, radius, chunk, lblock)
+    p = make_params(x.shape[::-1], eb, eb_mode, radius, chunk, lblock, order)
     L = lib(omp)
     cap = L.gbsz_ref_compress_bound(C.byref(p))
     if cap == 0:
@@ -267,7 +270,7 @@ def sections(archive):
     off_exc = off_out + 8 * m
     off_str = al(off_exc + 8 * e)
     d = dict(radius=R, nchunk=nc, m=m, e=e, words=w, maxlen=u32(104), chunk=u32(72), lblock=u32(108),
-             total=u64(112), n=u64(40),
+             total=u64(112), n=u64(40), order=u32(120), ndim=u32(8),
              sc=np.frombuffer(b[56:68], dtype=np.float32).copy(),
              off_len=off_len, off_bits=off_bits, off_out=off_out, off_exc=off_exc, off_str=off_str)
     d["len"] = a[off_len:off_len + 2 * R].copy()

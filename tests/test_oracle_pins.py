@@ -546,3 +546,114 @@ def test_block_mode_inside_one_block_changes_only_the_flag():
     a1 = ref.compress(x, 1e-3, ref.EB_REL, radius=512, chunk=64, lblock=1)
     diff = np.flatnonzero(a0 != a1)
     assert a0.size == a1.size and np.all((diff >= 108) & (diff < 112))
+
+
+# ---------------------------------------------------------------------------
+# Lorenzo predictor of order n > 1 (Sec. 3.1.2, binomial coefficients)
+
+def cumsum_wrap(a, ax):
+    s = np.cumsum(a.astype(np.int64), axis=ax)
+    return ((s + (1 << 31)) % (1 << 32) - (1 << 31)).astype(np.int32)
+
+
+@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("shape", [(41,), (9, 13), (5, 7, 6), (1, 11), (4, 1, 9)])
+def test_lorenzo_order_n_inverted_by_n_prefix_sums(order, shape):
+    """Closed form: the order-n residual is the n-th difference along every
+    axis (the binomial coefficients of (1 - shift)^n per axis), so n inclusive
+    prefix sums along every axis, modulo 2^32, give the integers back."""
+    rng = np.random.default_rng(order * 100 + sum(shape))
+    q = rng.integers(-2**31, 2**31, shape, dtype=np.int64).astype(np.int32)
+    r = ref.lorenzo_delta(q, order=order)
+    for _ in range(order):
+        for ax in range(r.ndim):
+            r = cumsum_wrap(r, ax)
+    assert np.array_equal(r, q)
+
+
+def test_lorenzo_order2_2d_point_by_hand():
+    # n = 2 in 2D: the residual at (y, x) is sum over a, b in 0..2 of
+    # C(2,a) C(2,b) (-1)^(a+b) q[y-a, x-b]; written out term by term
+    rng = np.random.default_rng(5)
+    q = rng.integers(-50, 50, (5, 6)).astype(np.int32)
+    d = ref.lorenzo_delta(q, order=2)
+    y, x = 3, 4
+    want = (q[y, x] - 2 * q[y, x - 1] + q[y, x - 2]
+            - 2 * q[y - 1, x] + 4 * q[y - 1, x - 1] - 2 * q[y - 1, x - 2]
+            + q[y - 2, x] - 2 * q[y - 2, x - 1] + q[y - 2, x - 2])
+    assert d[y, x] == want
+    # a point on the first row sees only its own row (zeros outside the field)
+    assert d[0, 3] == q[0, 3] - 2 * q[0, 2] + q[0, 1]
+
+
+def test_lorenzo_order3_kills_quadratics():
+    # the third difference of a quadratic vanishes away from the boundary
+    t = np.arange(40, dtype=np.int64)
+    q = (3 * t * t - 7 * t + 11).astype(np.int32)
+    d = ref.lorenzo_delta(q, order=3)
+    assert np.all(d[3:] == 0) and np.any(d[:3] != 0)
+
+
+@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("shape", [(50,), (7, 9), (4, 5, 6)])
+def test_reconstruct_order_n_recovers_integers(order, shape):
+    """The cascading reconstruction (each point predicted from the points
+    already rebuilt) inverts the order-n residual: with 2eb = 1 the output is
+    the prequantized integers themselves."""
+    rng = np.random.default_rng(order + len(shape))
+    q = rng.integers(-3000, 3000, shape).astype(np.int32)
+    flat = ref.lorenzo_delta(q, order=order).ravel()
+    R = 64
+    inc = np.abs(flat) < R
+    codes = np.where(inc, flat + R, 0).astype(np.uint16)
+    oi = np.flatnonzero(~inc).astype(np.uint32)
+    e = np.zeros(0, np.uint32)
+    x = ref.reconstruct(codes, shape, R, oi, flat[~inc], e, e, 1.0, order=order)
+    assert np.array_equal(x, q.astype(np.float32))
+
+
+@pytest.mark.parametrize("order", [2, 3])
+@pytest.mark.parametrize("shape,eb", [((3001,), 1e-3), ((45, 61), 1e-4), ((11, 17, 19), 1e-3)])
+def test_order_n_archive_roundtrip_and_codes(order, shape, eb):
+    rng = np.random.default_rng(order * 7 + len(shape))
+    x = np.cumsum(np.cumsum(rng.normal(0, 1, shape), axis=-1), axis=0).astype(np.float32)
+    a = ref.compress(x, eb, ref.EB_REL, radius=128, chunk=256, order=order)
+    s = ref.sections(a)
+    assert s["order"] == order
+    y = ref.decompress(a)
+    sc = ref.error_bound(x, eb, ref.EB_REL)
+    assert np.all(np.abs(x.astype(np.float64) - y) <= float(sc[0]))
+    dq = ref.dualquant(x, sc, 128, order=order)
+    assert np.array_equal(ref.inflate(s["stream"], s["bits"], x.size, 256, s["len"]), dq["codes"])
+
+
+def test_order_defaults_and_limits():
+    rng = np.random.default_rng(2)
+    x = rng.normal(0, 1, (20, 20)).astype(np.float32)
+    a0 = ref.compress(x, 1e-3, order=0)
+    a1 = ref.compress(x, 1e-3, order=1)
+    assert np.array_equal(a0, a1) and ref.sections(a1)["order"] == 1
+    with pytest.raises(ref.OracleError):
+        ref.compress(x, 1e-3, order=4)
+    with pytest.raises(ref.OracleError):
+        ref.compress(x, 1e-3, order=2, lblock=1)
+
+
+# ---------------------------------------------------------------------------
+# 4D fields (QMCPACK-like, 288x115x69x69 in the paper's datasets) are
+# predicted as 3D with the two slowest axes folded into one
+
+def test_4d_archive_is_the_folded_3d_archive():
+    rng = np.random.default_rng(4)
+    x4 = np.cumsum(rng.normal(0, 1, (3, 4, 5, 6)), axis=-1).astype(np.float32)
+    a4 = ref.compress(x4, 1e-3, chunk=64)
+    a3 = ref.compress(x4.reshape(12, 5, 6), 1e-3, chunk=64)
+    diff = set(np.flatnonzero(a4 != a3).tolist())
+    header_fields = set(range(8, 12)) | set(range(32, 40)) | set(range(124, 128))  # ndim, dims[2], dims[3]
+    assert a4.size == a3.size and diff and diff <= header_fields
+    p, n = ref.archive_info(a4)
+    assert p.ndim == 4 and [p.dims[i] for i in range(4)] == [6, 5, 4, 3] and n == x4.size
+    y = ref.decompress(a4)
+    assert y.shape == x4.shape
+    sc = ref.error_bound(x4, 1e-3, ref.EB_REL)
+    assert np.all(np.abs(x4.astype(np.float64) - y) <= float(sc[0]))
