@@ -51,7 +51,9 @@ typedef enum {
 typedef enum { GBSZ_EB_ABS = 0, GBSZ_EB_REL = 1 } gbsz_eb_mode;
 
 /* Compression parameters.
- *   ndim     1, 2 or 3 (Lorenzo predictor dimensionality, Sec. 3.1.2)
+ *   ndim     1, 2, 3 (Lorenzo predictor dimensionality, Sec. 3.1.2) or 4:
+ *            a 4D field (the QMCPACK shape of Sec. 4) is predicted as 3D
+ *            over dims[0], dims[1] and dims[2]*dims[3]
  *   dims     extents, dims[0] fastest; entries >= ndim must be 1;
  *            product n in [1, 2^32)
  *   eb       error bound: absolute (GBSZ_EB_ABS) or relative to the value
@@ -67,15 +69,21 @@ typedef enum { GBSZ_EB_ABS = 0, GBSZ_EB_REL = 1 } gbsz_eb_mode;
  *            outside the field are 0); 1: the paper's blocks (Sec. 3.1.1,
  *            "Chunking and Padding": 32 in 1D, 16x16 in 2D, 8x8x8 in 3D),
  *            each surrounded by a padding layer of zeros, so every block is
- *            predicted and reconstructed on its own.  Stored in the archive. */
+ *            predicted and reconstructed on its own.  Stored in the archive.
+ *   lorenzo_order  n of the Lorenzo predictor with binomial coefficients
+ *            (Sec. 3.1.2): 0 or 1 = first order (the default), 2 or 3; the
+ *            residual is then the n-th difference along every dimension.
+ *            Orders above 1 need lorenzo_block = 0.  Stored in the archive
+ *            (as 1..3). */
 typedef struct {
     uint32_t ndim;
-    uint64_t dims[3];
+    uint64_t dims[4];
     double eb;
     uint32_t eb_mode;
     uint32_t radius;
     uint32_t chunk;
     uint32_t lorenzo_block;
+    uint32_t lorenzo_order;
 } gbsz_params;
 
 /* Creates a context on CUDA device `device` (must be compute capability
@@ -86,6 +94,16 @@ gbsz_status gbsz_create(gbsz_ctx **out, int device);
 
 /* Frees everything the context owns.  Waits for its pending work.  NULL ok. */
 void gbsz_destroy(gbsz_ctx *ctx);
+
+/* Context options: knobs of the kernels that never change archive bytes.
+ *   GBSZ_OPT_CODEWORD_BITS  width of the (bitwidth, codeword) table entries
+ *     the encoder reads.  0 (default) = the paper's adaptive choice (Sec.
+ *     3.2.2): 32-bit entries when the longest code has at most 24 bits, else
+ *     64; 64 = always 64-bit entries (the "enc.64" column of the paper's
+ *     encode/deflate table, for comparison).
+ * Errors: INVALID_ARG (NULL context, unknown option or value). */
+#define GBSZ_OPT_CODEWORD_BITS 1
+gbsz_status gbsz_set_option(gbsz_ctx *ctx, int option, int64_t value);
 
 /* Worst-case archive size in bytes for these parameters (0 if invalid).
  * Host-only, no device work. */
@@ -99,7 +117,8 @@ uint32_t gbsz_auto_chunk(const gbsz_params *p);
  * hand, Sec. 4.2).  Times compress + decompress of the field at d_field for
  * chunk sizes 256..4096 and the rule's choice on `stream` (CUDA events, best
  * of two runs each), and writes *out = *p with the fastest chunk.  The choice
- * is remembered per context for the key (ndim, dims, radius, lorenzo_block):
+ * is remembered per context for the key (ndim, dims, radius, lorenzo_block,
+ * lorenzo_order):
  * later calls with the same key return it without measuring, so every
  * single or batched call given *out produces the same archive.  *ms (may be
  * NULL) gets the measured time of the chosen chunk (0 when remembered).

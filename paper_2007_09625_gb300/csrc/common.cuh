@@ -27,7 +27,7 @@ enum : uint32_t {
     H_MAGIC = 0, H_VERSION = 4, H_HDRBYTES = 6, H_NDIM = 8, H_EBMODE = 12,
     H_DIMS = 16, H_N = 40, H_EB = 48, H_EBF = 56, H_EBX2 = 60, H_INV2EB = 64,
     H_RADIUS = 68, H_CHUNK = 72, H_NCHUNK = 76, H_M = 80, H_E = 88, H_W = 96,
-    H_MAXLEN = 104, H_LBLOCK = 108, H_TOTAL = 112
+    H_MAXLEN = 104, H_LBLOCK = 108, H_TOTAL = 112, H_ORDER = 120, H_DIM3 = 124
 };
 
 __host__ __device__ inline uint64_t align16(uint64_t v) { return (v + 15) & ~uint64_t(15); }
@@ -299,6 +299,9 @@ struct QuantArgs {
     uint32_t *unit_exc;   // exceptions per encoder unit (zeroed by the caller)
     uint32_t unit_shift;  // log2 of the encoder unit in points
     uint32_t lblock;      // 1: Lorenzo inside the paper's blocks (zero padding layer)
+    uint32_t order;       // Lorenzo order n (1..3)
+    int32_t *qint;        // order > 1: prequantized integers (scratch, n entries)
+    uint32_t *excm;       // order > 1: exception bit per point (zeroed, n/32 + 1 words)
     Control *ctl;
     int num_sms;
 };
@@ -310,7 +313,7 @@ __host__ __device__ constexpr uint32_t lorenzo_block_extent(uint32_t ndim)
 
 void launch_minmax_eb(const float *x, uint64_t n, Control *ctl, double eb, uint32_t mode,
                       int num_sms, cudaStream_t st);
-void launch_dualquant(const QuantArgs &a, cudaStream_t st);
+int launch_dualquant(const QuantArgs &a, cudaStream_t st);  // returns kernels launched
 
 struct CodebookArgs {
     const uint32_t *hist;  // for compress; NULL for the decode-table build
@@ -369,9 +372,10 @@ struct EncodeArgs {
     ulonglong2 *unit_off;   // their exclusive prefix sums
     ulonglong2 *scan_part;  // scan scratch
     Control *ctl;
-    // header fields
-    uint32_t ndim, eb_mode, lblock;
-    uint64_t dims[3];
+    uint32_t cw64_only;     // 1: read 64-bit codeword entries whatever the longest code
+    // header fields (the field's own shape; 4D is not folded here)
+    uint32_t ndim, eb_mode, lblock, order;
+    uint64_t dims[4];
     double eb;
     int num_sms;
 };
@@ -413,9 +417,10 @@ struct ReconArgs {
     float ebx2;
     int32_t *dscr;
     uint32_t lblock;      // 1: block-local reconstruction (the paper's blocks)
+    uint32_t order;       // Lorenzo order n (1..3)
     uint32_t *faces;      // carry scratch; 1D: the tile sums left by the decoder
     uint64_t faces_cap;   // entries
-    uint32_t *scan_partial;  // scratch for the 1D carry scan
+    uint32_t *scan_partial;  // scratch for the 1D carry scan (order > 1: scan_partials(n) entries)
     float *out;
     Control *ctl;
     int num_sms;

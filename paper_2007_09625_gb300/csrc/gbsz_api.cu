@@ -135,6 +135,7 @@ struct Slot {
     Control *ctl = nullptr;
     // per-field scratch (grown on demand)
     Buf codes, dscr, unit_tot, unit_off, unit_part, unit_exc, lane_bits, chunk_off, faces, scan_part;
+    Buf qint, excm;  // Lorenzo order > 1: prequantized integers, exception bits
     // fixed-size scratch
     Buf hist, cw64, cw32, codes_only, keyA, keyB, nodef, parent, distA, distB, parA, parB;
     Buf lut, lutf, first, count, start, sorted;
@@ -163,7 +164,7 @@ struct Slot {
     void release()
     {
         for (Buf *b : {&codes, &dscr, &unit_tot, &unit_off, &unit_part, &unit_exc, &lane_bits, &chunk_off, &faces, &scan_part,
-                       &hist, &cw64,
+                       &qint, &excm, &hist, &cw64,
                        &cw32, &codes_only, &keyA, &keyB, &nodef, &parent, &distA, &distB, &parA, &parB, &lut, &lutf,
                        &first, &count, &start, &sorted})
             b->release();
@@ -193,9 +194,11 @@ struct gbsz_ctx {
     uint32_t last_nbins = 0;
     float last_sc[3] = {0, 0, 0};  // error-bound scalars of the last compress
     bool have_compress = false, have_decompress = false;
+    // options
+    uint32_t cw64_only = 0;  // GBSZ_OPT_CODEWORD_BITS = 64
     // captured batch calls
     BatchGraph gcomp, gdecomp;
-    // autotuned chunks, keyed by (ndim, dims, radius, lorenzo_block)
+    // autotuned chunks, keyed by (ndim, dims, radius, lorenzo_block, lorenzo_order)
     std::vector<std::pair<std::vector<uint64_t>, uint32_t>> tuned;
     Buf tune_arc, tune_out;
     // timing
@@ -236,9 +239,9 @@ namespace {
 
 bool valid_params(const gbsz_params *p, uint64_t *n_out)
 {
-    if (!p || p->ndim < 1 || p->ndim > 3) return false;
+    if (!p || p->ndim < 1 || p->ndim > 4) return false;
     uint64_t n = 1;
-    for (uint32_t i = 0; i < 3; i++) {
+    for (uint32_t i = 0; i < 4; i++) {
         const uint64_t d = p->dims[i];
         if (d == 0 || d >= (1ull << 32)) return false;
         if (i >= p->ndim && d != 1) return false;
@@ -249,9 +252,22 @@ bool valid_params(const gbsz_params *p, uint64_t *n_out)
     if (p->eb_mode != GBSZ_EB_ABS && p->eb_mode != GBSZ_EB_REL) return false;
     if (p->radius < 2 || p->radius > 32768) return false;
     if (p->chunk != 0 && (p->chunk < 64 || p->chunk > 65536 || (p->chunk & (p->chunk - 1)))) return false;
-    if (p->lorenzo_block > 1) return false;
+    if (p->lorenzo_block > 1 || p->lorenzo_order > 3) return false;
+    if (p->lorenzo_block && p->lorenzo_order > 1) return false;
     *n_out = n;
     return true;
+}
+
+uint32_t order_of(const gbsz_params &p) { return p.lorenzo_order ? p.lorenzo_order : 1u; }
+
+// The predictor's geometry: a 4D field is predicted as 3D with its two
+// slowest extents folded into one.
+uint32_t lorenzo_geom(const gbsz_params &p, uint64_t d[3])
+{
+    d[0] = p.dims[0];
+    d[1] = p.dims[1];
+    d[2] = p.ndim == 4 ? p.dims[2] * p.dims[3] : p.dims[2];
+    return p.ndim == 4 ? 3u : p.ndim;
 }
 
 uint32_t auto_chunk(uint64_t n)
@@ -340,6 +356,9 @@ gbsz_status parse_header(const uint8_t *b, size_t bytes, Header *h)
     p.ndim = rd<uint32_t>(b, H_NDIM);
     p.eb_mode = rd<uint32_t>(b, H_EBMODE);
     for (int i = 0; i < 3; i++) p.dims[i] = rd<uint64_t>(b, H_DIMS + 8 * i);
+    p.dims[3] = rd<uint32_t>(b, H_DIM3);
+    p.lorenzo_order = rd<uint32_t>(b, H_ORDER);
+    if (p.lorenzo_order < 1) return GBSZ_ERR_CORRUPT;  // written as 1..3
     p.eb = rd<double>(b, H_EB);
     p.radius = rd<uint32_t>(b, H_RADIUS);
     p.chunk = rd<uint32_t>(b, H_CHUNK);
@@ -389,6 +408,7 @@ gbsz_status check_compress(const float *d_field, const gbsz_params *pin, const v
 bool reserve_compress(Slot *s, const gbsz_params &p, uint64_t n)
 {
     const uint64_t nunits = encode_units(n, p.chunk);
+    if (order_of(p) > 1 && !(s->qint.ensure(n * 4 + 64) && s->excm.ensure((n / 32 + 1) * 4))) return false;
     return s->codes.ensure(n * 2 + 64) && s->dscr.ensure(n * 8 + 64) && s->unit_tot.ensure(nunits * 16) &&
            s->lane_bits.ensure((n / 64 + 64) * 4) && s->unit_off.ensure(nunits * 16) &&
            s->unit_part.ensure(scan_partials(nunits) * 16 + 64) && s->unit_exc.ensure(nunits * 4);
@@ -397,10 +417,13 @@ bool reserve_compress(Slot *s, const gbsz_params &p, uint64_t n)
 bool reserve_decompress(Slot *s, const Header &h)
 {
     const uint64_t n = h.n;
-    const uint64_t nfaces = recon_faces_entries(h.p.ndim, h.p.dims);
+    uint64_t gd[3];
+    const uint64_t nfaces = recon_faces_entries(lorenzo_geom(h.p, gd), gd);
     const uint64_t nscan = std::max<uint64_t>(h.nchunk, nfaces);
+    // order > 1 scans the whole 1D field (4-byte partials)
+    const uint64_t scan_bytes = std::max<uint64_t>(scan_partials(nscan) * 8, order_of(h.p) > 1 ? scan_partials(n) * 4 : 0);
     return s->codes.ensure(n * 2 + 64) && s->dscr.ensure(n * 8 + 64) && s->chunk_off.ensure(h.nchunk * 8 + 8) &&
-           s->faces.ensure(nfaces * 4 + 16) && s->scan_part.ensure(scan_partials(nscan) * 8 + 64);
+           s->faces.ensure(nfaces * 4 + 16) && s->scan_part.ensure(scan_bytes + 64);
 }
 
 // Enqueues S0-S6 of one field on stream st using slot s; no synchronisation.
@@ -409,10 +432,12 @@ gbsz_status enqueue_compress(gbsz_ctx *c, Slot *s, const float *d_field, const g
 {
     const uint32_t nbins = 2 * p.radius;
     const uint64_t nunits = encode_units(n, p.chunk);
+    const uint32_t order = order_of(p);
     if (!reserve_compress(s, p, n)) return GBSZ_ERR_OOM;
     cudaMemsetAsync(s->ctl, 0, sizeof(Control), st);
     cudaMemsetAsync(s->hist.p, 0, nbins * 4, st);
     cudaMemsetAsync(s->unit_exc.p, 0, nunits * 4, st);
+    if (order > 1) cudaMemsetAsync(s->excm.p, 0, (n / 32 + 1) * 4, st);
 
     cudaEvent_t e0;
     stage_begin(c, st, &e0);
@@ -421,8 +446,7 @@ gbsz_status enqueue_compress(gbsz_ctx *c, Slot *s, const float *d_field, const g
 
     QuantArgs q{};
     q.x = d_field;
-    for (int i = 0; i < 3; i++) q.dims[i] = p.dims[i];
-    q.ndim = p.ndim;
+    q.ndim = lorenzo_geom(p, q.dims);
     q.radius = p.radius;
     q.codes = s->codes.as<uint16_t>();
     q.dscr = s->dscr.as<int2>();
@@ -430,10 +454,13 @@ gbsz_status enqueue_compress(gbsz_ctx *c, Slot *s, const float *d_field, const g
     q.unit_exc = s->unit_exc.as<uint32_t>();
     q.unit_shift = encode_unit_shift(p.chunk);
     q.lblock = p.lorenzo_block;
+    q.order = order;
+    q.qint = order > 1 ? s->qint.as<int32_t>() : nullptr;
+    q.excm = order > 1 ? s->excm.as<uint32_t>() : nullptr;
     q.ctl = s->ctl;
     q.num_sms = c->num_sms;
     stage_begin(c, st, &e0);
-    launch_dualquant(q, st);
+    const int nq = launch_dualquant(q, st);
     stage_end(c, st, 1, e0);
 
     CodebookArgs cb = codebook_args(s);
@@ -465,7 +492,9 @@ gbsz_status enqueue_compress(gbsz_ctx *c, Slot *s, const float *d_field, const g
     en.ndim = p.ndim;
     en.eb_mode = p.eb_mode;
     en.lblock = p.lorenzo_block;
-    for (int i = 0; i < 3; i++) en.dims[i] = p.dims[i];
+    en.order = order;
+    en.cw64_only = c->cw64_only;
+    for (int i = 0; i < 4; i++) en.dims[i] = p.dims[i];
     en.eb = p.eb;
     en.num_sms = c->num_sms;
     int nenc = 0;
@@ -474,7 +503,7 @@ gbsz_status enqueue_compress(gbsz_ctx *c, Slot *s, const float *d_field, const g
         nenc += launch_encode(en, st, ph);
         stage_end(c, st, 3 + ph, e0);
     }
-    c->launches += 3 + nenc;
+    c->launches += 2 + nq + nenc;
     return GBSZ_OK;
 }
 
@@ -483,10 +512,14 @@ gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void
                                cudaStream_t st)
 {
     const uint64_t n = h.n;
-    const uint64_t nfaces = recon_faces_entries(h.p.ndim, h.p.dims);
+    uint64_t gd[3];
+    const uint32_t gnd = lorenzo_geom(h.p, gd);
+    const uint32_t order = order_of(h.p);
+    const uint64_t nfaces = recon_faces_entries(gnd, gd);
+    const bool tile_sums = gnd == 1 && !h.p.lorenzo_block && order == 1;
     if (!reserve_decompress(s, h)) return GBSZ_ERR_OOM;
     cudaMemsetAsync(s->ctl, 0, sizeof(Control), st);
-    if (h.p.ndim == 1) cudaMemsetAsync(s->faces.p, 0, nfaces * 4, st);  // tile sums
+    if (tile_sums) cudaMemsetAsync(s->faces.p, 0, nfaces * 4, st);
     const uint8_t *arc = static_cast<const uint8_t *>(d_archive);
 
     CodebookArgs cb = codebook_args(s);
@@ -521,7 +554,7 @@ gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void
     d.num_sms = c->num_sms;
     d.chunk_off = s->chunk_off.as<unsigned long long>();
     d.scan_partial = s->scan_part.as<unsigned long long>();
-    d.tile_sums = h.p.ndim == 1 && !h.p.lorenzo_block ? s->faces.as<uint32_t>() : nullptr;
+    d.tile_sums = tile_sums ? s->faces.as<uint32_t>() : nullptr;
     d.codes = s->codes.as<uint16_t>();
     d.ctl = s->ctl;
     int ndec = 0;
@@ -538,12 +571,13 @@ gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void
     r.off_exc = h.L.exc;
     r.m = h.m;
     r.e = h.e;
-    r.ndim = h.p.ndim;
-    for (int i = 0; i < 3; i++) r.dims[i] = h.p.dims[i];
+    r.ndim = gnd;
+    for (int i = 0; i < 3; i++) r.dims[i] = gd[i];
     r.radius = h.p.radius;
     r.ebx2 = h.ebx2;
     r.dscr = s->dscr.as<int32_t>();
     r.lblock = h.p.lorenzo_block;
+    r.order = order;
     r.faces = s->faces.as<uint32_t>();
     r.faces_cap = nfaces;
     r.scan_partial = s->scan_part.as<uint32_t>();
@@ -692,6 +726,17 @@ void gbsz_destroy(gbsz_ctx *c)
     delete c;
 }
 
+gbsz_status gbsz_set_option(gbsz_ctx *c, int option, int64_t value)
+{
+    if (!c) return GBSZ_ERR_INVALID_ARG;
+    if (option == GBSZ_OPT_CODEWORD_BITS) {
+        if (value != 0 && value != 64) return GBSZ_ERR_INVALID_ARG;
+        c->cw64_only = value == 64 ? 1u : 0u;
+        return GBSZ_OK;
+    }
+    return GBSZ_ERR_INVALID_ARG;
+}
+
 uint32_t gbsz_auto_chunk(const gbsz_params *p)
 {
     uint64_t n;
@@ -705,7 +750,8 @@ gbsz_status gbsz_autotune(gbsz_ctx *c, const float *d_field, const gbsz_params *
     uint64_t n;
     if (!c || !d_field || !p || !out || !valid_params(p, &n)) return GBSZ_ERR_INVALID_ARG;
     DevGuard g(c->device);
-    const std::vector<uint64_t> key{p->ndim, p->dims[0], p->dims[1], p->dims[2], p->radius, p->lorenzo_block};
+    const std::vector<uint64_t> key{p->ndim,   p->dims[0], p->dims[1],        p->dims[2],
+                                    p->dims[3], p->radius,  p->lorenzo_block, order_of(*p)};
     *out = *p;
     if (ms) *ms = 0.0f;
     for (const auto &t : c->tuned)
@@ -867,8 +913,9 @@ gbsz_status gbsz_compress_batch(gbsz_ctx *c, uint32_t count, const float *const 
         key_add(key, &d_fields[i], sizeof(void *));
         key_add(key, &d_archives[i], sizeof(void *));
         key_add(key, &capacities[i], sizeof(size_t));
-        key.insert(key.end(), {rp[i].ndim, rp[i].dims[0], rp[i].dims[1], rp[i].dims[2], rp[i].eb_mode,
-                               rp[i].radius, rp[i].chunk, rp[i].lorenzo_block});
+        key.insert(key.end(), {rp[i].ndim, rp[i].dims[0], rp[i].dims[1], rp[i].dims[2], rp[i].dims[3],
+                               rp[i].eb_mode, rp[i].radius, rp[i].chunk, rp[i].lorenzo_block,
+                               rp[i].lorenzo_order, c->cw64_only});
         key_add(key, &rp[i].eb, sizeof(double));
         key.push_back((uint64_t)statuses[i]);
     }

@@ -148,6 +148,8 @@ __device__ void write_header(const EncodeArgs &a, const Layout &L, uint64_t nchu
     h[H_MAXLEN / 4] = maxlen;
     h[H_LBLOCK / 4] = a.lblock;
     set64(H_TOTAL, L.total);
+    h[H_ORDER / 4] = a.order;
+    h[H_DIM3 / 4] = (uint32_t)a.dims[3];  // below 2^32 as n is
     for (int i = 0; i < (int)(kHeaderBytes / 4); i++) put_u32(a.archive + 4 * i, h[i]);
     for (uint64_t b = L.len + a.nbins; b < L.bits; b++) a.archive[b] = 0;
     for (uint64_t b = L.bits + 4 * nchunk; b < L.outl; b++) a.archive[b] = 0;
@@ -577,7 +579,7 @@ __global__ void __launch_bounds__(kEncThreads, 4) k_encode_count(EncodeArgs a, u
     uint32_t *part = s_cnt + (threadIdx.x >> 5) * kPartWords;
     uint32_t *tab = s_cnt + kWarps * kPartWords;
     if (a.ctl->error & (DERR_EB | DERR_INTERNAL)) return;
-    const bool w32 = a.ctl->maxlen <= 24;
+    const bool w32 = !a.cw64_only && a.ctl->maxlen <= 24;
     if (a.nbins <= kCountSmemBins) {
         for (uint32_t i = threadIdx.x; i < a.nbins; i += blockDim.x) {
             const uint32_t len = w32 ? a.cw32[i] >> 24 : (uint32_t)(a.cw64[i] >> 56);
@@ -594,10 +596,10 @@ __global__ void __launch_bounds__(kEncThreads, 3) k_encode_pack(EncodeArgs a, ui
     uint4 *slot = s_dyn + (threadIdx.x >> 5) * (kRound / 8);  // 8 KB per warp
     unsigned long long *s_tab = reinterpret_cast<unsigned long long *>(s_dyn + kWarps * (kRound / 8));
     if (a.ctl->error & (DERR_EB | DERR_INTERNAL)) return;
-    const bool w32 = a.ctl->maxlen <= 24;
+    const bool w32 = !a.cw64_only && a.ctl->maxlen <= 24;
     // each call sees where its table lives, so shared-memory tables are read
     // with shared loads
-    const bool pair = a.ctl->maxlen <= 16;
+    const bool pair = w32 && a.ctl->maxlen <= 16;
     if (use_smem) {
         load_table(a, 1, s_tab, w32);
         if (pair) pack_units<true, true>(a, nunits, Table<true>{s_tab}, slot);

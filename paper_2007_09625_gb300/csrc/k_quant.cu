@@ -545,6 +545,74 @@ __global__ void __launch_bounds__(kQ3Threads) k_dualquant_3d(QuantArgs a, uint32
     hist_flush(h, a.hist, a.ctl);
 }
 
+// ---------------------------------------------------------------------------
+// Order n > 1 (Lorenzo predictor with binomial coefficients, Sec. 3.1.2).
+// The prequantized integers go to a scratch copy first, exceptions to a bit
+// mask; a second kernel evaluates the stencil of all (n+1)^d - 1 earlier
+// neighbours of every point from that copy, with zeros outside the field.
+// The neighbour k steps back weighs -prod_j (-1)^k_j C(n, k_j): the
+// expansion of 1 - prod_j (1 - S_j)^n, so the residual is the n-th
+// difference along every dimension.  One thread per point; the neighbours
+// are re-read through L1/L2.
+
+__global__ void __launch_bounds__(256) k_prequant_int(QuantArgs a, uint64_t n)
+{
+    if (a.ctl->error & DERR_EB) return;
+    const EbScalars sc = load_scalars(a.ctl);
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        bool ex;
+        a.qint[i] = prequant(a.x[i], sc, ex);
+        if (ex) atomicOr(&a.excm[i >> 5], 1u << (i & 31));
+    }
+}
+
+__host__ __device__ constexpr uint32_t binom_c(uint32_t n, uint32_t k)
+{
+    return k == 0 ? 1u : binom_c(n, k - 1) * (n - k + 1) / k;
+}
+
+template <int D, int ORDER>
+__global__ void __launch_bounds__(256) k_lorenzo_order(QuantArgs a, uint32_t n)
+{
+    extern __shared__ uint32_t sh_hist[];
+    HistState h;
+    hist_init(h, sh_hist, a.radius);
+    __syncthreads();
+    if (a.ctl->error & DERR_EB) return;
+    const uint32_t nx = (uint32_t)a.dims[0], ny = D >= 2 ? (uint32_t)a.dims[1] : 1u;
+    const uint32_t sz = nx * ny;  // below 2^32 as n is
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i64 = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i64 < n; i64 += stride) {
+        const uint32_t i = (uint32_t)i64;
+        const uint32_t x = i % nx, r = i / nx;
+        const uint32_t y = D >= 2 ? r % ny : 0u, z = D >= 3 ? r / ny : 0u;
+        uint32_t p = 0;
+#pragma unroll
+        for (int kz = 0; kz <= (D >= 3 ? ORDER : 0); kz++)
+#pragma unroll
+            for (int ky = 0; ky <= (D >= 2 ? ORDER : 0); ky++)
+#pragma unroll
+                for (int kx = 0; kx <= ORDER; kx++) {
+                    if (kx + ky + kz == 0) continue;
+                    if ((uint32_t)kx > x || (uint32_t)ky > y || (uint32_t)kz > z) continue;
+                    const uint32_t c = binom_c(ORDER, kx) * binom_c(ORDER, ky) * binom_c(ORDER, kz);
+                    const uint32_t v = (uint32_t)a.qint[i - kx - ky * nx - kz * sz] * c;
+                    p = ((kx + ky + kz) & 1) ? p + v : p - v;
+                }
+        const bool ex = (a.excm[i >> 5] >> (i & 31)) & 1u;
+        a.codes[i] = (uint16_t)emit_point(h, a, i, (uint32_t)a.qint[i] - p, ex);
+    }
+    hist_flush(h, a.hist, a.ctl);
+}
+
+template <int D>
+void launch_order(const QuantArgs &a, uint32_t n, int grid, size_t hist_bytes, cudaStream_t st)
+{
+    if (a.order == 2) k_lorenzo_order<D, 2><<<grid, 256, hist_bytes, st>>>(a, n);
+    else k_lorenzo_order<D, 3><<<grid, 256, hist_bytes, st>>>(a, n);
+}
+
 }  // namespace
 
 void launch_minmax_eb(const float *x, uint64_t n, Control *ctl, double eb, uint32_t mode, int num_sms,
@@ -562,10 +630,19 @@ void launch_minmax_eb(const float *x, uint64_t n, Control *ctl, double eb, uint3
         k_minmax<false><<<grid, 256, 0, st>>>(x, n, ctl, eb, mode);
 }
 
-void launch_dualquant(const QuantArgs &a, cudaStream_t st)
+int launch_dualquant(const QuantArgs &a, cudaStream_t st)
 {
     const uint32_t nbins = 2 * a.radius;
     const size_t hist_bytes = sizeof(uint32_t) * std::min<uint32_t>(nbins, kWinBins);
+    if (a.order > 1) {
+        const uint64_t n = a.dims[0] * a.dims[1] * a.dims[2];
+        const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>((n + 255) / 256, (uint64_t)a.num_sms * 8));
+        k_prequant_int<<<grid, 256, 0, st>>>(a, n);
+        if (a.ndim == 1) launch_order<1>(a, (uint32_t)n, grid, hist_bytes, st);
+        else if (a.ndim == 2) launch_order<2>(a, (uint32_t)n, grid, hist_bytes, st);
+        else launch_order<3>(a, (uint32_t)n, grid, hist_bytes, st);
+        return 2;
+    }
     if (a.ndim == 1) {
         const uint64_t n = a.dims[0];
         const uint32_t ntiles = (uint32_t)((n + kQ1Tile - 1) / kQ1Tile);
@@ -592,6 +669,7 @@ void launch_dualquant(const QuantArgs &a, cudaStream_t st)
         const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)a.num_sms * 8);
         k_dualquant_3d<<<grid, kQ3Threads, hist_bytes, st>>>(a, ntx, nty, ntz, (uint32_t)tz);
     }
+    return 1;
 }
 
 }  // namespace gbsz

@@ -97,7 +97,6 @@ __global__ void k_scatter_outliers(ReconArgs a, uint64_t n)
         if (ok) ok &= a.codes[idx] == 0;
         if (ok) {
             a.dscr[idx] = d;
-            if (a.ndim == 1) atomicAdd(&a.faces[idx / kRecon1DTile], (uint32_t)d);
         } else {
             atomicOr(&a.ctl->error, DERR_CORRUPT);
         }
@@ -555,6 +554,156 @@ struct TileOp {
     __device__ void total(T) const {}
 };
 
+// ---------------------------------------------------------------------------
+// Order n > 1: the residual is prod_j (1 - S_j)^n q, so q comes back from n
+// inclusive prefix sums along every dimension, modulo 2^32.  The residuals
+// are expanded into an int32 array (code - R; outliers scattered on top),
+// then every sum is a pass of its own: a 1D field as one device-wide scan,
+// rows along x in 2D/3D one warp per row, and columns along y or z in
+// 32-point segments (segment totals, a carry scan down every column, then
+// the segments again), adjacent threads on adjacent columns.
+
+__global__ void k_residuals(ReconArgs a, uint64_t n)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride) {
+        const uint32_t c = a.codes[i];
+        a.dscr[i] = c ? (int32_t)(c - a.radius) : 0;  // outliers are written by the scatter
+    }
+}
+
+struct InclusiveOp {  // in-place inclusive scan through the exclusive-scan kernels
+    using T = uint32_t;
+    uint32_t *v;
+    __device__ T load(uint64_t i) const { return v[i]; }
+    __device__ void store(uint64_t i, T excl) const { v[i] += excl; }
+    __device__ void total(T) const {}
+};
+
+__global__ void __launch_bounds__(256) k_scan_rows(uint32_t *v, uint64_t nx, uint64_t nrows)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t r = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < nrows; r += nw) {
+        uint32_t *row = v + r * nx;
+        uint32_t carry = 0;
+        for (uint64_t x0 = 0; x0 < nx; x0 += 32) {
+            const uint64_t x = x0 + lane;
+            uint32_t t = x < nx ? row[x] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, t, o);
+                if (lane >= (uint32_t)o) t += u;
+            }
+            t += carry;
+            if (x < nx) row[x] = t;
+            carry = __shfl_sync(0xffffffffu, t, 31);
+        }
+    }
+}
+
+constexpr uint32_t kSeg = 32;
+
+// Column geometry: element k of column (o, i) at o * len * s + k * s + i.
+struct Cols {
+    uint64_t s, len, outer, nseg;
+};
+
+__global__ void k_seg_sums(const uint32_t *v, Cols c, uint32_t *tmp)
+{
+    const uint64_t total = c.outer * c.nseg * c.s, stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+        const uint64_t i = t % c.s, rest = t / c.s, g = rest % c.nseg, o = rest / c.nseg;
+        const uint64_t k0 = g * kSeg, k1 = min(c.len, k0 + kSeg);
+        const uint32_t *col = v + o * c.len * c.s + i;
+        uint32_t sum = 0;
+        for (uint64_t k = k0; k < k1; k++) sum += col[k * c.s];
+        tmp[t] = sum;
+    }
+}
+
+__global__ void k_seg_carry(Cols c, uint32_t *tmp)
+{
+    const uint64_t total = c.outer * c.s, stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+        const uint64_t i = t % c.s, o = t / c.s;
+        uint32_t *col = tmp + o * c.nseg * c.s + i;
+        uint32_t run = 0;
+        for (uint64_t g = 0; g < c.nseg; g++) {
+            const uint32_t x = col[g * c.s];
+            col[g * c.s] = run;
+            run += x;
+        }
+    }
+}
+
+__global__ void k_seg_apply(uint32_t *v, Cols c, const uint32_t *tmp)
+{
+    const uint64_t total = c.outer * c.nseg * c.s, stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += stride) {
+        const uint64_t i = t % c.s, rest = t / c.s, g = rest % c.nseg, o = rest / c.nseg;
+        const uint64_t k0 = g * kSeg, k1 = min(c.len, k0 + kSeg);
+        uint32_t *col = v + o * c.len * c.s + i;
+        uint32_t run = tmp[t];
+        for (uint64_t k = k0; k < k1; k++) {
+            run += col[k * c.s];
+            col[k * c.s] = run;
+        }
+    }
+}
+
+__global__ void k_dequant(ReconArgs a, uint64_t n)
+{
+    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += stride)
+        a.out[i] = recon_value(a.dscr[i], a.ebx2);
+}
+
+int launch_reconstruct_order(const ReconArgs &a, const Geo &g, uint64_t n, cudaStream_t st)
+{
+    int nl = 0;
+    auto grid_for = [&](uint64_t work) {
+        return (int)std::max<uint64_t>(1, std::min<uint64_t>((work + 255) / 256, (uint64_t)a.num_sms * 16));
+    };
+    uint32_t *v = reinterpret_cast<uint32_t *>(a.dscr);
+    uint32_t *tmp = v + ((n + 3) & ~3ull);  // the second half of the per-point scratch
+    k_residuals<<<grid_for(n), 256, 0, st>>>(a, n);
+    nl++;
+    if (a.m) {
+        k_scatter_outliers<<<grid_for(a.m), 256, 0, st>>>(a, n);
+        nl++;
+    }
+    for (uint32_t pass = 0; pass < a.order; pass++) {
+        for (uint32_t d = 0; d < g.ndim; d++) {
+            if (g.n[d] < 2) continue;
+            if (d == 0 && g.ndim == 1) {
+                nl += launch_scan(InclusiveOp{v}, n, a.scan_partial, st);
+            } else if (d == 0) {
+                const uint64_t rows = n / g.n[0];
+                k_scan_rows<<<grid_for(rows * 32), 256, 0, st>>>(v, g.n[0], rows);
+                nl++;
+            } else {
+                Cols c;
+                c.s = d == 1 ? g.n[0] : g.n[0] * g.n[1];
+                c.len = g.n[d];
+                c.outer = n / (c.s * c.len);
+                c.nseg = (c.len + kSeg - 1) / kSeg;
+                k_seg_sums<<<grid_for(c.outer * c.nseg * c.s), 256, 0, st>>>(v, c, tmp);
+                k_seg_carry<<<grid_for(c.outer * c.s), 256, 0, st>>>(c, tmp);
+                k_seg_apply<<<grid_for(c.outer * c.nseg * c.s), 256, 0, st>>>(v, c, tmp);
+                nl += 3;
+            }
+        }
+    }
+    k_dequant<<<grid_for(n), 256, 0, st>>>(a, n);
+    nl++;
+    if (a.e) {
+        k_patch_exceptions<<<grid_for(a.e), 256, 0, st>>>(a, n);
+        nl++;
+    }
+    return nl;
+}
+
 }  // namespace
 
 uint64_t recon_faces_entries(uint32_t ndim, const uint64_t dims[3])
@@ -566,6 +715,11 @@ void launch_reconstruct(const ReconArgs &a, cudaStream_t st, int *launches)
 {
     const Geo g = make_geo(a.ndim, a.dims);
     const uint64_t n = g.n[0] * g.n[1] * g.n[2];
+    if (a.order > 1) {
+        const int nlo = launch_reconstruct_order(a, g, n, st);
+        if (launches) *launches += nlo;
+        return;
+    }
     int nl = 0;
     uint32_t *start1d = reinterpret_cast<uint32_t *>(a.dscr);  // 1D: per-tile outlier starts
     const uint64_t ngroups = g.ntiles;

@@ -40,7 +40,9 @@ SIGNATURES = {
     "gbsz_compress_batch": ([_P, C.c_uint32, _P, _P, _P, _P, _P, _P, _P], C.c_int),
     "gbsz_decompress_batch": ([_P, C.c_uint32, _P, _P, _P, _P, _P, _P], C.c_int),
     "gbsz_autotune": ([_P, _P, _P, _P, C.POINTER(C.c_float), _P], C.c_int),
+    "gbsz_set_option": ([_P, C.c_int, C.c_int64], C.c_int),
 }
+OPT_CODEWORD_BITS = 1
 
 
 class GbszError(RuntimeError):
@@ -51,9 +53,9 @@ class GbszError(RuntimeError):
 
 
 class Params(C.Structure):
-    _fields_ = [("ndim", C.c_uint32), ("dims", C.c_uint64 * 3), ("eb", C.c_double),
+    _fields_ = [("ndim", C.c_uint32), ("dims", C.c_uint64 * 4), ("eb", C.c_double),
                 ("eb_mode", C.c_uint32), ("radius", C.c_uint32), ("chunk", C.c_uint32),
-                ("lorenzo_block", C.c_uint32)]
+                ("lorenzo_block", C.c_uint32), ("lorenzo_order", C.c_uint32)]
 
 
 _lib = None
@@ -78,16 +80,18 @@ def status_str(s):
     return load().gbsz_status_str(int(s)).decode()
 
 
-def make_params(dims, eb, eb_mode=EB_REL, radius=512, chunk=0, lblock=0):
-    """dims: extents with the fastest-varying first (x, y, z).  lblock = 1:
-    Lorenzo inside the paper's blocks (see gbsz_params.lorenzo_block)."""
+def make_params(dims, eb, eb_mode=EB_REL, radius=512, chunk=0, lblock=0, order=1):
+    """dims: extents with the fastest-varying first (x, y, z, w; a 4D field
+    is predicted as 3D with z and w folded).  lblock = 1: Lorenzo inside the
+    paper's blocks (see gbsz_params.lorenzo_block); order: Lorenzo order n."""
     dims = [int(d) for d in dims]
     p = Params()
     p.ndim = len(dims)
-    for i in range(3):
+    for i in range(4):
         p.dims[i] = dims[i] if i < len(dims) else 1
     p.eb, p.eb_mode, p.radius, p.chunk = float(eb), int(eb_mode), int(radius), int(chunk)
     p.lorenzo_block = int(lblock)
+    p.lorenzo_order = int(order)
     return p
 
 
@@ -96,8 +100,8 @@ def field_dims(t):
     return list(t.shape)[::-1]
 
 
-def compress_bound(dims, eb=1e-4, eb_mode=EB_REL, radius=512, chunk=0, lblock=0):
-    return load().gbsz_compress_bound(C.byref(make_params(dims, eb, eb_mode, radius, chunk, lblock)))
+def compress_bound(dims, eb=1e-4, eb_mode=EB_REL, radius=512, chunk=0, lblock=0, order=1):
+    return load().gbsz_compress_bound(C.byref(make_params(dims, eb, eb_mode, radius, chunk, lblock, order)))
 
 
 def _stream(stream=None):
@@ -129,11 +133,12 @@ class Context:
             pass
 
     # -- device-buffer API -------------------------------------------------
-    def compress(self, field, eb, eb_mode=EB_REL, radius=512, chunk=0, out=None, stream=None, lblock=0):
+    def compress(self, field, eb, eb_mode=EB_REL, radius=512, chunk=0, out=None, stream=None, lblock=0,
+                 order=1):
         """field: contiguous float32 CUDA tensor (C order, last axis fastest).
         Returns (archive uint8 tensor on the device, nbytes)."""
         assert field.is_cuda and field.dtype == torch.float32 and field.is_contiguous()
-        p = make_params(field_dims(field), eb, eb_mode, radius, chunk, lblock)
+        p = make_params(field_dims(field), eb, eb_mode, radius, chunk, lblock, order)
         cap = load().gbsz_compress_bound(C.byref(p))
         if cap == 0:
             raise GbszError(ERR_INVALID_ARG, "compress_bound")
@@ -146,10 +151,10 @@ class Context:
             raise GbszError(st, "gbsz_compress")
         return out, nbytes.value
 
-    def autotune(self, field, eb, eb_mode=EB_REL, radius=512, lblock=0, stream=None):
+    def autotune(self, field, eb, eb_mode=EB_REL, radius=512, lblock=0, stream=None, order=1):
         """Measured chunk choice for this field's (rank, dims, radius) (see
         gbsz_autotune).  Returns (Params with the chosen chunk, ms)."""
-        p = make_params(field_dims(field), eb, eb_mode, radius, 0, lblock)
+        p = make_params(field_dims(field), eb, eb_mode, radius, 0, lblock, order)
         out = Params()
         ms = C.c_float()
         st = load().gbsz_autotune(self.h, C.c_void_p(field.data_ptr()), C.byref(p), C.byref(out), C.byref(ms),
@@ -230,6 +235,11 @@ class Context:
         if st != OK:
             raise GbszError(st, "gbsz_decompress_batch")
         return outs, list(sts)
+
+    def set_option(self, option, value):
+        st = load().gbsz_set_option(self.h, int(option), int(value))
+        if st != OK:
+            raise GbszError(st, "gbsz_set_option")
 
     # -- host-buffer API ---------------------------------------------------
     def compress_host(self, field_np, eb, eb_mode=EB_REL, radius=512, chunk=0, out=None, stream=None,

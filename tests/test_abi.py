@@ -75,8 +75,17 @@ def test_archive_info_parses_oracle_archives(lib, oracle):
     x = rng.normal(size=(7, 9, 11)).astype(np.float32)
     a = oracle.compress(x, 1e-3, oracle.EB_REL, radius=64, chunk=128)
     p, n = gbsz.archive_info(a, a.size)
-    assert n == x.size and p.ndim == 3 and list(p.dims) == [11, 9, 7]
-    assert p.radius == 64 and p.chunk == 128 and p.eb_mode == gbsz.EB_REL
+    assert n == x.size and p.ndim == 3 and list(p.dims) == [11, 9, 7, 1]
+    assert p.radius == 64 and p.chunk == 128 and p.eb_mode == gbsz.EB_REL and p.lorenzo_order == 1
+    x4 = rng.normal(size=(2, 3, 5, 7)).astype(np.float32)
+    a4 = oracle.compress(x4, 1e-3, oracle.EB_REL, radius=64, chunk=64, order=2)
+    p4, n4 = gbsz.archive_info(a4, a4.size)
+    assert n4 == x4.size and p4.ndim == 4 and list(p4.dims) == [7, 5, 3, 2] and p4.lorenzo_order == 2
+    for order in (0, 4):  # stored orders are 1..3
+        bad = a4.copy()
+        bad[120:124] = np.frombuffer(np.uint32(order).tobytes(), np.uint8)
+        with pytest.raises(gbsz.GbszError):
+            gbsz.archive_info(bad, bad.size)
     bad = a.copy()
     bad[0] ^= 1
     with pytest.raises(gbsz.GbszError):

@@ -147,3 +147,28 @@ def test_autotune_choice_is_remembered_and_reproducible(gb, ctx):
     arcs, nbs, _ = ctx.compress_batch([t, t], None, params=[p, p])
     torch.cuda.synchronize()
     assert all(n_ == oa.size and np.array_equal(a[:n_].cpu().numpy(), oa) for a, n_ in zip(arcs, nbs))
+
+
+def test_batch_with_orders_blocks_and_4d(gb, ctx):
+    """A batch mixing Lorenzo orders, the per-block mode and a 4D field gives
+    each field's single-call archive and the oracle's."""
+    shapes = [(60001,), (90, 130), (17, 23, 29), (3, 4, 19, 21), (40000,), (55, 66)]
+    fields = [workloads.field_for("walk" if len(s) == 1 else "sinus", s, seed=900 + i) for i, s in enumerate(shapes)]
+    opts = [(2, 0), (3, 0), (2, 0), (1, 0), (1, 1), (1, 1)]  # (order, lblock)
+    ts = [torch.from_numpy(f).cuda() for f in fields]
+    params = [gb.make_params(gb.field_dims(t), 1e-4, gb.EB_REL, 512, 256, lblock=lb, order=o)
+              for t, (o, lb) in zip(ts, opts)]
+    arcs, nbs, sts = ctx.compress_batch(ts, None, params=params)
+    torch.cuda.synchronize()
+    assert all(s == gb.OK for s in sts)
+    for i, f in enumerate(fields):
+        o, lb = opts[i]
+        oa = ref.compress(f, 1e-4, ref.EB_REL, 512, 256, lblock=lb, order=o)
+        assert np.array_equal(arcs[i][:nbs[i]].cpu().numpy(), oa), i
+    outs = [torch.empty_like(t) for t in ts]
+    outs, dsts = ctx.decompress_batch(arcs, nbs, outs)
+    torch.cuda.synchronize()
+    assert all(s == gb.OK for s in dsts)
+    for i in range(len(fields)):
+        yo = ref.decompress(arcs[i][:nbs[i]].cpu().numpy())
+        assert np.array_equal(outs[i].cpu().numpy().view(np.uint32), yo.view(np.uint32)), i

@@ -23,18 +23,23 @@ def ctx(gb):
     c.close()
 
 
-def compare_stages(gb, ctx, x, eb, eb_mode, R, C, lblock=0):
+def fold3(x):
+    """A 4D field as the 3D field its predictor sees (two slowest axes folded)."""
+    return x.reshape((x.shape[0] * x.shape[1],) + x.shape[2:]) if x.ndim == 4 else x
+
+
+def compare_stages(gb, ctx, x, eb, eb_mode, R, C, lblock=0, order=1):
     """Compress on the GPU and with the oracle; assert each stage equal.
     Returns (gpu archive tensor, nbytes, oracle archive)."""
     xt = torch.from_numpy(np.ascontiguousarray(x)).cuda()
-    arc, nb = ctx.compress(xt, eb, eb_mode, R, C, lblock=lblock)
+    arc, nb = ctx.compress(xt, eb, eb_mode, R, C, lblock=lblock, order=order)
     torch.cuda.synchronize()
     ga = arc[:nb].cpu().numpy()
     n = x.size
     sc = ref.error_bound(x, eb, eb_mode)
     gsc = ctx.debug_copy(gb.DEBUG_SCALARS, 3, np.float32)
     assert np.array_equal(gsc.view(np.uint32), sc.view(np.uint32)), (gsc, sc)
-    dq = ref.dualquant(x, sc, R, lblock=lblock)
+    dq = ref.dualquant(fold3(x), sc, R, lblock=lblock, order=order)
     gcodes = ctx.debug_copy(gb.DEBUG_CODES, n, np.uint16)
     if not np.array_equal(gcodes, dq["codes"]):
         bad = np.flatnonzero(gcodes != dq["codes"])
@@ -49,7 +54,7 @@ def compare_stages(gb, ctx, x, eb, eb_mode, R, C, lblock=0):
     gs = ref.sections(ga)
     assert np.array_equal(gs["len"], ln), "code lengths differ"
     assert np.array_equal(gcw, cw), "canonical codewords differ"
-    oa = ref.compress(x, eb, eb_mode, radius=R, chunk=C, lblock=lblock)
+    oa = ref.compress(x, eb, eb_mode, radius=R, chunk=C, lblock=lblock, order=order)
     os_ = ref.sections(oa)
     for key in ("maxlen", "m", "e", "words", "nchunk"):
         assert gs[key] == os_[key], (key, gs[key], os_[key])
@@ -74,8 +79,8 @@ def check_decompress(gb, ctx, arc, nb, oa, x, eb, eb_mode):
         raise AssertionError(f"reconstruction differs at {bad.size} points, first {bad[:8]}")
     dcodes = ctx.debug_copy(gb.DEBUG_DECODED, x.size, np.uint16)
     s_ = ref.sections(oa)
-    assert np.array_equal(dcodes, ref.dualquant(x, ref.error_bound(x, eb, eb_mode), s_["radius"],
-                                                lblock=s_["lblock"])["codes"])
+    assert np.array_equal(dcodes, ref.dualquant(fold3(x), ref.error_bound(x, eb, eb_mode), s_["radius"],
+                                                lblock=s_["lblock"], order=s_["order"])["codes"])
     sc = ref.error_bound(x, eb, eb_mode)
     fin = np.isfinite(x)
     err = np.abs(x[fin].astype(np.float64) - y[fin].astype(np.float64))
@@ -244,3 +249,72 @@ def test_parity_per_block_lorenzo(gb, ctx, kind, shape, eb, mode, R, C):
     arc, nb, oa = compare_stages(gb, ctx, x, eb, mode, R, C, lblock=1)
     assert ref.sections(oa)["lblock"] == 1
     check_decompress(gb, ctx, arc, nb, oa, x, eb, mode)
+
+
+ORDER_CASES = [
+    # Lorenzo predictor of order n (Sec. 3.1.2, binomial coefficients)
+    ("walk", (100003,), 1e-4, ref.EB_REL, 512, 4096, 2),
+    ("walk", (70001,), 1e-3, ref.EB_REL, 64, 256, 3),
+    ("sinus", (181, 1037), 1e-4, ref.EB_REL, 512, 1024, 2),
+    ("grf", (150, 170), 1e-4, ref.EB_REL, 32768, 256, 3),
+    ("lognormal", (37, 41, 67), 1e-3, ref.EB_REL, 512, 256, 2),
+    ("sinus", (20, 9, 33), 1e-4, ref.EB_REL, 64, 64, 3),
+    ("sinus", (70, 1, 45), 1e-4, ref.EB_REL, 512, 1024, 2),
+]
+
+
+@pytest.mark.parametrize("kind,shape,eb,mode,R,C,order", ORDER_CASES,
+                         ids=[f"ord{c[6]}-{c[0]}{'x'.join(map(str, c[1]))}-R{c[4]}" for c in ORDER_CASES])
+def test_parity_lorenzo_order(gb, ctx, kind, shape, eb, mode, R, C, order):
+    x = workloads.field_for(kind, shape, seed=sum(shape) + 5 * R + order)
+    arc, nb, oa = compare_stages(gb, ctx, x, eb, mode, R, C, order=order)
+    assert ref.sections(oa)["order"] == order
+    check_decompress(gb, ctx, arc, nb, oa, x, eb, mode)
+
+
+def test_lorenzo_order_nonfinite_and_exceptions(gb, ctx):
+    x = workloads.field_for("sinus", (90, 110), seed=17)
+    x[3, 4] = np.nan
+    x[50, 0] = np.inf
+    x[7, 99] = np.float32(3e38)
+    for order in (2, 3):
+        arc, nb, oa = compare_stages(gb, ctx, x, 1e-4, ref.EB_REL, 512, 512, order=order)
+        assert ref.sections(oa)["e"] >= 2  # the NaN and the Inf
+        check_decompress(gb, ctx, arc, nb, oa, x, 1e-4, ref.EB_REL)
+
+
+FOLD_CASES = [
+    # 4D fields (QMCPACK-like), predicted as 3D over the folded two slowest axes
+    ("sinus", (3, 5, 29, 31), 1e-4, 512, 256, 1),
+    ("sinus", (6, 10, 33, 47), 1e-3, 512, 1024, 1),
+    ("sinus", (4, 3, 17, 23), 1e-4, 64, 128, 2),
+]
+
+
+@pytest.mark.parametrize("kind,shape,eb,R,C,order", FOLD_CASES,
+                         ids=[f"4d-{'x'.join(map(str, c[1]))}-ord{c[5]}" for c in FOLD_CASES])
+def test_parity_4d_fields(gb, ctx, kind, shape, eb, R, C, order):
+    x = workloads.field_for(kind, shape, seed=sum(shape) + order)
+    arc, nb, oa = compare_stages(gb, ctx, x, eb, ref.EB_REL, R, C, order=order)
+    s_ = ref.sections(oa)
+    assert s_["ndim"] == 4
+    check_decompress(gb, ctx, arc, nb, oa, x, eb, ref.EB_REL)
+
+
+@pytest.mark.parametrize("kind,shape,R,C", [("walk", (100003,), 512, 4096), ("grf", (181, 1037), 512, 1024),
+                                             ("grf", (300, 200), 32768, 4096), ("lognormal", (37, 41, 67), 512, 256)])
+def test_codeword_width_option_keeps_bytes(gb, ctx, kind, shape, R, C):
+    """64-bit codeword entries (the paper's enc.64) give the same archive as
+    the adaptive 32-bit choice (Sec. 3.2.2)."""
+    x = workloads.field_for(kind, shape, seed=sum(shape) + 11)
+    xt = torch.from_numpy(x).cuda()
+    a32, n32 = ctx.compress(xt, 1e-4, ref.EB_REL, R, C)
+    a32 = a32[:n32].clone()
+    ctx.set_option(gb.OPT_CODEWORD_BITS, 64)
+    try:
+        a64, n64 = ctx.compress(xt, 1e-4, ref.EB_REL, R, C)
+    finally:
+        ctx.set_option(gb.OPT_CODEWORD_BITS, 0)
+    torch.cuda.synchronize()
+    assert n64 == n32 and torch.equal(a64[:n64], a32)
+    assert np.array_equal(a32.cpu().numpy(), ref.compress(x, 1e-4, ref.EB_REL, radius=R, chunk=C))
