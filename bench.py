@@ -45,6 +45,9 @@ def parse():
     ap.add_argument("--cpu-sample-log2", type=int, default=26)
     ap.add_argument("--skip-batch", action="store_true",
                     help="skip the batched vs per-field measurement (16 x 1800x3600 fields)")
+    ap.add_argument("--skip-micro", action="store_true",
+                    help="skip the codebook-vs-bins and 32/64-bit codeword micro-benchmarks")
+    ap.add_argument("--skip-serving", action="store_true", help="skip the serving-mix measurement")
     return ap.parse_args()
 
 
@@ -100,6 +103,128 @@ def batch_vs_per_field(ctx, gbsz, workloads, dev, steps=5):
             "per_field_gbs": res["per_field"], "batched_gbs": res["batched"],
             "speedup": res["batched"] / res["per_field"], "steps": steps,
             "graph_replays": int(g1[1] - g0[1] + g1[3] - g0[3])}
+
+
+def codebook_vs_bins(ctx, gbsz, dev, reps=5):
+    """Codebook build time against the number of bins (2R = 128 .. 65536),
+    the paper's codebook micro-benchmark (Sec. 3.2.2, its evaluation of the
+    codebook stage): a white-noise field of 2^22 points with an absolute eb
+    of 2.12 / R, so the residuals spread over most of the bins (residual
+    standard deviation about R / 3)."""
+    import torch
+    g = torch.Generator(device=dev)
+    g.manual_seed(1006)
+    x = torch.randn(1 << 22, generator=g, device=dev, dtype=torch.float32)
+    out = []
+    for R in [64 << k for k in range(10)]:
+        eb = 2.12 / R
+        arc = torch.empty(gbsz.compress_bound([x.numel()], eb, gbsz.EB_ABS, R, 4096), dtype=torch.uint8, device=dev)
+        ctx.compress(x, eb, gbsz.EB_ABS, R, 4096, out=arc)  # warm-up
+        torch.cuda.synchronize(dev)
+        ctx.profile_read()
+        ctx.profile_enable(True)
+        for _ in range(reps):
+            ctx.compress(x, eb, gbsz.EB_ABS, R, 4096, out=arc)
+        ms, calls, _ = ctx.profile_read()
+        ctx.profile_enable(False)
+        hist = ctx.debug_copy(gbsz.DEBUG_HIST, 2 * R, np.uint32)
+        out.append({"bins": 2 * R, "used_bins": int((hist > 0).sum()),
+                    "codebook_us": 1e3 * ms[2] / max(calls[2], 1)})
+    return {"workload": "2^22 N(0,1) white noise, abs eb 2.12/R, chunk 4096", "points": out}
+
+
+def encode_width(ctx, gbsz, x, eb, radius, chunk, dev, reps=5):
+    """Encode (bit counts + offset scan + pack) with the adaptive 32-bit
+    codeword entries against forced 64-bit entries (the paper's enc.32 /
+    enc.64 comparison), on the benchmark's own field; the archives must be
+    the same bytes."""
+    import torch
+    res = {}
+    arcs = {}
+    for name, width in (("enc32", 0), ("enc64", 64)):
+        ctx.set_option(gbsz.OPT_CODEWORD_BITS, width)
+        try:
+            arc = torch.empty(gbsz.compress_bound([x.numel()], eb, gbsz.EB_REL, radius, chunk), dtype=torch.uint8,
+                              device=dev)
+            _, nb = ctx.compress(x, eb, gbsz.EB_REL, radius, chunk, out=arc)
+            torch.cuda.synchronize(dev)
+            ctx.profile_read()
+            ctx.profile_enable(True)
+            for _ in range(reps):
+                _, nb = ctx.compress(x, eb, gbsz.EB_REL, radius, chunk, out=arc)
+            ms, calls, _ = ctx.profile_read()
+            ctx.profile_enable(False)
+        finally:
+            ctx.set_option(gbsz.OPT_CODEWORD_BITS, 0)
+        enc_ms = sum(ms[3:6]) / reps
+        res[name] = {"encode_ms": enc_ms, "encode_gbs": 4.0 * x.numel() / (enc_ms / 1e3) / 1e9,
+                     "pack_ms": ms[5] / reps}
+        arcs[name] = (arc, nb)
+    (a32, n32), (a64, n64) = arcs["enc32"], arcs["enc64"]
+    res["same_bytes"] = bool(n32 == n64 and torch.equal(a32[:n32], a64[:n64]))
+    return res
+
+
+def serving(gbsz, workloads, serve, dev, pool_size=32, requests=256, rate=200.0, max_bytes=32 << 20):
+    """Serving mix (Poisson arrivals, half compress and half decompress, mixed
+    ranks and sizes): p50 / p99 latency and throughput at the offered rate,
+    then with every request submitted at once (capacity), and a bit-equality
+    check of every result against the same request run alone."""
+    import time
+    import torch
+    rng = np.random.default_rng(1005)
+    desc = workloads.serving_mix(count=pool_size, seed=1005, max_bytes=max_bytes)
+    gens = {1: "sinus", 2: "walk", 3: "grf", 4: "lognormal"}
+    pool = []
+    for d in desc:
+        kind = gens[d["gen"]]
+        if d["rank"] == 1:
+            kind = "walk"
+        elif kind == "walk":
+            kind = "sinus"
+        pool.append((torch.from_numpy(workloads.field_for(kind, d["shape"], seed=2000 + d["id"])).to(dev), d["rel"]))
+    alone = gbsz.Context(dev.index or 0)
+    ref_arc, ref_out = [], []
+    for f, rel in pool:
+        a, nb = alone.compress(f, rel)
+        ref_arc.append((a[:nb].clone(), nb))
+        ref_out.append(alone.decompress(a, nb))
+    torch.cuda.synchronize(dev)
+    alone.close()
+    picks = [(int(rng.integers(0, pool_size)), bool(rng.random() < 0.5)) for _ in range(requests)]
+    gaps = rng.exponential(1.0 / rate, requests)
+
+    def run(paced):
+        srv = serve.Server(workers=2, max_batch=8, mem_budget=64 << 30).start()
+        reqs = []
+        for (k, comp), gap in zip(picks, gaps):
+            f, rel = pool[k]
+            if comp:
+                reqs.append((k, comp, srv.submit(serve.COMPRESS, f, eb=rel)))
+            else:
+                a, nb = ref_arc[k]
+                reqs.append((k, comp, srv.submit(serve.DECOMPRESS, a, nbytes=nb)))
+            if paced:
+                time.sleep(float(gap))
+        equal = True
+        for k, comp, r in reqs:
+            out = r.wait(600)
+            if comp:
+                arc, nb = out
+                equal &= nb == ref_arc[k][1] and torch.equal(arc[:nb], ref_arc[k][0])
+            else:
+                equal &= torch.equal(out.view(torch.int32), ref_out[k].view(torch.int32))
+        st = srv.stats()
+        srv.stop()
+        return st, equal
+
+    paced, eq1 = run(True)
+    burst, eq2 = run(False)
+    keep = ("p50_ms", "p99_ms", "throughput_gbs", "mean_batch")
+    return {"workload": f"{requests} requests over {pool_size} fields of rank 1-3, 256 KiB-{max_bytes >> 20} MiB "
+                        f"log-uniform, rel eb 1e-2/1e-3/1e-4, half compress, Poisson {rate:g} req/s",
+            "offered": {k: paced[k] for k in keep}, "all_at_once": {k: burst[k] for k in keep},
+            "bit_equal_to_alone": bool(eq1 and eq2)}
 
 
 def workload_config(a, n, chunk):
@@ -396,6 +521,16 @@ def main():
     if not a.skip_batch:
         batch = batch_vs_per_field(ctx, gbsz, workloads, dev)
 
+    micro = None
+    if rank == 0 and not a.skip_micro:
+        micro = {"codebook_vs_bins": codebook_vs_bins(ctx, gbsz, dev),
+                 "codeword_width": encode_width(ctx, gbsz, x, a.rel, a.radius, chunk, dev)}
+
+    serving_res = None
+    if rank == 0 and not a.skip_serving:
+        from paper_2007_09625_gb300 import serve
+        serving_res = serving(gbsz, workloads, serve, dev)
+
     cpu = None
     if rank == 0 and not a.skip_cpu_baseline:
         ns = min(n, 1 << a.cpu_sample_log2)
@@ -422,7 +557,7 @@ def main():
                 "pipeline_roofline": pipe,
                 "stage_ms_per_step": {nm: stage_ms[i] / a.steps for i, nm in enumerate(stage_names)},
                 "roofline": roofline, "kernels": per_kernel, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
-                "batch_vs_per_field": batch,
+                "batch_vs_per_field": batch, "micro": micro, "serving": serving_res,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist:
