@@ -186,6 +186,26 @@ gbsz_status gbsz_decompress_host(gbsz_ctx *ctx, const void *h_archive,
                                  size_t bytes, float *h_field,
                                  uint64_t capacity_elems, void *stream);
 
+/* Asynchronous form of gbsz_decompress_host, for pipelines that upload the
+ * next field while this one downloads: parses the header from h_archive,
+ * enqueues the archive upload, the decompression and the field download on
+ * `stream`, and returns without waiting.  The call uses scratch of its own,
+ * so other calls on the context may run meanwhile (on other streams); one
+ * asynchronous call may be pending per context.  h_archive and h_field must
+ * stay valid and unmodified until gbsz_async_wait returns.  Pinned host
+ * buffers are needed for the copies to overlap other work.
+ * Errors at the call: INVALID_ARG (NULL, or a call already pending),
+ * CORRUPT (header), CAPACITY, OOM, CUDA.  Device-side checks are reported
+ * by gbsz_async_wait. */
+gbsz_status gbsz_decompress_host_async(gbsz_ctx *ctx, const void *h_archive,
+                                       size_t bytes, float *h_field,
+                                       uint64_t capacity_elems, void *stream);
+
+/* Waits for the pending asynchronous call, if any, and returns its status
+ * (GBSZ_OK when nothing is pending): CORRUPT, CUDA or TIMEOUT as for
+ * gbsz_decompress. */
+gbsz_status gbsz_async_wait(gbsz_ctx *ctx);
+
 /* Parses a host copy of an archive header (at least 128 bytes; `bytes` is
  * the archive's full size, used for the size check).  Fills *out and *n.
  * Host-only.  Errors: INVALID_ARG (NULL), CORRUPT. */

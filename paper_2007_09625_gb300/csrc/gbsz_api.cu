@@ -189,6 +189,15 @@ struct gbsz_ctx {
     cudaEvent_t fork = nullptr;
     // staging of the host-buffer API
     Buf stage_field, stage_archive;
+    // the pending asynchronous host decompress: its own slot, staging,
+    // control copy and completion event, so that synchronous calls on the
+    // context can run while it is in flight
+    Slot *aslot = nullptr;
+    Buf astage_field, astage_archive;
+    HostBuf<Control> actl;
+    cudaEvent_t adone = nullptr;
+    bool apending = false;
+    uint64_t azeros = 0;  // outliers the pending call's archive declares
     // last call (debug copies)
     uint64_t last_n = 0, last_dn = 0;
     uint32_t last_nbins = 0;
@@ -709,6 +718,14 @@ void gbsz_destroy(gbsz_ctx *c)
         delete s;
     }
     c->slots.clear();
+    if (c->aslot) {
+        c->aslot->release();
+        delete c->aslot;
+    }
+    c->astage_field.release();
+    c->astage_archive.release();
+    c->actl.release();
+    if (c->adone) cudaEventDestroy(c->adone);
     c->gcomp.drop();
     c->gdecomp.drop();
     c->tune_arc.release();
@@ -1060,6 +1077,53 @@ gbsz_status gbsz_decompress_host(gbsz_ctx *c, const void *h_archive, size_t byte
         cudaStreamSynchronize(st) != cudaSuccess)
         return GBSZ_ERR_CUDA;
     return GBSZ_OK;
+}
+
+gbsz_status gbsz_decompress_host_async(gbsz_ctx *c, const void *h_archive, size_t bytes, float *h_field,
+                                       uint64_t capacity_elems, void *stream)
+{
+    if (!c || !h_archive || !h_field || c->apending) return GBSZ_ERR_INVALID_ARG;
+    Header h;
+    gbsz_status s = parse_header(static_cast<const uint8_t *>(h_archive), bytes, &h);
+    if (s != GBSZ_OK) return s;
+    if (h.n > capacity_elems) return GBSZ_ERR_CAPACITY;
+    DevGuard g(c->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (!c->aslot) {
+        c->aslot = new Slot();
+        if (!c->aslot->init()) {
+            c->aslot->release();
+            delete c->aslot;
+            c->aslot = nullptr;
+            return GBSZ_ERR_OOM;
+        }
+    }
+    if (!c->adone && cudaEventCreateWithFlags(&c->adone, cudaEventDisableTiming) != cudaSuccess) return GBSZ_ERR_CUDA;
+    if (!c->actl.ensure(1) || !c->astage_field.ensure(h.n * 4) || !c->astage_archive.ensure(h.total))
+        return GBSZ_ERR_OOM;
+    if (cudaMemcpyAsync(c->astage_archive.p, h_archive, h.total, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return GBSZ_ERR_CUDA;
+    s = enqueue_decompress(c, c->aslot, h, c->astage_archive.p, c->astage_field.as<float>(), st);
+    if (s != GBSZ_OK) return s;
+    if (cudaMemcpyAsync(h_field, c->astage_field.p, h.n * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaMemcpyAsync(c->actl.p, c->aslot->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaEventRecord(c->adone, st) != cudaSuccess)
+        return GBSZ_ERR_CUDA;
+    c->azeros = h.m;
+    c->apending = true;
+    return GBSZ_OK;
+}
+
+gbsz_status gbsz_async_wait(gbsz_ctx *c)
+{
+    if (!c) return GBSZ_ERR_INVALID_ARG;
+    if (!c->apending) return GBSZ_OK;
+    DevGuard g(c->device);
+    c->apending = false;
+    if (cudaEventSynchronize(c->adone) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GBSZ_ERR_CUDA;
+    const Control &ctl = c->actl.p[0];
+    if (ctl.error) return map_device_error(ctl.error);
+    return ctl.zeros == c->azeros ? GBSZ_OK : GBSZ_ERR_CORRUPT;
 }
 
 gbsz_status gbsz_debug_copy(gbsz_ctx *c, int which, void *h_dst, size_t bytes)

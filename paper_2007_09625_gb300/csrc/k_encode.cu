@@ -361,6 +361,7 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
         const uint32_t rounds = multi ? (uint32_t)((ulen + kRound - 1) / kRound) : 1u;
         const ulonglong2 off = a.unit_off[u];
         const unsigned long long W0 = off.x, O0 = off.y & 0xFFFFFFFFull, E0 = off.y >> 32;
+        const bool unit_exc = any_exc && a.unit_exc[u] != 0;  // exceptions of the unit, counted by dual-quant
         if (u == nunits - 1 && lane == 0) {
             const ulonglong2 tot = a.unit_tot[u];
             const unsigned long long W = W0 + tot.x;
@@ -511,14 +512,13 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
             // outliers and exceptions in index order
             const uint32_t nz = __popcll(zlo) + __popcll(zhi);
             uint32_t ne = 0;
-            if (any_exc) {
+            if (unit_exc) {
                 for (unsigned long long m = zlo; m; m &= m - 1) ne += a.dscr[s0 + __ffsll(m) - 1].y != 0;
                 for (unsigned long long m = zhi; m; m &= m - 1) ne += a.dscr[s0 + 63 + __ffsll(m)].y != 0;
             }
             const uint32_t oinc = warp_incl_scan(nz), einc = warp_incl_scan(ne);
             uint64_t oi = O0 + o_run + (oinc - nz), ei = E0 + e_run + (einc - ne);
-            auto emit_outlier = [&](uint64_t idx) {
-                const int2 dv = a.dscr[idx];
+            auto emit_outlier = [&](uint64_t idx, int2 dv) {
                 const uint64_t o8 = L0.outl + 8 * oi++;
                 if (o8 + 8 <= a.capacity) {
                     put_u32(a.archive + o8, (uint32_t)idx);
@@ -536,8 +536,32 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
                     }
                 }
             };
-            for (unsigned long long m = zlo; m; m &= m - 1) emit_outlier(s0 + __ffsll(m) - 1);
-            for (unsigned long long m = zhi; m; m &= m - 1) emit_outlier(s0 + 63 + __ffsll(m));
+            // four of the lane's outliers at a time: their residuals are
+            // loaded together, then written in index order
+            unsigned long long mlo = zlo, mhi = zhi;
+            while (mlo | mhi) {
+                uint64_t idx[4];
+                bool has[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) {
+                    has[k] = (mlo | mhi) != 0;
+                    uint32_t j = 0;
+                    if (mlo) {
+                        j = __ffsll(mlo) - 1;
+                        mlo &= mlo - 1;
+                    } else if (mhi) {
+                        j = 63 + __ffsll(mhi);
+                        mhi &= mhi - 1;
+                    }
+                    idx[k] = s0 + j;
+                }
+                int2 dv[4];
+#pragma unroll
+                for (int k = 0; k < 4; k++) dv[k] = has[k] ? a.dscr[idx[k]] : make_int2(0, 0);
+#pragma unroll
+                for (int k = 0; k < 4; k++)
+                    if (has[k]) emit_outlier(idx[k], dv[k]);
+            }
             o_run += __shfl_sync(0xffffffffu, oinc, 31);
             e_run += __shfl_sync(0xffffffffu, einc, 31);
             round_bits += rtot;

@@ -41,6 +41,8 @@ SIGNATURES = {
     "gbsz_decompress_batch": ([_P, C.c_uint32, _P, _P, _P, _P, _P, _P], C.c_int),
     "gbsz_autotune": ([_P, _P, _P, _P, C.POINTER(C.c_float), _P], C.c_int),
     "gbsz_set_option": ([_P, C.c_int, C.c_int64], C.c_int),
+    "gbsz_decompress_host_async": ([_P, _P, C.c_size_t, _P, C.c_uint64, _P], C.c_int),
+    "gbsz_async_wait": ([_P], C.c_int),
 }
 OPT_CODEWORD_BITS = 1
 
@@ -258,6 +260,20 @@ class Context:
         if st != OK:
             raise GbszError(st, "gbsz_compress_host")
         return out, nbytes.value
+
+    def decompress_host_async(self, archive, nbytes, out, stream=None):
+        """Enqueue a host-buffer decompress and return at once (see
+        gbsz_decompress_host_async); async_wait() reports its status."""
+        aptr, _ = _host_ptr(archive)
+        optr, _ = _host_ptr(out)
+        st = load().gbsz_decompress_host_async(self.h, aptr, int(nbytes), optr, _numel(out), _stream(stream))
+        if st != OK:
+            raise GbszError(st, "gbsz_decompress_host_async")
+
+    def async_wait(self):
+        st = load().gbsz_async_wait(self.h)
+        if st != OK:
+            raise GbszError(st, "gbsz_async_wait")
 
     def decompress_host(self, archive, nbytes, out, stream=None):
         aptr, _ = _host_ptr(archive)

@@ -176,6 +176,41 @@ def test_host_buffer_api(gb, ctx):
     assert np.array_equal(y.view(np.uint32), ref.decompress(oa).view(np.uint32))
 
 
+def test_async_host_decompress_pipeline(gb, ctx):
+    """gbsz_decompress_host_async: results equal the oracle's while
+    synchronous calls run on the context meanwhile; one call may be pending;
+    device-side corruption is reported by the wait."""
+    xs = [workloads.field_for("walk", (200003,), seed=40 + i) for i in range(3)]
+    arcs = [torch.empty(gb.compress_bound([x.size], 1e-4), dtype=torch.uint8).pin_memory() for x in xs]
+    outs = [torch.empty(x.shape, dtype=torch.float32).pin_memory() for x in xs]
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    nbs = []
+    for i, x in enumerate(xs):
+        _, nb = ctx.compress_host(torch.from_numpy(x).pin_memory(), 1e-4, out=arcs[i], stream=s1)
+        nbs.append(nb)
+        ctx.async_wait()
+        ctx.decompress_host_async(arcs[i], nb, outs[i], stream=s2)
+        if i == 1:
+            with pytest.raises(gb.GbszError):  # one pending call at a time
+                ctx.decompress_host_async(arcs[0], nbs[0], outs[0], stream=s2)
+    ctx.async_wait()
+    ctx.async_wait()  # nothing pending: ok
+    for i, x in enumerate(xs):
+        oa = arcs[i][:nbs[i]].numpy()
+        assert np.array_equal(oa, ref.compress(x, 1e-4, ref.EB_REL, 512, gb.auto_chunk([x.size])))
+        assert np.array_equal(outs[i].numpy().view(np.uint32), ref.decompress(oa).view(np.uint32)), i
+    # chunk 0 claims two more words than it has: the word-offset scan on the
+    # device finds the total off, and the wait reports it
+    bad = arcs[0][:nbs[0]].clone().pin_memory()
+    o = ref.sections(bad.numpy())["off_bits"]
+    b0 = int(bad[o:o + 4].numpy().view(np.uint32)[0]) + 64
+    bad[o:o + 4] = torch.from_numpy(np.array([b0], np.uint32).view(np.uint8))
+    ctx.decompress_host_async(bad, nbs[0], outs[0], stream=s2)
+    with pytest.raises(gb.GbszError) as e:
+        ctx.async_wait()
+    assert e.value.status == gb.ERR_CORRUPT
+
+
 def test_gpu_decodes_oracle_archives(gb, ctx):
     x = workloads.field_for("lognormal", (21, 30, 50), seed=13)
     oa = ref.compress(x, 1e-4, ref.EB_REL, radius=1024, chunk=128)
