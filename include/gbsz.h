@@ -206,6 +206,53 @@ gbsz_status gbsz_decompress_host_async(gbsz_ctx *ctx, const void *h_archive,
  * gbsz_decompress. */
 gbsz_status gbsz_async_wait(gbsz_ctx *ctx);
 
+/* Serving loop (continuous batching).  A server owns `workers` threads, each
+ * with its own context and stream.  Submitted requests wait in a FIFO queue;
+ * a free worker takes the oldest requests, as many as fit `mem_budget` bytes
+ * of context scratch (about 12 bytes per point each) and at most `max_batch`,
+ * and runs them with gbsz_compress_batch / gbsz_decompress_batch, so batches
+ * of different workers overlap on the GPU.  Every result is the same bytes as
+ * the single-field call's.  The paper has no serving layer; this is the
+ * batching its block-wise design allows, for many independent fields.
+ *   gbsz_server_create   workers in [1, 64], max_batch in [1, 1024],
+ *                        mem_budget > 0.  Errors: INVALID_ARG, OOM, and the
+ *                        errors of gbsz_create.
+ *   gbsz_server_destroy  runs every queued request, then frees the server.
+ *   gbsz_server_submit_* queue one request and return its ticket (> 0).  The
+ *                        device buffers belong to the caller and must stay
+ *                        valid until the request is done; the input must be
+ *                        complete on the device when submitted.  Errors:
+ *                        INVALID_ARG, CAPACITY (the request alone needs more
+ *                        than mem_budget; it is not queued).
+ *   gbsz_server_poll     *done = 1 and *status / *out_bytes (archive bytes for
+ *                        a compress, field bytes for a decompress) once the
+ *                        request is done; the ticket is then released.
+ *                        INVALID_ARG for an unknown or released ticket.
+ *   gbsz_server_wait     the same, waiting up to timeout_s seconds (< 0: no
+ *                        limit); TIMEOUT if still pending.
+ *   gbsz_server_stats    out6 = {completed requests, p50 latency ms, p99
+ *                        latency ms, mean batch size, input GB/s over the
+ *                        span, span s from first arrival to last completion}.
+ */
+typedef struct gbsz_server gbsz_server;
+gbsz_status gbsz_server_create(gbsz_server **out, int device, uint32_t workers,
+                               uint32_t max_batch, uint64_t mem_budget);
+void gbsz_server_destroy(gbsz_server *s);
+gbsz_status gbsz_server_submit_compress(gbsz_server *s, const float *d_field,
+                                        const gbsz_params *p, void *d_archive,
+                                        size_t capacity, uint64_t *ticket);
+gbsz_status gbsz_server_submit_decompress(gbsz_server *s,
+                                          const void *d_archive, size_t bytes,
+                                          float *d_field,
+                                          uint64_t capacity_elems,
+                                          uint64_t *ticket);
+gbsz_status gbsz_server_poll(gbsz_server *s, uint64_t ticket, int *done,
+                             gbsz_status *status, size_t *out_bytes);
+gbsz_status gbsz_server_wait(gbsz_server *s, uint64_t ticket,
+                             double timeout_s, gbsz_status *status,
+                             size_t *out_bytes);
+gbsz_status gbsz_server_stats(gbsz_server *s, double *out6);
+
 /* Parses a host copy of an archive header (at least 128 bytes; `bytes` is
  * the archive's full size, used for the size check).  Fills *out and *n.
  * Host-only.  Errors: INVALID_ARG (NULL), CORRUPT. */

@@ -14,8 +14,8 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libgbsz.so")
 SOURCES = ["gbsz_api.cu", "k_quant.cu", "k_codebook.cu", "k_encode.cu", "k_decode.cu", "k_recon.cu",
-           "noalloc.cu"]
-HEADERS = ["common.cuh", "scan.cuh"]
+           "noalloc.cu", "server.cu"]
+HEADERS = ["common.cuh", "scan.cuh", "server_core.h"]
 
 NVCC = os.environ.get("NVCC", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -43,6 +43,13 @@ SIGNATURES = {
     "gbsz_set_option": ([_P, C.c_int, C.c_int64], C.c_int),
     "gbsz_decompress_host_async": ([_P, _P, C.c_size_t, _P, C.c_uint64, _P], C.c_int),
     "gbsz_async_wait": ([_P], C.c_int),
+    "gbsz_server_create": ([C.POINTER(C.c_void_p), C.c_int, C.c_uint32, C.c_uint32, C.c_uint64], C.c_int),
+    "gbsz_server_destroy": ([_P], None),
+    "gbsz_server_submit_compress": ([_P, _P, _P, _P, C.c_size_t, C.POINTER(C.c_uint64)], C.c_int),
+    "gbsz_server_submit_decompress": ([_P, _P, C.c_size_t, _P, C.c_uint64, C.POINTER(C.c_uint64)], C.c_int),
+    "gbsz_server_poll": ([_P, C.c_uint64, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)], C.c_int),
+    "gbsz_server_wait": ([_P, C.c_uint64, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_size_t)], C.c_int),
+    "gbsz_server_stats": ([_P, _P], C.c_int),
 }
 OPT_CODEWORD_BITS = 1
 

@@ -3,8 +3,9 @@ the oracle byte for byte, in the launch configuration the benchmark uses
 (automatic chunk, device-resident buffers, one context reused).
 
 Sizes: 64^3 sinusoids; 2^28 random walk with 1% spikes (the benchmark
-workload); one 1800x3600 power-law field at rel 1e-3 and 1e-4; 512^3
-lognormal at radius 512 and 32768.  The oracle runs multi-threaded where
+workload), also in the per-block Lorenzo mode; one 1800x3600 power-law field
+at rel 1e-3 and 1e-4; 512^3 lognormal at radius 512 and 32768, and with the
+order-2 predictor; a field of the paper's 4D QMCPACK shape 288x115x69x69.  The oracle runs multi-threaded where
 its loops allow; these tests take a few minutes.
 """
 import numpy as np
@@ -24,14 +25,14 @@ def ctx(gb):
     c.close()
 
 
-def roundtrip_vs_oracle(gb, ctx, x, rel, R):
+def roundtrip_vs_oracle(gb, ctx, x, rel, R, order=1, lblock=0):
     n = x.size
     chunk = gb.auto_chunk(list(x.shape)[::-1], R)
     xt = torch.from_numpy(x).cuda()
-    arc, nb = ctx.compress(xt, rel, gb.EB_REL, R, chunk)
+    arc, nb = ctx.compress(xt, rel, gb.EB_REL, R, chunk, order=order, lblock=lblock)
     y = ctx.decompress(arc, nb)
     torch.cuda.synchronize()
-    oa = ref.compress(x, rel, ref.EB_REL, radius=R, chunk=chunk, omp=True)
+    oa = ref.compress(x, rel, ref.EB_REL, radius=R, chunk=chunk, omp=True, order=order, lblock=lblock)
     ga = arc[:nb].cpu().numpy()
     if not (nb == oa.size and np.array_equal(ga, oa)):
         gs, os_ = ref.sections(ga), ref.sections(oa)
@@ -72,3 +73,26 @@ def test_grf_1800x3600(gb, ctx, rel):
 def test_lognormal_512cubed(gb, ctx, R):
     x = workloads.lognormal_3d(512, seed=1004)
     roundtrip_vs_oracle(gb, ctx, x, 1e-4, R)
+
+
+def test_random_walk_2p28_per_block(gb, ctx):
+    x = workloads.random_walk_1d(1 << 28, seed=1002)
+    roundtrip_vs_oracle(gb, ctx, x, 1e-4, 512, lblock=1)
+
+
+def test_lognormal_512cubed_order2(gb, ctx):
+    x = workloads.lognormal_3d(512, seed=1004)
+    roundtrip_vs_oracle(gb, ctx, x, 1e-4, 512, order=2)
+
+
+def test_qmcpack_shape_4d(gb, ctx):
+    """288x115x69x69 (the paper's QMCPACK extents): a smooth separable field
+    plus noise, predicted as 3D over the folded two slowest axes."""
+    rng = np.random.default_rng(1007)
+    a = np.arange(288, dtype=np.float32)[:, None, None, None]
+    b = np.arange(115, dtype=np.float32)[None, :, None, None]
+    c = np.arange(69, dtype=np.float32)[None, None, :, None]
+    d = np.arange(69, dtype=np.float32)[None, None, None, :]
+    x = np.sin(a / 7) + np.cos(b / 5) + np.sin(c / 3) * np.cos(d / 4)
+    x = (x + rng.normal(0, 1e-3, x.shape).astype(np.float32)).astype(np.float32)
+    roundtrip_vs_oracle(gb, ctx, x, 1e-4, 512)

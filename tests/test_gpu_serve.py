@@ -62,3 +62,35 @@ def test_mixed_stream_matches_alone(gb):
     srv.stop()
     alone.close()
     assert st["requests"] == len(fields) and st["p99_ms"] >= st["p50_ms"]
+
+
+def test_server_reports_per_request_errors_and_budget(gb):
+    from oracle import ref
+    x = torch.from_numpy(workloads.field_for("walk", (300001,), seed=5)).cuda()
+    alone = gb.Context(0)
+    a, nb = alone.compress(x, 1e-4)
+    y_alone = alone.decompress(a, nb)
+    torch.cuda.synchronize()
+    bad = a[:nb].clone()
+    o = ref.sections(bad.cpu().numpy())["off_bits"]
+    b0 = int(bad[o:o + 4].cpu().numpy().view(np.uint32)[0]) + 64  # chunk 0 claims two more words
+    bad[o:o + 4] = torch.from_numpy(np.array([b0], np.uint32).view(np.uint8)).cuda()
+    torch.cuda.synchronize()
+    srv = serve.Server(workers=2, max_batch=2, mem_budget=64 << 20).start()
+    good = srv.submit(serve.DECOMPRESS, a, nbytes=nb)
+    broken = srv.submit(serve.DECOMPRESS, bad, nbytes=nb)
+    comp = srv.submit(serve.COMPRESS, x, eb=1e-4)
+    too_big = srv.submit(serve.COMPRESS, torch.zeros(8 << 20, device="cuda"), eb=1e-4)  # 12 B/point > 64 MiB
+    assert torch.equal(good.wait(60).view(torch.int32), y_alone.view(torch.int32))
+    with pytest.raises(gb.GbszError) as e:
+        broken.wait(60)
+    assert e.value.status == gb.ERR_CORRUPT
+    arc, n2 = comp.wait(60)
+    assert n2 == nb and torch.equal(arc[:n2], a[:nb])
+    assert too_big.status == "rejected"
+    with pytest.raises(MemoryError):
+        too_big.wait(1)
+    st = srv.stats()
+    srv.stop()
+    alone.close()
+    assert st["requests"] == 2  # completed without error
