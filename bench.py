@@ -227,6 +227,16 @@ def serving(gbsz, workloads, serve, dev, pool_size=32, requests=256, rate=200.0,
             "bit_equal_to_alone": bool(eq1 and eq2)}
 
 
+def workload_chunk(n):
+    """The Huffman chunk the library's rule picks for n points (chunk = 0):
+    about 1024 chunks per SM of a 152-SM GB300, a power of two in 64..4096.
+    Both arms of the benchmark use it, so they run the same configuration."""
+    c = 64
+    while c < 4096 and 2 * c <= n // (152 * 1024):
+        c *= 2
+    return c
+
+
 def workload_config(a, n, chunk):
     return {"workload": f"1D random walk 2^{a.log2n} FP32 (1% spikes), rel eb {a.rel:g}, radius {a.radius}, "
                         f"chunk {chunk}", "n": n, "eb_mode": "rel", "eb": a.rel, "radius": a.radius,
@@ -358,7 +368,7 @@ def run_reference(a):
     n_full = 1 << a.log2n
     ns = min(n_full, 1 << a.cpu_sample_log2)
     x = workloads.random_walk_1d(n_full, seed=1002)[:ns].copy()
-    chunk = a.chunk or 4096
+    chunk = a.chunk or workload_chunk(n_full)
     for _ in range(a.warmup):
         cpu_oracle_time(x, a, chunk)
     ts = []
@@ -399,6 +409,7 @@ def main():
     x = torch.from_numpy(x_host).to(dev)
     ctx = gbsz.Context(local)
     chunk = a.chunk or gbsz.auto_chunk([n], a.radius)
+    assert a.chunk or chunk == workload_chunk(n), "chunk rule differs between the arms"
     bound = gbsz.compress_bound([n], a.rel, gbsz.EB_REL, a.radius, chunk)
     arc = torch.empty(bound, dtype=torch.uint8, device=dev)
     y = torch.empty_like(x)
