@@ -315,33 +315,11 @@ __device__ __forceinline__ uint32_t ld_shared_pred32(bool p, const void *addr, u
     return v;
 }
 
-// Window of the fast decoder: hi, lo, q0 = words v .. v+2.  Two codes of at
-// most 15 bits cross at most one word boundary per step, so three words
-// cover both lookups; word v+3 is read at the start of the step and shifted
-// in with selects if a word was consumed.
-struct Window3 {
-    uint32_t v, bo, hi, lo, q0;
-};
-
-__device__ __forceinline__ void step3(Window3 &w, uint32_t nxt, uint32_t len)
+__device__ __forceinline__ void decode_two(Window &w, const Ring<kRingFast> &rg, const uint32_t *l1,
+                                           const uint16_t *ft, uint32_t shift, uint32_t &minlen, bool act1,
+                                           bool act2, uint32_t &s1, uint32_t &s2)
 {
-    w.bo += len;
-    const bool adv = w.bo >= 32;
-    w.bo &= 31u;
-    w.v += adv ? 1u : 0u;
-    w.hi = adv ? w.lo : w.hi;
-    w.lo = adv ? w.q0 : w.lo;
-    w.q0 = adv ? nxt : w.q0;
-}
-
-// A code missing from the level-1 table is longer than 8 bits or not in the
-// codebook; the complete table tells which (length 0: not a code), and an
-// active lane that meets one marks its chunk bad.
-__device__ __forceinline__ void decode_two(Window3 &w, const Ring<kRingFast> &rg, const uint32_t *l1,
-                                           const uint16_t *ft, uint32_t shift, bool &bad, bool act1, bool act2,
-                                           uint32_t &s1, uint32_t &s2)
-{
-    const uint32_t nxt = rg.at(w.v + 3);
+    const uint32_t nxt = rg.at(w.v + 4);
     const uint32_t c0 = __funnelshift_l(w.lo, w.hi, w.bo);
     const uint32_t c1 = __funnelshift_l(w.q0, w.lo, w.bo);
     uint32_t e = l1[(c0 >> (32 - kL1Bits)) * 32];
@@ -355,47 +333,48 @@ __device__ __forceinline__ void decode_two(Window3 &w, const Ring<kRingFast> &rg
             l1n = f & 15u;
             s1 = f >> 4;
             l2n = 0;
-            bad |= act1 && l1n == 0;
         }
     }
-    // the second code, when it is not in the first entry: a second level-1
-    // lookup after the first code (some lane of the warp nearly always needs
-    // it, so it is predicated rather than voted on)
     const bool need2 = l2n == 0;
-    const uint32_t cur2 = __funnelshift_l(c1, c0, l1n);  // the bits after the first code (l1n < 16)
-    const uint32_t e2 = ld_shared_pred32(need2, l1 + (cur2 >> (32 - kL1Bits)) * 32, 0u);
-    uint32_t l2b = e2 & 15u, s2b = (e2 >> 8) & 0xFFFu;
-    const bool long2 = need2 && l2b == 0;
-    if (__any_sync(0xffffffffu, long2)) {
-        const uint32_t f = ld_ft_pred(long2, ft + (cur2 >> shift), 0u);
-        if (long2) {
-            l2b = f & 15u;
-            s2b = f >> 4;
-            bad |= act2 && l2b == 0;
+    if (__any_sync(0xffffffffu, need2)) {
+        const uint32_t cur2 = __funnelshift_l(c1, c0, l1n);  // the bits after the first code (l1n < 16)
+        const uint32_t e2 = ld_shared_pred32(need2, l1 + (cur2 >> (32 - kL1Bits)) * 32, 0u);
+        uint32_t l2b = e2 & 15u, s2b = (e2 >> 8) & 0xFFFu;
+        const bool long2 = need2 && l2b == 0;
+        if (__any_sync(0xffffffffu, long2)) {
+            const uint32_t f = ld_ft_pred(long2, ft + (cur2 >> shift), 0u);
+            if (long2) {
+                l2b = f & 15u;
+                s2b = f >> 4;
+            }
+        }
+        if (need2) {
+            l2n = l2b;
+            s2 = s2b;
         }
     }
-    l2n = need2 ? l2b : l2n;
-    s2 = need2 ? s2b : s2;
     l1n = act1 ? l1n : 0u;
     l2n = act2 ? l2n : 0u;
-    step3(w, nxt, l1n + l2n);
+    minlen = min(minlen, min(act1 ? l1n : 15u, act2 ? l2n : 15u));
+    step(w, nxt, l1n + l2n);
 }
 
 // single code (the odd last symbol of a chunk)
-__device__ __forceinline__ uint32_t decode_two_level(Window3 &w, const Ring<kRingFast> &rg, const uint32_t *l1,
-                                                     const uint16_t *ft, uint32_t shift, bool &bad, bool active)
+__device__ __forceinline__ uint32_t decode_two_level(Window &w, const Ring<kRingFast> &rg, const uint32_t *l1,
+                                                     const uint16_t *ft, uint32_t shift, uint32_t &minlen,
+                                                     bool active)
 {
     uint32_t s1, s2;
-    decode_two(w, rg, l1, ft, shift, bad, active, false, s1, s2);
+    decode_two(w, rg, l1, ft, shift, minlen, active, false, s1, s2);
     return s1;
 }
 
 // One chunk of cnt symbols; the warp runs kend >= cnt symbol steps (GUARD:
 // some lane's chunk is shorter than the warp's longest).
 template <bool MULTI_TILE, bool GUARD>
-__device__ __forceinline__ void decode_chunk(const DecodeArgs &a, Ring<kRingFast> &rg, Window3 &w, const uint32_t *l1,
+__device__ __forceinline__ void decode_chunk(const DecodeArgs &a, Ring<kRingFast> &rg, Window &w, const uint32_t *l1,
                                              const uint16_t *ft, uint32_t shift, uint64_t s0, uint32_t cnt,
-                                             uint32_t kend, unsigned long long &zeros, bool &bad)
+                                             uint32_t kend, unsigned long long &zeros, uint32_t &minlen)
 {
     const uint32_t R = a.radius;
     uint32_t ssum = 0, tz = 0, tstart = 0;
@@ -406,7 +385,7 @@ __device__ __forceinline__ void decode_chunk(const DecodeArgs &a, Ring<kRingFast
         uint32_t sy[kBatch];
 #pragma unroll
         for (int j = 0; j < (int)kBatch; j += 2)
-            decode_two(w, rg, l1, ft, shift, bad, !GUARD || k + j < cnt, !GUARD || k + j + 1 < cnt, sy[j],
+            decode_two(w, rg, l1, ft, shift, minlen, !GUARD || k + j < cnt, !GUARD || k + j + 1 < cnt, sy[j],
                        sy[j + 1]);
         if (!GUARD || k + kBatch <= cnt) {
             const uint4 o = make_uint4(sy[0] | (sy[1] << 16), sy[2] | (sy[3] << 16), sy[4] | (sy[5] << 16),
@@ -439,7 +418,7 @@ __device__ __forceinline__ void decode_chunk(const DecodeArgs &a, Ring<kRingFast
     if (full < kend) {
         rg.refill(w.v);
         for (uint32_t k = full; k < kend; k++) {
-            const uint32_t sym = decode_two_level(w, rg, l1, ft, shift, bad, !GUARD || k < cnt);
+            const uint32_t sym = decode_two_level(w, rg, l1, ft, shift, minlen, !GUARD || k < cnt);
             if (!GUARD || k < cnt) {
                 ssum += sym;
                 tz += sym == 0;
@@ -503,16 +482,16 @@ __global__ void __launch_bounds__(kDecFastThreads, 2) k_decode_fast(DecodeArgs a
         const uint32_t cnt = live ? (uint32_t)(a.n - s0 < a.chunk ? a.n - s0 : a.chunk) : 0u;
         Ring<kRingFast> rg;
         rg.start(warp_ring, lane, stream + coff, coff < a.words ? a.words - coff : 0);
-        Window3 w{0, 0, rg.at(0), rg.at(1), rg.at(2)};
-        bool cbad = false;
+        Window w{0, 0, rg.at(0), rg.at(1), rg.at(2), rg.at(3)};
+        uint32_t minlen = 15;
         if (__all_sync(0xffffffffu, cnt == a.chunk)) {
-            decode_chunk<MULTI_TILE, false>(a, rg, w, l1, ft, shift, s0, cnt, cnt, zeros, cbad);
+            decode_chunk<MULTI_TILE, false>(a, rg, w, l1, ft, shift, s0, cnt, cnt, zeros, minlen);
         } else {
             const uint32_t cmax = __reduce_max_sync(0xffffffffu, cnt);
-            decode_chunk<MULTI_TILE, true>(a, rg, w, l1, ft, shift, s0, cnt, cmax, zeros, cbad);
+            decode_chunk<MULTI_TILE, true>(a, rg, w, l1, ft, shift, s0, cnt, cmax, zeros, minlen);
         }
         cp_async_wait<0>();  // the ring is reused by the next chunk
-        if (live) bad |= cbad || (uint64_t)w.v * 32 + w.bo != nbits;
+        if (live) bad |= minlen == 0 || (uint64_t)w.v * 32 + w.bo != nbits;
         __syncwarp();
     }
     if (bad) atomicOr(&a.ctl->error, DERR_CORRUPT);
