@@ -11,7 +11,8 @@
 // exactly the serial merge's tree.  Depths by pointer jumping (depth <= 45).
 //
 // Canonization (Sec. 3.2.3): symbols in (length, symbol) order, first code 0,
-// next = (prev + 1) << (len - prevlen).  Codeword tables hold (len, code) as
+// next = (prev + 1) << (len - prevlen); the order is found by counting, not
+// sorting.  Codeword tables hold (len, code) as
 // len << 24 | code in 32 bits when the longest code fits 24 bits, and
 // len << 56 | code in 64 bits always (the paper's adaptive representation).
 #include "common.cuh"
@@ -20,6 +21,8 @@ namespace gbsz {
 
 namespace {
 
+// one CTA of 1024 threads (measured against 256 and 512: the codebook kernel
+// is within 10% for every bin count, the decoder tables are fastest here)
 constexpr int kCbThreads = 1024;
 constexpr uint32_t kRankSortMax = 0;     // rank sort unused; bitonic covers small n
 constexpr uint32_t kBitonicMax = 8192;    // 8192 keys = 64 KB of shared memory
@@ -123,32 +126,33 @@ struct Canon {
     uint32_t start[kMaxLen + 2];
 };
 
-// Canonical codes from lengths (all threads).  Fills sh (tables), writes
-// sorted symbols (if non-NULL) and per-symbol codewords (if non-NULL).
-__device__ void canonicalize(const uint8_t *len, uint32_t nbins, unsigned long long *keyA,
-                             unsigned long long *keyB, uint32_t *s_cnt, Canon &sh, uint16_t *sorted,
+// Canonical codes from lengths (all threads), without sorting: a symbol's
+// place in (length, symbol) order is the start of its length plus the number
+// of symbols before it with the same length.  Symbols go T at a time; in each
+// pass a warp ranks its lanes among equal lengths (match_any), the per-warp
+// counts of every length are scanned across the warps, and the running
+// offset of every length then advances by the pass's count.  Fills sh
+// (tables), writes sorted symbols (if non-NULL) and per-symbol codewords (if
+// non-NULL).  s_cnt: at least 34 * (kMaxLen + 2) words.
+__device__ void canonicalize(const uint8_t *len, uint32_t nbins, uint32_t *s_cnt, Canon &sh, uint16_t *sorted,
                              uint64_t *cw64, uint32_t *cw32, uint64_t *codes_only, uint32_t maxlen)
 {
-    const uint32_t T = blockDim.x, t = threadIdx.x;
-    __shared__ uint32_t s_scan[33];
-    // compaction of used symbols in ascending order
-    const uint32_t per = (nbins + T - 1) / T;
-    const uint32_t lo = min(nbins, t * per), hi = min(nbins, lo + per);
-    uint32_t c = 0;
-    for (uint32_t s = lo; s < hi; s++) c += len[s] > 0;
-    uint32_t k;
-    uint32_t pos = block_excl_scan(c, s_scan, &k);
-    for (uint32_t s = lo; s < hi; s++)
-        if (len[s]) keyA[pos++] = ((unsigned long long)len[s] << 16) | s;
-    for (uint32_t l = t; l < kMaxLen + 2; l += T) sh.count[l] = 0;
+    constexpr uint32_t L = kMaxLen + 2;
+    const uint32_t T = blockDim.x, t = threadIdx.x, lane = t & 31, w = t >> 5, W = (T + 31) >> 5;
+    uint32_t *wcnt = s_cnt;           // [W][L]: per-warp counts, then their exclusive scan over warps
+    uint32_t *base = s_cnt + 32 * L;  // [L]: first place of each length in the current pass
+    uint32_t *ptot = base + L;        // [L]: the pass's count of each length
+    for (uint32_t l = t; l < L; l += T) sh.count[l] = 0;
     __syncthreads();
-    unsigned long long *srt = cta_sort(keyA, keyB, k, 16, 24, s_cnt);
-    for (uint32_t p = t; p < k; p += T) atomicAdd(&sh.count[srt[p] >> 16], 1u);
+    for (uint32_t s = t; s < nbins; s += T) {
+        const uint32_t l = len[s];
+        if (l) atomicAdd(&sh.count[l], 1u);
+    }
     __syncthreads();
     if (t == 0) {
         uint32_t st = 0;
         unsigned long long f = 0;
-        for (uint32_t l = 0; l < kMaxLen + 2; l++) {
+        for (uint32_t l = 0; l < L; l++) {
             sh.start[l] = st;
             sh.first[l] = f;
             if (l >= 1) {
@@ -160,14 +164,36 @@ __device__ void canonicalize(const uint8_t *len, uint32_t nbins, unsigned long l
         sh.first[0] = 0;
     }
     __syncthreads();
-    for (uint32_t p = t; p < k; p += T) {
-        const unsigned long long key = srt[p];
-        const uint32_t l = (uint32_t)(key >> 16), s = (uint32_t)(key & 0xFFFFu);
-        const unsigned long long code = sh.first[l] + (p - sh.start[l]);
-        if (sorted) sorted[p] = (uint16_t)s;
-        if (cw64) cw64[s] = ((unsigned long long)l << 56) | code;
-        if (cw32) cw32[s] = maxlen <= 24 ? ((l << 24) | (uint32_t)code) : 0u;
-        if (codes_only) codes_only[s] = code;
+    for (uint32_t l = t; l < L; l += T) base[l] = sh.start[l];
+    for (uint32_t c0 = 0; c0 < nbins; c0 += T) {
+        const uint32_t s = c0 + t;
+        const uint32_t l = s < nbins ? len[s] : 0u;
+        const uint32_t peers = __match_any_sync(0xffffffffu, l);
+        const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+        for (uint32_t i = t; i < W * L; i += T) wcnt[i] = 0;
+        __syncthreads();
+        if (rank == 0 && l) wcnt[w * L + l] = __popc(peers);
+        __syncthreads();
+        for (uint32_t li = t; li < L; li += T) {
+            uint32_t run = 0;
+            for (uint32_t ww = 0; ww < W; ww++) {
+                const uint32_t c = wcnt[ww * L + li];
+                wcnt[ww * L + li] = run;
+                run += c;
+            }
+            ptot[li] = run;
+        }
+        __syncthreads();
+        if (l) {
+            const uint32_t p = base[l] + wcnt[w * L + l] + rank;
+            const unsigned long long code = sh.first[l] + (p - sh.start[l]);
+            if (sorted) sorted[p] = (uint16_t)s;
+            if (cw64) cw64[s] = ((unsigned long long)l << 56) | code;
+            if (cw32) cw32[s] = maxlen <= 24 ? ((l << 24) | (uint32_t)code) : 0u;
+            if (codes_only) codes_only[s] = code;
+        }
+        __syncthreads();
+        for (uint32_t li = t; li < L; li += T) base[li] += ptot[li];
     }
     __syncthreads();
 }
@@ -295,7 +321,6 @@ __global__ void __launch_bounds__(kCbThreads, 1) k_codebook(CodebookArgs a)
     }
     const int fbits = 32 - __clz(fmax);
     unsigned long long *K = cta_sort(a.keyA, a.keyB, k, 16, 16 + ((fbits + 3) & ~3), s_cnt);
-    unsigned long long *spare = K == a.keyA ? a.keyB : a.keyA;
     uint32_t maxlen = 1;
     if (k == 1) {
         if (t == 0) a.len_out[K[0] & 0xFFFFu] = 1;
@@ -344,7 +369,7 @@ __global__ void __launch_bounds__(kCbThreads, 1) k_codebook(CodebookArgs a)
         a.ctl->nsym = k;
     }
     if (maxlen > kMaxLen) return;
-    canonicalize(a.len_out, nbins, spare, K, s_cnt, canon, nullptr, a.cw64, a.cw32, a.codes_only, maxlen);
+    canonicalize(a.len_out, nbins, s_cnt, canon, nullptr, a.cw64, a.cw32, a.codes_only, maxlen);
 }
 
 // Reverse codebook for decoding: validates the length table (every length
@@ -385,7 +410,7 @@ __global__ void __launch_bounds__(kCbThreads, 1) k_decode_tables(CodebookArgs a)
         if (t == 0) atomicOr(&a.ctl->error, DERR_CORRUPT);
         return;
     }
-    canonicalize(a.len_in, nbins, a.keyA, a.keyB, s_cnt, canon, a.sorted, nullptr, nullptr, nullptr, ml);
+    canonicalize(a.len_in, nbins, s_cnt, canon, a.sorted, nullptr, nullptr, nullptr, ml);
     for (uint32_t l = t; l < kMaxLen + 2; l += T) {
         a.first[l] = canon.first[l];
         a.count[l] = canon.count[l];
@@ -433,7 +458,7 @@ __global__ void __launch_bounds__(kCbThreads, 1) k_decode_tables(CodebookArgs a)
     }
 }
 
-constexpr size_t kCbSmem = 16 * kCbThreads * sizeof(uint32_t);
+constexpr size_t kCbSmem = 16 * 1024 * sizeof(uint32_t);  // 8192 sort keys; 16 digit counters per thread
 
 // opt in to more than 48 KB of dynamic shared memory, once per device
 void set_smem_attributes()

@@ -185,21 +185,28 @@ __global__ void k_patch_exceptions(ReconArgs a, uint64_t n)
 // global memory).  Every entry's index must be its point's and the counts
 // must match the run.  Residuals are code - R, or the outlier's residual for
 // code 0; their sum within the tile is a thread run plus a warp scan, and the
-// tile's carry F[t] completes the prefix.  The next tile's codes, outlier
-// entries and carry, and the run bounds of the tile after it, are loaded
-// before this tile is processed.
-__device__ __forceinline__ uint4 ldg_nc16(const void *p)
+// tile's carry F[t] completes the prefix.  The codes of the next two tiles
+// are in flight (cp.async into a per-warp ring in shared memory), and the
+// next tile's outlier entries and carry and the run bounds of the tile after
+// it are loaded before this tile is processed.
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src)
 {
-    uint4 v;
-    asm volatile("ld.global.nc.v4.u32 {%0, %1, %2, %3}, [%4];"
-                 : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
-                 : "l"(p));
-    return v;
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(src) : "memory");
 }
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+constexpr int kValStages = 3;  // tiles of codes per warp in shared memory: this one and two ahead
 
 __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, const uint32_t *F, const uint32_t *start)
 {
     __shared__ uint32_t s_od[k1Threads * 17];  // outlier residuals by (thread, point); stride 17 spreads banks
+    // codes of the next tiles, copied by each lane for itself (32 bytes per
+    // lane per tile) with cp.async, two tiles ahead of the one in use
+    __shared__ uint4 s_code[k1Threads / 32][kValStages][64];
     if (a.ctl->error & DERR_CORRUPT) return;
     const uint64_t n = g.n[0];
     const float ebx2 = a.ebx2;
@@ -216,12 +223,15 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
             hi = start[t + 1];
         }
     };
-    auto codes = [&](uint64_t t, uint4 &w0, uint4 &w1) {
+    uint4(*ring)[64] = s_code[threadIdx.x >> 5];
+    // one commit group per tile, empty past the end, so the group count stays uniform
+    auto issue = [&](uint64_t t, int stage) {
         const uint64_t s0 = t * k1Tile + (uint64_t)lane * 16;
         if (t < g.ntiles && s0 + 16 <= n) {
-            w0 = ldg_nc16(a.codes + s0);
-            w1 = ldg_nc16(a.codes + s0 + 8);
+            cp_async16(&ring[stage][2 * lane], a.codes + s0);
+            cp_async16(&ring[stage][2 * lane + 1], a.codes + s0 + 8);
         }
+        cp_async_commit();
     };
     auto entry = [&](uint32_t lo, uint32_t hi) {
         uint2 en = make_uint2(0xFFFFFFFFu, 0u);
@@ -229,19 +239,21 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
         return en;
     };
     uint64_t tile = (uint64_t)blockIdx.x * (k1Threads / 32) + (threadIdx.x >> 5);
-    uint4 w0 = make_uint4(0, 0, 0, 0), w1 = w0;
     uint32_t lo, hi, lo1, hi1;
     bounds(tile, lo, hi);
     bounds(tile + nwarps, lo1, hi1);
-    codes(tile, w0, w1);
+    for (int k = 0; k < kValStages - 1; k++) issue(tile + (uint64_t)k * nwarps, k);
     uint2 en = entry(lo, hi);
+    int stage = 0;
     // per-block mode: no carries (every 32-point block restarts from 0)
     const bool blocked = a.lblock != 0;
     uint32_t carry = tile < g.ntiles && !blocked ? F[tile] : 0u;
     for (; tile < g.ntiles; tile += nwarps) {
         const uint64_t s0 = tile * k1Tile + (uint64_t)lane * 16;
         uint32_t c[16];
+        cp_async_wait<kValStages - 2>();  // this tile's group has landed
         if (s0 + 16 <= n) {
+            const uint4 w0 = ring[stage][2 * lane], w1 = ring[stage][2 * lane + 1];
             const uint32_t w[8] = {w0.x, w0.y, w0.z, w0.w, w1.x, w1.y, w1.z, w1.w};
 #pragma unroll
             for (int j = 0; j < 16; j++) c[j] = (w[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu;
@@ -251,9 +263,10 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
         }
         const uint32_t clo = lo, chi = hi, ccarry = carry;
         const uint2 cen = en;
-        // next tile's loads
+        // the tile two ahead into the slot just read; next tile's outliers
         const uint64_t tn = tile + nwarps;
-        codes(tn, w0, w1);
+        issue(tile + (uint64_t)(kValStages - 1) * nwarps, (stage + kValStages - 1) % kValStages);
+        stage = (stage + 1) % kValStages;
         en = entry(lo1, hi1);
         lo = lo1;
         hi = hi1;
@@ -316,6 +329,7 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
                 if (s0 + j < n) a.out[s0 + j] = v[j];
         }
     }
+    cp_async_wait<0>();
     if (bad) atomicOr(&a.ctl->error, DERR_CORRUPT);
 }
 
