@@ -53,6 +53,9 @@ struct Table {
         }
     }
     __device__ __forceinline__ uint32_t raw32(uint32_t sym) const { return static_cast<const uint32_t *>(tab)[sym]; }
+    // PAIR layout in shared memory: {code, length} in two words, so a pair
+    // of codewords is joined without masking or shifting the length out
+    __device__ __forceinline__ uint2 split(uint32_t sym) const { return static_cast<const uint2 *>(tab)[sym]; }
     __device__ __forceinline__ uint32_t len_of(uint32_t sym) const
     {
         if (CW32) return static_cast<const uint32_t *>(tab)[sym] >> 24;
@@ -432,10 +435,9 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
                     if (CW32 && PAIR) {
 #pragma unroll
                         for (int k = 0; k < 4; k++) {
-                            const uint32_t e0 = tab.raw32(v[k] & 0xFFFFu), e1 = tab.raw32(v[k] >> 16);
-                            const uint32_t l1 = e1 >> 24;
-                            const uint32_t len = (e0 >> 24) + l1;
-                            acc = (acc << len) | (((e0 & 0xFFFFFFu) << l1) | (e1 & 0xFFFFFFu));
+                            const uint2 e0 = tab.split(v[k] & 0xFFFFu), e1 = tab.split(v[k] >> 16);
+                            const uint32_t len = e0.y + e1.y;
+                            acc = (acc << len) | ((e0.x << e1.y) | e1.x);
                             nacc += len;
                             const bool full_w = nacc >= 32;
                             nacc -= full_w ? 32u : 0u;
@@ -474,7 +476,13 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
                     const uint32_t c = ln.g[j];
                     uint32_t len;
                     unsigned long long code;
-                    tab.get(c, len, code);
+                    if (PAIR) {  // the {code, length} layout
+                        const uint2 e = tab.split(c);
+                        len = e.y;
+                        code = e.x;
+                    } else {
+                        tab.get(c, len, code);
+                    }
                     uint32_t w[2], nw;
                     append<CW32>(acc, nacc, code, len, w, nw);
                     for (uint32_t q = 0; q < nw; q++) {
@@ -573,10 +581,16 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
 // The codeword width is chosen on the device from the longest code length
 // the codebook kernel found: 32-bit entries when it is at most 24 bits.
 __device__ __forceinline__ const void *load_table(const EncodeArgs &a, uint32_t use_smem, unsigned long long *s_tab,
-                                                  bool w32)
+                                                  bool w32, bool pair = false)
 {
     if (!use_smem) return w32 ? (const void *)a.cw32 : (const void *)a.cw64;
-    if (w32) {
+    if (pair) {
+        uint2 *st = reinterpret_cast<uint2 *>(s_tab);
+        for (uint32_t i = threadIdx.x; i < a.nbins; i += blockDim.x) {
+            const uint32_t e = a.cw32[i];
+            st[i] = make_uint2(e & 0xFFFFFFu, e >> 24);
+        }
+    } else if (w32) {
         uint32_t *st = reinterpret_cast<uint32_t *>(s_tab);
         for (uint32_t i = threadIdx.x; i < a.nbins; i += blockDim.x) st[i] = a.cw32[i];
     } else {
@@ -625,7 +639,7 @@ __global__ void __launch_bounds__(kEncThreads, 3) k_encode_pack(EncodeArgs a, ui
     // with shared loads
     const bool pair = w32 && a.ctl->maxlen <= 16;
     if (use_smem) {
-        load_table(a, 1, s_tab, w32);
+        load_table(a, 1, s_tab, w32, pair);
         if (pair) pack_units<true, true>(a, nunits, Table<true>{s_tab}, slot);
         else if (w32) pack_units<true, false>(a, nunits, Table<true>{s_tab}, slot);
         else pack_units<false, false>(a, nunits, Table<false>{s_tab}, slot);
