@@ -294,52 +294,53 @@ __device__ __forceinline__ uint32_t ld_ft_pred(bool p, const uint16_t *addr, uin
 }
 
 // Two codes per step.  The level-1 entry of the window's top byte holds the
-// first code and, when it fits in the same byte, the second:
-// len1 | len2 << 4 | sym1 << 8 | sym2 << 20 (len1 = 0: the first code is
-// longer than 8 bits; len2 = 0: the second is not in the byte).  Missing
+// first code and, when it fits in the same byte, the second, as 8 bytes:
+// x = sym1 | sym2 << 16 (the two symbols as they are stored), y = len1 |
+// len2 << 8 (len1 = 0: the first code is longer than 8 bits; len2 = 0: the
+// second is not in the byte).  Missing
 // codes come from a second level-1 lookup after the first code and, for codes
 // longer than 8 bits, from the complete table in global memory; each of these
 // runs only when some lane of the warp needs it.  act1 / act2 = false (lanes past the end
 // of a short chunk, kept in step for the warp votes): that code consumes no
 // bits and its length is not checked.
-__device__ __forceinline__ uint32_t ld_shared_pred32(bool p, const void *addr, uint32_t keep)
+__device__ __forceinline__ uint2 ld_shared_pred64(bool p, const void *addr)
 {
-    uint32_t v = keep;
+    uint2 v = make_uint2(0u, 0u);
     const uint32_t a = (uint32_t)__cvta_generic_to_shared(addr);
     asm volatile(
         "{\n\t.reg .pred q;\n\t"
-        "setp.ne.u32 q, %1, 0;\n\t"
-        "@q ld.shared.u32 %0, [%2];\n\t}"
-        : "+r"(v)
+        "setp.ne.u32 q, %2, 0;\n\t"
+        "@q ld.shared.v2.u32 {%0, %1}, [%3];\n\t}"
+        : "+r"(v.x), "+r"(v.y)
         : "r"((uint32_t)p), "r"(a));
     return v;
 }
 
-__device__ __forceinline__ void decode_two(Window &w, const Ring<kRingFast> &rg, const uint32_t *l1,
-                                           const uint16_t *ft, uint32_t shift, uint32_t &minlen, bool act1,
-                                           bool act2, uint32_t &s1, uint32_t &s2)
+// Returns the two symbols packed as stored (sym1 | sym2 << 16).
+__device__ __forceinline__ uint32_t decode_two(Window &w, const Ring<kRingFast> &rg, const uint2 *l1,
+                                               const uint16_t *ft, uint32_t shift, uint32_t &minlen, bool act1,
+                                               bool act2)
 {
     const uint32_t nxt = rg.at(w.v + 4);
     const uint32_t c0 = __funnelshift_l(w.lo, w.hi, w.bo);
     const uint32_t c1 = __funnelshift_l(w.q0, w.lo, w.bo);
-    uint32_t e = l1[(c0 >> (32 - kL1Bits)) * 32];
-    uint32_t l1n = e & 15u, l2n = (e >> 4) & 15u;
-    s1 = (e >> 8) & 0xFFFu;
-    s2 = e >> 20;
+    const uint2 e = l1[(c0 >> (32 - kL1Bits)) * 32];
+    uint32_t sw = e.x;
+    uint32_t l1n = e.y & 0xFFu, l2n = e.y >> 8;
     const bool long1 = l1n == 0;
     if (__any_sync(0xffffffffu, long1)) {
         const uint32_t f = ld_ft_pred(long1, ft + (c0 >> shift), 0u);
         if (long1) {
             l1n = f & 15u;
-            s1 = f >> 4;
+            sw = f >> 4;
             l2n = 0;
         }
     }
     const bool need2 = l2n == 0;
     if (__any_sync(0xffffffffu, need2)) {
         const uint32_t cur2 = __funnelshift_l(c1, c0, l1n);  // the bits after the first code (l1n < 16)
-        const uint32_t e2 = ld_shared_pred32(need2, l1 + (cur2 >> (32 - kL1Bits)) * 32, 0u);
-        uint32_t l2b = e2 & 15u, s2b = (e2 >> 8) & 0xFFFu;
+        const uint2 e2 = ld_shared_pred64(need2, l1 + (cur2 >> (32 - kL1Bits)) * 32);
+        uint32_t l2b = e2.y & 0xFFu, s2b = e2.x & 0xFFFFu;
         const bool long2 = need2 && l2b == 0;
         if (__any_sync(0xffffffffu, long2)) {
             const uint32_t f = ld_ft_pred(long2, ft + (cur2 >> shift), 0u);
@@ -350,29 +351,28 @@ __device__ __forceinline__ void decode_two(Window &w, const Ring<kRingFast> &rg,
         }
         if (need2) {
             l2n = l2b;
-            s2 = s2b;
+            sw = (sw & 0xFFFFu) | (s2b << 16);
         }
     }
     l1n = act1 ? l1n : 0u;
     l2n = act2 ? l2n : 0u;
     minlen = min(minlen, min(act1 ? l1n : 15u, act2 ? l2n : 15u));
     step(w, nxt, l1n + l2n);
+    return sw;
 }
 
 // single code (the odd last symbol of a chunk)
-__device__ __forceinline__ uint32_t decode_two_level(Window &w, const Ring<kRingFast> &rg, const uint32_t *l1,
+__device__ __forceinline__ uint32_t decode_two_level(Window &w, const Ring<kRingFast> &rg, const uint2 *l1,
                                                      const uint16_t *ft, uint32_t shift, uint32_t &minlen,
                                                      bool active)
 {
-    uint32_t s1, s2;
-    decode_two(w, rg, l1, ft, shift, minlen, active, false, s1, s2);
-    return s1;
+    return decode_two(w, rg, l1, ft, shift, minlen, active, false) & 0xFFFFu;
 }
 
 // One chunk of cnt symbols; the warp runs kend >= cnt symbol steps (GUARD:
 // some lane's chunk is shorter than the warp's longest).
 template <bool MULTI_TILE, bool GUARD>
-__device__ __forceinline__ void decode_chunk(const DecodeArgs &a, Ring<kRingFast> &rg, Window &w, const uint32_t *l1,
+__device__ __forceinline__ void decode_chunk(const DecodeArgs &a, Ring<kRingFast> &rg, Window &w, const uint2 *l1,
                                              const uint16_t *ft, uint32_t shift, uint64_t s0, uint32_t cnt,
                                              uint32_t kend, unsigned long long &zeros, uint32_t &minlen)
 {
@@ -382,14 +382,12 @@ __device__ __forceinline__ void decode_chunk(const DecodeArgs &a, Ring<kRingFast
     const uint32_t full = kend & ~(kBatch - 1);
     for (uint32_t k = 0; k < full; k += kBatch) {
         rg.refill(w.v);
-        uint32_t sy[kBatch];
+        uint32_t pw[kBatch / 2];  // symbol pairs as stored
 #pragma unroll
         for (int j = 0; j < (int)kBatch; j += 2)
-            decode_two(w, rg, l1, ft, shift, minlen, !GUARD || k + j < cnt, !GUARD || k + j + 1 < cnt, sy[j],
-                       sy[j + 1]);
+            pw[j / 2] = decode_two(w, rg, l1, ft, shift, minlen, !GUARD || k + j < cnt, !GUARD || k + j + 1 < cnt);
         if (!GUARD || k + kBatch <= cnt) {
-            const uint4 o = make_uint4(sy[0] | (sy[1] << 16), sy[2] | (sy[3] << 16), sy[4] | (sy[5] << 16),
-                                       sy[6] | (sy[7] << 16));
+            const uint4 o = make_uint4(pw[0], pw[1], pw[2], pw[3]);
             // symbols are below 4096 here, so the halves of the word sum cannot carry
             const uint32_t t4 = o.x + o.y + o.z + o.w;
             ssum += (t4 & 0xFFFFu) + (t4 >> 16);
@@ -399,9 +397,10 @@ __device__ __forceinline__ void decode_chunk(const DecodeArgs &a, Ring<kRingFast
 #pragma unroll
             for (int j = 0; j < (int)kBatch; j++) {
                 if (k + j < cnt) {
-                    ssum += sy[j];
-                    tz += sy[j] == 0;
-                    out[k + j] = (uint16_t)sy[j];
+                    const uint32_t sy = (pw[j / 2] >> ((j & 1) * 16)) & 0xFFFFu;
+                    ssum += sy;
+                    tz += sy == 0;
+                    out[k + j] = (uint16_t)sy;
                 }
             }
         }
@@ -437,7 +436,7 @@ template <bool MULTI_TILE>
 __global__ void __launch_bounds__(kDecFastThreads, 2) k_decode_fast(DecodeArgs a)
 {
     extern __shared__ uint32_t s_dyn[];  // rings, level-1 table (lane-replicated)
-    uint32_t *l1tab = s_dyn + kDecFastThreads * kRingFast;
+    uint2 *l1tab = reinterpret_cast<uint2 *>(s_dyn + kDecFastThreads * kRingFast);
     const uint32_t B = a.fast_bits, shift = 32 - B;
     const uint16_t *gft = static_cast<const uint16_t *>(a.lutf);
     const uint16_t *ft = gft;
@@ -450,13 +449,13 @@ __global__ void __launch_bounds__(kDecFastThreads, 2) k_decode_fast(DecodeArgs a
         const uint32_t i = k >> 5;
         const uint32_t f = ft_at(i);
         const uint32_t la = f & 15u;
-        uint32_t e = 0;
+        uint2 e = make_uint2(0u, 0u);
         if (la >= 1 && la <= kL1Bits) {
-            e = la | ((f >> 4) << 8);
+            e = make_uint2(f >> 4, la);
             if (la < kL1Bits) {
                 const uint32_t g2 = ft_at((i << la) & 0xFFu);
                 const uint32_t lb = g2 & 15u;
-                if (lb >= 1 && lb <= kL1Bits - la) e |= (lb << 4) | ((g2 >> 4) << 20);
+                if (lb >= 1 && lb <= kL1Bits - la) e = make_uint2((f >> 4) | ((g2 >> 4) << 16), la | (lb << 8));
             }
         }
         l1tab[k] = e;
@@ -467,7 +466,7 @@ __global__ void __launch_bounds__(kDecFastThreads, 2) k_decode_fast(DecodeArgs a
     const uint32_t *bits_tab = reinterpret_cast<const uint32_t *>(a.archive + a.off_bits);
     uint32_t *warp_ring = s_dyn + (threadIdx.x >> 5) * kRingFast * 32;
     const uint32_t lane = threadIdx.x & 31;
-    const uint32_t *l1 = l1tab + lane;
+    const uint2 *l1 = l1tab + lane;
     unsigned long long zeros = 0;
     bool bad = false;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -521,14 +520,14 @@ int launch_decode(const DecodeArgs &a, cudaStream_t st, int phase)
         const int most = (int)(kDecThreads * kRing * 4 + kSortedSmemMax * sizeof(uint16_t));
         cudaFuncSetAttribute(k_decode<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         cudaFuncSetAttribute(k_decode<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-        const int most_fast = (int)(kDecFastThreads * kRingFast * 4 + (4u << (5 + kL1Bits)));
+        const int most_fast = (int)(kDecFastThreads * kRingFast * 4 + (8u << (5 + kL1Bits)));
         cudaFuncSetAttribute(k_decode_fast<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
         cudaFuncSetAttribute(k_decode_fast<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
         attr_done |= bit;
     }
     const bool multi = a.chunk > kRecon1DTile;
     if (a.fast_bits) {
-        const size_t dyn_fast = (size_t)kDecFastThreads * kRingFast * 4 + (4u << (5 + kL1Bits));
+        const size_t dyn_fast = (size_t)kDecFastThreads * kRingFast * 4 + (8u << (5 + kL1Bits));
         const uint64_t want = (a.nchunk + kDecFastThreads - 1) / kDecFastThreads;
         const int per_sm = 2;
         const unsigned g = (unsigned)std::min<uint64_t>(want, (uint64_t)(a.num_sms ? a.num_sms : 1) * per_sm);
