@@ -445,8 +445,9 @@ __global__ void __launch_bounds__(kDecFastThreads, 2) k_decode_fast(DecodeArgs a
     auto ft_at = [&](uint32_t byte) -> uint32_t {  // complete-table entry of an 8-bit prefix
         return B >= kL1Bits ? gft[byte << (B - kL1Bits)] : gft[byte >> (kL1Bits - B)];
     };
-    for (uint32_t k = threadIdx.x; k < (32u << kL1Bits); k += blockDim.x) {
-        const uint32_t i = k >> 5;
+    // the 256 entries once (in the ring area, not in use yet), then one copy per lane
+    uint2 *l1once = reinterpret_cast<uint2 *>(s_dyn);
+    for (uint32_t i = threadIdx.x; i < (1u << kL1Bits); i += blockDim.x) {
         const uint32_t f = ft_at(i);
         const uint32_t la = f & 15u;
         uint2 e = make_uint2(0u, 0u);
@@ -458,8 +459,10 @@ __global__ void __launch_bounds__(kDecFastThreads, 2) k_decode_fast(DecodeArgs a
                 if (lb >= 1 && lb <= kL1Bits - la) e = make_uint2((f >> 4) | ((g2 >> 4) << 16), la | (lb << 8));
             }
         }
-        l1tab[k] = e;
+        l1once[i] = e;
     }
+    __syncthreads();
+    for (uint32_t k = threadIdx.x; k < (32u << kL1Bits); k += blockDim.x) l1tab[k] = l1once[k >> 5];
     __syncthreads();
     if (a.ctl->error & DERR_CORRUPT) return;
     const uint32_t *stream = reinterpret_cast<const uint32_t *>(a.archive + a.off_stream);
