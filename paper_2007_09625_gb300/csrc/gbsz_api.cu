@@ -141,6 +141,9 @@ struct Slot {
     Buf lut, lutf, first, count, start, sorted;
     cudaStream_t stream = nullptr;  // used by batch calls
     cudaEvent_t done = nullptr;
+    // the decoder tables are built on a second stream while the chunk offsets are scanned
+    cudaStream_t aux = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
 
     bool init()
     {
@@ -151,7 +154,10 @@ struct Slot {
             return false;
         }
         if (cudaStreamCreateWithFlags(&stream, cudaStreamNonBlocking) != cudaSuccess ||
-            cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess) {
+            cudaEventCreateWithFlags(&done, cudaEventDisableTiming) != cudaSuccess ||
+            cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&join, cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
             return false;
         }
@@ -174,6 +180,11 @@ struct Slot {
         stream = nullptr;
         if (done) cudaEventDestroy(done);
         done = nullptr;
+        if (aux) cudaStreamDestroy(aux);
+        aux = nullptr;
+        if (fork) cudaEventDestroy(fork);
+        if (join) cudaEventDestroy(join);
+        fork = join = nullptr;
     }
 };
 
@@ -537,10 +548,15 @@ gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void
     cb.expect_maxlen = h.maxlen;
     cb.fast_bits = fast_lut_bits(h.maxlen, cb.nbins);
     cb.fast_pair = 0;  // the decoder builds its own first level from the complete table
+    // decoder tables (one CTA) on the slot's second stream, beside the
+    // chunk-offset scan below; joined before the symbols are decoded
     cudaEvent_t e0;
-    stage_begin(c, st, &e0);
-    launch_decode_tables(cb, st);
-    stage_end(c, st, 6, e0);
+    cudaEventRecord(s->fork, st);
+    cudaStreamWaitEvent(s->aux, s->fork, 0);
+    stage_begin(c, s->aux, &e0);
+    launch_decode_tables(cb, s->aux);
+    stage_end(c, s->aux, 6, e0);
+    cudaEventRecord(s->join, s->aux);
 
     DecodeArgs d{};
     d.archive = arc;
@@ -568,6 +584,7 @@ gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void
     d.ctl = s->ctl;
     int ndec = 0;
     for (int ph = 0; ph < 2; ph++) {
+        if (ph == 1) cudaStreamWaitEvent(st, s->join, 0);
         stage_begin(c, st, &e0);
         ndec += launch_decode(d, st, ph);
         stage_end(c, st, 7 + ph, e0);
