@@ -382,13 +382,33 @@ template <int TX, int TY, int TZ, int NT>
 __device__ void tile_prefix(const ReconArgs &a, const Geo &g, uint64_t tile, uint32_t *sm)
 {
     constexpr int NE = TX * TY * TZ;
+    constexpr int PER = NE / NT;
+    static_assert(NE % NT == 0, "whole points per thread");
     const uint64_t tx = tile % g.nt[0], ty = (tile / g.nt[0]) % g.nt[1], tz = tile / ((uint64_t)g.nt[0] * g.nt[1]);
     const uint64_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
-    for (int l = threadIdx.x; l < NE; l += NT) {
+    auto gidx = [&](int l, bool &in) -> uint64_t {
         const int x = l % TX, y = (l / TX) % TY, z = l / (TX * TY);
         const uint64_t gx = x0 + x, gy = y0 + y, gz = z0 + z;
-        uint32_t v = 0;
-        if (gx < g.n[0] && gy < g.n[1] && gz < g.n[2]) v = delta_of(a, (gz * g.n[1] + gy) * g.n[0] + gx);
+        in = gx < g.n[0] && gy < g.n[1] && gz < g.n[2];
+        return (gz * g.n[1] + gy) * g.n[0] + gx;
+    };
+    // all of the thread's codes are loaded before any is used, so the loads
+    // overlap; the few outliers' residuals follow
+    uint32_t code[PER];
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+        bool in;
+        const uint64_t i = gidx((int)threadIdx.x + j * NT, in);
+        code[j] = in ? (uint32_t)a.codes[i] : a.radius;  // outside the field: residual 0
+    }
+#pragma unroll
+    for (int j = 0; j < PER; j++) {
+        const int l = (int)threadIdx.x + j * NT;
+        uint32_t v = code[j] - a.radius;
+        if (code[j] == 0) {
+            bool in;
+            v = (uint32_t)a.dscr[gidx(l, in)];
+        }
         sm[l] = v;
     }
     __syncthreads();
@@ -473,10 +493,15 @@ __global__ void __launch_bounds__(NT) k_values(ReconArgs a, Geo g, const uint32_
     const float ebx2 = a.ebx2;
     for (uint64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
         const uint64_t tc[3] = {tile % g.nt[0], (tile / g.nt[0]) % g.nt[1], tile / ((uint64_t)g.nt[0] * g.nt[1])};
-        // stage the carries of every subset
+        // stage the carries of every subset: each subset's array has at most
+        // NT entries, so a thread loads one entry of each, all loads at once
         int cbase[8];
+        uint32_t cv[8];
         int cb = 0;
-        for (int A = 1; A <= nA; A++) {
+#pragma unroll
+        for (int A = 1; A <= 7; A++) {
+            cv[A] = 0;
+            if (A > nA) continue;
             const int sz = (int)g.size[A];
             cbase[A] = cb;
             bool has = true;
@@ -489,10 +514,12 @@ __global__ void __launch_bounds__(NT) k_values(ReconArgs a, Geo g, const uint32_
                 }
             }
             const uint64_t ptile = (pt[2] * g.nt[1] + pt[1]) * g.nt[0] + pt[0];
-            const uint32_t *src = F + g.off[A] + ptile * (uint64_t)sz;
-            for (int ci = threadIdx.x; ci < sz; ci += NT) carry[cb + ci] = has ? src[ci] : 0u;
+            if (has && (int)threadIdx.x < sz) cv[A] = F[g.off[A] + ptile * (uint64_t)sz + threadIdx.x];
             cb += sz;
         }
+#pragma unroll
+        for (int A = 1; A <= 7; A++)
+            if (A <= nA && (int)threadIdx.x < (int)g.size[A]) carry[cbase[A] + threadIdx.x] = cv[A];
         tile_prefix<TX, TY, TZ, NT>(a, g, tile, sm);
         const uint64_t x0 = tc[0] * TX, y0 = tc[1] * TY, z0 = tc[2] * TZ;
         for (int l = threadIdx.x; l < TX * TY * TZ; l += NT) {
@@ -537,6 +564,31 @@ __global__ void k_scan_lines(Geo g, int A, int d, uint64_t nlines, uint32_t *F)
     for (uint32_t i = 0; i < g.nt[d]; i++, p += stride) {
         run += F[p];
         F[p] = run;
+    }
+}
+
+// one warp per line, 32 entries at a time: for few lines, where a thread per
+// line would leave most of the GPU idle behind one long serial chain
+__global__ void __launch_bounds__(256) k_scan_lines_warp(Geo g, int A, int d, uint64_t nlines, uint32_t *F)
+{
+    const uint32_t lane = threadIdx.x & 31, len = g.nt[d];
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    for (uint64_t line = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; line < nlines; line += nw) {
+        uint64_t stride;
+        const uint64_t p0 = line_base(g, A, d, line, stride);
+        uint32_t carry = 0;
+        for (uint32_t i0 = 0; i0 < len; i0 += 32) {
+            const uint32_t i = i0 + lane;
+            uint32_t v = i < len ? F[p0 + i * stride] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= (uint32_t)o) v += u;
+            }
+            v += carry;
+            if (i < len) F[p0 + i * stride] = v;
+            carry = __shfl_sync(0xffffffffu, v, 31);
+        }
     }
 }
 
@@ -771,6 +823,10 @@ void launch_reconstruct(const ReconArgs &a, cudaStream_t st, int *launches)
                 const uint64_t nlines = g.size[A] * (g.ntiles / g.nt[d]);
                 if (g.nt[d] > 2048) {
                     k_scan_lines_cta<<<(unsigned)nlines, 1024, 0, st>>>(g, A, d, a.faces);
+                } else if (nlines < (uint64_t)a.num_sms * 256) {
+                    const uint64_t blocks = (nlines + 7) / 8;  // eight warps per block
+                    k_scan_lines_warp<<<(unsigned)std::min<uint64_t>(blocks, (uint64_t)a.num_sms * 8), 256, 0, st>>>(
+                        g, A, d, nlines, a.faces);
                 } else {
                     k_scan_lines<<<(unsigned)((nlines + 255) / 256), 256, 0, st>>>(g, A, d, nlines, a.faces);
                 }
