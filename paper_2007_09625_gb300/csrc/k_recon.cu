@@ -378,43 +378,67 @@ __global__ void __launch_bounds__(D == 2 ? 256 : 512) k_values_blocked(ReconArgs
 // ---------------------------------------------------------------------------
 // 2D / 3D tiles through shared memory
 
+// Tile geometry known at compile time.  Thread t's j-th point is l = t + j*NT:
+// with NT a multiple of TX its x is t % TX for every j, and its row index
+// (y + TY z inside the tile) is t / TX + j * NT / TX.  Point indices fit in 32
+// bits (n < 2^32).
+template <int TX, int TY, int TZ, int NT>
+struct TileGeo {
+    static constexpr int NE = TX * TY * TZ, PER = NE / NT, RPJ = NT / TX;
+    static_assert(NE % NT == 0 && NT % TX == 0, "whole rows per thread step");
+    static constexpr int D = TZ > 1 ? 3 : 2;
+    static constexpr int NA = D == 3 ? 7 : 3;  // nonempty subsets of the dimensions
+    // entries of subset A's array per tile, and where it starts in the staged carries
+    __host__ __device__ static constexpr int size(int A)
+    {
+        return ((A & 1) ? 1 : TX) * ((A & 2) ? 1 : TY) * ((A & 4) ? 1 : TZ);
+    }
+    __host__ __device__ static constexpr int base(int A)
+    {
+        int b = 0;  // a loop, not recursion: it must inline into the kernels
+        for (int B = 1; B < A; B++) b += size(B);
+        return b;
+    }
+    // index of point (x, y, z) in subset A's array: the coordinates not in A
+    __host__ __device__ static constexpr int comp(int A, int x, int y, int z)
+    {
+        return ((A & 1) ? 0 : x) + ((A & 2) ? 0 : y * ((A & 1) ? 1 : TX)) +
+               ((A & 4) ? 0 : z * ((A & 1) ? 1 : TX) * ((A & 2) ? 1 : TY));
+    }
+};
+
 template <int TX, int TY, int TZ, int NT>
 __device__ void tile_prefix(const ReconArgs &a, const Geo &g, uint64_t tile, uint32_t *sm)
 {
-    constexpr int NE = TX * TY * TZ;
-    constexpr int PER = NE / NT;
-    static_assert(NE % NT == 0, "whole points per thread");
-    const uint64_t tx = tile % g.nt[0], ty = (tile / g.nt[0]) % g.nt[1], tz = tile / ((uint64_t)g.nt[0] * g.nt[1]);
-    const uint64_t x0 = tx * TX, y0 = ty * TY, z0 = tz * TZ;
-    auto gidx = [&](int l, bool &in) -> uint64_t {
-        const int x = l % TX, y = (l / TX) % TY, z = l / (TX * TY);
-        const uint64_t gx = x0 + x, gy = y0 + y, gz = z0 + z;
-        in = gx < g.n[0] && gy < g.n[1] && gz < g.n[2];
-        return (gz * g.n[1] + gy) * g.n[0] + gx;
-    };
+    using TG = TileGeo<TX, TY, TZ, NT>;
+    const uint32_t tx = (uint32_t)(tile % g.nt[0]), ty = (uint32_t)((tile / g.nt[0]) % g.nt[1]),
+                   tz = (uint32_t)(tile / ((uint64_t)g.nt[0] * g.nt[1]));
+    const uint32_t n0 = (uint32_t)g.n[0], n1 = (uint32_t)g.n[1], n2 = (uint32_t)g.n[2];
+    const uint32_t gx = tx * TX + threadIdx.x % TX;
+    const uint32_t r0 = threadIdx.x / TX;
     // all of the thread's codes are loaded before any is used, so the loads
     // overlap; the few outliers' residuals follow
-    uint32_t code[PER];
+    uint32_t code[TG::PER];
 #pragma unroll
-    for (int j = 0; j < PER; j++) {
-        bool in;
-        const uint64_t i = gidx((int)threadIdx.x + j * NT, in);
-        code[j] = in ? (uint32_t)a.codes[i] : a.radius;  // outside the field: residual 0
+    for (int j = 0; j < TG::PER; j++) {
+        const uint32_t r = r0 + j * TG::RPJ, gy = ty * TY + r % TY, gz = tz * TZ + r / TY;
+        const bool in = gx < n0 && gy < n1 && gz < n2;
+        code[j] = in ? (uint32_t)a.codes[(gz * n1 + gy) * n0 + gx] : a.radius;  // outside: residual 0
     }
 #pragma unroll
-    for (int j = 0; j < PER; j++) {
-        const int l = (int)threadIdx.x + j * NT;
+    for (int j = 0; j < TG::PER; j++) {
         uint32_t v = code[j] - a.radius;
         if (code[j] == 0) {
-            bool in;
-            v = (uint32_t)a.dscr[gidx(l, in)];
+            const uint32_t r = r0 + j * TG::RPJ, gy = ty * TY + r % TY, gz = tz * TZ + r / TY;
+            v = (uint32_t)a.dscr[(gz * n1 + gy) * n0 + gx];
         }
-        sm[l] = v;
+        sm[threadIdx.x + j * NT] = v;
     }
     __syncthreads();
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     for (int line = warp; line < TY * TZ; line += NT / 32) {
         uint32_t carry = 0;
+#pragma unroll
         for (int seg = 0; seg < TX / 32; seg++) {
             const int idx = line * TX + seg * 32 + lane;
             const uint32_t v = warp_incl_scan(sm[idx]) + carry;
@@ -427,6 +451,7 @@ __device__ void tile_prefix(const ReconArgs &a, const Geo &g, uint64_t tile, uin
         for (int line = threadIdx.x; line < TX * TZ; line += NT) {
             const int x = line % TX, z = line / TX;
             uint32_t run = 0;
+#pragma unroll
             for (int y = 0; y < TY; y++) {
                 const int idx = (z * TY + y) * TX + x;
                 run += sm[idx];
@@ -438,6 +463,7 @@ __device__ void tile_prefix(const ReconArgs &a, const Geo &g, uint64_t tile, uin
     if (TZ > 1) {
         for (int line = threadIdx.x; line < TX * TY; line += NT) {
             uint32_t run = 0;
+#pragma unroll
             for (int z = 0; z < TZ; z++) {
                 const int idx = z * TX * TY + line;
                 run += sm[idx];
@@ -448,29 +474,18 @@ __device__ void tile_prefix(const ReconArgs &a, const Geo &g, uint64_t tile, uin
     }
 }
 
-// local index, inside the array of subset A, of the point (x, y, z)
-template <int TX, int TY, int TZ>
-__device__ __forceinline__ int comp_index(int A, int x, int y, int z)
-{
-    int ci = 0, mul = 1;
-    if (!(A & 1)) { ci += x * mul; mul *= TX; }
-    if (!(A & 2)) { ci += y * mul; mul *= TY; }
-    if (!(A & 4)) { ci += z * mul; }
-    return ci;
-}
-
 template <int TX, int TY, int TZ, int NT>
-__global__ void __launch_bounds__(NT) k_faces(ReconArgs a, Geo g, uint32_t *F)
+__global__ void __launch_bounds__(NT, NT >= 512 ? 3 : 6) k_faces(ReconArgs a, Geo g, uint32_t *F)
 {
+    using TG = TileGeo<TX, TY, TZ, NT>;
     __shared__ uint32_t sm[TX * TY * TZ];
     if (a.ctl->error & DERR_CORRUPT) return;
-    const int nA = g.ndim == 2 ? 3 : 7;
     for (uint64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
         tile_prefix<TX, TY, TZ, NT>(a, g, tile, sm);
-        for (int A = 1; A <= nA; A++) {
-            const uint64_t sz = g.size[A];
-            uint32_t *dst = F + g.off[A] + tile * sz;
-            for (int ci = threadIdx.x; ci < (int)sz; ci += NT) {
+        for (int A = 1; A <= TG::NA; A++) {
+            const int sz = TG::size(A);
+            uint32_t *dst = F + g.off[A] + tile * (uint64_t)sz;
+            for (int ci = threadIdx.x; ci < sz; ci += NT) {
                 // complement coordinates from ci, A coordinates at the last index
                 int r = ci, x = TX - 1, y = TY - 1, z = TZ - 1;
                 if (!(A & 1)) { x = r % TX; r /= TX; }
@@ -486,26 +501,25 @@ __global__ void __launch_bounds__(NT) k_faces(ReconArgs a, Geo g, uint32_t *F)
 template <int TX, int TY, int TZ, int NT>
 __global__ void __launch_bounds__(NT) k_values(ReconArgs a, Geo g, const uint32_t *F)
 {
+    using TG = TileGeo<TX, TY, TZ, NT>;
     __shared__ uint32_t sm[TX * TY * TZ];
-    __shared__ uint32_t carry[TX * TY + TX * TZ + TY * TZ + TX + TY + TZ + 1];
+    __shared__ uint32_t carry[TG::base(TG::NA) + TG::size(TG::NA)];
     if (a.ctl->error & DERR_CORRUPT) return;
-    const int nA = g.ndim == 2 ? 3 : 7;
     const float ebx2 = a.ebx2;
     for (uint64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
-        const uint64_t tc[3] = {tile % g.nt[0], (tile / g.nt[0]) % g.nt[1], tile / ((uint64_t)g.nt[0] * g.nt[1])};
+        const uint32_t tc[3] = {(uint32_t)(tile % g.nt[0]), (uint32_t)((tile / g.nt[0]) % g.nt[1]),
+                                (uint32_t)(tile / ((uint64_t)g.nt[0] * g.nt[1]))};
         // stage the carries of every subset: each subset's array has at most
         // NT entries, so a thread loads one entry of each, all loads at once
-        int cbase[8];
-        uint32_t cv[8];
-        int cb = 0;
+        uint32_t cv[TG::NA + 1];
 #pragma unroll
-        for (int A = 1; A <= 7; A++) {
+        for (int A = 1; A <= TG::NA; A++) {
+            static_assert(TG::size(1) <= NT && TG::size(2) <= NT && (TG::D == 2 || TG::size(4) <= NT),
+                          "one carry entry per thread and subset");
             cv[A] = 0;
-            if (A > nA) continue;
-            const int sz = (int)g.size[A];
-            cbase[A] = cb;
             bool has = true;
-            uint64_t pt[3];
+            uint32_t pt[3];
+#pragma unroll
             for (int d = 0; d < 3; d++) {
                 pt[d] = tc[d];
                 if ((A >> d) & 1) {
@@ -513,21 +527,21 @@ __global__ void __launch_bounds__(NT) k_values(ReconArgs a, Geo g, const uint32_
                     pt[d] = tc[d] - 1;
                 }
             }
-            const uint64_t ptile = (pt[2] * g.nt[1] + pt[1]) * g.nt[0] + pt[0];
-            if (has && (int)threadIdx.x < sz) cv[A] = F[g.off[A] + ptile * (uint64_t)sz + threadIdx.x];
-            cb += sz;
+            const uint64_t ptile = ((uint64_t)pt[2] * g.nt[1] + pt[1]) * g.nt[0] + pt[0];
+            if (has && (int)threadIdx.x < TG::size(A)) cv[A] = F[g.off[A] + ptile * (uint64_t)TG::size(A) + threadIdx.x];
         }
 #pragma unroll
-        for (int A = 1; A <= 7; A++)
-            if (A <= nA && (int)threadIdx.x < (int)g.size[A]) carry[cbase[A] + threadIdx.x] = cv[A];
+        for (int A = 1; A <= TG::NA; A++)
+            if ((int)threadIdx.x < TG::size(A)) carry[TG::base(A) + threadIdx.x] = cv[A];
         tile_prefix<TX, TY, TZ, NT>(a, g, tile, sm);
-        const uint64_t x0 = tc[0] * TX, y0 = tc[1] * TY, z0 = tc[2] * TZ;
+        const uint64_t x0 = (uint64_t)tc[0] * TX, y0 = (uint64_t)tc[1] * TY, z0 = (uint64_t)tc[2] * TZ;
         for (int l = threadIdx.x; l < TX * TY * TZ; l += NT) {
             const int x = l % TX, y = (l / TX) % TY, z = l / (TX * TY);
             const uint64_t gx = x0 + x, gy = y0 + y, gz = z0 + z;
             if (gx < g.n[0] && gy < g.n[1] && gz < g.n[2]) {
                 uint32_t s = sm[l];
-                for (int A = 1; A <= nA; A++) s += carry[cbase[A] + comp_index<TX, TY, TZ>(A, x, y, z)];
+#pragma unroll
+                for (int A = 1; A <= TG::NA; A++) s += carry[TG::base(A) + TG::comp(A, x, y, z)];
                 a.out[(gz * g.n[1] + gy) * g.n[0] + gx] = recon_value((int32_t)s, ebx2);
             }
         }
