@@ -454,6 +454,7 @@ __global__ void __launch_bounds__(kQ2Threads) k_dualquant_2d(QuantArgs a, uint32
 constexpr int kQ3Threads = 256;
 constexpr int kQ3T = 32;
 
+template <bool WIN>
 __global__ void __launch_bounds__(kQ3Threads) k_dualquant_3d(QuantArgs a, uint32_t ntx, uint32_t nty,
                                                              uint32_t ntz, uint32_t tz)
 {
@@ -464,9 +465,11 @@ __global__ void __launch_bounds__(kQ3Threads) k_dualquant_3d(QuantArgs a, uint32
     __syncthreads();
     if (a.ctl->error & DERR_EB) return;
     const EbScalars sc = load_scalars(a.ctl);
-    const int64_t nx = a.dims[0], ny = a.dims[1], nz = a.dims[2];
+    // point indices fit in 32 bits (n < 2^32)
+    const uint32_t nx = (uint32_t)a.dims[0], ny = (uint32_t)a.dims[1], nz = (uint32_t)a.dims[2];
     const uint32_t ntiles = ntx * nty * ntz;
     const int lx = threadIdx.x & 31, ly0 = threadIdx.x >> 5;
+    constexpr uint32_t B3 = lorenzo_block_extent(3);
     // halo point of this thread (if any), as plane-local coordinates (+1 offset)
     int hx = -2, hy = -2;
     if (threadIdx.x < 33) {
@@ -478,34 +481,41 @@ __global__ void __launch_bounds__(kQ3Threads) k_dualquant_3d(QuantArgs a, uint32
     }
     int buf = 0;
     for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const int64_t x0 = (int64_t)(tile % ntx) * kQ3T;
-        const int64_t y0 = (int64_t)((tile / ntx) % nty) * kQ3T;
-        const int64_t z0 = (int64_t)(tile / (ntx * nty)) * tz;
-        const int64_t z1 = min(nz, z0 + (int64_t)tz);
-        const int64_t gx = x0 + lx;
-        const int64_t ghx = x0 + hx, ghy = y0 + hy;
+        const uint32_t x0 = (tile % ntx) * kQ3T, y0 = ((tile / ntx) % nty) * kQ3T;
+        const int z0 = (int)((tile / (ntx * nty)) * tz), z1 = (int)min(nz, (uint32_t)z0 + tz);
+        const uint32_t gx = x0 + lx;
+        const int ghx = (int)x0 + hx, ghy = (int)y0 + hy;
         const bool has_halo = hx > -2;
-        const bool halo_in = has_halo && ghx >= 0 && ghy >= 0 && ghx < nx && ghy < ny;
+        const bool halo_in = has_halo && ghx >= 0 && ghy >= 0 && (uint32_t)ghx < nx && (uint32_t)ghy < ny;
+        // per-block mode: neighbours across a block face are padding (0)
+        const uint32_t mL = (a.lblock && gx % B3 == 0) ? 0u : ~0u;
+        uint32_t mU[4];
+        bool inpt[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint32_t gy = y0 + ly0 + 8 * j;
+            mU[j] = (a.lblock && gy % B3 == 0) ? 0u : ~0u;
+            inpt[j] = gx < nx && gy < ny;
+        }
         float cur[4], nxt[4], hcur = 0.0f, hnxt = 0.0f;
-        auto load_plane = [&](int64_t z, float *v, float &hv) {
+        auto load_plane = [&](int z, float *v, float &hv) {
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                const int64_t gy = y0 + ly0 + 8 * j;
-                v[j] = (z >= 0 && gx < nx && gy < ny) ? a.x[((uint64_t)z * ny + gy) * nx + gx] : 0.0f;
+                const uint32_t gy = y0 + ly0 + 8 * j;
+                v[j] = (z >= 0 && inpt[j]) ? a.x[((uint32_t)z * ny + gy) * nx + gx] : 0.0f;
             }
-            hv = (z >= 0 && halo_in) ? a.x[((uint64_t)z * ny + ghy) * nx + ghx] : 0.0f;
+            hv = (z >= 0 && halo_in) ? a.x[((uint32_t)z * ny + (uint32_t)ghy) * nx + (uint32_t)ghx] : 0.0f;
         };
         load_plane(z0 - 1, cur, hcur);
-        for (int64_t z = z0 - 1; z < z1; z++) {
+        for (int z = z0 - 1; z < z1; z++) {
             if (z + 1 < z1) load_plane(z + 1, nxt, hnxt);
             int32_t q[4];
             bool ex[4];
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                const int64_t gy = y0 + ly0 + 8 * j;
                 q[j] = 0;
                 ex[j] = false;
-                if (z >= 0 && gx < nx && gy < ny) q[j] = prequant(cur[j], sc, ex[j]);
+                if (z >= 0 && inpt[j]) q[j] = prequant(cur[j], sc, ex[j]);
                 pl[buf][ly0 + 8 * j + 1][lx + 1] = q[j];
             }
             if (has_halo) {
@@ -516,25 +526,24 @@ __global__ void __launch_bounds__(kQ3Threads) k_dualquant_3d(QuantArgs a, uint32
             if (z >= z0) {
                 const int prev = buf == 0 ? 2 : buf - 1;
                 const int X = lx + 1;
+                const uint32_t mB = (a.lblock && (uint32_t)z % B3 == 0) ? 0u : ~0u;
+                const uint32_t(*c)[kQ3T + 1] = (const uint32_t(*)[kQ3T + 1])pl[buf];
+                const uint32_t(*p)[kQ3T + 1] = (const uint32_t(*)[kQ3T + 1])pl[prev];
+                uint32_t pk = 0;
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
                     const int Y = ly0 + 8 * j + 1;
-                    const int64_t gy = y0 + Y - 1;
-                    if (gx < nx && gy < ny) {
-                        const uint32_t(*c)[kQ3T + 1] = (const uint32_t(*)[kQ3T + 1])pl[buf];
-                        const uint32_t(*p)[kQ3T + 1] = (const uint32_t(*)[kQ3T + 1])pl[prev];
-                        // per-block mode: neighbours across a block face are padding (0)
-                        const uint32_t B3 = lorenzo_block_extent(3);
-                        const uint32_t mL = (a.lblock && gx % B3 == 0) ? 0u : ~0u;
-                        const uint32_t mU = (a.lblock && gy % B3 == 0) ? 0u : ~0u;
-                        const uint32_t mB = (a.lblock && z % B3 == 0) ? 0u : ~0u;
-                        const uint32_t d = c[Y][X] - (c[Y][X - 1] & mL) - (c[Y - 1][X] & mU) - (p[Y][X] & mB) +
-                                           (c[Y - 1][X - 1] & mL & mU) + (p[Y][X - 1] & mL & mB) +
-                                           (p[Y - 1][X] & mU & mB) - (p[Y - 1][X - 1] & mL & mU & mB);
-                        const uint64_t idx = ((uint64_t)z * ny + gy) * nx + gx;
-                        a.codes[idx] = (uint16_t)emit_point(h, a, idx, d, ex[j]);
+                    if (inpt[j]) {
+                        const uint32_t mLU = mL & mU[j], mLB = mL & mB, mUB = mU[j] & mB;
+                        const uint32_t d = c[Y][X] - (c[Y][X - 1] & mL) - (c[Y - 1][X] & mU[j]) - (p[Y][X] & mB) +
+                                           (c[Y - 1][X - 1] & mLU) + (p[Y][X - 1] & mLB) + (p[Y - 1][X] & mUB) -
+                                           (p[Y - 1][X - 1] & mLU & mB);
+                        const uint32_t idx = ((uint32_t)z * ny + (y0 + Y - 1)) * nx + gx;
+                        a.codes[idx] = (uint16_t)point_1d<WIN>(h, a, idx, d, ex[j], pk);
+                        if (ex[j]) atomicAdd(&a.unit_exc[idx >> a.unit_shift], 1u);
                     }
                 }
+                unpack_central(h, pk);
             }
             buf = buf == 2 ? 0 : buf + 1;
 #pragma unroll
@@ -542,7 +551,8 @@ __global__ void __launch_bounds__(kQ3Threads) k_dualquant_3d(QuantArgs a, uint32
             hcur = hnxt;
         }
     }
-    hist_flush(h, a.hist, a.ctl);
+    if (WIN) h.n_out = 0;  // taken from bin 0 below
+    hist_flush(h, a.hist, a.ctl, WIN);
 }
 
 // ---------------------------------------------------------------------------
@@ -667,7 +677,8 @@ int launch_dualquant(const QuantArgs &a, cudaStream_t st)
         const uint32_t ntz = (uint32_t)((nz + tz - 1) / tz);
         const uint64_t ntiles = (uint64_t)ntx * nty * ntz;
         const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)a.num_sms * 8);
-        k_dualquant_3d<<<grid, kQ3Threads, hist_bytes, st>>>(a, ntx, nty, ntz, (uint32_t)tz);
+        if (nbins <= kWinBins) k_dualquant_3d<true><<<grid, kQ3Threads, hist_bytes, st>>>(a, ntx, nty, ntz, (uint32_t)tz);
+        else k_dualquant_3d<false><<<grid, kQ3Threads, hist_bytes, st>>>(a, ntx, nty, ntz, (uint32_t)tz);
     }
     return 1;
 }
