@@ -366,15 +366,16 @@ __global__ void __launch_bounds__(kQ1Threads) k_dualquant_1d(QuantArgs a, uint32
 }
 
 // ---------------------------------------------------------------------------
-// 2D: 128 threads; tile 512 (x) x 32 (y) swept row by row.  Each thread holds
+// 2D: 128 threads; tile 512 (x) x 8 (y) swept row by row.  Each thread holds
 // 4 points of a row (x = x0 + tid + 128 j).  Three row buffers of prequantized
 // integers in shared memory (slot 0 = the halo column x0 - 1); the next row's
 // floats are prefetched into registers while the current row is processed.
 
 constexpr int kQ2Threads = 128;
 constexpr int kQ2TX = 512;
-constexpr int kQ2TY = 32;
+constexpr int kQ2TY = 8;
 
+template <bool WIN>
 __global__ void __launch_bounds__(kQ2Threads) k_dualquant_2d(QuantArgs a, uint32_t ntx, uint32_t nty)
 {
     extern __shared__ uint32_t sh_hist[];
@@ -384,33 +385,43 @@ __global__ void __launch_bounds__(kQ2Threads) k_dualquant_2d(QuantArgs a, uint32
     __syncthreads();
     if (a.ctl->error & DERR_EB) return;
     const EbScalars sc = load_scalars(a.ctl);
-    const uint64_t nx = a.dims[0], ny = a.dims[1];
+    // point indices fit in 32 bits (n < 2^32)
+    const uint32_t nx = (uint32_t)a.dims[0], ny = (uint32_t)a.dims[1];
     const uint32_t ntiles = ntx * nty;
+    constexpr uint32_t B2 = lorenzo_block_extent(2);
     int buf = 0;
     for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
-        const uint64_t x0 = (uint64_t)(tile % ntx) * kQ2TX;
-        const int64_t y0 = (int64_t)(tile / ntx) * kQ2TY;
-        const int64_t y1 = min((int64_t)ny, y0 + kQ2TY);
+        const uint32_t x0 = (tile % ntx) * kQ2TX;
+        const int y0 = (int)((tile / ntx) * kQ2TY);
+        const int y1 = (int)min(ny, (uint32_t)y0 + kQ2TY);
+        // per-block mode: neighbours across a block edge are padding (0)
+        uint32_t mL[4];
+        bool inx[4];
+#pragma unroll
+        for (int j = 0; j < 4; j++) {
+            const uint32_t x = x0 + threadIdx.x + 128u * j;
+            mL[j] = (a.lblock && x % B2 == 0) ? 0u : ~0u;
+            inx[j] = x < nx;
+        }
         float cur[4], nxt[4], hcur = 0.0f, hnxt = 0.0f;
-        auto load_row = [&](int64_t y, float *v, float &hv) {
+        auto load_row = [&](int y, float *v, float &hv) {
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                const uint64_t x = x0 + threadIdx.x + 128u * j;
-                v[j] = (y >= 0 && x < nx) ? a.x[(uint64_t)y * nx + x] : 0.0f;
+                const uint32_t x = x0 + threadIdx.x + 128u * j;
+                v[j] = (y >= 0 && inx[j]) ? a.x[(uint32_t)y * nx + x] : 0.0f;
             }
-            if (threadIdx.x == 0) hv = (y >= 0 && x0 > 0) ? a.x[(uint64_t)y * nx + x0 - 1] : 0.0f;
+            if (threadIdx.x == 0) hv = (y >= 0 && x0 > 0) ? a.x[(uint32_t)y * nx + x0 - 1] : 0.0f;
         };
         load_row(y0 - 1, cur, hcur);
-        for (int64_t y = y0 - 1; y < y1; y++) {
+        for (int y = y0 - 1; y < y1; y++) {
             if (y + 1 < y1) load_row(y + 1, nxt, hnxt);
             int32_t q[4];
             bool ex[4];
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                const uint64_t x = x0 + threadIdx.x + 128u * j;
                 q[j] = 0;
                 ex[j] = false;
-                if (y >= 0 && x < nx) q[j] = prequant(cur[j], sc, ex[j]);
+                if (y >= 0 && inx[j]) q[j] = prequant(cur[j], sc, ex[j]);
                 rows[buf][1 + threadIdx.x + 128 * j] = q[j];
             }
             if (threadIdx.x == 0) {
@@ -420,21 +431,21 @@ __global__ void __launch_bounds__(kQ2Threads) k_dualquant_2d(QuantArgs a, uint32
             __syncthreads();
             if (y >= y0) {
                 const int prev = buf == 0 ? 2 : buf - 1;
+                const uint32_t mU = (a.lblock && (uint32_t)y % B2 == 0) ? 0u : ~0u;
+                uint32_t pk = 0;
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
                     const uint32_t lx = threadIdx.x + 128u * j;
-                    const uint64_t x = x0 + lx;
-                    if (x < nx) {
-                        // per-block mode: neighbours across a block edge are padding (0)
-                        const uint32_t mL = (a.lblock && x % lorenzo_block_extent(2) == 0) ? 0u : ~0u;
-                        const uint32_t mU = (a.lblock && (uint64_t)y % lorenzo_block_extent(2) == 0) ? 0u : ~0u;
-                        const uint32_t d = (uint32_t)q[j] - ((uint32_t)rows[buf][lx] & mL) -
+                    if (inx[j]) {
+                        const uint32_t d = (uint32_t)q[j] - ((uint32_t)rows[buf][lx] & mL[j]) -
                                            ((uint32_t)rows[prev][lx + 1] & mU) +
-                                           ((uint32_t)rows[prev][lx] & mL & mU);
-                        const uint64_t idx = (uint64_t)y * nx + x;
-                        a.codes[idx] = (uint16_t)emit_point(h, a, idx, d, ex[j]);
+                                           ((uint32_t)rows[prev][lx] & mL[j] & mU);
+                        const uint32_t idx = (uint32_t)y * nx + x0 + lx;
+                        a.codes[idx] = (uint16_t)point_1d<WIN>(h, a, idx, d, ex[j], pk);
+                        if (ex[j]) atomicAdd(&a.unit_exc[idx >> a.unit_shift], 1u);
                     }
                 }
+                unpack_central(h, pk);
             }
             buf = buf == 2 ? 0 : buf + 1;
 #pragma unroll
@@ -442,7 +453,8 @@ __global__ void __launch_bounds__(kQ2Threads) k_dualquant_2d(QuantArgs a, uint32
             hcur = hnxt;
         }
     }
-    hist_flush(h, a.hist, a.ctl);
+    if (WIN) h.n_out = 0;  // taken from bin 0 below
+    hist_flush(h, a.hist, a.ctl, WIN);
 }
 
 // ---------------------------------------------------------------------------
@@ -667,7 +679,8 @@ int launch_dualquant(const QuantArgs &a, cudaStream_t st)
         const uint32_t nty = (uint32_t)((a.dims[1] + kQ2TY - 1) / kQ2TY);
         const uint64_t ntiles = (uint64_t)ntx * nty;
         const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)a.num_sms * 12);
-        k_dualquant_2d<<<grid, kQ2Threads, hist_bytes, st>>>(a, ntx, nty);
+        if (nbins <= kWinBins) k_dualquant_2d<true><<<grid, kQ2Threads, hist_bytes, st>>>(a, ntx, nty);
+        else k_dualquant_2d<false><<<grid, kQ2Threads, hist_bytes, st>>>(a, ntx, nty);
     } else {
         const uint32_t ntx = (uint32_t)((a.dims[0] + kQ3T - 1) / kQ3T);
         const uint32_t nty = (uint32_t)((a.dims[1] + kQ3T - 1) / kQ3T);
