@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--skip-micro", action="store_true",
                     help="skip the codebook-vs-bins and 32/64-bit codeword micro-benchmarks")
     ap.add_argument("--skip-serving", action="store_true", help="skip the serving-mix measurement")
+    ap.add_argument("--skip-configs", action="store_true",
+                    help="skip the other single-field workloads (64^3, 1800x3600, 512^3)")
     return ap.parse_args()
 
 
@@ -225,6 +227,36 @@ def serving(gbsz, workloads, serve, dev, pool_size=32, requests=256, rate=200.0,
                         f"log-uniform, rel eb 1e-2/1e-3/1e-4, half compress, Poisson {rate:g} req/s",
             "offered": {k: paced[k] for k in keep}, "all_at_once": {k: burst[k] for k in keep},
             "bit_equal_to_alone": bool(eq1 and eq2)}
+
+
+def other_configs(ctx, gbsz, workloads, dev, reps=5):
+    """The other single-field workloads, compress + decompress of one field
+    each at rel eb 1e-4, radius 512, automatic chunk: 64^3 sinusoids, one
+    1800x3600 power-law field, 512^3 lognormal density."""
+    import torch
+    cases = [("64^3 sinusoids + noise (3D)", lambda: workloads.sinusoids_3d(64, seed=1001)),
+             ("1800x3600 power-law field (2D)", lambda: workloads.grf_2d_batch(nfields=1, seed=1003, masked=(0,))[0]),
+             ("512^3 lognormal density (3D)", lambda: workloads.lognormal_3d(512, seed=1004))]
+    out = []
+    for name, make in cases:
+        x = torch.from_numpy(make()).to(dev)
+        arc = torch.empty(gbsz.compress_bound(gbsz.field_dims(x), 1e-4), dtype=torch.uint8, device=dev)
+        y = torch.empty_like(x)
+        _, nb = ctx.compress(x, 1e-4, out=arc)
+        ctx.decompress(arc, nb, out=y)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        for _ in range(reps):
+            ctx.compress(x, 1e-4, out=arc)
+            ctx.decompress(arc, nb, out=y)
+        e1.record()
+        torch.cuda.synchronize(dev)
+        ms = e0.elapsed_time(e1) / reps
+        out.append({"workload": name, "bytes": x.numel() * 4, "ms_per_step": ms,
+                    "gbs": x.numel() * 4 / (ms / 1e3) / 1e9, "compression_ratio": x.numel() * 4 / nb})
+        del x, y, arc
+    return out
 
 
 def workload_chunk(n):
@@ -561,6 +593,10 @@ def main():
         micro = {"codebook_vs_bins": codebook_vs_bins(ctx, gbsz, dev),
                  "codeword_width": encode_width(ctx, gbsz, x, a.rel, a.radius, chunk, dev)}
 
+    configs_res = None
+    if rank == 0 and not a.skip_configs:
+        configs_res = other_configs(ctx, gbsz, workloads, dev)
+
     serving_res = None
     if rank == 0 and not a.skip_serving:
         from paper_2007_09625_gb300 import serve
@@ -593,6 +629,7 @@ def main():
                 "stage_ms_per_step": {nm: stage_ms[i] / a.steps for i, nm in enumerate(stage_names)},
                 "roofline": roofline, "kernels": per_kernel, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "batch_vs_per_field": batch, "micro": micro, "serving": serving_res,
+                "other_single_field": configs_res,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist:
