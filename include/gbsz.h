@@ -271,6 +271,9 @@ const char *gbsz_status_str(gbsz_status s);
  *   4 canonical codewords of the last compress (uint64[2R]: code, no length)
  *   5 batch graph counters (uint64[4]: compress captures, compress replays,
  *     decompress captures, decompress replays)
+ *   6 the same for single-field calls (gbsz_compress / gbsz_decompress
+ *     repeated with the same buffers and parameters on a capturable stream
+ *     are replayed as CUDA graphs)
  * `bytes` must equal the buffer's size.  Synchronises the context's last
  * stream.  Errors: INVALID_ARG, CUDA. */
 gbsz_status gbsz_debug_copy(gbsz_ctx *ctx, int which, void *h_dst,

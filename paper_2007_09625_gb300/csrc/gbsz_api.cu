@@ -216,8 +216,8 @@ struct gbsz_ctx {
     bool have_compress = false, have_decompress = false;
     // options
     uint32_t cw64_only = 0;  // GBSZ_OPT_CODEWORD_BITS = 64
-    // captured batch calls
-    BatchGraph gcomp, gdecomp;
+    // captured batch calls, and captured single-field calls
+    BatchGraph gcomp, gdecomp, gsc, gsd;
     // autotuned chunks, keyed by (ndim, dims, radius, lorenzo_block, lorenzo_order)
     std::vector<std::pair<std::vector<uint64_t>, uint32_t>> tuned;
     Buf tune_arc, tune_out;
@@ -745,6 +745,8 @@ void gbsz_destroy(gbsz_ctx *c)
     if (c->adone) cudaEventDestroy(c->adone);
     c->gcomp.drop();
     c->gdecomp.drop();
+    c->gsc.drop();
+    c->gsd.drop();
     c->tune_arc.release();
     c->tune_out.release();
     c->stage_field.release();
@@ -864,14 +866,29 @@ gbsz_status gbsz_compress(gbsz_ctx *c, const float *d_field, const gbsz_params *
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     c->last_stream = st;
     Slot *sl = c->slots[0];
-    s = enqueue_compress(c, sl, d_field, p, n, d_archive, capacity, st);
+    // a call repeated with the same buffers and parameters is replayed as a
+    // CUDA graph (captured on its second identical occurrence; not on the
+    // legacy default stream, which cannot be captured)
+    std::vector<uint64_t> key{0x5Cu, (uint64_t)(uintptr_t)c->ctl_host.p};
+    key_add(key, &d_field, sizeof(void *));
+    key_add(key, &d_archive, sizeof(void *));
+    key_add(key, &capacity, sizeof(size_t));
+    key.insert(key.end(), {p.ndim, p.dims[0], p.dims[1], p.dims[2], p.dims[3], p.eb_mode, p.radius, p.chunk,
+                           p.lorenzo_block, p.lorenzo_order, c->cw64_only});
+    key_add(key, &p.eb, sizeof(double));
+    auto enqueue = [&]() -> gbsz_status {
+        gbsz_status es = enqueue_compress(c, sl, d_field, p, n, d_archive, capacity, st);
+        if (es == GBSZ_OK &&
+            cudaMemcpyAsync(c->ctl_host.p, sl->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            es = GBSZ_ERR_CUDA;
+        return es;
+    };
+    s = run_batch(c, c->gsc, key, st, enqueue);
     if (s != GBSZ_OK) return s;
     c->last_n = n;
     c->last_nbins = 2 * p.radius;
     c->have_compress = true;
-    if (cudaMemcpyAsync(c->ctl_host.p, sl->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
-        return GBSZ_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GBSZ_ERR_CUDA;
     const Control &ch = c->ctl_host.p[0];
     *out_bytes = (size_t)ch.total;
     c->last_sc[0] = ch.eb;
@@ -909,13 +926,23 @@ gbsz_status gbsz_decompress(gbsz_ctx *c, const void *d_archive, size_t bytes, fl
     if (s != GBSZ_OK) return s;
     if (h.n > capacity_elems) return GBSZ_ERR_CAPACITY;
     Slot *sl = c->slots[0];
-    s = enqueue_decompress(c, sl, h, d_archive, d_field, st);
+    std::vector<uint64_t> key{0x5Du, (uint64_t)(uintptr_t)c->ctl_host.p};
+    key_add(key, &d_archive, sizeof(void *));
+    key_add(key, &d_field, sizeof(void *));
+    key_add(key, &bytes, sizeof(size_t));
+    key_add(key, c->h_header.p, kHeaderBytes);
+    auto enqueue = [&]() -> gbsz_status {
+        gbsz_status es = enqueue_decompress(c, sl, h, d_archive, d_field, st);
+        if (es == GBSZ_OK &&
+            cudaMemcpyAsync(c->ctl_host.p, sl->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st) != cudaSuccess)
+            es = GBSZ_ERR_CUDA;
+        return es;
+    };
+    s = run_batch(c, c->gsd, key, st, enqueue);
     if (s != GBSZ_OK) return s;
     c->last_dn = h.n;
     c->have_decompress = true;
-    if (cudaMemcpyAsync(c->ctl_host.p, sl->ctl, sizeof(Control), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
-        cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess)
-        return GBSZ_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GBSZ_ERR_CUDA;
     return decompress_status(c->ctl_host.p[0], h);
 }
 
@@ -1159,9 +1186,11 @@ gbsz_status gbsz_debug_copy(gbsz_ctx *c, int which, void *h_dst, size_t bytes)
         return GBSZ_OK;
     case 3: src = sl->codes.p; need = c->have_decompress ? c->last_dn * 2 : 0; break;
     case 4: src = sl->codes_only.p; need = c->have_compress ? c->last_nbins * 8 : 0; break;
-    case 5: {
+    case 5:
+    case 6: {
         if (bytes != 32) return GBSZ_ERR_INVALID_ARG;
-        const uint64_t v[4] = {c->gcomp.captures, c->gcomp.replays, c->gdecomp.captures, c->gdecomp.replays};
+        const BatchGraph &gc = which == 5 ? c->gcomp : c->gsc, &gd = which == 5 ? c->gdecomp : c->gsd;
+        const uint64_t v[4] = {gc.captures, gc.replays, gd.captures, gd.replays};
         std::memcpy(h_dst, v, 32);
         return GBSZ_OK;
     }

@@ -18,7 +18,7 @@ EB_ABS, EB_REL = 0, 1
 NSTAGE = 11
 STAGES = ["error_bound", "dualquant_hist", "codebook", "encode_count", "encode_scan", "encode_pack",
           "decode_tables", "decode_offsets", "decode", "reconstruct", "other"]
-DEBUG_CODES, DEBUG_HIST, DEBUG_SCALARS, DEBUG_DECODED, DEBUG_CODEWORDS, DEBUG_GRAPHS = range(6)
+DEBUG_CODES, DEBUG_HIST, DEBUG_SCALARS, DEBUG_DECODED, DEBUG_CODEWORDS, DEBUG_GRAPHS, DEBUG_GRAPHS_SINGLE = range(7)
 
 # every entry point of include/gbsz.h with its ctypes signature
 _P = C.c_void_p

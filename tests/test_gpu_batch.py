@@ -172,3 +172,30 @@ def test_batch_with_orders_blocks_and_4d(gb, ctx):
     for i in range(len(fields)):
         yo = ref.decompress(arcs[i][:nbs[i]].cpu().numpy())
         assert np.array_equal(outs[i].cpu().numpy().view(np.uint32), yo.view(np.uint32)), i
+
+
+def test_single_calls_replayed_as_graphs_follow_new_data(gb, ctx):
+    """Identical single-field calls on a capturable stream are replayed as
+    CUDA graphs; a replay reads the buffers' current contents, so new data in
+    the same buffers gives that data's archive and reconstruction."""
+    s = torch.cuda.Stream()
+    x = torch.from_numpy(workloads.field_for("sinus", (90, 130), seed=71)).cuda()
+    arc = torch.empty(gb.compress_bound(gb.field_dims(x), 1e-4), dtype=torch.uint8, device="cuda")
+    y = torch.empty_like(x)
+    g0 = ctx.debug_copy(gb.DEBUG_GRAPHS_SINGLE, 4, np.uint64)
+    # the same data four times (each kind: eager, eager, captured, replayed),
+    # then new data in the same buffers (the compress graph replays on it)
+    for i, seed in enumerate([71, 71, 71, 71, 72, 73]):
+        f = workloads.field_for("sinus", (90, 130), seed=seed)
+        with torch.cuda.stream(s):
+            x.copy_(torch.from_numpy(f))
+        s.synchronize()
+        _, nb = ctx.compress(x, 1e-4, out=arc, stream=s)
+        ctx.decompress(arc, nb, out=y, stream=s)
+        s.synchronize()
+        oa = ref.compress(f, 1e-4, ref.EB_REL, 512, gb.auto_chunk([130, 90]))
+        assert nb == oa.size and np.array_equal(arc[:nb].cpu().numpy(), oa), i
+        assert np.array_equal(y.cpu().numpy().view(np.uint32), ref.decompress(oa).view(np.uint32)), i
+    g1 = ctx.debug_copy(gb.DEBUG_GRAPHS_SINGLE, 4, np.uint64)
+    d = g1 - g0
+    assert d[0] >= 1 and d[1] >= 1 and d[2] >= 1 and d[3] >= 1, (g0, g1)
