@@ -271,13 +271,16 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeArgs a, uint32_t s
 
 // Two-level decode for archives whose codes all fit the complete table
 // (at most kFastLutMax bits).  Level 1 resolves every code of at most 8 bits
-// from the window's top byte; it is replicated once per lane with lane l's
-// copy in bank l (entry i of lane l at word 32 i + l), so the 32 lookups of a
-// warp never conflict.  Longer codes take the complete table (16-bit
+// from the window's top byte.  Its 8-byte entries are replicated 16 times
+// (entry i of copy c at 8-byte slot 16 i + c, lane l reading copy l % 16):
+// the 16 lanes of each half warp, which one 8-byte shared access serves
+// together, read 16 different copies in 32 different banks, so the lookups
+// never conflict.  Longer codes take the complete table (16-bit
 // entries (sym << 4) | len over B = maxlen bits) under a warp-uniform branch.
 // A pattern that matches no code has length 0; the smallest length seen is
 // checked after the chunk.
 constexpr uint32_t kL1Bits = 8;
+constexpr uint32_t kL1Copies = 16;
 
 // complete-table entry from global memory (read-only path; the rarely used
 // part of the table stays in L1)
@@ -324,7 +327,7 @@ __device__ __forceinline__ uint32_t decode_two(Window &w, const Ring<kRingFast> 
     const uint32_t nxt = rg.at(w.v + 4);
     const uint32_t c0 = __funnelshift_l(w.lo, w.hi, w.bo);
     const uint32_t c1 = __funnelshift_l(w.q0, w.lo, w.bo);
-    const uint2 e = l1[(c0 >> (32 - kL1Bits)) * 32];
+    const uint2 e = l1[(c0 >> (32 - kL1Bits)) * kL1Copies];
     uint32_t sw = e.x;
     uint32_t l1n = e.y & 0xFFu, l2n = e.y >> 8;
     const bool long1 = l1n == 0;
@@ -339,7 +342,7 @@ __device__ __forceinline__ uint32_t decode_two(Window &w, const Ring<kRingFast> 
     const bool need2 = l2n == 0;
     if (__any_sync(0xffffffffu, need2)) {
         const uint32_t cur2 = __funnelshift_l(c1, c0, l1n);  // the bits after the first code (l1n < 16)
-        const uint2 e2 = ld_shared_pred64(need2, l1 + (cur2 >> (32 - kL1Bits)) * 32);
+        const uint2 e2 = ld_shared_pred64(need2, l1 + (cur2 >> (32 - kL1Bits)) * kL1Copies);
         uint32_t l2b = e2.y & 0xFFu, s2b = e2.x & 0xFFFFu;
         const bool long2 = need2 && l2b == 0;
         if (__any_sync(0xffffffffu, long2)) {
@@ -462,14 +465,14 @@ __global__ void __launch_bounds__(kDecFastThreads, 2) k_decode_fast(DecodeArgs a
         l1once[i] = e;
     }
     __syncthreads();
-    for (uint32_t k = threadIdx.x; k < (32u << kL1Bits); k += blockDim.x) l1tab[k] = l1once[k >> 5];
+    for (uint32_t k = threadIdx.x; k < (kL1Copies << kL1Bits); k += blockDim.x) l1tab[k] = l1once[k / kL1Copies];
     __syncthreads();
     if (a.ctl->error & DERR_CORRUPT) return;
     const uint32_t *stream = reinterpret_cast<const uint32_t *>(a.archive + a.off_stream);
     const uint32_t *bits_tab = reinterpret_cast<const uint32_t *>(a.archive + a.off_bits);
     uint32_t *warp_ring = s_dyn + (threadIdx.x >> 5) * kRingFast * 32;
     const uint32_t lane = threadIdx.x & 31;
-    const uint2 *l1 = l1tab + lane;
+    const uint2 *l1 = l1tab + lane % kL1Copies;
     unsigned long long zeros = 0;
     bool bad = false;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
@@ -523,14 +526,14 @@ int launch_decode(const DecodeArgs &a, cudaStream_t st, int phase)
         const int most = (int)(kDecThreads * kRing * 4 + kSortedSmemMax * sizeof(uint16_t));
         cudaFuncSetAttribute(k_decode<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         cudaFuncSetAttribute(k_decode<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-        const int most_fast = (int)(kDecFastThreads * kRingFast * 4 + (8u << (5 + kL1Bits)));
+        const int most_fast = (int)(kDecFastThreads * kRingFast * 4 + 8u * kL1Copies * (1u << kL1Bits));
         cudaFuncSetAttribute(k_decode_fast<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
         cudaFuncSetAttribute(k_decode_fast<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
         attr_done |= bit;
     }
     const bool multi = a.chunk > kRecon1DTile;
     if (a.fast_bits) {
-        const size_t dyn_fast = (size_t)kDecFastThreads * kRingFast * 4 + (8u << (5 + kL1Bits));
+        const size_t dyn_fast = (size_t)kDecFastThreads * kRingFast * 4 + 8u * kL1Copies * (1u << kL1Bits);
         const uint64_t want = (a.nchunk + kDecFastThreads - 1) / kDecFastThreads;
         const int per_sm = 2;
         const unsigned g = (unsigned)std::min<uint64_t>(want, (uint64_t)(a.num_sms ? a.num_sms : 1) * per_sm);

@@ -405,14 +405,100 @@ struct TileGeo {
         return ((A & 1) ? 0 : x) + ((A & 2) ? 0 : y * ((A & 1) ? 1 : TX)) +
                ((A & 4) ? 0 : z * ((A & 1) ? 1 : TX) * ((A & 2) ? 1 : TY));
     }
+    // Column layout (3D tiles of 32-wide rows with one thread per (x, y)):
+    // thread t owns the z-column (t % TX, t / TX) and scans it in registers;
+    // the staged tile's rows are padded to TX + 1 words, so that scans along
+    // y (a thread per (x, z) line) and along x (HPR threads per row) hit 32
+    // different banks.
+    static constexpr bool COL = D == 3 && TX == 32 && NT == TX * TY && TX * TZ <= NT;
+    static constexpr int RS = COL ? TX + 1 : TX;  // words per staged row
+    static constexpr int SMW = TY * TZ * RS;
+    __host__ __device__ static constexpr int sidx(int x, int y, int z) { return (z * TY + y) * RS + x; }
 };
 
+// tile coordinates of a tile index (tile counts fit in 32 bits: n < 2^32)
+__device__ __forceinline__ void tile_coords(const Geo &g, uint32_t tile, uint32_t tc[3])
+{
+    const uint32_t nt0 = g.nt[0], nt1 = g.nt[1];
+    const uint32_t r = tile / nt0;
+    tc[0] = tile - r * nt0;
+    tc[1] = r % nt1;
+    tc[2] = r / nt1;
+}
+
+// Tile-local inclusive 3D prefix sum of the residuals in the column layout:
+// z in registers, then y and x through the padded staging array.
 template <int TX, int TY, int TZ, int NT>
-__device__ void tile_prefix(const ReconArgs &a, const Geo &g, uint64_t tile, uint32_t *sm)
+__device__ void tile_prefix_col(const ReconArgs &a, const Geo &g, const uint32_t tc[3], uint32_t *sm)
 {
     using TG = TileGeo<TX, TY, TZ, NT>;
-    const uint32_t tx = (uint32_t)(tile % g.nt[0]), ty = (uint32_t)((tile / g.nt[0]) % g.nt[1]),
-                   tz = (uint32_t)(tile / ((uint64_t)g.nt[0] * g.nt[1]));
+    static_assert(TG::COL, "column layout");
+    const uint32_t n0 = (uint32_t)g.n[0], n1 = (uint32_t)g.n[1], n2 = (uint32_t)g.n[2];
+    const int x = threadIdx.x % TX, y = threadIdx.x / TX;
+    const uint32_t gx = tc[0] * TX + x, gy = tc[1] * TY + y, gz0 = tc[2] * TZ;
+    const bool inxy = gx < n0 && gy < n1;
+    const uint32_t plane = n0 * n1;
+    const uint32_t base = (gz0 * n1 + gy) * n0 + gx;  // only dereferenced in range
+    uint32_t code[TZ];
+#pragma unroll
+    for (int z = 0; z < TZ; z++)
+        code[z] = inxy && gz0 + z < n2 ? (uint32_t)a.codes[base + z * plane] : a.radius;  // outside: residual 0
+    uint32_t run = 0;
+#pragma unroll
+    for (int z = 0; z < TZ; z++) {
+        uint32_t v = code[z] - a.radius;
+        if (code[z] == 0) v = (uint32_t)a.dscr[base + z * plane];
+        run += v;
+        sm[TG::sidx(x, y, z)] = run;
+    }
+    __syncthreads();
+    // along y: a thread per (x, z) line
+    for (int line = threadIdx.x; line < TX * TZ; line += NT) {
+        const int lx = line % TX, lz = line / TX;
+        uint32_t r = 0;
+#pragma unroll
+        for (int yy = 0; yy < TY; yy++) {
+            const int i = TG::sidx(lx, yy, lz);
+            r += sm[i];
+            sm[i] = r;
+        }
+    }
+    __syncthreads();
+    // along x: HPR threads per row (adjacent lanes), SEG points each, then
+    // the segment totals scanned across the HPR lanes
+    constexpr int ROWS = TY * TZ, HPR = NT / ROWS, SEG = TX / HPR;
+    static_assert(NT % ROWS == 0 && HPR >= 1 && HPR <= 32 && TX % HPR == 0, "row split");
+    {
+        const int row = threadIdx.x / HPR, seg = threadIdx.x % HPR;
+        uint32_t *p = sm + row * TG::RS + seg * SEG;
+        uint32_t v[SEG];
+        uint32_t r = 0;
+#pragma unroll
+        for (int i = 0; i < SEG; i++) {
+            r += p[i];
+            v[i] = r;
+        }
+        uint32_t incl = r;
+#pragma unroll
+        for (int o = 1; o < HPR; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o, HPR);
+            if (seg >= o) incl += t;
+        }
+        const uint32_t excl = incl - r;
+#pragma unroll
+        for (int i = 0; i < SEG; i++) p[i] = v[i] + excl;
+    }
+    __syncthreads();
+}
+
+// Tile-local inclusive prefix sum in the row layout (2D tiles): thread t's
+// j-th point is l = t + j * NT; rows scanned by warps, columns by threads.
+template <int TX, int TY, int TZ, int NT>
+__device__ void tile_prefix_rows(const ReconArgs &a, const Geo &g, const uint32_t tc[3], uint32_t *sm)
+{
+    using TG = TileGeo<TX, TY, TZ, NT>;
+    static_assert(TG::RS == TX, "row-major staging");
+    const uint32_t tx = tc[0], ty = tc[1], tz = tc[2];
     const uint32_t n0 = (uint32_t)g.n[0], n1 = (uint32_t)g.n[1], n2 = (uint32_t)g.n[2];
     const uint32_t gx = tx * TX + threadIdx.x % TX;
     const uint32_t r0 = threadIdx.x / TX;
@@ -475,13 +561,22 @@ __device__ void tile_prefix(const ReconArgs &a, const Geo &g, uint64_t tile, uin
 }
 
 template <int TX, int TY, int TZ, int NT>
+__device__ __forceinline__ void tile_prefix(const ReconArgs &a, const Geo &g, const uint32_t tc[3], uint32_t *sm)
+{
+    if constexpr (TileGeo<TX, TY, TZ, NT>::COL) tile_prefix_col<TX, TY, TZ, NT>(a, g, tc, sm);
+    else tile_prefix_rows<TX, TY, TZ, NT>(a, g, tc, sm);
+}
+
+template <int TX, int TY, int TZ, int NT>
 __global__ void __launch_bounds__(NT, NT >= 512 ? 3 : 6) k_faces(ReconArgs a, Geo g, uint32_t *F)
 {
     using TG = TileGeo<TX, TY, TZ, NT>;
-    __shared__ uint32_t sm[TX * TY * TZ];
+    __shared__ uint32_t sm[TG::SMW];
     if (a.ctl->error & DERR_CORRUPT) return;
-    for (uint64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
-        tile_prefix<TX, TY, TZ, NT>(a, g, tile, sm);
+    for (uint32_t tile = blockIdx.x; tile < (uint32_t)g.ntiles; tile += gridDim.x) {
+        uint32_t tc[3];
+        tile_coords(g, tile, tc);
+        tile_prefix<TX, TY, TZ, NT>(a, g, tc, sm);
         for (int A = 1; A <= TG::NA; A++) {
             const int sz = TG::size(A);
             uint32_t *dst = F + g.off[A] + tile * (uint64_t)sz;
@@ -491,7 +586,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 3 : 6) k_faces(ReconArgs a, Ge
                 if (!(A & 1)) { x = r % TX; r /= TX; }
                 if (!(A & 2)) { y = r % TY; r /= TY; }
                 if (!(A & 4)) { z = r; }
-                dst[ci] = sm[(z * TY + y) * TX + x];
+                dst[ci] = sm[TG::sidx(x, y, z)];
             }
         }
         __syncthreads();
@@ -502,13 +597,13 @@ template <int TX, int TY, int TZ, int NT>
 __global__ void __launch_bounds__(NT) k_values(ReconArgs a, Geo g, const uint32_t *F)
 {
     using TG = TileGeo<TX, TY, TZ, NT>;
-    __shared__ uint32_t sm[TX * TY * TZ];
+    __shared__ uint32_t sm[TG::SMW];
     __shared__ uint32_t carry[TG::base(TG::NA) + TG::size(TG::NA)];
     if (a.ctl->error & DERR_CORRUPT) return;
     const float ebx2 = a.ebx2;
-    for (uint64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
-        const uint32_t tc[3] = {(uint32_t)(tile % g.nt[0]), (uint32_t)((tile / g.nt[0]) % g.nt[1]),
-                                (uint32_t)(tile / ((uint64_t)g.nt[0] * g.nt[1]))};
+    for (uint32_t tile = blockIdx.x; tile < (uint32_t)g.ntiles; tile += gridDim.x) {
+        uint32_t tc[3];
+        tile_coords(g, tile, tc);
         // stage the carries of every subset: each subset's array has at most
         // NT entries, so a thread loads one entry of each, all loads at once
         uint32_t cv[TG::NA + 1];
@@ -533,16 +628,33 @@ __global__ void __launch_bounds__(NT) k_values(ReconArgs a, Geo g, const uint32_
 #pragma unroll
         for (int A = 1; A <= TG::NA; A++)
             if ((int)threadIdx.x < TG::size(A)) carry[TG::base(A) + threadIdx.x] = cv[A];
-        tile_prefix<TX, TY, TZ, NT>(a, g, tile, sm);
-        const uint64_t x0 = (uint64_t)tc[0] * TX, y0 = (uint64_t)tc[1] * TY, z0 = (uint64_t)tc[2] * TZ;
-        for (int l = threadIdx.x; l < TX * TY * TZ; l += NT) {
-            const int x = l % TX, y = (l / TX) % TY, z = l / (TX * TY);
-            const uint64_t gx = x0 + x, gy = y0 + y, gz = z0 + z;
-            if (gx < g.n[0] && gy < g.n[1] && gz < g.n[2]) {
-                uint32_t s = sm[l];
+        tile_prefix<TX, TY, TZ, NT>(a, g, tc, sm);
+        const uint32_t n0 = (uint32_t)g.n[0], n1 = (uint32_t)g.n[1], n2 = (uint32_t)g.n[2];
+        const uint32_t x0 = tc[0] * TX, y0 = tc[1] * TY, z0 = tc[2] * TZ;
+        if constexpr (TG::COL) {
+            // the thread's own column: x, y fixed, z = 0 .. TZ-1
+            const int x = threadIdx.x % TX, y = threadIdx.x / TX;
+            const uint32_t gx = x0 + x, gy = y0 + y;
+            const uint32_t plane = n0 * n1, base = (z0 * n1 + gy) * n0 + gx;
+            if (gx < n0 && gy < n1) {
 #pragma unroll
-                for (int A = 1; A <= TG::NA; A++) s += carry[TG::base(A) + TG::comp(A, x, y, z)];
-                a.out[(gz * g.n[1] + gy) * g.n[0] + gx] = recon_value((int32_t)s, ebx2);
+                for (int z = 0; z < TZ; z++) {
+                    uint32_t s = sm[TG::sidx(x, y, z)];
+#pragma unroll
+                    for (int A = 1; A <= TG::NA; A++) s += carry[TG::base(A) + TG::comp(A, x, y, z)];
+                    if (z0 + z < n2) a.out[base + z * plane] = recon_value((int32_t)s, ebx2);
+                }
+            }
+        } else {
+            for (int l = threadIdx.x; l < TX * TY * TZ; l += NT) {
+                const int x = l % TX, y = (l / TX) % TY, z = l / (TX * TY);
+                const uint32_t gx = x0 + x, gy = y0 + y, gz = z0 + z;
+                if (gx < n0 && gy < n1 && gz < n2) {
+                    uint32_t s = sm[TG::sidx(x, y, z)];
+#pragma unroll
+                    for (int A = 1; A <= TG::NA; A++) s += carry[TG::base(A) + TG::comp(A, x, y, z)];
+                    a.out[(gz * n1 + gy) * n0 + gx] = recon_value((int32_t)s, ebx2);
+                }
             }
         }
         __syncthreads();
