@@ -461,7 +461,13 @@ __global__ void __launch_bounds__(kQ2Threads) k_dualquant_2d(QuantArgs a, uint32
 // 3D: 256 threads; tile 32 (x) x 32 (y) swept along z over tz planes.  Thread
 // (lx = tid % 32, ly = tid / 32 + 8 j) holds 4 points of a plane.  Threads
 // 0..64 also prequantize one halo point each: the column x0 - 1 for
-// y0-1..y0+31 and the row y0 - 1 for x0..x0+31.  Three plane buffers.
+// y0-1..y0+31 and the row y0 - 1 for x0..x0+31.  The 3D Lorenzo residual is
+// taken as its separable form: the z-difference r = q(z) - q(z-1) of each
+// point comes from the thread's own previous integer (a register), and the
+// residual is the 2D Lorenzo stencil of r in the plane,
+//   d = r(x,y) - r(x-1,y) - r(x,y-1) + r(x-1,y-1),
+// which expands to the eight-term stencil exactly (modulo 2^32), masks of
+// the per-block mode included.  Two plane buffers of r, one barrier a plane.
 
 constexpr int kQ3Threads = 256;
 constexpr int kQ3T = 32;
@@ -471,7 +477,7 @@ __global__ void __launch_bounds__(kQ3Threads) k_dualquant_3d(QuantArgs a, uint32
                                                              uint32_t ntz, uint32_t tz)
 {
     extern __shared__ uint32_t sh_hist[];
-    __shared__ int32_t pl[3][kQ3T + 1][kQ3T + 1];
+    __shared__ uint32_t rp[2][kQ3T + 1][kQ3T + 1];
     HistState h;
     hist_init(h, sh_hist, a.radius);
     __syncthreads();
@@ -519,47 +525,55 @@ __global__ void __launch_bounds__(kQ3Threads) k_dualquant_3d(QuantArgs a, uint32
             hv = (z >= 0 && halo_in) ? a.x[((uint32_t)z * ny + (uint32_t)ghy) * nx + (uint32_t)ghx] : 0.0f;
         };
         load_plane(z0 - 1, cur, hcur);
+        uint32_t qprev[4] = {0u, 0u, 0u, 0u}, hprev = 0u;  // integers of the plane before (0 outside)
         for (int z = z0 - 1; z < z1; z++) {
             if (z + 1 < z1) load_plane(z + 1, nxt, hnxt);
-            int32_t q[4];
+            uint32_t q[4];
             bool ex[4];
 #pragma unroll
             for (int j = 0; j < 4; j++) {
-                q[j] = 0;
+                q[j] = 0u;
                 ex[j] = false;
-                if (z >= 0 && inpt[j]) q[j] = prequant(cur[j], sc, ex[j]);
-                pl[buf][ly0 + 8 * j + 1][lx + 1] = q[j];
+                if (z >= 0 && inpt[j]) q[j] = (uint32_t)prequant(cur[j], sc, ex[j]);
             }
-            if (has_halo) {
+            uint32_t hq = 0u;
+            if (z >= 0 && halo_in) {
                 bool dummy;
-                pl[buf][hy + 1][hx + 1] = (z >= 0 && halo_in) ? prequant(hcur, sc, dummy) : 0;
+                hq = (uint32_t)prequant(hcur, sc, dummy);
             }
-            __syncthreads();
             if (z >= z0) {
-                const int prev = buf == 0 ? 2 : buf - 1;
-                const int X = lx + 1;
                 const uint32_t mB = (a.lblock && (uint32_t)z % B3 == 0) ? 0u : ~0u;
-                const uint32_t(*c)[kQ3T + 1] = (const uint32_t(*)[kQ3T + 1])pl[buf];
-                const uint32_t(*p)[kQ3T + 1] = (const uint32_t(*)[kQ3T + 1])pl[prev];
+                uint32_t(*c)[kQ3T + 1] = rp[buf];
+                uint32_t r[4];
+#pragma unroll
+                for (int j = 0; j < 4; j++) {
+                    r[j] = q[j] - (qprev[j] & mB);
+                    c[ly0 + 8 * j + 1][lx + 1] = r[j];
+                }
+                if (has_halo) c[hy + 1][hx + 1] = hq - (hprev & mB);
+                __syncthreads();
+                const int X = lx + 1;
                 uint32_t pk = 0;
 #pragma unroll
                 for (int j = 0; j < 4; j++) {
                     const int Y = ly0 + 8 * j + 1;
                     if (inpt[j]) {
-                        const uint32_t mLU = mL & mU[j], mLB = mL & mB, mUB = mU[j] & mB;
-                        const uint32_t d = c[Y][X] - (c[Y][X - 1] & mL) - (c[Y - 1][X] & mU[j]) - (p[Y][X] & mB) +
-                                           (c[Y - 1][X - 1] & mLU) + (p[Y][X - 1] & mLB) + (p[Y - 1][X] & mUB) -
-                                           (p[Y - 1][X - 1] & mLU & mB);
+                        const uint32_t d = r[j] - (c[Y][X - 1] & mL) - (c[Y - 1][X] & mU[j]) +
+                                           (c[Y - 1][X - 1] & mL & mU[j]);
                         const uint32_t idx = ((uint32_t)z * ny + (y0 + Y - 1)) * nx + gx;
                         a.codes[idx] = (uint16_t)point_1d<WIN>(h, a, idx, d, ex[j], pk);
                         if (ex[j]) atomicAdd(&a.unit_exc[idx >> a.unit_shift], 1u);
                     }
                 }
                 unpack_central(h, pk);
+                buf ^= 1;
             }
-            buf = buf == 2 ? 0 : buf + 1;
 #pragma unroll
-            for (int j = 0; j < 4; j++) cur[j] = nxt[j];
+            for (int j = 0; j < 4; j++) {
+                qprev[j] = q[j];
+                cur[j] = nxt[j];
+            }
+            hprev = hq;
             hcur = hnxt;
         }
     }
