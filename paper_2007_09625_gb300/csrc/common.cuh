@@ -324,7 +324,8 @@ struct CodebookArgs {
     uint32_t *cw32;        // (len << 24) | code, valid when maxlen <= 24
     uint64_t *codes_only;  // plain codewords (debug copy)
     // decode tables
-    uint32_t *lut;         // 1 << kLutBits entries: (sym << 8) | len, 0 = long code
+    uint32_t *lut;         // 1 << kLutBits entries: (sym << 8) | len, 0 = long code;
+                           // then the second level (kLut2Words words, see kLut2Prefixes)
     unsigned long long *first;   // [kMaxLen + 2] first canonical code per length
     uint32_t *count;       // [kMaxLen + 2]
     uint32_t *start;       // [kMaxLen + 2]
@@ -339,6 +340,16 @@ struct CodebookArgs {
     Control *ctl;
 };
 constexpr int kLutBits = 12;
+// Second level of the decode table: for the kLut2Prefixes 12-bit prefixes
+// from the smallest one that starts a longer code (canonical codes put all
+// of them at the top), the code under each prefix and each value of the
+// next kLut2Bits bits, as 16-bit entries (sym << 5) | len when that code has
+// at most 12 + kLut2Bits bits and the symbol is below 2048, else 0.  Stored
+// after the 4096 first-level entries: the first prefix (one word), then the
+// entries.
+constexpr uint32_t kLut2Bits = 4, kLut2Prefixes = 128;
+constexpr uint32_t kLut2Entries = kLut2Prefixes << kLut2Bits;
+constexpr uint32_t kLut2Words = 1 + kLut2Entries / 2;
 // When every code is at most kFastLutMax bits and symbols fit 12 bits, the
 // decoder uses one complete table indexed by B = maxlen bits.  Up to
 // kPairLutMax bits an entry resolves the first code of its prefix and, when

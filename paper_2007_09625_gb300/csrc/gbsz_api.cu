@@ -164,7 +164,7 @@ struct Slot {
         return hist.ensure(B * 4) && cw64.ensure(B * 8) && cw32.ensure(B * 4) && codes_only.ensure(B * 8) &&
                keyA.ensure(B * 8) && keyB.ensure(B * 8) && nodef.ensure(B * 4) && parent.ensure(2 * B * 4) &&
                distA.ensure(2 * B * 4) && distB.ensure(2 * B * 4) && parA.ensure(2 * B * 4) &&
-               parB.ensure(2 * B * 4) && lut.ensure((1u << kLutBits) * 4) && lutf.ensure(kFastLutBytes) && first.ensure((kMaxLen + 2) * 8) &&
+               parB.ensure(2 * B * 4) && lut.ensure(((1u << kLutBits) + kLut2Words) * 4) && lutf.ensure(kFastLutBytes) && first.ensure((kMaxLen + 2) * 8) &&
                count.ensure((kMaxLen + 2) * 4) && start.ensure((kMaxLen + 2) * 4) && sorted.ensure(B * 2);
     }
     void release()

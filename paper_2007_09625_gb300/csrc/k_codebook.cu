@@ -417,6 +417,7 @@ __global__ void __launch_bounds__(kCbThreads, 1) k_decode_tables(CodebookArgs a)
         a.start[l] = canon.start[l];
     }
     // lookup table: canonical decode of every 12-bit prefix
+    uint32_t lo = 1u << kLutBits;  // smallest prefix that starts a longer code
     for (uint32_t v = t; v < (1u << kLutBits); v += T) {
         uint32_t e = 0;
         for (uint32_t l = 1; l <= (uint32_t)kLutBits && l <= ml; l++) {
@@ -428,6 +429,26 @@ __global__ void __launch_bounds__(kCbThreads, 1) k_decode_tables(CodebookArgs a)
             }
         }
         a.lut[v] = e;
+        if (e == 0) lo = min(lo, v);
+    }
+    lo = (1u << kLutBits) - 1 - block_max((1u << kLutBits) - 1 - min(lo, (1u << kLutBits) - 1), s_scan);
+    // second level under the prefixes lo .. lo + kLut2Prefixes - 1
+    uint32_t *l2w = a.lut + (1u << kLutBits);
+    uint16_t *l2 = reinterpret_cast<uint16_t *>(l2w + 1);
+    if (t == 0) l2w[0] = lo;
+    for (uint32_t k = t; k < kLut2Entries; k += T) {
+        const uint32_t v = lo + (k >> kLut2Bits);
+        const uint32_t pat = (v << kLut2Bits) | (k & ((1u << kLut2Bits) - 1));  // 16-bit string
+        uint32_t e = 0;
+        for (uint32_t l = kLutBits + 1; v < (1u << kLutBits) && l <= kLutBits + kLut2Bits && l <= ml; l++) {
+            const unsigned long long off = (unsigned long long)(pat >> (kLutBits + kLut2Bits - l)) - canon.first[l];
+            if (off < canon.count[l]) {
+                const uint32_t sym = a.sorted[canon.start[l] + off];
+                if (sym < 2048u) e = (sym << 5) | l;
+                break;
+            }
+        }
+        l2[k] = (uint16_t)e;
     }
     // complete table over fast_bits-bit prefixes (every code fits)
     const uint32_t B = a.fast_bits;

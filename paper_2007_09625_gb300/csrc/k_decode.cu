@@ -126,6 +126,8 @@ struct Window {
 
 struct DecTables {
     const uint32_t *lut;
+    const uint16_t *lut2;  // second level (kLut2Entries) and its first prefix
+    uint32_t l2lo;
     const unsigned long long *first;
     const uint32_t *count, *start;
     const uint16_t *sorted;
@@ -161,7 +163,14 @@ __device__ __forceinline__ uint32_t decode_one(Window &w, const Ring<kRing> &rg,
 {
     const uint32_t nxt = rg.at(w.v + 4);
     const uint32_t cur = __funnelshift_l(w.lo, w.hi, w.bo);
-    const uint32_t e = t.lut[cur >> (32 - kLutBits)];
+    uint32_t e = t.lut[cur >> (32 - kLutBits)];
+    if (e == 0) {  // longer than 12 bits: the second level resolves codes of up to 16
+        const uint32_t j = (cur >> (32 - kLutBits)) - t.l2lo;
+        const uint32_t e2 = j < kLut2Prefixes ? t.lut2[(j << kLut2Bits) | ((cur >> (32 - kLutBits - kLut2Bits)) &
+                                                                            ((1u << kLut2Bits) - 1))]
+                                              : 0u;
+        e = ((e2 >> 5) << 8) | (e2 & 31u);
+    }
     uint32_t sym = e >> 8, len = e & 0xFFu;
     if (e == 0) {
         // a code longer than the table: search the canonical tables, then
@@ -197,11 +206,14 @@ template <bool MULTI_TILE>
 __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeArgs a, uint32_t sorted_in_smem)
 {
     __shared__ uint32_t lut[1 << kLutBits];
+    __shared__ uint16_t lut2[kLut2Entries];
     __shared__ unsigned long long first[kMaxLen + 2];
     __shared__ uint32_t count[kMaxLen + 2], start[kMaxLen + 2];
     extern __shared__ uint32_t s_dyn[];  // rings, then the sorted symbols
     uint16_t *s_sorted = reinterpret_cast<uint16_t *>(s_dyn + kDecThreads * kRing);
     for (uint32_t i = threadIdx.x; i < (1u << kLutBits); i += blockDim.x) lut[i] = a.lut[i];
+    const uint16_t *g2 = reinterpret_cast<const uint16_t *>(a.lut + (1u << kLutBits) + 1);
+    for (uint32_t i = threadIdx.x; i < kLut2Entries; i += blockDim.x) lut2[i] = g2[i];
     for (uint32_t i = threadIdx.x; i < kMaxLen + 2; i += blockDim.x) {
         first[i] = a.first[i];
         count[i] = a.count[i];
@@ -212,7 +224,7 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeArgs a, uint32_t s
     if (a.ctl->error & DERR_CORRUPT) return;
     const uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (c >= a.nchunk) return;
-    DecTables t{lut, first, count, start, sorted_in_smem ? s_sorted : a.sorted, a.maxlen};
+    DecTables t{lut, lut2, a.lut[1u << kLutBits], first, count, start, sorted_in_smem ? s_sorted : a.sorted, a.maxlen};
     const uint32_t *stream = reinterpret_cast<const uint32_t *>(a.archive + a.off_stream);
     const uint32_t nbits = reinterpret_cast<const uint32_t *>(a.archive + a.off_bits)[c];
     const uint64_t coff = a.chunk_off[c];
