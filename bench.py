@@ -264,10 +264,11 @@ def other_configs(ctx, gbsz, workloads, dev, reps=5):
 
 def workload_chunk(n):
     """The Huffman chunk the library's rule picks for n points (chunk = 0):
-    about 1024 chunks per SM of a 152-SM GB300, a power of two in 64..4096.
-    Both arms of the benchmark use it, so they run the same configuration."""
+    the smallest power of two in 64..4096 whose chunks fit in one wave of
+    1024 decoding threads per SM on a 152-SM GB300.  Both arms of the
+    benchmark use it, so they run the same configuration."""
     c = 64
-    while c < 4096 and 2 * c <= n // (152 * 1024):
+    while c < 4096 and c * 152 * 1024 < n:
         c *= 2
     return c
 
@@ -290,7 +291,7 @@ DRAM_TRAFFIC = {
     "encode_pack": (909849344, ('k_encode.cu', 'common.cuh', 'scan.cuh'), "1ab7d54bb98f439d"),
     "decode": (727569152, ('k_decode.cu', 'common.cuh', 'scan.cuh'), "263ed0f4cfa5383f"),
 }
-TRAFFIC_CONFIG = (28, 1e-4, 512, 1024)  # log2 n, rel eb, radius, chunk of the capture
+TRAFFIC_CONFIG = (28, 1e-4, 512, 2048)  # log2 n, rel eb, radius, chunk of the capture
 
 
 def measured_traffic(stage, config):

@@ -110,7 +110,8 @@ gbsz_status gbsz_set_option(gbsz_ctx *ctx, int option, int64_t value);
 size_t gbsz_compress_bound(const gbsz_params *p);
 
 /* Chunk size that chunk = 0 resolves to for these parameters (a fixed rule
- * of n: about 1024 chunks per SM of a GB300, 64..4096 symbols). */
+ * of n: the smallest power of two in 64..4096 whose chunks fit in one wave of
+ * 1024 decoding threads per SM on a 152-SM GB300). */
 uint32_t gbsz_auto_chunk(const gbsz_params *p);
 
 /* Measured choice of the Huffman chunk (Sec. 3.2.4; the paper tunes it by

@@ -292,12 +292,14 @@ uint32_t lorenzo_geom(const gbsz_params &p, uint64_t d[3])
 
 uint32_t auto_chunk(uint64_t n)
 {
-    // Decoding is sequential inside a chunk, one thread per chunk: aim for
-    // about 1024 chunks per SM of a 152-SM GB300, between 64 and 4096 symbols.
-    // Depends on n only, so equal inputs always give equal archives.
-    uint64_t target = n / (152ull * 1024ull);
+    // Decoding is sequential inside a chunk, one thread per chunk, and the
+    // decoders keep 1024 threads resident per SM: the smallest power of two
+    // (64..4096 symbols) whose chunks fit in one such wave on a 152-SM GB300,
+    // so no partial second wave trails the first.  Depends on n only, so
+    // equal inputs always give equal archives.
+    const uint64_t wave = 152ull * 1024ull;
     uint32_t c = 64;
-    while (c < 4096 && (uint64_t)c * 2 <= target) c *= 2;
+    while (c < 4096 && (uint64_t)c * wave < n) c *= 2;
     return c;
 }
 

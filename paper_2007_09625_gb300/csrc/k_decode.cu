@@ -202,29 +202,11 @@ __device__ __forceinline__ uint32_t zeros_in(uint32_t pair)  // code-0 halves of
     return __popc(__vcmpeq2(pair, 0u)) >> 4;
 }
 
+// one chunk c of the general decoder (any code length)
 template <bool MULTI_TILE>
-__global__ void __launch_bounds__(kDecThreads) k_decode(DecodeArgs a, uint32_t sorted_in_smem)
+__device__ __forceinline__ void decode_chunk_general(const DecodeArgs &a, const DecTables &t, uint32_t *s_dyn,
+                                                     uint64_t c)
 {
-    __shared__ uint32_t lut[1 << kLutBits];
-    __shared__ uint16_t lut2[kLut2Entries];
-    __shared__ unsigned long long first[kMaxLen + 2];
-    __shared__ uint32_t count[kMaxLen + 2], start[kMaxLen + 2];
-    extern __shared__ uint32_t s_dyn[];  // rings, then the sorted symbols
-    uint16_t *s_sorted = reinterpret_cast<uint16_t *>(s_dyn + kDecThreads * kRing);
-    for (uint32_t i = threadIdx.x; i < (1u << kLutBits); i += blockDim.x) lut[i] = a.lut[i];
-    const uint16_t *g2 = reinterpret_cast<const uint16_t *>(a.lut + (1u << kLutBits) + 1);
-    for (uint32_t i = threadIdx.x; i < kLut2Entries; i += blockDim.x) lut2[i] = g2[i];
-    for (uint32_t i = threadIdx.x; i < kMaxLen + 2; i += blockDim.x) {
-        first[i] = a.first[i];
-        count[i] = a.count[i];
-        start[i] = a.start[i];
-    }
-    for (uint32_t i = threadIdx.x; i < sorted_in_smem; i += blockDim.x) s_sorted[i] = a.sorted[i];
-    __syncthreads();
-    if (a.ctl->error & DERR_CORRUPT) return;
-    const uint64_t c = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (c >= a.nchunk) return;
-    DecTables t{lut, lut2, a.lut[1u << kLutBits], first, count, start, sorted_in_smem ? s_sorted : a.sorted, a.maxlen};
     const uint32_t *stream = reinterpret_cast<const uint32_t *>(a.archive + a.off_stream);
     const uint32_t nbits = reinterpret_cast<const uint32_t *>(a.archive + a.off_bits)[c];
     const uint64_t coff = a.chunk_off[c];
@@ -279,6 +261,39 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeArgs a, uint32_t s
     // a valid chunk ends exactly at its recorded bit count
     if (bad || (uint64_t)w.v * 32 + w.bo != nbits) atomicOr(&a.ctl->error, DERR_CORRUPT);
     if (zeros) atomicAdd(&a.ctl->zeros, (unsigned long long)zeros);
+}
+
+// Persistent: warp task k is chunks 32k .. 32k+31, one per lane; block b's
+// warp w takes tasks w * gridDim.x + b, w * gridDim.x + b + (warps in the
+// grid), ...  Tasks are spread over the blocks first, so every block, and so
+// every SM, gets the same number of tasks to within one.
+template <bool MULTI_TILE>
+__global__ void __launch_bounds__(kDecThreads) k_decode(DecodeArgs a, uint32_t sorted_in_smem)
+{
+    __shared__ uint32_t lut[1 << kLutBits];
+    __shared__ uint16_t lut2[kLut2Entries];
+    __shared__ unsigned long long first[kMaxLen + 2];
+    __shared__ uint32_t count[kMaxLen + 2], start[kMaxLen + 2];
+    extern __shared__ uint32_t s_dyn[];  // rings, then the sorted symbols
+    uint16_t *s_sorted = reinterpret_cast<uint16_t *>(s_dyn + kDecThreads * kRing);
+    for (uint32_t i = threadIdx.x; i < (1u << kLutBits); i += blockDim.x) lut[i] = a.lut[i];
+    const uint16_t *g2 = reinterpret_cast<const uint16_t *>(a.lut + (1u << kLutBits) + 1);
+    for (uint32_t i = threadIdx.x; i < kLut2Entries; i += blockDim.x) lut2[i] = g2[i];
+    for (uint32_t i = threadIdx.x; i < kMaxLen + 2; i += blockDim.x) {
+        first[i] = a.first[i];
+        count[i] = a.count[i];
+        start[i] = a.start[i];
+    }
+    for (uint32_t i = threadIdx.x; i < sorted_in_smem; i += blockDim.x) s_sorted[i] = a.sorted[i];
+    __syncthreads();
+    if (a.ctl->error & DERR_CORRUPT) return;
+    const DecTables t{lut, lut2, a.lut[1u << kLutBits], first, count, start, sorted_in_smem ? s_sorted : a.sorted,
+                      a.maxlen};
+    const uint64_t ntask = (a.nchunk + 31) / 32, tstride = (uint64_t)(blockDim.x >> 5) * gridDim.x;
+    for (uint64_t k = (uint64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x; k < ntask; k += tstride) {
+        const uint64_t c = k * 32 + (threadIdx.x & 31);
+        if (c < a.nchunk) decode_chunk_general<MULTI_TILE>(a, t, s_dyn, c);
+    }
 }
 
 // Two-level decode for archives whose codes all fit the complete table
@@ -489,7 +504,11 @@ __global__ void __launch_bounds__(kDecFastThreads, 2) k_decode_fast(DecodeArgs a
     bool bad = false;
     const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
     // whole warps iterate together (the level-1 fallback votes across the
-    // warp); lanes past the last chunk decode nothing
+    // warp); lanes past the last chunk decode nothing.  Consecutive chunks go
+    // to consecutive threads: spreading warp tasks evenly over the blocks
+    // instead (as k_decode does) measured about 4% slower here (2^28 symbols
+    // in 2048-symbol chunks), since it does not even out the warps per
+    // scheduler, which bound this latency-bound loop.
     for (uint64_t cw = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; cw < a.nchunk; cw += stride) {
         const uint64_t c = cw + lane;
         const bool live = c < a.nchunk;
@@ -526,11 +545,14 @@ int launch_decode(const DecodeArgs &a, cudaStream_t st, int phase)
     op.maxbits = (unsigned long long)a.chunk * kMaxLen;
     op.ctl = a.ctl;
     if (phase == 0) return launch_scan(op, a.nchunk, a.scan_partial, st);
-    const uint64_t grid = (a.nchunk + kDecThreads - 1) / kDecThreads;
+    const uint64_t ntask = (a.nchunk + 31) / 32;
     const uint32_t nb = 2 * a.radius;
     const uint32_t in_smem = nb <= kSortedSmemMax ? nb : 0u;
     const size_t dyn = (size_t)kDecThreads * kRing * 4 + in_smem * sizeof(uint16_t);
     static unsigned long long attr_done = 0;  // one bit per device id < 64
+    // k_decode blocks resident per SM, by device, MULTI_TILE and the sorted
+    // table's size in shared memory (steps of 512 symbols); 0: not queried yet
+    static int resident[64][2][kSortedSmemMax / 512 + 1];
     int dev = 0;
     cudaGetDevice(&dev);
     const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0;
@@ -551,10 +573,29 @@ int launch_decode(const DecodeArgs &a, cudaStream_t st, int phase)
         const unsigned g = (unsigned)std::min<uint64_t>(want, (uint64_t)(a.num_sms ? a.num_sms : 1) * per_sm);
         if (multi) k_decode_fast<true><<<g, kDecFastThreads, dyn_fast, st>>>(a);
         else k_decode_fast<false><<<g, kDecFastThreads, dyn_fast, st>>>(a);
-    } else if (multi) {
-        k_decode<true><<<(unsigned)grid, kDecThreads, dyn, st>>>(a, in_smem);
     } else {
-        k_decode<false><<<(unsigned)grid, kDecThreads, dyn, st>>>(a, in_smem);
+        // persistent: as many blocks as are resident at once
+        const uint32_t qb = (in_smem + 511) / 512;
+        int per_sm = 1;
+        if (bit) {
+            int &r = resident[dev][multi ? 1 : 0][qb];
+            if (r == 0) {
+                const size_t dq = (size_t)kDecThreads * kRing * 4 + (size_t)qb * 512 * sizeof(uint16_t);
+                int blocks = 0;
+                const cudaError_t e =
+                    multi ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_decode<true>, kDecThreads, dq)
+                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_decode<false>, kDecThreads, dq);
+                if (e != cudaSuccess) {
+                    cudaGetLastError();
+                    blocks = 0;
+                }
+                r = blocks > 0 ? blocks : 1;
+            }
+            per_sm = r;
+        }
+        const unsigned g = (unsigned)std::min<uint64_t>(ntask, (uint64_t)(a.num_sms ? a.num_sms : 1) * per_sm);
+        if (multi) k_decode<true><<<g, kDecThreads, dyn, st>>>(a, in_smem);
+        else k_decode<false><<<g, kDecThreads, dyn, st>>>(a, in_smem);
     }
     return 1;
 }

@@ -594,7 +594,7 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 3 : 6) k_faces(ReconArgs a, Ge
 }
 
 template <int TX, int TY, int TZ, int NT>
-__global__ void __launch_bounds__(NT) k_values(ReconArgs a, Geo g, const uint32_t *F)
+__global__ void __launch_bounds__(NT, NT >= 512 ? 4 : 8) k_values(ReconArgs a, Geo g, const uint32_t *F)
 {
     using TG = TileGeo<TX, TY, TZ, NT>;
     __shared__ uint32_t sm[TG::SMW];

@@ -54,10 +54,13 @@ def test_compress_bound_and_invalid_params(lib):
 
 
 def test_auto_chunk_rule(lib):
-    assert gbsz.auto_chunk([1 << 28]) == 1024
+    # smallest power of two (64..4096) with n <= chunk * 1024 * 152
+    assert gbsz.auto_chunk([1 << 28]) == 2048
+    assert gbsz.auto_chunk([2048 * 1024 * 152]) == 2048
+    assert gbsz.auto_chunk([2048 * 1024 * 152 + 1]) == 4096
     assert gbsz.auto_chunk([1 << 30]) == 4096
     assert gbsz.auto_chunk([64, 64, 64]) == 64
-    assert gbsz.auto_chunk([512, 512, 512]) == 512
+    assert gbsz.auto_chunk([512, 512, 512]) == 1024
     assert gbsz.auto_chunk([3600, 1800]) == 64
 
 
