@@ -21,6 +21,12 @@ CASES = [
     ("walk", (50000,), 1e-6, ref.EB_REL, 32768, 1024),
     ("grf", (150, 170), 1e-5, ref.EB_REL, 64, 4096),
     ("lognormal", (21, 23, 25), 1e-4, ref.EB_REL, 64, 128),
+    # wide codebooks: codes of 13-16 bits (the general decoder's second table
+    # level) and longer (its per-length search) -- 157 + 44 and 520 + 51 of
+    # them in the bit-flip test's archives; the targeted test's lognormal
+    # archive tops out at 15 bits and so takes the fast decoder instead
+    ("grf", (300, 410), 1e-4, ref.EB_REL, 512, 256),
+    ("lognormal", (60, 61, 63), 1e-4, ref.EB_REL, 512, 256),
 ]
 
 
