@@ -449,13 +449,17 @@ def main():
     bound = gbsz.compress_bound([n], a.rel, gbsz.EB_REL, a.radius, chunk)
     arc = torch.empty(bound, dtype=torch.uint8, device=dev)
     y = torch.empty_like(x)
-    stream = torch.cuda.current_stream(dev)
+    # a stream of its own: repeated calls on the same buffers are captured as
+    # CUDA graphs by the library (after two eager calls) and replayed, stage
+    # timing events included
+    stream = torch.cuda.Stream(dev)
 
     def step():
-        _, nb = ctx.compress(x, a.rel, gbsz.EB_REL, a.radius, chunk, out=arc)
-        ctx.decompress(arc, nb, out=y)
+        _, nb = ctx.compress(x, a.rel, gbsz.EB_REL, a.radius, chunk, out=arc, stream=stream)
+        ctx.decompress(arc, nb, out=y, stream=stream)
         return nb
 
+    torch.cuda.synchronize(dev)  # inputs and buffers made on the default stream are ready
     for _ in range(max(a.warmup, 0)):
         nb = step()
     torch.cuda.synchronize(dev)

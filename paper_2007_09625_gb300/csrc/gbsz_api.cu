@@ -112,23 +112,26 @@ template <typename T> struct HostBuf {
 // the allocation generation; the first call with a key runs eagerly, the
 // second is captured, later ones replay the graph (one launch instead of
 // about a dozen kernels, copies and memsets per field).
+struct StageRec {
+    int stage;
+    cudaEvent_t a, b;
+};
+
 struct BatchGraph {
     std::vector<uint64_t> key;   // key of the captured graph
     std::vector<uint64_t> seen;  // key of the last eager call
     cudaGraphExec_t exec = nullptr;
     uint64_t launches = 0;       // kernels in one replay
     uint64_t captures = 0, replays = 0;
+    // stage timing events recorded by the graph's own nodes (captured while
+    // profiling); every replay records them again
+    std::vector<StageRec> recs;
     void drop()
     {
         if (exec) cudaGraphExecDestroy(exec);
         exec = nullptr;
         key.clear();
     }
-};
-
-struct StageRec {
-    int stage;
-    cudaEvent_t a, b;
 };
 
 struct Slot {
@@ -226,6 +229,9 @@ struct gbsz_ctx {
     std::vector<StageRec> recs;
     std::vector<cudaEvent_t> pool;
     uint64_t launches = 0;
+    double prof_ms[GBSZ_NSTAGE] = {};     // stage times collected from graph replays
+    uint64_t prof_n[GBSZ_NSTAGE] = {};
+    BatchGraph *prof_pending = nullptr;  // replayed graph whose stage events await collection
 
     cudaEvent_t ev()
     {
@@ -313,19 +319,31 @@ gbsz_status map_device_error(uint32_t e)
     return GBSZ_OK;
 }
 
+// A stage event.  In a stream that is being captured, a plain record would
+// only order the captured work; an external record becomes an event-record
+// node of the graph, recorded again by every replay.
+void record_stage_event(cudaEvent_t e, cudaStream_t st)
+{
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) == cudaSuccess && cs == cudaStreamCaptureStatusActive)
+        cudaEventRecordWithFlags(e, st, cudaEventRecordExternal);
+    else
+        cudaEventRecord(e, st);
+}
+
 void stage_begin(gbsz_ctx *c, cudaStream_t st, cudaEvent_t *e)
 {
     *e = nullptr;
     if (!c->profiling) return;
     *e = c->ev();
-    cudaEventRecord(*e, st);
+    record_stage_event(*e, st);
 }
 
 void stage_end(gbsz_ctx *c, cudaStream_t st, int stage, cudaEvent_t a)
 {
     if (!c->profiling || !a) return;
     cudaEvent_t b = c->ev();
-    cudaEventRecord(b, st);
+    record_stage_event(b, st);
     c->recs.push_back({stage, a, b});
 }
 
@@ -634,20 +652,29 @@ namespace {
 // Runs `enqueue` (which forks the caller's stream st to the slot streams and
 // joins them back) either eagerly, or through the context's graph for this
 // kind of batch: replayed if `key` matches the captured one, captured if it
-// matches the previous eager call's.  Profiling always runs eagerly (its
-// events are recorded at enqueue time).
+// matches the previous eager call's.  While profiling, the stage events are
+// captured as event-record nodes of the graph; the caller collects their
+// times (prof_collect) after it has synchronized with the replay.
 template <typename F>
 gbsz_status run_batch(gbsz_ctx *c, BatchGraph &bg, std::vector<uint64_t> &key, cudaStream_t st, F enqueue)
 {
-    key.push_back(g_alloc_gen.load());
-    if (!c->profiling && bg.exec && key == bg.key) {
+    key.push_back(c->profiling ? 1u : 0u);
+    key.push_back(g_alloc_gen.load());  // last: checked again after a capture
+    if (bg.exec && key == bg.key) {
         c->launches += bg.launches;
         bg.replays++;
+        if (!bg.recs.empty()) c->prof_pending = &bg;
         return cudaGraphLaunch(bg.exec, st) == cudaSuccess ? GBSZ_OK : GBSZ_ERR_CUDA;
     }
-    if (!c->profiling && key == bg.seen) {
+    if (key == bg.seen) {
         bg.drop();
+        for (auto &r : bg.recs) {  // the old graph's events
+            c->pool.push_back(r.a);
+            c->pool.push_back(r.b);
+        }
+        bg.recs.clear();
         const uint64_t l0 = c->launches;
+        const size_t r0 = c->recs.size();
         cudaGraph_t graph = nullptr;
         if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
             const gbsz_status es = enqueue();
@@ -658,6 +685,9 @@ gbsz_status run_batch(gbsz_ctx *c, BatchGraph &bg, std::vector<uint64_t> &key, c
                 bg.key = key;
                 bg.launches = c->launches - l0;
                 bg.captures++;
+                bg.recs.assign(c->recs.begin() + r0, c->recs.end());  // now the graph's
+                c->recs.resize(r0);
+                if (!bg.recs.empty()) c->prof_pending = &bg;
                 return cudaGraphLaunch(bg.exec, st) == cudaSuccess ? GBSZ_OK : GBSZ_ERR_CUDA;
             }
             if (graph) cudaGraphDestroy(graph);
@@ -665,10 +695,31 @@ gbsz_status run_batch(gbsz_ctx *c, BatchGraph &bg, std::vector<uint64_t> &key, c
         }
         cudaGetLastError();  // a failed capture leaves nothing behind; run eagerly
         c->launches = l0;
+        for (size_t i = r0; i < c->recs.size(); i++) {  // events of the failed capture
+            c->pool.push_back(c->recs[i].a);
+            c->pool.push_back(c->recs[i].b);
+        }
+        c->recs.resize(r0);
     }
     const gbsz_status es = enqueue();
     bg.seen = key;
     return es;
+}
+
+// After the caller has synchronized with a replayed graph: its stage times.
+void prof_collect(gbsz_ctx *c)
+{
+    BatchGraph *bg = c->prof_pending;
+    c->prof_pending = nullptr;
+    if (!bg) return;
+    for (const auto &r : bg->recs) {
+        float t = 0;
+        if (r.stage >= 0 && r.stage < GBSZ_NSTAGE && cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+            c->prof_ms[r.stage] += t;
+            c->prof_n[r.stage]++;
+        }
+    }
+    cudaGetLastError();
 }
 
 inline void key_add(std::vector<uint64_t> &k, const void *p, size_t bytes)
@@ -759,6 +810,11 @@ void gbsz_destroy(gbsz_ctx *c)
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
+    for (BatchGraph *bg : {&c->gcomp, &c->gdecomp, &c->gsc, &c->gsd})
+        for (auto &r : bg->recs) {
+            cudaEventDestroy(r.a);
+            cudaEventDestroy(r.b);
+        }
     for (auto e : c->pool) cudaEventDestroy(e);
     if (c->fork) cudaEventDestroy(c->fork);
     delete c;
@@ -891,6 +947,7 @@ gbsz_status gbsz_compress(gbsz_ctx *c, const float *d_field, const gbsz_params *
     c->last_nbins = 2 * p.radius;
     c->have_compress = true;
     if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GBSZ_ERR_CUDA;
+    prof_collect(c);
     const Control &ch = c->ctl_host.p[0];
     *out_bytes = (size_t)ch.total;
     c->last_sc[0] = ch.eb;
@@ -945,6 +1002,7 @@ gbsz_status gbsz_decompress(gbsz_ctx *c, const void *d_archive, size_t bytes, fl
     c->last_dn = h.n;
     c->have_decompress = true;
     if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GBSZ_ERR_CUDA;
+    prof_collect(c);
     return decompress_status(c->ctl_host.p[0], h);
 }
 
@@ -1002,6 +1060,7 @@ gbsz_status gbsz_compress_batch(gbsz_ctx *c, uint32_t count, const float *const 
     const gbsz_status es = run_batch(c, c->gcomp, key, st, enqueue);
     if (es != GBSZ_OK) return es;
     if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GBSZ_ERR_CUDA;
+    prof_collect(c);
     gbsz_status first = GBSZ_OK;
     for (uint32_t i = 0; i < count; i++) {
         if (statuses[i] == GBSZ_OK) {
@@ -1076,6 +1135,7 @@ gbsz_status gbsz_decompress_batch(gbsz_ctx *c, uint32_t count, const void *const
     const gbsz_status es = run_batch(c, c->gdecomp, key, st, enqueue);
     if (es != GBSZ_OK) return es;
     if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GBSZ_ERR_CUDA;
+    prof_collect(c);
     gbsz_status first = GBSZ_OK;
     for (uint32_t i = 0; i < count; i++) {
         if (statuses[i] == GBSZ_OK) statuses[i] = decompress_status(c->ctl_host.p[i], hs[i]);
@@ -1229,6 +1289,12 @@ gbsz_status gbsz_profile_read(gbsz_ctx *c, double *ms, uint64_t *calls, uint64_t
         c->pool.push_back(r.b);
     }
     c->recs.clear();
+    for (int i = 0; i < GBSZ_NSTAGE; i++) {
+        acc[i] += c->prof_ms[i];
+        cnt[i] += c->prof_n[i];
+        c->prof_ms[i] = 0;
+        c->prof_n[i] = 0;
+    }
     if (ms)
         for (int i = 0; i < GBSZ_NSTAGE; i++) ms[i] = acc[i];
     if (calls)

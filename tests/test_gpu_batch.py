@@ -199,3 +199,35 @@ def test_single_calls_replayed_as_graphs_follow_new_data(gb, ctx):
     g1 = ctx.debug_copy(gb.DEBUG_GRAPHS_SINGLE, 4, np.uint64)
     d = g1 - g0
     assert d[0] >= 1 and d[1] >= 1 and d[2] >= 1 and d[3] >= 1, (g0, g1)
+
+
+def test_profiling_survives_graph_replay(gb, ctx):
+    """Stage timing while identical calls are captured and replayed: every
+    call of every stage is counted, with a positive time, and the archive
+    and reconstruction stay the oracle's."""
+    s = torch.cuda.Stream()
+    f = workloads.field_for("walk", (300001,), seed=81)
+    x = torch.from_numpy(f).cuda()
+    arc = torch.empty(gb.compress_bound(gb.field_dims(x), 1e-4), dtype=torch.uint8, device="cuda")
+    y = torch.empty_like(x)
+    torch.cuda.synchronize()
+    g0 = ctx.debug_copy(gb.DEBUG_GRAPHS_SINGLE, 4, np.uint64)
+    ctx.profile_read()
+    ctx.profile_enable(True)
+    calls = 6
+    try:
+        for _ in range(calls):
+            _, nb = ctx.compress(x, 1e-4, out=arc, stream=s)
+            ctx.decompress(arc, nb, out=y, stream=s)
+        s.synchronize()
+        ms, cnt, launches = ctx.profile_read()
+    finally:
+        ctx.profile_enable(False)
+    g1 = ctx.debug_copy(gb.DEBUG_GRAPHS_SINGLE, 4, np.uint64)
+    assert (g1 - g0)[1] >= 1 and (g1 - g0)[3] >= 1, (g0, g1)  # compress and decompress replayed
+    for i, name in enumerate(gb.STAGES[:10]):
+        assert cnt[i] == calls and ms[i] > 0, (name, cnt[i], ms[i])
+    assert launches > 0
+    oa = ref.compress(f, 1e-4, ref.EB_REL, 512, gb.auto_chunk([f.size]))
+    assert nb == oa.size and np.array_equal(arc[:nb].cpu().numpy(), oa)
+    assert np.array_equal(y.cpu().numpy().view(np.uint32), ref.decompress(oa).view(np.uint32))
