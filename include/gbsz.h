@@ -281,7 +281,9 @@ gbsz_status gbsz_debug_copy(gbsz_ctx *ctx, int which, void *h_dst,
                             size_t bytes);
 
 /* Stage timing.  While enabled, every compress/decompress records CUDA
- * events around each stage on its stream.  gbsz_profile_read synchronises,
+ * events around each stage on its stream; calls replayed as CUDA graphs
+ * record them through the graph's own event nodes, and the call collects
+ * those times after it synchronises.  gbsz_profile_read synchronises,
  * adds up the stage durations recorded since the last read, and returns
  * them with the count of kernel launches.  Stage indices:
  *   0 error bound, 1 dual-quant+histogram, 2 codebook,
