@@ -508,14 +508,14 @@ def main():
     dec_ms = sum(stage_ms[6:10]) / a.steps
     cr = 4.0 * n / nb
 
-    # roofline of the dominant stage (algorithmic bytes)
+    # roofline of the dominant stage (algorithmic bytes per launch, below)
     peaks, peak_kind = read_peaks()
     hbm = float(peaks.get("hbm_gbs", 6800.0))
     m_out = int(np.frombuffer(arc[80:88].cpu().numpy().tobytes(), np.uint64)[0])
     w_words = int(np.frombuffer(arc[96:104].cpu().numpy().tobytes(), np.uint64)[0])
     f = m_out / n
     nc = (n + chunk - 1) // chunk
-    alg = {  # algorithmic bytes per launch of each single-kernel stage (see DESIGN.md, section 6)
+    alg = {  # algorithmic bytes per launch of each single-kernel stage
         0: 4.0 * n,                                               # minmax: read the field
         1: 6.0 * n + 8.0 * m_out,                                 # dual-quant: field in, codes out, residuals
         3: 2.0 * n + n / 32.0 + 4.0 * nc,                         # count: codes in; lane bits, chunk bits out
