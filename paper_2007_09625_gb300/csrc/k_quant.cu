@@ -415,15 +415,28 @@ __global__ void __launch_bounds__(kQ2Threads) k_dualquant_2d(QuantArgs a, uint32
         load_row(y0 - 1, cur, hcur);
         for (int y = y0 - 1; y < y1; y++) {
             if (y + 1 < y1) load_row(y + 1, nxt, hnxt);
+            // the prequant fast path for the row's points; the few it cannot
+            // decide take the full watchdog in a branch the warp rarely enters
             int32_t q[4];
             bool ex[4];
+            uint32_t slow = 0;
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 q[j] = 0;
                 ex[j] = false;
-                if (y >= 0 && inx[j]) q[j] = prequant(cur[j], sc, ex[j]);
-                rows[buf][1 + threadIdx.x + 128 * j] = q[j];
+                if (y >= 0 && inx[j]) {
+                    bool ok;
+                    q[j] = prequant_fast(cur[j], sc, ok);
+                    slow |= (ok ? 0u : 1u) << j;
+                }
             }
+            if (slow) {
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    if (slow & (1u << j)) q[j] = prequant_full(cur[j], sc, ex[j]);
+            }
+#pragma unroll
+            for (int j = 0; j < 4; j++) rows[buf][1 + threadIdx.x + 128 * j] = q[j];
             if (threadIdx.x == 0) {
                 bool dummy;
                 rows[buf][0] = (y >= 0 && x0 > 0) ? prequant(hcur, sc, dummy) : 0;
@@ -528,18 +541,34 @@ __global__ void __launch_bounds__(kQ3Threads) k_dualquant_3d(QuantArgs a, uint32
         uint32_t qprev[4] = {0u, 0u, 0u, 0u}, hprev = 0u;  // integers of the plane before (0 outside)
         for (int z = z0 - 1; z < z1; z++) {
             if (z + 1 < z1) load_plane(z + 1, nxt, hnxt);
-            uint32_t q[4];
+            // the prequant fast path for the plane's points and the halo
+            // point; the few it cannot decide take the full watchdog in a
+            // branch the warp rarely enters
+            uint32_t q[4], hq = 0u, slow = 0;
             bool ex[4];
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 q[j] = 0u;
                 ex[j] = false;
-                if (z >= 0 && inpt[j]) q[j] = (uint32_t)prequant(cur[j], sc, ex[j]);
+                if (z >= 0 && inpt[j]) {
+                    bool ok;
+                    q[j] = (uint32_t)prequant_fast(cur[j], sc, ok);
+                    slow |= (ok ? 0u : 1u) << j;
+                }
             }
-            uint32_t hq = 0u;
             if (z >= 0 && halo_in) {
-                bool dummy;
-                hq = (uint32_t)prequant(hcur, sc, dummy);
+                bool ok;
+                hq = (uint32_t)prequant_fast(hcur, sc, ok);
+                slow |= (ok ? 0u : 1u) << 4;
+            }
+            if (slow) {
+#pragma unroll
+                for (int j = 0; j < 4; j++)
+                    if (slow & (1u << j)) q[j] = (uint32_t)prequant_full(cur[j], sc, ex[j]);
+                if (slow & 16u) {
+                    bool dummy;
+                    hq = (uint32_t)prequant_full(hcur, sc, dummy);
+                }
             }
             if (z >= z0) {
                 const uint32_t mB = (a.lblock && (uint32_t)z % B3 == 0) ? 0u : ~0u;
