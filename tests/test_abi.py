@@ -64,6 +64,19 @@ def test_auto_chunk_rule(lib):
     assert gbsz.auto_chunk([3600, 1800]) == 64
 
 
+def test_bench_chunk_rule_matches_library(lib):
+    """The benchmark restates the rule so that its reference arm runs the same
+    configuration without the library; both must agree for every n."""
+    import sys
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+    rng = np.random.default_rng(5)
+    ns = [1, 63, 64, 155648, 155649, 64 * 155648, 64 * 155648 + 1, 1 << 26, 1 << 28, (1 << 32) - 1]
+    ns += [int(v) for v in rng.integers(1, 1 << 32, 200)]
+    for n in ns:
+        assert bench.workload_chunk(n) == gbsz.auto_chunk([n]), n
+
+
 def test_null_context_and_pointers_rejected(lib):
     nb = C.c_size_t()
     p = gbsz.make_params([10], 1e-3)
