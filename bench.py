@@ -2,7 +2,7 @@
 
 Workload (default): the 1D random walk of 2^28 values (1 GiB) with 1% spikes,
 value-range-relative error bound 1e-4, radius 512 (1024 bins), Huffman
-chunk 4096.  One step = one compress and one decompress of the resident
+chunk by the library's rule (2048 symbols at 2^28).  One step = one compress and one decompress of the resident
 field through the C ABI.  `value` = input bytes of all ranks / (max over
 ranks of the timed K steps), in GB/s (1e9 bytes/s).
 
@@ -39,7 +39,7 @@ def parse():
     ap.add_argument("--log2n", type=int, default=28, help="field size 2^k (default: the 2^28 workload)")
     ap.add_argument("--rel", type=float, default=1e-4)
     ap.add_argument("--radius", type=int, default=512)
-    ap.add_argument("--chunk", type=int, default=0, help="0 = automatic (4096 at 2^28)")
+    ap.add_argument("--chunk", type=int, default=0, help="0 = the library's rule (2048 at 2^28)")
     ap.add_argument("--skip-cpu-baseline", action="store_true")
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--cpu-sample-log2", type=int, default=26)
@@ -230,35 +230,62 @@ def serving(gbsz, workloads, serve, dev, pool_size=32, requests=256, rate=200.0,
 
 
 def other_configs(ctx, gbsz, workloads, dev, reps=5):
-    """The other single-field workloads, compress + decompress of one field
-    each at rel eb 1e-4, radius 512, automatic chunk: 64^3 sinusoids, one
-    1800x3600 power-law field, 512^3 lognormal density."""
+    """The other single-field workloads, compress and decompress of one
+    resident field each, radius 512 unless stated, automatic chunk: 64^3
+    sinusoids and one 1800x3600 power-law field at rel eb 1e-4; 64^3 at chunk
+    4096 as the workload states it; the 512^3 lognormal density at rel eb
+    1e-2, 1e-3, 1e-4 and 1e-5, each at radius 512 and 32768.  Per point:
+    compress and decompress GB/s, compression ratio, max |x - x'| / eb."""
     import torch
-    cases = [("64^3 sinusoids + noise (3D)", lambda: workloads.sinusoids_3d(64, seed=1001)),
-             ("1800x3600 power-law field (2D)", lambda: workloads.grf_2d_batch(nfields=1, seed=1003, masked=(0,))[0]),
-             ("512^3 lognormal density (3D)", lambda: workloads.lognormal_3d(512, seed=1004))]
+    sin64 = lambda: workloads.sinusoids_3d(64, seed=1001)
+    cases = [("64^3 sinusoids + noise (3D)", sin64, 1e-4, 512, 0),
+             ("64^3 sinusoids + noise (3D), chunk 4096", sin64, 1e-4, 512, 4096),
+             ("1800x3600 power-law field (2D)", lambda: workloads.grf_2d_batch(nfields=1, seed=1003, masked=(0,))[0],
+              1e-4, 512, 0)]
+    for R in (512, 32768):
+        for rel in (1e-2, 1e-3, 1e-4, 1e-5):
+            cases.append((f"512^3 lognormal density (3D), rel eb {rel:g}, radius {R}", "lognormal512", rel, R, 0))
     out = []
     stream = torch.cuda.Stream(dev)  # capturable: repeated calls replay as CUDA graphs
-    for name, make in cases:
-        x = torch.from_numpy(make()).to(dev)
-        arc = torch.empty(gbsz.compress_bound(gbsz.field_dims(x), 1e-4), dtype=torch.uint8, device=dev)
+    cache = {}
+    for name, make, rel, R, chunk in cases:
+        if isinstance(make, str):
+            if make not in cache:
+                cache.clear()
+                cache[make] = torch.from_numpy(workloads.lognormal_3d(512, seed=1004)).to(dev)
+            x = cache[make]
+        else:
+            cache.clear()
+            x = torch.from_numpy(make()).to(dev)
+        dims = gbsz.field_dims(x)
+        arc = torch.empty(gbsz.compress_bound(dims, rel, gbsz.EB_REL, R, chunk), dtype=torch.uint8, device=dev)
         y = torch.empty_like(x)
         torch.cuda.synchronize(dev)
         for _ in range(3):
-            _, nb = ctx.compress(x, 1e-4, out=arc, stream=stream)
+            _, nb = ctx.compress(x, rel, gbsz.EB_REL, R, chunk, out=arc, stream=stream)
             ctx.decompress(arc, nb, out=y, stream=stream)
         stream.synchronize()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(3)]
+        ev[0].record(stream)
         for _ in range(reps):
-            ctx.compress(x, 1e-4, out=arc, stream=stream)
+            ctx.compress(x, rel, gbsz.EB_REL, R, chunk, out=arc, stream=stream)
+        ev[1].record(stream)
+        for _ in range(reps):
             ctx.decompress(arc, nb, out=y, stream=stream)
-        e1.record(stream)
+        ev[2].record(stream)
         torch.cuda.synchronize(dev)
-        ms = e0.elapsed_time(e1) / reps
-        out.append({"workload": name, "bytes": x.numel() * 4, "ms_per_step": ms,
-                    "gbs": x.numel() * 4 / (ms / 1e3) / 1e9, "compression_ratio": x.numel() * 4 / nb})
-        del x, y, arc
+        cms, dms = ev[0].elapsed_time(ev[1]) / reps, ev[1].elapsed_time(ev[2]) / reps
+        eb = float(np.frombuffer(arc[56:60].cpu().numpy().tobytes(), np.float32)[0])
+        fin = torch.isfinite(x)
+        err = float((x.double() - y.double()).abs()[fin].max()) / eb
+        gb_ = x.numel() * 4 / 1e9
+        out.append({"workload": name, "bytes": x.numel() * 4, "rel_eb": rel, "radius": R,
+                    "chunk": chunk or gbsz.auto_chunk(dims, R), "ms_per_step": cms + dms,
+                    "gbs": gb_ / ((cms + dms) / 1e3), "compress_gbs": gb_ / (cms / 1e3),
+                    "decompress_gbs": gb_ / (dms / 1e3), "compression_ratio": x.numel() * 4 / nb,
+                    "max_err_over_eb": err})
+        del y, arc
+    cache.clear()
     return out
 
 
@@ -281,9 +308,9 @@ def workload_config(a, n, chunk):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each
-# single-kernel stage on the full 2^28-point walk, from one ncu capture
-# (profiles/dram_walk1d_2e28.md), with a digest of the sources the kernel was
-# built from; a number is reported only while those sources are unchanged.
+# single-kernel stage on the full 2^28-point walk, from one ncu capture, with a
+# digest of the sources the kernel was built from; a number is reported only
+# while those sources are unchanged.
 DRAM_TRAFFIC = {
     "error_bound": (1076764160, ('k_quant.cu', 'common.cuh'), "2718c49ae181230f"),
     "dualquant_hist": (1752118784, ('k_quant.cu', 'common.cuh'), "2718c49ae181230f"),

@@ -298,13 +298,14 @@ gbsz_status gbsz_profile_read(gbsz_ctx *ctx, double *ms, uint64_t *calls,
 
 /* Huffman codebook from a histogram without allocating device memory.  The
  * paper has no counterpart: it exists for callers that cannot call
- * cudaMalloc -- code running during CUDA graph capture, frameworks that own
- * all device memory through their own pool, processes under a fixed memory
- * budget.  It runs the compressor's codebook kernel (S4) with its scratch in
- * a fixed device array that the library defines (sized for 65536 symbols,
- * about 4 MB, held on every GPU that loads the library until exit).
+ * cudaMalloc -- host frameworks that own all device memory through their
+ * own pool and forbid driver allocations, and processes under a fixed
+ * device-memory budget that a library allocating on its own could exceed.
+ * It runs the compressor's codebook kernel (S4) with its scratch in a fixed
+ * device array that the library defines (sized for 65536 symbols, about
+ * 4 MB, held on every GPU that loads the library until exit).
  *   d_hist   device uint32[nbins] symbol frequencies (nbins in [1, 65536];
- *            at least one nonzero)
+ *            at least one nonzero; their total below 2^32)
  *   d_len    device uint8[nbins] out: code lengths (0 = symbol absent)
  *   d_code   device uint64[nbins] out: canonical codewords, right-aligned
  *   maxlen   host out (may be NULL): longest code length
@@ -314,7 +315,8 @@ gbsz_status gbsz_profile_read(gbsz_ctx *ctx, double *ms, uint64_t *calls,
  * calls whose work overlaps on the GPU race, so serialise them.  Synchronises
  * `stream` to report errors.  Allocates nothing (no cudaMalloc, cudaFree or
  * allocating library routine).
- * Errors: INVALID_ARG (bad sizes, NULL, all-zero histogram), CUDA. */
+ * Errors: INVALID_ARG (bad sizes, NULL, all-zero histogram, total of the
+ * frequencies >= 2^32), CUDA. */
 gbsz_status gbsz_codebook_noalloc(const uint32_t *d_hist, uint32_t nbins,
                                   uint8_t *d_len, uint64_t *d_code,
                                   uint32_t *maxlen, void *stream);

@@ -51,7 +51,8 @@ __host__ __device__ inline Layout make_layout(uint32_t radius, uint64_t nchunk, 
 
 // device status bits (Control::error)
 enum : uint32_t {
-    DERR_CAPACITY = 1u, DERR_CORRUPT = 2u, DERR_TIMEOUT = 4u, DERR_EB = 8u, DERR_INTERNAL = 16u
+    DERR_CAPACITY = 1u, DERR_CORRUPT = 2u, DERR_TIMEOUT = 4u, DERR_EB = 8u, DERR_INTERNAL = 16u,
+    DERR_RANGE = 32u  // an input outside what the kernel supports (codebook: histogram total >= 2^32)
 };
 
 // Per-call device control block.  Zeroed by one memset at the start of each
@@ -65,7 +66,6 @@ struct Control {
     uint32_t maxlen;
     unsigned long long n_out;  // outliers (code 0), counted by the dual-quant kernel
     unsigned long long n_exc;  // verbatim exceptions
-    uint32_t ticket;           // unused (kept for layout stability)
     uint32_t nsym;             // codebook: symbols with nonzero frequency
     unsigned long long words;  // encode: total stream words
     unsigned long long total;  // encode: archive bytes

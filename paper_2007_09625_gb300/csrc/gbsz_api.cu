@@ -313,7 +313,7 @@ gbsz_status map_device_error(uint32_t e)
 {
     if (e & DERR_INTERNAL) return GBSZ_ERR_CUDA;
     if (e & DERR_TIMEOUT) return GBSZ_ERR_TIMEOUT;
-    if (e & DERR_EB) return GBSZ_ERR_INVALID_ARG;
+    if (e & (DERR_EB | DERR_RANGE)) return GBSZ_ERR_INVALID_ARG;
     if (e & DERR_CORRUPT) return GBSZ_ERR_CORRUPT;
     if (e & DERR_CAPACITY) return GBSZ_ERR_CAPACITY;
     return GBSZ_OK;

@@ -17,6 +17,8 @@
 // len << 56 | code in 64 bits always (the paper's adaptive representation).
 #include "common.cuh"
 
+#include <atomic>
+
 namespace gbsz {
 
 namespace {
@@ -24,7 +26,6 @@ namespace {
 // one CTA of 1024 threads (measured against 256 and 512: the codebook kernel
 // is within 10% for every bin count, the decoder tables are fastest here)
 constexpr int kCbThreads = 1024;
-constexpr uint32_t kRankSortMax = 0;     // rank sort unused; bitonic covers small n
 constexpr uint32_t kBitonicMax = 8192;    // 8192 keys = 64 KB of shared memory
 // merge state (4k words) in shared memory up to this many used symbols, and
 // the pointer-jumping buffers too (12k words in all) up to kDepthSmemMax
@@ -66,26 +67,6 @@ __device__ unsigned long long *cta_sort(unsigned long long *a, unsigned long lon
             }
         }
         for (uint32_t i = t; i < n; i += T) b[i] = sk[i];
-        __syncthreads();
-        return b;
-    }
-    if (n <= kRankSortMax) {
-        // rank sort through shared memory: rank = number of smaller keys
-        unsigned long long *sk = reinterpret_cast<unsigned long long *>(s_cnt);
-        const unsigned long long mask =
-            (bit_hi >= 64 ? ~0ull : ((1ull << bit_hi) - 1)) & ~((1ull << bit_lo) - 1);
-        for (uint32_t i = t; i < n; i += T) sk[i] = a[i];
-        __syncthreads();
-        for (uint32_t i = t; i < n; i += T) {
-            const unsigned long long ki = sk[i];
-            const unsigned long long mi = ki & mask;
-            uint32_t r = 0;
-            for (uint32_t j = 0; j < n; j++) {
-                const unsigned long long mj = sk[j] & mask;
-                r += (mj < mi) || (mj == mi && j < i);
-            }
-            b[r] = ki;
-        }
         __syncthreads();
         return b;
     }
@@ -292,20 +273,31 @@ __global__ void __launch_bounds__(kCbThreads, 1) k_codebook(CodebookArgs a)
     extern __shared__ uint32_t s_cnt[];  // 16 * kCbThreads words
     __shared__ Canon canon;
     __shared__ uint32_t s_scan[33];
+    __shared__ unsigned long long s_scan64[33];
     const uint32_t T = blockDim.x, t = threadIdx.x, nbins = a.nbins;
 
     // symbols with nonzero frequency, keys (freq << 16 | sym) in symbol order
     const uint32_t per = (nbins + T - 1) / T;
     const uint32_t lo = min(nbins, t * per), hi = min(nbins, lo + per);
     uint32_t c = 0, fmax = 0;
+    unsigned long long ftot = 0;
     for (uint32_t s = lo; s < hi; s++) {
         const uint32_t f = a.hist[s];
         c += f > 0;
         fmax = max(fmax, f);
+        ftot += f;
     }
     uint32_t k;
     uint32_t pos = block_excl_scan(c, s_scan, &k);
     fmax = block_max(fmax, s_scan);
+    // the merge adds frequencies in 32 bits: a histogram whose total reaches
+    // 2^32 is refused (the compressor's fields have fewer than 2^32 points)
+    unsigned long long total;
+    block_excl_scan64(ftot, s_scan64, &total);
+    if (total >= (1ull << 32)) {
+        if (t == 0) atomicOr(&a.ctl->error, DERR_RANGE);
+        return;
+    }
     for (uint32_t s = lo; s < hi; s++) {
         const uint32_t f = a.hist[s];
         if (f) a.keyA[pos++] = ((unsigned long long)f << 16) | s;
@@ -482,16 +474,18 @@ __global__ void __launch_bounds__(kCbThreads, 1) k_decode_tables(CodebookArgs a)
 constexpr size_t kCbSmem = 16 * 1024 * sizeof(uint32_t);  // 8192 sort keys; 16 digit counters per thread
 
 // opt in to more than 48 KB of dynamic shared memory, once per device
+// (host threads may race here: the bits are atomic, and setting an attribute
+// twice is harmless)
 void set_smem_attributes()
 {
-    static unsigned long long done = 0;  // one bit per device id < 64
+    static std::atomic<unsigned long long> done{0};  // one bit per device id < 64
     int dev = 0;
     cudaGetDevice(&dev);
     const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0;
-    if (bit && (done & bit)) return;
+    if (bit && (done.load() & bit)) return;
     cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem);
     cudaFuncSetAttribute(k_decode_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem);
-    done |= bit;
+    done.fetch_or(bit);
 }
 
 }  // namespace

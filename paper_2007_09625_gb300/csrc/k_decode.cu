@@ -20,6 +20,7 @@
 #include "scan.cuh"
 
 #include <algorithm>
+#include <atomic>
 
 namespace gbsz {
 
@@ -549,21 +550,23 @@ int launch_decode(const DecodeArgs &a, cudaStream_t st, int phase)
     const uint32_t nb = 2 * a.radius;
     const uint32_t in_smem = nb <= kSortedSmemMax ? nb : 0u;
     const size_t dyn = (size_t)kDecThreads * kRing * 4 + in_smem * sizeof(uint16_t);
-    static unsigned long long attr_done = 0;  // one bit per device id < 64
+    // host threads may race here: the state is atomic, and setting an
+    // attribute or querying the occupancy twice is harmless
+    static std::atomic<unsigned long long> attr_done{0};  // one bit per device id < 64
     // k_decode blocks resident per SM, by device, MULTI_TILE and the sorted
     // table's size in shared memory (steps of 512 symbols); 0: not queried yet
-    static int resident[64][2][kSortedSmemMax / 512 + 1];
+    static std::atomic<int> resident[64][2][kSortedSmemMax / 512 + 1];
     int dev = 0;
     cudaGetDevice(&dev);
     const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0;
-    if (!bit || !(attr_done & bit)) {
+    if (!bit || !(attr_done.load() & bit)) {
         const int most = (int)(kDecThreads * kRing * 4 + kSortedSmemMax * sizeof(uint16_t));
         cudaFuncSetAttribute(k_decode<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         cudaFuncSetAttribute(k_decode<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
         const int most_fast = (int)(kDecFastThreads * kRingFast * 4 + 8u * kL1Copies * (1u << kL1Bits));
         cudaFuncSetAttribute(k_decode_fast<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
         cudaFuncSetAttribute(k_decode_fast<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
-        attr_done |= bit;
+        attr_done.fetch_or(bit);
     }
     const bool multi = a.chunk > kRecon1DTile;
     if (a.fast_bits) {
@@ -578,8 +581,8 @@ int launch_decode(const DecodeArgs &a, cudaStream_t st, int phase)
         const uint32_t qb = (in_smem + 511) / 512;
         int per_sm = 1;
         if (bit) {
-            int &r = resident[dev][multi ? 1 : 0][qb];
-            if (r == 0) {
+            std::atomic<int> &r = resident[dev][multi ? 1 : 0][qb];
+            if (r.load() == 0) {
                 const size_t dq = (size_t)kDecThreads * kRing * 4 + (size_t)qb * 512 * sizeof(uint16_t);
                 int blocks = 0;
                 const cudaError_t e =
@@ -589,9 +592,9 @@ int launch_decode(const DecodeArgs &a, cudaStream_t st, int phase)
                     cudaGetLastError();
                     blocks = 0;
                 }
-                r = blocks > 0 ? blocks : 1;
+                r.store(blocks > 0 ? blocks : 1);
             }
-            per_sm = r;
+            per_sm = r.load();
         }
         const unsigned g = (unsigned)std::min<uint64_t>(ntask, (uint64_t)(a.num_sms ? a.num_sms : 1) * per_sm);
         if (multi) k_decode<true><<<g, kDecThreads, dyn, st>>>(a, in_smem);

@@ -24,6 +24,8 @@
 // point; it is read only where there are outliers (exception flags only when
 // the field has exceptions at all), and the field only for exceptions.
 #include "common.cuh"
+
+#include <atomic>
 #include "scan.cuh"
 
 #include <algorithm>
@@ -660,18 +662,20 @@ struct UnitOp {
 };
 
 // opt in to the dynamic shared memory the kernels need, once per device
+// (host threads may race here: the bits are atomic, and setting an attribute
+// twice is harmless)
 void set_encode_smem()
 {
-    static unsigned long long done = 0;  // one bit per device id < 64
+    static std::atomic<unsigned long long> done{0};  // one bit per device id < 64
     int dev = 0;
     cudaGetDevice(&dev);
     const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0;
-    if (bit && (done & bit)) return;
+    if (bit && (done.load() & bit)) return;
     const size_t most = (size_t)kWarps * kRound * 2 + 4096 * 8;
     cudaFuncSetAttribute(k_encode_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
     cudaFuncSetAttribute(k_encode_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)((kWarps * kPartWords + kCountSmemBins) * 4));
-    done |= bit;
+    done.fetch_or(bit);
 }
 
 }  // namespace

@@ -1,12 +1,12 @@
 // noalloc.cu -- gbsz_codebook_noalloc: the Huffman codebook kernel (S4) for
 // callers that must not allocate device memory.
 //
-// Some callers cannot call cudaMalloc: code that runs while a CUDA graph is
-// being captured (allocation is not a capturable operation), host frameworks
-// that own all device memory through their own pool and forbid driver
-// allocations, and processes under a fixed device-memory budget.  For them,
-// this entry point runs the same codebook kernel as the compressor, with all
-// of its scratch in one file-scope device array of fixed size instead of a
+// Some callers cannot call cudaMalloc: host frameworks that own all device
+// memory through their own pool and forbid driver allocations behind their
+// back, and processes that run under a fixed device-memory budget where a
+// library allocating on its own could push them over it.  For them, this
+// entry point runs the same codebook kernel as the compressor, with all of
+// its scratch in one file-scope device array of fixed size instead of a
 // context's allocations.
 //
 // The array is sized for the largest alphabet the format allows (65536
@@ -14,6 +14,8 @@
 // the process exits.  Every call shares it and it keeps the last call's
 // contents, so two calls whose kernels overlap on the GPU race: serialise
 // them (one stream, or events).  The control block is cleared on every call.
+// The call reads its status back and synchronises its stream before it
+// returns.
 #include "../../include/gbsz.h"
 #include "common.cuh"
 

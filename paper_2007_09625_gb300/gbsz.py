@@ -346,14 +346,19 @@ def auto_chunk(dims, radius=512):
     return load().gbsz_auto_chunk(C.byref(make_params(dims, 1e-4, EB_REL, radius, 0)))
 
 
-def codebook_noalloc(hist, stream=None):
+def codebook_noalloc(hist, stream=None, out=None):
     """Code lengths and canonical codewords from a device histogram, through
     the entry point that allocates no device memory (see gbsz.h).  The output
-    tensors are allocated here by torch; the library allocates nothing."""
+    tensors are allocated here by torch unless `out` = (lengths, codewords,
+    ...) from an earlier call is given; the library allocates nothing."""
     assert hist.is_cuda and hist.dtype == torch.int32 and hist.is_contiguous()
     nb = hist.numel()
-    ln = torch.empty(nb, dtype=torch.uint8, device=hist.device)
-    code = torch.empty(nb, dtype=torch.int64, device=hist.device)
+    if out is not None:
+        ln, code = out[0], out[1]
+        assert ln.numel() == nb and code.numel() == nb and ln.dtype == torch.uint8 and code.dtype == torch.int64
+    else:
+        ln = torch.empty(nb, dtype=torch.uint8, device=hist.device)
+        code = torch.empty(nb, dtype=torch.int64, device=hist.device)
     mx = C.c_uint32()
     st = load().gbsz_codebook_noalloc(C.c_void_p(hist.data_ptr()), nb, C.c_void_p(ln.data_ptr()),
                                       C.c_void_p(code.data_ptr()), C.byref(mx), _stream(stream))

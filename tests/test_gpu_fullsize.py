@@ -4,8 +4,8 @@ the oracle byte for byte, in the launch configuration the benchmark uses
 
 Sizes: 64^3 sinusoids; 2^28 random walk with 1% spikes (the benchmark
 workload), also in the per-block Lorenzo mode; one 1800x3600 power-law field
-at rel 1e-3 and 1e-4; 512^3 lognormal at radius 512 and 32768, and with the
-order-2 predictor; a field of the paper's 4D QMCPACK shape 288x115x69x69.  The oracle runs multi-threaded where
+at rel 1e-3 and 1e-4; 512^3 lognormal at rel 1e-2, 1e-3, 1e-4 and 1e-5, each
+at radius 512 and 32768, and with the order-2 predictor; a field of the paper's 4D QMCPACK shape 288x115x69x69.  The oracle runs multi-threaded where
 its loops allow; these tests take a few minutes.
 """
 import numpy as np
@@ -69,10 +69,16 @@ def test_grf_1800x3600(gb, ctx, rel):
     roundtrip_vs_oracle(gb, ctx, x, rel, 512)
 
 
+@pytest.fixture(scope="module")
+def lognormal512():
+    return workloads.lognormal_3d(512, seed=1004)
+
+
+# the 512^3 error-bound sweep: relative eb 1e-2 .. 1e-5 at 1024 and 65536 bins
 @pytest.mark.parametrize("R", [512, 32768])
-def test_lognormal_512cubed(gb, ctx, R):
-    x = workloads.lognormal_3d(512, seed=1004)
-    roundtrip_vs_oracle(gb, ctx, x, 1e-4, R)
+@pytest.mark.parametrize("rel", [1e-2, 1e-3, 1e-4, 1e-5])
+def test_lognormal_512cubed(gb, ctx, lognormal512, rel, R):
+    roundtrip_vs_oracle(gb, ctx, lognormal512, rel, R)
 
 
 def test_random_walk_2p28_per_block(gb, ctx):
@@ -80,9 +86,8 @@ def test_random_walk_2p28_per_block(gb, ctx):
     roundtrip_vs_oracle(gb, ctx, x, 1e-4, 512, lblock=1)
 
 
-def test_lognormal_512cubed_order2(gb, ctx):
-    x = workloads.lognormal_3d(512, seed=1004)
-    roundtrip_vs_oracle(gb, ctx, x, 1e-4, 512, order=2)
+def test_lognormal_512cubed_order2(gb, ctx, lognormal512):
+    roundtrip_vs_oracle(gb, ctx, lognormal512, 1e-4, 512, order=2)
 
 
 def test_qmcpack_shape_4d(gb, ctx):

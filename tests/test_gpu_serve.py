@@ -1,13 +1,15 @@
 """The serving loop on the GPU: a stream of mixed compress / decompress
 requests arriving while others run gives, for every request, exactly the
-bytes (archives) and floats (reconstructions) that the same request gives
-alone.  Integer / bit-exact results, so the tolerance is equality."""
+bytes (archives) and floats (reconstructions) that the oracle gives for the
+same input, and that the same request gives alone.  Integer / bit-exact
+results, so the tolerance is equality."""
 import time
 
 import numpy as np
 import pytest
 import torch
 
+from oracle import ref
 from paper_2007_09625_gb300 import serve, workloads
 
 pytestmark = pytest.mark.gpu
@@ -38,6 +40,12 @@ def test_mixed_stream_matches_alone(gb):
         a, nb = alone.compress(torch.from_numpy(f).cuda(), rels[i % 3])
         ref_arcs.append((a[:nb].clone(), nb))
         ref_out.append(alone.decompress(a, nb).cpu().numpy())
+        # the oracle's archive and reconstruction for the same request
+        chunk = gb.auto_chunk(list(f.shape)[::-1], 512)
+        oa = ref.compress(f, rels[i % 3], ref.EB_REL, radius=512, chunk=chunk, omp=True)
+        assert nb == oa.size and np.array_equal(a[:nb].cpu().numpy(), oa), i
+        yo = ref.decompress(oa, omp=True)
+        assert np.array_equal(ref_out[-1].view(np.uint32), yo.view(np.uint32)), i
     torch.cuda.synchronize()
 
     srv = serve.Server(workers=2, max_batch=4, mem_budget=2 << 30).start()
@@ -65,7 +73,6 @@ def test_mixed_stream_matches_alone(gb):
 
 
 def test_server_reports_per_request_errors_and_budget(gb):
-    from oracle import ref
     x = torch.from_numpy(workloads.field_for("walk", (300001,), seed=5)).cuda()
     alone = gb.Context(0)
     a, nb = alone.compress(x, 1e-4)
