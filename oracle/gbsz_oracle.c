@@ -44,14 +44,31 @@
  * when they are far apart the difference exceeds eb by orders of magnitude.
  *
  * Build: gcc -O2 -std=c11 -ffp-contract=off (no fast-math).  An OpenMP build
- * of the same file parallelises only the element-wise loops marked below and
- * yields identical bytes.
+ * of the same file is the multi-core CPU baseline: it runs the element-wise
+ * loops marked below in parallel, and replaces the serial loops over chunks,
+ * over the outlier list and over the reconstruction cascade with the
+ * restatements in the "OpenMP build" section (each computes the same values
+ * and statuses in independent pieces).  Both builds yield identical bytes;
+ * the single-threaded build never compiles that section.
  */
 #include "gbsz_oracle.h"
 
 #include <math.h>
 #include <stdlib.h>
 #include <string.h>
+
+#ifdef _OPENMP
+#include <omp.h>
+/* the OpenMP build's restatements of serial steps (defined with S7 below) */
+static void par_minmax(const float *x, uint64_t n, int *any_out, float *lo_out, float *hi_out);
+static void par_postquant(const float *x, const int32_t *delta, const uint8_t *exc, uint64_t n,
+                          uint32_t radius, uint16_t *codes, uint32_t *out_idx, int32_t *out_delta,
+                          uint64_t *m, uint32_t *exc_idx, uint32_t *exc_raw, uint64_t *e);
+static int par_histogram(const uint16_t *codes, uint64_t n, uint32_t nbins, uint32_t *hist);
+static int par_deflate(const uint16_t *codes, uint64_t n, uint32_t chunk, const uint8_t *len,
+                       const uint64_t *code, uint32_t *bits, uint32_t *stream, uint64_t stream_cap,
+                       uint64_t *words);
+#endif
 
 /* ------------------------------------------------------------------------ */
 /* archive layout (little-endian), written out independently of the CUDA side */
@@ -128,12 +145,16 @@ int gbsz_ref_error_bound(const float *x, uint64_t n, uint32_t eb_mode,
     if (eb_mode == REF_EB_REL) {
         int any = 0;
         float lo = 0.0f, hi = 0.0f;
+#ifdef _OPENMP
+        par_minmax(x, n, &any, &lo, &hi);
+#else
         for (uint64_t i = 0; i < n; i++) {
             if (!isfinite(x[i])) continue;
             if (!any) { lo = hi = x[i]; any = 1; }
             if (x[i] < lo) lo = x[i];
             if (x[i] > hi) hi = x[i];
         }
+#endif
         double range = (double)hi - (double)lo;
         if (!any || range == 0.0) e = (float)eb;
         else e = (float)(eb * range);
@@ -259,14 +280,19 @@ int gbsz_ref_lorenzo_delta_blocked(const int32_t *q, uint32_t ndim,
     if (ndim < 1 || ndim > 3 || order < 1 || order > 4 || lblock > 1) return REF_ERR_INVALID_ARG;
     uint64_t d[3] = {1, 1, 1};
     for (uint32_t i = 0; i < ndim; i++) d[i] = dims[i];
-#pragma omp parallel for
-    for (int64_t zz = 0; zz < (int64_t)d[2]; zz++) {
-        uint64_t z = (uint64_t)zz;
-        for (uint64_t y = 0; y < d[1]; y++)
-            for (uint64_t x = 0; x < d[0]; x++) {
-                uint64_t i = x + d[0] * (y + d[1] * z);
-                delta[i] = (int32_t)((uint32_t)q[i] - lorenzo_predict(q, d, ndim, order, lblock, x, y, z));
-            }
+    /* every residual reads only q: rows (or, in 1D, runs of 65536 points)
+     * are independent */
+    const uint64_t rows = d[1] * d[2], run = 65536;
+    const int64_t parts = rows > 1 ? (int64_t)rows : (int64_t)((d[0] + run - 1) / run);
+#pragma omp parallel for schedule(static)
+    for (int64_t r = 0; r < parts; r++) {
+        const uint64_t y = rows > 1 ? (uint64_t)r % d[1] : 0, z = rows > 1 ? (uint64_t)r / d[1] : 0;
+        const uint64_t x0 = rows > 1 ? 0 : (uint64_t)r * run;
+        const uint64_t x1 = rows > 1 ? d[0] : (x0 + run < d[0] ? x0 + run : d[0]);
+        for (uint64_t x = x0; x < x1; x++) {
+            uint64_t i = x + d[0] * (y + d[1] * z);
+            delta[i] = (int32_t)((uint32_t)q[i] - lorenzo_predict(q, d, ndim, order, lblock, x, y, z));
+        }
     }
     return REF_OK;
 }
@@ -305,6 +331,9 @@ int gbsz_ref_dualquant_ex(const float *x, uint32_t ndim,
     /* prediction on the prequantized integers, then postquant */
     gbsz_ref_lorenzo_delta_blocked(q, ndim, dims, order, lblock, delta);
     uint64_t nm = 0, ne = 0;
+#ifdef _OPENMP
+    par_postquant(x, delta, exc, n, radius, codes, out_idx, out_delta, &nm, exc_idx, exc_raw, &ne);
+#else
     for (uint64_t i = 0; i < n; i++) {
         int32_t dl = delta[i];
         int in_cap = dl > -(int32_t)radius && dl < (int32_t)radius;
@@ -324,6 +353,7 @@ int gbsz_ref_dualquant_ex(const float *x, uint32_t ndim,
             ne++;
         }
     }
+#endif
     *m = nm;
     *e = ne;
     if (q_keep) memcpy(q_keep, q, n * sizeof(int32_t));
@@ -348,6 +378,9 @@ int gbsz_ref_histogram(const uint16_t *codes, uint64_t n, uint32_t nbins,
                        uint32_t *hist)
 {
     memset(hist, 0, nbins * sizeof(uint32_t));
+#ifdef _OPENMP
+    return par_histogram(codes, n, nbins, hist);
+#endif
     for (uint64_t i = 0; i < n; i++) {
         if (codes[i] >= nbins) return REF_ERR_INVALID_ARG;
         hist[codes[i]]++;
@@ -461,6 +494,9 @@ int gbsz_ref_deflate(const uint16_t *codes, uint64_t n, uint32_t chunk,
                      uint32_t *bits, uint32_t *stream, uint64_t stream_cap,
                      uint64_t *words)
 {
+#ifdef _OPENMP
+    return par_deflate(codes, n, chunk, len, code, bits, stream, stream_cap, words);
+#endif
     uint64_t nc = nchunks(n, chunk);
     uint64_t w = 0;
     for (uint64_t c = 0; c < nc; c++) {
@@ -522,6 +558,346 @@ static int revbook_build(const uint8_t *len, uint32_t nbins, revbook_t *rb)
     return REF_OK;
 }
 
+/* ------------------------------------------------------------------------ */
+/* OpenMP build: serial steps restated in independent pieces               */
+/*
+ * Compiled only with -fopenmp.  Each function computes exactly what the
+ * serial loop it replaces computes (same values, same status), splitting the
+ * work where the step itself has independent parts:
+ *   par_minmax     S0: min / max of finite values, per range, then merged
+ *                  (min and max do not depend on the order);
+ *   par_postquant  S2: codes per range, then each range writes its outliers
+ *                  and exceptions at offsets from a prefix sum of the counts
+ *                  (index order is kept);
+ *   par_histogram  S3: per-thread histograms added together;
+ *   par_deflate    S5: bits of every chunk, word offsets by a prefix sum,
+ *                  then every chunk packs its own words (chunks are
+ *                  independent by construction of the format);
+ *   par_inflate    S7: word offsets by a prefix sum, then every chunk decodes
+ *                  on its own;
+ *   par_cascade    S8: the cascade of Algorithm 2, each point predicted from
+ *                  points already rebuilt, but in an order that lets threads
+ *                  work at once: blocks of the per-block mode are
+ *                  independent; a 1D field's order-1 cascade restarts every
+ *                  range from the prefix sum of the residuals before it
+ *                  (q[i-1] is exactly that sum); 2D and 3D fields go in
+ *                  wavefronts of rows (3D: row (y, z) needs only rows of
+ *                  smaller y + z) or of row pieces (2D: piece (b, y) needs
+ *                  only pieces of smaller b + y).
+ */
+#ifdef _OPENMP
+static void par_minmax(const float *x, uint64_t n, int *any_out, float *lo_out, float *hi_out)
+{
+    int any = 0;
+    float lo = 0.0f, hi = 0.0f;
+#pragma omp parallel
+    {
+        int a = 0;
+        float l = 0.0f, h = 0.0f;
+#pragma omp for schedule(static) nowait
+        for (int64_t i = 0; i < (int64_t)n; i++) {
+            if (!isfinite(x[i])) continue;
+            if (!a) { l = h = x[i]; a = 1; }
+            if (x[i] < l) l = x[i];
+            if (x[i] > h) h = x[i];
+        }
+#pragma omp critical
+        if (a) {
+            if (!any) { lo = l; hi = h; any = 1; }
+            if (l < lo) lo = l;
+            if (h > hi) hi = h;
+        }
+    }
+    *any_out = any;
+    *lo_out = lo;
+    *hi_out = hi;
+}
+
+/* index ranges for the two-pass steps: about 64k points each */
+static uint64_t par_parts(uint64_t n) { return n / 65536 + 1; }
+static uint64_t part_lo(uint64_t n, uint64_t p, uint64_t parts) { return n * p / parts; }
+
+static void par_postquant(const float *x, const int32_t *delta, const uint8_t *exc, uint64_t n,
+                          uint32_t radius, uint16_t *codes, uint32_t *out_idx, int32_t *out_delta,
+                          uint64_t *m, uint32_t *exc_idx, uint32_t *exc_raw, uint64_t *e)
+{
+    const uint64_t P = par_parts(n);
+    uint64_t *cm = (uint64_t *)calloc(P + 1, sizeof(uint64_t));
+    uint64_t *ce = (uint64_t *)calloc(P + 1, sizeof(uint64_t));
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < (int64_t)P; p++) {
+        uint64_t nm = 0, ne = 0;
+        for (uint64_t i = part_lo(n, p, P); i < part_lo(n, p + 1, P); i++) {
+            int32_t dl = delta[i];
+            int in_cap = dl > -(int32_t)radius && dl < (int32_t)radius;
+            codes[i] = (in_cap && !exc[i]) ? (uint16_t)(dl + (int32_t)radius) : 0;
+            nm += codes[i] == 0;
+            ne += exc[i] != 0;
+        }
+        cm[p + 1] = nm;
+        ce[p + 1] = ne;
+    }
+    for (uint64_t p = 0; p < P; p++) {
+        cm[p + 1] += cm[p];
+        ce[p + 1] += ce[p];
+    }
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < (int64_t)P; p++) {
+        uint64_t nm = cm[p], ne = ce[p];
+        for (uint64_t i = part_lo(n, p, P); i < part_lo(n, p + 1, P); i++) {
+            if (codes[i] == 0) {
+                out_idx[nm] = (uint32_t)i;
+                out_delta[nm] = delta[i];
+                nm++;
+            }
+            if (exc[i]) {
+                uint32_t raw;
+                memcpy(&raw, &x[i], 4);
+                exc_idx[ne] = (uint32_t)i;
+                exc_raw[ne] = raw;
+                ne++;
+            }
+        }
+    }
+    *m = cm[P];
+    *e = ce[P];
+    free(cm);
+    free(ce);
+}
+
+static int par_histogram(const uint16_t *codes, uint64_t n, uint32_t nbins, uint32_t *hist)
+{
+    int bad = 0;
+#pragma omp parallel reduction(| : bad)
+    {
+        uint32_t *h = (uint32_t *)calloc(nbins, sizeof(uint32_t));
+        if (!h) bad = 2;
+#pragma omp for schedule(static)
+        for (int64_t i = 0; i < (int64_t)n; i++) {
+            if (!h) continue;
+            if (codes[i] >= nbins) bad = 1;
+            else h[codes[i]]++;
+        }
+        if (h) {
+#pragma omp critical
+            for (uint32_t s = 0; s < nbins; s++) hist[s] += h[s];
+        }
+        free(h);
+    }
+    return bad & 2 ? REF_ERR_OOM : bad ? REF_ERR_INVALID_ARG : REF_OK;
+}
+
+static int par_deflate(const uint16_t *codes, uint64_t n, uint32_t chunk, const uint8_t *len,
+                       const uint64_t *code, uint32_t *bits, uint32_t *stream, uint64_t stream_cap,
+                       uint64_t *words)
+{
+    const uint64_t nc = nchunks(n, chunk);
+    uint64_t *cb = (uint64_t *)malloc(nc * sizeof(uint64_t)); /* bits, or bits before an absent symbol */
+    uint64_t *off = (uint64_t *)malloc(nc * sizeof(uint64_t));
+    uint8_t *absent = (uint8_t *)malloc(nc);
+    if (!cb || !off || !absent) {
+        free(cb); free(off); free(absent);
+        return REF_ERR_OOM;
+    }
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t c = 0; c < (int64_t)nc; c++) {
+        uint64_t lo = (uint64_t)c * chunk, hi = lo + chunk < n ? lo + chunk : n, pos = 0;
+        absent[c] = 0;
+        for (uint64_t i = lo; i < hi; i++) {
+            if (len[codes[i]] == 0) { absent[c] = 1; break; }
+            pos += len[codes[i]];
+        }
+        cb[c] = pos;
+    }
+    /* statuses in the order the serial loop meets them: a bit past the
+     * capacity, or a symbol without a code, whichever comes first */
+    uint64_t w = 0;
+    int st = REF_OK;
+    for (uint64_t c = 0; c < nc && st == REF_OK; c++) {
+        if (cb[c] > 0 && w + (cb[c] - 1) / 32 >= stream_cap) st = REF_ERR_CAPACITY;
+        else if (absent[c]) st = REF_ERR_INVALID_ARG;
+        off[c] = w;
+        w += (cb[c] + 31) / 32;
+    }
+    if (st == REF_OK) {
+#pragma omp parallel for schedule(dynamic, 64)
+        for (int64_t c = 0; c < (int64_t)nc; c++) {
+            uint64_t lo = (uint64_t)c * chunk, hi = lo + chunk < n ? lo + chunk : n, pos = 0;
+            for (uint64_t i = lo; i < hi; i++) {
+                uint32_t l = len[codes[i]];
+                for (int b = (int)l - 1; b >= 0; b--) { /* MSB first */
+                    uint64_t word = off[c] + pos / 32;
+                    if (pos % 32 == 0) stream[word] = 0;
+                    if ((code[codes[i]] >> b) & 1u) stream[word] |= 1u << (31 - pos % 32);
+                    pos++;
+                }
+            }
+            bits[c] = (uint32_t)pos;
+        }
+        *words = w;
+    }
+    free(cb); free(off); free(absent);
+    return st;
+}
+
+static int par_inflate(const uint32_t *stream, uint64_t words, const uint32_t *bits, uint64_t n,
+                       uint32_t chunk, const revbook_t *rb, uint16_t *codes)
+{
+    const uint64_t nc = nchunks(n, chunk);
+    uint64_t *off = (uint64_t *)malloc(nc * sizeof(uint64_t) + 8);
+    if (!off) return REF_ERR_OOM;
+    uint64_t w = 0;
+    int st = REF_OK;
+    for (uint64_t c = 0; c < nc; c++) {
+        off[c] = w;
+        w += ((uint64_t)bits[c] + 31) / 32;
+        if (w > words) { st = REF_ERR_CORRUPT; break; }
+    }
+    if (st == REF_OK) {
+        int bad = 0;
+#pragma omp parallel for schedule(dynamic, 64) reduction(| : bad)
+        for (int64_t c = 0; c < (int64_t)nc; c++) {
+            uint64_t lo = (uint64_t)c * chunk, hi = lo + chunk < n ? lo + chunk : n;
+            uint64_t nb = bits[c], pos = 0;
+            int ok = 1;
+            for (uint64_t i = lo; i < hi && ok; i++) {
+                uint64_t v = 0;
+                uint32_t l = 0;
+                for (;;) {
+                    if (pos >= nb || l >= rb->maxlen) { ok = 0; break; }
+                    uint32_t bit = (stream[off[c] + pos / 32] >> (31 - pos % 32)) & 1u;
+                    v = (v << 1) | bit;
+                    pos++;
+                    l++;
+                    if (v - rb->first[l] < rb->count[l]) {
+                        codes[i] = (uint16_t)rb->sorted[rb->start[l] + (uint32_t)(v - rb->first[l])];
+                        break;
+                    }
+                }
+            }
+            if (!ok || pos != nb) bad = 1;
+        }
+        if (bad) st = REF_ERR_CORRUPT;
+    }
+    free(off);
+    return st;
+}
+
+/* one point of the cascade: q = p + delta (mod 2^32) */
+static void cascade_point(int32_t *q, const int32_t *dl, const uint64_t d[3], uint32_t ndim, uint32_t order,
+                          uint32_t lblock, uint64_t x, uint64_t y, uint64_t z)
+{
+    const uint64_t i = x + d[0] * (y + d[1] * z);
+    q[i] = (int32_t)(lorenzo_predict(q, d, ndim, order, lblock, x, y, z) + (uint32_t)dl[i]);
+}
+
+static int par_cascade(const uint16_t *codes, uint32_t ndim, const uint64_t d[3], uint32_t radius,
+                       uint32_t lblock, uint32_t order, const uint32_t *out_idx, const int32_t *out_delta,
+                       uint64_t m, int32_t *q)
+{
+    const uint64_t n = d[0] * d[1] * d[2];
+    const uint64_t P = par_parts(n);
+    int32_t *dl = (int32_t *)malloc(n * sizeof(int32_t) + 4);
+    uint64_t *cz = (uint64_t *)calloc(P + 1, sizeof(uint64_t));
+    if (!dl || !cz) {
+        free(dl); free(cz);
+        return REF_ERR_OOM;
+    }
+    /* The serial loop takes the outliers in index order: the r-th code-0
+     * point takes entry r.  It succeeds exactly when there are m code-0
+     * points and entry r names the r-th of them (then no entry can name a
+     * point whose code is not 0). */
+#pragma omp parallel for schedule(static)
+    for (int64_t p = 0; p < (int64_t)P; p++) {
+        uint64_t z0 = 0;
+        for (uint64_t i = part_lo(n, p, P); i < part_lo(n, p + 1, P); i++) z0 += codes[i] == 0;
+        cz[p + 1] = z0;
+    }
+    for (uint64_t p = 0; p < P; p++) cz[p + 1] += cz[p];
+    int bad = cz[P] != m;
+    if (!bad) {
+#pragma omp parallel for schedule(static) reduction(| : bad)
+        for (int64_t p = 0; p < (int64_t)P; p++) {
+            uint64_t r = cz[p];
+            for (uint64_t i = part_lo(n, p, P); i < part_lo(n, p + 1, P); i++) {
+                if (codes[i] != 0) {
+                    dl[i] = (int32_t)codes[i] - (int32_t)radius;
+                } else {
+                    if (out_idx[r] != i) bad = 1;
+                    dl[i] = out_delta[r++];
+                }
+            }
+        }
+    }
+    free(cz);
+    if (bad) {
+        free(dl);
+        return REF_ERR_CORRUPT;
+    }
+    if (lblock) {
+        /* every block of the per-block mode is a field of its own */
+        const uint64_t B = gbsz_ref_lorenzo_block_extent(ndim);
+        const uint64_t nb0 = (d[0] + B - 1) / B, nb1 = ndim >= 2 ? (d[1] + B - 1) / B : 1,
+                       nb2 = ndim >= 3 ? (d[2] + B - 1) / B : 1;
+#pragma omp parallel for schedule(dynamic, 256)
+        for (int64_t b = 0; b < (int64_t)(nb0 * nb1 * nb2); b++) {
+            const uint64_t bx = (uint64_t)b % nb0, by = ((uint64_t)b / nb0) % nb1, bz = (uint64_t)b / (nb0 * nb1);
+            const uint64_t Bz = ndim >= 3 ? B : 1, By = ndim >= 2 ? B : 1;
+            for (uint64_t z = bz * Bz; z < d[2] && z < (bz + 1) * Bz; z++)
+                for (uint64_t y = by * By; y < d[1] && y < (by + 1) * By; y++)
+                    for (uint64_t x = bx * B; x < d[0] && x < (bx + 1) * B; x++)
+                        cascade_point(q, dl, d, ndim, order, lblock, x, y, z);
+        }
+    } else if (ndim == 1 && order == 1) {
+        /* range p starts from the sum of every residual before it, which is
+         * q at the point before the range */
+        uint32_t *carry = (uint32_t *)calloc(P + 1, sizeof(uint32_t));
+        if (!carry) { free(dl); return REF_ERR_OOM; }
+#pragma omp parallel for schedule(static)
+        for (int64_t p = 0; p < (int64_t)P; p++) {
+            uint32_t sum = 0;
+            for (uint64_t i = part_lo(n, p, P); i < part_lo(n, p + 1, P); i++) sum += (uint32_t)dl[i];
+            carry[p + 1] = sum;
+        }
+        for (uint64_t p = 0; p < P; p++) carry[p + 1] += carry[p];
+#pragma omp parallel for schedule(static)
+        for (int64_t p = 0; p < (int64_t)P; p++) {
+            const uint64_t lo = part_lo(n, p, P), hi = part_lo(n, p + 1, P);
+            if (lo == hi) continue;
+            q[lo] = (int32_t)(carry[p] + (uint32_t)dl[lo]);
+            for (uint64_t x = lo + 1; x < hi; x++) cascade_point(q, dl, d, ndim, order, lblock, x, 0, 0);
+        }
+        free(carry);
+    } else if (ndim == 1) {
+        for (uint64_t x = 0; x < d[0]; x++) cascade_point(q, dl, d, ndim, order, lblock, x, 0, 0);
+    } else {
+        /* tasks (b, y, z): x in [b W, (b+1) W) of row (y, z); a point's
+         * neighbours lie in tasks of smaller b + y + z, or earlier in its own
+         * task (W >= order) */
+        const uint64_t W = ndim == 2 ? 128 : d[0];
+        const uint64_t nbx = (d[0] + W - 1) / W;
+        const uint64_t kmax = (nbx - 1) + (d[1] - 1) + (d[2] - 1);
+        for (uint64_t k = 0; k <= kmax; k++) {
+            /* tasks of wavefront k: z from zlo, y = k - b - z */
+            const uint64_t zlo = k > (nbx - 1) + (d[1] - 1) ? k - (nbx - 1) - (d[1] - 1) : 0;
+            const uint64_t zhi = k < d[2] - 1 ? k : d[2] - 1;
+            const uint64_t nz = zhi - zlo + 1;
+#pragma omp parallel for schedule(dynamic, 1) collapse(2)
+            for (int64_t zi = 0; zi < (int64_t)nz; zi++)
+                for (int64_t b = 0; b < (int64_t)nbx; b++) {
+                    const uint64_t z = zlo + (uint64_t)zi;
+                    if ((uint64_t)b + z > k || k - (uint64_t)b - z > d[1] - 1) continue;
+                    const uint64_t y = k - (uint64_t)b - z;
+                    for (uint64_t x = (uint64_t)b * W; x < d[0] && x < ((uint64_t)b + 1) * W; x++)
+                        cascade_point(q, dl, d, ndim, order, lblock, x, y, z);
+                }
+        }
+    }
+    free(dl);
+    return REF_OK;
+}
+#endif /* _OPENMP */
+
 int gbsz_ref_inflate(const uint32_t *stream, uint64_t words,
                      const uint32_t *bits, uint64_t n, uint32_t chunk,
                      const uint8_t *len, uint32_t nbins, uint16_t *codes)
@@ -529,6 +905,11 @@ int gbsz_ref_inflate(const uint32_t *stream, uint64_t words,
     revbook_t rb;
     int st = revbook_build(len, nbins, &rb);
     if (st) return st;
+#ifdef _OPENMP
+    st = par_inflate(stream, words, bits, n, chunk, &rb, codes);
+    free(rb.sorted);
+    return st;
+#endif
     uint64_t nc = nchunks(n, chunk), w = 0;
     for (uint64_t c = 0; c < nc && st == REF_OK; c++) {
         uint64_t lo = c * chunk, hi = lo + chunk < n ? lo + chunk : n;
@@ -576,6 +957,12 @@ int gbsz_ref_reconstruct_ex(const uint16_t *codes, uint32_t ndim,
     uint64_t n = d[0] * d[1] * d[2];
     int32_t *q = (int32_t *)malloc(n * sizeof(int32_t) + 1);
     if (!q) return REF_ERR_OOM;
+#ifdef _OPENMP
+    {
+        const int pst = par_cascade(codes, ndim, d, radius, lblock, order, out_idx, out_delta, m, q);
+        if (pst) { free(q); return pst; }
+    }
+#else
     uint64_t j = 0; /* next outlier */
     for (uint64_t z = 0; z < d[2]; z++)
         for (uint64_t y = 0; y < d[1]; y++)
@@ -594,6 +981,7 @@ int gbsz_ref_reconstruct_ex(const uint16_t *codes, uint32_t ndim,
                 q[i] = (int32_t)(p + (uint32_t)dl);
             }
     if (j != m) { free(q); return REF_ERR_CORRUPT; }
+#endif
 #pragma omp parallel for
     for (int64_t i = 0; i < (int64_t)n; i++) xr[i] = recon_value(q[i], ebx2);
     for (uint64_t t = 0; t < e; t++) {
@@ -617,6 +1005,17 @@ int gbsz_ref_reconstruct(const uint16_t *codes, uint32_t ndim,
 
 /* ------------------------------------------------------------------------ */
 /* whole path                                                                 */
+
+/* threads the parallel loops of this build use (1 in the single-threaded
+ * build) */
+int gbsz_ref_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
 
 size_t gbsz_ref_compress_bound(const gbsz_ref_params *p)
 {
@@ -705,8 +1104,10 @@ int gbsz_ref_compress(const float *x, const gbsz_ref_params *p, void *archive,
         put_u32(a, 120, lorenzo_order(p));
         put_u32(a, 124, p->ndim == 4 ? (uint32_t)p->dims[3] : 1u); /* below 2^32 as n is */
         memcpy(a + off_len, len, nbins);
-        for (uint64_t c = 0; c < nc; c++) put_u32(a, off_bits + 4 * c, bits[c]);
-        for (uint64_t t = 0; t < m; t++) {
+#pragma omp parallel for
+        for (int64_t c = 0; c < (int64_t)nc; c++) put_u32(a, off_bits + 4 * c, bits[c]);
+#pragma omp parallel for
+        for (int64_t t = 0; t < (int64_t)m; t++) {
             put_u32(a, off_out + 8 * t, oidx[t]);
             put_u32(a, off_out + 8 * t + 4, (uint32_t)odel[t]);
         }
@@ -714,7 +1115,8 @@ int gbsz_ref_compress(const float *x, const gbsz_ref_params *p, void *archive,
             put_u32(a, off_exc + 8 * t, eidx[t]);
             put_u32(a, off_exc + 8 * t + 4, eraw[t]);
         }
-        for (uint64_t t = 0; t < w; t++) put_u32(a, off_str + 4 * t, stream[t]);
+#pragma omp parallel for
+        for (int64_t t = 0; t < (int64_t)w; t++) put_u32(a, off_str + 4 * t, stream[t]);
     }
 done:
     free(codes); free(oidx); free(odel); free(eidx); free(eraw);
@@ -818,11 +1220,17 @@ int gbsz_ref_decompress(const void *archive, size_t bytes, float *x,
         }
         if (wsum != h.w) { st = REF_ERR_CORRUPT; goto done; }
     }
-    for (uint64_t t = 0; t < h.w; t++) stream[t] = get_u32(a, h.off_str + 4 * t);
-    for (uint64_t t = 0; t < h.m; t++) {
-        oidx[t] = get_u32(a, h.off_out + 8 * t);
-        odel[t] = (int32_t)get_u32(a, h.off_out + 8 * t + 4);
-        if (oidx[t] >= h.n || (t > 0 && oidx[t] <= oidx[t - 1])) { st = REF_ERR_CORRUPT; goto done; }
+#pragma omp parallel for
+    for (int64_t t = 0; t < (int64_t)h.w; t++) stream[t] = get_u32(a, h.off_str + 4 * t);
+    {
+        int bad = 0; /* outlier indices: in range and strictly ascending */
+#pragma omp parallel for reduction(| : bad)
+        for (int64_t t = 0; t < (int64_t)h.m; t++) {
+            oidx[t] = get_u32(a, h.off_out + 8 * t);
+            odel[t] = (int32_t)get_u32(a, h.off_out + 8 * t + 4);
+            if (oidx[t] >= h.n || (t > 0 && oidx[t] <= get_u32(a, h.off_out + 8 * (t - 1)))) bad = 1;
+        }
+        if (bad) { st = REF_ERR_CORRUPT; goto done; }
     }
     for (uint64_t t = 0; t < h.e; t++) {
         eidx[t] = get_u32(a, h.off_exc + 8 * t);

@@ -56,6 +56,10 @@ typedef struct {
  * (Sec. 3.1.1, "Chunking and Padding"): 32 in 1D, 16 in 2D, 8 in 3D. */
 uint32_t gbsz_ref_lorenzo_block_extent(uint32_t ndim);
 
+/* Threads the parallel loops use: omp_get_max_threads() in the OpenMP
+ * build, 1 in the single-threaded one. */
+int gbsz_ref_threads(void);
+
 /* S0 -- error bound scalars (value-range-relative bound, footnote of Sec.
  * 3.2.2).  out[0] = eb, out[1] = 2*eb, out[2] = 1/(2*eb), all FP32. */
 int gbsz_ref_error_bound(const float *x, uint64_t n, uint32_t eb_mode,

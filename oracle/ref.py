@@ -49,6 +49,7 @@ def lib(omp=False):
         P = C.c_void_p
         u32, u64 = C.c_uint32, C.c_uint64
         sig = {
+            "gbsz_ref_threads": [],
             "gbsz_ref_error_bound": [P, u64, u32, C.c_double, P],
             "gbsz_ref_prequant_one": [C.c_float, P, P],
             "gbsz_ref_lorenzo_delta": [P, u32, P, u32, P],
@@ -76,6 +77,11 @@ def lib(omp=False):
         L.gbsz_ref_lorenzo_block_extent.restype = u32
         _lib[key] = L
     return _lib[key]
+
+
+def threads(omp=False):
+    """Threads the given build's parallel loops use."""
+    return lib(omp).gbsz_ref_threads()
 
 
 def _p(a):
