@@ -570,6 +570,11 @@ def main():
     step_bytes = n * (20.0 + 16.0 * f + 8.0 / cr)
     pipe_gbs = step_bytes / (ms_step / 1e3) / 1e9
     pipe = {"alg_bytes_per_step": step_bytes, "achieved_gbs": pipe_gbs, "peak": hbm, "frac": pipe_gbs / hbm}
+    # compress and decompress each against the same bytes (12 + 8f + 4/CR and 8 + 8f + 4/CR per point)
+    cbytes, dbytes = n * (12.0 + 8.0 * f + 4.0 / cr), n * (8.0 + 8.0 * f + 4.0 / cr)
+    if comp_ms and dec_ms:
+        pipe["compress_frac"] = cbytes / (comp_ms / 1e3) / 1e9 / hbm
+        pipe["decompress_frac"] = dbytes / (dec_ms / 1e3) / 1e9 / hbm
     # every single-kernel stage against the same peak
     per_kernel = {}
     for st_i, by in alg.items():
