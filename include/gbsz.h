@@ -209,12 +209,18 @@ gbsz_status gbsz_async_wait(gbsz_ctx *ctx);
 
 /* Serving loop (continuous batching).  A server owns `workers` threads, each
  * with its own context and stream.  Submitted requests wait in a FIFO queue;
- * a free worker takes the oldest requests, as many as fit `mem_budget` bytes
- * of context scratch (about 12 bytes per point each) and at most `max_batch`,
- * and runs them with gbsz_compress_batch / gbsz_decompress_batch, so batches
- * of different workers overlap on the GPU.  Every result is the same bytes as
- * the single-field call's.  The paper has no serving layer; this is the
- * batching its block-wise design allows, for many independent fields.
+ * a free worker takes the oldest requests, at most `max_batch`, and runs them
+ * with gbsz_compress_batch / gbsz_decompress_batch, so batches of different
+ * workers overlap on the GPU.  `mem_budget` bounds the device memory the
+ * workers' contexts hold (gbsz_memory_usage), idle or busy: a batch is
+ * admitted only if an upper bound of its worker's memory after it
+ * (gbsz_scratch_bytes of every request plus any new slot) keeps the sum over
+ * workers within the budget; after the batch the worker's measured memory
+ * is counted; a worker that cannot admit the oldest request releases its
+ * scratch first (gbsz_release_scratch).  The caller's fields and archives are
+ * not counted.  Every result is the same bytes as the single-field call's.
+ * The paper has no serving layer; this is the batching its block-wise design
+ * allows, for many independent fields.
  *   gbsz_server_create   workers in [1, 64], max_batch in [1, 1024],
  *                        mem_budget > 0.  Errors: INVALID_ARG, OOM, and the
  *                        errors of gbsz_create.
@@ -222,9 +228,11 @@ gbsz_status gbsz_async_wait(gbsz_ctx *ctx);
  *   gbsz_server_submit_* queue one request and return its ticket (> 0).  The
  *                        device buffers belong to the caller and must stay
  *                        valid until the request is done; the input must be
- *                        complete on the device when submitted.  Errors:
- *                        INVALID_ARG, CAPACITY (the request alone needs more
- *                        than mem_budget; it is not queued).
+ *                        complete on the device when submitted (a
+ *                        decompress reads the archive's 128-byte header at
+ *                        submission, synchronously).  Errors: INVALID_ARG,
+ *                        CORRUPT (header), CAPACITY (the request alone needs
+ *                        more than mem_budget; it is not queued).
  *   gbsz_server_poll     *done = 1 and *status / *out_bytes (archive bytes for
  *                        a compress, field bytes for a decompress) once the
  *                        request is done; the ticket is then released.
@@ -253,6 +261,32 @@ gbsz_status gbsz_server_wait(gbsz_server *s, uint64_t ticket,
                              double timeout_s, gbsz_status *status,
                              size_t *out_bytes);
 gbsz_status gbsz_server_stats(gbsz_server *s, double *out6);
+/* out4 = {device bytes counted against the budget now, their peak, scratch
+ * releases to admit requests, batches after which a worker held more than
+ * its bound (0 unless the bound is wrong)}.  Errors: INVALID_ARG. */
+gbsz_status gbsz_server_memory(gbsz_server *s, uint64_t *out4);
+
+/* Device memory of a context.  The paper has no counterpart: these serve
+ * callers that budget device memory (the serving loop above).
+ *   gbsz_memory_usage     *device_bytes = bytes of device memory the context
+ *                         holds now (every slot's scratch and tables, staging
+ *                         of the host-buffer calls); *slots (may be NULL) =
+ *                         its scratch slots (1 .. 8).  Host-only.
+ *   gbsz_release_scratch  waits for the device, then frees every slot's
+ *                         scratch sized by field, every slot but the first,
+ *                         and all staging; drops captured graphs.  The next
+ *                         call reallocates what it needs.  INVALID_ARG while
+ *                         an asynchronous host decompress is pending.
+ *   gbsz_scratch_bytes    *field_bytes = scratch one field with parameters p
+ *                         adds to a slot (for_decompress: p as the archive
+ *                         states it); *slot_bytes = the fixed tables of one
+ *                         slot.  Host-only.  Either pointer may be NULL.
+ * Errors: INVALID_ARG (NULL context or invalid p), CUDA. */
+gbsz_status gbsz_memory_usage(gbsz_ctx *ctx, uint64_t *device_bytes,
+                              uint32_t *slots);
+gbsz_status gbsz_release_scratch(gbsz_ctx *ctx);
+gbsz_status gbsz_scratch_bytes(const gbsz_params *p, int for_decompress,
+                               uint64_t *field_bytes, uint64_t *slot_bytes);
 
 /* Parses a host copy of an archive header (at least 128 bytes; `bytes` is
  * the archive's full size, used for the size check).  Fills *out and *n.

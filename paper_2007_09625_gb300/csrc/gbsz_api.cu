@@ -170,6 +170,23 @@ struct Slot {
                parB.ensure(2 * B * 4) && lut.ensure(((1u << kLutBits) + kLut2Words) * 4) && lutf.ensure(kFastLutBytes) && first.ensure((kMaxLen + 2) * 8) &&
                count.ensure((kMaxLen + 2) * 4) && start.ensure((kMaxLen + 2) * 4) && sorted.ensure(B * 2);
     }
+    // device bytes held (buffers and the control block)
+    uint64_t bytes() const
+    {
+        uint64_t t = ctl ? sizeof(Control) : 0;
+        for (const Buf *b : {&codes, &dscr, &unit_tot, &unit_off, &unit_part, &unit_exc, &lane_bits, &chunk_off, &faces,
+                             &scan_part, &qint, &excm, &hist, &cw64, &cw32, &codes_only, &keyA, &keyB, &nodef, &parent,
+                             &distA, &distB, &parA, &parB, &lut, &lutf, &first, &count, &start, &sorted})
+            t += b->cap;
+        return t;
+    }
+    // frees the scratch sized by field (kept: the fixed-size tables)
+    void release_field_scratch()
+    {
+        for (Buf *b : {&codes, &dscr, &unit_tot, &unit_off, &unit_part, &unit_exc, &lane_bits, &chunk_off, &faces,
+                       &scan_part, &qint, &excm})
+            b->release();
+    }
     void release()
     {
         for (Buf *b : {&codes, &dscr, &unit_tot, &unit_off, &unit_part, &unit_exc, &lane_bits, &chunk_off, &faces, &scan_part,
@@ -442,6 +459,31 @@ gbsz_status check_compress(const float *d_field, const gbsz_params *pin, const v
         return GBSZ_ERR_CAPACITY;
     }
     return GBSZ_OK;
+}
+
+// bytes a Buf holds after ensure(bytes)
+inline uint64_t buf_bytes(uint64_t bytes) { return std::max<uint64_t>(bytes, 256); }
+
+// Device bytes of the per-field scratch reserve_compress / reserve_decompress
+// allocate in a slot for one field (p resolved: chunk != 0).
+uint64_t compress_scratch(const gbsz_params &p, uint64_t n)
+{
+    const uint64_t nunits = encode_units(n, p.chunk);
+    uint64_t t = buf_bytes(n * 2 + 64) + buf_bytes(n * 8 + 64) + buf_bytes(nunits * 16) + buf_bytes((n / 64 + 64) * 4) +
+                 buf_bytes(nunits * 16) + buf_bytes(scan_partials(nunits) * 16 + 64) + buf_bytes(nunits * 4);
+    if (order_of(p) > 1) t += buf_bytes(n * 4 + 64) + buf_bytes((n / 32 + 1) * 4);
+    return t;
+}
+
+uint64_t decompress_scratch(const gbsz_params &p, uint64_t n)
+{
+    uint64_t gd[3];
+    const uint64_t nchunk = (n + p.chunk - 1) / p.chunk;
+    const uint64_t nfaces = recon_faces_entries(lorenzo_geom(p, gd), gd);
+    const uint64_t nscan = std::max<uint64_t>(nchunk, nfaces);
+    const uint64_t scan_bytes = std::max<uint64_t>(scan_partials(nscan) * 8, order_of(p) > 1 ? scan_partials(n) * 4 : 0);
+    return buf_bytes(n * 2 + 64) + buf_bytes(n * 8 + 64) + buf_bytes(nchunk * 8 + 8) + buf_bytes(nfaces * 4 + 16) +
+           buf_bytes(scan_bytes + 64);
 }
 
 // Sizes a slot's scratch for one field (allocates only when it grows).
@@ -1261,6 +1303,72 @@ gbsz_status gbsz_debug_copy(gbsz_ctx *c, int which, void *h_dst, size_t bytes)
     if (need == 0 || bytes != need) return GBSZ_ERR_INVALID_ARG;
     if (cudaStreamSynchronize(c->last_stream) != cudaSuccess) return GBSZ_ERR_CUDA;
     if (cudaMemcpy(h_dst, src, need, cudaMemcpyDeviceToHost) != cudaSuccess) return GBSZ_ERR_CUDA;
+    return GBSZ_OK;
+}
+
+gbsz_status gbsz_memory_usage(gbsz_ctx *c, uint64_t *device_bytes, uint32_t *slots)
+{
+    if (!c || !device_bytes) return GBSZ_ERR_INVALID_ARG;
+    uint64_t t = 0;
+    for (const Slot *sl : c->slots) t += sl->bytes();
+    if (c->aslot) t += c->aslot->bytes();
+    for (const Buf *b : {&c->stage_field, &c->stage_archive, &c->astage_field, &c->astage_archive, &c->tune_arc,
+                         &c->tune_out})
+        t += b->cap;
+    *device_bytes = t;
+    if (slots) *slots = (uint32_t)c->slots.size();
+    return GBSZ_OK;
+}
+
+gbsz_status gbsz_release_scratch(gbsz_ctx *c)
+{
+    if (!c) return GBSZ_ERR_INVALID_ARG;
+    if (c->apending) return GBSZ_ERR_INVALID_ARG;
+    DevGuard g(c->device);
+    if (cudaDeviceSynchronize() != cudaSuccess) {
+        cudaGetLastError();
+        return GBSZ_ERR_CUDA;
+    }
+    for (BatchGraph *bg : {&c->gcomp, &c->gdecomp, &c->gsc, &c->gsd}) {
+        bg->drop();
+        bg->seen.clear();
+    }
+    while (c->slots.size() > 1) {
+        c->slots.back()->release();
+        delete c->slots.back();
+        c->slots.pop_back();
+    }
+    c->slots[0]->release_field_scratch();
+    if (c->aslot) {
+        c->aslot->release();
+        delete c->aslot;
+        c->aslot = nullptr;
+    }
+    for (Buf *b : {&c->stage_field, &c->stage_archive, &c->astage_field, &c->astage_archive, &c->tune_arc,
+                   &c->tune_out})
+        b->release();
+    c->have_compress = c->have_decompress = false;
+    return GBSZ_OK;
+}
+
+gbsz_status gbsz_scratch_bytes(const gbsz_params *p, int for_decompress, uint64_t *field_bytes,
+                               uint64_t *slot_bytes)
+{
+    uint64_t n;
+    if (!p || !valid_params(p, &n)) return GBSZ_ERR_INVALID_ARG;
+    gbsz_params q = *p;
+    if (q.chunk == 0) q.chunk = auto_chunk(n);
+    if (field_bytes) *field_bytes = for_decompress ? decompress_scratch(q, n) : compress_scratch(q, n);
+    if (slot_bytes) {
+        const uint64_t B = kMaxBins;
+        uint64_t t = sizeof(Control);
+        for (uint64_t b : {B * 4, B * 8, B * 4, B * 8, B * 8, B * 8, B * 4, 2 * B * 4, 2 * B * 4, 2 * B * 4, 2 * B * 4,
+                           2 * B * 4, (uint64_t)((1u << kLutBits) + kLut2Words) * 4, (uint64_t)kFastLutBytes,
+                           (uint64_t)(kMaxLen + 2) * 8, (uint64_t)(kMaxLen + 2) * 4, (uint64_t)(kMaxLen + 2) * 4,
+                           B * 2})
+            t += buf_bytes(b);
+        *slot_bytes = t;
+    }
     return GBSZ_OK;
 }
 

@@ -7,6 +7,7 @@
 
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <new>
 
 static_assert(sizeof(gbsz_params) <= sizeof(((gbsz_srv::Request *)nullptr)->params), "params do not fit");
@@ -101,13 +102,51 @@ public:
         }
     }
 
+    uint64_t resident(void *p) override
+    {
+        CudaWorker *w = static_cast<CudaWorker *>(p);
+        uint64_t b = 0;
+        gbsz_memory_usage(w->ctx, &b, nullptr);
+        return b;
+    }
+
+    // now + every request's field scratch + the fixed tables of the slots
+    // the batch calls add (a batch uses up to 8 slots)
+    uint64_t estimate(void *p, const std::vector<gbsz_srv::Request *> &batch) override
+    {
+        CudaWorker *w = static_cast<CudaWorker *>(p);
+        uint64_t b = 0;
+        uint32_t slots = 1;
+        gbsz_memory_usage(w->ctx, &b, &slots);
+        size_t nc = 0, nd = 0;
+        for (auto *r : batch) {
+            b += r->mem;
+            (r->kind == gbsz_srv::kCompress ? nc : nd)++;
+        }
+        const uint32_t want = (uint32_t)std::min<size_t>(std::max(nc, nd), 8);
+        if (want > slots) b += (uint64_t)(want - slots) * slot_bytes();
+        return b;
+    }
+
+    void trim(void *p) override { gbsz_release_scratch(static_cast<CudaWorker *>(p)->ctx); }
+
+    uint64_t least(uint64_t mem) override { return slot_bytes() + mem; }
+
 private:
+    static uint64_t slot_bytes()
+    {
+        gbsz_params q{};
+        q.ndim = 1;
+        q.dims[0] = 1;
+        q.dims[1] = q.dims[2] = q.dims[3] = 1;
+        q.eb = 1.0;
+        q.radius = 2;
+        uint64_t sb = 0;
+        gbsz_scratch_bytes(&q, 0, nullptr, &sb);
+        return sb;
+    }
     int dev_;
 };
-
-// device scratch a request holds in a worker's context while it runs (codes,
-// residuals, encoder and decoder tables): about 12 bytes per point
-constexpr uint64_t kScratchPerPoint = 12;
 
 }  // namespace
 
@@ -161,7 +200,7 @@ gbsz_status gbsz_server_submit_compress(gbsz_server *s, const float *d_field, co
     r.n = 1;
     for (uint32_t i = 0; i < p->ndim; i++) r.n *= p->dims[i];
     std::memcpy(r.params, p, sizeof(gbsz_params));
-    r.mem = kScratchPerPoint * r.n;
+    if (gbsz_scratch_bytes(p, 0, &r.mem, nullptr) != GBSZ_OK) return GBSZ_ERR_INVALID_ARG;
     *ticket = s->core.submit(r);
     return *ticket ? GBSZ_OK : GBSZ_ERR_CAPACITY;
 }
@@ -176,8 +215,19 @@ gbsz_status gbsz_server_submit_decompress(gbsz_server *s, const void *d_archive,
     r.in_bytes = bytes;
     r.out = d_field;
     r.cap = capacity_elems;
-    r.n = capacity_elems;
-    r.mem = kScratchPerPoint * r.n;
+    // the archive's parameters fix the scratch its decompression takes
+    unsigned char hdr[128];
+    if (bytes < sizeof(hdr)) return GBSZ_ERR_CORRUPT;
+    if (cudaMemcpy(hdr, d_archive, sizeof(hdr), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return GBSZ_ERR_CUDA;
+    }
+    gbsz_params hp;
+    uint64_t n = 0;
+    const gbsz_status hs = gbsz_archive_info(hdr, bytes, &hp, &n);
+    if (hs != GBSZ_OK) return hs;
+    r.n = n;
+    if (gbsz_scratch_bytes(&hp, 1, &r.mem, nullptr) != GBSZ_OK) return GBSZ_ERR_CORRUPT;
     *ticket = s->core.submit(r);
     return *ticket ? GBSZ_OK : GBSZ_ERR_CAPACITY;
 }
@@ -213,6 +263,16 @@ gbsz_status gbsz_server_stats(gbsz_server *s, double *out6)
 {
     if (!s || !out6) return GBSZ_ERR_INVALID_ARG;
     s->core.stats(out6);
+    return GBSZ_OK;
+}
+
+gbsz_status gbsz_server_memory(gbsz_server *s, uint64_t *out4)
+{
+    if (!s || !out4) return GBSZ_ERR_INVALID_ARG;
+    out4[0] = s->core.in_use();
+    out4[1] = s->core.peak();
+    out4[2] = s->core.trims();
+    out4[3] = s->core.overruns();
     return GBSZ_OK;
 }
 

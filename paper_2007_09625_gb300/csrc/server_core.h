@@ -1,5 +1,6 @@
 // server_core.h -- host logic of the continuous-batching request loop:
-// a FIFO queue, admission by a device-memory budget, batches of at most
+// a FIFO queue, admission by a device-memory budget (every worker's resident
+// context memory counted), batches of at most
 // max_batch requests taken by worker threads, completion tickets and latency
 // statistics.  Pure C++ (no CUDA): the work itself is done by an Executor,
 // which the library implements with its batch entry points (server.cu) and
@@ -37,6 +38,13 @@ struct Request {
     bool done = false;
 };
 
+// Device memory of a worker is its resident state: what its context holds
+// between batches (fixed tables and scratch grown for the largest fields it
+// ran).  The core counts every worker's resident bytes against the budget
+// at all times, and admits a batch only if the worker's resident bytes after
+// it -- estimated from above before, measured after -- keep the total within
+// the budget.  A worker that cannot admit the oldest request because of
+// memory releases its own scratch first.
 class Executor {
 public:
     virtual ~Executor() = default;
@@ -44,6 +52,14 @@ public:
     virtual void free_worker(void *w) = 0;
     // runs a batch; sets status and out_bytes of every request
     virtual void run(void *w, std::vector<Request *> &batch) = 0;
+    // device bytes the worker holds now
+    virtual uint64_t resident(void *w) = 0;
+    // an upper bound of resident(w) after running the batch
+    virtual uint64_t estimate(void *w, const std::vector<Request *> &batch) = 0;
+    // releases the worker's scratch, keeping what it needs to exist
+    virtual void trim(void *w) = 0;
+    // the least a worker holds after running one request of `mem` scratch bytes
+    virtual uint64_t least(uint64_t mem) = 0;
 };
 
 inline double now_s()
@@ -71,7 +87,15 @@ public:
             }
             states.push_back(w);
         }
-        for (void *w : states) threads_.emplace_back([this, w] { worker_loop(w); });
+        held_.assign(states.size(), 0);
+        for (size_t i = 0; i < states.size(); i++) {
+            held_[i] = ex_->resident(states[i]);
+            in_use_ += held_[i];
+        }
+        for (size_t i = 0; i < states.size(); i++) {
+            void *w = states[i];
+            threads_.emplace_back([this, w, i] { worker_loop(w, i); });
+        }
         return true;
     }
 
@@ -80,7 +104,7 @@ public:
     uint64_t submit(const Request &r)
     {
         std::lock_guard<std::mutex> g(mu_);
-        if (stopping_ || r.mem > budget_) return 0;
+        if (stopping_ || ex_->least(r.mem) > budget_) return 0;
         Request *q = new Request(r);
         q->id = next_id_++;
         q->t_arrive = now_s();
@@ -135,11 +159,28 @@ public:
         out[4] = out[5] > 0 ? (double)in_bytes_ / out[5] / 1e9 : 0;
     }
 
-    // admitted memory now (for tests)
+    // counted device memory now, and its peak (for tests)
     uint64_t in_use()
     {
         std::lock_guard<std::mutex> g(mu_);
         return in_use_;
+    }
+    uint64_t peak()
+    {
+        std::lock_guard<std::mutex> g(mu_);
+        return peak_;
+    }
+    // times a worker released its scratch to admit a request; batches after
+    // which a worker held more than estimated (should stay 0)
+    uint64_t trims()
+    {
+        std::lock_guard<std::mutex> g(mu_);
+        return trims_;
+    }
+    uint64_t overruns()
+    {
+        std::lock_guard<std::mutex> g(mu_);
+        return over_;
     }
 
     // finishes every queued request, then joins the workers
@@ -171,39 +212,69 @@ private:
         return 1;
     }
 
-    // the oldest requests, as many as fit the budget and max_batch; empty
-    // when stopping with nothing queued
-    std::vector<Request *> take_batch()
+    // The oldest requests, as many as fit the budget and max_batch, for
+    // worker i; *charged = the worker's resident bytes counted while they run
+    // (the estimate).  Empty when stopping with nothing queued.
+    std::vector<Request *> take_batch(void *w, size_t i, uint64_t *charged)
     {
         std::unique_lock<std::mutex> g(mu_);
+        bool trimmed = false;  // released this worker's scratch since its last batch
         for (;;) {
             std::vector<Request *> b;
+            uint64_t est = held_[i];
             while (!queue_.empty() && b.size() < max_batch_) {
-                Request *r = queue_.front();
-                if (in_use_ + r->mem > budget_) break;
+                b.push_back(queue_.front());
+                const uint64_t e = ex_->estimate(w, b);
+                if (in_use_ - held_[i] + e > budget_) {
+                    b.pop_back();
+                    break;
+                }
+                est = e;
                 queue_.pop_front();
-                in_use_ += r->mem;
-                b.push_back(r);
             }
-            if (!b.empty()) return b;
+            if (!b.empty()) {
+                in_use_ += est - held_[i];
+                *charged = est;
+                peak_ = std::max(peak_, in_use_);
+                return b;
+            }
             if (stopping_ && queue_.empty()) return b;
+            if (!queue_.empty() && !trimmed && held_[i] > ex_->least(0)) {
+                // blocked by memory: release this worker's scratch, then retry
+                g.unlock();
+                ex_->trim(w);
+                const uint64_t now = ex_->resident(w);
+                g.lock();
+                in_use_ = in_use_ - held_[i] + now;
+                held_[i] = now;
+                trims_++;
+                trimmed = true;
+                cv_work_.notify_all();
+                continue;
+            }
             cv_work_.wait_for(g, std::chrono::milliseconds(50));
         }
     }
 
-    void worker_loop(void *w)
+    void worker_loop(void *w, size_t i)
     {
         for (;;) {
-            std::vector<Request *> b = take_batch();
+            uint64_t charged = 0;
+            std::vector<Request *> b = take_batch(w, i, &charged);
             if (b.empty()) break;
             const double t0 = now_s();
             for (Request *r : b) r->t_start = t0;
             ex_->run(w, b);
+            const uint64_t now = ex_->resident(w);
             const double t1 = now_s();
             std::lock_guard<std::mutex> g(mu_);
+            // count what the worker holds now (the estimate bounded it from above)
+            in_use_ = in_use_ - charged + now;
+            held_[i] = now;
+            if (now > charged) over_++;
+            peak_ = std::max(peak_, in_use_);
             batches_.push_back((uint32_t)b.size());
             for (Request *r : b) {
-                in_use_ -= r->mem;
                 r->t_done = t1;
                 r->done = true;
                 if (r->status == 0) {
@@ -227,7 +298,8 @@ private:
     std::deque<Request *> queue_;
     std::unordered_map<uint64_t, Request *> all_;
     std::vector<std::thread> threads_;
-    uint64_t next_id_ = 1, in_use_ = 0, in_bytes_ = 0;
+    uint64_t next_id_ = 1, in_use_ = 0, in_bytes_ = 0, peak_ = 0, trims_ = 0, over_ = 0;
+    std::vector<uint64_t> held_;  // resident bytes of every worker between batches
     bool stopping_ = false;
     std::vector<double> lat_;
     std::vector<uint32_t> batches_;

@@ -50,6 +50,10 @@ SIGNATURES = {
     "gbsz_server_poll": ([_P, C.c_uint64, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_size_t)], C.c_int),
     "gbsz_server_wait": ([_P, C.c_uint64, C.c_double, C.POINTER(C.c_int), C.POINTER(C.c_size_t)], C.c_int),
     "gbsz_server_stats": ([_P, _P], C.c_int),
+    "gbsz_server_memory": ([_P, _P], C.c_int),
+    "gbsz_memory_usage": ([_P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)], C.c_int),
+    "gbsz_release_scratch": ([_P], C.c_int),
+    "gbsz_scratch_bytes": ([_P, C.c_int, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int),
 }
 OPT_CODEWORD_BITS = 1
 
@@ -245,6 +249,19 @@ class Context:
             raise GbszError(st, "gbsz_decompress_batch")
         return outs, list(sts)
 
+    def memory_usage(self):
+        """(device bytes the context holds, its scratch slots)."""
+        b, k = C.c_uint64(), C.c_uint32()
+        st = load().gbsz_memory_usage(self.h, C.byref(b), C.byref(k))
+        if st != OK:
+            raise GbszError(st, "gbsz_memory_usage")
+        return b.value, k.value
+
+    def release_scratch(self):
+        st = load().gbsz_release_scratch(self.h)
+        if st != OK:
+            raise GbszError(st, "gbsz_release_scratch")
+
     def set_option(self, option, value):
         st = load().gbsz_set_option(self.h, int(option), int(value))
         if st != OK:
@@ -340,6 +357,16 @@ def archive_info(header_bytes, nbytes=None):
     if st != OK:
         raise GbszError(st, "gbsz_archive_info")
     return p, n.value
+
+
+def scratch_bytes(dims, eb=1e-4, eb_mode=EB_REL, radius=512, chunk=0, lblock=0, order=1, for_decompress=False):
+    """(scratch one such field adds to a context slot, fixed bytes of one slot)."""
+    f, sl = C.c_uint64(), C.c_uint64()
+    st = load().gbsz_scratch_bytes(C.byref(make_params(dims, eb, eb_mode, radius, chunk, lblock, order)),
+                                   1 if for_decompress else 0, C.byref(f), C.byref(sl))
+    if st != OK:
+        raise GbszError(st, "gbsz_scratch_bytes")
+    return f.value, sl.value
 
 
 def auto_chunk(dims, radius=512):

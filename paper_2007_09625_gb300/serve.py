@@ -63,25 +63,31 @@ class Server:
         self.h = h
         return self
 
-    def submit(self, kind, data, nbytes=None, **params):
+    def submit(self, kind, data, nbytes=None, out=None, **params):
         """compress: data = contiguous float32 CUDA tensor, params eb, eb_mode,
         radius, chunk, lblock, order as for Context.compress.  decompress:
         data = uint8 CUDA archive tensor, nbytes its size.  The input must be
-        complete on the device (the producing stream synchronised)."""
+        complete on the device (the producing stream synchronised).  out: the
+        output tensor (archive bytes, or the field), allocated here if None
+        (an archive then gets the worst-case size)."""
         L = gbsz.load()
         t = C.c_uint64()
         if kind == COMPRESS:
             p = gbsz.make_params(gbsz.field_dims(data), params.get("eb", 1e-4), params.get("eb_mode", gbsz.EB_REL),
                                  params.get("radius", 512), params.get("chunk", 0), params.get("lblock", 0),
                                  params.get("order", 1))
-            out = torch.empty(L.gbsz_compress_bound(C.byref(p)), dtype=torch.uint8, device=data.device)
+            if out is None:
+                out = torch.empty(L.gbsz_compress_bound(C.byref(p)), dtype=torch.uint8, device=data.device)
+            assert out.dtype == torch.uint8 and out.is_contiguous()
             st = L.gbsz_server_submit_compress(self.h, C.c_void_p(data.data_ptr()), C.byref(p),
                                                C.c_void_p(out.data_ptr()), out.numel(), C.byref(t))
         else:
             nbytes = data.numel() if nbytes is None else int(nbytes)
-            p, n = gbsz.archive_info(data[:128].cpu().numpy(), nbytes)
-            shape = [int(p.dims[i]) for i in range(p.ndim)][::-1]
-            out = torch.empty(shape, dtype=torch.float32, device=data.device)
+            if out is None:
+                p, n = gbsz.archive_info(data[:128].cpu().numpy(), nbytes)
+                shape = [int(p.dims[i]) for i in range(p.ndim)][::-1]
+                out = torch.empty(shape, dtype=torch.float32, device=data.device)
+            assert out.dtype == torch.float32 and out.is_contiguous()
             st = L.gbsz_server_submit_decompress(self.h, C.c_void_p(data.data_ptr()), nbytes,
                                                  C.c_void_p(out.data_ptr()), out.numel(), C.byref(t))
         # the output's allocation is ordered on the current stream: let it
@@ -104,6 +110,16 @@ class Server:
         d = dict(zip(keys, list(out)))
         d["requests"] = int(d["requests"])
         return d
+
+    def memory(self):
+        """Device memory the server counts against its budget: bytes now,
+        their peak, scratch releases to admit requests, batches whose worker
+        ended above its bound (0 unless the bound is wrong)."""
+        out = (C.c_uint64 * 4)()
+        st = gbsz.load().gbsz_server_memory(self.h, out)
+        if st != gbsz.OK:
+            raise gbsz.GbszError(st, "gbsz_server_memory")
+        return dict(zip(("in_use", "peak", "releases", "overruns"), list(out)))
 
     def stop(self):
         if self.h:

@@ -164,3 +164,56 @@ def field_for(kind, shape, seed):
         f += rng.normal(0, 1e-3 * (f.max() - f.min()), shape)
         return f.astype(np.float32)
     raise ValueError(kind)
+
+
+def field_on_device(kind, shape, seed, device):
+    """The generators of field_for, computed with torch on `device` (for the
+    serving mix, whose 256 fields of up to 512 MiB would take minutes on the
+    host).  Seeded by a device generator, so the values differ from
+    field_for's numpy stream but follow the same recipe: a Gaussian random
+    walk (step 1e-2), a power-law Gaussian random field (slope -3 in 2D,
+    -2.5 otherwise) of unit variance, its exponential, or a sum of 8
+    random-phase sinusoids plus noise of 1e-3 of the range."""
+    import torch
+    g = torch.Generator(device=device)
+    g.manual_seed(int(seed))
+    n = 1
+    for s in shape:
+        n *= s
+    if kind == "walk":
+        steps = torch.randn(n, generator=g, device=device, dtype=torch.float32) * 1e-2
+        return torch.cumsum(steps.double(), 0).float().reshape(shape)
+    if kind in ("grf", "lognormal"):
+        slope = -3.0 if (kind == "grf" and len(shape) == 2) else -2.5
+        w = torch.randn(shape, generator=g, device=device, dtype=torch.float32)
+        W = torch.fft.rfftn(w)
+        del w
+        k2 = torch.zeros(W.shape, device=device, dtype=torch.float32)
+        for ax, s in enumerate(shape):
+            kk = torch.fft.rfftfreq(s, device=device) if ax == len(shape) - 1 else torch.fft.fftfreq(s, device=device)
+            sh = [1] * len(shape)
+            sh[ax] = kk.numel()
+            k2 += kk.float().reshape(sh) ** 2
+        k2.view(-1)[0] = 1.0
+        amp = k2 ** (slope / 4.0)
+        amp.view(-1)[0] = 0.0
+        W *= amp
+        del amp, k2
+        f = torch.fft.irfftn(W, s=shape)
+        del W
+        f = (f - f.mean()) / f.std()
+        return torch.exp(f) if kind == "lognormal" else f.contiguous()
+    if kind == "sinus":
+        f = torch.zeros(shape, device=device, dtype=torch.float32)
+        grids = torch.meshgrid(*[torch.arange(s, device=device, dtype=torch.float32) / s for s in shape],
+                               indexing="ij")
+        for _ in range(8):
+            k = torch.randint(1, 9, (len(shape),), generator=g, device=device).float()
+            a = 0.5 + 0.5 * torch.rand((), generator=g, device=device)
+            ph = 2 * np.pi * torch.rand((), generator=g, device=device)
+            arg = sum(kk * gg for kk, gg in zip(k, grids)) * (2 * np.pi) + ph
+            f += a * torch.sin(arg)
+        rng_ = f.max() - f.min()
+        f += torch.randn(shape, generator=g, device=device) * (1e-3 * rng_)
+        return f
+    raise ValueError(kind)

@@ -1,8 +1,9 @@
 """Host logic of the native serving loop (server_core.h) with a stand-in
-executor, no GPU: FIFO admission by memory budget, batch size limit,
-admission of requests that arrive while others run, rejection of requests
-above the budget, tickets and latency statistics.  The harness is compiled
-here with the host compiler."""
+executor, no GPU: FIFO admission by a device-memory budget that counts every
+worker's resident memory (idle or busy), release of a worker's scratch when
+it blocks admission, batch size limit, admission of requests that arrive
+while others run, rejection of requests above the budget, tickets and
+latency statistics.  The harness is compiled here with the host compiler."""
 import ctypes as C
 import os
 import subprocess
@@ -25,13 +26,14 @@ def lib():
                        check=True)
     L = C.CDLL(LIB)
     P, u32, u64 = C.c_void_p, C.c_uint32, C.c_uint64
-    L.h_new.argtypes, L.h_new.restype = [u32, u32, u64, C.c_int], P
+    L.h_new.argtypes, L.h_new.restype = [u32, u32, u64, C.c_int, u64], P
     L.h_submit.argtypes, L.h_submit.restype = [P, C.c_int, u64, u64], u64
     L.h_wait.argtypes, L.h_wait.restype = [P, u64, C.c_double, C.POINTER(C.c_int), C.POINTER(u64)], C.c_int
     L.h_poll.argtypes, L.h_poll.restype = [P, u64, C.POINTER(C.c_int), C.POINTER(u64)], C.c_int
     L.h_stats.argtypes = [P, P]
     L.h_times.argtypes = [P, u64, C.POINTER(C.c_double), C.POINTER(C.c_double)]
     L.h_limits.argtypes = [P, C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(u64)]
+    L.h_memory.argtypes = [P] + [C.POINTER(u64)] * 4
     L.h_stop.argtypes = [P]
     L.h_free.argtypes = [P]
     return L
@@ -56,7 +58,7 @@ def stats(L, h):
 
 
 def test_all_requests_complete_within_limits(lib):
-    h = lib.h_new(3, 4, 10_000, 20)
+    h = lib.h_new(3, 4, 10_000, 20, 0)
     tickets = []
     for i in range(40):
         n = 10 + (i * 37) % 290
@@ -77,7 +79,7 @@ def test_all_requests_complete_within_limits(lib):
 
 
 def test_requests_arriving_during_work_are_admitted(lib):
-    h = lib.h_new(2, 2, 1 << 20, 200)
+    h = lib.h_new(2, 2, 1 << 20, 200, 0)
     first = lib.h_submit(h, 0, 10, 40)
     time.sleep(0.05)  # the first batch is running now
     second = lib.h_submit(h, 0, 10, 40)
@@ -93,7 +95,7 @@ def test_requests_arriving_during_work_are_admitted(lib):
 
 
 def test_memory_budget_serialises_and_rejects(lib):
-    h = lib.h_new(4, 8, 1000, 50)
+    h = lib.h_new(4, 8, 1000, 50, 0)
     big = [lib.h_submit(h, 0, 150, 600) for _ in range(4)]  # 600 bytes each: one at a time
     assert lib.h_submit(h, 0, 1000, 4000) == 0  # above the whole budget: rejected
     for t in big:
@@ -105,7 +107,7 @@ def test_memory_budget_serialises_and_rejects(lib):
 
 
 def test_poll_pending_then_done_and_stop_drains(lib):
-    h = lib.h_new(1, 1, 1 << 20, 100)
+    h = lib.h_new(1, 1, 1 << 20, 100, 0)
     ts = [lib.h_submit(h, 1, 5, 1) for _ in range(3)]
     st, ob = C.c_int(), C.c_uint64()
     assert lib.h_poll(h, ts[2], C.byref(st), C.byref(ob)) == 0  # queued behind the others
@@ -114,4 +116,41 @@ def test_poll_pending_then_done_and_stop_drains(lib):
     lib.h_stop(h)  # runs everything queued
     assert lib.h_submit(h, 0, 5, 1) == 0  # no new work after stop
     assert stats(lib, h)[0] == 3
+    lib.h_free(h)
+
+
+def memory(L, h):
+    v = [C.c_uint64() for _ in range(4)]
+    L.h_memory(h, *[C.byref(x) for x in v])
+    return [x.value for x in v]
+
+
+def test_resident_memory_counts_against_the_budget(lib):
+    """Each worker holds 100 bytes of fixed tables plus the scratch of the
+    largest request it ran; idle workers' memory stays counted, and a worker
+    whose memory blocks the next request releases it."""
+    h = lib.h_new(3, 4, 2000, 30, 100)
+    assert memory(lib, h)[0] == 300  # three idle workers, fixed tables only
+    ts = [lib.h_submit(h, i % 2, 100, 900) for i in range(6)]  # 900-byte scratch: one at a time
+    assert lib.h_submit(h, 0, 10, 1901) == 0  # above the budget with one worker's tables
+    for t in ts:
+        assert wait(lib, h, t)[0] == 0
+    lib.h_stop(h)
+    in_use, peak, trims, over = memory(lib, h)
+    assert peak <= 2000 and over == 0
+    assert trims >= 1  # a worker holding 1000 bytes had to let go for another to run
+    assert limits(lib, h)[2] <= 2000
+    lib.h_free(h)
+
+
+def test_small_requests_share_the_budget(lib):
+    h = lib.h_new(4, 8, 10_000, 10, 100)
+    ts = [lib.h_submit(h, 0, 10, 50 + i) for i in range(64)]
+    for t in ts:
+        assert wait(lib, h, t)[0] == 0
+    lib.h_stop(h)
+    in_use, peak, trims, over = memory(lib, h)
+    assert peak <= 10_000 and over == 0 and trims == 0
+    s = stats(lib, h)
+    assert s[0] == 64 and s[3] > 1  # batched
     lib.h_free(h)
