@@ -286,6 +286,37 @@ __device__ __forceinline__ uint32_t block_max(uint32_t v, uint32_t *sh)
 
 
 // ---------------------------------------------------------------------------
+// Grouped launches.  A kernel body sees its block index and grid size
+// through a VGrid, so the same body runs as a launch of its own or as one
+// field's share of a grouped launch that covers many fields of a batch: item
+// i owns the blocks [first[i], first[i+1]) of the grid and runs the body
+// with blocks 0 .. first[i+1] - first[i] - 1 of its own virtual grid.
+struct VGrid {
+    uint32_t bid, nb;
+};
+
+__device__ __forceinline__ VGrid vgrid_self() { return VGrid{blockIdx.x, gridDim.x}; }
+
+// The item that owns this block (all threads; contains a barrier).
+__device__ __forceinline__ uint32_t group_item(const uint32_t *first, uint32_t nitems, VGrid &vg)
+{
+    __shared__ uint32_t s_item;
+    if (threadIdx.x == 0) {
+        uint32_t lo = 0, hi = nitems;  // first[lo] <= blockIdx.x < first[hi]
+        while (hi - lo > 1) {
+            const uint32_t m = (lo + hi) >> 1;
+            if (first[m] <= blockIdx.x) lo = m;
+            else hi = m;
+        }
+        s_item = lo;
+    }
+    __syncthreads();
+    const uint32_t i = s_item;
+    vg = VGrid{blockIdx.x - first[i], first[i + 1] - first[i]};
+    return i;
+}
+
+// ---------------------------------------------------------------------------
 // launch wrappers implemented in the kernel translation units
 
 struct QuantArgs {
@@ -314,6 +345,28 @@ __host__ __device__ constexpr uint32_t lorenzo_block_extent(uint32_t ndim)
 void launch_minmax_eb(const float *x, uint64_t n, Control *ctl, double eb, uint32_t mode,
                       int num_sms, cudaStream_t st);
 int launch_dualquant(const QuantArgs &a, cudaStream_t st);  // returns kernels launched
+
+// grouped S0-S3 (items and block tables in device memory)
+struct MinmaxItem {
+    const float *x;
+    uint64_t n;
+    Control *ctl;
+    double eb;
+    uint32_t mode;
+};
+struct QuantItem {
+    QuantArgs a;
+    uint32_t t[4];  // tiles: 1D {ntiles}; 2D {ntx, nty}; 3D {ntx, nty, ntz, z planes per tile}
+};
+// blocks of one field's S0 in a grouped launch
+uint32_t minmax_blocks(uint64_t n, uint32_t mode, int num_sms);
+// one order-1 field's S1-S3: its blocks, tile parameters, kernel variant
+// (D * 4 + VEC * 2 + WIN) and dynamic shared memory
+uint32_t dualquant_plan(const QuantArgs &a, uint32_t t[4], int *variant, size_t *smem);
+void launch_minmax_group(const MinmaxItem *items, const uint32_t *first, uint32_t ni, uint32_t blocks, bool vec,
+                         cudaStream_t st);
+void launch_dualquant_group(int variant, const QuantItem *items, const uint32_t *first, uint32_t ni,
+                            uint32_t blocks, size_t smem, cudaStream_t st);
 
 struct CodebookArgs {
     const uint32_t *hist;  // for compress; NULL for the decode-table build
@@ -365,6 +418,7 @@ __host__ __device__ inline uint32_t fast_lut_bits(uint32_t maxlen, uint32_t nbin
 }
 
 void launch_codebook(const CodebookArgs &a, cudaStream_t st);
+void launch_codebook_group(const CodebookArgs *items, uint32_t count, cudaStream_t st);  // one CTA per field
 void launch_decode_tables(const CodebookArgs &a, cudaStream_t st);
 
 struct EncodeArgs {
@@ -392,6 +446,36 @@ struct EncodeArgs {
 };
 // phase 0: count, 1: scan of the unit totals, 2: pack; returns kernels launched
 int launch_encode(const EncodeArgs &a, cudaStream_t st, int phase);
+
+// grouped S5 (items and block tables in device memory)
+struct EncodeItem {
+    EncodeArgs a;
+    uint64_t nunits;
+    uint32_t use_smem;
+};
+// exclusive scan of one field's unit totals (words, outliers | exceptions << 32)
+struct UnitScan {
+    using T = ulonglong2;
+    const ulonglong2 *tot;
+    ulonglong2 *off;
+    __device__ T load(uint64_t i) const { return tot[i]; }
+    __device__ void store(uint64_t i, T v) const { off[i] = v; }
+    __device__ void total(T) const {}
+};
+template <typename Op> struct ScanItem {
+    using OpT = Op;
+    Op o;
+    uint64_t n;
+    typename Op::T *partial;
+    __device__ const Op &op() const { return o; }
+};
+// one field's S5 in a grouped launch: its item, the blocks of count (0) and
+// pack (1), their dynamic shared memory, and the units to scan
+void encode_plan(const EncodeArgs &a, EncodeItem *it, uint32_t blocks[2], size_t smem[2], uint64_t *scan_items);
+void launch_encode_group(int phase, const EncodeItem *items, const uint32_t *first, uint32_t ni, uint32_t blocks,
+                         size_t smem, cudaStream_t st);  // phase 0: count, 1: pack
+int launch_unit_scan_group(const ScanItem<UnitScan> *items, const uint32_t *first, uint32_t ni, uint32_t blocks,
+                           cudaStream_t st);
 uint64_t encode_units(uint64_t n, uint32_t chunk);        // units (per-unit totals) of the encoder
 uint32_t encode_unit_shift(uint32_t chunk);                // log2 of the encoder unit in points
 

@@ -268,7 +268,7 @@ __device__ void phase_merge(const uint32_t *LF, uint32_t *F, uint32_t *P, uint32
     __syncthreads();
 }
 
-__global__ void __launch_bounds__(kCbThreads, 1) k_codebook(CodebookArgs a)
+__device__ __forceinline__ void codebook_body(const CodebookArgs &a)
 {
     extern __shared__ uint32_t s_cnt[];  // 16 * kCbThreads words
     __shared__ Canon canon;
@@ -362,6 +362,17 @@ __global__ void __launch_bounds__(kCbThreads, 1) k_codebook(CodebookArgs a)
     }
     if (maxlen > kMaxLen) return;
     canonicalize(a.len_out, nbins, s_cnt, canon, nullptr, a.cw64, a.cw32, a.codes_only, maxlen);
+}
+
+__global__ void __launch_bounds__(kCbThreads, 1) k_codebook(const __grid_constant__ CodebookArgs a)
+{
+    codebook_body(a);
+}
+
+// grouped: block i builds field i's codebook
+__global__ void __launch_bounds__(kCbThreads, 1) k_codebook_group(const CodebookArgs *items)
+{
+    codebook_body(items[blockIdx.x]);
 }
 
 // Reverse codebook for decoding: validates the length table (every length
@@ -485,6 +496,7 @@ void set_smem_attributes()
     if (bit && (done.load() & bit)) return;
     cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem);
     cudaFuncSetAttribute(k_decode_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem);
+    cudaFuncSetAttribute(k_codebook_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem);
     done.fetch_or(bit);
 }
 
@@ -494,6 +506,12 @@ void launch_codebook(const CodebookArgs &a, cudaStream_t st)
 {
     set_smem_attributes();
     k_codebook<<<1, kCbThreads, kCbSmem, st>>>(a);
+}
+
+void launch_codebook_group(const CodebookArgs *items, uint32_t count, cudaStream_t st)
+{
+    set_smem_attributes();
+    k_codebook_group<<<count, kCbThreads, kCbSmem, st>>>(items);
 }
 
 void launch_decode_tables(const CodebookArgs &a, cudaStream_t st)

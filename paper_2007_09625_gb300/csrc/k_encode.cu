@@ -233,7 +233,8 @@ __device__ __forceinline__ uint32_t count_tail(const EncodeArgs &a, const CT &ct
 }
 
 template <typename CT>
-__device__ __forceinline__ void count_units(const EncodeArgs &a, uint64_t nunits, const CT &ct, uint32_t *part)
+__device__ __forceinline__ void count_units(const EncodeArgs &a, uint64_t nunits, const CT &ct, uint32_t *part,
+                                            VGrid vg)
 {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t n = a.n;
@@ -246,8 +247,8 @@ __device__ __forceinline__ void count_units(const EncodeArgs &a, uint64_t nunits
     const Layout L0 = make_layout(a.radius, nchunk, a.ctl->n_out, a.ctl->n_exc, 0);
     const bool first_of_chunk = (lane & (ug.G - 1)) == 0;
     const uint32_t *myseg = part + (lane / segs) * kPartStride + (lane % segs) * per;
-    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t gw = ((uint64_t)vg.bid * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nw = ((uint64_t)vg.nb * blockDim.x) >> 5;
     for (uint64_t u = gw; u < nunits; u += nw) {
         const uint64_t ubase = u * ug.U;
         const uint64_t ulen = n - ubase < ug.U ? n - ubase : ug.U;
@@ -342,7 +343,7 @@ __device__ __forceinline__ void append(unsigned long long &acc, uint32_t &nacc, 
 // at most 32 bits before they enter the accumulator, so each pair needs one
 // shift-in and one full-word test.
 template <bool CW32, bool PAIR>
-__device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW32> &tab, uint4 *slot)
+__device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW32> &tab, uint4 *slot, VGrid vg)
 {
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t n = a.n;
@@ -357,8 +358,8 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
     uint32_t *stream = reinterpret_cast<uint32_t *>(a.archive + L0.stream);
     const uint64_t stream_cap = a.capacity > L0.stream ? (a.capacity - L0.stream) / 4 : 0;
     const bool first_of_chunk = (lane & (G - 1)) == 0;
-    const uint64_t gw = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-    const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
+    const uint64_t gw = ((uint64_t)vg.bid * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)vg.nb * blockDim.x) >> 5;
     bool cap_err = false;
     for (uint64_t u = gw; u < nunits; u += nwarps) {
         const uint64_t ubase = u * ug.U;
@@ -606,14 +607,14 @@ constexpr uint32_t kCountSmemBins = 8192;
 constexpr uint32_t kPartWords = 16 * kPartStride;  // per warp, S <= 128
 
 __device__ __forceinline__ void count_dispatch(const EncodeArgs &a, uint64_t nunits, uint32_t *part, uint32_t *tab,
-                                               bool w32)
+                                               bool w32, VGrid vg)
 {
-    if (a.nbins <= kCountSmemBins) count_units(a, nunits, CountSmem{tab}, part);
-    else if (w32) count_units(a, nunits, CountGlobal<true>{Table<true>{a.cw32}}, part);
-    else count_units(a, nunits, CountGlobal<false>{Table<false>{a.cw64}}, part);
+    if (a.nbins <= kCountSmemBins) count_units(a, nunits, CountSmem{tab}, part, vg);
+    else if (w32) count_units(a, nunits, CountGlobal<true>{Table<true>{a.cw32}}, part, vg);
+    else count_units(a, nunits, CountGlobal<false>{Table<false>{a.cw64}}, part, vg);
 }
 
-__global__ void __launch_bounds__(kEncThreads, 4) k_encode_count(EncodeArgs a, uint64_t nunits)
+__device__ __forceinline__ void count_body(const EncodeArgs &a, uint64_t nunits, VGrid vg)
 {
     extern __shared__ uint32_t s_cnt[];
     uint32_t *part = s_cnt + (threadIdx.x >> 5) * kPartWords;
@@ -627,10 +628,15 @@ __global__ void __launch_bounds__(kEncThreads, 4) k_encode_count(EncodeArgs a, u
         }
         __syncthreads();
     }
-    count_dispatch(a, nunits, part, tab, w32);
+    count_dispatch(a, nunits, part, tab, w32, vg);
 }
 
-__global__ void __launch_bounds__(kEncThreads, 3) k_encode_pack(EncodeArgs a, uint64_t nunits, uint32_t use_smem)
+__global__ void __launch_bounds__(kEncThreads, 4) k_encode_count(const __grid_constant__ EncodeArgs a, uint64_t nunits)
+{
+    count_body(a, nunits, vgrid_self());
+}
+
+__device__ __forceinline__ void pack_body(const EncodeArgs &a, uint64_t nunits, uint32_t use_smem, VGrid vg)
 {
     extern __shared__ uint4 s_dyn[];
     uint4 *slot = s_dyn + (threadIdx.x >> 5) * (kRound / 8);  // 8 KB per warp
@@ -642,24 +648,37 @@ __global__ void __launch_bounds__(kEncThreads, 3) k_encode_pack(EncodeArgs a, ui
     const bool pair = w32 && a.ctl->maxlen <= 16;
     if (use_smem) {
         load_table(a, 1, s_tab, w32, pair);
-        if (pair) pack_units<true, true>(a, nunits, Table<true>{s_tab}, slot);
-        else if (w32) pack_units<true, false>(a, nunits, Table<true>{s_tab}, slot);
-        else pack_units<false, false>(a, nunits, Table<false>{s_tab}, slot);
+        if (pair) pack_units<true, true>(a, nunits, Table<true>{s_tab}, slot, vg);
+        else if (w32) pack_units<true, false>(a, nunits, Table<true>{s_tab}, slot, vg);
+        else pack_units<false, false>(a, nunits, Table<false>{s_tab}, slot, vg);
     } else {
-        if (w32) pack_units<true, false>(a, nunits, Table<true>{a.cw32}, slot);
-        else pack_units<false, false>(a, nunits, Table<false>{a.cw64}, slot);
+        if (w32) pack_units<true, false>(a, nunits, Table<true>{a.cw32}, slot, vg);
+        else pack_units<false, false>(a, nunits, Table<false>{a.cw64}, slot, vg);
     }
 }
 
-// exclusive scan of the unit totals (words, outliers | exceptions << 32)
-struct UnitOp {
-    using T = ulonglong2;
-    const ulonglong2 *tot;
-    ulonglong2 *off;
-    __device__ T load(uint64_t i) const { return tot[i]; }
-    __device__ void store(uint64_t i, T v) const { off[i] = v; }
-    __device__ void total(T) const {}
-};
+__global__ void __launch_bounds__(kEncThreads, 3) k_encode_pack(const __grid_constant__ EncodeArgs a, uint64_t nunits,
+                                                                uint32_t use_smem)
+{
+    pack_body(a, nunits, use_smem, vgrid_self());
+}
+
+// grouped: the count / pack of every field of a batch in one launch
+__global__ void __launch_bounds__(kEncThreads, 4) k_encode_count_group(const EncodeItem *items, const uint32_t *first,
+                                                                       uint32_t ni)
+{
+    VGrid vg;
+    const EncodeItem &e = items[group_item(first, ni, vg)];
+    count_body(e.a, e.nunits, vg);
+}
+
+__global__ void __launch_bounds__(kEncThreads, 3) k_encode_pack_group(const EncodeItem *items, const uint32_t *first,
+                                                                      uint32_t ni)
+{
+    VGrid vg;
+    const EncodeItem &e = items[group_item(first, ni, vg)];
+    pack_body(e.a, e.nunits, e.use_smem, vg);
+}
 
 // opt in to the dynamic shared memory the kernels need, once per device
 // (host threads may race here: the bits are atomic, and setting an attribute
@@ -674,6 +693,9 @@ void set_encode_smem()
     const size_t most = (size_t)kWarps * kRound * 2 + 4096 * 8;
     cudaFuncSetAttribute(k_encode_pack, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
     cudaFuncSetAttribute(k_encode_count, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)((kWarps * kPartWords + kCountSmemBins) * 4));
+    cudaFuncSetAttribute(k_encode_pack_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)most);
+    cudaFuncSetAttribute(k_encode_count_group, cudaFuncAttributeMaxDynamicSharedMemorySize,
                          (int)((kWarps * kPartWords + kCountSmemBins) * 4));
     done.fetch_or(bit);
 }
@@ -709,10 +731,38 @@ int launch_encode(const EncodeArgs &a, cudaStream_t st, int phase)
         k_encode_count<<<grid, kEncThreads, smem, st>>>(a, nunits);
         return 1;
     }
-    if (phase == 1) return launch_scan(UnitOp{a.unit_tot, a.unit_off}, nunits, a.scan_part, st);
+    if (phase == 1) return launch_scan(UnitScan{a.unit_tot, a.unit_off}, nunits, a.scan_part, st);
     const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)a.num_sms * 3));
     k_encode_pack<<<grid, kEncThreads, (size_t)kWarps * kRound * 2 + tab, st>>>(a, nunits, use_smem);
     return 1;
+}
+
+void encode_plan(const EncodeArgs &a, EncodeItem *it, uint32_t blocks[2], size_t smem[2], uint64_t *scan_items)
+{
+    const uint64_t nunits = encode_units(a.n, a.chunk);
+    it->a = a;
+    it->nunits = nunits;
+    it->use_smem = a.nbins <= 4096 ? 1u : 0u;
+    const uint64_t want = (nunits + kWarps - 1) / kWarps;
+    blocks[0] = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)a.num_sms * 4));
+    blocks[1] = (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)a.num_sms * 3));
+    smem[0] = (kWarps * kPartWords + (a.nbins <= kCountSmemBins ? a.nbins : 0)) * 4;
+    smem[1] = (size_t)kWarps * kRound * 2 + (it->use_smem ? (size_t)a.nbins * 8 : 0);
+    *scan_items = nunits;
+}
+
+void launch_encode_group(int phase, const EncodeItem *items, const uint32_t *first, uint32_t ni, uint32_t blocks,
+                         size_t smem, cudaStream_t st)
+{
+    set_encode_smem();
+    if (phase == 0) k_encode_count_group<<<blocks, kEncThreads, smem, st>>>(items, first, ni);
+    else k_encode_pack_group<<<blocks, kEncThreads, smem, st>>>(items, first, ni);
+}
+
+int launch_unit_scan_group(const ScanItem<UnitScan> *items, const uint32_t *first, uint32_t ni, uint32_t blocks,
+                           cudaStream_t st)
+{
+    return launch_scan_group(items, first, ni, blocks, st);
 }
 
 }  // namespace gbsz

@@ -62,12 +62,12 @@ __device__ __forceinline__ void mm_update(float v, uint32_t &kmax, uint32_t &kmi
 }
 
 template <bool VEC>
-__global__ void __launch_bounds__(256) k_minmax(const float *__restrict__ x, uint64_t n, Control *ctl,
-                                                double eb, uint32_t mode)
+__device__ __forceinline__ void minmax_body(const float *__restrict__ x, uint64_t n, Control *ctl, double eb,
+                                            uint32_t mode, VGrid vg)
 {
     uint32_t kmax = 0, kmin = 0;
-    const uint64_t tid = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t tid = (uint64_t)vg.bid * blockDim.x + threadIdx.x;
+    const uint64_t stride = (uint64_t)vg.nb * blockDim.x;
     if (VEC) {
         const float4 *x4 = reinterpret_cast<const float4 *>(x);
         const uint64_t n4 = n / 4;
@@ -116,7 +116,7 @@ __global__ void __launch_bounds__(256) k_minmax(const float *__restrict__ x, uin
         if (kmax) atomicMax(&ctl->max_key, kmax);
         if (kmin) atomicMax(&ctl->min_key_inv, kmin);
         __threadfence();
-        s_last = atomicAdd(&ctl->s0_done, 1u) == gridDim.x - 1;
+        s_last = atomicAdd(&ctl->s0_done, 1u) == vg.nb - 1;
     }
     __syncthreads();
     if (s_last && threadIdx.x == 0) {
@@ -127,7 +127,27 @@ __global__ void __launch_bounds__(256) k_minmax(const float *__restrict__ x, uin
     }
 }
 
+template <bool VEC>
+__global__ void __launch_bounds__(256) k_minmax(const float *__restrict__ x, uint64_t n, Control *ctl, double eb,
+                                                uint32_t mode)
+{
+    minmax_body<VEC>(x, n, ctl, eb, mode, vgrid_self());
+}
+
 __global__ void k_eb_abs(Control *ctl, double eb) { finalize_eb(ctl, eb, 0, 0, 0); }
+
+// grouped S0: an absolute bound takes one block (no reduction)
+template <bool VEC>
+__global__ void __launch_bounds__(256) k_minmax_group(const MinmaxItem *items, const uint32_t *first, uint32_t ni)
+{
+    VGrid vg;
+    const MinmaxItem &m = items[group_item(first, ni, vg)];
+    if (m.mode == 0) {
+        if (threadIdx.x == 0) finalize_eb(m.ctl, m.eb, 0, 0, 0);
+        return;
+    }
+    minmax_body<VEC>(m.x, m.n, m.ctl, m.eb, m.mode, vg);
+}
 
 // ---------------------------------------------------------------------------
 // S1-S3 shared pieces
@@ -280,7 +300,7 @@ __device__ __forceinline__ void unpack_central(HistState &h, uint32_t &pk)
 }
 
 template <bool VEC, bool WIN>
-__global__ void __launch_bounds__(kQ1Threads) k_dualquant_1d(QuantArgs a, uint32_t ntiles)
+__device__ __forceinline__ void dualquant_1d_body(const QuantArgs &a, uint32_t ntiles, VGrid vg)
 {
     extern __shared__ uint32_t sh_hist[];
     HistState h;
@@ -289,7 +309,7 @@ __global__ void __launch_bounds__(kQ1Threads) k_dualquant_1d(QuantArgs a, uint32
     if (a.ctl->error & DERR_EB) return;
     const EbScalars sc = load_scalars(a.ctl);
     const uint32_t n = (uint32_t)a.dims[0];
-    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (uint32_t tile = vg.bid; tile < ntiles; tile += vg.nb) {
         const uint32_t e0 = tile * kQ1Tile + threadIdx.x * kQ1Per;
         float v[kQ1Per];
         float vp = 0.0f;
@@ -365,6 +385,12 @@ __global__ void __launch_bounds__(kQ1Threads) k_dualquant_1d(QuantArgs a, uint32
     hist_flush(h, a.hist, a.ctl, WIN);
 }
 
+template <bool VEC, bool WIN>
+__global__ void __launch_bounds__(kQ1Threads) k_dualquant_1d(const __grid_constant__ QuantArgs a, uint32_t ntiles)
+{
+    dualquant_1d_body<VEC, WIN>(a, ntiles, vgrid_self());
+}
+
 // ---------------------------------------------------------------------------
 // 2D: 128 threads; tile 512 (x) x 8 (y) swept row by row.  Each thread holds
 // 4 points of a row (x = x0 + tid + 128 j).  Three row buffers of prequantized
@@ -376,7 +402,7 @@ constexpr int kQ2TX = 512;
 constexpr int kQ2TY = 8;
 
 template <bool WIN>
-__global__ void __launch_bounds__(kQ2Threads) k_dualquant_2d(QuantArgs a, uint32_t ntx, uint32_t nty)
+__device__ __forceinline__ void dualquant_2d_body(const QuantArgs &a, uint32_t ntx, uint32_t nty, VGrid vg)
 {
     extern __shared__ uint32_t sh_hist[];
     __shared__ int32_t rows[3][kQ2TX + 1];
@@ -390,7 +416,7 @@ __global__ void __launch_bounds__(kQ2Threads) k_dualquant_2d(QuantArgs a, uint32
     const uint32_t ntiles = ntx * nty;
     constexpr uint32_t B2 = lorenzo_block_extent(2);
     int buf = 0;
-    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (uint32_t tile = vg.bid; tile < ntiles; tile += vg.nb) {
         const uint32_t x0 = (tile % ntx) * kQ2TX;
         const int y0 = (int)((tile / ntx) * kQ2TY);
         const int y1 = (int)min(ny, (uint32_t)y0 + kQ2TY);
@@ -470,6 +496,13 @@ __global__ void __launch_bounds__(kQ2Threads) k_dualquant_2d(QuantArgs a, uint32
     hist_flush(h, a.hist, a.ctl, WIN);
 }
 
+template <bool WIN>
+__global__ void __launch_bounds__(kQ2Threads) k_dualquant_2d(const __grid_constant__ QuantArgs a, uint32_t ntx,
+                                                             uint32_t nty)
+{
+    dualquant_2d_body<WIN>(a, ntx, nty, vgrid_self());
+}
+
 // ---------------------------------------------------------------------------
 // 3D: 256 threads; tile 32 (x) x 32 (y) swept along z over tz planes.  Thread
 // (lx = tid % 32, ly = tid / 32 + 8 j) holds 4 points of a plane.  Threads
@@ -486,8 +519,8 @@ constexpr int kQ3Threads = 256;
 constexpr int kQ3T = 32;
 
 template <bool WIN>
-__global__ void __launch_bounds__(kQ3Threads) k_dualquant_3d(QuantArgs a, uint32_t ntx, uint32_t nty,
-                                                             uint32_t ntz, uint32_t tz)
+__device__ __forceinline__ void dualquant_3d_body(const QuantArgs &a, uint32_t ntx, uint32_t nty, uint32_t ntz,
+                                                  uint32_t tz, VGrid vg)
 {
     extern __shared__ uint32_t sh_hist[];
     __shared__ uint32_t rp[2][kQ3T + 1][kQ3T + 1];
@@ -511,7 +544,7 @@ __global__ void __launch_bounds__(kQ3Threads) k_dualquant_3d(QuantArgs a, uint32
         hy = -1;
     }
     int buf = 0;
-    for (uint32_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    for (uint32_t tile = vg.bid; tile < ntiles; tile += vg.nb) {
         const uint32_t x0 = (tile % ntx) * kQ3T, y0 = ((tile / ntx) % nty) * kQ3T;
         const int z0 = (int)((tile / (ntx * nty)) * tz), z1 = (int)min(nz, (uint32_t)z0 + tz);
         const uint32_t gx = x0 + lx;
@@ -610,6 +643,26 @@ __global__ void __launch_bounds__(kQ3Threads) k_dualquant_3d(QuantArgs a, uint32
     hist_flush(h, a.hist, a.ctl, WIN);
 }
 
+template <bool WIN>
+__global__ void __launch_bounds__(kQ3Threads) k_dualquant_3d(const __grid_constant__ QuantArgs a, uint32_t ntx,
+                                                             uint32_t nty, uint32_t ntz, uint32_t tz)
+{
+    dualquant_3d_body<WIN>(a, ntx, nty, ntz, tz, vgrid_self());
+}
+
+// grouped S1-S3: one launch per kernel variant over every field of the
+// variant (D = 1, 2, 3; VEC for D = 1)
+template <int D, bool VEC, bool WIN>
+__global__ void __launch_bounds__(D == 1 ? kQ1Threads : D == 2 ? kQ2Threads : kQ3Threads)
+    k_dualquant_group(const QuantItem *items, const uint32_t *first, uint32_t ni)
+{
+    VGrid vg;
+    const QuantItem &q = items[group_item(first, ni, vg)];
+    if (D == 1) dualquant_1d_body<VEC, WIN>(q.a, q.t[0], vg);
+    else if (D == 2) dualquant_2d_body<WIN>(q.a, q.t[0], q.t[1], vg);
+    else dualquant_3d_body<WIN>(q.a, q.t[0], q.t[1], q.t[2], q.t[3], vg);
+}
+
 // ---------------------------------------------------------------------------
 // Order n > 1 (Lorenzo predictor with binomial coefficients, Sec. 3.1.2).
 // The prequantized integers go to a scratch copy first, exceptions to a bit
@@ -693,6 +746,69 @@ void launch_minmax_eb(const float *x, uint64_t n, Control *ctl, double eb, uint3
         k_minmax<true><<<grid, 256, 0, st>>>(x, n, ctl, eb, mode);
     else
         k_minmax<false><<<grid, 256, 0, st>>>(x, n, ctl, eb, mode);
+}
+
+uint32_t minmax_blocks(uint64_t n, uint32_t mode, int num_sms)
+{
+    if (mode == 0) return 1;
+    const uint64_t need = (n / 4 + 255) / 256;
+    return (uint32_t)std::max<uint64_t>(1, std::min<uint64_t>(need, (uint64_t)num_sms * 8));
+}
+
+void launch_minmax_group(const MinmaxItem *items, const uint32_t *first, uint32_t ni, uint32_t blocks, bool vec,
+                         cudaStream_t st)
+{
+    if (vec) k_minmax_group<true><<<blocks, 256, 0, st>>>(items, first, ni);
+    else k_minmax_group<false><<<blocks, 256, 0, st>>>(items, first, ni);
+}
+
+uint32_t dualquant_plan(const QuantArgs &a, uint32_t t[4], int *variant, size_t *smem)
+{
+    const uint32_t nbins = 2 * a.radius;
+    const bool win = nbins <= kWinBins;
+    *smem = sizeof(uint32_t) * std::min<uint32_t>(nbins, kWinBins);
+    t[0] = t[1] = t[2] = t[3] = 0;
+    if (a.ndim == 1) {
+        const uint64_t n = a.dims[0];
+        t[0] = (uint32_t)((n + kQ1Tile - 1) / kQ1Tile);
+        const bool vec = (reinterpret_cast<uintptr_t>(a.x) & 15) == 0;
+        *variant = 4 + (vec ? 2 : 0) + (win ? 1 : 0);
+        return (uint32_t)std::min<uint64_t>(t[0], (uint64_t)a.num_sms * 8);
+    }
+    if (a.ndim == 2) {
+        t[0] = (uint32_t)((a.dims[0] + kQ2TX - 1) / kQ2TX);
+        t[1] = (uint32_t)((a.dims[1] + kQ2TY - 1) / kQ2TY);
+        *variant = 8 + (win ? 1 : 0);
+        return (uint32_t)std::min<uint64_t>((uint64_t)t[0] * t[1], (uint64_t)a.num_sms * 12);
+    }
+    const uint32_t ntx = (uint32_t)((a.dims[0] + kQ3T - 1) / kQ3T);
+    const uint32_t nty = (uint32_t)((a.dims[1] + kQ3T - 1) / kQ3T);
+    const uint64_t nz = a.dims[2];
+    uint64_t tz = nz;
+    while (tz > 4 && (uint64_t)ntx * nty * ((nz + tz - 1) / tz) < (uint64_t)a.num_sms * 8) tz = (tz + 1) / 2;
+    const uint32_t ntz = (uint32_t)((nz + tz - 1) / tz);
+    t[0] = ntx;
+    t[1] = nty;
+    t[2] = ntz;
+    t[3] = (uint32_t)tz;
+    *variant = 12 + (win ? 1 : 0);
+    return (uint32_t)std::min<uint64_t>((uint64_t)ntx * nty * ntz, (uint64_t)a.num_sms * 8);
+}
+
+void launch_dualquant_group(int variant, const QuantItem *items, const uint32_t *first, uint32_t ni,
+                            uint32_t blocks, size_t smem, cudaStream_t st)
+{
+    switch (variant) {
+    case 4: k_dualquant_group<1, false, false><<<blocks, kQ1Threads, smem, st>>>(items, first, ni); break;
+    case 5: k_dualquant_group<1, false, true><<<blocks, kQ1Threads, smem, st>>>(items, first, ni); break;
+    case 6: k_dualquant_group<1, true, false><<<blocks, kQ1Threads, smem, st>>>(items, first, ni); break;
+    case 7: k_dualquant_group<1, true, true><<<blocks, kQ1Threads, smem, st>>>(items, first, ni); break;
+    case 8: k_dualquant_group<2, false, false><<<blocks, kQ2Threads, smem, st>>>(items, first, ni); break;
+    case 9: k_dualquant_group<2, false, true><<<blocks, kQ2Threads, smem, st>>>(items, first, ni); break;
+    case 12: k_dualquant_group<3, false, false><<<blocks, kQ3Threads, smem, st>>>(items, first, ni); break;
+    case 13: k_dualquant_group<3, false, true><<<blocks, kQ3Threads, smem, st>>>(items, first, ni); break;
+    default: break;
+    }
 }
 
 int launch_dualquant(const QuantArgs &a, cudaStream_t st)

@@ -48,22 +48,22 @@ template <> __device__ __forceinline__ ulonglong2 scan_zero<ulonglong2>() { retu
 // Op provides: using T; T load(uint64_t i) const; void store(uint64_t i, T v) const;
 // void check(uint64_t i) const (optional validation, may be empty)
 template <typename Op>
-__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Op op, uint64_t n, typename Op::T *partial)
+__device__ __forceinline__ void scan_reduce_body(const Op &op, uint64_t n, typename Op::T *partial, uint32_t bid)
 {
     using T = typename Op::T;
     __shared__ unsigned long long sh[66];
-    const uint64_t base = blockIdx.x * kScanBlock + (uint64_t)threadIdx.x * kScanPer;
+    const uint64_t base = bid * kScanBlock + (uint64_t)threadIdx.x * kScanPer;
     T s = scan_zero<T>();
 #pragma unroll
     for (int j = 0; j < kScanPer; j++)
         if (base + j < n) s += op.load(base + j);
     T tot;
     block_excl_scan_t(s, sh, &tot);
-    if (threadIdx.x == 0) partial[blockIdx.x] = tot;
+    if (threadIdx.x == 0) partial[bid] = tot;
 }
 
 template <typename Op>
-__global__ void __launch_bounds__(kScanThreads) k_scan_top(Op op, uint64_t nb, typename Op::T *partial)
+__device__ __forceinline__ void scan_top_body(const Op &op, uint64_t nb, typename Op::T *partial)
 {
     using T = typename Op::T;
     __shared__ unsigned long long sh[66];
@@ -82,11 +82,11 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_top(Op op, uint64_t nb, t
 }
 
 template <typename Op>
-__global__ void __launch_bounds__(kScanThreads) k_scan_apply(Op op, uint64_t n, const typename Op::T *partial)
+__device__ __forceinline__ void scan_apply_body(const Op &op, uint64_t n, const typename Op::T *partial, uint32_t bid)
 {
     using T = typename Op::T;
     __shared__ unsigned long long sh[66];
-    const uint64_t base = blockIdx.x * kScanBlock + (uint64_t)threadIdx.x * kScanPer;
+    const uint64_t base = bid * kScanBlock + (uint64_t)threadIdx.x * kScanPer;
     T v[kScanPer];
     T s = scan_zero<T>();
 #pragma unroll
@@ -95,12 +95,30 @@ __global__ void __launch_bounds__(kScanThreads) k_scan_apply(Op op, uint64_t n, 
         s += v[j];
     }
     T tot;
-    T run = block_excl_scan_t(s, sh, &tot) + partial[blockIdx.x];
+    T run = block_excl_scan_t(s, sh, &tot) + partial[bid];
 #pragma unroll
     for (int j = 0; j < kScanPer; j++) {
         if (base + j < n) op.store(base + j, run);
         run += v[j];
     }
+}
+
+template <typename Op>
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce(Op op, uint64_t n, typename Op::T *partial)
+{
+    scan_reduce_body(op, n, partial, blockIdx.x);
+}
+
+template <typename Op>
+__global__ void __launch_bounds__(kScanThreads) k_scan_top(Op op, uint64_t nb, typename Op::T *partial)
+{
+    scan_top_body(op, nb, partial);
+}
+
+template <typename Op>
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply(Op op, uint64_t n, const typename Op::T *partial)
+{
+    scan_apply_body(op, n, partial, blockIdx.x);
 }
 
 // partial: scratch of at least ceil(n / kScanBlock) entries
@@ -114,6 +132,48 @@ inline int launch_scan(const Op &op, uint64_t n, typename Op::T *partial, cudaSt
     k_scan_apply<Op><<<(unsigned)nb, kScanThreads, 0, st>>>(op, n, partial);
     return 3;
 }
+
+// Grouped: the scans of many fields in three launches.  Item provides
+// using Op; Op op() const; uint64_t n; typename Op::T *partial.  Item i owns
+// ceil(n / kScanBlock) blocks of the reduce and apply grids (first[]) and
+// block i of the top grid.
+template <typename Item>
+__global__ void __launch_bounds__(kScanThreads) k_scan_reduce_group(const Item *items, const uint32_t *first,
+                                                                   uint32_t ni)
+{
+    VGrid vg;
+    const Item &it = items[group_item(first, ni, vg)];
+    scan_reduce_body(it.op(), it.n, it.partial, vg.bid);
+}
+
+template <typename Item>
+__global__ void __launch_bounds__(kScanThreads) k_scan_top_group(const Item *items)
+{
+    const Item &it = items[blockIdx.x];
+    scan_top_body(it.op(), (it.n + kScanBlock - 1) / kScanBlock, it.partial);
+}
+
+template <typename Item>
+__global__ void __launch_bounds__(kScanThreads) k_scan_apply_group(const Item *items, const uint32_t *first,
+                                                                  uint32_t ni)
+{
+    VGrid vg;
+    const Item &it = items[group_item(first, ni, vg)];
+    scan_apply_body(it.op(), it.n, it.partial, vg.bid);
+}
+
+// blocks = first[ni] (every item with n >= 1); returns kernels launched
+template <typename Item>
+inline int launch_scan_group(const Item *items, const uint32_t *first, uint32_t ni, uint32_t blocks, cudaStream_t st)
+{
+    if (ni == 0 || blocks == 0) return 0;
+    k_scan_reduce_group<Item><<<blocks, kScanThreads, 0, st>>>(items, first, ni);
+    k_scan_top_group<Item><<<ni, kScanThreads, 0, st>>>(items);
+    k_scan_apply_group<Item><<<blocks, kScanThreads, 0, st>>>(items, first, ni);
+    return 3;
+}
+
+inline uint64_t scan_blocks(uint64_t n) { return (n + kScanBlock - 1) / kScanBlock; }
 
 inline uint64_t scan_partials(uint64_t n) { return (n + kScanBlock - 1) / kScanBlock + 1; }
 

@@ -56,6 +56,7 @@ SIGNATURES = {
     "gbsz_scratch_bytes": ([_P, C.c_int, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int),
 }
 OPT_CODEWORD_BITS = 1
+OPT_BATCH_MODE = 3
 
 
 class GbszError(RuntimeError):

@@ -1,7 +1,9 @@
 """Batched compress/decompress: every field of a batch gives exactly the
 bytes (archive) and floats (reconstruction) that a single-field call gives,
-and the oracle too; fields run on several internal streams, so this also
-checks that no state leaks between concurrently running fields."""
+and the oracle too.  Batch compress runs every stage of all fields in one
+launch per kernel (grouped) or the fields' own launches on several internal
+streams; both are checked, so this also checks that no state leaks between
+fields running together."""
 import numpy as np
 import pytest
 import torch
@@ -231,3 +233,49 @@ def test_profiling_survives_graph_replay(gb, ctx):
     oa = ref.compress(f, 1e-4, ref.EB_REL, 512, gb.auto_chunk([f.size]))
     assert nb == oa.size and np.array_equal(arc[:nb].cpu().numpy(), oa)
     assert np.array_equal(y.cpu().numpy().view(np.uint32), ref.decompress(oa).view(np.uint32))
+
+
+def test_grouped_batch_equals_slot_streams_and_oracle(gb, ctx):
+    """One launch per stage for the whole batch: ranks 1-4, absolute and
+    relative bounds, radii from 64 to 32768, chunks 64 to 8192, the per-block
+    mode, a field whose pointer is not 16-byte aligned; the archives equal
+    the slot-stream path's and the oracle's."""
+    rng = np.random.default_rng(950)
+    kinds = [("walk", (70001,)), ("sinus", (90, 131)), ("lognormal", (17, 23, 29)), ("walk", (1,)),
+             ("grf", (200, 300)), ("sinus", (3, 4, 19, 21)), ("walk", (300007,)), ("lognormal", (40, 40, 41))]
+    fields, params, ts = [], [], []
+    base = torch.empty(400_000, dtype=torch.float32, device="cuda")
+    for i, (kind, shape) in enumerate(kinds):
+        f = workloads.field_for(kind if len(shape) < 4 else "sinus", shape if len(shape) < 4 else shape[1:],
+                                seed=960 + i)
+        if len(shape) == 4:
+            f = np.concatenate([f[None] * (1 + 0.01 * k) for k in range(shape[0])]).astype(np.float32)
+        fields.append(f)
+        if i == 6:  # a view 4 bytes into a buffer: not 16-byte aligned
+            t = base[1:1 + f.size].view(f.shape)
+            t.copy_(torch.from_numpy(f))
+        else:
+            t = torch.from_numpy(f).cuda()
+        ts.append(t)
+        mode = gb.EB_ABS if i % 3 == 2 else gb.EB_REL
+        eb = 1e-3 if mode == gb.EB_ABS else [1e-4, 1e-3, 1e-2][i % 3]
+        R = [512, 64, 32768, 512][i % 4]
+        C = [0, 64, 256, 8192][i % 4]
+        params.append(gb.make_params(gb.field_dims(t), eb, mode, R, C, lblock=1 if i in (1, 4) else 0))
+    torch.cuda.synchronize()
+    results = {}
+    for mode_ in (0, 1):
+        ctx.set_option(gb.OPT_BATCH_MODE, mode_)
+        try:
+            arcs, nbs, sts = ctx.compress_batch(ts, None, params=params)
+            torch.cuda.synchronize()
+        finally:
+            ctx.set_option(gb.OPT_BATCH_MODE, 0)
+        assert all(s_ == gb.OK for s_ in sts), sts
+        results[mode_] = [a[:n].cpu().numpy() for a, n in zip(arcs, nbs)]
+    for i, f in enumerate(fields):
+        p = params[i]
+        oa = ref.compress(f, p.eb, p.eb_mode, p.radius, p.chunk or gb.auto_chunk(list(f.shape)[::-1], p.radius),
+                          lblock=p.lorenzo_block)
+        assert np.array_equal(results[0][i], results[1][i]), i
+        assert np.array_equal(results[0][i], oa), i
