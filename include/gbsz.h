@@ -103,12 +103,14 @@ void gbsz_destroy(gbsz_ctx *ctx);
  *     encode/deflate table, for comparison).
  * Errors: INVALID_ARG (NULL context, unknown option or value). */
 #define GBSZ_OPT_CODEWORD_BITS 1
-/*   GBSZ_OPT_BATCH_MODE  how gbsz_compress_batch runs a batch: 0 (default) =
- *     one launch per stage for all fields (each field owning a range of the
- *     grid's blocks) when the batch has at least two fields, all of Lorenzo
- *     order 1, averaging at most 2^21 points; otherwise every field's own
- *     launches on up to 8 slot streams; 1 = always the slot streams (for
- *     comparison).  The archives are the same bytes either way. */
+/*   GBSZ_OPT_BATCH_MODE  how gbsz_compress_batch and gbsz_decompress_batch
+ *     run a batch: 0 (default) = one launch per stage (per kernel variant)
+ *     for all fields, each field owning a range of the grid's blocks (its
+ *     tiles, units or chunks), when the batch has at least two fields, all
+ *     of Lorenzo order 1, averaging at most 2^21 points; otherwise every
+ *     field's own launches on up to 8 slot streams; 1 = always the slot
+ *     streams (for comparison).  The results are the same bytes either
+ *     way. */
 #define GBSZ_OPT_BATCH_MODE 3
 gbsz_status gbsz_set_option(gbsz_ctx *ctx, int option, int64_t value);
 

@@ -11,6 +11,8 @@
 
 #include <cstdint>
 #include <cuda_runtime.h>
+#include <functional>
+#include <vector>
 
 namespace gbsz {
 
@@ -476,6 +478,7 @@ void launch_encode_group(int phase, const EncodeItem *items, const uint32_t *fir
                          size_t smem, cudaStream_t st);  // phase 0: count, 1: pack
 int launch_unit_scan_group(const ScanItem<UnitScan> *items, const uint32_t *first, uint32_t ni, uint32_t blocks,
                            cudaStream_t st);
+void launch_decode_tables_group(const CodebookArgs *items, uint32_t count, cudaStream_t st);  // one CTA per field
 uint64_t encode_units(uint64_t n, uint32_t chunk);        // units (per-unit totals) of the encoder
 uint32_t encode_unit_shift(uint32_t chunk);                // log2 of the encoder unit in points
 
@@ -501,6 +504,54 @@ constexpr uint32_t kRecon1DTile = 512;  // 1D reconstruction tile (points): one 
 // phase 0: chunk word offsets (scan), 1: symbols; returns kernels launched
 int launch_decode(const DecodeArgs &a, cudaStream_t st, int phase);
 
+// chunk word offsets: the exclusive prefix sum of ceil(bits / 32) over the
+// archive's chunk table; a count above the longest chunk, or a total other
+// than the header's, marks the archive corrupt
+struct ChunkWords {
+    using T = unsigned long long;
+    const uint32_t *bits;
+    unsigned long long *off;
+    unsigned long long words, maxbits;
+    Control *ctl;
+    __device__ T load(uint64_t i) const
+    {
+        const uint32_t b = bits[i];
+        if (b > maxbits) {
+            atomicOr(&ctl->error, DERR_CORRUPT);
+            return 0;
+        }
+        return (b + 31ull) / 32;
+    }
+    __device__ void store(uint64_t i, T v) const { off[i] = v; }
+    __device__ void total(T t) const
+    {
+        if (t != words) atomicOr(&ctl->error, DERR_CORRUPT);
+    }
+};
+inline ChunkWords chunk_words_op(const DecodeArgs &a)
+{
+    ChunkWords op;
+    op.bits = reinterpret_cast<const uint32_t *>(a.archive + a.off_bits);
+    op.off = a.chunk_off;
+    op.words = a.words;
+    op.maxbits = (unsigned long long)a.chunk * kMaxLen;
+    op.ctl = a.ctl;
+    return op;
+}
+
+// grouped S7 (items and block tables in device memory)
+struct DecodeItem {
+    DecodeArgs a;
+    uint32_t sorted_in_smem;
+};
+// one field's decoder launch: blocks, variant (2: complete-table decoder,
+// + 1: tiles of several chunks) and dynamic shared memory
+unsigned decode_plan(const DecodeArgs &a, DecodeItem *it, int *variant, size_t *dyn);
+void launch_decode_group(int variant, const DecodeItem *items, const uint32_t *first, uint32_t ni, uint32_t blocks,
+                         size_t dyn, cudaStream_t st);
+int launch_offsets_scan_group(const ScanItem<ChunkWords> *items, const uint32_t *first, uint32_t ni, uint32_t blocks,
+                              cudaStream_t st);
+
 struct ReconArgs {
     const uint16_t *codes;
     const uint8_t *archive;
@@ -522,5 +573,14 @@ struct ReconArgs {
 };
 uint64_t recon_faces_entries(uint32_t ndim, const uint64_t dims[3]);
 void launch_reconstruct(const ReconArgs &a, cudaStream_t st, int *launches);
+
+// A launch of a grouped plan: given the plan's device address, enqueues its
+// kernels on st and returns how many.
+using GroupLaunch = std::function<int(const uint8_t *, cudaStream_t)>;
+// Appends the grouped S8 of `count` order-1 fields to `plan` (host bytes,
+// copied to the device before the launches run) and its launches, in stage
+// order, to `launches`.
+void plan_reconstruct_group(const ReconArgs *ra, uint32_t count, std::vector<uint8_t> &plan,
+                            std::vector<GroupLaunch> &launches);
 
 }  // namespace gbsz

@@ -237,7 +237,7 @@ struct gbsz_ctx {
     // options
     uint32_t cw64_only = 0;  // GBSZ_OPT_CODEWORD_BITS = 64
     // captured batch calls, and captured single-field calls
-    BatchGraph gcomp, gdecomp, gsc, gsd, ggcomp;
+    BatchGraph gcomp, gdecomp, gsc, gsd, ggcomp, ggdecomp;
     // grouped batch calls: every field's scratch in one arena, the launch
     // plan (items and block tables) built in pinned memory and copied over
     Buf garena, gplan_dev;
@@ -1099,6 +1099,229 @@ gbsz_status compress_batch_grouped(gbsz_ctx *c, uint32_t count, const float *con
     return run_batch(c, c->ggcomp, key, st, enqueue);
 }
 
+// One field's decompress scratch in the arena (base = nullptr only sizes it).
+struct FieldDScratch {
+    Control *ctl;
+    uint32_t *lut, *count, *start;
+    void *lutf;
+    unsigned long long *first;
+    uint16_t *sorted, *codes;
+    int2 *dscr;
+    unsigned long long *chunk_off;
+    uint32_t *faces;
+    void *scan_part;
+};
+
+uint64_t layout_dfield(uint8_t *base, const Header &h, FieldDScratch *f)
+{
+    const uint64_t n = h.n, nb = 2ull * h.p.radius;
+    uint64_t gd[3];
+    const uint64_t nfaces = recon_faces_entries(lorenzo_geom(h.p, gd), gd);
+    uint64_t off = 0;
+    auto take = [&](uint64_t bytes) -> void * {
+        void *q = base ? base + off : nullptr;
+        off += up256(bytes);
+        return q;
+    };
+    f->ctl = static_cast<Control *>(take(sizeof(Control)));
+    f->lut = static_cast<uint32_t *>(take(((1u << kLutBits) + kLut2Words) * 4));
+    f->lutf = take(kFastLutBytes);
+    f->first = static_cast<unsigned long long *>(take((kMaxLen + 2) * 8));
+    f->count = static_cast<uint32_t *>(take((kMaxLen + 2) * 4));
+    f->start = static_cast<uint32_t *>(take((kMaxLen + 2) * 4));
+    f->sorted = static_cast<uint16_t *>(take(nb * 2));
+    f->codes = static_cast<uint16_t *>(take(n * 2 + 64));
+    f->dscr = static_cast<int2 *>(take(n * 8 + 64));
+    f->chunk_off = static_cast<unsigned long long *>(take(h.nchunk * 8 + 8));
+    f->faces = static_cast<uint32_t *>(take(nfaces * 4 + 16));
+    f->scan_part = take(scan_partials(std::max<uint64_t>(h.nchunk, nfaces)) * 8 + 64);
+    return off;
+}
+
+bool dgroupable(uint32_t count, const std::vector<Header> &hs, const gbsz_status *statuses)
+{
+    if (count < 2) return false;
+    uint64_t total = 0;
+    for (uint32_t i = 0; i < count; i++) {
+        if (statuses[i] != GBSZ_OK || order_of(hs[i].p) != 1) return false;
+        total += hs[i].n;
+    }
+    return total <= kGroupedMeanPoints * count;
+}
+
+gbsz_status decompress_batch_grouped(gbsz_ctx *c, uint32_t count, const std::vector<Header> &hs,
+                                     const void *const *d_archives, float *const *d_fields,
+                                     std::vector<uint64_t> &key, cudaStream_t st)
+{
+    std::vector<uint64_t> foff(count + 1, 0);
+    FieldDScratch tmp;
+    for (uint32_t i = 0; i < count; i++) foff[i + 1] = foff[i] + layout_dfield(nullptr, hs[i], &tmp);
+    if (!c->garena.ensure(foff[count])) return GBSZ_ERR_OOM;
+    uint8_t *arena = c->garena.as<uint8_t>();
+    std::vector<FieldDScratch> fs(count);
+    for (uint32_t i = 0; i < count; i++) layout_dfield(arena + foff[i], hs[i], &fs[i]);
+
+    std::vector<CodebookArgs> tab(count);
+    std::vector<ScanItem<ChunkWords>> osc;
+    std::vector<uint32_t> osc_b;
+    std::vector<DecodeItem> di(count);
+    std::vector<int> dvar(count);
+    std::vector<uint32_t> d_b(count);
+    size_t d_smem[4] = {0, 0, 0, 0};
+    std::vector<ReconArgs> ra(count);
+    std::vector<ZeroRange> zr;
+    std::vector<Control *> ctls(count);
+    for (uint32_t i = 0; i < count; i++) {
+        const Header &h = hs[i];
+        const FieldDScratch &f = fs[i];
+        const uint8_t *arc = static_cast<const uint8_t *>(d_archives[i]);
+        uint64_t gd[3];
+        const uint32_t gnd = lorenzo_geom(h.p, gd);
+        const uint64_t nfaces = recon_faces_entries(gnd, gd);
+        const bool tile_sums = gnd == 1 && !h.p.lorenzo_block;
+        zr.push_back({f.ctl, sizeof(Control)});
+        if (tile_sums) zr.push_back({f.faces, nfaces * 4});
+        ctls[i] = f.ctl;
+        CodebookArgs &cb = tab[i];
+        cb = CodebookArgs{};
+        cb.len_in = arc + kHeaderBytes;
+        cb.nbins = 2 * h.p.radius;
+        cb.expect_maxlen = h.maxlen;
+        cb.fast_bits = fast_lut_bits(h.maxlen, cb.nbins);
+        cb.fast_pair = 0;
+        cb.lut = f.lut;
+        cb.lutf = f.lutf;
+        cb.first = f.first;
+        cb.count = f.count;
+        cb.start = f.start;
+        cb.sorted = f.sorted;
+        cb.ctl = f.ctl;
+        DecodeArgs d{};
+        d.archive = arc;
+        d.n = h.n;
+        d.chunk = h.p.chunk;
+        d.nchunk = (uint32_t)h.nchunk;
+        d.radius = h.p.radius;
+        d.maxlen = h.maxlen;
+        d.words = h.w;
+        d.off_bits = h.L.bits;
+        d.off_stream = h.L.stream;
+        d.lut = f.lut;
+        d.first = f.first;
+        d.count = f.count;
+        d.start = f.start;
+        d.sorted = f.sorted;
+        d.lutf = f.lutf;
+        d.fast_bits = cb.fast_bits;
+        d.fast_pair = 0;
+        d.num_sms = c->num_sms;
+        d.chunk_off = f.chunk_off;
+        d.scan_partial = static_cast<unsigned long long *>(f.scan_part);
+        d.tile_sums = tile_sums ? f.faces : nullptr;
+        d.codes = f.codes;
+        d.ctl = f.ctl;
+        osc.push_back(ScanItem<ChunkWords>{chunk_words_op(d), h.nchunk, d.scan_partial});
+        osc_b.push_back((uint32_t)scan_blocks(h.nchunk));
+        size_t dyn = 0;
+        d_b[i] = decode_plan(d, &di[i], &dvar[i], &dyn);
+        d_smem[dvar[i]] = std::max(d_smem[dvar[i]], dyn);
+        ReconArgs &r = ra[i];
+        r = ReconArgs{};
+        r.codes = f.codes;
+        r.archive = arc;
+        r.off_outl = h.L.outl;
+        r.off_exc = h.L.exc;
+        r.m = h.m;
+        r.e = h.e;
+        r.ndim = gnd;
+        for (int k = 0; k < 3; k++) r.dims[k] = gd[k];
+        r.radius = h.p.radius;
+        r.ebx2 = h.ebx2;
+        r.dscr = reinterpret_cast<int32_t *>(f.dscr);
+        r.lblock = h.p.lorenzo_block;
+        r.order = 1;
+        r.faces = f.faces;
+        r.faces_cap = nfaces;
+        r.scan_partial = static_cast<uint32_t *>(f.scan_part);
+        r.out = d_fields[i];
+        r.ctl = f.ctl;
+        r.num_sms = c->num_sms;
+    }
+    PlanBuilder pb;
+    const uint64_t o_zr = pb.put(zr.data(), zr.size());
+    const uint64_t o_tab = pb.put(tab.data(), count);
+    const uint64_t o_osc = pb.put(osc.data(), osc.size());
+    const std::vector<uint32_t> oscf = firsts(osc_b);
+    const uint64_t o_oscf = pb.put(oscf.data(), oscf.size());
+    struct DGroup {
+        int variant;
+        uint32_t ni, blocks;
+        uint64_t o_items, o_first;
+    };
+    std::vector<DGroup> dg;
+    for (int v = 0; v < 4; v++) {
+        std::vector<DecodeItem> items;
+        std::vector<uint32_t> bl;
+        for (uint32_t i = 0; i < count; i++)
+            if (dvar[i] == v) {
+                items.push_back(di[i]);
+                bl.push_back(d_b[i]);
+            }
+        if (items.empty()) continue;
+        const std::vector<uint32_t> f = firsts(bl);
+        DGroup g{v, (uint32_t)items.size(), f.back(), 0, 0};
+        g.o_items = pb.put(items.data(), items.size());
+        g.o_first = pb.put(f.data(), f.size());
+        dg.push_back(g);
+    }
+    std::vector<GroupLaunch> recon;
+    plan_reconstruct_group(ra.data(), count, pb.buf, recon);
+    const uint64_t o_ctl = pb.put(ctls.data(), ctls.size());
+    const uint64_t o_cdst = pb.put<uint8_t>(nullptr, 0);
+    pb.buf.resize(o_cdst + (uint64_t)count * sizeof(Control));
+    const uint64_t plan_bytes = pb.buf.size();
+    if (!c->gplan_host.ensure(plan_bytes) || !c->gplan_dev.ensure(plan_bytes)) return GBSZ_ERR_OOM;
+    std::memcpy(c->gplan_host.p, pb.buf.data(), plan_bytes);
+    uint8_t *dp = c->gplan_dev.as<uint8_t>();
+    key.push_back(0x6Du);  // grouped
+    key.push_back((uint64_t)(uintptr_t)c->gplan_host.p);
+    key.push_back((uint64_t)(uintptr_t)dp);
+    key.push_back((uint64_t)(uintptr_t)arena);
+
+    auto enqueue = [&]() -> gbsz_status {
+        int nl = 0;
+        cudaEvent_t e0;
+        cudaMemcpyAsync(dp, c->gplan_host.p, plan_bytes, cudaMemcpyHostToDevice, st);
+        k_zero_group<<<(unsigned)std::min<size_t>(zr.size(), (size_t)c->num_sms * 8), 256, 0, st>>>(
+            reinterpret_cast<const ZeroRange *>(dp + o_zr), (uint32_t)zr.size());
+        stage_begin(c, st, &e0);
+        launch_decode_tables_group(reinterpret_cast<const CodebookArgs *>(dp + o_tab), count, st);
+        stage_end(c, st, 6, e0);
+        stage_begin(c, st, &e0);
+        nl += launch_offsets_scan_group(reinterpret_cast<const ScanItem<ChunkWords> *>(dp + o_osc),
+                                        reinterpret_cast<const uint32_t *>(dp + o_oscf), count, oscf.back(), st);
+        stage_end(c, st, 7, e0);
+        stage_begin(c, st, &e0);
+        for (const DGroup &g : dg) {
+            launch_decode_group(g.variant, reinterpret_cast<const DecodeItem *>(dp + g.o_items),
+                                reinterpret_cast<const uint32_t *>(dp + g.o_first), g.ni, g.blocks,
+                                d_smem[g.variant], st);
+            nl++;
+        }
+        stage_end(c, st, 8, e0);
+        stage_begin(c, st, &e0);
+        for (const GroupLaunch &l : recon) nl += l(dp, st);
+        stage_end(c, st, 9, e0);
+        Control *cdst = reinterpret_cast<Control *>(dp + o_cdst);
+        k_gather_ctl<<<(unsigned)std::min<uint32_t>(count, (uint32_t)c->num_sms * 4), 64, 0, st>>>(
+            reinterpret_cast<Control *const *>(dp + o_ctl), count, cdst);
+        cudaMemcpyAsync(c->ctl_host.p, cdst, (size_t)count * sizeof(Control), cudaMemcpyDeviceToHost, st);
+        c->launches += 3 + nl;
+        return cudaGetLastError() == cudaSuccess ? GBSZ_OK : GBSZ_ERR_CUDA;
+    };
+    return run_batch(c, c->ggdecomp, key, st, enqueue);
+}
+
 }  // namespace
 
 extern "C" {
@@ -1168,6 +1391,7 @@ void gbsz_destroy(gbsz_ctx *c)
     c->gsc.drop();
     c->gsd.drop();
     c->ggcomp.drop();
+    c->ggdecomp.drop();
     c->garena.release();
     c->gplan_dev.release();
     c->gplan_host.release();
@@ -1181,7 +1405,7 @@ void gbsz_destroy(gbsz_ctx *c)
         cudaEventDestroy(r.a);
         cudaEventDestroy(r.b);
     }
-    for (BatchGraph *bg : {&c->gcomp, &c->gdecomp, &c->gsc, &c->gsd, &c->ggcomp})
+    for (BatchGraph *bg : {&c->gcomp, &c->gdecomp, &c->gsc, &c->gsd, &c->ggcomp, &c->ggdecomp})
         for (auto &r : bg->recs) {
             cudaEventDestroy(r.a);
             cudaEventDestroy(r.b);
@@ -1496,7 +1720,8 @@ gbsz_status gbsz_decompress_batch(gbsz_ctx *c, uint32_t count, const void *const
         statuses[i] = parse_header(c->h_header.p + (size_t)i * kHeaderBytes, bytes[i], &hs[i]);
         if (statuses[i] == GBSZ_OK && hs[i].n > capacities[i]) statuses[i] = GBSZ_ERR_CAPACITY;
     }
-    for (uint32_t i = 0; i < count; i++)
+    const bool grouped = c->batch_mode == 0 && dgroupable(count, hs, statuses);
+    for (uint32_t i = 0; i < count && !grouped; i++)
         if (statuses[i] == GBSZ_OK && !reserve_decompress(c->slots[i % K], hs[i])) statuses[i] = GBSZ_ERR_OOM;
     std::vector<uint64_t> key{0xDEu, count, (uint64_t)K, (uint64_t)(uintptr_t)c->ctl_host.p};
     for (uint32_t i = 0; i < count; i++) {
@@ -1505,6 +1730,18 @@ gbsz_status gbsz_decompress_batch(gbsz_ctx *c, uint32_t count, const void *const
         key_add(key, &bytes[i], sizeof(size_t));
         key.push_back((uint64_t)statuses[i]);
         if (statuses[i] == GBSZ_OK) key_add(key, c->h_header.p + (size_t)i * kHeaderBytes, kHeaderBytes);
+    }
+    if (grouped) {
+        const gbsz_status gs = decompress_batch_grouped(c, count, hs, d_archives, d_fields, key, st);
+        if (gs != GBSZ_OK) return gs;
+        if (cudaStreamSynchronize(st) != cudaSuccess || cudaGetLastError() != cudaSuccess) return GBSZ_ERR_CUDA;
+        prof_collect(c);
+        gbsz_status first = GBSZ_OK;
+        for (uint32_t i = 0; i < count; i++) {
+            statuses[i] = decompress_status(c->ctl_host.p[i], hs[i]);
+            if (first == GBSZ_OK) first = statuses[i];
+        }
+        return first;
     }
     auto enqueue = [&]() -> gbsz_status {
         cudaEventRecord(c->fork, st);
@@ -1646,7 +1883,9 @@ gbsz_status gbsz_debug_copy(gbsz_ctx *c, int which, void *h_dst, size_t bytes)
         // batch compress: the slot-stream graphs and the grouped ones together
         const uint64_t cap = gc.captures + (which == 5 ? c->ggcomp.captures : 0);
         const uint64_t rep = gc.replays + (which == 5 ? c->ggcomp.replays : 0);
-        const uint64_t v[4] = {cap, rep, gd.captures, gd.replays};
+        const uint64_t dcap = gd.captures + (which == 5 ? c->ggdecomp.captures : 0);
+        const uint64_t drep = gd.replays + (which == 5 ? c->ggdecomp.replays : 0);
+        const uint64_t v[4] = {cap, rep, dcap, drep};
         std::memcpy(h_dst, v, 32);
         return GBSZ_OK;
     }
@@ -1681,7 +1920,7 @@ gbsz_status gbsz_release_scratch(gbsz_ctx *c)
         cudaGetLastError();
         return GBSZ_ERR_CUDA;
     }
-    for (BatchGraph *bg : {&c->gcomp, &c->gdecomp, &c->gsc, &c->gsd, &c->ggcomp}) {
+    for (BatchGraph *bg : {&c->gcomp, &c->gdecomp, &c->gsc, &c->gsd, &c->ggcomp, &c->ggdecomp}) {
         bg->drop();
         bg->seen.clear();
     }

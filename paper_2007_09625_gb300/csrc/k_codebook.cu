@@ -379,7 +379,7 @@ __global__ void __launch_bounds__(kCbThreads, 1) k_codebook_group(const Codebook
 // <= 45, the header's maximum matches, Kraft sum <= 1), then builds the
 // canonical tables and a 2^12-entry lookup of (symbol, length) for codes of
 // at most 12 bits.
-__global__ void __launch_bounds__(kCbThreads, 1) k_decode_tables(CodebookArgs a)
+__device__ __forceinline__ void decode_tables_body(const CodebookArgs &a)
 {
     extern __shared__ uint32_t s_cnt[];
     __shared__ Canon canon;
@@ -482,6 +482,17 @@ __global__ void __launch_bounds__(kCbThreads, 1) k_decode_tables(CodebookArgs a)
     }
 }
 
+__global__ void __launch_bounds__(kCbThreads, 1) k_decode_tables(const __grid_constant__ CodebookArgs a)
+{
+    decode_tables_body(a);
+}
+
+// grouped: block i builds field i's decode tables
+__global__ void __launch_bounds__(kCbThreads, 1) k_decode_tables_group(const CodebookArgs *items)
+{
+    decode_tables_body(items[blockIdx.x]);
+}
+
 constexpr size_t kCbSmem = 16 * 1024 * sizeof(uint32_t);  // 8192 sort keys; 16 digit counters per thread
 
 // opt in to more than 48 KB of dynamic shared memory, once per device
@@ -497,6 +508,7 @@ void set_smem_attributes()
     cudaFuncSetAttribute(k_codebook, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem);
     cudaFuncSetAttribute(k_decode_tables, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem);
     cudaFuncSetAttribute(k_codebook_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem);
+    cudaFuncSetAttribute(k_decode_tables_group, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kCbSmem);
     done.fetch_or(bit);
 }
 
@@ -518,6 +530,12 @@ void launch_decode_tables(const CodebookArgs &a, cudaStream_t st)
 {
     set_smem_attributes();
     k_decode_tables<<<1, kCbThreads, kCbSmem, st>>>(a);
+}
+
+void launch_decode_tables_group(const CodebookArgs *items, uint32_t count, cudaStream_t st)
+{
+    set_smem_attributes();
+    k_decode_tables_group<<<count, kCbThreads, kCbSmem, st>>>(items);
 }
 
 }  // namespace gbsz

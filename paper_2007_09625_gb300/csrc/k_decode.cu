@@ -29,27 +29,7 @@ namespace {
 constexpr int kDecThreads = 256;
 constexpr uint32_t kSortedSmemMax = 8192;  // symbols whose table is copied to shared memory
 
-struct WordsOp {
-    using T = unsigned long long;
-    const uint32_t *bits;
-    unsigned long long *off;
-    unsigned long long words, maxbits;
-    Control *ctl;
-    __device__ T load(uint64_t i) const
-    {
-        const uint32_t b = bits[i];
-        if (b > maxbits) {
-            atomicOr(&ctl->error, DERR_CORRUPT);
-            return 0;
-        }
-        return (b + 31ull) / 32;
-    }
-    __device__ void store(uint64_t i, T v) const { off[i] = v; }
-    __device__ void total(T t) const
-    {
-        if (t != words) atomicOr(&ctl->error, DERR_CORRUPT);
-    }
-};
+
 
 constexpr uint32_t kRing = 32;       // stream words per thread in shared memory (any code length)
 constexpr uint32_t kRingFast = 16;   // the same for codes of at most kFastLutMax bits
@@ -269,7 +249,7 @@ __device__ __forceinline__ void decode_chunk_general(const DecodeArgs &a, const 
 // grid), ...  Tasks are spread over the blocks first, so every block, and so
 // every SM, gets the same number of tasks to within one.
 template <bool MULTI_TILE>
-__global__ void __launch_bounds__(kDecThreads) k_decode(DecodeArgs a, uint32_t sorted_in_smem)
+__device__ __forceinline__ void decode_general_body(const DecodeArgs &a, uint32_t sorted_in_smem, VGrid vg)
 {
     __shared__ uint32_t lut[1 << kLutBits];
     __shared__ uint16_t lut2[kLut2Entries];
@@ -290,11 +270,17 @@ __global__ void __launch_bounds__(kDecThreads) k_decode(DecodeArgs a, uint32_t s
     if (a.ctl->error & DERR_CORRUPT) return;
     const DecTables t{lut, lut2, a.lut[1u << kLutBits], first, count, start, sorted_in_smem ? s_sorted : a.sorted,
                       a.maxlen};
-    const uint64_t ntask = (a.nchunk + 31) / 32, tstride = (uint64_t)(blockDim.x >> 5) * gridDim.x;
-    for (uint64_t k = (uint64_t)(threadIdx.x >> 5) * gridDim.x + blockIdx.x; k < ntask; k += tstride) {
+    const uint64_t ntask = (a.nchunk + 31) / 32, tstride = (uint64_t)(blockDim.x >> 5) * vg.nb;
+    for (uint64_t k = (uint64_t)(threadIdx.x >> 5) * vg.nb + vg.bid; k < ntask; k += tstride) {
         const uint64_t c = k * 32 + (threadIdx.x & 31);
         if (c < a.nchunk) decode_chunk_general<MULTI_TILE>(a, t, s_dyn, c);
     }
+}
+
+template <bool MULTI_TILE>
+__global__ void __launch_bounds__(kDecThreads) k_decode(const __grid_constant__ DecodeArgs a, uint32_t sorted_in_smem)
+{
+    decode_general_body<MULTI_TILE>(a, sorted_in_smem, vgrid_self());
 }
 
 // Two-level decode for archives whose codes all fit the complete table
@@ -464,7 +450,7 @@ __device__ __forceinline__ void decode_chunk(const DecodeArgs &a, Ring<kRingFast
 }
 
 template <bool MULTI_TILE>
-__global__ void __launch_bounds__(kDecFastThreads, 2) k_decode_fast(DecodeArgs a)
+__device__ __forceinline__ void decode_fast_body(const DecodeArgs &a, VGrid vg)
 {
     extern __shared__ uint32_t s_dyn[];  // rings, level-1 table (lane-replicated)
     uint2 *l1tab = reinterpret_cast<uint2 *>(s_dyn + kDecFastThreads * kRingFast);
@@ -503,14 +489,14 @@ __global__ void __launch_bounds__(kDecFastThreads, 2) k_decode_fast(DecodeArgs a
     const uint2 *l1 = l1tab + lane % kL1Copies;
     unsigned long long zeros = 0;
     bool bad = false;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t stride = (uint64_t)vg.nb * blockDim.x;
     // whole warps iterate together (the level-1 fallback votes across the
     // warp); lanes past the last chunk decode nothing.  Consecutive chunks go
     // to consecutive threads: spreading warp tasks evenly over the blocks
     // instead (as k_decode does) measured about 4% slower here (2^28 symbols
     // in 2048-symbol chunks), since it does not even out the warps per
     // scheduler, which bound this latency-bound loop.
-    for (uint64_t cw = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x - lane; cw < a.nchunk; cw += stride) {
+    for (uint64_t cw = (uint64_t)vg.bid * blockDim.x + threadIdx.x - lane; cw < a.nchunk; cw += stride) {
         const uint64_t c = cw + lane;
         const bool live = c < a.nchunk;
         const uint32_t nbits = live ? bits_tab[c] : 0u;
@@ -535,72 +521,130 @@ __global__ void __launch_bounds__(kDecFastThreads, 2) k_decode_fast(DecodeArgs a
     if (zeros) atomicAdd(&a.ctl->zeros, zeros);
 }
 
+template <bool MULTI_TILE>
+__global__ void __launch_bounds__(kDecFastThreads, 2) k_decode_fast(const __grid_constant__ DecodeArgs a)
+{
+    decode_fast_body<MULTI_TILE>(a, vgrid_self());
+}
+
+// grouped decoders: one launch per variant over every field of the variant
+template <bool FAST, bool MULTI_TILE>
+__global__ void __launch_bounds__(FAST ? kDecFastThreads : kDecThreads, FAST ? 2 : 1)
+    k_decode_group(const DecodeItem *items, const uint32_t *first, uint32_t ni)
+{
+    VGrid vg;
+    const DecodeItem &d = items[group_item(first, ni, vg)];
+    if (FAST) decode_fast_body<MULTI_TILE>(d.a, vg);
+    else decode_general_body<MULTI_TILE>(d.a, d.sorted_in_smem, vg);
+}
+
 }  // namespace
 
 int launch_decode(const DecodeArgs &a, cudaStream_t st, int phase)
 {
-    WordsOp op;
-    op.bits = reinterpret_cast<const uint32_t *>(a.archive + a.off_bits);
-    op.off = a.chunk_off;
-    op.words = a.words;
-    op.maxbits = (unsigned long long)a.chunk * kMaxLen;
-    op.ctl = a.ctl;
+    const ChunkWords op = chunk_words_op(a);
     if (phase == 0) return launch_scan(op, a.nchunk, a.scan_partial, st);
+    DecodeItem it;
+    int variant;
+    size_t dyn;
+    const unsigned g = decode_plan(a, &it, &variant, &dyn);
+    const bool multi = variant & 1;
+    if (variant & 2) {
+        if (multi) k_decode_fast<true><<<g, kDecFastThreads, dyn, st>>>(a);
+        else k_decode_fast<false><<<g, kDecFastThreads, dyn, st>>>(a);
+    } else {
+        if (multi) k_decode<true><<<g, kDecThreads, dyn, st>>>(a, it.sorted_in_smem);
+        else k_decode<false><<<g, kDecThreads, dyn, st>>>(a, it.sorted_in_smem);
+    }
+    return 1;
+}
+
+namespace {
+
+// opt in to the dynamic shared memory of the decoders, once per device
+// (host threads may race here: the bits are atomic, and setting an
+// attribute twice is harmless)
+void set_decode_smem(int dev)
+{
+    static std::atomic<unsigned long long> attr_done{0};  // one bit per device id < 64
+    const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0;
+    if (bit && (attr_done.load() & bit)) return;
+    const int most = (int)(kDecThreads * kRing * 4 + kSortedSmemMax * sizeof(uint16_t));
+    const int most_fast = (int)(kDecFastThreads * kRingFast * 4 + 8u * kL1Copies * (1u << kL1Bits));
+    cudaFuncSetAttribute(k_decode<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(k_decode<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(k_decode_fast<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
+    cudaFuncSetAttribute(k_decode_fast<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
+    cudaFuncSetAttribute(k_decode_group<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(k_decode_group<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
+    cudaFuncSetAttribute(k_decode_group<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
+    cudaFuncSetAttribute(k_decode_group<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
+    attr_done.fetch_or(bit);
+}
+
+}  // namespace
+
+unsigned decode_plan(const DecodeArgs &a, DecodeItem *it, int *variant, size_t *dyn_out)
+{
+    int dev = 0;
+    cudaGetDevice(&dev);
+    set_decode_smem(dev);
+    it->a = a;
     const uint64_t ntask = (a.nchunk + 31) / 32;
     const uint32_t nb = 2 * a.radius;
     const uint32_t in_smem = nb <= kSortedSmemMax ? nb : 0u;
-    const size_t dyn = (size_t)kDecThreads * kRing * 4 + in_smem * sizeof(uint16_t);
-    // host threads may race here: the state is atomic, and setting an
-    // attribute or querying the occupancy twice is harmless
-    static std::atomic<unsigned long long> attr_done{0};  // one bit per device id < 64
-    // k_decode blocks resident per SM, by device, MULTI_TILE and the sorted
-    // table's size in shared memory (steps of 512 symbols); 0: not queried yet
-    static std::atomic<int> resident[64][2][kSortedSmemMax / 512 + 1];
-    int dev = 0;
-    cudaGetDevice(&dev);
-    const unsigned long long bit = dev >= 0 && dev < 64 ? 1ull << dev : 0;
-    if (!bit || !(attr_done.load() & bit)) {
-        const int most = (int)(kDecThreads * kRing * 4 + kSortedSmemMax * sizeof(uint16_t));
-        cudaFuncSetAttribute(k_decode<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-        cudaFuncSetAttribute(k_decode<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
-        const int most_fast = (int)(kDecFastThreads * kRingFast * 4 + 8u * kL1Copies * (1u << kL1Bits));
-        cudaFuncSetAttribute(k_decode_fast<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
-        cudaFuncSetAttribute(k_decode_fast<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
-        attr_done.fetch_or(bit);
-    }
+    it->sorted_in_smem = in_smem;
     const bool multi = a.chunk > kRecon1DTile;
+    const uint64_t sms = (uint64_t)(a.num_sms ? a.num_sms : 1);
     if (a.fast_bits) {
-        const size_t dyn_fast = (size_t)kDecFastThreads * kRingFast * 4 + 8u * kL1Copies * (1u << kL1Bits);
+        *variant = 2 + (multi ? 1 : 0);
+        *dyn_out = (size_t)kDecFastThreads * kRingFast * 4 + 8u * kL1Copies * (1u << kL1Bits);
         const uint64_t want = (a.nchunk + kDecFastThreads - 1) / kDecFastThreads;
-        const int per_sm = 2;
-        const unsigned g = (unsigned)std::min<uint64_t>(want, (uint64_t)(a.num_sms ? a.num_sms : 1) * per_sm);
-        if (multi) k_decode_fast<true><<<g, kDecFastThreads, dyn_fast, st>>>(a);
-        else k_decode_fast<false><<<g, kDecFastThreads, dyn_fast, st>>>(a);
-    } else {
-        // persistent: as many blocks as are resident at once
-        const uint32_t qb = (in_smem + 511) / 512;
-        int per_sm = 1;
-        if (bit) {
-            std::atomic<int> &r = resident[dev][multi ? 1 : 0][qb];
-            if (r.load() == 0) {
-                const size_t dq = (size_t)kDecThreads * kRing * 4 + (size_t)qb * 512 * sizeof(uint16_t);
-                int blocks = 0;
-                const cudaError_t e =
-                    multi ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_decode<true>, kDecThreads, dq)
-                          : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_decode<false>, kDecThreads, dq);
-                if (e != cudaSuccess) {
-                    cudaGetLastError();
-                    blocks = 0;
-                }
-                r.store(blocks > 0 ? blocks : 1);
-            }
-            per_sm = r.load();
-        }
-        const unsigned g = (unsigned)std::min<uint64_t>(ntask, (uint64_t)(a.num_sms ? a.num_sms : 1) * per_sm);
-        if (multi) k_decode<true><<<g, kDecThreads, dyn, st>>>(a, in_smem);
-        else k_decode<false><<<g, kDecThreads, dyn, st>>>(a, in_smem);
+        return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(want, sms * 2));
     }
-    return 1;
+    *variant = multi ? 1 : 0;
+    *dyn_out = (size_t)kDecThreads * kRing * 4 + in_smem * sizeof(uint16_t);
+    // persistent: as many blocks as are resident at once.  k_decode blocks
+    // resident per SM, by device, MULTI_TILE and the sorted table's size in
+    // shared memory (steps of 512 symbols); 0: not queried yet
+    static std::atomic<int> resident[64][2][kSortedSmemMax / 512 + 1];
+    const uint32_t qb = (in_smem + 511) / 512;
+    int per_sm = 1;
+    if (dev >= 0 && dev < 64) {
+        std::atomic<int> &r = resident[dev][multi ? 1 : 0][qb];
+        if (r.load() == 0) {
+            const size_t dq = (size_t)kDecThreads * kRing * 4 + (size_t)qb * 512 * sizeof(uint16_t);
+            int blocks = 0;
+            const cudaError_t e =
+                multi ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_decode<true>, kDecThreads, dq)
+                      : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks, k_decode<false>, kDecThreads, dq);
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                blocks = 0;
+            }
+            r.store(blocks > 0 ? blocks : 1);
+        }
+        per_sm = r.load();
+    }
+    return (unsigned)std::max<uint64_t>(1, std::min<uint64_t>(ntask, sms * per_sm));
+}
+
+void launch_decode_group(int variant, const DecodeItem *items, const uint32_t *first, uint32_t ni, uint32_t blocks,
+                         size_t dyn, cudaStream_t st)
+{
+    switch (variant) {
+    case 0: k_decode_group<false, false><<<blocks, kDecThreads, dyn, st>>>(items, first, ni); break;
+    case 1: k_decode_group<false, true><<<blocks, kDecThreads, dyn, st>>>(items, first, ni); break;
+    case 2: k_decode_group<true, false><<<blocks, kDecFastThreads, dyn, st>>>(items, first, ni); break;
+    case 3: k_decode_group<true, true><<<blocks, kDecFastThreads, dyn, st>>>(items, first, ni); break;
+    default: break;
+    }
+}
+
+int launch_offsets_scan_group(const ScanItem<ChunkWords> *items, const uint32_t *first, uint32_t ni, uint32_t blocks,
+                              cudaStream_t st)
+{
+    return launch_scan_group(items, first, ni, blocks, st);
 }
 
 }  // namespace gbsz

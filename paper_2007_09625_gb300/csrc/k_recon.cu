@@ -21,6 +21,8 @@
 #include "scan.cuh"
 
 #include <algorithm>
+#include <cstring>
+#include <type_traits>
 
 namespace gbsz {
 
@@ -85,11 +87,11 @@ __device__ __forceinline__ uint32_t delta_of(const ReconArgs &a, uint64_t i)
 // ---------------------------------------------------------------------------
 // 1. outliers
 
-__global__ void k_scatter_outliers(ReconArgs a, uint64_t n)
+__device__ __forceinline__ void scatter_outliers_body(const ReconArgs &a, uint64_t n, VGrid vg)
 {
     const uint8_t *o = a.archive + a.off_outl;
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.m;
-         t += (uint64_t)gridDim.x * blockDim.x) {
+    for (uint64_t t = (uint64_t)vg.bid * blockDim.x + threadIdx.x; t < a.m;
+         t += (uint64_t)vg.nb * blockDim.x) {
         const uint32_t idx = *reinterpret_cast<const uint32_t *>(o + 8 * t);
         const int32_t d = *reinterpret_cast<const int32_t *>(o + 8 * t + 4);
         bool ok = idx < n;
@@ -103,6 +105,11 @@ __global__ void k_scatter_outliers(ReconArgs a, uint64_t n)
     }
 }
 
+__global__ void k_scatter_outliers(const __grid_constant__ ReconArgs a, uint64_t n)
+{
+    scatter_outliers_body(a, n, vgrid_self());
+}
+
 // 1D: the outlier residuals go to the tile sums (added to the in-cap sums
 // the decoder left there), and every 512-point tile g learns where its
 // outliers start in the index-ordered list: start[g] = first outlier with
@@ -111,14 +118,15 @@ __global__ void k_scatter_outliers(ReconArgs a, uint64_t n)
 // one atomic.
 constexpr uint32_t kGroup1D = kRecon1DTile;
 
-__global__ void k_outlier_tiles_1d(ReconArgs a, uint64_t n, uint64_t ngroups, uint32_t *start)
+__device__ __forceinline__ void outlier_tiles_1d_body(const ReconArgs &a, uint64_t n, uint64_t ngroups, uint32_t *start,
+                                                      VGrid vg)
 {
     const uint8_t *o = a.archive + a.off_outl;
     const uint32_t lane = threadIdx.x & 31;
-    const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+    const uint64_t stride = (uint64_t)vg.nb * blockDim.x;
     // whole warps stay in the loop so the shuffles see every lane
     const uint64_t tmax = (a.m + 31) & ~31ull;
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < tmax; t += stride) {
+    for (uint64_t t = (uint64_t)vg.bid * blockDim.x + threadIdx.x; t < tmax; t += stride) {
         const bool live = t < a.m;
         uint32_t idx = 0, d = 0;
         bool ok = true;
@@ -159,11 +167,16 @@ __global__ void k_outlier_tiles_1d(ReconArgs a, uint64_t n, uint64_t ngroups, ui
     }
 }
 
-__global__ void k_patch_exceptions(ReconArgs a, uint64_t n)
+__global__ void k_outlier_tiles_1d(const __grid_constant__ ReconArgs a, uint64_t n, uint64_t ngroups, uint32_t *start)
+{
+    outlier_tiles_1d_body(a, n, ngroups, start, vgrid_self());
+}
+
+__device__ __forceinline__ void patch_exceptions_body(const ReconArgs &a, uint64_t n, VGrid vg)
 {
     const uint8_t *e = a.archive + a.off_exc;
-    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < a.e;
-         t += (uint64_t)gridDim.x * blockDim.x) {
+    for (uint64_t t = (uint64_t)vg.bid * blockDim.x + threadIdx.x; t < a.e;
+         t += (uint64_t)vg.nb * blockDim.x) {
         const uint32_t idx = *reinterpret_cast<const uint32_t *>(e + 8 * t);
         const uint32_t raw = *reinterpret_cast<const uint32_t *>(e + 8 * t + 4);
         bool ok = idx < n;
@@ -172,6 +185,11 @@ __global__ void k_patch_exceptions(ReconArgs a, uint64_t n)
         if (ok) reinterpret_cast<uint32_t *>(a.out)[idx] = raw;
         else atomicOr(&a.ctl->error, DERR_CORRUPT);
     }
+}
+
+__global__ void k_patch_exceptions(const __grid_constant__ ReconArgs a, uint64_t n)
+{
+    patch_exceptions_body(a, n, vgrid_self());
 }
 
 // ---------------------------------------------------------------------------
@@ -201,7 +219,8 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 
 constexpr int kValStages = 3;  // tiles of codes per warp in shared memory: this one and two ahead
 
-__global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, const uint32_t *F, const uint32_t *start)
+__device__ __forceinline__ void values_1d_body(const ReconArgs &a, const Geo &g, const uint32_t *F, const uint32_t *start,
+                                               VGrid vg)
 {
     __shared__ uint32_t s_od[k1Threads * 17];  // outlier residuals by (thread, point); stride 17 spreads banks
     // codes of the next tiles, copied by each lane for itself (32 bytes per
@@ -214,7 +233,7 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
     const uint32_t lane = threadIdx.x & 31;
     const uint2 *ol = reinterpret_cast<const uint2 *>(a.archive + a.off_outl);
     uint32_t *od = s_od + threadIdx.x * 17;
-    const uint64_t nwarps = (uint64_t)gridDim.x * (k1Threads / 32);
+    const uint64_t nwarps = (uint64_t)vg.nb * (k1Threads / 32);
     bool bad = false;
     auto bounds = [&](uint64_t t, uint32_t &lo, uint32_t &hi) {
         lo = hi = 0;
@@ -238,7 +257,7 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
         if (lo + lane < hi) en = ol[lo + lane];
         return en;
     };
-    uint64_t tile = (uint64_t)blockIdx.x * (k1Threads / 32) + (threadIdx.x >> 5);
+    uint64_t tile = (uint64_t)vg.bid * (k1Threads / 32) + (threadIdx.x >> 5);
     uint32_t lo, hi, lo1, hi1;
     bounds(tile, lo, hi);
     bounds(tile + nwarps, lo1, hi1);
@@ -333,6 +352,12 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
     if (bad) atomicOr(&a.ctl->error, DERR_CORRUPT);
 }
 
+__global__ void __launch_bounds__(k1Threads) k_values_1d(const __grid_constant__ ReconArgs a, const __grid_constant__ Geo g,
+                                                         const uint32_t *F, const uint32_t *start)
+{
+    values_1d_body(a, g, F, start, vgrid_self());
+}
+
 // ---------------------------------------------------------------------------
 // Per-block mode, 2D / 3D: every B^D block is reconstructed on its own as a
 // d-dimensional inclusive prefix sum of its residuals (zero padding around
@@ -340,7 +365,7 @@ __global__ void __launch_bounds__(k1Threads) k_values_1d(ReconArgs a, Geo g, con
 // memory.
 
 template <int D>
-__global__ void __launch_bounds__(D == 2 ? 256 : 512) k_values_blocked(ReconArgs a, Geo g)
+__device__ __forceinline__ void values_blocked_body(const ReconArgs &a, const Geo &g, VGrid vg)
 {
     constexpr uint32_t B = lorenzo_block_extent(D);
     constexpr uint32_t NB = D == 2 ? B * B : B * B * B;
@@ -351,7 +376,7 @@ __global__ void __launch_bounds__(D == 2 ? 256 : 512) k_values_blocked(ReconArgs
     const uint64_t nbx = (g.n[0] + B - 1) / B, nby = (g.n[1] + B - 1) / B;
     const uint64_t nbz = D == 3 ? (g.n[2] + B - 1) / B : 1;
     const uint64_t nblocks = nbx * nby * nbz;
-    for (uint64_t blk = blockIdx.x; blk < nblocks; blk += gridDim.x) {
+    for (uint64_t blk = vg.bid; blk < nblocks; blk += vg.nb) {
         const uint64_t gx = (blk % nbx) * B + lx, gy = ((blk / nbx) % nby) * B + ly;
         const uint64_t gz = D == 3 ? (blk / (nbx * nby)) * B + lz : 0;
         const bool in = gx < g.n[0] && gy < g.n[1] && gz < g.n[2];
@@ -373,6 +398,13 @@ __global__ void __launch_bounds__(D == 2 ? 256 : 512) k_values_blocked(ReconArgs
         if (in) a.out[idx] = recon_value((int32_t)v, a.ebx2);
         __syncthreads();  // s0 / s1 are reused by the next block
     }
+}
+
+template <int D>
+__global__ void __launch_bounds__(D == 2 ? 256 : 512) k_values_blocked(const __grid_constant__ ReconArgs a,
+                                                                       const __grid_constant__ Geo g)
+{
+    values_blocked_body<D>(a, g, vgrid_self());
 }
 
 // ---------------------------------------------------------------------------
@@ -568,12 +600,12 @@ __device__ __forceinline__ void tile_prefix(const ReconArgs &a, const Geo &g, co
 }
 
 template <int TX, int TY, int TZ, int NT>
-__global__ void __launch_bounds__(NT, NT >= 512 ? 3 : 6) k_faces(ReconArgs a, Geo g, uint32_t *F)
+__device__ __forceinline__ void faces_body(const ReconArgs &a, const Geo &g, uint32_t *F, VGrid vg)
 {
     using TG = TileGeo<TX, TY, TZ, NT>;
     __shared__ uint32_t sm[TG::SMW];
     if (a.ctl->error & DERR_CORRUPT) return;
-    for (uint32_t tile = blockIdx.x; tile < (uint32_t)g.ntiles; tile += gridDim.x) {
+    for (uint32_t tile = vg.bid; tile < (uint32_t)g.ntiles; tile += vg.nb) {
         uint32_t tc[3];
         tile_coords(g, tile, tc);
         tile_prefix<TX, TY, TZ, NT>(a, g, tc, sm);
@@ -594,14 +626,21 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 3 : 6) k_faces(ReconArgs a, Ge
 }
 
 template <int TX, int TY, int TZ, int NT>
-__global__ void __launch_bounds__(NT, NT >= 512 ? 4 : 8) k_values(ReconArgs a, Geo g, const uint32_t *F)
+__global__ void __launch_bounds__(NT, NT >= 512 ? 3 : 6) k_faces(const __grid_constant__ ReconArgs a,
+                                                              const __grid_constant__ Geo g, uint32_t *F)
+{
+    faces_body<TX, TY, TZ, NT>(a, g, F, vgrid_self());
+}
+
+template <int TX, int TY, int TZ, int NT>
+__device__ __forceinline__ void values_body(const ReconArgs &a, const Geo &g, const uint32_t *F, VGrid vg)
 {
     using TG = TileGeo<TX, TY, TZ, NT>;
     __shared__ uint32_t sm[TG::SMW];
     __shared__ uint32_t carry[TG::base(TG::NA) + TG::size(TG::NA)];
     if (a.ctl->error & DERR_CORRUPT) return;
     const float ebx2 = a.ebx2;
-    for (uint32_t tile = blockIdx.x; tile < (uint32_t)g.ntiles; tile += gridDim.x) {
+    for (uint32_t tile = vg.bid; tile < (uint32_t)g.ntiles; tile += vg.nb) {
         uint32_t tc[3];
         tile_coords(g, tile, tc);
         // stage the carries of every subset: each subset's array has at most
@@ -661,6 +700,13 @@ __global__ void __launch_bounds__(NT, NT >= 512 ? 4 : 8) k_values(ReconArgs a, G
     }
 }
 
+template <int TX, int TY, int TZ, int NT>
+__global__ void __launch_bounds__(NT, NT >= 512 ? 4 : 8) k_values(const __grid_constant__ ReconArgs a,
+                                                              const __grid_constant__ Geo g, const uint32_t *F)
+{
+    values_body<TX, TY, TZ, NT>(a, g, F, vgrid_self());
+}
+
 // ---------------------------------------------------------------------------
 // 3. inclusive scans of a subset's array along one tile-grid dimension
 
@@ -695,11 +741,11 @@ __global__ void k_scan_lines(Geo g, int A, int d, uint64_t nlines, uint32_t *F)
 
 // one warp per line, 32 entries at a time: for few lines, where a thread per
 // line would leave most of the GPU idle behind one long serial chain
-__global__ void __launch_bounds__(256) k_scan_lines_warp(Geo g, int A, int d, uint64_t nlines, uint32_t *F)
+__device__ __forceinline__ void scan_lines_warp_body(const Geo &g, int A, int d, uint64_t nlines, uint32_t *F, VGrid vg)
 {
     const uint32_t lane = threadIdx.x & 31, len = g.nt[d];
-    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5;
-    for (uint64_t line = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; line < nlines; line += nw) {
+    const uint64_t nw = ((uint64_t)vg.nb * blockDim.x) >> 5;
+    for (uint64_t line = ((uint64_t)vg.bid * blockDim.x + threadIdx.x) >> 5; line < nlines; line += nw) {
         uint64_t stride;
         const uint64_t p0 = line_base(g, A, d, line, stride);
         uint32_t carry = 0;
@@ -716,6 +762,12 @@ __global__ void __launch_bounds__(256) k_scan_lines_warp(Geo g, int A, int d, ui
             carry = __shfl_sync(0xffffffffu, v, 31);
         }
     }
+}
+
+__global__ void __launch_bounds__(256) k_scan_lines_warp(const __grid_constant__ Geo g, int A, int d, uint64_t nlines,
+                                                         uint32_t *F)
+{
+    scan_lines_warp_body(g, A, d, nlines, F, vgrid_self());
 }
 
 // one CTA per long line
@@ -896,7 +948,208 @@ int launch_reconstruct_order(const ReconArgs &a, const Geo &g, uint64_t n, cudaS
     return nl;
 }
 
+// ---------------------------------------------------------------------------
+// Grouped reconstruction: every stage of many fields in one launch per
+// kernel (variant), each field owning a range of the grid's blocks.
+
+struct RItem {
+    ReconArgs a;
+    Geo g;
+    uint64_t n;
+};
+struct LineItem {
+    Geo g;
+    uint32_t *F;
+    uint64_t nlines;
+    int A, d;
+};
+
+__global__ void k_scatter_outliers_group(const RItem *items, const uint32_t *first, uint32_t ni)
+{
+    VGrid vg;
+    const RItem &it = items[group_item(first, ni, vg)];
+    scatter_outliers_body(it.a, it.n, vg);
+}
+
+__global__ void k_outlier_tiles_1d_group(const RItem *items, const uint32_t *first, uint32_t ni)
+{
+    VGrid vg;
+    const RItem &it = items[group_item(first, ni, vg)];
+    outlier_tiles_1d_body(it.a, it.n, it.g.ntiles, reinterpret_cast<uint32_t *>(it.a.dscr), vg);
+}
+
+__global__ void k_patch_exceptions_group(const RItem *items, const uint32_t *first, uint32_t ni)
+{
+    VGrid vg;
+    const RItem &it = items[group_item(first, ni, vg)];
+    patch_exceptions_body(it.a, it.n, vg);
+}
+
+__global__ void __launch_bounds__(k1Threads) k_values_1d_group(const RItem *items, const uint32_t *first, uint32_t ni)
+{
+    VGrid vg;
+    const RItem &it = items[group_item(first, ni, vg)];
+    values_1d_body(it.a, it.g, it.a.faces, reinterpret_cast<const uint32_t *>(it.a.dscr), vg);
+}
+
+template <int D>
+__global__ void __launch_bounds__(D == 2 ? 256 : 512) k_values_blocked_group(const RItem *items, const uint32_t *first,
+                                                                            uint32_t ni)
+{
+    VGrid vg;
+    const RItem &it = items[group_item(first, ni, vg)];
+    values_blocked_body<D>(it.a, it.g, vg);
+}
+
+template <int TX, int TY, int TZ, int NT>
+__global__ void __launch_bounds__(NT, NT >= 512 ? 3 : 6) k_faces_group(const RItem *items, const uint32_t *first,
+                                                                      uint32_t ni)
+{
+    VGrid vg;
+    const RItem &it = items[group_item(first, ni, vg)];
+    faces_body<TX, TY, TZ, NT>(it.a, it.g, it.a.faces, vg);
+}
+
+template <int TX, int TY, int TZ, int NT>
+__global__ void __launch_bounds__(NT, NT >= 512 ? 4 : 8) k_values_group(const RItem *items, const uint32_t *first,
+                                                                       uint32_t ni)
+{
+    VGrid vg;
+    const RItem &it = items[group_item(first, ni, vg)];
+    values_body<TX, TY, TZ, NT>(it.a, it.g, it.a.faces, vg);
+}
+
+__global__ void __launch_bounds__(256) k_scan_lines_group(const LineItem *items, const uint32_t *first, uint32_t ni)
+{
+    VGrid vg;
+    const LineItem &it = items[group_item(first, ni, vg)];
+    scan_lines_warp_body(it.g, it.A, it.d, it.nlines, it.F, vg);
+}
+
+// appends an array to the plan (16-byte aligned); returns its offset
+template <typename T> uint64_t plan_put(std::vector<uint8_t> &plan, const std::vector<T> &v)
+{
+    const uint64_t off = (plan.size() + 15) & ~uint64_t(15);
+    plan.resize(off + sizeof(T) * v.size());
+    if (!v.empty()) std::memcpy(plan.data() + off, v.data(), sizeof(T) * v.size());
+    return off;
+}
+
+// one grouped launch: items and their blocks
+template <typename T> struct GroupList {
+    std::vector<T> items;
+    std::vector<uint32_t> first{0};
+    void add(const T &it, uint64_t blocks)
+    {
+        items.push_back(it);
+        first.push_back(first.back() + (uint32_t)std::max<uint64_t>(1, blocks));
+    }
+    bool empty() const { return items.empty(); }
+};
+
 }  // namespace
+
+void plan_reconstruct_group(const ReconArgs *ra, uint32_t count, std::vector<uint8_t> &plan,
+                            std::vector<GroupLaunch> &launches)
+{
+    GroupList<RItem> tiles1d, scatter, exc, val1d, blk2, blk3, faces2, faces3, val2, val3;
+    GroupList<ScanItem<TileOp>> tscan;
+    std::vector<GroupList<LineItem>> lines(8 * 3);  // by (A, d)
+    for (uint32_t f = 0; f < count; f++) {
+        const ReconArgs &a = ra[f];
+        const Geo g = make_geo(a.ndim, a.dims);
+        const uint64_t n = g.n[0] * g.n[1] * g.n[2];
+        const uint64_t sms = (uint64_t)a.num_sms;
+        const RItem it{a, g, n};
+        if (a.m) {
+            const uint64_t grid = std::min<uint64_t>((a.m + 255) / 256, sms * 16);
+            (g.ndim == 1 ? tiles1d : scatter).add(it, grid);
+        }
+        const uint64_t gridt = std::min<uint64_t>(g.ntiles, sms * 8);
+        if (a.lblock && g.ndim > 1) {
+            const uint32_t B = lorenzo_block_extent(g.ndim);
+            uint64_t nb = 1;
+            for (uint32_t d = 0; d < g.ndim; d++) nb *= (g.n[d] + B - 1) / B;
+            (g.ndim == 2 ? blk2 : blk3).add(it, std::min<uint64_t>(nb, sms * 8));
+        } else {
+            if (g.ndim == 1) {
+                if (!a.lblock)
+                    tscan.add(ScanItem<TileOp>{TileOp{a.faces}, g.ntiles, a.scan_partial}, scan_blocks(g.ntiles));
+            } else {
+                (g.ndim == 2 ? faces2 : faces3).add(it, gridt);
+                for (int A = 1; A < 8; A++) {
+                    if (!g.size[A]) continue;
+                    for (int d = 0; d < (int)g.ndim; d++) {
+                        if (!((A >> d) & 1) || g.nt[d] < 2) continue;
+                        const uint64_t nlines = g.size[A] * (g.ntiles / g.nt[d]);
+                        lines[A * 3 + d].add(LineItem{g, a.faces, nlines, A, d}, std::min<uint64_t>((nlines + 7) / 8, sms * 8));
+                    }
+                }
+            }
+            if (g.ndim == 1) {
+                const uint64_t blocks = (g.ntiles + k1Threads / 32 - 1) / (k1Threads / 32);
+                val1d.add(it, std::min<uint64_t>(blocks, sms * 4));
+            } else {
+                (g.ndim == 2 ? val2 : val3).add(it, gridt);
+            }
+        }
+        if (a.e) exc.add(it, std::min<uint64_t>((a.e + 255) / 256, sms * 16));
+    }
+    // launches in stage order; each closure reads its arrays at the plan's device address
+    auto emit = [&](auto &list, auto launch) {
+        if (list.empty()) return;
+        const uint64_t oi = plan_put(plan, list.items), of = plan_put(plan, list.first);
+        const uint32_t ni = (uint32_t)list.items.size(), blocks = list.first.back();
+        using Item = typename std::remove_reference<decltype(list.items[0])>::type;
+        launches.push_back([=](const uint8_t *dev, cudaStream_t st) {
+            launch(reinterpret_cast<const Item *>(dev + oi), reinterpret_cast<const uint32_t *>(dev + of), ni, blocks,
+                   st);
+            return 1;
+        });
+    };
+    emit(tiles1d, [](const RItem *i, const uint32_t *f, uint32_t ni, uint32_t b, cudaStream_t st) {
+        k_outlier_tiles_1d_group<<<b, 256, 0, st>>>(i, f, ni);
+    });
+    emit(scatter, [](const RItem *i, const uint32_t *f, uint32_t ni, uint32_t b, cudaStream_t st) {
+        k_scatter_outliers_group<<<b, 256, 0, st>>>(i, f, ni);
+    });
+    if (!tscan.empty()) {
+        const uint64_t oi = plan_put(plan, tscan.items), of = plan_put(plan, tscan.first);
+        const uint32_t ni = (uint32_t)tscan.items.size(), blocks = tscan.first.back();
+        launches.push_back([=](const uint8_t *dev, cudaStream_t st) {
+            return launch_scan_group(reinterpret_cast<const ScanItem<TileOp> *>(dev + oi),
+                                     reinterpret_cast<const uint32_t *>(dev + of), ni, blocks, st);
+        });
+    }
+    emit(faces2, [](const RItem *i, const uint32_t *f, uint32_t ni, uint32_t b, cudaStream_t st) {
+        k_faces_group<k2TX, k2TY, 1, k2Threads><<<b, k2Threads, 0, st>>>(i, f, ni);
+    });
+    emit(faces3, [](const RItem *i, const uint32_t *f, uint32_t ni, uint32_t b, cudaStream_t st) {
+        k_faces_group<k3TX, k3TY, k3TZ, k3Threads><<<b, k3Threads, 0, st>>>(i, f, ni);
+    });
+    for (auto &l : lines)
+        emit(l, [](const LineItem *i, const uint32_t *f, uint32_t ni, uint32_t b, cudaStream_t st) {
+            k_scan_lines_group<<<b, 256, 0, st>>>(i, f, ni);
+        });
+    emit(val1d, [](const RItem *i, const uint32_t *f, uint32_t ni, uint32_t b, cudaStream_t st) {
+        k_values_1d_group<<<b, k1Threads, 0, st>>>(i, f, ni);
+    });
+    emit(val2, [](const RItem *i, const uint32_t *f, uint32_t ni, uint32_t b, cudaStream_t st) {
+        k_values_group<k2TX, k2TY, 1, k2Threads><<<b, k2Threads, 0, st>>>(i, f, ni);
+    });
+    emit(val3, [](const RItem *i, const uint32_t *f, uint32_t ni, uint32_t b, cudaStream_t st) {
+        k_values_group<k3TX, k3TY, k3TZ, k3Threads><<<b, k3Threads, 0, st>>>(i, f, ni);
+    });
+    emit(blk2, [](const RItem *i, const uint32_t *f, uint32_t ni, uint32_t b, cudaStream_t st) {
+        k_values_blocked_group<2><<<b, 256, 0, st>>>(i, f, ni);
+    });
+    emit(blk3, [](const RItem *i, const uint32_t *f, uint32_t ni, uint32_t b, cudaStream_t st) {
+        k_values_blocked_group<3><<<b, 512, 0, st>>>(i, f, ni);
+    });
+    emit(exc, [](const RItem *i, const uint32_t *f, uint32_t ni, uint32_t b, cudaStream_t st) {
+        k_patch_exceptions_group<<<b, 256, 0, st>>>(i, f, ni);
+    });
+}
 
 uint64_t recon_faces_entries(uint32_t ndim, const uint64_t dims[3])
 {

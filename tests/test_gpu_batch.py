@@ -273,9 +273,52 @@ def test_grouped_batch_equals_slot_streams_and_oracle(gb, ctx):
             ctx.set_option(gb.OPT_BATCH_MODE, 0)
         assert all(s_ == gb.OK for s_ in sts), sts
         results[mode_] = [a[:n].cpu().numpy() for a, n in zip(arcs, nbs)]
+    oas = []
     for i, f in enumerate(fields):
         p = params[i]
         oa = ref.compress(f, p.eb, p.eb_mode, p.radius, p.chunk or gb.auto_chunk(list(f.shape)[::-1], p.radius),
                           lblock=p.lorenzo_block)
         assert np.array_equal(results[0][i], results[1][i]), i
         assert np.array_equal(results[0][i], oa), i
+        oas.append(oa)
+    # and back, both ways, to the oracle's floats
+    arcs = [torch.from_numpy(a).cuda() for a in oas]
+    nbs = [a.size for a in oas]
+    for mode_ in (0, 1):
+        outs = [torch.empty(f.shape, dtype=torch.float32, device="cuda") for f in fields]
+        ctx.set_option(gb.OPT_BATCH_MODE, mode_)
+        try:
+            outs, dsts = ctx.decompress_batch(arcs, nbs, outs)
+            torch.cuda.synchronize()
+        finally:
+            ctx.set_option(gb.OPT_BATCH_MODE, 0)
+        assert all(s_ == gb.OK for s_ in dsts), (mode_, dsts)
+        for i, oa in enumerate(oas):
+            yo = ref.decompress(oa)
+            assert np.array_equal(outs[i].cpu().numpy().view(np.uint32), yo.view(np.uint32)), (mode_, i)
+
+
+def test_grouped_batch_reports_corrupt_fields(gb, ctx):
+    """A corrupt archive inside a grouped decompress batch fails alone."""
+    fields = [workloads.field_for("walk", (50000 + 1000 * i,), seed=970 + i) for i in range(6)]
+    oas = [ref.compress(f, 1e-4, ref.EB_REL, 64, 256) for f in fields]
+    bad = oas[3].copy()
+    o = ref.sections(bad)["off_bits"]
+    v = int.from_bytes(bad[o:o + 4].tobytes(), "little") + 64
+    bad[o:o + 4] = np.frombuffer(v.to_bytes(4, "little"), np.uint8)
+    arcs = [torch.from_numpy(a if i != 3 else bad).cuda() for i, a in enumerate(oas)]
+    outs = [torch.empty(f.shape, dtype=torch.float32, device="cuda") for f in fields]
+    with pytest.raises(gb.GbszError):
+        ctx.decompress_batch(arcs, [a.size for a in oas], outs)
+    import ctypes as C
+    k = len(arcs)
+    ap = (C.c_void_p * k)(*[a.data_ptr() for a in arcs])
+    by = (C.c_size_t * k)(*[a.numel() for a in arcs])
+    op = (C.c_void_p * k)(*[o_.data_ptr() for o_ in outs])
+    caps = (C.c_uint64 * k)(*[o_.numel() for o_ in outs])
+    sts = (C.c_int * k)()
+    gb.load().gbsz_decompress_batch(ctx.h, k, ap, by, op, caps, sts, C.c_void_p(torch.cuda.current_stream().cuda_stream))
+    torch.cuda.synchronize()
+    assert list(sts) == [0, 0, 0, gb.ERR_CORRUPT, 0, 0]
+    for i in (0, 1, 2, 4, 5):
+        assert np.array_equal(outs[i].cpu().numpy().view(np.uint32), ref.decompress(oas[i]).view(np.uint32)), i
