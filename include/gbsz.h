@@ -112,6 +112,16 @@ void gbsz_destroy(gbsz_ctx *ctx);
  *     streams (for comparison).  The results are the same bytes either
  *     way. */
 #define GBSZ_OPT_BATCH_MODE 3
+/*   GBSZ_OPT_DECODER  which Huffman decoder (S7) runs.  Thread: one thread
+ *     walks each chunk.  Warp: the 32 lanes of a warp decode 32 ranges of a
+ *     chunk's bits and re-synchronise; for 1D fields of order-1 whole-field
+ *     Lorenzo under 2^30 points it also reconstructs the values (S8) in the
+ *     same kernel.  Chunks of more than 4096 symbols always take the thread
+ *     decoder, and so do 1D order-1 fields of 2^30 points or more.
+ *     0 (default) = warp for fields of at most 32 chunks per SM in chunks
+ *     of at least 1024 symbols, else thread; 1 = thread always; 2 = warp wherever it applies.  The results
+ *     and statuses are the same either way. */
+#define GBSZ_OPT_DECODER 4
 gbsz_status gbsz_set_option(gbsz_ctx *ctx, int option, int64_t value);
 
 /* Worst-case archive size in bytes for these parameters (0 if invalid).
@@ -311,7 +321,8 @@ const char *gbsz_status_str(gbsz_status s);
  *   0 quant codes of the last compress (uint16[n])
  *   1 histogram of the last compress (uint32[2R])
  *   2 error-bound scalars of the last compress (float[3]: eb, 2eb, 1/(2eb))
- *   3 quant codes decoded by the last decompress (uint16[n])
+ *   3 quant codes decoded by the last decompress (uint16[n]; INVALID_ARG
+ *     when it took the fused 1D decoder, whose codes never leave the chip)
  *   4 canonical codewords of the last compress (uint64[2R]: code, no length)
  *   5 batch graph counters (uint64[4]: compress captures, compress replays,
  *     decompress captures, decompress replays)

@@ -13,7 +13,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libgbsz.so")
-SOURCES = ["gbsz_api.cu", "k_quant.cu", "k_codebook.cu", "k_encode.cu", "k_decode.cu", "k_recon.cu",
+SOURCES = ["gbsz_api.cu", "k_quant.cu", "k_codebook.cu", "k_encode.cu", "k_decode.cu", "k_decode_warp.cu", "k_recon.cu",
            "noalloc.cu", "server.cu"]
 HEADERS = ["common.cuh", "scan.cuh", "server_core.h"]
 

@@ -74,6 +74,7 @@ struct Control {
     unsigned long long zeros;  // decode: code-0 symbols decoded
     unsigned long long out_chk; // encode: outliers emitted (check)
     unsigned long long exc_chk; // encode: exceptions emitted (check)
+    uint32_t ticket;            // warp decoder: next chunk to take
 };
 
 struct EbScalars {
@@ -504,6 +505,27 @@ constexpr uint32_t kRecon1DTile = 512;  // 1D reconstruction tile (points): one 
 // phase 0: chunk word offsets (scan), 1: symbols; returns kernels launched
 int launch_decode(const DecodeArgs &a, cudaStream_t st, int phase);
 
+// S7 with one warp per chunk (k_decode_warp.cu).  fuse = 0: the chunk's codes
+// go to d.codes; 1: 1D order-1 fields only, S8 in the same pass: the values
+// go to out, the codes stay on chip (needs n < 2^30, d.fast_bits != 0,
+// d.chunk <= kWarpMaxChunk).  look: nchunk zeroed words; odp: exclusive
+// prefix sums of the outliers' residuals (m + 1 entries).
+constexpr uint32_t kWarpMaxChunk = 4096;
+struct WarpDecodeArgs {
+    DecodeArgs d;
+    const uint2 *outl;  // outlier list: (index, residual) in index order
+    const uint32_t *odp;
+    uint64_t m;
+    float ebx2;
+    float *out;
+    unsigned long long *look;
+};
+// kernels launched (one)
+int launch_decode_warp(const WarpDecodeArgs &w, bool fuse, cudaStream_t st);
+// exclusive prefix sums of the outliers' residuals into odp[0..m] (m + 1
+// entries; partial: scan_partials(m + 1) entries); returns kernels launched
+int launch_outlier_prefix(const uint2 *outl, uint64_t m, uint32_t *odp, uint32_t *partial, cudaStream_t st);
+
 // chunk word offsets: the exclusive prefix sum of ceil(bits / 32) over the
 // archive's chunk table; a count above the longest chunk, or a total other
 // than the header's, marks the archive corrupt
@@ -573,6 +595,9 @@ struct ReconArgs {
 };
 uint64_t recon_faces_entries(uint32_t ndim, const uint64_t dims[3]);
 void launch_reconstruct(const ReconArgs &a, cudaStream_t st, int *launches);
+// the verbatim exceptions on top of the values (codes NULL: not checked
+// against code 0); returns kernels launched
+int launch_exceptions(const ReconArgs &a, cudaStream_t st);
 
 // A launch of a grouped plan: given the plan's device address, enqueues its
 // kernels on st and returns how many.

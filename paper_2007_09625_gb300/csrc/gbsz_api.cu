@@ -234,8 +234,10 @@ struct gbsz_ctx {
     uint32_t last_nbins = 0;
     float last_sc[3] = {0, 0, 0};  // error-bound scalars of the last compress
     bool have_compress = false, have_decompress = false;
+    bool decoded_codes = false;  // the last decompress left its codes in slot 0's buffer
     // options
     uint32_t cw64_only = 0;  // GBSZ_OPT_CODEWORD_BITS = 64
+    uint32_t decoder = 0;    // GBSZ_OPT_DECODER
     // captured batch calls, and captured single-field calls
     BatchGraph gcomp, gdecomp, gsc, gsd, ggcomp, ggdecomp;
     // grouped batch calls: every field's scratch in one arena, the launch
@@ -486,7 +488,8 @@ uint64_t decompress_scratch(const gbsz_params &p, uint64_t n)
     const uint64_t nchunk = (n + p.chunk - 1) / p.chunk;
     const uint64_t nfaces = recon_faces_entries(lorenzo_geom(p, gd), gd);
     const uint64_t nscan = std::max<uint64_t>(nchunk, nfaces);
-    const uint64_t scan_bytes = std::max<uint64_t>(scan_partials(nscan) * 8, order_of(p) > 1 ? scan_partials(n) * 4 : 0);
+    const uint64_t scan_bytes = std::max<uint64_t>({scan_partials(nscan) * 8, order_of(p) > 1 ? scan_partials(n) * 4 : 0,
+                                                    scan_partials(n + 1) * 4});
     return buf_bytes(n * 2 + 64) + buf_bytes(n * 8 + 64) + buf_bytes(nchunk * 8 + 8) + buf_bytes(nfaces * 4 + 16) +
            buf_bytes(scan_bytes + 64);
 }
@@ -507,8 +510,10 @@ bool reserve_decompress(Slot *s, const Header &h)
     uint64_t gd[3];
     const uint64_t nfaces = recon_faces_entries(lorenzo_geom(h.p, gd), gd);
     const uint64_t nscan = std::max<uint64_t>(h.nchunk, nfaces);
-    // order > 1 scans the whole 1D field (4-byte partials)
-    const uint64_t scan_bytes = std::max<uint64_t>(scan_partials(nscan) * 8, order_of(h.p) > 1 ? scan_partials(n) * 4 : 0);
+    // order > 1 scans the whole 1D field, the warp decoder's fused mode the
+    // outlier list (4-byte partials)
+    const uint64_t scan_bytes = std::max<uint64_t>({scan_partials(nscan) * 8, order_of(h.p) > 1 ? scan_partials(n) * 4 : 0,
+                                                    scan_partials(h.m + 1) * 4});
     return s->codes.ensure(n * 2 + 64) && s->dscr.ensure(n * 8 + 64) && s->chunk_off.ensure(h.nchunk * 8 + 8) &&
            s->faces.ensure(nfaces * 4 + 16) && s->scan_part.ensure(scan_bytes + 64);
 }
@@ -594,6 +599,27 @@ gbsz_status enqueue_compress(gbsz_ctx *c, Slot *s, const float *d_field, const g
     return GBSZ_OK;
 }
 
+// Which decoder a field takes: the thread-per-chunk decoders, the
+// warp-per-chunk decoder writing codes, or the warp-per-chunk decoder with
+// the 1D reconstruction fused in.  By default the warp decoder takes fields
+// of at most 32 chunks per SM in chunks of at least 1024 symbols: there a
+// thread-per-chunk decoder leaves most of the GPU idle while each thread
+// walks its long chunk.  With more chunks, or short ones, the thread
+// decoders finish first (fewer instructions per symbol, and no
+// re-synchronisation or look-back per chunk).
+enum class WarpUse { Thread, Codes, Fused };
+
+WarpUse warp_use(const gbsz_ctx *c, const Header &h, uint32_t gnd, uint32_t order)
+{
+    if (c->decoder == 1 || h.p.chunk > kWarpMaxChunk) return WarpUse::Thread;
+    if (c->decoder == 0 && (h.nchunk > 32ull * (uint64_t)c->num_sms || h.p.chunk < 1024)) return WarpUse::Thread;
+    // 1D order-1 fields get their tile sums from the thread decoder, or are
+    // reconstructed inside the warp decoder
+    const bool line = gnd == 1 && !h.p.lorenzo_block && order == 1;
+    if (line) return h.n < (1ull << 30) ? WarpUse::Fused : WarpUse::Thread;
+    return WarpUse::Codes;
+}
+
 // Enqueues S7-S8 of one parsed archive on stream st using slot s.
 gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void *d_archive, float *d_field,
                                cudaStream_t st)
@@ -603,10 +629,14 @@ gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void
     const uint32_t gnd = lorenzo_geom(h.p, gd);
     const uint32_t order = order_of(h.p);
     const uint64_t nfaces = recon_faces_entries(gnd, gd);
-    const bool tile_sums = gnd == 1 && !h.p.lorenzo_block && order == 1;
+    const WarpUse wu = warp_use(c, h, gnd, order);
+    if (s == c->slots[0]) c->decoded_codes = wu != WarpUse::Fused;
+    const bool tile_sums = gnd == 1 && !h.p.lorenzo_block && order == 1 && wu != WarpUse::Fused;
     if (!reserve_decompress(s, h)) return GBSZ_ERR_OOM;
     cudaMemsetAsync(s->ctl, 0, sizeof(Control), st);
     if (tile_sums) cudaMemsetAsync(s->faces.p, 0, nfaces * 4, st);
+    // fused: the look-back words in the (unused) code buffer
+    if (wu == WarpUse::Fused) cudaMemsetAsync(s->codes.p, 0, h.nchunk * 8, st);
     const uint8_t *arc = static_cast<const uint8_t *>(d_archive);
 
     CodebookArgs cb = codebook_args(s);
@@ -650,11 +680,44 @@ gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void
     d.codes = s->codes.as<uint16_t>();
     d.ctl = s->ctl;
     int ndec = 0;
-    for (int ph = 0; ph < 2; ph++) {
-        if (ph == 1) cudaStreamWaitEvent(st, s->join, 0);
+    stage_begin(c, st, &e0);
+    ndec += launch_decode(d, st, 0);
+    if (wu == WarpUse::Fused)
+        ndec += launch_outlier_prefix(reinterpret_cast<const uint2 *>(arc + h.L.outl), h.m, s->dscr.as<uint32_t>(),
+                                      s->scan_part.as<uint32_t>(), st);
+    stage_end(c, st, 7, e0);
+    cudaStreamWaitEvent(st, s->join, 0);
+    stage_begin(c, st, &e0);
+    if (wu == WarpUse::Thread) {
+        ndec += launch_decode(d, st, 1);
+    } else {
+        WarpDecodeArgs w{};
+        w.d = d;
+        w.outl = reinterpret_cast<const uint2 *>(arc + h.L.outl);
+        w.odp = s->dscr.as<uint32_t>();
+        w.m = h.m;
+        w.ebx2 = h.ebx2;
+        w.out = d_field;
+        w.look = s->codes.as<unsigned long long>();
+        ndec += launch_decode_warp(w, wu == WarpUse::Fused, st);
+    }
+    stage_end(c, st, 8, e0);
+    if (wu == WarpUse::Fused) {  // S8 ran inside the decoder; only the verbatim exceptions remain
+        ReconArgs r{};
+        r.archive = arc;
+        r.off_exc = h.L.exc;
+        r.e = h.e;
+        r.ndim = 1;
+        r.dims[0] = n;
+        r.dims[1] = r.dims[2] = 1;
+        r.out = d_field;
+        r.ctl = s->ctl;
+        r.num_sms = c->num_sms;
         stage_begin(c, st, &e0);
-        ndec += launch_decode(d, st, ph);
-        stage_end(c, st, 7 + ph, e0);
+        const int nl = launch_exceptions(r, st);
+        stage_end(c, st, 9, e0);
+        c->launches += 1 + ndec + nl;
+        return GBSZ_OK;
     }
 
     ReconArgs r{};
@@ -706,6 +769,7 @@ template <typename F>
 gbsz_status run_batch(gbsz_ctx *c, BatchGraph &bg, std::vector<uint64_t> &key, cudaStream_t st, F enqueue)
 {
     key.push_back(c->profiling ? 1u : 0u);
+    key.push_back(c->decoder);
     key.push_back(g_alloc_gen.load());  // last: checked again after a capture
     if (bg.exec && key == bg.key) {
         c->launches += bg.launches;
@@ -1423,6 +1487,11 @@ gbsz_status gbsz_set_option(gbsz_ctx *c, int option, int64_t value)
         c->batch_mode = (uint32_t)value;
         return GBSZ_OK;
     }
+    if (option == GBSZ_OPT_DECODER) {
+        if (value < 0 || value > 2) return GBSZ_ERR_INVALID_ARG;
+        c->decoder = (uint32_t)value;
+        return GBSZ_OK;
+    }
     if (option == GBSZ_OPT_CODEWORD_BITS) {
         if (value != 0 && value != 64) return GBSZ_ERR_INVALID_ARG;
         c->cw64_only = value == 64 ? 1u : 0u;
@@ -1874,7 +1943,7 @@ gbsz_status gbsz_debug_copy(gbsz_ctx *c, int which, void *h_dst, size_t bytes)
         if (!c->have_compress || bytes != 12) return GBSZ_ERR_INVALID_ARG;
         std::memcpy(h_dst, c->last_sc, 12);
         return GBSZ_OK;
-    case 3: src = sl->codes.p; need = c->have_decompress ? c->last_dn * 2 : 0; break;
+    case 3: src = sl->codes.p; need = c->have_decompress && c->decoded_codes ? c->last_dn * 2 : 0; break;
     case 4: src = sl->codes_only.p; need = c->have_compress ? c->last_nbins * 8 : 0; break;
     case 5:
     case 6: {

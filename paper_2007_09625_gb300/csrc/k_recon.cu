@@ -96,7 +96,7 @@ __device__ __forceinline__ void scatter_outliers_body(const ReconArgs &a, uint64
         const int32_t d = *reinterpret_cast<const int32_t *>(o + 8 * t + 4);
         bool ok = idx < n;
         if (t > 0) ok &= idx > *reinterpret_cast<const uint32_t *>(o + 8 * (t - 1));
-        if (ok) ok &= a.codes[idx] == 0;
+        if (ok && a.codes) ok &= a.codes[idx] == 0;  // no codes: the fused 1D decoder kept them on chip
         if (ok) {
             a.dscr[idx] = d;
         } else {
@@ -181,7 +181,7 @@ __device__ __forceinline__ void patch_exceptions_body(const ReconArgs &a, uint64
         const uint32_t raw = *reinterpret_cast<const uint32_t *>(e + 8 * t + 4);
         bool ok = idx < n;
         if (t > 0) ok &= idx > *reinterpret_cast<const uint32_t *>(e + 8 * (t - 1));
-        if (ok) ok &= a.codes[idx] == 0;
+        if (ok && a.codes) ok &= a.codes[idx] == 0;  // no codes: the fused 1D decoder kept them on chip
         if (ok) reinterpret_cast<uint32_t *>(a.out)[idx] = raw;
         else atomicOr(&a.ctl->error, DERR_CORRUPT);
     }
@@ -1224,12 +1224,18 @@ void launch_reconstruct(const ReconArgs &a, cudaStream_t st, int *launches)
         }
         nl++;
     }
-    if (a.e) {
-        const int grid = (int)std::min<uint64_t>((a.e + 255) / 256, (uint64_t)a.num_sms * 16);
-        k_patch_exceptions<<<grid, 256, 0, st>>>(a, n);
-        nl++;
-    }
+    nl += launch_exceptions(a, st);
     if (launches) *launches += nl;
+}
+
+int launch_exceptions(const ReconArgs &a, cudaStream_t st)
+{
+    if (!a.e) return 0;
+    const Geo g = make_geo(a.ndim, a.dims);
+    const uint64_t n = g.n[0] * g.n[1] * g.n[2];
+    const int grid = (int)std::min<uint64_t>((a.e + 255) / 256, (uint64_t)a.num_sms * 16);
+    k_patch_exceptions<<<grid, 256, 0, st>>>(a, n);
+    return 1;
 }
 
 }  // namespace gbsz

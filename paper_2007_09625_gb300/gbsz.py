@@ -57,6 +57,7 @@ SIGNATURES = {
 }
 OPT_CODEWORD_BITS = 1
 OPT_BATCH_MODE = 3
+OPT_DECODER = 4
 
 
 class GbszError(RuntimeError):

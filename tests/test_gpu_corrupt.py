@@ -17,6 +17,7 @@ CASES = [
     # with one and several tiles per chunk, 1D through the long-code decoder,
     # 2D and 3D; every case has outliers and most have exceptions
     ("walk", (70001,), 1e-4, ref.EB_REL, 16, 256),
+    ("walk", (300007,), 1e-4, ref.EB_REL, 512, 2048),
     ("walk", (70001,), 3e-5, ref.EB_REL, 32, 8192),
     ("walk", (50000,), 1e-6, ref.EB_REL, 32768, 1024),
     ("grf", (150, 170), 1e-5, ref.EB_REL, 64, 4096),
@@ -37,11 +38,20 @@ def ctx(gb):
     c.close()
 
 
-def gpu_status(gb, ctx, a, shape):
+@pytest.fixture(params=[0, 1, 2], ids=["default", "thread", "warp"])
+def decoder(request):
+    return request.param
+
+
+def gpu_status(gb, ctx, a, shape, decoder=0):
     t = torch.from_numpy(np.ascontiguousarray(a)).cuda()
     out = torch.empty(shape, dtype=torch.float32, device="cuda")
-    st = ctx.decompress_status(t, a.size, out)
-    torch.cuda.synchronize()
+    ctx.set_option(gb.OPT_DECODER, decoder)
+    try:
+        st = ctx.decompress_status(t, a.size, out)
+        torch.cuda.synchronize()
+    finally:
+        ctx.set_option(gb.OPT_DECODER, 0)
     return st, out.cpu().numpy()
 
 
@@ -78,20 +88,20 @@ def targeted(a):
 
 
 @pytest.mark.parametrize("kind,shape,eb,mode,R,C", CASES, ids=[f"{c[0]}{'x'.join(map(str, c[1]))}-R{c[4]}" for c in CASES])
-def test_targeted_corruptions_are_rejected(gb, ctx, kind, shape, eb, mode, R, C):
+def test_targeted_corruptions_are_rejected(gb, ctx, decoder, kind, shape, eb, mode, R, C):
     x = workloads.field_for(kind, shape, seed=77 + R)
     a = ref.compress(x, eb, mode, radius=R, chunk=C)
     for name, b in targeted(a).items():
-        st, _ = gpu_status(gb, ctx, b, shape)
+        st, _ = gpu_status(gb, ctx, b, shape, decoder)
         assert st != gb.OK, name
         assert ref.decompress_status(b) != ref.OK, name
     # the context still decodes a valid archive
-    st, y = gpu_status(gb, ctx, a, shape)
+    st, y = gpu_status(gb, ctx, a, shape, decoder)
     assert st == gb.OK and np.array_equal(y.view(np.uint32), ref.decompress(a).view(np.uint32))
 
 
 @pytest.mark.parametrize("kind,shape,eb,mode,R,C", CASES, ids=[f"{c[0]}{'x'.join(map(str, c[1]))}-R{c[4]}" for c in CASES])
-def test_stream_bit_flips_agree_with_oracle(gb, ctx, kind, shape, eb, mode, R, C):
+def test_stream_bit_flips_agree_with_oracle(gb, ctx, decoder, kind, shape, eb, mode, R, C):
     """Single-bit flips inside the bitstream: the GPU either rejects the
     archive or decodes it to exactly the oracle's floats."""
     x = workloads.field_for(kind, shape, seed=91 + R)
@@ -103,11 +113,11 @@ def test_stream_bit_flips_agree_with_oracle(gb, ctx, kind, shape, eb, mode, R, C
         b = a.copy()
         pos = int(rng.integers(lo, hi))
         b[pos] ^= np.uint8(1 << int(rng.integers(0, 8)))
-        st, y = gpu_status(gb, ctx, b, shape)
+        st, y = gpu_status(gb, ctx, b, shape, decoder)
         ost = ref.decompress_status(b)
         assert st in (gb.OK, gb.ERR_CORRUPT)
         if st == gb.OK:
             assert ost == ref.OK
             assert np.array_equal(y.view(np.uint32), ref.decompress(b).view(np.uint32))
-    st, y = gpu_status(gb, ctx, a, shape)
+    st, y = gpu_status(gb, ctx, a, shape, decoder)
     assert st == gb.OK
