@@ -122,6 +122,14 @@ void gbsz_destroy(gbsz_ctx *ctx);
  *     of at least 1024 symbols, else thread; 1 = thread always; 2 = warp wherever it applies.  The results
  *     and statuses are the same either way. */
 #define GBSZ_OPT_DECODER 4
+/*   GBSZ_OPT_LORENZO_SLAB  extent of a dual-quant tile along its swept
+ *     dimension (S1+S2, Sec. 3.1): rows for 2D fields (tiles of 512 x slab
+ *     points), planes for 3D (tiles of 32 x 32 x slab).  0 (default) = the
+ *     autotuner's choice for the field's key, else the built-in rule (8 rows;
+ *     planes halved from the full depth until there are 8 tiles per SM or 4
+ *     planes); 1..65536 = that extent.  The archive is the same either way
+ *     (the tile boundaries only decide which threads compute which points). */
+#define GBSZ_OPT_LORENZO_SLAB 5
 gbsz_status gbsz_set_option(gbsz_ctx *ctx, int option, int64_t value);
 
 /* Worst-case archive size in bytes for these parameters (0 if invalid).
@@ -134,18 +142,32 @@ size_t gbsz_compress_bound(const gbsz_params *p);
 uint32_t gbsz_auto_chunk(const gbsz_params *p);
 
 /* Measured choice of the Huffman chunk (Sec. 3.2.4; the paper tunes it by
- * hand, Sec. 4.2).  Times compress + decompress of the field at d_field for
- * chunk sizes 256..4096 and the rule's choice on `stream` (CUDA events, best
- * of two runs each), and writes *out = *p with the fastest chunk.  The choice
- * is remembered per context for the key (ndim, dims, radius, lorenzo_block,
- * lorenzo_order):
- * later calls with the same key return it without measuring, so every
- * single or batched call given *out produces the same archive.  *ms (may be
- * NULL) gets the measured time of the chosen chunk (0 when remembered).
+ * hand, Sec. 4.2) and of two knobs that leave the bytes alone.  On `stream`
+ * (CUDA events, best of two runs after a warm-up each):
+ *   1. compress + decompress of the field at d_field for chunk sizes
+ *      256..4096 and the rule's choice; *out = *p with the fastest chunk;
+ *   2. at that chunk (if at most 4096), decompress with the thread-per-chunk
+ *      and the warp-per-chunk decoders (GBSZ_OPT_DECODER 1 and 2);
+ *   3. for 2D and 3D fields of Lorenzo order 1, compress with dual-quant
+ *      tiles of 4..64 rows / planes and the built-in rule
+ *      (GBSZ_OPT_LORENZO_SLAB).
+ * The choices are remembered per context for the key (ndim, dims, radius,
+ * lorenzo_block, lorenzo_order): later calls with the same key return the
+ * chunk without measuring, so every single or batched call given *out
+ * produces the same archive, and calls on fields of the key use the tuned
+ * decoder (for archives of the tuned chunk) and tile extent while the
+ * context's options for them are 0.  *ms (may be NULL) gets the measured
+ * compress + decompress time of the chosen chunk (0 when remembered).
  * Allocates scratch for one archive and one field.  Errors: INVALID_ARG,
  * OOM, CUDA, and any error of the compress/decompress calls it makes. */
 gbsz_status gbsz_autotune(gbsz_ctx *ctx, const float *d_field, const gbsz_params *p,
                           gbsz_params *out, float *ms, void *stream);
+
+/* What gbsz_autotune chose for the key of *p: knobs[0] = chunk, knobs[1] =
+ * decoder (1 thread, 2 warp per chunk; 0 = not measured: chunk above 4096),
+ * knobs[2] = dual-quant tile extent (0 = the built-in rule).  Host-only.
+ * Errors: INVALID_ARG (NULL argument, or no choice remembered for the key). */
+gbsz_status gbsz_tuned_knobs(gbsz_ctx *ctx, const gbsz_params *p, uint32_t knobs[3]);
 
 /* Compresses n = prod(dims) floats at d_field into the archive at d_archive
  * (device memory, 16-byte aligned, `capacity` bytes).  Stages: S0 error

@@ -338,6 +338,7 @@ struct QuantArgs {
     uint32_t *excm;       // order > 1: exception bit per point (zeroed, n/32 + 1 words)
     Control *ctl;
     int num_sms;
+    uint32_t slab;  // rows (2D) or planes (3D) each tile sweeps; 0 = the built-in rule
 };
 // block extent of the per-block Lorenzo mode (Sec. 3.1.1): 32, 16x16, 8x8x8
 __host__ __device__ constexpr uint32_t lorenzo_block_extent(uint32_t ndim)

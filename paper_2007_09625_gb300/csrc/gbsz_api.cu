@@ -15,6 +15,7 @@
 #include "scan.cuh"
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <cstring>
@@ -210,6 +211,13 @@ struct Slot {
 
 }  // namespace
 
+// what gbsz_autotune chose for one key: the chunk (part of the archive), and
+// two knobs that leave the bytes alone -- the decoder (1 thread, 2 warp per
+// chunk) and the rows / planes each dual-quant tile sweeps (0: the rule)
+struct Tuned {
+    uint32_t chunk, decoder, slab;
+};
+
 struct gbsz_ctx {
     int device = 0;
     int num_sms = 152;
@@ -238,6 +246,7 @@ struct gbsz_ctx {
     // options
     uint32_t cw64_only = 0;  // GBSZ_OPT_CODEWORD_BITS = 64
     uint32_t decoder = 0;    // GBSZ_OPT_DECODER
+    uint32_t slab = 0;       // GBSZ_OPT_LORENZO_SLAB
     // captured batch calls, and captured single-field calls
     BatchGraph gcomp, gdecomp, gsc, gsd, ggcomp, ggdecomp;
     // grouped batch calls: every field's scratch in one arena, the launch
@@ -245,8 +254,9 @@ struct gbsz_ctx {
     Buf garena, gplan_dev;
     HostBuf<uint8_t> gplan_host;
     uint32_t batch_mode = 0;  // GBSZ_OPT_BATCH_MODE: 0 grouped launches where possible, 1 slot streams
-    // autotuned chunks, keyed by (ndim, dims, radius, lorenzo_block, lorenzo_order)
-    std::vector<std::pair<std::vector<uint64_t>, uint32_t>> tuned;
+    // autotuned knobs, keyed by (ndim, dims, radius, lorenzo_block, lorenzo_order)
+    std::vector<std::pair<std::array<uint64_t, 8>, Tuned>> tuned;
+    uint64_t tuned_gen = 0;  // bumped when an entry is added (captured graphs depend on it)
     Buf tune_arc, tune_out;
     // timing
     bool profiling = false;
@@ -518,6 +528,30 @@ bool reserve_decompress(Slot *s, const Header &h)
            s->faces.ensure(nfaces * 4 + 16) && s->scan_part.ensure(scan_bytes + 64);
 }
 
+// the autotuner's key of a field: (ndim, dims, radius, lorenzo_block, lorenzo_order)
+std::array<uint64_t, 8> tune_key(const gbsz_params &p)
+{
+    return {p.ndim, p.dims[0], p.dims[1], p.dims[2], p.dims[3], p.radius, p.lorenzo_block, order_of(p)};
+}
+
+const Tuned *find_tuned(const gbsz_ctx *c, const gbsz_params &p)
+{
+    if (c->tuned.empty()) return nullptr;
+    const std::array<uint64_t, 8> k = tune_key(p);
+    for (const auto &t : c->tuned)
+        if (t.first == k) return &t.second;
+    return nullptr;
+}
+
+// rows (2D) or planes (3D) each dual-quant tile sweeps: the option, else the
+// tuned choice for this field's key, else 0 (the kernels' rule)
+uint32_t slab_for(const gbsz_ctx *c, const gbsz_params &p)
+{
+    if (c->slab) return c->slab;
+    const Tuned *t = find_tuned(c, p);
+    return t ? t->slab : 0u;
+}
+
 // Enqueues S0-S6 of one field on stream st using slot s; no synchronisation.
 gbsz_status enqueue_compress(gbsz_ctx *c, Slot *s, const float *d_field, const gbsz_params &p, uint64_t n,
                              void *d_archive, size_t capacity, cudaStream_t st)
@@ -551,6 +585,7 @@ gbsz_status enqueue_compress(gbsz_ctx *c, Slot *s, const float *d_field, const g
     q.excm = order > 1 ? s->excm.as<uint32_t>() : nullptr;
     q.ctl = s->ctl;
     q.num_sms = c->num_sms;
+    q.slab = slab_for(c, p);
     stage_begin(c, st, &e0);
     const int nq = launch_dualquant(q, st);
     stage_end(c, st, 1, e0);
@@ -611,8 +646,13 @@ enum class WarpUse { Thread, Codes, Fused };
 
 WarpUse warp_use(const gbsz_ctx *c, const Header &h, uint32_t gnd, uint32_t order)
 {
-    if (c->decoder == 1 || h.p.chunk > kWarpMaxChunk) return WarpUse::Thread;
-    if (c->decoder == 0 && (h.nchunk > 32ull * (uint64_t)c->num_sms || h.p.chunk < 1024)) return WarpUse::Thread;
+    uint32_t dec = c->decoder;
+    if (dec == 0) {  // the tuned choice for this key, when it was measured at this chunk
+        const Tuned *t = find_tuned(c, h.p);
+        if (t && t->chunk == h.p.chunk) dec = t->decoder;
+    }
+    if (dec == 1 || h.p.chunk > kWarpMaxChunk) return WarpUse::Thread;
+    if (dec == 0 && (h.nchunk > 32ull * (uint64_t)c->num_sms || h.p.chunk < 1024)) return WarpUse::Thread;
     // 1D order-1 fields get their tile sums from the thread decoder, or are
     // reconstructed inside the warp decoder
     const bool line = gnd == 1 && !h.p.lorenzo_block && order == 1;
@@ -770,6 +810,8 @@ gbsz_status run_batch(gbsz_ctx *c, BatchGraph &bg, std::vector<uint64_t> &key, c
 {
     key.push_back(c->profiling ? 1u : 0u);
     key.push_back(c->decoder);
+    key.push_back(c->slab);
+    key.push_back(c->tuned_gen);
     key.push_back(g_alloc_gen.load());  // last: checked again after a capture
     if (bg.exec && key == bg.key) {
         c->launches += bg.launches;
@@ -1015,6 +1057,7 @@ gbsz_status compress_batch_grouped(gbsz_ctx *c, uint32_t count, const float *con
         q.order = 1;
         q.ctl = f.ctl;
         q.num_sms = c->num_sms;
+        q.slab = slab_for(c, p);
         size_t sm = 0;
         q_b[i] = dualquant_plan(q, qi[i].t, &qvar[i], &sm);
         q_smem = std::max(q_smem, sm);
@@ -1487,6 +1530,11 @@ gbsz_status gbsz_set_option(gbsz_ctx *c, int option, int64_t value)
         c->batch_mode = (uint32_t)value;
         return GBSZ_OK;
     }
+    if (option == GBSZ_OPT_LORENZO_SLAB) {
+        if (value < 0 || value > 65536) return GBSZ_ERR_INVALID_ARG;
+        c->slab = (uint32_t)value;
+        return GBSZ_OK;
+    }
     if (option == GBSZ_OPT_DECODER) {
         if (value < 0 || value > 2) return GBSZ_ERR_INVALID_ARG;
         c->decoder = (uint32_t)value;
@@ -1513,15 +1561,12 @@ gbsz_status gbsz_autotune(gbsz_ctx *c, const float *d_field, const gbsz_params *
     uint64_t n;
     if (!c || !d_field || !p || !out || !valid_params(p, &n)) return GBSZ_ERR_INVALID_ARG;
     DevGuard g(c->device);
-    const std::vector<uint64_t> key{p->ndim,   p->dims[0], p->dims[1],        p->dims[2],
-                                    p->dims[3], p->radius,  p->lorenzo_block, order_of(*p)};
     *out = *p;
     if (ms) *ms = 0.0f;
-    for (const auto &t : c->tuned)
-        if (t.first == key) {
-            out->chunk = t.second;
-            return GBSZ_OK;
-        }
+    if (const Tuned *t = find_tuned(c, *p)) {
+        out->chunk = t->chunk;
+        return GBSZ_OK;
+    }
     std::vector<uint32_t> cand{256, 512, 1024, 2048, 4096};
     const uint32_t rule = auto_chunk(n);
     if (std::find(cand.begin(), cand.end(), rule) == cand.end()) cand.push_back(rule);
@@ -1534,35 +1579,88 @@ gbsz_status gbsz_autotune(gbsz_ctx *c, const float *d_field, const gbsz_params *
     if (!c->tune_arc.ensure(cap) || !c->tune_out.ensure(n * 4)) return GBSZ_ERR_OOM;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     cudaEvent_t e0 = c->ev(), e1 = c->ev();
-    float best = -1.0f;
-    uint32_t best_c = rule;
     gbsz_status status = GBSZ_OK;
-    for (uint32_t C : cand) {
-        q.chunk = C;
+    size_t nb = 0;
+    // best of two timed runs after a warm-up; what = 1 compress, 2 decompress, 3 both
+    auto timed = [&](int what) -> float {
         float tmin = -1.0f;
-        for (int rep = 0; rep < 3 && status == GBSZ_OK; rep++) {  // the first run is a warm-up
-            size_t nb = 0;
+        for (int rep = 0; rep < 3 && status == GBSZ_OK; rep++) {
             cudaEventRecord(e0, st);
-            status = gbsz_compress(c, d_field, &q, c->tune_arc.p, cap, &nb, stream);
-            if (status == GBSZ_OK) status = gbsz_decompress(c, c->tune_arc.p, nb, c->tune_out.as<float>(), n, stream);
+            if (what & 1) status = gbsz_compress(c, d_field, &q, c->tune_arc.p, cap, &nb, stream);
+            if (status == GBSZ_OK && (what & 2))
+                status = gbsz_decompress(c, c->tune_arc.p, nb, c->tune_out.as<float>(), n, stream);
             cudaEventRecord(e1, st);
             if (cudaEventSynchronize(e1) != cudaSuccess) status = GBSZ_ERR_CUDA;
             float t = 0.0f;
             cudaEventElapsedTime(&t, e0, e1);
             if (rep > 0 && (tmin < 0.0f || t < tmin)) tmin = t;
         }
+        return tmin;
+    };
+    // 1. the Huffman chunk (changes the archive), with the knobs as they are
+    float best = -1.0f;
+    Tuned tu{rule, 0, 0};
+    for (uint32_t C : cand) {
+        q.chunk = C;
+        const float t = timed(3);
         if (status != GBSZ_OK) break;
-        if (best < 0.0f || tmin < best) {
-            best = tmin;
-            best_c = C;
+        if (best < 0.0f || t < best) {
+            best = t;
+            tu.chunk = C;
         }
+    }
+    q.chunk = tu.chunk;
+    const uint32_t save_dec = c->decoder, save_slab = c->slab;
+    // 2. the decoder's granularity: a thread or a warp per chunk (same floats)
+    if (status == GBSZ_OK && tu.chunk <= kWarpMaxChunk) {
+        status = gbsz_compress(c, d_field, &q, c->tune_arc.p, cap, &nb, stream);
+        float bt = -1.0f;
+        for (uint32_t dec : {1u, 2u}) {
+            c->decoder = dec;
+            const float t = timed(2);
+            if (status != GBSZ_OK) break;
+            if (bt < 0.0f || t < bt) {
+                bt = t;
+                tu.decoder = dec;
+            }
+        }
+        c->decoder = save_dec;
+    }
+    // 3. the dual-quant tile's extent along y (2D) or z (3D) (same bytes)
+    uint64_t gd[3];
+    const uint32_t gnd = lorenzo_geom(*p, gd);
+    if (status == GBSZ_OK && gnd > 1 && order_of(*p) == 1) {
+        float bt = -1.0f;
+        for (uint32_t sl : {0u, 4u, 8u, 16u, 32u, 64u}) {
+            if (sl > gd[gnd - 1]) break;
+            c->slab = sl;
+            const float t = timed(1);
+            if (status != GBSZ_OK) break;
+            if (bt < 0.0f || t < bt) {
+                bt = t;
+                tu.slab = sl;
+            }
+        }
+        c->slab = save_slab;
     }
     c->pool.push_back(e0);
     c->pool.push_back(e1);
     if (status != GBSZ_OK) return status;
-    c->tuned.push_back({key, best_c});
-    out->chunk = best_c;
+    c->tuned.push_back({tune_key(*p), tu});
+    c->tuned_gen++;
+    out->chunk = tu.chunk;
     if (ms) *ms = best;
+    return GBSZ_OK;
+}
+
+gbsz_status gbsz_tuned_knobs(gbsz_ctx *c, const gbsz_params *p, uint32_t knobs[3])
+{
+    if (!c || !p || !knobs) return GBSZ_ERR_INVALID_ARG;
+    const Tuned *t = find_tuned(c, *p);
+    if (!t) return GBSZ_ERR_INVALID_ARG;
+    knobs[0] = t->chunk;
+    knobs[1] = t->decoder;
+    knobs[2] = t->slab;
     return GBSZ_OK;
 }
 

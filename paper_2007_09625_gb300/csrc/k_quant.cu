@@ -392,7 +392,7 @@ __global__ void __launch_bounds__(kQ1Threads) k_dualquant_1d(const __grid_consta
 }
 
 // ---------------------------------------------------------------------------
-// 2D: 128 threads; tile 512 (x) x 8 (y) swept row by row.  Each thread holds
+// 2D: 128 threads; tile 512 (x) x ty (y, 8 unless set) swept row by row.  Each thread holds
 // 4 points of a row (x = x0 + tid + 128 j).  Three row buffers of prequantized
 // integers in shared memory (slot 0 = the halo column x0 - 1); the next row's
 // floats are prefetched into registers while the current row is processed.
@@ -402,7 +402,8 @@ constexpr int kQ2TX = 512;
 constexpr int kQ2TY = 8;
 
 template <bool WIN>
-__device__ __forceinline__ void dualquant_2d_body(const QuantArgs &a, uint32_t ntx, uint32_t nty, VGrid vg)
+__device__ __forceinline__ void dualquant_2d_body(const QuantArgs &a, uint32_t ntx, uint32_t nty, uint32_t ty,
+                                                  VGrid vg)
 {
     extern __shared__ uint32_t sh_hist[];
     __shared__ int32_t rows[3][kQ2TX + 1];
@@ -418,8 +419,8 @@ __device__ __forceinline__ void dualquant_2d_body(const QuantArgs &a, uint32_t n
     int buf = 0;
     for (uint32_t tile = vg.bid; tile < ntiles; tile += vg.nb) {
         const uint32_t x0 = (tile % ntx) * kQ2TX;
-        const int y0 = (int)((tile / ntx) * kQ2TY);
-        const int y1 = (int)min(ny, (uint32_t)y0 + kQ2TY);
+        const int y0 = (int)((tile / ntx) * ty);
+        const int y1 = (int)min(ny, (uint32_t)y0 + ty);
         // per-block mode: neighbours across a block edge are padding (0)
         uint32_t mL[4];
         bool inx[4];
@@ -498,9 +499,9 @@ __device__ __forceinline__ void dualquant_2d_body(const QuantArgs &a, uint32_t n
 
 template <bool WIN>
 __global__ void __launch_bounds__(kQ2Threads) k_dualquant_2d(const __grid_constant__ QuantArgs a, uint32_t ntx,
-                                                             uint32_t nty)
+                                                             uint32_t nty, uint32_t ty)
 {
-    dualquant_2d_body<WIN>(a, ntx, nty, vgrid_self());
+    dualquant_2d_body<WIN>(a, ntx, nty, ty, vgrid_self());
 }
 
 // ---------------------------------------------------------------------------
@@ -659,7 +660,7 @@ __global__ void __launch_bounds__(D == 1 ? kQ1Threads : D == 2 ? kQ2Threads : kQ
     VGrid vg;
     const QuantItem &q = items[group_item(first, ni, vg)];
     if (D == 1) dualquant_1d_body<VEC, WIN>(q.a, q.t[0], vg);
-    else if (D == 2) dualquant_2d_body<WIN>(q.a, q.t[0], q.t[1], vg);
+    else if (D == 2) dualquant_2d_body<WIN>(q.a, q.t[0], q.t[1], q.t[2], vg);
     else dualquant_3d_body<WIN>(q.a, q.t[0], q.t[1], q.t[2], q.t[3], vg);
 }
 
@@ -762,6 +763,35 @@ void launch_minmax_group(const MinmaxItem *items, const uint32_t *first, uint32_
     else k_minmax_group<false><<<blocks, 256, 0, st>>>(items, first, ni);
 }
 
+// 2D tiles: t = {tiles along x, tiles along y, rows per tile}
+static void tiles_2d(const QuantArgs &a, uint32_t t[4])
+{
+    const uint32_t ty = a.slab ? a.slab : (uint32_t)kQ2TY;
+    t[0] = (uint32_t)((a.dims[0] + kQ2TX - 1) / kQ2TX);
+    t[1] = (uint32_t)((a.dims[1] + ty - 1) / ty);
+    t[2] = ty;
+    t[3] = 0;
+}
+
+// 3D tiles: t = {tiles along x, y, z, planes per tile}; by default the
+// planes halve from the whole depth until there are 8 tiles per SM (or 4 planes)
+static void tiles_3d(const QuantArgs &a, uint32_t t[4])
+{
+    const uint32_t ntx = (uint32_t)((a.dims[0] + kQ3T - 1) / kQ3T);
+    const uint32_t nty = (uint32_t)((a.dims[1] + kQ3T - 1) / kQ3T);
+    const uint64_t nz = a.dims[2];
+    uint64_t tz = nz;
+    if (a.slab) {
+        tz = std::min<uint64_t>(a.slab, nz);
+    } else {
+        while (tz > 4 && (uint64_t)ntx * nty * ((nz + tz - 1) / tz) < (uint64_t)a.num_sms * 8) tz = (tz + 1) / 2;
+    }
+    t[0] = ntx;
+    t[1] = nty;
+    t[2] = (uint32_t)((nz + tz - 1) / tz);
+    t[3] = (uint32_t)tz;
+}
+
 uint32_t dualquant_plan(const QuantArgs &a, uint32_t t[4], int *variant, size_t *smem)
 {
     const uint32_t nbins = 2 * a.radius;
@@ -776,23 +806,13 @@ uint32_t dualquant_plan(const QuantArgs &a, uint32_t t[4], int *variant, size_t 
         return (uint32_t)std::min<uint64_t>(t[0], (uint64_t)a.num_sms * 8);
     }
     if (a.ndim == 2) {
-        t[0] = (uint32_t)((a.dims[0] + kQ2TX - 1) / kQ2TX);
-        t[1] = (uint32_t)((a.dims[1] + kQ2TY - 1) / kQ2TY);
+        tiles_2d(a, t);
         *variant = 8 + (win ? 1 : 0);
         return (uint32_t)std::min<uint64_t>((uint64_t)t[0] * t[1], (uint64_t)a.num_sms * 12);
     }
-    const uint32_t ntx = (uint32_t)((a.dims[0] + kQ3T - 1) / kQ3T);
-    const uint32_t nty = (uint32_t)((a.dims[1] + kQ3T - 1) / kQ3T);
-    const uint64_t nz = a.dims[2];
-    uint64_t tz = nz;
-    while (tz > 4 && (uint64_t)ntx * nty * ((nz + tz - 1) / tz) < (uint64_t)a.num_sms * 8) tz = (tz + 1) / 2;
-    const uint32_t ntz = (uint32_t)((nz + tz - 1) / tz);
-    t[0] = ntx;
-    t[1] = nty;
-    t[2] = ntz;
-    t[3] = (uint32_t)tz;
+    tiles_3d(a, t);
     *variant = 12 + (win ? 1 : 0);
-    return (uint32_t)std::min<uint64_t>((uint64_t)ntx * nty * ntz, (uint64_t)a.num_sms * 8);
+    return (uint32_t)std::min<uint64_t>((uint64_t)t[0] * t[1] * t[2], (uint64_t)a.num_sms * 8);
 }
 
 void launch_dualquant_group(int variant, const QuantItem *items, const uint32_t *first, uint32_t ni,
@@ -834,23 +854,19 @@ int launch_dualquant(const QuantArgs &a, cudaStream_t st)
         else if (win) k_dualquant_1d<false, true><<<grid, kQ1Threads, hist_bytes, st>>>(a, ntiles);
         else k_dualquant_1d<false, false><<<grid, kQ1Threads, hist_bytes, st>>>(a, ntiles);
     } else if (a.ndim == 2) {
-        const uint32_t ntx = (uint32_t)((a.dims[0] + kQ2TX - 1) / kQ2TX);
-        const uint32_t nty = (uint32_t)((a.dims[1] + kQ2TY - 1) / kQ2TY);
-        const uint64_t ntiles = (uint64_t)ntx * nty;
+        uint32_t t[4];
+        tiles_2d(a, t);
+        const uint64_t ntiles = (uint64_t)t[0] * t[1];
         const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)a.num_sms * 12);
-        if (nbins <= kWinBins) k_dualquant_2d<true><<<grid, kQ2Threads, hist_bytes, st>>>(a, ntx, nty);
-        else k_dualquant_2d<false><<<grid, kQ2Threads, hist_bytes, st>>>(a, ntx, nty);
+        if (nbins <= kWinBins) k_dualquant_2d<true><<<grid, kQ2Threads, hist_bytes, st>>>(a, t[0], t[1], t[2]);
+        else k_dualquant_2d<false><<<grid, kQ2Threads, hist_bytes, st>>>(a, t[0], t[1], t[2]);
     } else {
-        const uint32_t ntx = (uint32_t)((a.dims[0] + kQ3T - 1) / kQ3T);
-        const uint32_t nty = (uint32_t)((a.dims[1] + kQ3T - 1) / kQ3T);
-        const uint64_t nz = a.dims[2];
-        uint64_t tz = nz;
-        while (tz > 4 && (uint64_t)ntx * nty * ((nz + tz - 1) / tz) < (uint64_t)a.num_sms * 8) tz = (tz + 1) / 2;
-        const uint32_t ntz = (uint32_t)((nz + tz - 1) / tz);
-        const uint64_t ntiles = (uint64_t)ntx * nty * ntz;
+        uint32_t t[4];
+        tiles_3d(a, t);
+        const uint64_t ntiles = (uint64_t)t[0] * t[1] * t[2];
         const int grid = (int)std::min<uint64_t>(ntiles, (uint64_t)a.num_sms * 8);
-        if (nbins <= kWinBins) k_dualquant_3d<true><<<grid, kQ3Threads, hist_bytes, st>>>(a, ntx, nty, ntz, (uint32_t)tz);
-        else k_dualquant_3d<false><<<grid, kQ3Threads, hist_bytes, st>>>(a, ntx, nty, ntz, (uint32_t)tz);
+        if (nbins <= kWinBins) k_dualquant_3d<true><<<grid, kQ3Threads, hist_bytes, st>>>(a, t[0], t[1], t[2], t[3]);
+        else k_dualquant_3d<false><<<grid, kQ3Threads, hist_bytes, st>>>(a, t[0], t[1], t[2], t[3]);
     }
     return 1;
 }

@@ -53,11 +53,13 @@ SIGNATURES = {
     "gbsz_server_memory": ([_P, _P], C.c_int),
     "gbsz_memory_usage": ([_P, C.POINTER(C.c_uint64), C.POINTER(C.c_uint32)], C.c_int),
     "gbsz_release_scratch": ([_P], C.c_int),
+    "gbsz_tuned_knobs": ([_P, _P, _P], C.c_int),
     "gbsz_scratch_bytes": ([_P, C.c_int, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int),
 }
 OPT_CODEWORD_BITS = 1
 OPT_BATCH_MODE = 3
 OPT_DECODER = 4
+OPT_LORENZO_SLAB = 5
 
 
 class GbszError(RuntimeError):
@@ -177,6 +179,15 @@ class Context:
         if st != OK:
             raise GbszError(st, "gbsz_autotune")
         return out, ms.value
+
+    def tuned_knobs(self, params):
+        """(chunk, decoder, slab) that autotune chose for params' key (see
+        gbsz_tuned_knobs)."""
+        k = (C.c_uint32 * 3)()
+        st = load().gbsz_tuned_knobs(self.h, C.byref(params), k)
+        if st != OK:
+            raise GbszError(st, "gbsz_tuned_knobs")
+        return tuple(k)
 
     def compress_params(self, field, params, out=None, stream=None):
         """Compress with an explicit Params (e.g. from autotune)."""

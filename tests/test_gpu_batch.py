@@ -151,6 +151,52 @@ def test_autotune_choice_is_remembered_and_reproducible(gb, ctx):
     assert all(n_ == oa.size and np.array_equal(a[:n_].cpu().numpy(), oa) for a, n_ in zip(arcs, nbs))
 
 
+def test_autotune_reports_knobs_and_tuned_calls_match_oracle(gb, ctx):
+    """The tuner's decoder and tile-extent choices are reported per key, and
+    compress / decompress calls that use them (options at 0) give the
+    oracle's archive and floats."""
+    for kind, shape in (("lognormal", (40, 48, 56)), ("grf", (257, 333))):
+        f = workloads.field_for(kind, shape, seed=12)
+        t = torch.from_numpy(f).cuda()
+        p, _ = ctx.autotune(t, 1e-4)
+        chunk, decoder, slab = ctx.tuned_knobs(p)
+        assert chunk == p.chunk
+        assert decoder in ((1, 2) if p.chunk <= 4096 else (0,))
+        assert slab in (0, 4, 8, 16, 32, 64)
+        arc, nb = ctx.compress_params(t, p)
+        oa = ref.compress(f, 1e-4, ref.EB_REL, 512, p.chunk)
+        assert nb == oa.size and np.array_equal(arc[:nb].cpu().numpy(), oa)
+        y = ctx.decompress(arc, nb)
+        torch.cuda.synchronize()
+        assert np.array_equal(y.cpu().numpy().view(np.uint32), ref.decompress(oa).view(np.uint32))
+    with pytest.raises(gb.GbszError):
+        ctx.tuned_knobs(gb.make_params([5, 6, 7], 1e-4))
+
+
+@pytest.mark.parametrize("kind,shape,lblock", [("lognormal", (37, 41, 67), 0), ("sinus", (45, 50, 61), 1),
+                                               ("grf", (181, 1037), 0), ("sinus", (150, 170), 1)])
+def test_lorenzo_slab_option_keeps_bytes(gb, ctx, kind, shape, lblock):
+    """Any dual-quant tile extent along the swept dimension gives the
+    oracle's archive, in single and grouped batch calls."""
+    f = workloads.field_for(kind, shape, seed=13)
+    t = torch.from_numpy(f).cuda()
+    oa = ref.compress(f, 1e-4, ref.EB_REL, 512, 1024, lblock=lblock)
+    try:
+        for slab in (1, 3, 4, 7, 16, 64, 1000):
+            ctx.set_option(gb.OPT_LORENZO_SLAB, slab)
+            arc, nb = ctx.compress(t, 1e-4, gb.EB_REL, 512, 1024, lblock=lblock)
+            torch.cuda.synchronize()
+            assert nb == oa.size and np.array_equal(arc[:nb].cpu().numpy(), oa), slab
+            p = gb.make_params(gb.field_dims(t), 1e-4, gb.EB_REL, 512, 1024, lblock=lblock)
+            arcs, nbs, _ = ctx.compress_batch([t, t], None, params=[p, p])
+            torch.cuda.synchronize()
+            assert all(n_ == oa.size and np.array_equal(a[:n_].cpu().numpy(), oa) for a, n_ in zip(arcs, nbs)), slab
+    finally:
+        ctx.set_option(gb.OPT_LORENZO_SLAB, 0)
+    with pytest.raises(gb.GbszError):
+        ctx.set_option(gb.OPT_LORENZO_SLAB, 65537)
+
+
 def test_batch_with_orders_blocks_and_4d(gb, ctx):
     """A batch mixing Lorenzo orders, the per-block mode and a 4D field gives
     each field's single-call archive and the oracle's."""
