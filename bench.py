@@ -49,6 +49,7 @@ def parse():
     ap.add_argument("--skip-micro", action="store_true",
                     help="skip the codebook-vs-bins and 32/64-bit codeword micro-benchmarks")
     ap.add_argument("--skip-serving", action="store_true", help="skip the serving-mix measurement")
+    ap.add_argument("--skip-tune", action="store_true", help="skip the autotuner measurement")
     ap.add_argument("--skip-configs", action="store_true",
                     help="skip the other single-field workloads (64^3, 1800x3600, 512^3)")
     return ap.parse_args()
@@ -307,6 +308,57 @@ def other_configs(ctx, gbsz, workloads, dev, reps=5):
                     "max_err_over_eb": err})
         del y, arc
     cache.clear()
+    return out
+
+
+def autotuned(gbsz, workloads, dev, reps=5):
+    """The autotuner on three of the stated workloads (64^3 sinusoids, one
+    1800x3600 power-law field, the 512^3 lognormal density; rel eb 1e-4,
+    radius 512): compress + decompress GB/s with the built-in rules, then the
+    tuner's choice (chunk, decoder, dual-quant tile extent) and the GB/s with
+    it, in a context of its own."""
+    import time
+    import torch
+    cases = [("64^3 sinusoids + noise (3D)", lambda: workloads.sinusoids_3d(64, seed=1001)),
+             ("1800x3600 power-law field (2D)", lambda: workloads.grf_2d_batch(nfields=1, seed=1003, masked=(0,))[0]),
+             ("512^3 lognormal density (3D)", lambda: workloads.lognormal_3d(512, seed=1004))]
+    ctx = gbsz.Context(dev)
+    stream = torch.cuda.Stream(dev)
+    out = []
+
+    def gbs(x, p):
+        arc = torch.empty(gbsz.load().gbsz_compress_bound(gbsz.C.byref(p)), dtype=torch.uint8, device=dev)
+        y = torch.empty_like(x)
+        for _ in range(3):
+            _, nb = ctx.compress_params(x, p, out=arc, stream=stream)
+            ctx.decompress(arc, nb, out=y, stream=stream)
+        stream.synchronize()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(2)]
+        ev[0].record(stream)
+        for _ in range(reps):
+            _, nb = ctx.compress_params(x, p, out=arc, stream=stream)
+            ctx.decompress(arc, nb, out=y, stream=stream)
+        ev[1].record(stream)
+        torch.cuda.synchronize(dev)
+        return x.numel() * 4 / 1e9 / (ev[0].elapsed_time(ev[1]) / reps / 1e3)
+
+    for name, make in cases:
+        x = torch.from_numpy(make()).to(dev)
+        rule = gbsz.make_params(gbsz.field_dims(x), 1e-4, gbsz.EB_REL, 512, 0)
+        rule.chunk = gbsz.auto_chunk(gbsz.field_dims(x), 512)
+        before = gbs(x, rule)
+        t0 = time.perf_counter()
+        p, _ = ctx.autotune(x, 1e-4, stream=stream)
+        tune_s = time.perf_counter() - t0
+        chunk, decoder, slab = ctx.tuned_knobs(p)
+        after = gbs(x, p)
+        out.append({"workload": name, "rule": {"chunk": rule.chunk, "gbs": before},
+                    "tuned": {"chunk": chunk, "decoder": {0: "not measured", 1: "thread per chunk",
+                                                          2: "warp per chunk"}[decoder],
+                              "slab": slab or "rule", "gbs": after},
+                    "tune_seconds": tune_s})
+        del x
+    ctx.close()
     return out
 
 
@@ -665,6 +717,10 @@ def main():
     if rank == 0 and not a.skip_configs:
         configs_res = other_configs(ctx, gbsz, workloads, dev)
 
+    tune_res = None
+    if rank == 0 and not a.skip_tune:
+        tune_res = autotuned(gbsz, workloads, dev)
+
     serving_res = None
     if rank == 0 and not a.skip_serving:
         from paper_2007_09625_gb300 import serve
@@ -699,7 +755,7 @@ def main():
                 "stage_ms_per_step": {nm: stage_ms[i] / a.steps for i, nm in enumerate(stage_names)},
                 "roofline": roofline, "kernels": per_kernel, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "batch_vs_per_field": batch, "micro": micro, "serving": serving_res,
-                "other_single_field": configs_res,
+                "other_single_field": configs_res, "autotune": tune_res,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist:

@@ -13,6 +13,9 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libgbsz.so")
+# the bounds-checking build: every GBSZ_CHECK in the kernels compiled in
+CHECK_BUILD = os.path.join(ROOT, "_build_check")
+CHECK_LIB = os.path.join(PKG, "libgbsz_check.so")
 SOURCES = ["gbsz_api.cu", "k_quant.cu", "k_codebook.cu", "k_encode.cu", "k_decode.cu", "k_decode_warp.cu", "k_recon.cu",
            "noalloc.cu", "server.cu"]
 HEADERS = ["common.cuh", "scan.cuh", "server_core.h"]
@@ -32,13 +35,18 @@ def _newest_input():
     return max(os.path.getmtime(p) for p in paths)
 
 
-def build(force=False, verbose=False, extra_flags=()):
-    if not force and os.path.exists(LIB) and os.path.getmtime(LIB) >= _newest_input():
-        return LIB
-    os.makedirs(BUILD, exist_ok=True)
+def build(force=False, verbose=False, extra_flags=(), check=False):
+    """check=True: the bounds-checking build (-DGBSZ_BOUNDS_CHECK) into
+    libgbsz_check.so, objects in _build_check/."""
+    lib, bdir = (CHECK_LIB, CHECK_BUILD) if check else (LIB, BUILD)
+    if check:
+        extra_flags = tuple(extra_flags) + ("-DGBSZ_BOUNDS_CHECK",)
+    if not force and os.path.exists(lib) and os.path.getmtime(lib) >= _newest_input():
+        return lib
+    os.makedirs(bdir, exist_ok=True)
 
     def compile_one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(bdir, src.replace(".cu", ".o"))
         cmd = [NVCC, *FLAGS, *extra_flags, "-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
         return src, obj, r.returncode, r.stdout.decode()
@@ -52,14 +60,14 @@ def build(force=False, verbose=False, extra_flags=()):
     if failed:
         raise RuntimeError("nvcc failed for " + ", ".join(r[0] for r in failed))
     objs = [r[1] for r in results]
-    tmp = LIB + ".tmp"
+    tmp = lib + ".tmp"
     cmd = [NVCC, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)
     if r.returncode:
         sys.stderr.write(r.stdout.decode())
         raise RuntimeError("link failed")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

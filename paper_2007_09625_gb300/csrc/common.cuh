@@ -54,7 +54,8 @@ __host__ __device__ inline Layout make_layout(uint32_t radius, uint64_t nchunk, 
 // device status bits (Control::error)
 enum : uint32_t {
     DERR_CAPACITY = 1u, DERR_CORRUPT = 2u, DERR_TIMEOUT = 4u, DERR_EB = 8u, DERR_INTERNAL = 16u,
-    DERR_RANGE = 32u  // an input outside what the kernel supports (codebook: histogram total >= 2^32)
+    DERR_RANGE = 32u,  // an input outside what the kernel supports (codebook: histogram total >= 2^32)
+    DERR_BOUNDS = 64u  // bounds-checking build: an index check failed
 };
 
 // Per-call device control block.  Zeroed by one memset at the start of each
@@ -76,6 +77,22 @@ struct Control {
     unsigned long long exc_chk; // encode: exceptions emitted (check)
     uint32_t ticket;            // warp decoder: next chunk to take
 };
+
+// Bounds-checking build (compiled with -DGBSZ_BOUNDS_CHECK): GBSZ_CHECK(cond,
+// ctl) guards an access at an index a kernel computed -- true when cond
+// holds; otherwise it records DERR_BOUNDS in ctl and is false, and the caller
+// skips the access.  In the normal build it is the constant true and cond is
+// not evaluated.
+#ifdef GBSZ_BOUNDS_CHECK
+__device__ __forceinline__ bool bounds_hold(bool c, Control *ctl)
+{
+    if (!c) atomicOr(&ctl->error, DERR_BOUNDS);
+    return c;
+}
+#define GBSZ_CHECK(cond, ctl) (::gbsz::bounds_hold((cond), (ctl)))
+#else
+#define GBSZ_CHECK(cond, ctl) true
+#endif
 
 struct EbScalars {
     float eb, ebx2, inv2eb;
@@ -340,6 +357,7 @@ struct QuantArgs {
     int num_sms;
     uint32_t slab;  // rows (2D) or planes (3D) each tile sweeps; 0 = the built-in rule
 };
+__host__ __device__ inline uint64_t npoints(const QuantArgs &a) { return a.dims[0] * a.dims[1] * a.dims[2]; }
 // block extent of the per-block Lorenzo mode (Sec. 3.1.1): 32, 16x16, 8x8x8
 __host__ __device__ constexpr uint32_t lorenzo_block_extent(uint32_t ndim)
 {

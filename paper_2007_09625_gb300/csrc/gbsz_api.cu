@@ -345,6 +345,7 @@ uint32_t auto_chunk(uint64_t n)
 
 gbsz_status map_device_error(uint32_t e)
 {
+    if (e & DERR_BOUNDS) return GBSZ_ERR_BOUNDS;
     if (e & DERR_INTERNAL) return GBSZ_ERR_CUDA;
     if (e & DERR_TIMEOUT) return GBSZ_ERR_TIMEOUT;
     if (e & (DERR_EB | DERR_RANGE)) return GBSZ_ERR_INVALID_ARG;
@@ -1444,6 +1445,7 @@ const char *gbsz_status_str(gbsz_status s)
     case GBSZ_ERR_CUDA: return "CUDA error";
     case GBSZ_ERR_TIMEOUT: return "bounded device wait timed out";
     case GBSZ_ERR_UNSUPPORTED: return "unsupported device";
+    case GBSZ_ERR_BOUNDS: return "index check failed (bounds-checking build)";
     }
     return "unknown status";
 }

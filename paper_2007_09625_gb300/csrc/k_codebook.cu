@@ -350,7 +350,7 @@ __device__ __forceinline__ void codebook_body(const CodebookArgs &a)
         for (uint32_t i = t; i < k; i += T) {
             const uint32_t d = da[i];
             ml = max(ml, d);
-            a.len_out[K[i] & 0xFFFFu] = (uint8_t)min(d, 255u);
+            if (GBSZ_CHECK((K[i] & 0xFFFFu) < a.nbins, a.ctl)) a.len_out[K[i] & 0xFFFFu] = (uint8_t)min(d, 255u);
         }
         maxlen = block_max(ml, s_scan);
         if (t == 0 && maxlen > kMaxLen) atomicOr(&a.ctl->error, DERR_INTERNAL);
@@ -427,7 +427,9 @@ __device__ __forceinline__ void decode_tables_body(const CodebookArgs &a)
             const unsigned long long code = v >> (kLutBits - l);
             const unsigned long long off = code - canon.first[l];
             if (off < canon.count[l]) {
-                e = ((uint32_t)a.sorted[canon.start[l] + off] << 8) | l;
+                e = GBSZ_CHECK(canon.start[l] + off < a.nbins, a.ctl)
+                        ? ((uint32_t)a.sorted[canon.start[l] + off] << 8) | l
+                        : 0u;
                 break;
             }
         }
@@ -446,7 +448,7 @@ __device__ __forceinline__ void decode_tables_body(const CodebookArgs &a)
         for (uint32_t l = kLutBits + 1; v < (1u << kLutBits) && l <= kLutBits + kLut2Bits && l <= ml; l++) {
             const unsigned long long off = (unsigned long long)(pat >> (kLutBits + kLut2Bits - l)) - canon.first[l];
             if (off < canon.count[l]) {
-                const uint32_t sym = a.sorted[canon.start[l] + off];
+                const uint32_t sym = GBSZ_CHECK(canon.start[l] + off < a.nbins, a.ctl) ? a.sorted[canon.start[l] + off] : 0xFFFFu;
                 if (sym < 2048u) e = (sym << 5) | l;
                 break;
             }
@@ -461,7 +463,7 @@ __device__ __forceinline__ void decode_tables_body(const CodebookArgs &a)
             const unsigned long long off = (unsigned long long)(bits >> (nb - l)) - canon.first[l];
             if (off < canon.count[l]) {
                 len = l;
-                return a.sorted[canon.start[l] + off];
+                return GBSZ_CHECK(canon.start[l] + off < a.nbins, a.ctl) ? a.sorted[canon.start[l] + off] : 0u;
             }
         }
         len = 0;

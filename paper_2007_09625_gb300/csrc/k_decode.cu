@@ -113,6 +113,8 @@ struct DecTables {
     const uint32_t *count, *start;
     const uint16_t *sorted;
     uint32_t maxlen;
+    uint32_t nsorted;  // entries of sorted (bins)
+    Control *ctl;
 };
 
 template <uint32_t RW>
@@ -162,7 +164,7 @@ __device__ __forceinline__ uint32_t decode_one(Window &w, const Ring<kRing> &rg,
             const unsigned long long off = (v64 >> (64 - l)) - t.first[l];
             if (off < t.count[l]) {
                 len = l;
-                sym = t.sorted[t.start[l] + off];
+                sym = GBSZ_CHECK(t.start[l] + off < t.nsorted, t.ctl) ? t.sorted[t.start[l] + off] : 0u;
                 break;
             }
         }
@@ -212,12 +214,13 @@ __device__ __forceinline__ void decode_chunk_general(const DecodeArgs &a, const 
         }
         const uint4 o = make_uint4(sy[0] | (sy[1] << 16), sy[2] | (sy[3] << 16), sy[4] | (sy[5] << 16),
                                    sy[6] | (sy[7] << 16));
-        *reinterpret_cast<uint4 *>(out + k) = o;
+        if (GBSZ_CHECK(s0 + k + kBatch <= a.n, a.ctl)) *reinterpret_cast<uint4 *>(out + k) = o;
         tz += zeros_in(o.x) + zeros_in(o.y) + zeros_in(o.z) + zeros_in(o.w);
         if (MULTI_TILE && a.tile_sums && ((s0 + k + kBatch) & (kRecon1DTile - 1)) == 0) {
             // residual sum of the tile's in-cap codes: sum(code) - R * (#nonzero), mod 2^32
             const uint32_t m = k + kBatch - tstart;
-            atomicAdd(&a.tile_sums[(s0 + k) / kRecon1DTile], ssum - R * (m - tz));
+            if (GBSZ_CHECK((s0 + k) / kRecon1DTile < (a.n + kRecon1DTile - 1) / kRecon1DTile, a.ctl))
+                atomicAdd(&a.tile_sums[(s0 + k) / kRecon1DTile], ssum - R * (m - tz));
             zeros += tz;
             ssum = tz = 0;
             tstart = k + kBatch;
@@ -230,13 +233,13 @@ __device__ __forceinline__ void decode_chunk_general(const DecodeArgs &a, const 
             const uint32_t sym = decode_one(w, rg, t, bad);
             ssum += sym;
             tz += sym == 0;
-            out[k] = (uint16_t)sym;
+            if (GBSZ_CHECK(s0 + k < a.n, a.ctl)) out[k] = (uint16_t)sym;
         }
     }
     zeros += tz;
     if (a.tile_sums && cnt > tstart) {
         const uint32_t tsum = ssum - R * (cnt - tstart - tz);
-        if (tsum) atomicAdd(&a.tile_sums[(s0 + cnt - 1) / kRecon1DTile], tsum);
+        if (tsum && GBSZ_CHECK(s0 + cnt - 1 < a.n, a.ctl)) atomicAdd(&a.tile_sums[(s0 + cnt - 1) / kRecon1DTile], tsum);
     }
     cp_async_wait<0>();  // nothing may still be landing in the ring when the block exits
     // a valid chunk ends exactly at its recorded bit count
@@ -268,8 +271,8 @@ __device__ __forceinline__ void decode_general_body(const DecodeArgs &a, uint32_
     for (uint32_t i = threadIdx.x; i < sorted_in_smem; i += blockDim.x) s_sorted[i] = a.sorted[i];
     __syncthreads();
     if (a.ctl->error & DERR_CORRUPT) return;
-    const DecTables t{lut, lut2, a.lut[1u << kLutBits], first, count, start, sorted_in_smem ? s_sorted : a.sorted,
-                      a.maxlen};
+    const DecTables t{lut,    lut2,     a.lut[1u << kLutBits], first, count, start, sorted_in_smem ? s_sorted : a.sorted,
+                      a.maxlen, 2 * a.radius, a.ctl};
     const uint64_t ntask = (a.nchunk + 31) / 32, tstride = (uint64_t)(blockDim.x >> 5) * vg.nb;
     for (uint64_t k = (uint64_t)(threadIdx.x >> 5) * vg.nb + vg.bid; k < ntask; k += tstride) {
         const uint64_t c = k * 32 + (threadIdx.x & 31);
@@ -408,7 +411,7 @@ __device__ __forceinline__ void decode_chunk(const DecodeArgs &a, Ring<kRingFast
             // symbols are below 4096 here, so the halves of the word sum cannot carry
             const uint32_t t4 = o.x + o.y + o.z + o.w;
             ssum += (t4 & 0xFFFFu) + (t4 >> 16);
-            *reinterpret_cast<uint4 *>(out + k) = o;
+            if (GBSZ_CHECK(s0 + k + kBatch <= a.n, a.ctl)) *reinterpret_cast<uint4 *>(out + k) = o;
             tz += zeros_in(o.x) + zeros_in(o.y) + zeros_in(o.z) + zeros_in(o.w);
         } else {
 #pragma unroll
@@ -417,7 +420,7 @@ __device__ __forceinline__ void decode_chunk(const DecodeArgs &a, Ring<kRingFast
                     const uint32_t sy = (pw[j / 2] >> ((j & 1) * 16)) & 0xFFFFu;
                     ssum += sy;
                     tz += sy == 0;
-                    out[k + j] = (uint16_t)sy;
+                    if (GBSZ_CHECK(s0 + k + j < a.n, a.ctl)) out[k + j] = (uint16_t)sy;
                 }
             }
         }
@@ -425,7 +428,8 @@ __device__ __forceinline__ void decode_chunk(const DecodeArgs &a, Ring<kRingFast
             ((s0 + k + kBatch) & (kRecon1DTile - 1)) == 0) {
             // residual sum of the tile's in-cap codes: sum(code) - R * (#nonzero), mod 2^32
             const uint32_t m = k + kBatch - tstart;
-            atomicAdd(&a.tile_sums[(s0 + k) / kRecon1DTile], ssum - R * (m - tz));
+            if (GBSZ_CHECK((s0 + k) / kRecon1DTile < (a.n + kRecon1DTile - 1) / kRecon1DTile, a.ctl))
+                atomicAdd(&a.tile_sums[(s0 + k) / kRecon1DTile], ssum - R * (m - tz));
             zeros += tz;
             ssum = tz = 0;
             tstart = k + kBatch;
@@ -438,14 +442,14 @@ __device__ __forceinline__ void decode_chunk(const DecodeArgs &a, Ring<kRingFast
             if (!GUARD || k < cnt) {
                 ssum += sym;
                 tz += sym == 0;
-                out[k] = (uint16_t)sym;
+                if (GBSZ_CHECK(s0 + k < a.n, a.ctl)) out[k] = (uint16_t)sym;
             }
         }
     }
     zeros += tz;
     if (a.tile_sums && cnt > tstart) {
         const uint32_t tsum = ssum - R * (cnt - tstart - tz);
-        if (tsum) atomicAdd(&a.tile_sums[(s0 + cnt - 1) / kRecon1DTile], tsum);
+        if (tsum && GBSZ_CHECK(s0 + cnt - 1 < a.n, a.ctl)) atomicAdd(&a.tile_sums[(s0 + cnt - 1) / kRecon1DTile], tsum);
     }
 }
 

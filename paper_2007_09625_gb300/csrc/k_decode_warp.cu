@@ -397,11 +397,13 @@ __device__ __forceinline__ void decode_warp_body(const WarpDecodeArgs &wa)
             for (uint32_t j = 0; j < tc;) {
                 const Codes cd = lk(b);
                 uint32_t adv = cd.l1;
-                cbuf[o + j++] = (uint16_t)cd.s1;
+                if (GBSZ_CHECK(o + j < a.chunk, a.ctl)) cbuf[o + j] = (uint16_t)cd.s1;
+                j++;
                 isum += cd.s1 ? cd.s1 - R : 0u;
                 zc += cd.s1 == 0;
                 if (cd.l2 && j < tc) {
-                    cbuf[o + j++] = (uint16_t)cd.s2;
+                    if (GBSZ_CHECK(o + j < a.chunk, a.ctl)) cbuf[o + j] = (uint16_t)cd.s2;
+                    j++;
                     isum += cd.s2 ? cd.s2 - R : 0u;
                     zc += cd.s2 == 0;
                     adv += cd.l2;
@@ -418,8 +420,10 @@ __device__ __forceinline__ void decode_warp_body(const WarpDecodeArgs &wa)
                 uint16_t *dst = a.codes + s0;
                 const uint32_t n8 = al16 ? cnt / 8 : 0;
                 for (uint32_t i = lane; i < n8; i += 32)
-                    reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(cbuf)[i];
-                for (uint32_t i = n8 * 8 + lane; i < cnt; i += 32) dst[i] = cbuf[i];
+                    if (GBSZ_CHECK(s0 + 8 * i + 8 <= a.n, a.ctl))
+                        reinterpret_cast<uint4 *>(dst)[i] = reinterpret_cast<const uint4 *>(cbuf)[i];
+                for (uint32_t i = n8 * 8 + lane; i < cnt; i += 32)
+                    if (GBSZ_CHECK(s0 + i < a.n, a.ctl)) dst[i] = cbuf[i];
             }
             __syncwarp();
             continue;
@@ -491,7 +495,8 @@ __device__ __forceinline__ void decode_warp_body(const WarpDecodeArgs &wa)
 #pragma unroll
             for (int j = 0; j < 4; j++) {
                 if (cc[j] == 0) {
-                    const uint2 en = wa.outl[ord++];
+                    const uint2 en = GBSZ_CHECK(ord < wa.m, a.ctl) ? wa.outl[ord] : make_uint2(kNone, 0u);
+                    ord++;
                     bad |= en.x != (uint32_t)(s0 + q + j);
                     dv[j] = en.y;
                 } else {
@@ -507,7 +512,10 @@ __device__ __forceinline__ void decode_warp_body(const WarpDecodeArgs &wa)
                 run += dv[j];
                 v[j] = recon_value((int32_t)run, ebx2);
             }
-            if (al16 && q + 4 <= cnt) {
+            const uint32_t nst = q + 4 <= cnt ? 4u : q < cnt ? cnt - q : 0u;  // points this lane stores
+            if (!GBSZ_CHECK(nst == 0 || s0 + q + nst <= a.n, a.ctl)) {
+                // (bounds-checking build) skip the row's stores
+            } else if (al16 && q + 4 <= cnt) {
                 *reinterpret_cast<float4 *>(out + q) = make_float4(v[0], v[1], v[2], v[3]);
             } else {
 #pragma unroll

@@ -293,7 +293,7 @@ __device__ __forceinline__ void count_units(const EncodeArgs &a, uint64_t nunits
                 uint32_t cw = 0;
                 if (first_of_chunk && cnt) {
                     cw = (cb + 31) / 32;
-                    put_u32(a.archive + L0.bits + 4 * (s0 / C), cb);
+                    if (GBSZ_CHECK(s0 / C < (n + C - 1) / C, a.ctl)) put_u32(a.archive + L0.bits + 4 * (s0 / C), cb);
                 }
                 unit_words += warp_sum(cw);
             }
@@ -303,7 +303,8 @@ __device__ __forceinline__ void count_units(const EncodeArgs &a, uint64_t nunits
         const uint32_t unit_exc = a.unit_exc[u];
         if (ug.multi) {
             unit_words = (uint32_t)((chunk_bits + 31) / 32);
-            if (lane == 0) put_u32(a.archive + L0.bits + 4 * u, (uint32_t)chunk_bits);
+            if (lane == 0 && GBSZ_CHECK(u < (n + C - 1) / C, a.ctl))
+                put_u32(a.archive + L0.bits + 4 * u, (uint32_t)chunk_bits);
         }
         if (lane == 0)
             a.unit_tot[u] = make_ulonglong2(unit_words, (unsigned long long)unit_out | ((unsigned long long)unit_exc << 32));
@@ -524,8 +525,10 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
             const uint32_t nz = __popcll(zlo) + __popcll(zhi);
             uint32_t ne = 0;
             if (unit_exc) {
-                for (unsigned long long m = zlo; m; m &= m - 1) ne += a.dscr[s0 + __ffsll(m) - 1].y != 0;
-                for (unsigned long long m = zhi; m; m &= m - 1) ne += a.dscr[s0 + 63 + __ffsll(m)].y != 0;
+                for (unsigned long long m = zlo; m; m &= m - 1)
+                    if (GBSZ_CHECK(s0 + __ffsll(m) - 1 < n, a.ctl)) ne += a.dscr[s0 + __ffsll(m) - 1].y != 0;
+                for (unsigned long long m = zhi; m; m &= m - 1)
+                    if (GBSZ_CHECK(s0 + 63 + __ffsll(m) < n, a.ctl)) ne += a.dscr[s0 + 63 + __ffsll(m)].y != 0;
             }
             const uint32_t oinc = warp_incl_scan(nz), einc = warp_incl_scan(ne);
             uint64_t oi = O0 + o_run + (oinc - nz), ei = E0 + e_run + (einc - ne);
@@ -568,7 +571,8 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
                 }
                 int2 dv[4];
 #pragma unroll
-                for (int k = 0; k < 4; k++) dv[k] = has[k] ? a.dscr[idx[k]] : make_int2(0, 0);
+                for (int k = 0; k < 4; k++)
+                    dv[k] = has[k] && GBSZ_CHECK(idx[k] < n, a.ctl) ? a.dscr[idx[k]] : make_int2(0, 0);
 #pragma unroll
                 for (int k = 0; k < 4; k++)
                     if (has[k]) emit_outlier(idx[k], dv[k]);

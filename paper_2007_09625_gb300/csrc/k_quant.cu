@@ -164,6 +164,7 @@ struct HistState {
     uint32_t R;
     uint32_t c_lo, c_mid, c_hi;
     uint32_t n_out, n_exc;
+    Control *ctl;
 };
 
 __device__ __forceinline__ void hist_add(HistState &h, uint32_t code, uint32_t *ghist)
@@ -177,12 +178,13 @@ __device__ __forceinline__ void hist_add(HistState &h, uint32_t code, uint32_t *
     } else {
         const uint32_t b = code - h.lo;
         if (b < h.nsh) atomicAdd(&h.sh[b], 1u);
-        else atomicAdd(&ghist[code], 1u);
+        else if (GBSZ_CHECK(code < 2 * h.R, h.ctl)) atomicAdd(&ghist[code], 1u);
     }
 }
 
-__device__ __forceinline__ void hist_init(HistState &h, uint32_t *sh, uint32_t R)
+__device__ __forceinline__ void hist_init(HistState &h, uint32_t *sh, uint32_t R, Control *ctl)
 {
+    h.ctl = ctl;
     h.sh = sh;
     h.R = R;
     const uint32_t nbins = 2 * R;
@@ -232,11 +234,12 @@ __device__ __forceinline__ uint32_t emit_point(HistState &h, const QuantArgs &a,
                                                uint32_t delta, bool exc)
 {
     const uint32_t code = postquant(delta, exc, (int32_t)h.R);
+    const bool in = GBSZ_CHECK(idx < npoints(a), a.ctl);
     if (code == 0) {
-        a.dscr[idx] = make_int2((int32_t)delta, exc ? 1 : 0);
+        if (in) a.dscr[idx] = make_int2((int32_t)delta, exc ? 1 : 0);
         h.n_out++;
     }
-    if (exc) atomicAdd(&a.unit_exc[idx >> a.unit_shift], 1u);
+    if (exc && in) atomicAdd(&a.unit_exc[idx >> a.unit_shift], 1u);
     h.n_exc += exc;
     hist_add(h, code, a.hist);
     return code;
@@ -274,19 +277,20 @@ __device__ __forceinline__ uint32_t point_1d(HistState &h, const QuantArgs &a, u
     if (WIN) {
         // predicated shared-memory add: no branch around it
         const uint32_t addr = (uint32_t)__cvta_generic_to_shared(h.sh + code);
+        const bool add = !central && GBSZ_CHECK(code < h.nsh, a.ctl);
         asm volatile(
             "{\n\t.reg .pred p;\n\t"
             "setp.ne.u32 p, %0, 0;\n\t"
-            "@p red.shared.add.u32 [%1], 1;\n\t}" ::"r"((uint32_t)!central),
+            "@p red.shared.add.u32 [%1], 1;\n\t}" ::"r"((uint32_t)add),
             "r"(addr)
             : "memory");
     } else if (!central) {
         const uint32_t b = code - h.lo;
         if (b < h.nsh) atomicAdd(&h.sh[b], 1u);
-        else atomicAdd(&a.hist[code], 1u);
+        else if (GBSZ_CHECK(code < 2 * h.R, a.ctl)) atomicAdd(&a.hist[code], 1u);
         h.n_out += code == 0;
     }
-    if (code == 0) a.dscr[idx] = make_int2((int32_t)d, exc ? 1 : 0);
+    if (code == 0 && GBSZ_CHECK(idx < npoints(a), a.ctl)) a.dscr[idx] = make_int2((int32_t)d, exc ? 1 : 0);
     h.n_exc += exc;
     return code;
 }
@@ -304,7 +308,7 @@ __device__ __forceinline__ void dualquant_1d_body(const QuantArgs &a, uint32_t n
 {
     extern __shared__ uint32_t sh_hist[];
     HistState h;
-    hist_init(h, sh_hist, a.radius);
+    hist_init(h, sh_hist, a.radius, a.ctl);
     __syncthreads();
     if (a.ctl->error & DERR_EB) return;
     const EbScalars sc = load_scalars(a.ctl);
@@ -364,10 +368,12 @@ __device__ __forceinline__ void dualquant_1d_body(const QuantArgs &a, uint32_t n
                 qprev = q[j];
             }
             uint4 *o = reinterpret_cast<uint4 *>(a.codes + e0);
+            if (GBSZ_CHECK(e0 + kQ1Per <= n, a.ctl)) {
             o[0] = make_uint4(code[0] | (code[1] << 16), code[2] | (code[3] << 16), code[4] | (code[5] << 16),
                               code[6] | (code[7] << 16));
             o[1] = make_uint4(code[8] | (code[9] << 16), code[10] | (code[11] << 16), code[12] | (code[13] << 16),
                               code[14] | (code[15] << 16));
+            }
         } else {
 #pragma unroll
             for (int j = 0; j < kQ1Per; j++) {
@@ -379,7 +385,7 @@ __device__ __forceinline__ void dualquant_1d_body(const QuantArgs &a, uint32_t n
         }
         unpack_central(h, pk);
         // the 16 points of a run lie in one encoder unit (units are 2^k >= 2048 points)
-        if (h.n_exc != exc0) atomicAdd(&a.unit_exc[e0 >> a.unit_shift], h.n_exc - exc0);
+        if (h.n_exc != exc0 && GBSZ_CHECK(e0 < n, a.ctl)) atomicAdd(&a.unit_exc[e0 >> a.unit_shift], h.n_exc - exc0);
     }
     if (WIN) h.n_out = 0;  // taken from bin 0 below
     hist_flush(h, a.hist, a.ctl, WIN);
@@ -408,7 +414,7 @@ __device__ __forceinline__ void dualquant_2d_body(const QuantArgs &a, uint32_t n
     extern __shared__ uint32_t sh_hist[];
     __shared__ int32_t rows[3][kQ2TX + 1];
     HistState h;
-    hist_init(h, sh_hist, a.radius);
+    hist_init(h, sh_hist, a.radius, a.ctl);
     __syncthreads();
     if (a.ctl->error & DERR_EB) return;
     const EbScalars sc = load_scalars(a.ctl);
@@ -481,8 +487,11 @@ __device__ __forceinline__ void dualquant_2d_body(const QuantArgs &a, uint32_t n
                                            ((uint32_t)rows[prev][lx + 1] & mU) +
                                            ((uint32_t)rows[prev][lx] & mL[j] & mU);
                         const uint32_t idx = (uint32_t)y * nx + x0 + lx;
-                        a.codes[idx] = (uint16_t)point_1d<WIN>(h, a, idx, d, ex[j], pk);
-                        if (ex[j]) atomicAdd(&a.unit_exc[idx >> a.unit_shift], 1u);
+                        const uint32_t cd = point_1d<WIN>(h, a, idx, d, ex[j], pk);
+                        if (GBSZ_CHECK(idx < npoints(a), a.ctl)) {
+                            a.codes[idx] = (uint16_t)cd;
+                            if (ex[j]) atomicAdd(&a.unit_exc[idx >> a.unit_shift], 1u);
+                        }
                     }
                 }
                 unpack_central(h, pk);
@@ -526,7 +535,7 @@ __device__ __forceinline__ void dualquant_3d_body(const QuantArgs &a, uint32_t n
     extern __shared__ uint32_t sh_hist[];
     __shared__ uint32_t rp[2][kQ3T + 1][kQ3T + 1];
     HistState h;
-    hist_init(h, sh_hist, a.radius);
+    hist_init(h, sh_hist, a.radius, a.ctl);
     __syncthreads();
     if (a.ctl->error & DERR_EB) return;
     const EbScalars sc = load_scalars(a.ctl);
@@ -624,8 +633,11 @@ __device__ __forceinline__ void dualquant_3d_body(const QuantArgs &a, uint32_t n
                         const uint32_t d = r[j] - (c[Y][X - 1] & mL) - (c[Y - 1][X] & mU[j]) +
                                            (c[Y - 1][X - 1] & mL & mU[j]);
                         const uint32_t idx = ((uint32_t)z * ny + (y0 + Y - 1)) * nx + gx;
-                        a.codes[idx] = (uint16_t)point_1d<WIN>(h, a, idx, d, ex[j], pk);
-                        if (ex[j]) atomicAdd(&a.unit_exc[idx >> a.unit_shift], 1u);
+                        const uint32_t cd = point_1d<WIN>(h, a, idx, d, ex[j], pk);
+                        if (GBSZ_CHECK(idx < npoints(a), a.ctl)) {
+                            a.codes[idx] = (uint16_t)cd;
+                            if (ex[j]) atomicAdd(&a.unit_exc[idx >> a.unit_shift], 1u);
+                        }
                     }
                 }
                 unpack_central(h, pk);
@@ -696,7 +708,7 @@ __global__ void __launch_bounds__(256) k_lorenzo_order(QuantArgs a, uint32_t n)
 {
     extern __shared__ uint32_t sh_hist[];
     HistState h;
-    hist_init(h, sh_hist, a.radius);
+    hist_init(h, sh_hist, a.radius, a.ctl);
     __syncthreads();
     if (a.ctl->error & DERR_EB) return;
     const uint32_t nx = (uint32_t)a.dims[0], ny = D >= 2 ? (uint32_t)a.dims[1] : 1u;

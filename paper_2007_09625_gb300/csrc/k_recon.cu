@@ -157,10 +157,11 @@ __device__ __forceinline__ void outlier_tiles_1d_body(const ReconArgs &a, uint64
             if (lane >= (uint32_t)off && lane - off >= seg0) sum += v;
         }
         const bool tail = lane == 31 || ((heads >> (lane + 1)) & 1u) || t + 1 >= a.m;
-        if (live && ok && tail) atomicAdd(&a.faces[T], sum);
+        if (live && ok && tail && GBSZ_CHECK(T < a.faces_cap, a.ctl)) atomicAdd(&a.faces[T], sum);
         if (live && ok) {
             const uint64_t G = idx / kGroup1D;
-            for (int64_t u = gprev + 1; u <= (int64_t)G; u++) start[u] = (uint32_t)t;
+            for (int64_t u = gprev + 1; u <= (int64_t)G; u++)
+                if (GBSZ_CHECK((uint64_t)u <= ngroups, a.ctl)) start[u] = (uint32_t)t;
             if (t + 1 == a.m)
                 for (uint64_t u = G + 1; u <= ngroups; u++) start[u] = (uint32_t)a.m;
         }
@@ -618,7 +619,7 @@ __device__ __forceinline__ void faces_body(const ReconArgs &a, const Geo &g, uin
                 if (!(A & 1)) { x = r % TX; r /= TX; }
                 if (!(A & 2)) { y = r % TY; r /= TY; }
                 if (!(A & 4)) { z = r; }
-                dst[ci] = sm[TG::sidx(x, y, z)];
+                if (GBSZ_CHECK(g.off[A] + tile * (uint64_t)sz + ci < a.faces_cap, a.ctl)) dst[ci] = sm[TG::sidx(x, y, z)];
             }
         }
         __syncthreads();
@@ -662,7 +663,9 @@ __device__ __forceinline__ void values_body(const ReconArgs &a, const Geo &g, co
                 }
             }
             const uint64_t ptile = ((uint64_t)pt[2] * g.nt[1] + pt[1]) * g.nt[0] + pt[0];
-            if (has && (int)threadIdx.x < TG::size(A)) cv[A] = F[g.off[A] + ptile * (uint64_t)TG::size(A) + threadIdx.x];
+            if (has && (int)threadIdx.x < TG::size(A) &&
+                GBSZ_CHECK(g.off[A] + ptile * (uint64_t)TG::size(A) + threadIdx.x < a.faces_cap, a.ctl))
+                cv[A] = F[g.off[A] + ptile * (uint64_t)TG::size(A) + threadIdx.x];
         }
 #pragma unroll
         for (int A = 1; A <= TG::NA; A++)
@@ -681,7 +684,8 @@ __device__ __forceinline__ void values_body(const ReconArgs &a, const Geo &g, co
                     uint32_t s = sm[TG::sidx(x, y, z)];
 #pragma unroll
                     for (int A = 1; A <= TG::NA; A++) s += carry[TG::base(A) + TG::comp(A, x, y, z)];
-                    if (z0 + z < n2) a.out[base + z * plane] = recon_value((int32_t)s, ebx2);
+                    if (z0 + z < n2 && GBSZ_CHECK((uint64_t)base + (uint64_t)z * plane < (uint64_t)plane * n2, a.ctl))
+                        a.out[base + z * plane] = recon_value((int32_t)s, ebx2);
                 }
             }
         } else {
@@ -692,7 +696,8 @@ __device__ __forceinline__ void values_body(const ReconArgs &a, const Geo &g, co
                     uint32_t s = sm[TG::sidx(x, y, z)];
 #pragma unroll
                     for (int A = 1; A <= TG::NA; A++) s += carry[TG::base(A) + TG::comp(A, x, y, z)];
-                    a.out[(gz * n1 + gy) * n0 + gx] = recon_value((int32_t)s, ebx2);
+                    if (GBSZ_CHECK(((uint64_t)gz * n1 + gy) * n0 + gx < (uint64_t)n0 * n1 * n2, a.ctl))
+                        a.out[(gz * n1 + gy) * n0 + gx] = recon_value((int32_t)s, ebx2);
                 }
             }
         }

@@ -11,9 +11,10 @@ import os
 import torch
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(_HERE, "libgbsz.so")
+# GBSZ_LIBRARY: another build of the library (the bounds-checking one)
+LIB_PATH = os.environ.get("GBSZ_LIBRARY") or os.path.join(_HERE, "libgbsz.so")
 
-OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CORRUPT, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED = range(8)
+OK, ERR_INVALID_ARG, ERR_CAPACITY, ERR_CORRUPT, ERR_OOM, ERR_CUDA, ERR_TIMEOUT, ERR_UNSUPPORTED, ERR_BOUNDS = range(9)
 EB_ABS, EB_REL = 0, 1
 NSTAGE = 11
 STAGES = ["error_bound", "dualquant_hist", "codebook", "encode_count", "encode_scan", "encode_pack",
