@@ -322,7 +322,7 @@ def autotuned(gbsz, workloads, dev, reps=5):
     cases = [("64^3 sinusoids + noise (3D)", lambda: workloads.sinusoids_3d(64, seed=1001)),
              ("1800x3600 power-law field (2D)", lambda: workloads.grf_2d_batch(nfields=1, seed=1003, masked=(0,))[0]),
              ("512^3 lognormal density (3D)", lambda: workloads.lognormal_3d(512, seed=1004))]
-    ctx = gbsz.Context(dev)
+    ctx = gbsz.Context(torch.device(dev).index or 0)
     stream = torch.cuda.Stream(dev)
     out = []
 

@@ -127,9 +127,10 @@ __device__ __forceinline__ void minmax_body(const float *__restrict__ x, uint64_
     }
 }
 
+// 8 blocks per SM resident (at most 32 registers): the grid is 8 blocks per SM
 template <bool VEC>
-__global__ void __launch_bounds__(256) k_minmax(const float *__restrict__ x, uint64_t n, Control *ctl, double eb,
-                                                uint32_t mode)
+__global__ void __launch_bounds__(256, 8) k_minmax(const float *__restrict__ x, uint64_t n, Control *ctl, double eb,
+                                                   uint32_t mode)
 {
     minmax_body<VEC>(x, n, ctl, eb, mode, vgrid_self());
 }
@@ -138,7 +139,7 @@ __global__ void k_eb_abs(Control *ctl, double eb) { finalize_eb(ctl, eb, 0, 0, 0
 
 // grouped S0: an absolute bound takes one block (no reduction)
 template <bool VEC>
-__global__ void __launch_bounds__(256) k_minmax_group(const MinmaxItem *items, const uint32_t *first, uint32_t ni)
+__global__ void __launch_bounds__(256, 8) k_minmax_group(const MinmaxItem *items, const uint32_t *first, uint32_t ni)
 {
     VGrid vg;
     const MinmaxItem &m = items[group_item(first, ni, vg)];
@@ -391,8 +392,9 @@ __device__ __forceinline__ void dualquant_1d_body(const QuantArgs &a, uint32_t n
     hist_flush(h, a.hist, a.ctl, WIN);
 }
 
+// four blocks per SM resident (at most 64 registers)
 template <bool VEC, bool WIN>
-__global__ void __launch_bounds__(kQ1Threads) k_dualquant_1d(const __grid_constant__ QuantArgs a, uint32_t ntiles)
+__global__ void __launch_bounds__(kQ1Threads, 4) k_dualquant_1d(const __grid_constant__ QuantArgs a, uint32_t ntiles)
 {
     dualquant_1d_body<VEC, WIN>(a, ntiles, vgrid_self());
 }
@@ -657,7 +659,7 @@ __device__ __forceinline__ void dualquant_3d_body(const QuantArgs &a, uint32_t n
 }
 
 template <bool WIN>
-__global__ void __launch_bounds__(kQ3Threads) k_dualquant_3d(const __grid_constant__ QuantArgs a, uint32_t ntx,
+__global__ void __launch_bounds__(kQ3Threads, 5) k_dualquant_3d(const __grid_constant__ QuantArgs a, uint32_t ntx,
                                                              uint32_t nty, uint32_t ntz, uint32_t tz)
 {
     dualquant_3d_body<WIN>(a, ntx, nty, ntz, tz, vgrid_self());
@@ -666,7 +668,7 @@ __global__ void __launch_bounds__(kQ3Threads) k_dualquant_3d(const __grid_consta
 // grouped S1-S3: one launch per kernel variant over every field of the
 // variant (D = 1, 2, 3; VEC for D = 1)
 template <int D, bool VEC, bool WIN>
-__global__ void __launch_bounds__(D == 1 ? kQ1Threads : D == 2 ? kQ2Threads : kQ3Threads)
+__global__ void __launch_bounds__(D == 1 ? kQ1Threads : D == 2 ? kQ2Threads : kQ3Threads, D == 1 ? 3 : 1)
     k_dualquant_group(const QuantItem *items, const uint32_t *first, uint32_t ni)
 {
     VGrid vg;
