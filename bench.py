@@ -50,6 +50,9 @@ def parse():
                     help="skip the codebook-vs-bins and 32/64-bit codeword micro-benchmarks")
     ap.add_argument("--skip-serving", action="store_true", help="skip the serving-mix measurement")
     ap.add_argument("--skip-tune", action="store_true", help="skip the autotuner measurement")
+    ap.add_argument("--oracle-configs", action="store_true",
+                    help="also time the oracle (one thread and every host core) on the 64^3, 16 x 1800x3600 "
+                         "and 512^3 workloads (about a minute of host time)")
     ap.add_argument("--skip-configs", action="store_true",
                     help="skip the other single-field workloads (64^3, 1800x3600, 512^3)")
     return ap.parse_args()
@@ -57,13 +60,21 @@ def parse():
 
 def batch_vs_per_field(ctx, gbsz, workloads, dev, steps=5):
     """16 fields of 1800x3600 (power-law -3 fields, four of them with masked
-    constant regions) at rel eb 1e-4: one compress+decompress per field in a
-    loop, versus one compress_batch + decompress_batch over all 16."""
+    constant regions) at rel eb 1e-4, and at 1e-3 beside it: one
+    compress+decompress per field in a loop, versus one compress_batch +
+    decompress_batch over all 16."""
     import torch
     fields = [torch.from_numpy(f).to(dev) for f in workloads.grf_2d_batch(16, seed=1003)]
+    res = batch_at(ctx, gbsz, fields, 1e-4, dev, steps)
+    res["rel_1e-3"] = batch_at(ctx, gbsz, fields, 1e-3, dev, steps)
+    return res
+
+
+def batch_at(ctx, gbsz, fields, rel, dev, steps):
+    import torch
     n_all = sum(f.numel() for f in fields)
-    params = [gbsz.make_params(gbsz.field_dims(f), 1e-4) for f in fields]
-    arcs = [torch.empty(gbsz.compress_bound(gbsz.field_dims(f), 1e-4), dtype=torch.uint8, device=dev)
+    params = [gbsz.make_params(gbsz.field_dims(f), rel) for f in fields]
+    arcs = [torch.empty(gbsz.compress_bound(gbsz.field_dims(f), rel), dtype=torch.uint8, device=dev)
             for f in fields]
     outs = [torch.empty_like(f) for f in fields]
     # a stream of its own: batch calls on it are captured once as CUDA graphs
@@ -73,7 +84,7 @@ def batch_vs_per_field(ctx, gbsz, workloads, dev, steps=5):
 
     def per_field():
         for f, a, o in zip(fields, arcs, outs):
-            _, nb = ctx.compress(f, 1e-4, out=a, stream=stream)
+            _, nb = ctx.compress(f, rel, out=a, stream=stream)
             ctx.decompress(a, nb, out=o, stream=stream)
 
     def batched():
@@ -94,7 +105,7 @@ def batch_vs_per_field(ctx, gbsz, workloads, dev, steps=5):
         torch.cuda.synchronize(dev)
         res[name] = 4.0 * n_all / (e0.elapsed_time(e1) / steps / 1e3) / 1e9
     # batched (graph-replayed) results are the single-field results
-    single, nb1 = ctx.compress(fields[5], 1e-4, stream=stream)
+    single, nb1 = ctx.compress(fields[5], rel, stream=stream)
     _, nbs, _ = ctx.compress_batch(fields, None, outs=arcs, params=params, stream=stream)
     stream.synchronize()
     assert nbs[5] == nb1 and torch.equal(arcs[5][:nb1], single[:nb1])
@@ -103,7 +114,8 @@ def batch_vs_per_field(ctx, gbsz, workloads, dev, steps=5):
     stream.synchronize()
     assert torch.equal(outs[5].view(torch.int32), y5.view(torch.int32))
     g1 = ctx.debug_copy(gbsz.DEBUG_GRAPHS, 4, np.uint64)
-    return {"workload": "16 x 1800x3600 FP32 power-law fields, rel eb 1e-4, radius 512",
+    return {"workload": f"16 x 1800x3600 FP32 power-law fields, rel eb {rel:g}, radius 512",
+            "compression_ratio": 4.0 * n_all / float(sum(nbs)),
             "per_field_gbs": res["per_field"], "batched_gbs": res["batched"],
             "speedup": res["batched"] / res["per_field"], "steps": steps,
             "graph_replays": int(g1[1] - g0[1] + g1[3] - g0[3])}
@@ -359,6 +371,43 @@ def autotuned(gbsz, workloads, dev, reps=5):
                     "tune_seconds": tune_s})
         del x
     ctx.close()
+    return out
+
+
+def oracle_configs(gbsz, workloads):
+    """The oracle on the host cores, single-threaded and OpenMP, compress and
+    decompress GB/s of input: 64^3 sinusoids (the rule's chunk and 4096),
+    the 16 1800x3600 fields at rel 1e-3 and 1e-4 (all 16 per step), and the
+    512^3 lognormal density at rel 1e-2..1e-5, radius 512 and 32768."""
+    from oracle import ref
+    sin64 = workloads.sinusoids_3d(64, seed=1001)
+    grf = workloads.grf_2d_batch(16, seed=1003)
+    logn = workloads.lognormal_3d(512, seed=1004)
+    cases = [("64^3 sinusoids, rel 1e-4, chunk 64", [sin64], 1e-4, 512, 64),
+             ("64^3 sinusoids, rel 1e-4, chunk 4096", [sin64], 1e-4, 512, 4096)]
+    for rel in (1e-3, 1e-4):
+        cases.append((f"16 x 1800x3600, rel {rel:g}", grf, rel, 512, gbsz.auto_chunk([3600, 1800], 512)))
+    for R in (512, 32768):
+        for rel in (1e-2, 1e-3, 1e-4, 1e-5):
+            cases.append((f"512^3 lognormal, rel {rel:g}, radius {R}", [logn], rel, R,
+                          gbsz.auto_chunk([512, 512, 512], R)))
+    out = []
+    for name, fields, rel, R, chunk in cases:
+        nbytes = 4 * sum(f.size for f in fields)
+        row = {"workload": name, "cores_omp": ref.threads(omp=True)}
+        for omp in (False, True):
+            tc = td = 0.0
+            size = 0
+            for f in fields:
+                t0 = time.perf_counter()
+                arc = ref.compress(f, rel, ref.EB_REL, R, chunk, omp=omp)
+                t1 = time.perf_counter()
+                ref.decompress(arc, omp=omp)
+                t2 = time.perf_counter()
+                tc, td, size = tc + t1 - t0, td + t2 - t1, size + arc.size
+            row["omp" if omp else "single"] = {"compress_gbs": nbytes / tc / 1e9, "decompress_gbs": nbytes / td / 1e9}
+            row["compression_ratio"] = nbytes / size
+        out.append(row)
     return out
 
 
@@ -717,6 +766,10 @@ def main():
     if rank == 0 and not a.skip_configs:
         configs_res = other_configs(ctx, gbsz, workloads, dev)
 
+    oracle_res = None
+    if rank == 0 and a.oracle_configs:
+        oracle_res = oracle_configs(gbsz, workloads)
+
     tune_res = None
     if rank == 0 and not a.skip_tune:
         tune_res = autotuned(gbsz, workloads, dev)
@@ -755,7 +808,7 @@ def main():
                 "stage_ms_per_step": {nm: stage_ms[i] / a.steps for i, nm in enumerate(stage_names)},
                 "roofline": roofline, "kernels": per_kernel, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": int(launches),
                 "batch_vs_per_field": batch, "micro": micro, "serving": serving_res,
-                "other_single_field": configs_res, "autotune": tune_res,
+                "other_single_field": configs_res, "autotune": tune_res, "oracle_configs": oracle_res,
                 "clocks": clocks}
         print(json.dumps(line), flush=True)
     if dist:
