@@ -132,6 +132,12 @@ void gbsz_destroy(gbsz_ctx *ctx);
  *     planes); 1..65536 = that extent.  The archive is the same either way
  *     (the tile boundaries only decide which threads compute which points). */
 #define GBSZ_OPT_LORENZO_SLAB 5
+/*   GBSZ_OPT_TEST_HOLD_CHUNK  test hook for the warp decoder's bounded wait:
+ *     -1 (default) = off; k >= 0 = chunk k never publishes its look-back
+ *     word, so the next chunk's wait runs out (after 1 s) and a fused 1D
+ *     decompress returns GBSZ_ERR_TIMEOUT; the context stays usable.  No
+ *     effect on the other decoders. */
+#define GBSZ_OPT_TEST_HOLD_CHUNK 6
 gbsz_status gbsz_set_option(gbsz_ctx *ctx, int option, int64_t value);
 
 /* Worst-case archive size in bytes for these parameters (0 if invalid).

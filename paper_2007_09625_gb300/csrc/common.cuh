@@ -538,6 +538,7 @@ struct WarpDecodeArgs {
     float ebx2;
     float *out;
     unsigned long long *look;
+    uint32_t hold_chunk;  // test hook: this chunk's look-back word is never published (~0u: none)
 };
 // kernels launched (one)
 int launch_decode_warp(const WarpDecodeArgs &w, bool fuse, cudaStream_t st);

@@ -247,6 +247,7 @@ struct gbsz_ctx {
     uint32_t cw64_only = 0;  // GBSZ_OPT_CODEWORD_BITS = 64
     uint32_t decoder = 0;    // GBSZ_OPT_DECODER
     uint32_t slab = 0;       // GBSZ_OPT_LORENZO_SLAB
+    uint32_t hold_chunk = ~0u;  // GBSZ_OPT_TEST_HOLD_CHUNK (~0u: none)
     // captured batch calls, and captured single-field calls
     BatchGraph gcomp, gdecomp, gsc, gsd, ggcomp, ggdecomp;
     // grouped batch calls: every field's scratch in one arena, the launch
@@ -740,6 +741,7 @@ gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void
         w.ebx2 = h.ebx2;
         w.out = d_field;
         w.look = s->codes.as<unsigned long long>();
+        w.hold_chunk = c->hold_chunk;
         ndec += launch_decode_warp(w, wu == WarpUse::Fused, st);
     }
     stage_end(c, st, 8, e0);
@@ -812,6 +814,7 @@ gbsz_status run_batch(gbsz_ctx *c, BatchGraph &bg, std::vector<uint64_t> &key, c
     key.push_back(c->profiling ? 1u : 0u);
     key.push_back(c->decoder);
     key.push_back(c->slab);
+    key.push_back(c->hold_chunk);
     key.push_back(c->tuned_gen);
     key.push_back(g_alloc_gen.load());  // last: checked again after a capture
     if (bg.exec && key == bg.key) {
@@ -1530,6 +1533,11 @@ gbsz_status gbsz_set_option(gbsz_ctx *c, int option, int64_t value)
     if (option == GBSZ_OPT_BATCH_MODE) {
         if (value != 0 && value != 1) return GBSZ_ERR_INVALID_ARG;
         c->batch_mode = (uint32_t)value;
+        return GBSZ_OK;
+    }
+    if (option == GBSZ_OPT_TEST_HOLD_CHUNK) {
+        if (value < -1 || value >= 0xFFFFFFFFll) return GBSZ_ERR_INVALID_ARG;
+        c->hold_chunk = value < 0 ? ~0u : (uint32_t)value;
         return GBSZ_OK;
     }
     if (option == GBSZ_OPT_LORENZO_SLAB) {

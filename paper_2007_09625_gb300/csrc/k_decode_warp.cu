@@ -30,8 +30,8 @@
 // inclusive prefix sum of the residuals along the field.  Each chunk's
 // in-cap residual sum and code-0 count are published for a decoupled
 // look-back over chunks (warps take chunks in order from a ticket counter,
-// so every chunk a warp waits for is held by a running warp; the wait is
-// bounded and reports a timeout).  The residuals of the outliers before the
+// so every chunk a warp waits for is held by a running warp; a wait longer
+// than 1 s gives up and the call reports a timeout).  The residuals of the outliers before the
 // chunk come from an exclusive scan of the outlier list's residuals at the
 // code-0 count before the chunk; the chunk's own outliers are matched, in
 // order, to its code-0 points.  Values leave as floats with coalesced 16-byte
@@ -59,7 +59,7 @@ static_assert(4u * (1u << kLutBits) + 2u * kLut2Entries + 16u * (kMaxLen + 2) + 
               "the general tables fit the table area");
 // look-back word: flag << 62 | code-0 count (30 bits) << 32 | in-cap residual sum
 constexpr unsigned long long kLbAgg = 1ull << 62, kLbInc = 2ull << 62;
-constexpr uint32_t kLbSpinMax = 1u << 22;  // polls before a look-back gives up (~0.3 s)
+constexpr unsigned long long kLbWaitNs = 1000000000ull;  // a look-back gives up after waiting 1 s
 constexpr uint32_t kNone = 0xFFFFFFFFu;
 
 __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long long *p)
@@ -67,6 +67,13 @@ __device__ __forceinline__ unsigned long long ld_relaxed(const unsigned long lon
     unsigned long long v;
     asm volatile("ld.relaxed.gpu.global.b64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
     return v;
+}
+
+__device__ __forceinline__ unsigned long long now_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
 }
 
 __device__ __forceinline__ void st_relaxed(unsigned long long *p, unsigned long long v)
@@ -431,13 +438,14 @@ __device__ __forceinline__ void decode_warp_body(const WarpDecodeArgs &wa)
         // fused S8: publish, look back, then the values
         const uint32_t S = __reduce_add_sync(0xffffffffu, isum);
         unsigned long long *look = wa.look;
-        if (lane == 0)
+        const bool publish = c != wa.hold_chunk;
+        if (lane == 0 && publish)
             st_relaxed(&look[c], ((c == 0 || !ok) ? kLbInc : kLbAgg) | ((unsigned long long)Z << 32) | S);
         if (!ok) continue;  // published as final, so no later chunk waits on it
         uint32_t Sp = 0, Zp = 0;
         if (c > 0) {
             int64_t base = (int64_t)c - 1;
-            uint32_t polls = 0;
+            const unsigned long long t0 = now_ns();
             for (;;) {
                 const int64_t idx = base - (int64_t)lane;
                 const unsigned long long v = idx >= 0 ? ld_relaxed(&look[idx]) : kLbInc;
@@ -447,7 +455,8 @@ __device__ __forceinline__ void decode_warp_body(const WarpDecodeArgs &wa)
                 const uint32_t fi = inc ? __ffs(inc) - 1 : 31u;
                 const unsigned need = fi == 31 ? 0xffffffffu : ((2u << fi) - 1u);
                 if (notyet & need) {
-                    if (++polls > kLbSpinMax) {
+                    // the same decision in every lane: the loop's votes need the whole warp
+                    if (__any_sync(0xffffffffu, now_ns() - t0 > kLbWaitNs)) {
                         timeout = true;
                         break;
                     }
@@ -460,7 +469,7 @@ __device__ __forceinline__ void decode_warp_body(const WarpDecodeArgs &wa)
                 if (inc) break;
                 base -= 32;
             }
-            if (lane == 0)
+            if (lane == 0 && publish)
                 st_relaxed(&look[c], kLbInc | ((unsigned long long)((Zp + Z) & 0x3FFFFFFFu) << 32) | (Sp + S));
             if (timeout) break;
         }

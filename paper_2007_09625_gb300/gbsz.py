@@ -61,6 +61,7 @@ OPT_CODEWORD_BITS = 1
 OPT_BATCH_MODE = 3
 OPT_DECODER = 4
 OPT_LORENZO_SLAB = 5
+OPT_TEST_HOLD_CHUNK = 6
 
 
 class GbszError(RuntimeError):
