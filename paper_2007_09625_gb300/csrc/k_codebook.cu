@@ -179,20 +179,134 @@ __device__ void canonicalize(const uint8_t *len, uint32_t nbins, uint32_t *s_cnt
     __syncthreads();
 }
 
+// The two-queue merge pair by pair on one thread, from the state (x leaves,
+// y internal nodes consumed, ni internal nodes made) to the end: leaf first
+// on equal frequency, internal nodes numbered in creation order.  The queue
+// heads and the nodes after them are kept in registers, so only the loads of
+// the next-but-one nodes are issued per pair, off the critical path.
+__device__ void serial_merge_from(const uint32_t *LF, uint32_t *F, uint32_t *P, uint32_t k, uint32_t x, uint32_t y,
+                                  uint32_t ni)
+{
+    uint32_t lx = x < k ? LF[x] : 0u, lxn = x + 1 < k ? LF[x + 1] : 0u;
+    uint32_t fy = y < ni ? F[y] : 0u, fyn = y + 1 < ni ? F[y + 1] : 0u;
+    for (; ni + 1 < k; ni++) {
+        uint32_t f = 0;
+        for (int r = 0; r < 2; r++) {
+            if (x < k && (y >= ni || lx <= fy)) {
+                f += lx;
+                P[x] = k + ni;
+                x++;
+                lx = lxn;
+                lxn = x + 1 < k ? LF[x + 1] : 0u;
+            } else {
+                f += fy;
+                P[k + y] = k + ni;
+                y++;
+                fy = fyn;
+                fyn = y + 1 < ni ? F[y + 1] : 0u;
+            }
+        }
+        F[ni] = f;
+        if (y == ni) fy = f;  // the node just made heads the internal queue
+        else if (y + 1 == ni) fyn = f;
+    }
+}
+
+// Entries of the ascending A[lo..hi) that are <= v, as lo + their count; the
+// whole warp (32-ary search: each round a probe per lane and a ballot).
+__device__ __forceinline__ uint32_t warp_upper(const uint32_t *A, uint32_t lo, uint32_t hi, unsigned long long v)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    while (hi - lo > 32) {
+        const uint32_t step = (hi - lo + 31) / 32;
+        const uint32_t i = lo + lane * step;
+        const uint32_t c = __popc(__ballot_sync(0xffffffffu, i < hi && (unsigned long long)A[i] <= v));
+        if (c == 0) return lo;
+        // the first entry above v lies after probe c - 1, at or before probe c
+        const uint32_t nhi = c < 32 ? min(hi, lo + c * step) : hi;
+        lo = lo + (c - 1) * step + 1;
+        hi = nhi;
+    }
+    const uint32_t i = lo + lane;
+    return lo + __popc(__ballot_sync(0xffffffffu, i < hi && (unsigned long long)A[i] <= v));
+}
+
+// The phases of the merge on one warp, from the state (lh leaves, ih internal
+// nodes consumed, ni made): searches by ballot, the pairs of a phase spread
+// over the lanes, warp barriers only; the last two pairs or fewer go
+// serially.  Returns the internal nodes made (k - 1 when complete).
+__device__ uint32_t warp_merge_from(const uint32_t *LF, uint32_t *F, uint32_t *P, uint32_t k, uint32_t lh,
+                                    uint32_t ih, uint32_t ni)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    while ((k - lh) + (ni - ih) > 1) {
+        uint32_t x = lh, y = ih;
+        unsigned long long f2 = 0;
+        for (int r = 0; r < 2; r++) {
+            if (x < k && (y >= ni || LF[x] <= F[y])) f2 += LF[x++];
+            else f2 += F[y++];
+        }
+        const uint32_t cl = warp_upper(LF, lh, k, f2) - lh, ci = warp_upper(F, ih, ni, f2) - ih;
+        const uint32_t np = (cl + ci) >> 1;
+        if (np <= 2) {
+            if (lane == 0) serial_merge_from(LF, F, P, k, lh, ih, ni);
+            __syncwarp();
+            return k - 1;
+        }
+        uint32_t xend = 0;  // leaves consumed through this lane's last pair
+        for (uint32_t p = lane; p < np; p += 32) {
+            const uint32_t d = 2 * p;
+            uint32_t l0 = d > ci ? d - ci : 0, l1 = min(d, cl);
+            while (l0 < l1) {  // merge-path split: leaves among the first d merged nodes
+                const uint32_t m = (l0 + l1) >> 1, b = d - m;
+                if (b == 0 || m == cl || F[ih + b - 1] < LF[lh + m]) l1 = m;
+                else l0 = m + 1;
+            }
+            uint32_t xx = l0, yy = d - l0, f = 0;
+            for (int r = 0; r < 2; r++) {
+                if (xx < cl && (yy >= ci || LF[lh + xx] <= F[ih + yy])) {
+                    f += LF[lh + xx];
+                    P[lh + xx] = k + ni + p;
+                    xx++;
+                } else {
+                    f += F[ih + yy];
+                    P[k + ih + yy] = k + ni + p;
+                    yy++;
+                }
+            }
+            F[ni + p] = f;
+            xend = xx;
+        }
+        __syncwarp();
+        const uint32_t xn = __shfl_sync(0xffffffffu, xend, (np - 1) & 31);
+        lh += xn;
+        ih += 2 * np - xn;
+        ni += np;
+    }
+    return ni;
+}
+
+// a phase pairing fewer nodes than this (one per lane) continues on one warp
+constexpr uint32_t kWarpPhaseMin = 32;
+
 // Two-queue Huffman merge in phases (all threads).  LF: leaf frequencies in
 // (frequency, symbol) order; F: internal frequencies in creation order; P:
 // parent of every node (leaves 0..k-1, internal node i has id k+i).  With a,
 // b the two smallest available nodes, every available node of frequency
 // <= a + b is consumed, in merge order (leaf first on equal frequency),
 // before any node not yet created, so the phase pairs that whole prefix.
-__device__ void phase_merge(const uint32_t *LF, uint32_t *F, uint32_t *P, uint32_t k, Control *ctl)
+// Once a phase would pair fewer than kWarpPhaseMin nodes, warp 0 finishes
+// (when the arrays are in shared memory: in global memory the warp's
+// dependent searches wait on L2 and the block's phases are faster).
+__device__ void phase_merge(const uint32_t *LF, uint32_t *F, uint32_t *P, uint32_t k, bool in_smem, Control *ctl)
 {
-    __shared__ uint32_t s_lh, s_ih, s_ni, s_cl, s_ci, s_np;
+    __shared__ uint32_t s_lh, s_ih, s_ni, s_cl, s_ci, s_np, s_warp;
     const uint32_t t = threadIdx.x, T = blockDim.x;
     if (t == 0) {
         s_lh = 0;
         s_ih = 0;
         s_ni = 0;
+        s_warp = 0;
     }
     __syncthreads();
     for (;;) {
@@ -223,6 +337,12 @@ __device__ void phase_merge(const uint32_t *LF, uint32_t *F, uint32_t *P, uint32
                 s_cl = l0 - lh;
                 s_ci = i0 - ih;
                 s_np = (s_cl + s_ci) >> 1;
+                // a small phase: its searches and block barriers cost more
+                // than its pairs (a skewed distribution makes many of them)
+                if (in_smem && s_np < kWarpPhaseMin) {
+                    s_warp = 1;
+                    s_np = 0;
+                }
             }
         }
         __syncthreads();
@@ -264,6 +384,11 @@ __device__ void phase_merge(const uint32_t *LF, uint32_t *F, uint32_t *P, uint32
         }
         __syncthreads();
     }
+    if (s_warp && t < 32) {
+        const uint32_t made = warp_merge_from(LF, F, P, k, s_lh, s_ih, s_ni);
+        if (t == 0) s_ni = made;
+    }
+    __syncthreads();
     if (t == 0 && s_ni != k - 1) atomicOr(&ctl->error, DERR_INTERNAL);
     __syncthreads();
 }
@@ -325,7 +450,7 @@ __device__ __forceinline__ void codebook_body(const CodebookArgs &a)
         uint32_t *P = sm_merge ? F + k : a.parent;
         for (uint32_t i = t; i < k; i += T) LF[i] = (uint32_t)(K[i] >> 16);
         __syncthreads();
-        phase_merge(LF, F, P, k, a.ctl);
+        phase_merge(LF, F, P, k, sm_merge, a.ctl);
         // depths by pointer jumping over 2k-1 nodes; root = 2k-2; depth <= 45
         const bool sm_depth = k <= kDepthSmemMax;
         const uint32_t N = 2 * k - 1, root = N - 1;
