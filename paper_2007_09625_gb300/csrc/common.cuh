@@ -544,7 +544,8 @@ struct WarpDecodeArgs {
 int launch_decode_warp(const WarpDecodeArgs &w, bool fuse, cudaStream_t st);
 // exclusive prefix sums of the outliers' residuals into odp[0..m] (m + 1
 // entries; partial: scan_partials(m + 1) entries); returns kernels launched
-int launch_outlier_prefix(const uint2 *outl, uint64_t m, uint32_t *odp, uint32_t *partial, cudaStream_t st);
+int launch_outlier_prefix(const uint2 *outl, uint64_t m, uint32_t *odp, uint32_t *partial, Control *ctl,
+                          cudaStream_t st);
 
 // chunk word offsets: the exclusive prefix sum of ceil(bits / 32) over the
 // archive's chunk table; a count above the longest chunk, or a total other

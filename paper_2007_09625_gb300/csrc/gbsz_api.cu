@@ -726,7 +726,7 @@ gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void
     ndec += launch_decode(d, st, 0);
     if (wu == WarpUse::Fused)
         ndec += launch_outlier_prefix(reinterpret_cast<const uint2 *>(arc + h.L.outl), h.m, s->dscr.as<uint32_t>(),
-                                      s->scan_part.as<uint32_t>(), st);
+                                      s->scan_part.as<uint32_t>(), s->ctl, st);
     stage_end(c, st, 7, e0);
     cudaStreamWaitEvent(st, s->join, 0);
     stage_begin(c, st, &e0);

@@ -547,7 +547,7 @@ __global__ void __launch_bounds__(FAST ? kDecFastThreads : kDecThreads, FAST ? 2
 int launch_decode(const DecodeArgs &a, cudaStream_t st, int phase)
 {
     const ChunkWords op = chunk_words_op(a);
-    if (phase == 0) return launch_scan(op, a.nchunk, a.scan_partial, st);
+    if (phase == 0) return launch_scan(op, a.nchunk, a.scan_partial, a.ctl, st);
     DecodeItem it;
     int variant;
     size_t dyn;

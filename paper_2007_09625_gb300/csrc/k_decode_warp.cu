@@ -605,9 +605,10 @@ int launch_decode_warp(const WarpDecodeArgs &w, bool fuse, cudaStream_t st)
     return 1;
 }
 
-int launch_outlier_prefix(const uint2 *outl, uint64_t m, uint32_t *odp, uint32_t *partial, cudaStream_t st)
+int launch_outlier_prefix(const uint2 *outl, uint64_t m, uint32_t *odp, uint32_t *partial, Control *ctl,
+                          cudaStream_t st)
 {
-    return launch_scan(OutlierResiduals{outl, m, odp}, m + 1, partial, st);
+    return launch_scan(OutlierResiduals{outl, m, odp}, m + 1, partial, ctl, st);
 }
 
 }  // namespace gbsz

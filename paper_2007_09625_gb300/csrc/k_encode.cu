@@ -735,7 +735,7 @@ int launch_encode(const EncodeArgs &a, cudaStream_t st, int phase)
         k_encode_count<<<grid, kEncThreads, smem, st>>>(a, nunits);
         return 1;
     }
-    if (phase == 1) return launch_scan(UnitScan{a.unit_tot, a.unit_off}, nunits, a.scan_part, st);
+    if (phase == 1) return launch_scan(UnitScan{a.unit_tot, a.unit_off}, nunits, a.scan_part, a.ctl, st);
     const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)a.num_sms * 3));
     k_encode_pack<<<grid, kEncThreads, (size_t)kWarps * kRound * 2 + tab, st>>>(a, nunits, use_smem);
     return 1;

@@ -926,7 +926,7 @@ int launch_reconstruct_order(const ReconArgs &a, const Geo &g, uint64_t n, cudaS
         for (uint32_t d = 0; d < g.ndim; d++) {
             if (g.n[d] < 2) continue;
             if (d == 0 && g.ndim == 1) {
-                nl += launch_scan(InclusiveOp{v}, n, a.scan_partial, st);
+                nl += launch_scan(InclusiveOp{v}, n, a.scan_partial, a.ctl, st);
             } else if (d == 0) {
                 const uint64_t rows = n / g.n[0];
                 k_scan_rows<<<grid_for(rows * 32), 256, 0, st>>>(v, g.n[0], rows);
@@ -1192,7 +1192,7 @@ void launch_reconstruct(const ReconArgs &a, cudaStream_t st, int *launches)
     } else {
         if (g.ndim == 1) {
             // tile sums were accumulated by the decoder and the outlier pass
-            if (!a.lblock) nl += launch_scan(TileOp{a.faces}, g.ntiles, a.scan_partial, st);
+            if (!a.lblock) nl += launch_scan(TileOp{a.faces}, g.ntiles, a.scan_partial, a.ctl, st);
         } else if (g.ndim == 2) {
             k_faces<k2TX, k2TY, 1, k2Threads><<<gridt, k2Threads, 0, st>>>(a, g, a.faces);
             nl++;
