@@ -44,7 +44,8 @@ typedef enum {
     GBSZ_ERR_CORRUPT = 3,     /* archive fails a consistency check */
     GBSZ_ERR_OOM = 4,         /* device or pinned allocation failed */
     GBSZ_ERR_CUDA = 5,        /* a CUDA runtime call failed */
-    GBSZ_ERR_TIMEOUT = 6,     /* a bounded device wait ran out (the warp decoder's look-back) */
+    GBSZ_ERR_TIMEOUT = 6,     /* a bounded device wait ran out (a look-back of the warp decoder
+                                 or of a scan waited more than 1 s) */
     GBSZ_ERR_UNSUPPORTED = 7, /* device is not sm_103 or feature absent */
     GBSZ_ERR_BOUNDS = 8       /* bounds-checking build only (-DGBSZ_BOUNDS_CHECK): a kernel's
                                  index check failed and the access was skipped */
