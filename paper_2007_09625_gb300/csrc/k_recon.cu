@@ -731,19 +731,6 @@ __device__ __forceinline__ uint64_t line_base(const Geo &g, int A, int d, uint64
     return g.off[A] + tile * sz + ci;
 }
 
-__global__ void k_scan_lines(Geo g, int A, int d, uint64_t nlines, uint32_t *F)
-{
-    const uint64_t line = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (line >= nlines) return;
-    uint64_t stride;
-    uint64_t p = line_base(g, A, d, line, stride);
-    uint32_t run = 0;
-    for (uint32_t i = 0; i < g.nt[d]; i++, p += stride) {
-        run += F[p];
-        F[p] = run;
-    }
-}
-
 // one warp per line, 32 entries at a time: for few lines, where a thread per
 // line would leave most of the GPU idle behind one long serial chain
 __device__ __forceinline__ void scan_lines_warp_body(const Geo &g, int A, int d, uint64_t nlines, uint32_t *F, VGrid vg)
@@ -769,12 +756,6 @@ __device__ __forceinline__ void scan_lines_warp_body(const Geo &g, int A, int d,
     }
 }
 
-__global__ void __launch_bounds__(256) k_scan_lines_warp(const __grid_constant__ Geo g, int A, int d, uint64_t nlines,
-                                                         uint32_t *F)
-{
-    scan_lines_warp_body(g, A, d, nlines, F, vgrid_self());
-}
-
 // one CTA per long line
 __global__ void __launch_bounds__(1024) k_scan_lines_cta(Geo g, int A, int d, uint32_t *F)
 {
@@ -791,6 +772,62 @@ __global__ void __launch_bounds__(1024) k_scan_lines_cta(Geo g, int A, int d, ui
     for (uint32_t i = lo; i < hi; i++) {
         run += F[p0 + i * stride];
         F[p0 + i * stride] = run;
+    }
+}
+
+// One pass along tile-grid dimension d over every subset that contains d
+// (subsets are separate arrays, and each subset's dimensions are scanned in
+// increasing order, pass by pass): lines numbered across the subsets.
+struct LinePass {
+    Geo g;
+    uint32_t *F;
+    int d, na;
+    int A[4];
+    uint64_t first[5];  // lines before subset i; first[na] = all lines
+};
+
+__device__ __forceinline__ uint64_t pass_line(const LinePass &p, uint64_t line, uint64_t &stride)
+{
+    int i = 0;
+    while (i + 1 < p.na && line >= p.first[i + 1]) i++;
+    return line_base(p.g, p.A[i], p.d, line - p.first[i], stride);
+}
+
+// a warp per line (few lines)
+__global__ void __launch_bounds__(256) k_scan_pass_warp(const __grid_constant__ LinePass p)
+{
+    const uint32_t lane = threadIdx.x & 31, len = p.g.nt[p.d];
+    const uint64_t nw = ((uint64_t)gridDim.x * blockDim.x) >> 5, nlines = p.first[p.na];
+    for (uint64_t line = ((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5; line < nlines; line += nw) {
+        uint64_t stride;
+        const uint64_t p0 = pass_line(p, line, stride);
+        uint32_t carry = 0;
+        for (uint32_t i0 = 0; i0 < len; i0 += 32) {
+            const uint32_t i = i0 + lane;
+            uint32_t v = i < len ? p.F[p0 + i * stride] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t u = __shfl_up_sync(0xffffffffu, v, o);
+                if (lane >= (uint32_t)o) v += u;
+            }
+            v += carry;
+            if (i < len) p.F[p0 + i * stride] = v;
+            carry = __shfl_sync(0xffffffffu, v, 31);
+        }
+    }
+}
+
+// a thread per line (many lines)
+__global__ void __launch_bounds__(256) k_scan_pass(const __grid_constant__ LinePass p)
+{
+    const uint64_t line = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (line >= p.first[p.na]) return;
+    uint64_t stride;
+    uint64_t q = pass_line(p, line, stride);
+    uint32_t run = 0;
+    for (uint32_t i = 0; i < p.g.nt[p.d]; i++, q += stride) {
+        run += p.F[q];
+        p.F[q] = run;
     }
 }
 
@@ -1059,7 +1096,10 @@ void plan_reconstruct_group(const ReconArgs *ra, uint32_t count, std::vector<uin
 {
     GroupList<RItem> tiles1d, scatter, exc, val1d, blk2, blk3, faces2, faces3, val2, val3;
     GroupList<ScanItem<TileOp>> tscan;
-    std::vector<GroupList<LineItem>> lines(8 * 3);  // by (A, d)
+    // one launch per tile-grid dimension: every field's subsets containing it
+    // (subsets are separate arrays; each is scanned along its dimensions in
+    // increasing order, launch by launch)
+    std::vector<GroupList<LineItem>> lines(3);
     for (uint32_t f = 0; f < count; f++) {
         const ReconArgs &a = ra[f];
         const Geo g = make_geo(a.ndim, a.dims);
@@ -1087,7 +1127,7 @@ void plan_reconstruct_group(const ReconArgs *ra, uint32_t count, std::vector<uin
                     for (int d = 0; d < (int)g.ndim; d++) {
                         if (!((A >> d) & 1) || g.nt[d] < 2) continue;
                         const uint64_t nlines = g.size[A] * (g.ntiles / g.nt[d]);
-                        lines[A * 3 + d].add(LineItem{g, a.faces, nlines, A, d}, std::min<uint64_t>((nlines + 7) / 8, sms * 8));
+                        lines[d].add(LineItem{g, a.faces, nlines, A, d}, std::min<uint64_t>((nlines + 7) / 8, sms * 8));
                     }
                 }
             }
@@ -1200,22 +1240,37 @@ void launch_reconstruct(const ReconArgs &a, cudaStream_t st, int *launches)
             k_faces<k3TX, k3TY, k3TZ, k3Threads><<<gridt, k3Threads, 0, st>>>(a, g, a.faces);
             nl++;
         }
-        for (int A = 1; A < 8 && g.ndim > 1; A++) {
-            if (!g.size[A]) continue;
-            for (int d = 0; d < (int)g.ndim; d++) {
-                if (!((A >> d) & 1) || g.nt[d] < 2) continue;
-                const uint64_t nlines = g.size[A] * (g.ntiles / g.nt[d]);
+        // carry scans: one launch per tile-grid dimension over every subset
+        // containing it (a CTA per line when lines are very long)
+        for (int d = 0; d < (int)g.ndim && g.ndim > 1; d++) {
+            if (g.nt[d] < 2) continue;
+            LinePass p{};
+            p.g = g;
+            p.F = a.faces;
+            p.d = d;
+            uint64_t nlines = 0;
+            for (int A = 1; A < 8; A++) {
+                if (!g.size[A] || !((A >> d) & 1)) continue;
+                const uint64_t nA = g.size[A] * (g.ntiles / g.nt[d]);
                 if (g.nt[d] > 2048) {
-                    k_scan_lines_cta<<<(unsigned)nlines, 1024, 0, st>>>(g, A, d, a.faces);
-                } else if (nlines < (uint64_t)a.num_sms * 256) {
-                    const uint64_t blocks = (nlines + 7) / 8;  // eight warps per block
-                    k_scan_lines_warp<<<(unsigned)std::min<uint64_t>(blocks, (uint64_t)a.num_sms * 8), 256, 0, st>>>(
-                        g, A, d, nlines, a.faces);
-                } else {
-                    k_scan_lines<<<(unsigned)((nlines + 255) / 256), 256, 0, st>>>(g, A, d, nlines, a.faces);
+                    k_scan_lines_cta<<<(unsigned)nA, 1024, 0, st>>>(g, A, d, a.faces);
+                    nl++;
+                    continue;
                 }
-                nl++;
+                p.A[p.na] = A;
+                p.first[p.na] = nlines;
+                p.na++;
+                nlines += nA;
             }
+            if (p.na == 0) continue;
+            p.first[p.na] = nlines;
+            if (nlines < (uint64_t)a.num_sms * 256) {
+                const uint64_t blocks = (nlines + 7) / 8;  // eight warps per block
+                k_scan_pass_warp<<<(unsigned)std::min<uint64_t>(blocks, (uint64_t)a.num_sms * 8), 256, 0, st>>>(p);
+            } else {
+                k_scan_pass<<<(unsigned)((nlines + 255) / 256), 256, 0, st>>>(p);
+            }
+            nl++;
         }
         if (g.ndim == 1) {
             // persistent: as many blocks as fit at once
