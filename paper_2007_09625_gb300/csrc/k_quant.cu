@@ -52,20 +52,22 @@ __device__ void finalize_eb(Control *ctl, double eb, uint32_t mode, uint32_t kma
     if (!ok) atomicOr(&ctl->error, DERR_EB);
 }
 
-__device__ __forceinline__ void mm_update(float v, uint32_t &kmax, uint32_t &kmin)
+// max and min over the finite values: v * 0 + v is v when v is finite and NaN
+// for +-Inf and NaN, which fmaxf / fminf ignore (three operations a value).
+// A zero may come back as either zero; the range max - min, and so the bound,
+// is the same.
+__device__ __forceinline__ void mm_update(float v, float &mx, float &mn)
 {
-    if ((__float_as_uint(v) & 0x7F800000u) != 0x7F800000u) {
-        const uint32_t k = ordered_key(v);
-        kmax = max(kmax, k);
-        kmin = max(kmin, ~k);
-    }
+    const float w = __fmaf_rn(v, 0.0f, v);
+    mx = fmaxf(mx, w);
+    mn = fminf(mn, w);
 }
 
 template <bool VEC>
 __device__ __forceinline__ void minmax_body(const float *__restrict__ x, uint64_t n, Control *ctl, double eb,
                                             uint32_t mode, VGrid vg)
 {
-    uint32_t kmax = 0, kmin = 0;
+    float mx = -INFINITY, mn = INFINITY;
     const uint64_t tid = (uint64_t)vg.bid * blockDim.x + threadIdx.x;
     const uint64_t stride = (uint64_t)vg.nb * blockDim.x;
     if (VEC) {
@@ -78,23 +80,25 @@ __device__ __forceinline__ void minmax_body(const float *__restrict__ x, uint64_
             for (int u = 0; u < 4; u++) v[u] = x4[i + u * stride];
 #pragma unroll
             for (int u = 0; u < 4; u++) {
-                mm_update(v[u].x, kmax, kmin);
-                mm_update(v[u].y, kmax, kmin);
-                mm_update(v[u].z, kmax, kmin);
-                mm_update(v[u].w, kmax, kmin);
+                mm_update(v[u].x, mx, mn);
+                mm_update(v[u].y, mx, mn);
+                mm_update(v[u].z, mx, mn);
+                mm_update(v[u].w, mx, mn);
             }
         }
         for (; i < n4; i += stride) {
             const float4 v = x4[i];
-            mm_update(v.x, kmax, kmin);
-            mm_update(v.y, kmax, kmin);
-            mm_update(v.z, kmax, kmin);
-            mm_update(v.w, kmax, kmin);
+            mm_update(v.x, mx, mn);
+            mm_update(v.y, mx, mn);
+            mm_update(v.z, mx, mn);
+            mm_update(v.w, mx, mn);
         }
-        for (uint64_t j = n4 * 4 + tid; j < n; j += stride) mm_update(x[j], kmax, kmin);
+        for (uint64_t j = n4 * 4 + tid; j < n; j += stride) mm_update(x[j], mx, mn);
     } else {
-        for (uint64_t j = tid; j < n; j += stride) mm_update(x[j], kmax, kmin);
+        for (uint64_t j = tid; j < n; j += stride) mm_update(x[j], mx, mn);
     }
+    // order-preserving keys for the reductions across the grid (0: no finite value)
+    uint32_t kmax = mx > -INFINITY ? ordered_key(mx) : 0u, kmin = mn < INFINITY ? ~ordered_key(mn) : 0u;
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
         kmax = max(kmax, __shfl_xor_sync(0xffffffffu, kmax, o));
