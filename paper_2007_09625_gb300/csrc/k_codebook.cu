@@ -29,8 +29,9 @@ constexpr int kCbThreads = 1024;
 constexpr uint32_t kBitonicMax = 8192;    // 8192 keys = 64 KB of shared memory
 // merge state (4k words) in shared memory up to this many used symbols, and
 // the pointer-jumping buffers too (12k words in all) up to kDepthSmemMax
-constexpr uint32_t kMergeSmemMax = 4096;
-constexpr uint32_t kDepthSmemMax = 1024;
+// (the dynamic shared memory is 32K words)
+constexpr uint32_t kMergeSmemMax = 8192;
+constexpr uint32_t kDepthSmemMax = 2048;
 
 // Stable sort of n unique 64-bit keys by bits [bit_lo, bit_hi); the keys are
 // already ordered by the bits below bit_lo.  Returns the buffer holding the
@@ -149,6 +150,7 @@ __device__ void canonicalize(const uint8_t *len, uint32_t nbins, uint32_t *s_cnt
     for (uint32_t c0 = 0; c0 < nbins; c0 += T) {
         const uint32_t s = c0 + t;
         const uint32_t l = s < nbins ? len[s] : 0u;
+        if (!__syncthreads_or(l != 0)) continue;  // no used symbol in these bins
         const uint32_t peers = __match_any_sync(0xffffffffu, l);
         const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
         for (uint32_t i = t; i < W * L; i += T) wcnt[i] = 0;
@@ -395,25 +397,31 @@ __device__ void phase_merge(const uint32_t *LF, uint32_t *F, uint32_t *P, uint32
 
 __device__ __forceinline__ void codebook_body(const CodebookArgs &a)
 {
-    extern __shared__ uint32_t s_cnt[];  // 16 * kCbThreads words
+    extern __shared__ uint32_t s_cnt[];  // kCbSmem bytes
     __shared__ Canon canon;
     __shared__ uint32_t s_scan[33];
     __shared__ unsigned long long s_scan64[33];
     const uint32_t T = blockDim.x, t = threadIdx.x, nbins = a.nbins;
 
-    // symbols with nonzero frequency, keys (freq << 16 | sym) in symbol order
-    const uint32_t per = (nbins + T - 1) / T;
-    const uint32_t lo = min(nbins, t * per), hi = min(nbins, lo + per);
+    // symbols with nonzero frequency, keys (freq << 16 | sym) in symbol order:
+    // warp w takes a contiguous run of bins in rounds of 32 consecutive bins
+    // (coalesced loads; ballot ranks keep the symbol order)
+    const uint32_t lane = t & 31, w = t >> 5, W = T >> 5;
+    const uint32_t seg = ((nbins + 32 * W - 1) / (32 * W)) * 32;
+    const uint32_t wlo = min(nbins, w * seg), whi = min(nbins, wlo + seg);
     uint32_t c = 0, fmax = 0;
     unsigned long long ftot = 0;
-    for (uint32_t s = lo; s < hi; s++) {
-        const uint32_t f = a.hist[s];
+    for (uint32_t s0 = wlo; s0 < whi; s0 += 32) {
+        const uint32_t s = s0 + lane;
+        const uint32_t f = s < whi ? a.hist[s] : 0u;
         c += f > 0;
         fmax = max(fmax, f);
         ftot += f;
     }
+    const uint32_t wc = __reduce_add_sync(0xffffffffu, c);
     uint32_t k;
-    uint32_t pos = block_excl_scan(c, s_scan, &k);
+    uint32_t wbase = block_excl_scan(lane == 0 ? wc : 0u, s_scan, &k);
+    wbase = __shfl_sync(0xffffffffu, wbase, 0);
     fmax = block_max(fmax, s_scan);
     // the merge adds frequencies in 32 bits: a histogram whose total reaches
     // 2^32 is refused (the compressor's fields have fewer than 2^32 points)
@@ -423,9 +431,14 @@ __device__ __forceinline__ void codebook_body(const CodebookArgs &a)
         if (t == 0) atomicOr(&a.ctl->error, DERR_RANGE);
         return;
     }
-    for (uint32_t s = lo; s < hi; s++) {
-        const uint32_t f = a.hist[s];
-        if (f) a.keyA[pos++] = ((unsigned long long)f << 16) | s;
+    for (uint32_t s0 = wlo; s0 < whi; s0 += 32) {
+        const uint32_t s = s0 + lane;
+        const uint32_t f = s < whi ? a.hist[s] : 0u;
+        const unsigned used = __ballot_sync(0xffffffffu, f > 0);
+        if (f) a.keyA[wbase + __popc(used & ((1u << lane) - 1u))] = ((unsigned long long)f << 16) | s;
+        wbase += __popc(used);
+    }
+    for (uint32_t s = t; s < nbins; s += T) {
         a.len_out[s] = 0;
         a.cw64[s] = 0;
         a.cw32[s] = 0;
@@ -620,7 +633,9 @@ __global__ void __launch_bounds__(kCbThreads, 1) k_decode_tables_group(const Cod
     decode_tables_body(items[blockIdx.x]);
 }
 
-constexpr size_t kCbSmem = 16 * 1024 * sizeof(uint32_t);  // 8192 sort keys; 16 digit counters per thread
+// 32K words: 8192 sort keys (or 16 digit counters per thread), and the merge
+// of up to kMergeSmemMax used symbols
+constexpr size_t kCbSmem = 32 * 1024 * sizeof(uint32_t);
 
 // opt in to more than 48 KB of dynamic shared memory, once per device
 // (host threads may race here: the bits are atomic, and setting an attribute
