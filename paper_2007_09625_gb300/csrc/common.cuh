@@ -447,6 +447,10 @@ struct EncodeArgs {
     const uint16_t *codes;
     const float *x;
     const int2 *dscr;
+    // code-0 bitmap (bit i of byte b: point 8b + i has code 0), or nullptr;
+    // when set, the count phase writes it for the points below n and pack
+    // leaves the outlier and exception records to k_encode_outliers
+    uint32_t *zbits;
     uint64_t n;
     uint32_t chunk, radius, nbins;
     const uint64_t *cw64;
@@ -466,7 +470,8 @@ struct EncodeArgs {
     double eb;
     int num_sms;
 };
-// phase 0: count, 1: scan of the unit totals, 2: pack; returns kernels launched
+// phase 0: count, 1: scan of the unit totals, 2: pack (and, with a code-0
+// bitmap, the outlier records); returns kernels launched
 int launch_encode(const EncodeArgs &a, cudaStream_t st, int phase);
 
 // grouped S5 (items and block tables in device memory)

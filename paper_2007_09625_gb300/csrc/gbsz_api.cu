@@ -140,6 +140,7 @@ struct Slot {
     // per-field scratch (grown on demand)
     Buf codes, dscr, unit_tot, unit_off, unit_part, unit_exc, lane_bits, chunk_off, faces, scan_part;
     Buf qint, excm;  // Lorenzo order > 1: prequantized integers, exception bits
+    Buf zbits;       // 1D order 1 (large fields): code-0 bitmap of the dual-quant kernel
     // fixed-size scratch
     Buf hist, cw64, cw32, codes_only, keyA, keyB, nodef, parent, distA, distB, parA, parB;
     Buf lut, lutf, first, count, start, sorted;
@@ -176,7 +177,7 @@ struct Slot {
     {
         uint64_t t = ctl ? sizeof(Control) : 0;
         for (const Buf *b : {&codes, &dscr, &unit_tot, &unit_off, &unit_part, &unit_exc, &lane_bits, &chunk_off, &faces,
-                             &scan_part, &qint, &excm, &hist, &cw64, &cw32, &codes_only, &keyA, &keyB, &nodef, &parent,
+                             &scan_part, &qint, &excm, &zbits, &hist, &cw64, &cw32, &codes_only, &keyA, &keyB, &nodef, &parent,
                              &distA, &distB, &parA, &parB, &lut, &lutf, &first, &count, &start, &sorted})
             t += b->cap;
         return t;
@@ -185,13 +186,13 @@ struct Slot {
     void release_field_scratch()
     {
         for (Buf *b : {&codes, &dscr, &unit_tot, &unit_off, &unit_part, &unit_exc, &lane_bits, &chunk_off, &faces,
-                       &scan_part, &qint, &excm})
+                       &scan_part, &qint, &excm, &zbits})
             b->release();
     }
     void release()
     {
         for (Buf *b : {&codes, &dscr, &unit_tot, &unit_off, &unit_part, &unit_exc, &lane_bits, &chunk_off, &faces, &scan_part,
-                       &qint, &excm, &hist, &cw64,
+                       &qint, &excm, &zbits, &hist, &cw64,
                        &cw32, &codes_only, &keyA, &keyB, &nodef, &parent, &distA, &distB, &parA, &parB, &lut, &lutf,
                        &first, &count, &start, &sorted})
             b->release();
@@ -483,6 +484,19 @@ gbsz_status check_compress(const float *d_field, const gbsz_params *pin, const v
 // bytes a Buf holds after ensure(bytes)
 inline uint64_t buf_bytes(uint64_t bytes) { return std::max<uint64_t>(bytes, 256); }
 
+// Single-field compression of a 1D order-1 field of at least this many
+// points leaves its outlier and exception records to k_encode_outliers, fed
+// by a code-0 bitmap (n/8 bytes) that the count phase writes; smaller fields
+// keep the records in pack (one launch fewer).
+constexpr uint64_t kZbitsMin = 1ull << 22;
+bool uses_zbits(const gbsz_params &p, uint64_t n)
+{
+    uint64_t gd[3];
+    return n >= kZbitsMin && order_of(p) == 1 && lorenzo_geom(p, gd) == 1;
+}
+// the bitmap rounded up to whole 128-point lanes (k_encode_outliers reads them whole)
+inline uint64_t zbits_bytes(uint64_t n) { return (n + 127) / 128 * 16 + 64; }
+
 // Device bytes of the per-field scratch reserve_compress / reserve_decompress
 // allocate in a slot for one field (p resolved: chunk != 0).
 uint64_t compress_scratch(const gbsz_params &p, uint64_t n)
@@ -491,6 +505,7 @@ uint64_t compress_scratch(const gbsz_params &p, uint64_t n)
     uint64_t t = buf_bytes(n * 2 + 64) + buf_bytes(n * 8 + 64) + buf_bytes(nunits * 16) + buf_bytes((n / 64 + 64) * 4) +
                  buf_bytes(nunits * 16) + buf_bytes(scan_partials(nunits) * 16 + 64) + buf_bytes(nunits * 4);
     if (order_of(p) > 1) t += buf_bytes(n * 4 + 64) + buf_bytes((n / 32 + 1) * 4);
+    if (uses_zbits(p, n)) t += buf_bytes(zbits_bytes(n));
     return t;
 }
 
@@ -511,6 +526,7 @@ bool reserve_compress(Slot *s, const gbsz_params &p, uint64_t n)
 {
     const uint64_t nunits = encode_units(n, p.chunk);
     if (order_of(p) > 1 && !(s->qint.ensure(n * 4 + 64) && s->excm.ensure((n / 32 + 1) * 4))) return false;
+    if (uses_zbits(p, n) && !s->zbits.ensure(zbits_bytes(n))) return false;
     return s->codes.ensure(n * 2 + 64) && s->dscr.ensure(n * 8 + 64) && s->unit_tot.ensure(nunits * 16) &&
            s->lane_bits.ensure((n / 64 + 64) * 4) && s->unit_off.ensure(nunits * 16) &&
            s->unit_part.ensure(scan_partials(nunits) * 16 + 64) && s->unit_exc.ensure(nunits * 4);
@@ -604,6 +620,7 @@ gbsz_status enqueue_compress(gbsz_ctx *c, Slot *s, const float *d_field, const g
     en.codes = q.codes;
     en.x = d_field;
     en.dscr = q.dscr;
+    en.zbits = uses_zbits(p, n) ? s->zbits.as<uint32_t>() : nullptr;
     en.n = n;
     en.chunk = p.chunk;
     en.radius = p.radius;

@@ -225,14 +225,38 @@ __device__ __forceinline__ uint32_t count8(const CT &ct, uint4 w)
 }
 
 template <typename CT>
-__device__ __forceinline__ uint32_t count_tail(const EncodeArgs &a, const CT &ct, uint64_t p, uint64_t n)
+__device__ __forceinline__ uint32_t count_tail(const EncodeArgs &a, const CT &ct, uint64_t p, uint64_t n, uint32_t &z)
 {
-    uint32_t s = 0;
-    for (uint32_t q = 0; q < 8 && p + q < n; q++) s += ct(a.codes[p + q]);
+    uint32_t s = 0, m = 0;
+    for (uint32_t q = 0; q < 8 && p + q < n; q++) {
+        const uint32_t e = ct(a.codes[p + q]);
+        s += e;
+        m += e << q;
+    }
+    z = m >> 16;
     return s;
 }
 
+// The code-0 positions of eight symbols (bit q: symbol q, x's low half
+// first) from their count entries: sum_q entry_q << q keeps the length parts
+// below bit 16 (255 * 45 < 2^16), so bits 16..23 are the code-0 flags.
 template <typename CT>
+__device__ __forceinline__ uint32_t count8z(const CT &ct, uint4 w, uint32_t &z)
+{
+    const uint32_t v[4] = {w.x, w.y, w.z, w.w};
+    uint32_t s = 0, m = 0;
+#pragma unroll
+    for (int q = 0; q < 4; q++) {
+        const uint32_t e0 = ct(v[q] & 0xFFFFu), e1 = ct(v[q] >> 16);
+        s += e0 + e1;
+        m += (e0 << (2 * q)) + (e1 << (2 * q + 1));
+    }
+    z = m >> 16;
+    return s;
+}
+
+// ZB: the kernel may write the code-0 bitmap (when a.zbits is set)
+template <bool ZB, typename CT>
 __device__ __forceinline__ void count_units(const EncodeArgs &a, uint64_t nunits, const CT &ct, uint32_t *part,
                                             VGrid vg)
 {
@@ -247,6 +271,7 @@ __device__ __forceinline__ void count_units(const EncodeArgs &a, uint64_t nunits
     const Layout L0 = make_layout(a.radius, nchunk, a.ctl->n_out, a.ctl->n_exc, 0);
     const bool first_of_chunk = (lane & (ug.G - 1)) == 0;
     const uint32_t *myseg = part + (lane / segs) * kPartStride + (lane % segs) * per;
+    uint8_t *zb8 = ZB ? reinterpret_cast<uint8_t *>(a.zbits) : nullptr;  // a byte per 8 points (coalesced stores)
     const uint64_t gw = ((uint64_t)vg.bid * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nw = ((uint64_t)vg.nb * blockDim.x) >> 5;
     for (uint64_t u = gw; u < nunits; u += nw) {
@@ -267,13 +292,25 @@ __device__ __forceinline__ void count_units(const EncodeArgs &a, uint64_t nunits
                     uint4 w[8];
 #pragma unroll
                     for (int i = 0; i < 8; i++) w[i] = ldg_nc16(src + 32 * (k + i));
+                    if (zb8) {
+                        const uint64_t b0 = r0 / 8 + 32ull * k + lane;
 #pragma unroll
-                    for (int i = 0; i < 8; i++) s8[i] = count8(ct, w[i]);
+                        for (int i = 0; i < 8; i++) {
+                            uint32_t z;
+                            s8[i] = count8z(ct, w[i], z);
+                            if (GBSZ_CHECK(b0 + 32 * i < (n + 7) / 8, a.ctl)) zb8[b0 + 32 * i] = (uint8_t)z;
+                        }
+                    } else {
+#pragma unroll
+                        for (int i = 0; i < 8; i++) s8[i] = count8(ct, w[i]);
+                    }
                 } else {
 #pragma unroll
                     for (int i = 0; i < 8; i++) {
                         const uint64_t p = r0 + 256ull * (k + i) + 8ull * lane;
-                        s8[i] = p + 8 <= n ? count8(ct, src[32 * (k + i)]) : count_tail(a, ct, p, n);
+                        uint32_t z = 0;
+                        s8[i] = p + 8 <= n ? count8z(ct, src[32 * (k + i)], z) : count_tail(a, ct, p, n, z);
+                        if (zb8 && p < n && GBSZ_CHECK(p / 8 < (n + 7) / 8, a.ctl)) zb8[p / 8] = (uint8_t)z;
                     }
                 }
 #pragma unroll
@@ -339,7 +376,79 @@ __device__ __forceinline__ void append(unsigned long long &acc, uint32_t &nacc, 
     }
 }
 
+// The outlier records (index, residual) and exception records (index, raw
+// value bits) of one round, in index order.  zlo / zhi mark the code-0 points
+// among the lane's S points from s0 (bit j: point s0 + j); orun / erun are
+// the warp's running record offsets, advanced by the round's totals.  A
+// lane's residuals are loaded four at a time, then written.
+__device__ __forceinline__ void emit_outliers(const EncodeArgs &a, const Layout &L0, uint64_t s0,
+                                              unsigned long long zlo, unsigned long long zhi, bool unit_exc,
+                                              uint64_t &orun, uint64_t &erun, bool &cap_err)
+{
+    const uint64_t n = a.n;
+    const uint32_t nz = __popcll(zlo) + __popcll(zhi);
+    uint32_t ne = 0;
+    if (unit_exc) {
+        for (unsigned long long m = zlo; m; m &= m - 1)
+            if (GBSZ_CHECK(s0 + __ffsll(m) - 1 < n, a.ctl)) ne += a.dscr[s0 + __ffsll(m) - 1].y != 0;
+        for (unsigned long long m = zhi; m; m &= m - 1)
+            if (GBSZ_CHECK(s0 + 63 + __ffsll(m) < n, a.ctl)) ne += a.dscr[s0 + 63 + __ffsll(m)].y != 0;
+    }
+    const uint32_t oinc = warp_incl_scan(nz), einc = warp_incl_scan(ne);
+    uint64_t oi = orun + (oinc - nz), ei = erun + (einc - ne);
+    auto emit_outlier = [&](uint64_t idx, int2 dv) {
+        const uint64_t o8 = L0.outl + 8 * oi++;
+        if (o8 + 8 <= a.capacity) {
+            put_u32(a.archive + o8, (uint32_t)idx);
+            put_u32(a.archive + o8 + 4, (uint32_t)dv.x);
+        } else {
+            cap_err = true;
+        }
+        if (dv.y) {
+            const uint64_t e8 = L0.exc + 8 * ei++;
+            if (e8 + 8 <= a.capacity) {
+                put_u32(a.archive + e8, (uint32_t)idx);
+                put_u32(a.archive + e8 + 4, __float_as_uint(a.x[idx]));
+            } else {
+                cap_err = true;
+            }
+        }
+    };
+    unsigned long long mlo = zlo, mhi = zhi;
+    while (mlo | mhi) {
+        uint64_t idx[4];
+        bool has[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++) {
+            has[k] = (mlo | mhi) != 0;
+            uint32_t j = 0;
+            if (mlo) {
+                j = __ffsll(mlo) - 1;
+                mlo &= mlo - 1;
+            } else if (mhi) {
+                j = 63 + __ffsll(mhi);
+                mhi &= mhi - 1;
+            }
+            idx[k] = s0 + j;
+        }
+        int2 dv[4];
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            dv[k] = has[k] && GBSZ_CHECK(idx[k] < n, a.ctl) ? a.dscr[idx[k]] : make_int2(0, 0);
+#pragma unroll
+        for (int k = 0; k < 4; k++)
+            if (has[k]) emit_outlier(idx[k], dv[k]);
+    }
+    orun += __shfl_sync(0xffffffffu, oinc, 31);
+    erun += __shfl_sync(0xffffffffu, einc, 31);
+}
+
 // Phase 3: pack every unit at its offsets; the last unit writes the header.
+// With a code-0 bitmap (1D order 1) the records are k_encode_outliers' work
+// and the lanes only pack.  (Zero masks and residual loads in the packing
+// warps cost 0.146 of 0.338 ms at 2^28 points with 1.6% outliers: pack runs
+// three blocks per SM for its shared-memory staging, too few warps to cover
+// the residuals' random loads.)
 // PAIR (longest code at most 16 bits): two codewords are joined into one of
 // at most 32 bits before they enter the accumulator, so each pair needs one
 // shift-in and one full-word test.
@@ -359,6 +468,7 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
     uint32_t *stream = reinterpret_cast<uint32_t *>(a.archive + L0.stream);
     const uint64_t stream_cap = a.capacity > L0.stream ? (a.capacity - L0.stream) / 4 : 0;
     const bool first_of_chunk = (lane & (G - 1)) == 0;
+    const bool zb = a.zbits != nullptr;  // records written by k_encode_outliers
     const uint64_t gw = ((uint64_t)vg.bid * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)vg.nb * blockDim.x) >> 5;
     bool cap_err = false;
@@ -368,7 +478,8 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
         const uint32_t rounds = multi ? (uint32_t)((ulen + kRound - 1) / kRound) : 1u;
         const ulonglong2 off = a.unit_off[u];
         const unsigned long long W0 = off.x, O0 = off.y & 0xFFFFFFFFull, E0 = off.y >> 32;
-        const bool unit_exc = any_exc && a.unit_exc[u] != 0;  // exceptions of the unit, counted by dual-quant
+        // exceptions of the unit, counted by dual-quant
+        const bool unit_exc = !zb && any_exc && a.unit_exc[u] != 0;
         if (u == nunits - 1 && lane == 0) {
             const ulonglong2 tot = a.unit_tot[u];
             const unsigned long long W = W0 + tot.x;
@@ -380,7 +491,7 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
             if (L.stream <= a.capacity) write_header(a, L, nchunk, M, E, W, a.ctl->maxlen);
         }
         unsigned long long round_bits = 0;  // multi: bits of earlier rounds of the chunk
-        uint32_t o_run = 0, e_run = 0;
+        uint64_t orun = O0, erun = E0;      // record offsets of this round
         uint32_t carry = 0;                 // multi: partial last word of the previous round
         for (uint32_t r = 0; r < rounds; r++) {
             const uint64_t r0 = ubase + (uint64_t)r * 32 * S, s0 = r0 + (uint64_t)lane * S;
@@ -426,15 +537,17 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
                 for (uint32_t j = 0; j < ln.nv; j++) {
                     const uint4 q4 = ln.vec(j);
                     const uint32_t v[4] = {q4.x, q4.y, q4.z, q4.w};
-                    // zero symbols of these 8, as bits 8j.. of the lane's mask
-                    const uint32_t z = ((__vcmpeq2(v[0], 0) & 0x00010001u) * 1u) |
-                                       ((__vcmpeq2(v[1], 0) & 0x00010001u) << 2) |
-                                       ((__vcmpeq2(v[2], 0) & 0x00010001u) << 4) |
-                                       ((__vcmpeq2(v[3], 0) & 0x00010001u) << 6);
-                    const uint32_t z8 = (z | (z >> 15)) & 0xFFu;
-                    if (z8) {
-                        if (j < 8) zlo |= (unsigned long long)z8 << (8 * j);
-                        else zhi |= (unsigned long long)z8 << (8 * (j - 8));
+                    if (!zb) {
+                        // zero symbols of these 8, as bits 8j.. of the lane's mask
+                        const uint32_t z = ((__vcmpeq2(v[0], 0) & 0x00010001u) * 1u) |
+                                           ((__vcmpeq2(v[1], 0) & 0x00010001u) << 2) |
+                                           ((__vcmpeq2(v[2], 0) & 0x00010001u) << 4) |
+                                           ((__vcmpeq2(v[3], 0) & 0x00010001u) << 6);
+                        const uint32_t z8 = (z | (z >> 15)) & 0xFFu;
+                        if (z8) {
+                            if (j < 8) zlo |= (unsigned long long)z8 << (8 * j);
+                            else zhi |= (unsigned long long)z8 << (8 * (j - 8));
+                        }
                     }
                     if (CW32 && PAIR) {
 #pragma unroll
@@ -493,7 +606,7 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
                         if (ok) lout[nw32] = w[q];
                         nw32++;
                     }
-                    if (c == 0) {
+                    if (c == 0 && !zb) {
                         if (j < 64) zlo |= 1ull << j;
                         else zhi |= 1ull << (j - 64);
                     }
@@ -521,65 +634,119 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
             }
             if (multi && lane == 0 && r > 0 && starts_mid && ok) lout[0] = head | prev_carry;
             if (multi && !(lane == 31 && has_tail)) carry = 0;
-            // outliers and exceptions in index order
-            const uint32_t nz = __popcll(zlo) + __popcll(zhi);
-            uint32_t ne = 0;
-            if (unit_exc) {
-                for (unsigned long long m = zlo; m; m &= m - 1)
-                    if (GBSZ_CHECK(s0 + __ffsll(m) - 1 < n, a.ctl)) ne += a.dscr[s0 + __ffsll(m) - 1].y != 0;
-                for (unsigned long long m = zhi; m; m &= m - 1)
-                    if (GBSZ_CHECK(s0 + 63 + __ffsll(m) < n, a.ctl)) ne += a.dscr[s0 + 63 + __ffsll(m)].y != 0;
-            }
-            const uint32_t oinc = warp_incl_scan(nz), einc = warp_incl_scan(ne);
-            uint64_t oi = O0 + o_run + (oinc - nz), ei = E0 + e_run + (einc - ne);
-            auto emit_outlier = [&](uint64_t idx, int2 dv) {
-                const uint64_t o8 = L0.outl + 8 * oi++;
-                if (o8 + 8 <= a.capacity) {
-                    put_u32(a.archive + o8, (uint32_t)idx);
-                    put_u32(a.archive + o8 + 4, (uint32_t)dv.x);
-                } else {
-                    cap_err = true;
+            if (!zb) emit_outliers(a, L0, s0, zlo, zhi, unit_exc, orun, erun, cap_err);
+            round_bits += rtot;
+        }
+    }
+    if (cap_err) atomicOr(&a.ctl->error, DERR_CAPACITY);
+}
+
+// Outlier and exception records from the dual-quant kernel's code-0 bitmap:
+// one warp per unit, its rounds in order as in pack, lane l reading the
+// bitmap words of the same S points as there (S / 32 = 2 or 4 words, one 8-
+// or 16-byte load).  The ranks are the bitmap's popcounts scanned across the
+// warp on top of the unit's offsets from the count/scan phases, so the
+// records land exactly where pack would have put them.  The warp lists the
+// round's code-0 points in rank order in shared memory; lane l then takes
+// records l, l + 32, ..., so its residual loads are issued together and the
+// records are stored coalesced; exceptions are ranked by ballot.  A round of
+// more than kOutWin outliers takes the per-lane path instead.  Bits of points
+// at or past n are cleared (their entries were never written).
+constexpr uint32_t kOutWin = 512;  // listed positions per warp (16-bit offsets in the round)
+
+__device__ void outlier_units(const EncodeArgs &a, uint64_t nunits, uint16_t *pos, VGrid vg)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const uint64_t n = a.n;
+    const uint32_t C = a.chunk;
+    const UnitGeom ug(C);
+    const uint32_t S = ug.S;
+    const uint64_t nchunk = (n + C - 1) / C;
+    const uint64_t M = a.ctl->n_out, E = a.ctl->n_exc;
+    const Layout L0 = make_layout(a.radius, nchunk, M, E, 0);
+    const uint64_t gw = ((uint64_t)vg.bid * blockDim.x + threadIdx.x) >> 5;
+    const uint64_t nwarps = ((uint64_t)vg.nb * blockDim.x) >> 5;
+    bool cap_err = false;
+    for (uint64_t u = gw; u < nunits; u += nwarps) {
+        const uint64_t ubase = u * ug.U;
+        const uint64_t ulen = n - ubase < ug.U ? n - ubase : ug.U;
+        const uint32_t rounds = ug.multi ? (uint32_t)((ulen + kRound - 1) / kRound) : 1u;
+        const ulonglong2 off = a.unit_off[u];
+        uint64_t orun = off.y & 0xFFFFFFFFull, erun = off.y >> 32;
+        const bool unit_exc = E != 0 && a.unit_exc[u] != 0;
+        for (uint32_t r = 0; r < rounds; r++) {
+            const uint64_t r0 = ubase + (uint64_t)r * 32 * S, s0 = r0 + (uint64_t)lane * S;
+            unsigned long long zlo = 0, zhi = 0;
+            if (s0 < n && GBSZ_CHECK(s0 + S <= (n + 127) / 128 * 128, a.ctl)) {
+                const uint32_t *zw = a.zbits + s0 / 32;
+                if (S == 128) {
+                    const uint4 q = *reinterpret_cast<const uint4 *>(zw);
+                    zlo = q.x | ((unsigned long long)q.y << 32);
+                    zhi = q.z | ((unsigned long long)q.w << 32);
+                } else {  // S = 64
+                    const uint2 q = *reinterpret_cast<const uint2 *>(zw);
+                    zlo = q.x | ((unsigned long long)q.y << 32);
                 }
-                if (dv.y) {
-                    const uint64_t e8 = L0.exc + 8 * ei++;
-                    if (e8 + 8 <= a.capacity) {
-                        put_u32(a.archive + e8, (uint32_t)idx);
-                        put_u32(a.archive + e8 + 4, __float_as_uint(a.x[idx]));
+                if (s0 + S > n) {  // the field's last lane
+                    const uint64_t k = n - s0;  // points of the lane, 1..S-1
+                    if (k < 64) {
+                        zlo &= (1ull << k) - 1;
+                        zhi = 0;
                     } else {
-                        cap_err = true;
+                        zhi &= (1ull << (k - 64)) - 1;
                     }
                 }
-            };
-            // four of the lane's outliers at a time: their residuals are
-            // loaded together, then written in index order
-            unsigned long long mlo = zlo, mhi = zhi;
-            while (mlo | mhi) {
+            }
+            const uint32_t nz = __popcll(zlo) + __popcll(zhi);
+            const uint32_t oinc = warp_incl_scan(nz), T = __shfl_sync(0xffffffffu, oinc, 31);
+            if (T > kOutWin) {
+                emit_outliers(a, L0, s0, zlo, zhi, unit_exc, orun, erun, cap_err);
+                continue;
+            }
+            uint32_t k = oinc - nz;
+            for (unsigned long long m = zlo; m; m &= m - 1) pos[k++] = (uint16_t)(lane * S + __ffsll(m) - 1);
+            for (unsigned long long m = zhi; m; m &= m - 1) pos[k++] = (uint16_t)(lane * S + 63 + __ffsll(m));
+            __syncwarp();
+            for (uint32_t k0 = 0; k0 < T; k0 += 128) {
                 uint64_t idx[4];
-                bool has[4];
-#pragma unroll
-                for (int k = 0; k < 4; k++) {
-                    has[k] = (mlo | mhi) != 0;
-                    uint32_t j = 0;
-                    if (mlo) {
-                        j = __ffsll(mlo) - 1;
-                        mlo &= mlo - 1;
-                    } else if (mhi) {
-                        j = 63 + __ffsll(mhi);
-                        mhi &= mhi - 1;
-                    }
-                    idx[k] = s0 + j;
-                }
                 int2 dv[4];
 #pragma unroll
-                for (int k = 0; k < 4; k++)
-                    dv[k] = has[k] && GBSZ_CHECK(idx[k] < n, a.ctl) ? a.dscr[idx[k]] : make_int2(0, 0);
+                for (int q = 0; q < 4; q++) {
+                    const uint32_t kk = k0 + 32 * q + lane;
+                    idx[q] = kk < T ? r0 + pos[kk] : 0;
+                    dv[q] = kk < T && GBSZ_CHECK(idx[q] < n, a.ctl) ? a.dscr[idx[q]] : make_int2(0, 0);
+                }
 #pragma unroll
-                for (int k = 0; k < 4; k++)
-                    if (has[k]) emit_outlier(idx[k], dv[k]);
+                for (int q = 0; q < 4; q++) {
+                    const uint32_t kk = k0 + 32 * q + lane;
+                    const bool valid = kk < T;
+                    if (valid) {
+                        const uint64_t o8 = L0.outl + 8 * (orun + kk);
+                        if (o8 + 8 <= a.capacity) {
+                            put_u32(a.archive + o8, (uint32_t)idx[q]);
+                            put_u32(a.archive + o8 + 4, (uint32_t)dv[q].x);
+                        } else {
+                            cap_err = true;
+                        }
+                    }
+                    if (unit_exc) {  // warp-uniform
+                        const bool ex = valid && dv[q].y != 0;
+                        const uint32_t b = __ballot_sync(0xffffffffu, ex);
+                        if (ex) {
+                            const uint64_t e8 = L0.exc + 8 * (erun + __popc(b & ((1u << lane) - 1)));
+                            if (e8 + 8 <= a.capacity) {
+                                put_u32(a.archive + e8, (uint32_t)idx[q]);
+                                put_u32(a.archive + e8 + 4, __float_as_uint(a.x[idx[q]]));
+                            } else {
+                                cap_err = true;
+                            }
+                        }
+                        erun += __popc(b);
+                    }
+                }
             }
-            o_run += __shfl_sync(0xffffffffu, oinc, 31);
-            e_run += __shfl_sync(0xffffffffu, einc, 31);
-            round_bits += rtot;
+            orun += T;
+            __syncwarp();  // the list is rewritten next round
         }
     }
     if (cap_err) atomicOr(&a.ctl->error, DERR_CAPACITY);
@@ -610,14 +777,16 @@ __device__ __forceinline__ const void *load_table(const EncodeArgs &a, uint32_t 
 constexpr uint32_t kCountSmemBins = 8192;
 constexpr uint32_t kPartWords = 16 * kPartStride;  // per warp, S <= 128
 
+template <bool ZB>
 __device__ __forceinline__ void count_dispatch(const EncodeArgs &a, uint64_t nunits, uint32_t *part, uint32_t *tab,
                                                bool w32, VGrid vg)
 {
-    if (a.nbins <= kCountSmemBins) count_units(a, nunits, CountSmem{tab}, part, vg);
-    else if (w32) count_units(a, nunits, CountGlobal<true>{Table<true>{a.cw32}}, part, vg);
-    else count_units(a, nunits, CountGlobal<false>{Table<false>{a.cw64}}, part, vg);
+    if (a.nbins <= kCountSmemBins) count_units<ZB>(a, nunits, CountSmem{tab}, part, vg);
+    else if (w32) count_units<ZB>(a, nunits, CountGlobal<true>{Table<true>{a.cw32}}, part, vg);
+    else count_units<ZB>(a, nunits, CountGlobal<false>{Table<false>{a.cw64}}, part, vg);
 }
 
+template <bool ZB>
 __device__ __forceinline__ void count_body(const EncodeArgs &a, uint64_t nunits, VGrid vg)
 {
     extern __shared__ uint32_t s_cnt[];
@@ -632,12 +801,12 @@ __device__ __forceinline__ void count_body(const EncodeArgs &a, uint64_t nunits,
         }
         __syncthreads();
     }
-    count_dispatch(a, nunits, part, tab, w32, vg);
+    count_dispatch<ZB>(a, nunits, part, tab, w32, vg);
 }
 
 __global__ void __launch_bounds__(kEncThreads, 4) k_encode_count(const __grid_constant__ EncodeArgs a, uint64_t nunits)
 {
-    count_body(a, nunits, vgrid_self());
+    count_body<true>(a, nunits, vgrid_self());
 }
 
 __device__ __forceinline__ void pack_body(const EncodeArgs &a, uint64_t nunits, uint32_t use_smem, VGrid vg)
@@ -667,13 +836,23 @@ __global__ void __launch_bounds__(kEncThreads, 3) k_encode_pack(const __grid_con
     pack_body(a, nunits, use_smem, vgrid_self());
 }
 
+// few registers and no shared memory: five blocks per SM keep many
+// residual loads in flight
+__global__ void __launch_bounds__(kEncThreads, 5) k_encode_outliers(const __grid_constant__ EncodeArgs a,
+                                                                    uint64_t nunits)
+{
+    __shared__ uint16_t s_pos[kWarps * kOutWin];
+    if (a.ctl->error & (DERR_EB | DERR_INTERNAL)) return;
+    outlier_units(a, nunits, s_pos + (threadIdx.x >> 5) * kOutWin, vgrid_self());
+}
+
 // grouped: the count / pack of every field of a batch in one launch
 __global__ void __launch_bounds__(kEncThreads, 4) k_encode_count_group(const EncodeItem *items, const uint32_t *first,
                                                                        uint32_t ni)
 {
     VGrid vg;
     const EncodeItem &e = items[group_item(first, ni, vg)];
-    count_body(e.a, e.nunits, vg);
+    count_body<false>(e.a, e.nunits, vg);  // batches write no bitmap
 }
 
 __global__ void __launch_bounds__(kEncThreads, 3) k_encode_pack_group(const EncodeItem *items, const uint32_t *first,
@@ -738,7 +917,10 @@ int launch_encode(const EncodeArgs &a, cudaStream_t st, int phase)
     if (phase == 1) return launch_scan(UnitScan{a.unit_tot, a.unit_off}, nunits, a.scan_part, a.ctl, st);
     const int grid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)a.num_sms * 3));
     k_encode_pack<<<grid, kEncThreads, (size_t)kWarps * kRound * 2 + tab, st>>>(a, nunits, use_smem);
-    return 1;
+    if (!a.zbits) return 1;
+    const int ogrid = (int)std::max<uint64_t>(1, std::min<uint64_t>(want, (uint64_t)a.num_sms * 5));
+    k_encode_outliers<<<ogrid, kEncThreads, 0, st>>>(a, nunits);
+    return 2;
 }
 
 void encode_plan(const EncodeArgs &a, EncodeItem *it, uint32_t blocks[2], size_t smem[2], uint64_t *scan_items)

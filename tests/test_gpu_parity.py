@@ -336,6 +336,46 @@ def test_lorenzo_order_nonfinite_and_exceptions(gb, ctx):
         check_decompress(gb, ctx, arc, nb, oa, x, 1e-4, ref.EB_REL)
 
 
+# 1D order-1 fields of 2^22 points and more: the dual-quant kernel leaves a
+# code-0 bitmap and a kernel of its own writes the outlier and exception
+# records (pack only packs).  Ragged tails, two and four bitmap words a lane
+# (chunk 64, chunk >= 128), units of four rounds (chunk 16384), and radius 2,
+# which makes most points outliers.
+ZB_CASES = [
+    ((1 << 22) + 12345, 1e-4, 512, 2048),
+    ((1 << 22) + 77, 1e-4, 512, 64),
+    ((1 << 22) + 3, 1e-5, 512, 16384),
+    (1 << 22, 1e-3, 2, 128),
+]
+
+
+@pytest.mark.parametrize("n,eb,R,C", ZB_CASES, ids=[f"walk{c[0]}-R{c[2]}-C{c[3]}" for c in ZB_CASES])
+def test_parity_outlier_kernel(gb, ctx, n, eb, R, C):
+    x = workloads.field_for("walk", (n,), seed=n % 1000 + R + C)
+    arc, nb, oa = compare_stages(gb, ctx, x, eb, ref.EB_REL, R, C)
+    assert ref.sections(oa)["m"] > 0
+    check_decompress(gb, ctx, arc, nb, oa, x, eb, ref.EB_REL)
+
+
+def test_outlier_kernel_exceptions_and_capacity(gb, ctx):
+    x = workloads.field_for("walk", ((1 << 22) + 999,), seed=23)
+    pos = np.random.default_rng(24).choice(x.size, 300, replace=False)
+    x[pos[:150]] = np.nan
+    x[pos[150:]] = np.inf
+    x[-1] = -np.inf  # the last point of the ragged tail
+    arc, nb, oa = compare_stages(gb, ctx, x, 1e-4, ref.EB_REL, 512, 2048)
+    s_ = ref.sections(oa)
+    assert s_["e"] >= 301 and s_["m"] > s_["e"]
+    check_decompress(gb, ctx, arc, nb, oa, x, 1e-4, ref.EB_REL)
+    # too small by one byte (the stream's end), and cut inside the outlier records
+    xt = torch.from_numpy(x).cuda()
+    p = gb.make_params([x.size], 1e-4, gb.EB_REL, 512, 2048)
+    for cap in (nb - 1, nb // 3):
+        small = torch.empty(cap, dtype=torch.uint8, device="cuda")
+        st, need = ctx.compress_status(xt, p, small)
+        assert st == gb.ERR_CAPACITY and need == nb, (cap, st, need)
+
+
 FOLD_CASES = [
     # 4D fields (QMCPACK-like), predicted as 3D over the folded two slowest axes
     ("sinus", (3, 5, 29, 31), 1e-4, 512, 256, 1),
