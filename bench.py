@@ -430,15 +430,15 @@ def workload_config(a, n, chunk):
 
 
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of each
-# single-kernel stage on the full 2^28-point walk, from one ncu capture, with a
-# digest of the sources the kernel was built from; a number is reported only
-# while those sources are unchanged.
+# stage's kernels (pack: pack + outliers) on the full 2^28-point walk, from one
+# ncu capture, with a digest of the sources the kernels were built from; a
+# number is reported only while those sources are unchanged.
 DRAM_TRAFFIC = {
-    "error_bound": (1081942528, ('k_quant.cu', 'common.cuh'), "7898479dc209a604"),
-    "dualquant_hist": (1751275520, ('k_quant.cu', 'common.cuh'), "7898479dc209a604"),
-    "encode_count": (545135104, ('k_encode.cu', 'common.cuh', 'scan.cuh'), "9cf2365a56d481ea"),
-    "encode_pack": (906545408, ('k_encode.cu', 'common.cuh', 'scan.cuh'), "9cf2365a56d481ea"),
-    "decode": (702106624, ('k_decode.cu', 'common.cuh', 'scan.cuh'), "68891e61ecea31b6"),
+    "error_bound": (1082052864, ('k_quant.cu', 'common.cuh'), "33a78258f3ef86d6"),
+    "dualquant_hist": (1751570688, ('k_quant.cu', 'common.cuh'), "33a78258f3ef86d6"),
+    "encode_count": (572903168, ('k_encode.cu', 'common.cuh', 'scan.cuh'), "0a904676a92bc64b"),
+    "encode_pack": (930744576, ('k_encode.cu', 'common.cuh', 'scan.cuh'), "0a904676a92bc64b"),
+    "decode": (702469120, ('k_decode.cu', 'common.cuh', 'scan.cuh'), "4204005d1a6fe388"),
 }
 TRAFFIC_CONFIG = (28, 1e-4, 512, 2048)  # log2 n, rel eb, radius, chunk of the capture
 
@@ -671,11 +671,16 @@ def main():
     w_words = int(np.frombuffer(arc[96:104].cpu().numpy().tobytes(), np.uint64)[0])
     f = m_out / n
     nc = (n + chunk - 1) // chunk
-    alg = {  # algorithmic bytes per launch of each single-kernel stage
+    # From 2^23 points the library's 1D order-1 path keeps a code-0 bitmap:
+    # the count kernel writes it (n/8 bytes) and the pack stage is pack plus
+    # k_encode_outliers, which reads it back with the residuals.
+    zb = n >= (1 << 23)
+    bm = n / 8.0 if zb else 0.0
+    alg = {  # algorithmic bytes per launch of each stage (one kernel, or pack + outliers)
         0: 4.0 * n,                                               # minmax: read the field
         1: 6.0 * n + 8.0 * m_out,                                 # dual-quant: field in, codes out, residuals
-        3: 2.0 * n + n / 32.0 + 4.0 * nc,                         # count: codes in; lane bits, chunk bits out
-        5: 2.0 * n + n / 32.0 + 16.0 * m_out + 4.0 * w_words,     # pack: codes, lane bits, residuals in; stream, outliers out
+        3: 2.0 * n + n / 32.0 + 4.0 * nc + bm,                    # count: codes in; lane bits, chunk bits (bitmap) out
+        5: 2.0 * n + n / 32.0 + 16.0 * m_out + 4.0 * w_words + bm,  # pack: codes, lane bits, residuals (bitmap) in; stream, records out
         8: 4.0 * w_words + 12.0 * nc + 2.0 * n,                   # decode: stream, bits, offsets in; codes out
     }
     dom = max(alg, key=lambda s: stage_ms[s])

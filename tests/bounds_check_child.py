@@ -46,9 +46,9 @@ def main():
         ("1d walk C2048", wf("walk", (300007,), 2), 1e-4, 512, 2048),
         ("1d walk C8192", wf("walk", (100003,), 3), 1e-4, 512, 8192),
         ("1d long codes R32768", wf("walk", (50000,), 4), 1e-6, 32768, 1024),
-        # from 2^22 points: code-0 bitmap and the separate outlier kernel
-        ("1d walk bitmap C64", wf("walk", ((1 << 22) + 77,), 41), 1e-4, 512, 64),
-        ("1d walk bitmap C16384", wf("walk", ((1 << 22) + 12345,), 42), 1e-4, 512, 16384),
+        # from 2^23 points: code-0 bitmap and the separate outlier kernel
+        ("1d walk bitmap C64", wf("walk", ((1 << 23) + 77,), 41), 1e-4, 512, 64),
+        ("1d walk bitmap C16384", wf("walk", ((1 << 23) + 12345,), 42), 1e-4, 512, 16384),
         ("2d grf", wf("grf", (181, 1037), 5), 1e-3, 512, 4096),
         ("2d grf R32768", wf("grf", (300, 410), 6), 1e-5, 32768, 256),
         ("3d lognormal", wf("lognormal", (37, 41, 67), 7), 1e-4, 512, 256),

@@ -336,16 +336,16 @@ def test_lorenzo_order_nonfinite_and_exceptions(gb, ctx):
         check_decompress(gb, ctx, arc, nb, oa, x, 1e-4, ref.EB_REL)
 
 
-# 1D order-1 fields of 2^22 points and more: the dual-quant kernel leaves a
+# 1D order-1 fields of 2^23 points and more: the dual-quant kernel leaves a
 # code-0 bitmap and a kernel of its own writes the outlier and exception
 # records (pack only packs).  Ragged tails, two and four bitmap words a lane
 # (chunk 64, chunk >= 128), units of four rounds (chunk 16384), and radius 2,
 # which makes most points outliers.
 ZB_CASES = [
-    ((1 << 22) + 12345, 1e-4, 512, 2048),
-    ((1 << 22) + 77, 1e-4, 512, 64),
-    ((1 << 22) + 3, 1e-5, 512, 16384),
-    (1 << 22, 1e-3, 2, 128),
+    ((1 << 23) + 12345, 1e-4, 512, 2048),
+    ((1 << 23) + 77, 1e-4, 512, 64),
+    ((1 << 23) + 3, 1e-5, 512, 16384),
+    (1 << 23, 1e-3, 2, 128),
 ]
 
 
@@ -358,7 +358,7 @@ def test_parity_outlier_kernel(gb, ctx, n, eb, R, C):
 
 
 def test_outlier_kernel_exceptions_and_capacity(gb, ctx):
-    x = workloads.field_for("walk", ((1 << 22) + 999,), seed=23)
+    x = workloads.field_for("walk", ((1 << 23) + 999,), seed=23)
     pos = np.random.default_rng(24).choice(x.size, 300, replace=False)
     x[pos[:150]] = np.nan
     x[pos[150:]] = np.inf
