@@ -55,7 +55,11 @@ __host__ __device__ inline Layout make_layout(uint32_t radius, uint64_t nchunk, 
 enum : uint32_t {
     DERR_CAPACITY = 1u, DERR_CORRUPT = 2u, DERR_TIMEOUT = 4u, DERR_EB = 8u, DERR_INTERNAL = 16u,
     DERR_RANGE = 32u,  // an input outside what the kernel supports (codebook: histogram total >= 2^32)
-    DERR_BOUNDS = 64u  // bounds-checking build: an index check failed
+    DERR_BOUNDS = 64u,  // bounds-checking build: an index check failed
+    // decompress planned from the header its context kept from the compress
+    // into the same buffer, and the archive's header is no longer that one
+    // (the host runs the call again from the archive's own header)
+    DERR_STALE = 128u
 };
 
 // Per-call device control block.  Zeroed by one memset at the start of each
@@ -366,6 +370,8 @@ __host__ __device__ constexpr uint32_t lorenzo_block_extent(uint32_t ndim)
 
 void launch_minmax_eb(const float *x, uint64_t n, Control *ctl, double eb, uint32_t mode,
                       int num_sms, cudaStream_t st);
+// sets DERR_STALE unless the kHeaderBytes at arc (4-byte aligned) equal expect
+void launch_header_check(const void *arc, const uint8_t *expect, Control *ctl, cudaStream_t st);
 int launch_dualquant(const QuantArgs &a, cudaStream_t st);  // returns kernels launched
 
 // grouped S0-S3 (items and block tables in device memory)

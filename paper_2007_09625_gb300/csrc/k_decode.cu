@@ -21,6 +21,7 @@
 
 #include <algorithm>
 #include <atomic>
+#include <cstring>
 
 namespace gbsz {
 
@@ -649,6 +650,29 @@ int launch_offsets_scan_group(const ScanItem<ChunkWords> *items, const uint32_t 
                               cudaStream_t st)
 {
     return launch_scan_group(items, first, ni, blocks, st);
+}
+
+namespace {
+struct HeaderWords {
+    uint32_t w[kHeaderBytes / 4];  // 32: one per lane
+};
+
+// one warp: the archive's header word by word against the copy the
+// decompression was planned from
+__global__ void k_header_check(const uint32_t *arc, const __grid_constant__ HeaderWords expect, Control *ctl)
+{
+    const uint32_t lane = threadIdx.x & 31;
+    const bool differs = arc[lane] != expect.w[lane];
+    if (__any_sync(0xffffffffu, differs) && lane == 0) atomicOr(&ctl->error, DERR_STALE);
+}
+}  // namespace
+
+void launch_header_check(const void *arc, const uint8_t *expect, Control *ctl, cudaStream_t st)
+{
+    static_assert(kHeaderBytes == 128, "one header word per lane");
+    HeaderWords h;
+    memcpy(h.w, expect, kHeaderBytes);
+    k_header_check<<<1, 32, 0, st>>>(static_cast<const uint32_t *>(arc), h, ctl);
 }
 
 }  // namespace gbsz

@@ -184,6 +184,45 @@ def test_capacity_error_reports_needed_size(gb, ctx):
     assert ctx.decompress_status(arc, nb, out) == gb.ERR_CAPACITY
 
 
+def test_decompress_of_own_archive_checks_the_cached_header(gb, ctx):
+    """A decompress of the buffer this context just compressed into plans from
+    the header that compress copied back, checked on the device before any
+    decoding.  An archive written into the buffer by other means is noticed
+    (on the host when the cached plan does not fit the call, else by the
+    device check) and decoded from its own header; a change that leaves the
+    header alone gives exactly what a decompress reading the header gives."""
+    xa = workloads.field_for("walk", (300007,), seed=31)
+    xb = workloads.field_for("sinus", (50, 60), seed=32)
+    ta, tb = torch.from_numpy(xa).cuda(), torch.from_numpy(xb).cuda()
+    arc_b, nb_b = ctx.compress(tb, 1e-4)
+    b_bytes = arc_b[:nb_b].clone()
+    yb = ref.decompress(ref.compress(xb, 1e-4, ref.EB_REL, 512, gb.auto_chunk(list(xb.shape)[::-1])))
+    buf, nba = ctx.compress(ta, 1e-4)
+    assert nb_b < nba
+    # the smaller archive B in A's buffer, output sized for B (host check)
+    buf[:nb_b].copy_(b_bytes)
+    out = torch.empty(xb.shape, dtype=torch.float32, device="cuda")
+    assert ctx.decompress_status(buf, nba, out) == gb.OK
+    assert np.array_equal(out.cpu().numpy().view(np.uint32), yb.view(np.uint32))
+    # again with an output large enough for A (the device check)
+    buf, nba = ctx.compress(ta, 1e-4, out=buf)
+    buf[:nb_b].copy_(b_bytes)
+    big = torch.empty(xa.size, dtype=torch.float32, device="cuda")
+    assert ctx.decompress_status(buf, nba, big) == gb.OK
+    assert np.array_equal(big[:xb.size].cpu().numpy().view(np.uint32), yb.ravel().view(np.uint32))
+    # a payload byte changed, header intact: the cached plan against a fresh read
+    buf, nba = ctx.compress(ta, 1e-4, out=buf)
+    buf[nba - 5] ^= 0x5A
+    y1 = torch.empty(xa.size, dtype=torch.float32, device="cuda")
+    s1 = ctx.decompress_status(buf, nba, y1)
+    ctx.compress(tb, 1e-4)  # the context's cached header now belongs to another buffer
+    y2 = torch.empty(xa.size, dtype=torch.float32, device="cuda")
+    s2 = ctx.decompress_status(buf, nba, y2)
+    assert s1 == s2
+    if s1 == gb.OK:
+        assert np.array_equal(y1.cpu().numpy().view(np.uint32), y2.cpu().numpy().view(np.uint32))
+
+
 def test_host_buffer_api(gb, ctx):
     x = workloads.field_for("sinus", (33, 45, 29), seed=12)
     a, nb = ctx.compress_host(x, 1e-4)
