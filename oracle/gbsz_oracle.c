@@ -74,9 +74,21 @@ static int par_deflate(const uint16_t *codes, uint64_t n, uint32_t chunk, const 
 /* archive layout (little-endian), written out independently of the CUDA side */
 
 #define A_MAGIC 0x5A534247u /* bytes 'G','B','S','Z' */
-#define A_VERSION 1u
+#define A_VERSION 2u
 #define A_HEADER 128u
 #define A_MAXLEN 45u /* deepest Huffman leaf possible when n < 2^32 */
+/* Chunk anchors (a section of this format, not of the paper): for a 1D field
+ * with one order-1 predictor and chunks of at least A_ANCHOR_CHUNK symbols,
+ * anchor[c] is the prequantized integer of the last point before chunk c
+ * (0 for c = 0), i.e. the value the reconstruction (Alg. 2) reaches there,
+ * modulo 2^32.  A decoder can then rebuild every chunk on its own; the
+ * oracle only checks them against its own cascade. */
+#define A_ANCHOR_CHUNK 1024u
+
+static int anchored(const gbsz_ref_params *p)
+{
+    return p->ndim == 1 && (p->lorenzo_order <= 1) && p->lorenzo_block == 0 && p->chunk >= A_ANCHOR_CHUNK;
+}
 
 static uint64_t align16(uint64_t v) { return (v + 15u) & ~(uint64_t)15u; }
 
@@ -941,14 +953,18 @@ int gbsz_ref_inflate(const uint32_t *stream, uint64_t words,
 /* ------------------------------------------------------------------------ */
 /* S8: reversed dual-quantization, reconstructed cascadingly (Algorithm 2)   */
 
-int gbsz_ref_reconstruct_ex(const uint16_t *codes, uint32_t ndim,
-                            const uint64_t dims[3], uint32_t radius,
-                            uint32_t lblock, uint32_t order,
-                            const uint32_t *out_idx,
-                            const int32_t *out_delta, uint64_t m,
-                            const uint32_t *exc_idx,
-                            const uint32_t *exc_raw, uint64_t e,
-                            float ebx2, float *xr)
+/* The cascade of Alg. 2; with anchors (na entries, chunk C), every anchor
+ * must equal the reconstructed integer of the point before its chunk (0 for
+ * the first chunk), else the archive is corrupt. */
+static int reconstruct_anchored(const uint16_t *codes, uint32_t ndim,
+                                const uint64_t dims[3], uint32_t radius,
+                                uint32_t lblock, uint32_t order,
+                                const uint32_t *out_idx,
+                                const int32_t *out_delta, uint64_t m,
+                                const uint32_t *exc_idx,
+                                const uint32_t *exc_raw, uint64_t e,
+                                float ebx2, float *xr,
+                                const uint32_t *anchors, uint64_t na, uint32_t chunk)
 {
     if (ndim < 1 || ndim > 3 || lblock > 1) return REF_ERR_INVALID_ARG;
     if (order < 1 || order > 3 || (lblock && order > 1)) return REF_ERR_INVALID_ARG;
@@ -982,6 +998,15 @@ int gbsz_ref_reconstruct_ex(const uint16_t *codes, uint32_t ndim,
             }
     if (j != m) { free(q); return REF_ERR_CORRUPT; }
 #endif
+    {
+        int bad = 0;
+#pragma omp parallel for reduction(| : bad)
+        for (int64_t c = 0; c < (int64_t)na; c++) {
+            const uint32_t want = c == 0 ? 0u : (uint32_t)q[(uint64_t)c * chunk - 1];
+            if (anchors[c] != want) bad = 1;
+        }
+        if (bad) { free(q); return REF_ERR_CORRUPT; }
+    }
 #pragma omp parallel for
     for (int64_t i = 0; i < (int64_t)n; i++) xr[i] = recon_value(q[i], ebx2);
     for (uint64_t t = 0; t < e; t++) {
@@ -990,6 +1015,19 @@ int gbsz_ref_reconstruct_ex(const uint16_t *codes, uint32_t ndim,
     }
     free(q);
     return REF_OK;
+}
+
+int gbsz_ref_reconstruct_ex(const uint16_t *codes, uint32_t ndim,
+                            const uint64_t dims[3], uint32_t radius,
+                            uint32_t lblock, uint32_t order,
+                            const uint32_t *out_idx,
+                            const int32_t *out_delta, uint64_t m,
+                            const uint32_t *exc_idx,
+                            const uint32_t *exc_raw, uint64_t e,
+                            float ebx2, float *xr)
+{
+    return reconstruct_anchored(codes, ndim, dims, radius, lblock, order, out_idx, out_delta, m, exc_idx,
+                                exc_raw, e, ebx2, xr, NULL, 0, 0);
 }
 
 int gbsz_ref_reconstruct(const uint16_t *codes, uint32_t ndim,
@@ -1023,7 +1061,7 @@ size_t gbsz_ref_compress_bound(const gbsz_ref_params *p)
     if (check_params(p, &n)) return 0;
     uint64_t nc = nchunks(n, p->chunk);
     uint64_t words_max = nc + (A_MAXLEN * n + 31) / 32;
-    return (size_t)(192 + 2ull * p->radius + 8 * nc + 16 * n + 4 * words_max);
+    return (size_t)(208 + 2ull * p->radius + 12 * nc + 16 * n + 4 * words_max);
 }
 
 int gbsz_ref_compress(const float *x, const gbsz_ref_params *p, void *archive,
@@ -1069,9 +1107,11 @@ int gbsz_ref_compress(const float *x, const gbsz_ref_params *p, void *archive,
     st = gbsz_ref_deflate(codes, n, C, len, code, bits, stream, scap, &w);
     if (st) goto done;
     {
+        const uint64_t na = anchored(p) ? nc : 0;
         uint64_t off_len = A_HEADER;
         uint64_t off_bits = align16(off_len + nbins);
-        uint64_t off_out = align16(off_bits + 4 * nc);
+        uint64_t off_anc = align16(off_bits + 4 * nc);
+        uint64_t off_out = align16(off_anc + 4 * na);
         uint64_t off_exc = off_out + 8 * m;
         uint64_t off_str = align16(off_exc + 8 * e);
         uint64_t total = off_str + 4 * w;
@@ -1106,6 +1146,13 @@ int gbsz_ref_compress(const float *x, const gbsz_ref_params *p, void *archive,
         memcpy(a + off_len, len, nbins);
 #pragma omp parallel for
         for (int64_t c = 0; c < (int64_t)nc; c++) put_u32(a, off_bits + 4 * c, bits[c]);
+        /* anchors: the prequantized integer of the point before each chunk */
+#pragma omp parallel for
+        for (int64_t c = 1; c < (int64_t)na; c++) {
+            int32_t qa;
+            gbsz_ref_prequant_one(x[(uint64_t)c * C - 1], sc, &qa);
+            put_u32(a, off_anc + 4 * c, (uint32_t)qa);
+        }
 #pragma omp parallel for
         for (int64_t t = 0; t < (int64_t)m; t++) {
             put_u32(a, off_out + 8 * t, oidx[t]);
@@ -1129,7 +1176,8 @@ typedef struct {
     uint64_t n, nc, m, e, w, total;
     float sc[3];
     uint32_t maxlen;
-    uint64_t off_len, off_bits, off_out, off_exc, off_str;
+    uint64_t off_len, off_bits, off_anc, off_out, off_exc, off_str;
+    uint64_t na; /* anchors: nc or 0 */
 } hdr_t;
 
 static int parse_header(const uint8_t *a, size_t bytes, hdr_t *h)
@@ -1170,7 +1218,9 @@ static int parse_header(const uint8_t *a, size_t bytes, hdr_t *h)
     if (h->w > h->nc + (A_MAXLEN * n + 31) / 32) return REF_ERR_CORRUPT;
     h->off_len = A_HEADER;
     h->off_bits = align16(h->off_len + 2ull * h->p.radius);
-    h->off_out = align16(h->off_bits + 4 * h->nc);
+    h->na = anchored(&h->p) ? h->nc : 0;
+    h->off_anc = align16(h->off_bits + 4 * h->nc);
+    h->off_out = align16(h->off_anc + 4 * h->na);
     h->off_exc = h->off_out + 8 * h->m;
     h->off_str = align16(h->off_exc + 8 * h->e);
     if (h->total != h->off_str + 4 * h->w || h->total > bytes) return REF_ERR_CORRUPT;
@@ -1208,7 +1258,8 @@ int gbsz_ref_decompress(const void *archive, size_t bytes, float *x,
     uint32_t *eidx = (uint32_t *)malloc(h.e * 4 + 4);
     uint32_t *eraw = (uint32_t *)malloc(h.e * 4 + 4);
     uint16_t *codes = (uint16_t *)malloc(h.n * 2 + 2);
-    if (!bits || !stream || !oidx || !odel || !eidx || !eraw || !codes) {
+    uint32_t *anc = (uint32_t *)malloc(h.na * 4 + 4);
+    if (!bits || !stream || !oidx || !odel || !eidx || !eraw || !codes || !anc) {
         st = REF_ERR_OOM;
         goto done;
     }
@@ -1236,15 +1287,16 @@ int gbsz_ref_decompress(const void *archive, size_t bytes, float *x,
         eidx[t] = get_u32(a, h.off_exc + 8 * t);
         eraw[t] = get_u32(a, h.off_exc + 8 * t + 4);
     }
+    for (uint64_t c = 0; c < h.na; c++) anc[c] = get_u32(a, h.off_anc + 4 * c);
     st = gbsz_ref_inflate(stream, h.w, bits, h.n, h.p.chunk, len, nbins, codes);
     if (st) goto done;
     {
         uint64_t dims[3];
         const uint32_t gnd = lorenzo_geometry(&h.p, dims);
-        st = gbsz_ref_reconstruct_ex(codes, gnd, dims, h.p.radius, h.p.lorenzo_block, h.p.lorenzo_order, oidx,
-                                     odel, h.m, eidx, eraw, h.e, h.sc[1], x);
+        st = reconstruct_anchored(codes, gnd, dims, h.p.radius, h.p.lorenzo_block, h.p.lorenzo_order, oidx,
+                                  odel, h.m, eidx, eraw, h.e, h.sc[1], x, anc, h.na, h.p.chunk);
     }
 done:
-    free(bits); free(stream); free(oidx); free(odel); free(eidx); free(eraw); free(codes);
+    free(bits); free(stream); free(oidx); free(odel); free(eidx); free(eraw); free(codes); free(anc);
     return st;
 }

@@ -144,7 +144,14 @@ int gbsz_ref_reconstruct_ex(const uint16_t *codes, uint32_t ndim,
                             const uint32_t *exc_raw, uint64_t e,
                             float ebx2, float *xr);
 
-/* Whole path: archive bytes and back. */
+/* Whole path: archive bytes and back.  Archive version 2: a 128-byte header,
+ * then 16-byte aligned sections len[2R] (u8), bits[nchunk] (u32), anchors
+ * (u32, nchunk entries for 1D fields with one order-1 predictor and chunks of
+ * at least 1024 symbols, else none: anchor[c] is the prequantized integer of
+ * the point before chunk c, 0 for c = 0), outliers[M] {u32 idx, i32 delta},
+ * exceptions[E] {u32 idx, u32 raw}, stream[W] (u32).  Decompression checks
+ * every anchor against the reconstructed integers (a mismatch is
+ * REF_ERR_CORRUPT). */
 size_t gbsz_ref_compress_bound(const gbsz_ref_params *p);
 int gbsz_ref_compress(const float *x, const gbsz_ref_params *p, void *archive,
                       size_t capacity, size_t *out_bytes);

@@ -260,6 +260,7 @@ def decompress_status(archive, capacity=None):
 
 # archive section helpers (the format, restated for the tests' field access)
 HEADER = 128
+ANCHOR_CHUNK = 1024
 
 
 def sections(archive):
@@ -270,17 +271,22 @@ def sections(archive):
     u64 = lambda o: int.from_bytes(b[o:o + 8], "little")
     R, nc, m, e, w = u32(68), u32(76), u64(80), u64(88), u64(96)
     al = lambda v: (v + 15) & ~15
+    # chunk anchors: 1D, one order-1 predictor, chunks of at least 1024 symbols
+    na = nc if (u32(8) == 1 and u32(120) <= 1 and u32(108) == 0 and u32(72) >= ANCHOR_CHUNK) else 0
     off_len = HEADER
     off_bits = al(off_len + 2 * R)
-    off_out = al(off_bits + 4 * nc)
+    off_anc = al(off_bits + 4 * nc)
+    off_out = al(off_anc + 4 * na)
     off_exc = off_out + 8 * m
     off_str = al(off_exc + 8 * e)
     d = dict(radius=R, nchunk=nc, m=m, e=e, words=w, maxlen=u32(104), chunk=u32(72), lblock=u32(108),
              total=u64(112), n=u64(40), order=u32(120), ndim=u32(8),
              sc=np.frombuffer(b[56:68], dtype=np.float32).copy(),
-             off_len=off_len, off_bits=off_bits, off_out=off_out, off_exc=off_exc, off_str=off_str)
+             off_len=off_len, off_bits=off_bits, off_anc=off_anc, off_out=off_out, off_exc=off_exc,
+             off_str=off_str, nanchor=na)
     d["len"] = a[off_len:off_len + 2 * R].copy()
     d["bits"] = np.frombuffer(b[off_bits:off_bits + 4 * nc], np.uint32).copy()
+    d["anchors"] = np.frombuffer(b[off_anc:off_anc + 4 * na], np.uint32).copy()
     o = np.frombuffer(b[off_out:off_out + 8 * m], np.uint32).reshape(-1, 2)
     d["out_idx"], d["out_delta"] = o[:, 0].copy(), o[:, 1].view(np.int32).copy()
     ex = np.frombuffer(b[off_exc:off_exc + 8 * e], np.uint32).reshape(-1, 2)

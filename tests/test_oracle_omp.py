@@ -13,6 +13,7 @@ from paper_2007_09625_gb300 import workloads
 CASES = [
     # (kind, shape, rel, radius, chunk, lblock, order)
     ("walk", (300007,), 1e-4, 512, 256, 0, 1),
+    ("walk", (300007,), 1e-4, 512, 2048, 0, 1),  # chunk anchors
     ("walk", (300007,), 1e-4, 512, 4096, 1, 1),
     ("walk", (100003,), 1e-3, 64, 128, 0, 2),
     ("walk", (100003,), 1e-3, 512, 1024, 0, 3),
@@ -61,10 +62,11 @@ def _status(lib, a, cap):
     return lib.gbsz_ref_decompress(a.ctypes.data_as(C.c_void_p), a.size, y.ctypes.data_as(C.c_void_p), cap)
 
 
-def test_omp_build_corrupt_archives_same_status():
+@pytest.mark.parametrize("chunk", [256, 1024])
+def test_omp_build_corrupt_archives_same_status(chunk):
     rng = np.random.default_rng(45)
     x = np.cumsum(rng.normal(0, 1, 20000)).astype(np.float32)
-    a = ref.compress(x, 1e-4, chunk=256)
+    a = ref.compress(x, 1e-4, chunk=chunk)
     s = ref.sections(a)
     st, om = ref.lib(), ref.lib(omp=True)
     cases = []
@@ -80,6 +82,10 @@ def test_omp_build_corrupt_archives_same_status():
         b = a.copy()
         idx = int(a[o:o + 4].view(np.uint32)[0])
         b[o:o + 4] = np.array([idx + 1 if idx + 1 < x.size else idx - 1], np.uint32).view(np.uint8)
+        cases.append(b)
+    for c in range(s["nanchor"]):  # every anchor off by one
+        b = a.copy()
+        b[s["off_anc"] + 4 * c:s["off_anc"] + 4 * c + 4] = (s["anchors"][c:c + 1] + np.uint32(1)).view(np.uint8)
         cases.append(b)
     for b in cases:
         assert _status(st, b, x.size) == _status(om, b, x.size)

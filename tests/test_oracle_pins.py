@@ -657,3 +657,73 @@ def test_4d_archive_is_the_folded_3d_archive():
     assert y.shape == x4.shape
     sc = ref.error_bound(x4, 1e-3, ref.EB_REL)
     assert np.all(np.abs(x4.astype(np.float64) - y) <= float(sc[0]))
+
+
+# ---------------------------------------------------------------------------
+# Chunk anchors (this format's section): 1D fields, one order-1 predictor,
+# chunks of at least 1024 symbols
+
+def _residuals(x, sc, R):
+    """Lorenzo residual of every point, from the dual-quant outputs: code - R,
+    or the outlier's residual for code 0."""
+    dq = ref.dualquant(x, sc, R)
+    d = dq["codes"].astype(np.int64) - R
+    d[dq["out_idx"]] = dq["out_delta"]
+    return d
+
+
+@pytest.mark.parametrize("n,chunk", [(20000, 1024), (65536, 4096), (9000, 65536), (70001, 2048)])
+def test_anchor_is_the_prefix_of_the_residuals(n, chunk):
+    """Order-1 1D Lorenzo residuals are first differences of the prequantized
+    integers, so the integer of the point before chunk c is the sum of every
+    residual before it (mod 2^32); the first chunk's anchor is 0.  The values
+    the oracle rebuilds there are fl(2eb * anchor), within eb of the input."""
+    rng = np.random.default_rng(n + chunk)
+    x = np.cumsum(rng.normal(0, 1e-2, n)).astype(np.float32)
+    x[rng.choice(n, n // 100, replace=False)] = rng.uniform(x.min(), x.max(), n // 100).astype(np.float32)
+    x[chunk - 1 if chunk < n else 0] = np.nan  # an exception right before a chunk
+    R = 512
+    a = ref.compress(x, 1e-4, ref.EB_REL, R, chunk)
+    s = ref.sections(a)
+    nc = (n + chunk - 1) // chunk
+    assert s["nanchor"] == nc and s["anchors"].size == nc
+    sc = ref.error_bound(x, 1e-4, ref.EB_REL)
+    pre = np.concatenate([[0], np.cumsum(_residuals(x, sc, R))]) % (1 << 32)
+    want = np.array([pre[c * chunk] for c in range(nc)], np.uint64)
+    assert np.array_equal(s["anchors"].astype(np.uint64), want)
+    assert s["anchors"][0] == 0
+    y = ref.decompress(a)
+    for c in range(1, nc):
+        p = c * chunk - 1
+        if np.isfinite(x[p]):
+            qf = np.float32(np.int32(np.uint32(s["anchors"][c])))
+            assert (np.float32(sc[1]) * qf).view(np.uint32) == y[p].view(np.uint32)
+            assert abs(float(x[p]) - float(y[p])) <= float(sc[0])
+        else:  # a non-finite value predicts as the integer 0
+            assert s["anchors"][c] == 0
+
+
+@pytest.mark.parametrize("shape,chunk,lblock,order", [((20000,), 512, 0, 1), ((20000,), 4096, 1, 1),
+                                                      ((20000,), 4096, 0, 2), ((100, 200), 4096, 0, 1),
+                                                      ((10, 20, 30), 2048, 0, 1)])
+def test_no_anchors_outside_their_case(shape, chunk, lblock, order):
+    # no section: the outliers follow the chunk table directly
+    rng = np.random.default_rng(chunk)
+    x = np.cumsum(rng.normal(0, 1, shape), axis=-1).astype(np.float32)
+    a = ref.compress(x, 1e-3, ref.EB_REL, 512, chunk, lblock=lblock, order=order)
+    s = ref.sections(a)
+    assert s["nanchor"] == 0 and s["off_out"] == ((s["off_bits"] + 4 * s["nchunk"] + 15) & ~15)
+    assert s["total"] == a.size
+
+
+def test_corrupt_anchor_is_detected():
+    rng = np.random.default_rng(11)
+    n, chunk = 30000, 1024
+    x = np.cumsum(rng.normal(0, 1e-2, n)).astype(np.float32)
+    a = ref.compress(x, 1e-4, ref.EB_REL, 512, chunk)
+    s = ref.sections(a)
+    assert ref.decompress_status(a) == ref.OK
+    for c in (0, 1, s["nchunk"] // 2, s["nchunk"] - 1):
+        b = a.copy()
+        b[s["off_anc"] + 4 * c] ^= np.uint8(4)
+        assert ref.decompress_status(b) == ref.ERR_CORRUPT, c
