@@ -434,11 +434,11 @@ def workload_config(a, n, chunk):
 # ncu capture, with a digest of the sources the kernels were built from; a
 # number is reported only while those sources are unchanged.
 DRAM_TRAFFIC = {
-    "error_bound": (1082052864, ('k_quant.cu', 'common.cuh'), "33a78258f3ef86d6"),
-    "dualquant_hist": (1751570688, ('k_quant.cu', 'common.cuh'), "33a78258f3ef86d6"),
-    "encode_count": (572903168, ('k_encode.cu', 'common.cuh', 'scan.cuh'), "0a904676a92bc64b"),
-    "encode_pack": (930744576, ('k_encode.cu', 'common.cuh', 'scan.cuh'), "0a904676a92bc64b"),
-    "decode": (702469120, ('k_decode.cu', 'common.cuh', 'scan.cuh'), "4204005d1a6fe388"),
+    "error_bound": (1079958528, ('k_quant.cu', 'common.cuh'), "46464c23b2bc0113"),
+    "dualquant_hist": (1750198869, ('k_quant.cu', 'common.cuh'), "46464c23b2bc0113"),
+    "encode_count": (572852651, ('k_encode.cu', 'common.cuh', 'scan.cuh'), "20d06f82e5e24a79"),
+    "encode_pack": (929902933, ('k_encode.cu', 'common.cuh', 'scan.cuh'), "20d06f82e5e24a79"),
+    "decode": (1353550080, ('k_decode.cu', 'common.cuh', 'scan.cuh'), "b3d57dfeab3e622a"),
 }
 TRAFFIC_CONFIG = (28, 1e-4, 512, 2048)  # log2 n, rel eb, radius, chunk of the capture
 
@@ -676,12 +676,22 @@ def main():
     # k_encode_outliers, which reads it back with the residuals.
     zb = n >= (1 << 23)
     bm = n / 8.0 if zb else 0.0
+    # Archives of 1D fields in chunks of >= 1024 symbols carry chunk anchors;
+    # with codes of at most 15 bits and more chunks than the warp decoder
+    # takes (32 per SM), the library's thread decoder writes the values
+    # itself (each chunk from its anchor): decode reads the stream, the chunk
+    # table, offsets, anchors, outlier starts and records and writes the
+    # field, and no separate reconstruction runs.
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    fused = chunk >= 1024 and maxlen <= 15 and nc > 32 * sms
     alg = {  # algorithmic bytes per launch of each stage (one kernel, or pack + outliers)
         0: 4.0 * n,                                               # minmax: read the field
         1: 6.0 * n + 8.0 * m_out,                                 # dual-quant: field in, codes out, residuals
         3: 2.0 * n + n / 32.0 + 4.0 * nc + bm,                    # count: codes in; lane bits, chunk bits (bitmap) out
         5: 2.0 * n + n / 32.0 + 16.0 * m_out + 4.0 * w_words + bm,  # pack: codes, lane bits, residuals (bitmap) in; stream, records out
-        8: 4.0 * w_words + 12.0 * nc + 2.0 * n,                   # decode: stream, bits, offsets in; codes out
+        # decode: stream, bits, offsets in; codes out -- or, fused, the
+        # anchors, outlier starts and records in and the values out
+        8: (4.0 * w_words + 20.0 * nc + 8.0 * m_out + 4.0 * n) if fused else (4.0 * w_words + 12.0 * nc + 2.0 * n),
     }
     dom = max(alg, key=lambda s: stage_ms[s])
     dom_ms = stage_ms[dom] / max(stage_calls[dom], 1)
@@ -691,16 +701,22 @@ def main():
                 "unit": "GB/s", "frac": achieved / hbm, "peak_kind": f"{peak_kind} (MEASURED_PEAKS hbm_gbs)",
                 "traffic": measured_traffic(stage_names[dom], (a.log2n, a.rel, a.radius, chunk)),
                 "alg_bytes_per_launch": alg[dom]}
-    # the whole compress+decompress step: 12 + 8f + 4/CR (compress, relative eb)
-    # plus 8 + 8f + 4/CR (decompress) bytes per point
-    step_bytes = n * (20.0 + 16.0 * f + 8.0 / cr)
+    # the whole compress+decompress step: 12 + 8f + 4/CR (compress, relative
+    # eb) plus, for decompress, 8 + 8f + 4/CR bytes per point with the codes
+    # written and read back, or 4 + 8f + 4/CR when the decoder writes the
+    # values itself
+    cbytes = n * (12.0 + 8.0 * f + 4.0 / cr)
+    dbytes = n * ((4.0 if fused else 8.0) + 8.0 * f + 4.0 / cr)
+    step_bytes = cbytes + dbytes
     pipe_gbs = step_bytes / (ms_step / 1e3) / 1e9
-    pipe = {"alg_bytes_per_step": step_bytes, "achieved_gbs": pipe_gbs, "peak": hbm, "frac": pipe_gbs / hbm}
-    # compress and decompress each against the same bytes (12 + 8f + 4/CR and 8 + 8f + 4/CR per point)
-    cbytes, dbytes = n * (12.0 + 8.0 * f + 4.0 / cr), n * (8.0 + 8.0 * f + 4.0 / cr)
+    pipe = {"alg_bytes_per_step": step_bytes, "achieved_gbs": pipe_gbs, "peak": hbm, "frac": pipe_gbs / hbm,
+            "decompress_fused": fused}
     if comp_ms and dec_ms:
         pipe["compress_frac"] = cbytes / (comp_ms / 1e3) / 1e9 / hbm
         pipe["decompress_frac"] = dbytes / (dec_ms / 1e3) / 1e9 / hbm
+        # against the two-kernel path's bytes (8 + 8f + 4/CR), for comparison
+        # with a decompress that writes the codes
+        pipe["decompress_frac_two_kernel_bytes"] = n * (8.0 + 8.0 * f + 4.0 / cr) / (dec_ms / 1e3) / 1e9 / hbm
     # every single-kernel stage against the same peak
     per_kernel = {}
     for st_i, by in alg.items():

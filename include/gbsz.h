@@ -12,6 +12,16 @@
  *   decompress : inflate [Sec. 3.3] -> reversed dual-quantization as a
  *                d-dimensional integer prefix sum [Alg. 2, Sec. 3.3]
  *
+ * Archive (version 2, little-endian): a 128-byte header, then 16-byte
+ * aligned sections -- code lengths (u8 per bin), bits per chunk (u32),
+ * chunk anchors, outliers {u32 index, i32 residual}, exceptions {u32 index,
+ * u32 raw float bits}, the bitstream (u32 words).  The anchors (this
+ * format's own section; the paper has none) exist for 1D fields with one
+ * order-1 predictor in chunks of at least 1024 symbols: one u32 per chunk,
+ * the prequantized integer of the point before it (0 for the first), which
+ * lets the decoder rebuild each chunk on its own.  Decompression checks
+ * every anchor against the integers it reconstructs.
+ *
  * Conventions shared by every entry point:
  *   - Pointers named d_* are CUDA device pointers on the context's device;
  *     h_* are host pointers.  The caller owns every buffer it passes; the
@@ -121,9 +131,14 @@ void gbsz_destroy(gbsz_ctx *ctx);
  *     Lorenzo under 2^30 points it also reconstructs the values (S8) in the
  *     same kernel.  Chunks of more than 4096 symbols always take the thread
  *     decoder, and so do 1D order-1 fields of 2^30 points or more.
+ *     With an anchored 1D archive (see the archive format above) whose codes
+ *     fit the complete table (at most 15 bits), the thread decoder writes
+ *     the values itself, each chunk from its anchor.
  *     0 (default) = warp for fields of at most 32 chunks per SM in chunks
- *     of at least 1024 symbols, else thread; 1 = thread always; 2 = warp wherever it applies.  The results
- *     and statuses are the same either way. */
+ *     of at least 1024 symbols, else thread; 1 = thread always; 2 = warp
+ *     wherever it applies; 3 = thread always, writing the codes for a
+ *     separate reconstruction pass even where the anchors allow the fused
+ *     one.  The results and statuses are the same either way. */
 #define GBSZ_OPT_DECODER 4
 /*   GBSZ_OPT_LORENZO_SLAB  extent of a dual-quant tile along its swept
  *     dimension (S1+S2, Sec. 3.1): rows for 2D fields (tiles of 512 x slab
@@ -192,7 +207,8 @@ gbsz_status gbsz_compress(gbsz_ctx *ctx, const float *d_field,
 /* Decompresses the archive at d_archive (`bytes` bytes, device memory,
  * 16-byte aligned) into d_field (room for capacity_elems floats, 16-byte
  * aligned).  Stages: S7 decode, S8 outlier scatter + prefix-sum
- * reconstruction + exception patch.  Reads the 128-byte header to the host
+ * reconstruction + exception patch (for anchored 1D archives S8 runs inside
+ * the decoder: each chunk from its anchor).  Reads the 128-byte header to the host
  * first and synchronises at the end to report device-side checks.
  * Errors: INVALID_ARG, CORRUPT, CAPACITY (field larger than capacity),
  * OOM, CUDA, TIMEOUT. */

@@ -1,9 +1,14 @@
 // common.cuh -- definitions shared by the sm_103a kernels of the compressor.
 //
-// Archive format (version 1), little-endian, sections 16-byte aligned:
+// Archive format (version 2), little-endian, sections 16-byte aligned:
 //   [0,128)          header (field offsets below)
 //   len[2R]          Huffman code length per quant code (uint8)
 //   bits[nchunk]     deflated bits per chunk (uint32)
+//   anchors          1D fields with one order-1 predictor and chunks of at
+//                    least kAnchorChunk symbols: nchunk uint32, the
+//                    prequantized integer of the point before each chunk (0
+//                    for the first), so each chunk can be rebuilt on its own;
+//                    no entries otherwise
 //   outliers[M]      {uint32 idx, int32 delta}, ascending idx
 //   exceptions[E]    {uint32 idx, uint32 raw float bits}, ascending idx
 //   stream[W]        uint32 words; each chunk starts on a word, MSB first
@@ -17,7 +22,8 @@
 namespace gbsz {
 
 constexpr uint32_t kMagic = 0x5A534247u;  // "GBSZ"
-constexpr uint16_t kVersion = 1;
+constexpr uint16_t kVersion = 2;
+constexpr uint32_t kAnchorChunk = 1024;  // smallest chunk whose 1D archives carry anchors
 constexpr uint32_t kHeaderBytes = 128;
 // Deepest possible Huffman leaf for n < 2^32 symbols: a leaf at depth d needs
 // a total weight >= Fibonacci(d + 2), and Fibonacci(48) > 2^32.
@@ -35,16 +41,25 @@ enum : uint32_t {
 __host__ __device__ inline uint64_t align16(uint64_t v) { return (v + 15) & ~uint64_t(15); }
 
 struct Layout {
-    uint64_t len, bits, outl, exc, stream, total;
+    uint64_t len, bits, anch, outl, exc, stream, total;
+    uint64_t nanch;  // anchor entries (nchunk or 0)
 };
 
+// whether a field's archive carries chunk anchors (ndim as in the header; order 0 reads as 1)
+__host__ __device__ inline bool anchored(uint32_t ndim, uint32_t order, uint32_t lblock, uint32_t chunk)
+{
+    return ndim == 1 && order <= 1 && lblock == 0 && chunk >= kAnchorChunk;
+}
+
 __host__ __device__ inline Layout make_layout(uint32_t radius, uint64_t nchunk, uint64_t m,
-                                              uint64_t e, uint64_t w)
+                                              uint64_t e, uint64_t w, bool anchors)
 {
     Layout L;
     L.len = kHeaderBytes;
     L.bits = align16(L.len + 2ull * radius);
-    L.outl = align16(L.bits + 4 * nchunk);
+    L.anch = align16(L.bits + 4 * nchunk);
+    L.nanch = anchors ? nchunk : 0;
+    L.outl = align16(L.anch + 4 * L.nanch);
     L.exc = L.outl + 8 * m;
     L.stream = align16(L.exc + 8 * e);
     L.total = L.stream + 4 * w;
@@ -360,6 +375,11 @@ struct QuantArgs {
     Control *ctl;
     int num_sms;
     uint32_t slab;  // rows (2D) or planes (3D) each tile sweeps; 0 = the built-in rule
+    // 1D fields whose archive carries chunk anchors: the archive's anchor
+    // section (anchors[c] = prequantized integer of point c * chunk - 1,
+    // anchors[0] = 0), else nullptr
+    uint32_t *anchors;
+    uint32_t chunk;
 };
 __host__ __device__ inline uint64_t npoints(const QuantArgs &a) { return a.dims[0] * a.dims[1] * a.dims[2]; }
 // block extent of the per-block Lorenzo mode (Sec. 3.1.1): 32, 16x16, 8x8x8
@@ -530,10 +550,28 @@ struct DecodeArgs {
     uint32_t *tile_sums;  // 1D: residual sum per 4096-point tile (zeroed), else NULL
     uint16_t *codes;
     Control *ctl;
+    // 1D reconstruction inside the complete-table decoder (anchored archives,
+    // launch_decode phase 2): the values, fl(2eb * q) with q from the chunk's
+    // anchor; the outlier list and each chunk's first entry in it (ostart,
+    // nchunk + 1 entries)
+    float *out;
+    float ebx2;
+    const uint32_t *anchors;
+    const uint2 *outl;
+    const uint32_t *ostart;
+    uint64_t m;
 };
 constexpr uint32_t kRecon1DTile = 512;  // 1D reconstruction tile (points): one warp of the value kernel
-// phase 0: chunk word offsets (scan), 1: symbols; returns kernels launched
+// phase 0: chunk word offsets (scan), 1: symbols, 2: values (fused S7-S8 of
+// an anchored 1D archive with a complete table; d.out, d.anchors, d.outl,
+// d.ostart set); returns kernels launched
 int launch_decode(const DecodeArgs &a, cudaStream_t st, int phase);
+// each chunk's first outlier: ostart[c] = first entry of the index-ordered
+// list with idx >= c * chunk, c = 0 .. nchunk (ostart[nchunk] = m); a list
+// out of order or out of range marks the archive corrupt; returns kernels
+// launched
+int launch_outlier_chunk_starts(const uint2 *outl, uint64_t m, uint64_t n, uint32_t chunk, uint32_t nchunk,
+                                uint32_t *ostart, Control *ctl, cudaStream_t st);
 
 // S7 with one warp per chunk (k_decode_warp.cu).  fuse = 0: the chunk's codes
 // go to d.codes; 1: 1D order-1 fields only, S8 in the same pass: the values
@@ -550,6 +588,7 @@ struct WarpDecodeArgs {
     float *out;
     unsigned long long *look;
     uint32_t hold_chunk;  // test hook: this chunk's look-back word is never published (~0u: none)
+    const uint32_t *anchors;  // anchored archives (fused only): checked against every chunk's last integer
 };
 // kernels launched (one)
 int launch_decode_warp(const WarpDecodeArgs &w, bool fuse, cudaStream_t st);
@@ -624,6 +663,8 @@ struct ReconArgs {
     float *out;
     Control *ctl;
     int num_sms;
+    const uint32_t *anchors;  // anchored 1D archives: checked against the reconstructed integers
+    uint32_t chunk;
 };
 uint64_t recon_faces_entries(uint32_t ndim, const uint64_t dims[3]);
 void launch_reconstruct(const ReconArgs &a, cudaStream_t st, int *launches);

@@ -466,7 +466,8 @@ gbsz_status parse_header(const uint8_t *b, size_t bytes, Header *h)
     h->total = rd<uint64_t>(b, H_TOTAL);
     if (h->m > n || h->e > h->m || h->maxlen < 1 || h->maxlen > kMaxLen) return GBSZ_ERR_CORRUPT;
     if (h->w > h->nchunk + (kMaxLen * n + 31) / 32) return GBSZ_ERR_CORRUPT;
-    h->L = make_layout(p.radius, h->nchunk, h->m, h->e, h->w);
+    h->L = make_layout(p.radius, h->nchunk, h->m, h->e, h->w,
+                       anchored(p.ndim, p.lorenzo_order, p.lorenzo_block, p.chunk));
     if (h->total != h->L.total || h->total > bytes) return GBSZ_ERR_CORRUPT;
     return GBSZ_OK;
 }
@@ -480,7 +481,8 @@ gbsz_status check_compress(const float *d_field, const gbsz_params *pin, const v
     *p = *pin;
     if (p->chunk == 0) p->chunk = auto_chunk(*n);
     const uint64_t nchunk = (*n + p->chunk - 1) / p->chunk;
-    const Layout Lmin = make_layout(p->radius, nchunk, 0, 0, 0);
+    const Layout Lmin =
+        make_layout(p->radius, nchunk, 0, 0, 0, anchored(p->ndim, p->lorenzo_order, p->lorenzo_block, p->chunk));
     if (capacity < Lmin.stream) {
         *need = Lmin.stream;
         return GBSZ_ERR_CAPACITY;
@@ -613,6 +615,10 @@ gbsz_status enqueue_compress(gbsz_ctx *c, Slot *s, const float *d_field, const g
     q.ctl = s->ctl;
     q.num_sms = c->num_sms;
     q.slab = slab_for(c, p);
+    q.chunk = p.chunk;
+    if (anchored(p.ndim, order, p.lorenzo_block, p.chunk))  // capacity checked by check_compress
+        q.anchors = reinterpret_cast<uint32_t *>(static_cast<uint8_t *>(d_archive) +
+                                                 make_layout(p.radius, (n + p.chunk - 1) / p.chunk, 0, 0, 0, true).anch);
     stage_begin(c, st, &e0);
     const int nq = launch_dualquant(q, st);
     stage_end(c, st, 1, e0);
@@ -670,7 +676,10 @@ gbsz_status enqueue_compress(gbsz_ctx *c, Slot *s, const float *d_field, const g
 // walks its long chunk.  With more chunks, or short ones, the thread
 // decoders finish first (fewer instructions per symbol, and no
 // re-synchronisation or look-back per chunk).
-enum class WarpUse { Thread, Codes, Fused };
+// ThreadValues: an anchored 1D archive whose codes fit the complete table is
+// reconstructed inside the thread-per-chunk decoder itself (each chunk from
+// its anchor), so the codes never reach HBM and no separate value pass runs.
+enum class WarpUse { Thread, Codes, Fused, ThreadValues };
 
 WarpUse warp_use(const gbsz_ctx *c, const Header &h, uint32_t gnd, uint32_t order)
 {
@@ -679,12 +688,15 @@ WarpUse warp_use(const gbsz_ctx *c, const Header &h, uint32_t gnd, uint32_t orde
         const Tuned *t = find_tuned(c, h.p);
         if (t && t->chunk == h.p.chunk) dec = t->decoder;
     }
-    if (dec == 1 || h.p.chunk > kWarpMaxChunk) return WarpUse::Thread;
-    if (dec == 0 && (h.nchunk > 32ull * (uint64_t)c->num_sms || h.p.chunk < 1024)) return WarpUse::Thread;
+    const WarpUse thread = dec != 3 && h.L.nanch && fast_lut_bits(h.maxlen, 2 * h.p.radius) != 0
+                               ? WarpUse::ThreadValues
+                               : WarpUse::Thread;
+    if (dec == 1 || dec == 3 || h.p.chunk > kWarpMaxChunk) return thread;
+    if (dec == 0 && (h.nchunk > 32ull * (uint64_t)c->num_sms || h.p.chunk < 1024)) return thread;
     // 1D order-1 fields get their tile sums from the thread decoder, or are
     // reconstructed inside the warp decoder
     const bool line = gnd == 1 && !h.p.lorenzo_block && order == 1;
-    if (line) return h.n < (1ull << 30) ? WarpUse::Fused : WarpUse::Thread;
+    if (line) return h.n < (1ull << 30) ? WarpUse::Fused : thread;
     return WarpUse::Codes;
 }
 
@@ -700,8 +712,9 @@ gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void
     const uint32_t order = order_of(h.p);
     const uint64_t nfaces = recon_faces_entries(gnd, gd);
     const WarpUse wu = warp_use(c, h, gnd, order);
-    if (s == c->slots[0]) c->decoded_codes = wu != WarpUse::Fused;
-    const bool tile_sums = gnd == 1 && !h.p.lorenzo_block && order == 1 && wu != WarpUse::Fused;
+    const bool own_values = wu == WarpUse::Fused || wu == WarpUse::ThreadValues;  // S8 inside the decoder
+    if (s == c->slots[0]) c->decoded_codes = !own_values;
+    const bool tile_sums = gnd == 1 && !h.p.lorenzo_block && order == 1 && !own_values;
     if (!reserve_decompress(s, h)) return GBSZ_ERR_OOM;
     cudaMemsetAsync(s->ctl, 0, sizeof(Control), st);
     if (expect) {
@@ -753,17 +766,29 @@ gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void
     d.tile_sums = tile_sums ? s->faces.as<uint32_t>() : nullptr;
     d.codes = s->codes.as<uint16_t>();
     d.ctl = s->ctl;
+    if (wu == WarpUse::ThreadValues) {
+        d.out = d_field;
+        d.ebx2 = h.ebx2;
+        d.anchors = reinterpret_cast<const uint32_t *>(arc + h.L.anch);
+        d.outl = reinterpret_cast<const uint2 *>(arc + h.L.outl);
+        d.ostart = s->dscr.as<uint32_t>();  // the residual buffer is not otherwise used here
+        d.m = h.m;
+    }
     int ndec = 0;
     stage_begin(c, st, &e0);
     ndec += launch_decode(d, st, 0);
     if (wu == WarpUse::Fused)
         ndec += launch_outlier_prefix(reinterpret_cast<const uint2 *>(arc + h.L.outl), h.m, s->dscr.as<uint32_t>(),
                                       s->scan_part.as<uint32_t>(), s->ctl, st);
+    if (wu == WarpUse::ThreadValues)
+        ndec += launch_outlier_chunk_starts(d.outl, h.m, n, h.p.chunk, d.nchunk, s->dscr.as<uint32_t>(), s->ctl, st);
     stage_end(c, st, 7, e0);
     cudaStreamWaitEvent(st, s->join, 0);
     stage_begin(c, st, &e0);
     if (wu == WarpUse::Thread) {
         ndec += launch_decode(d, st, 1);
+    } else if (wu == WarpUse::ThreadValues) {
+        ndec += launch_decode(d, st, 2);
     } else {
         WarpDecodeArgs w{};
         w.d = d;
@@ -774,10 +799,11 @@ gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void
         w.out = d_field;
         w.look = s->codes.as<unsigned long long>();
         w.hold_chunk = c->hold_chunk;
+        if (h.L.nanch) w.anchors = reinterpret_cast<const uint32_t *>(arc + h.L.anch);
         ndec += launch_decode_warp(w, wu == WarpUse::Fused, st);
     }
     stage_end(c, st, 8, e0);
-    if (wu == WarpUse::Fused) {  // S8 ran inside the decoder; only the verbatim exceptions remain
+    if (own_values) {  // S8 ran inside the decoder; only the verbatim exceptions remain
         ReconArgs r{};
         r.archive = arc;
         r.off_exc = h.L.exc;
@@ -815,6 +841,10 @@ gbsz_status enqueue_decompress(gbsz_ctx *c, Slot *s, const Header &h, const void
     r.out = d_field;
     r.ctl = s->ctl;
     r.num_sms = c->num_sms;
+    if (h.L.nanch) {
+        r.anchors = reinterpret_cast<const uint32_t *>(arc + h.L.anch);
+        r.chunk = h.p.chunk;
+    }
     int nl = 0;
     stage_begin(c, st, &e0);
     launch_reconstruct(r, st, &nl);
@@ -1094,6 +1124,10 @@ gbsz_status compress_batch_grouped(gbsz_ctx *c, uint32_t count, const float *con
         q.ctl = f.ctl;
         q.num_sms = c->num_sms;
         q.slab = slab_for(c, p);
+        q.chunk = p.chunk;
+        if (anchored(p.ndim, 1, p.lorenzo_block, p.chunk))  // capacities checked per field beforehand
+            q.anchors = reinterpret_cast<uint32_t *>(
+                static_cast<uint8_t *>(d_archives[i]) + make_layout(p.radius, (n + p.chunk - 1) / p.chunk, 0, 0, 0, true).anch);
         size_t sm = 0;
         q_b[i] = dualquant_plan(q, qi[i].t, &qvar[i], &sm);
         q_smem = std::max(q_smem, sm);
@@ -1389,6 +1423,10 @@ gbsz_status decompress_batch_grouped(gbsz_ctx *c, uint32_t count, const std::vec
         r.out = d_fields[i];
         r.ctl = f.ctl;
         r.num_sms = c->num_sms;
+        if (h.L.nanch) {
+            r.anchors = reinterpret_cast<const uint32_t *>(arc + h.L.anch);
+            r.chunk = h.p.chunk;
+        }
     }
     PlanBuilder pb;
     const uint64_t o_zr = pb.put(zr.data(), zr.size());
@@ -1578,7 +1616,7 @@ gbsz_status gbsz_set_option(gbsz_ctx *c, int option, int64_t value)
         return GBSZ_OK;
     }
     if (option == GBSZ_OPT_DECODER) {
-        if (value < 0 || value > 2) return GBSZ_ERR_INVALID_ARG;
+        if (value < 0 || value > 3) return GBSZ_ERR_INVALID_ARG;
         c->decoder = (uint32_t)value;
         return GBSZ_OK;
     }
@@ -1713,7 +1751,7 @@ size_t gbsz_compress_bound(const gbsz_params *p)
     const uint32_t C = p->chunk ? p->chunk : auto_chunk(n);
     const uint64_t nc = (n + C - 1) / C;
     const uint64_t words_max = nc + (kMaxLen * n + 31) / 32;
-    return (size_t)(192 + 2ull * p->radius + 8 * nc + 16 * n + 4 * words_max);
+    return (size_t)(208 + 2ull * p->radius + 12 * nc + 16 * n + 4 * words_max);  // anchors included
 }
 
 gbsz_status gbsz_compress(gbsz_ctx *c, const float *d_field, const gbsz_params *pin, void *d_archive,

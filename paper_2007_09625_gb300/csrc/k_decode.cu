@@ -454,16 +454,13 @@ __device__ __forceinline__ void decode_chunk(const DecodeArgs &a, Ring<kRingFast
     }
 }
 
-template <bool MULTI_TILE>
-__device__ __forceinline__ void decode_fast_body(const DecodeArgs &a, VGrid vg)
+// Level 1 from the complete table: the code at the start of each byte if it
+// has at most 8 bits, and the code after it if that fits in the byte; built
+// once per block in the (not yet used) ring area, then copied per lane.
+__device__ __forceinline__ void build_level1(const DecodeArgs &a, uint32_t *s_dyn, uint2 *l1tab)
 {
-    extern __shared__ uint32_t s_dyn[];  // rings, level-1 table (lane-replicated)
-    uint2 *l1tab = reinterpret_cast<uint2 *>(s_dyn + kDecFastThreads * kRingFast);
-    const uint32_t B = a.fast_bits, shift = 32 - B;
+    const uint32_t B = a.fast_bits;
     const uint16_t *gft = static_cast<const uint16_t *>(a.lutf);
-    const uint16_t *ft = gft;
-    // level 1 from the complete table: the code at the start of each byte if
-    // it has at most 8 bits, and the code after it if that fits in the byte
     auto ft_at = [&](uint32_t byte) -> uint32_t {  // complete-table entry of an 8-bit prefix
         return B >= kL1Bits ? gft[byte << (B - kL1Bits)] : gft[byte >> (kL1Bits - B)];
     };
@@ -486,6 +483,16 @@ __device__ __forceinline__ void decode_fast_body(const DecodeArgs &a, VGrid vg)
     __syncthreads();
     for (uint32_t k = threadIdx.x; k < (kL1Copies << kL1Bits); k += blockDim.x) l1tab[k] = l1once[k / kL1Copies];
     __syncthreads();
+}
+
+template <bool MULTI_TILE>
+__device__ __forceinline__ void decode_fast_body(const DecodeArgs &a, VGrid vg)
+{
+    extern __shared__ uint32_t s_dyn[];  // rings, level-1 table (lane-replicated)
+    uint2 *l1tab = reinterpret_cast<uint2 *>(s_dyn + kDecFastThreads * kRingFast);
+    const uint32_t B = a.fast_bits, shift = 32 - B;
+    const uint16_t *ft = static_cast<const uint16_t *>(a.lutf);
+    build_level1(a, s_dyn, l1tab);
     if (a.ctl->error & DERR_CORRUPT) return;
     const uint32_t *stream = reinterpret_cast<const uint32_t *>(a.archive + a.off_stream);
     const uint32_t *bits_tab = reinterpret_cast<const uint32_t *>(a.archive + a.off_bits);
@@ -532,6 +539,219 @@ __global__ void __launch_bounds__(kDecFastThreads, 2) k_decode_fast(const __grid
     decode_fast_body<MULTI_TILE>(a, vgrid_self());
 }
 
+// 32-byte store of eight values (out 32-byte aligned), else two 16-byte stores
+__device__ __forceinline__ void store8(float *out, const float (&v)[8], bool al32)
+{
+    if (al32) {
+        asm volatile("st.global.v8.f32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8};" ::"l"(out), "f"(v[0]), "f"(v[1]),
+                     "f"(v[2]), "f"(v[3]), "f"(v[4]), "f"(v[5]), "f"(v[6]), "f"(v[7])
+                     : "memory");
+    } else {
+        reinterpret_cast<float4 *>(out)[0] = make_float4(v[0], v[1], v[2], v[3]);
+        reinterpret_cast<float4 *>(out)[1] = make_float4(v[4], v[5], v[6], v[7]);
+    }
+}
+
+// A lane's place in the index-ordered outlier list: its chunk's entries are
+// op .. oend-1; the next two are loaded one batch ahead of their use.
+struct OutlierCursor {
+    uint32_t op, oend;
+    uint2 o1, o2;
+    __device__ __forceinline__ uint2 at(const DecodeArgs &a, uint32_t i) const
+    {
+        return i < oend ? a.outl[i] : make_uint2(0xFFFFFFFFu, 0u);
+    }
+    __device__ __forceinline__ void fetch(const DecodeArgs &a)
+    {
+        o1 = at(a, op);
+        o2 = at(a, op + 1);
+    }
+};
+
+// Residuals of `cnt8` (<= 8) decoded symbols starting at point p0: code - R,
+// and for code 0 the residual of the lane's next outlier entry, whose index
+// must be the point's.  The patch goes through the thread's two staging
+// slots in shared memory (the code-0 positions are only known at run time);
+// the branch around it is warp-uniform.
+__device__ __forceinline__ void residuals8(const DecodeArgs &a, const uint32_t (&pw)[4], uint32_t cnt8, uint64_t p0,
+                                           uint32_t (&d)[8], OutlierCursor &oc, uint4 *stg0, uint4 *stg1, bool &bad,
+                                           unsigned long long &zeros)
+{
+    const uint32_t R = a.radius;
+    uint32_t zm = 0;
+#pragma unroll
+    for (int j = 0; j < 8; j++) {
+        const uint32_t sy = (pw[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu;
+        const bool live = (uint32_t)j < cnt8;
+        d[j] = live ? sy - R : 0u;
+        zm |= (live && sy == 0 ? 1u : 0u) << j;
+    }
+    if (__any_sync(0xffffffffu, zm != 0)) {
+        *stg0 = make_uint4(d[0], d[1], d[2], d[3]);
+        *stg1 = make_uint4(d[4], d[5], d[6], d[7]);
+        uint32_t mm = zm, t = 0;
+        while (mm) {
+            const uint32_t j = __ffs(mm) - 1;
+            mm &= mm - 1;
+            const uint2 e = t == 0 ? oc.o1 : t == 1 ? oc.o2 : oc.at(a, oc.op + t);
+            bad |= oc.op + t >= oc.oend || e.x != (uint32_t)(p0 + j);
+            reinterpret_cast<uint32_t *>(j < 4 ? stg0 : stg1)[j & 3] = e.y;
+            t++;
+        }
+        if (t) {
+            oc.op += t;
+            zeros += t;
+            oc.fetch(a);
+        }
+        const uint4 u0 = *stg0, u1 = *stg1;
+        d[0] = u0.x; d[1] = u0.y; d[2] = u0.z; d[3] = u0.w;
+        d[4] = u1.x; d[5] = u1.y; d[6] = u1.z; d[7] = u1.w;
+    }
+}
+
+// One chunk of an anchored 1D archive decoded straight to values: q is the
+// running prequantized integer (from the chunk's anchor), each value is
+// fl(2eb * fl(q)) as in the separate reconstruction, and the eight values of
+// a batch leave in one 32-byte store.
+template <bool GUARD>
+__device__ __forceinline__ void decode_chunk_values(const DecodeArgs &a, Ring<kRingFast> &rg, Window &w,
+                                                    const uint2 *l1, const uint16_t *ft, uint32_t shift, uint64_t s0,
+                                                    uint32_t cnt, uint32_t kend, uint32_t &q, OutlierCursor &oc,
+                                                    uint4 *stg0, uint4 *stg1, bool al32, bool &bad,
+                                                    unsigned long long &zeros, uint32_t &minlen)
+{
+    const float ebx2 = a.ebx2;
+    float *out = a.out + s0;
+    for (uint32_t k = 0; k < kend; k += kBatch) {
+        rg.refill(w.v);
+        uint32_t pw[kBatch / 2];
+        if (k + kBatch <= kend) {
+#pragma unroll
+            for (int j = 0; j < (int)kBatch; j += 2)
+                pw[j / 2] = decode_two(w, rg, l1, ft, shift, minlen, !GUARD || k + j < cnt, !GUARD || k + j + 1 < cnt);
+        } else {  // the warp's last, partial batch: one code at a time
+#pragma unroll
+            for (int j = 0; j < (int)kBatch; j++) {
+                const uint32_t sy = k + j < kend ? decode_two_level(w, rg, l1, ft, shift, minlen, k + j < cnt) : 0u;
+                pw[j / 2] = (j & 1) ? pw[j / 2] | (sy << 16) : sy;
+            }
+        }
+        const uint32_t cnt8 = !GUARD || k + kBatch <= cnt ? kBatch : (k < cnt ? cnt - k : 0u);
+        uint32_t d[8];
+        residuals8(a, pw, cnt8, s0 + k, d, oc, stg0, stg1, bad, zeros);
+        float v[8];
+#pragma unroll
+        for (int j = 0; j < 8; j++) {
+            q += d[j];
+            v[j] = recon_value((int32_t)q, ebx2);
+        }
+        if (cnt8 == kBatch) {
+            if (GBSZ_CHECK(s0 + k + kBatch <= a.n, a.ctl)) store8(out + k, v, al32);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 8; j++)
+                if ((uint32_t)j < cnt8 && GBSZ_CHECK(s0 + k + j < a.n, a.ctl)) out[k + j] = v[j];
+        }
+    }
+}
+
+// The complete-table decoder with the 1D reconstruction fused in (anchored
+// archives): every lane starts its chunk at the chunk's anchor and its first
+// outlier entry, and afterwards checks that it consumed exactly its bits and
+// its outlier entries and reached the next chunk's anchor.
+__device__ __forceinline__ void decode_fast_values_body(const DecodeArgs &a, VGrid vg)
+{
+    extern __shared__ uint32_t s_dyn[];  // rings, level-1 table (lane-replicated), staging slots
+    uint2 *l1tab = reinterpret_cast<uint2 *>(s_dyn + kDecFastThreads * kRingFast);
+    uint4 *s_stage = reinterpret_cast<uint4 *>(l1tab + (kL1Copies << kL1Bits));
+    build_level1(a, s_dyn, l1tab);
+    if (a.ctl->error & DERR_CORRUPT) return;
+    const uint32_t shift = 32 - a.fast_bits;
+    const uint16_t *ft = static_cast<const uint16_t *>(a.lutf);
+    const uint32_t *stream = reinterpret_cast<const uint32_t *>(a.archive + a.off_stream);
+    const uint32_t *bits_tab = reinterpret_cast<const uint32_t *>(a.archive + a.off_bits);
+    uint32_t *warp_ring = s_dyn + (threadIdx.x >> 5) * kRingFast * 32;
+    uint4 *stg0 = s_stage + threadIdx.x, *stg1 = s_stage + kDecFastThreads + threadIdx.x;
+    const uint32_t lane = threadIdx.x & 31;
+    const uint2 *l1 = l1tab + lane % kL1Copies;
+    const bool al32 = (reinterpret_cast<uintptr_t>(a.out) & 31) == 0;
+    unsigned long long zeros = 0;
+    bool bad = false;
+    const uint64_t stride = (uint64_t)vg.nb * blockDim.x;
+    for (uint64_t cw = (uint64_t)vg.bid * blockDim.x + threadIdx.x - lane; cw < a.nchunk; cw += stride) {
+        const uint64_t c = cw + lane;
+        const bool live = c < a.nchunk;
+        const uint32_t nbits = live ? bits_tab[c] : 0u;
+        const uint64_t coff = live ? a.chunk_off[c] : 0u;
+        const uint64_t s0 = live ? c * a.chunk : 0u;
+        const uint32_t cnt = live ? (uint32_t)(a.n - s0 < a.chunk ? a.n - s0 : a.chunk) : 0u;
+        uint32_t q = live ? a.anchors[c] : 0u;
+        OutlierCursor oc;
+        oc.op = live ? a.ostart[c] : 0u;
+        oc.oend = live ? a.ostart[c + 1] : 0u;
+        if (oc.oend > a.m || oc.op > oc.oend) {  // (the start kernel flags a bad list; never read past it)
+            bad = true;
+            oc.op = oc.oend = 0;
+        }
+        oc.fetch(a);
+        Ring<kRingFast> rg;
+        rg.start(warp_ring, lane, stream + coff, coff < a.words ? a.words - coff : 0);
+        Window w{0, 0, rg.at(0), rg.at(1), rg.at(2), rg.at(3)};
+        uint32_t minlen = 15;
+        if (__all_sync(0xffffffffu, cnt == a.chunk)) {
+            decode_chunk_values<false>(a, rg, w, l1, ft, shift, s0, cnt, cnt, q, oc, stg0, stg1, al32, bad, zeros,
+                                       minlen);
+        } else {
+            const uint32_t cmax = __reduce_max_sync(0xffffffffu, cnt);
+            decode_chunk_values<true>(a, rg, w, l1, ft, shift, s0, cnt, cmax, q, oc, stg0, stg1, al32, bad, zeros,
+                                      minlen);
+        }
+        cp_async_wait<0>();  // the ring is reused by the next chunk
+        if (live) {
+            bad |= minlen == 0 || (uint64_t)w.v * 32 + w.bo != nbits || oc.op != oc.oend;
+            if (c == 0) bad |= a.anchors[0] != 0u;
+            if (c + 1 < a.nchunk) bad |= a.anchors[c + 1] != q;  // the next chunk starts where this one ends
+        }
+        __syncwarp();
+    }
+    if (bad) atomicOr(&a.ctl->error, DERR_CORRUPT);
+    if (zeros) atomicAdd(&a.ctl->zeros, zeros);
+}
+
+__global__ void __launch_bounds__(kDecFastThreads, 2) k_decode_fast_values(const __grid_constant__ DecodeArgs a)
+{
+    decode_fast_values_body(a, vgrid_self());
+}
+
+// rings, level-1 copies and the two staging slots of every thread
+constexpr size_t kFastValuesSmem =
+    (size_t)kDecFastThreads * kRingFast * 4 + 8u * kL1Copies * (1u << kL1Bits) + 2u * kDecFastThreads * 16u;
+
+// each chunk's first outlier (see launch_outlier_chunk_starts)
+__global__ void k_outlier_chunk_starts(const uint2 *outl, uint64_t m, uint64_t n, uint32_t chunk, uint32_t nchunk,
+                                       uint32_t *ostart, Control *ctl)
+{
+    for (uint64_t t = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; t < m; t += (uint64_t)gridDim.x * blockDim.x) {
+        const uint32_t idx = outl[t].x;
+        bool ok = idx < n;
+        int64_t gprev = -1;
+        if (t > 0) {
+            const uint32_t pidx = outl[t - 1].x;
+            ok &= idx > pidx;
+            gprev = (int64_t)(pidx / chunk);
+        }
+        if (!ok) {
+            atomicOr(&ctl->error, DERR_CORRUPT);
+            continue;
+        }
+        const int64_t g = (int64_t)(idx / chunk);
+        for (int64_t u = gprev + 1; u <= g; u++)
+            if (GBSZ_CHECK((uint64_t)u <= nchunk, ctl)) ostart[u] = (uint32_t)t;
+        if (t + 1 == m)
+            for (uint64_t u = (uint64_t)g + 1; u <= nchunk; u++) ostart[u] = (uint32_t)m;
+    }
+}
+
 // grouped decoders: one launch per variant over every field of the variant
 template <bool FAST, bool MULTI_TILE>
 __global__ void __launch_bounds__(FAST ? kDecFastThreads : kDecThreads, FAST ? 2 : 1)
@@ -553,6 +773,10 @@ int launch_decode(const DecodeArgs &a, cudaStream_t st, int phase)
     int variant;
     size_t dyn;
     const unsigned g = decode_plan(a, &it, &variant, &dyn);
+    if (phase == 2) {  // the values straight from the complete-table decoder
+        k_decode_fast_values<<<g, kDecFastThreads, kFastValuesSmem, st>>>(a);
+        return 1;
+    }
     const bool multi = variant & 1;
     if (variant & 2) {
         if (multi) k_decode_fast<true><<<g, kDecFastThreads, dyn, st>>>(a);
@@ -580,6 +804,7 @@ void set_decode_smem(int dev)
     cudaFuncSetAttribute(k_decode<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     cudaFuncSetAttribute(k_decode_fast<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
     cudaFuncSetAttribute(k_decode_fast<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
+    cudaFuncSetAttribute(k_decode_fast_values, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kFastValuesSmem);
     cudaFuncSetAttribute(k_decode_group<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     cudaFuncSetAttribute(k_decode_group<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     cudaFuncSetAttribute(k_decode_group<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
@@ -650,6 +875,19 @@ int launch_offsets_scan_group(const ScanItem<ChunkWords> *items, const uint32_t 
                               cudaStream_t st)
 {
     return launch_scan_group(items, first, ni, blocks, st);
+}
+
+int launch_outlier_chunk_starts(const uint2 *outl, uint64_t m, uint64_t n, uint32_t chunk, uint32_t nchunk,
+                                uint32_t *ostart, Control *ctl, cudaStream_t st)
+{
+    if (m == 0) {  // every chunk starts (and ends) at entry 0
+        cudaMemsetAsync(ostart, 0, ((size_t)nchunk + 1) * 4, st);
+        return 0;
+    }
+    const uint64_t want = (m + 255) / 256;
+    k_outlier_chunk_starts<<<(unsigned)std::min<uint64_t>(want, 4096), 256, 0, st>>>(outl, m, n, chunk, nchunk,
+                                                                                      ostart, ctl);
+    return 1;
 }
 
 namespace {

@@ -534,6 +534,11 @@ __device__ __forceinline__ void decode_warp_body(const WarpDecodeArgs &wa)
             carry += __shfl_sync(0xffffffffu, si, 31);
             zb += __shfl_sync(0xffffffffu, zi, 31);
         }
+        // anchored archive: the chunk's last integer is the next chunk's anchor
+        if (wa.anchors && lane == 0) {
+            if (c + 1 < a.nchunk && wa.anchors[c + 1] != carry) bad = true;
+            if (c == 0 && wa.anchors[0] != 0u) bad = true;
+        }
         __syncwarp();
     }
     if (lane == 0 && zeros) atomicAdd(&a.ctl->zeros, zeros);

@@ -121,6 +121,7 @@ __device__ __forceinline__ void stage_round(const uint16_t *codes, uint64_t r0, 
 }
 
 __device__ __forceinline__ void put_u32(uint8_t *p, uint32_t v) { *reinterpret_cast<uint32_t *>(p) = v; }
+__host__ __device__ inline bool anchors_of(const EncodeArgs &a) { return anchored(a.ndim, a.order, a.lblock, a.chunk); }
 
 // archive header and the zero bytes between sections (last unit's warp)
 __device__ void write_header(const EncodeArgs &a, const Layout &L, uint64_t nchunk, uint64_t m, uint64_t e,
@@ -157,7 +158,8 @@ __device__ void write_header(const EncodeArgs &a, const Layout &L, uint64_t nchu
     h[H_DIM3 / 4] = (uint32_t)a.dims[3];  // below 2^32 as n is
     for (int i = 0; i < (int)(kHeaderBytes / 4); i++) put_u32(a.archive + 4 * i, h[i]);
     for (uint64_t b = L.len + a.nbins; b < L.bits; b++) a.archive[b] = 0;
-    for (uint64_t b = L.bits + 4 * nchunk; b < L.outl; b++) a.archive[b] = 0;
+    for (uint64_t b = L.bits + 4 * nchunk; b < L.anch; b++) a.archive[b] = 0;
+    for (uint64_t b = L.anch + 4 * L.nanch; b < L.outl; b++) a.archive[b] = 0;  // anchors: written by dual-quant
     for (uint64_t b = L.exc + 8 * e; b < L.stream; b++) a.archive[b] = 0;
 }
 
@@ -268,7 +270,7 @@ __device__ __forceinline__ void count_units(const EncodeArgs &a, uint64_t nunits
     const uint32_t segs = 32 / per;        // segments per 256-symbol step
     const uint32_t steps = S / 8;          // 256-symbol steps per round: 8 or 16
     const uint64_t nchunk = (n + C - 1) / C;
-    const Layout L0 = make_layout(a.radius, nchunk, a.ctl->n_out, a.ctl->n_exc, 0);
+    const Layout L0 = make_layout(a.radius, nchunk, a.ctl->n_out, a.ctl->n_exc, 0, anchors_of(a));
     const bool first_of_chunk = (lane & (ug.G - 1)) == 0;
     const uint32_t *myseg = part + (lane / segs) * kPartStride + (lane % segs) * per;
     uint8_t *zb8 = ZB ? reinterpret_cast<uint8_t *>(a.zbits) : nullptr;  // a byte per 8 points (coalesced stores)
@@ -464,7 +466,7 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
     const uint64_t nchunk = (n + C - 1) / C;
     const uint64_t M = a.ctl->n_out, E = a.ctl->n_exc;
     const bool any_exc = E != 0;
-    const Layout L0 = make_layout(a.radius, nchunk, M, E, 0);
+    const Layout L0 = make_layout(a.radius, nchunk, M, E, 0, anchors_of(a));
     uint32_t *stream = reinterpret_cast<uint32_t *>(a.archive + L0.stream);
     const uint64_t stream_cap = a.capacity > L0.stream ? (a.capacity - L0.stream) / 4 : 0;
     const bool first_of_chunk = (lane & (G - 1)) == 0;
@@ -483,7 +485,7 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
         if (u == nunits - 1 && lane == 0) {
             const ulonglong2 tot = a.unit_tot[u];
             const unsigned long long W = W0 + tot.x;
-            const Layout L = make_layout(a.radius, nchunk, M, E, W);
+            const Layout L = make_layout(a.radius, nchunk, M, E, W, anchors_of(a));
             if (O0 + (tot.y & 0xFFFFFFFFull) != M || E0 + (tot.y >> 32) != E) atomicOr(&a.ctl->error, DERR_INTERNAL);
             a.ctl->words = W;
             a.ctl->total = L.total;
@@ -663,7 +665,7 @@ __device__ void outlier_units(const EncodeArgs &a, uint64_t nunits, uint16_t *po
     const uint32_t S = ug.S;
     const uint64_t nchunk = (n + C - 1) / C;
     const uint64_t M = a.ctl->n_out, E = a.ctl->n_exc;
-    const Layout L0 = make_layout(a.radius, nchunk, M, E, 0);
+    const Layout L0 = make_layout(a.radius, nchunk, M, E, 0, anchors_of(a));
     const uint64_t gw = ((uint64_t)vg.bid * blockDim.x + threadIdx.x) >> 5;
     const uint64_t nwarps = ((uint64_t)vg.nb * blockDim.x) >> 5;
     bool cap_err = false;

@@ -373,6 +373,11 @@ __device__ __forceinline__ void dualquant_1d_body(const QuantArgs &a, uint32_t n
                 code[j] = point_1d<WIN>(h, a, e0 + j, q[j] - qprev, (excm >> j) & 1u, pk);
                 qprev = q[j];
             }
+            // chunks are multiples of the run: only a run's last point can precede a chunk
+            if (a.anchors && ((e0 + kQ1Per) & (a.chunk - 1)) == 0 && e0 + kQ1Per < n &&
+                GBSZ_CHECK((e0 + kQ1Per) / a.chunk < (n + a.chunk - 1) / a.chunk, a.ctl))
+                a.anchors[(e0 + kQ1Per) / a.chunk] = qprev;
+            if (a.anchors && e0 == 0) a.anchors[0] = 0u;
             uint4 *o = reinterpret_cast<uint4 *>(a.codes + e0);
             if (GBSZ_CHECK(e0 + kQ1Per <= n, a.ctl)) {
             o[0] = make_uint4(code[0] | (code[1] << 16), code[2] | (code[3] << 16), code[4] | (code[5] << 16),
@@ -387,7 +392,12 @@ __device__ __forceinline__ void dualquant_1d_body(const QuantArgs &a, uint32_t n
                 const uint32_t q = (uint32_t)prequant(v[j], sc, exc);
                 if (e0 + j < n) a.codes[e0 + j] = (uint16_t)point_1d<WIN>(h, a, e0 + j, q - qprev, exc, pk);
                 qprev = q;
+                const uint64_t nxt = (uint64_t)e0 + j + 1;
+                if (a.anchors && nxt < n && (nxt & (a.chunk - 1)) == 0 &&
+                    GBSZ_CHECK(nxt / a.chunk < ((uint64_t)n + a.chunk - 1) / a.chunk, a.ctl))
+                    a.anchors[nxt / a.chunk] = q;
             }
+            if (a.anchors && e0 == 0) a.anchors[0] = 0u;
         }
         unpack_central(h, pk);
         // the 16 points of a run lie in one encoder unit (units are 2^k >= 2048 points)

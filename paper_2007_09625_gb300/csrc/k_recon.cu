@@ -339,6 +339,13 @@ __device__ __forceinline__ void values_1d_body(const ReconArgs &a, const Geo &g,
             run += d[j];
             v[j] = recon_value((int32_t)run, ebx2);
         }
+        if (a.anchors) {
+            // anchored archive: the integer before each chunk is its anchor
+            // (chunks are multiples of 16 points, so only a run's last point
+            // can precede one)
+            if (s0 + 16 < n && ((s0 + 16) & (a.chunk - 1)) == 0 && a.anchors[(s0 + 16) / a.chunk] != run) bad = true;
+            if (s0 == 0 && a.anchors[0] != 0u) bad = true;
+        }
         if (s0 + 16 <= n) {
             float4 *o = reinterpret_cast<float4 *>(a.out + s0);
 #pragma unroll

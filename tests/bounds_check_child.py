@@ -13,7 +13,7 @@ from oracle import ref  # noqa: E402
 from paper_2007_09625_gb300 import gbsz, workloads  # noqa: E402
 
 
-def check_field(ctx, name, x, rel, R, C, lblock=0, order=1, decoders=(0, 1, 2)):
+def check_field(ctx, name, x, rel, R, C, lblock=0, order=1, decoders=(0, 1, 2, 3)):
     t = torch.from_numpy(np.ascontiguousarray(x)).cuda()
     st = None
     try:
@@ -49,6 +49,9 @@ def main():
         # from 2^23 points: code-0 bitmap and the separate outlier kernel
         ("1d walk bitmap C64", wf("walk", ((1 << 23) + 77,), 41), 1e-4, 512, 64),
         ("1d walk bitmap C16384", wf("walk", ((1 << 23) + 12345,), 42), 1e-4, 512, 16384),
+        # anchored archives decoded straight to values by the thread decoder
+        ("1d walk anchored C1024", wf("walk", ((1 << 23) + 4321,), 43), 1e-4, 512, 1024),
+        ("1d walk anchored R2", wf("walk", ((1 << 20) + 9,), 44), 1e-4, 2, 2048),
         ("2d grf", wf("grf", (181, 1037), 5), 1e-3, 512, 4096),
         ("2d grf R32768", wf("grf", (300, 410), 6), 1e-5, 32768, 256),
         ("3d lognormal", wf("lognormal", (37, 41, 67), 7), 1e-4, 512, 256),
@@ -84,22 +87,19 @@ def main():
     print(("ok" if ok else f"FAIL") + f" grouped batch {list(sts)} {list(dsts)}", flush=True)
     # corrupt archives are rejected as corrupt, never as an index failure
     x = wf("walk", (70001,), 40)
-    a = ref.compress(x, 1e-4, ref.EB_REL, 16, 256)
-    s = ref.sections(a)
-    rng = np.random.default_rng(41)
     bad_status = []
-    for k in range(40):
-        b = a.copy()
-        b[int(rng.integers(s["off_str"], a.size))] ^= np.uint8(1 << int(rng.integers(0, 8)))
-        if k % 4 == 0:  # and an outlier index past the field
-            o = s["off_out"] + 8 * (s["m"] - 1)
-            b[o:o + 4] = np.frombuffer(np.uint32(0xFFFFFFF0).tobytes(), np.uint8)
-        for dec in (0, 1, 2):
-            ctx.set_option(gbsz.OPT_DECODER, dec)
-            st = ctx.decompress_status(torch.from_numpy(b).cuda(), b.size, torch.empty(x.shape, device="cuda"))
-            torch.cuda.synchronize()
-            if st not in (gbsz.OK, gbsz.ERR_CORRUPT):
-                bad_status.append((k, dec, st))
+    for C in (256, 1024):  # and an anchored archive
+        a = ref.compress(x, 1e-4, ref.EB_REL, 16, C)
+        s = ref.sections(a)
+        rng = np.random.default_rng(41 + C)
+        for k in range(40):
+            b = a.copy()
+            b[int(rng.integers(s["off_anc"] if s["nanchor"] else s["off_str"], a.size))] ^= \
+                np.uint8(1 << int(rng.integers(0, 8)))
+            if k % 4 == 0:  # and an outlier index past the field
+                o = s["off_out"] + 8 * (s["m"] - 1)
+                b[o:o + 4] = np.frombuffer(np.uint32(0xFFFFFFF0).tobytes(), np.uint8)
+            corrupt_status(ctx, b, x, k, C, bad_status)
     ctx.set_option(gbsz.OPT_DECODER, 0)
     print(("ok" if not bad_status else f"FAIL") + f" corrupt archives {bad_status[:5]}", flush=True)
     # the no-allocation codebook
@@ -109,6 +109,16 @@ def main():
     want, wmx = ref.huffman_lengths(hist.astype(np.uint32))
     print(("ok" if np.array_equal(ln.cpu().numpy(), want) and mx == wmx else "FAIL") + " no-alloc codebook", flush=True)
     ctx.close()
+
+
+def corrupt_status(ctx, b, x, k, C, bad_status):
+    """Every decoder reports the corrupt archive as OK or corrupt."""
+    for dec in (0, 1, 2, 3):
+        ctx.set_option(gbsz.OPT_DECODER, dec)
+        st = ctx.decompress_status(torch.from_numpy(b).cuda(), b.size, torch.empty(x.shape, device="cuda"))
+        torch.cuda.synchronize()
+        if st not in (gbsz.OK, gbsz.ERR_CORRUPT):
+            bad_status.append((C, k, dec, st))
 
 
 if __name__ == "__main__":

@@ -43,7 +43,8 @@ def test_compress_bound_and_invalid_params(lib):
     p = gbsz.make_params([1 << 20], 1e-4, gbsz.EB_REL, 512, 4096)
     b = lib.gbsz_compress_bound(C.byref(p))
     n = 1 << 20
-    assert b == 192 + 1024 + 8 * 256 + 16 * n + 4 * (256 + (45 * n + 31) // 32)
+    # header and padding, lengths, chunk bits and anchors, 16 B a point, the longest stream
+    assert b == 208 + 1024 + 12 * 256 + 16 * n + 4 * (256 + (45 * n + 31) // 32)
     for bad in (dict(dims=[0]), dict(dims=[1 << 32]), dict(dims=[1 << 16, 1 << 16]),
                 dict(eb=0.0), dict(eb=float("nan")), dict(radius=1), dict(radius=32769),
                 dict(chunk=32), dict(chunk=100), dict(chunk=131072)):

@@ -38,7 +38,7 @@ def ctx(gb):
     c.close()
 
 
-@pytest.fixture(params=[0, 1, 2], ids=["default", "thread", "warp"])
+@pytest.fixture(params=[0, 1, 2, 3], ids=["default", "thread", "warp", "thread-codes"])
 def decoder(request):
     return request.param
 
@@ -84,6 +84,11 @@ def targeted(a):
     ln[ln > 0] += 1
     out["lengths_plus_one"] = b
     out["truncated"] = a[:-16].copy()
+    for c in sorted({0, s["nanchor"] // 2, s["nanchor"] - 1}) if s["nanchor"] else ():
+        b = a.copy()  # a chunk anchor off by one
+        o = s["off_anc"] + 4 * c
+        b[o:o + 4] = (s["anchors"][c:c + 1] + np.uint32(1)).view(np.uint8)
+        out[f"anchor{c}+1"] = b
     return out
 
 
@@ -109,6 +114,8 @@ def test_stream_bit_flips_agree_with_oracle(gb, ctx, decoder, kind, shape, eb, m
     s = ref.sections(a)
     rng = np.random.default_rng(R + C)
     lo, hi = s["off_str"], a.size
+    if s["nanchor"]:  # the anchors too
+        lo = s["off_anc"]
     for _ in range(24):
         b = a.copy()
         pos = int(rng.integers(lo, hi))

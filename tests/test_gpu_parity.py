@@ -79,14 +79,15 @@ def decompress_with(gb, ctx, arc, nb, decoder):
 
 
 def check_decompress(gb, ctx, arc, nb, oa, x, eb, eb_mode):
-    """Every decoder (default, thread per chunk, warp per chunk) gives the
-    oracle's floats; those that leave decoded codes give the oracle's codes."""
+    """Every decoder (default, thread per chunk, warp per chunk, thread per
+    chunk with the codes written out) gives the oracle's floats; those that
+    leave decoded codes give the oracle's codes."""
     yo = ref.decompress(oa)
     s_ = ref.sections(oa)
     want_codes = ref.dualquant(fold3(x), ref.error_bound(x, eb, eb_mode), s_["radius"],
                                lblock=s_["lblock"], order=s_["order"])["codes"]
     codes_checked = 0
-    for decoder in (0, 1, 2):
+    for decoder in (0, 1, 2, 3):
         y = decompress_with(gb, ctx, arc, nb, decoder)
         assert y.shape == x.shape
         if not np.array_equal(y.view(np.uint32), yo.view(np.uint32)):
@@ -127,6 +128,41 @@ def test_parity(gb, ctx, kind, shape, eb, mode, R, C):
     x = workloads.field_for(kind, shape, seed=sum(shape) + R + C)
     arc, nb, oa = compare_stages(gb, ctx, x, eb, mode, R, C)
     check_decompress(gb, ctx, arc, nb, oa, x, eb, mode)
+
+
+# 1D fields whose archives carry chunk anchors (chunks of >= 1024 symbols):
+# the thread-per-chunk decoder rebuilds each chunk from its anchor.  Several
+# thousand chunks (the default decoder is the thread one), ragged last chunks,
+# radius 2 (most points outliers), radius 32768 (codes too long for the
+# complete table: the general decoder and the separate value pass), chunk
+# 65536 (one partial chunk per warp), and non-finite values (exceptions),
+# some right before a chunk.
+ANCHORED = [
+    # n, eb, R, C
+    ((1 << 23) + 12345, 1e-4, 512, 1024),
+    ((1 << 22) + 777, 1e-4, 512, 2048),
+    ((1 << 22) + 5, 1e-4, 2, 1024),
+    (3_000_017, 1e-4, 512, 4096),
+    (1_000_003, 1e-6, 32768, 1024),
+    (300_001, 1e-4, 512, 65536),
+]
+
+
+@pytest.mark.parametrize("n,eb,R,C", ANCHORED, ids=[f"n{c[0]}-R{c[2]}-C{c[3]}" for c in ANCHORED])
+def test_parity_anchored_1d(gb, ctx, n, eb, R, C):
+    x = workloads.random_walk_1d(n, seed=n % 1000 + C)
+    rng = np.random.default_rng(n)
+    bad = rng.choice(n, 40, replace=False)
+    x[bad[:10]] = np.nan
+    x[bad[10:15]] = np.inf
+    x[bad[15:20]] = -np.inf
+    for c in (1, 2, (n - 1) // C):  # points right before chunks
+        if 0 < c * C - 1 < n:
+            x[c * C - 1] = np.nan if c % 2 else -np.inf
+    arc, nb, oa = compare_stages(gb, ctx, x, eb, ref.EB_REL, R, C)
+    s_ = ref.sections(oa)
+    assert s_["nanchor"] == (n + C - 1) // C and s_["e"] >= 20
+    check_decompress(gb, ctx, arc, nb, oa, x, eb, ref.EB_REL)
 
 
 EDGE = {
