@@ -43,6 +43,13 @@ __device__ __forceinline__ void cp_async4(uint32_t *dst, const uint32_t *src)
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
 }
+// the same with src_bytes (4 or 0) read and the rest of the word zero-filled:
+// no branch around words past the end of the stream
+__device__ __forceinline__ void cp_async4_fill(uint32_t *dst, const uint32_t *src, uint32_t src_bytes)
+{
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;" ::"r"(d), "l"(src), "r"(src_bytes) : "memory");
+}
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
@@ -69,9 +76,8 @@ struct Ring {
 #pragma unroll
         for (uint32_t i = 0; i < Q; i++) {
             const uint32_t v = qnext * Q + i;
-            uint32_t *d = &at(v);
-            if (v < avail) cp_async4(d, src + v);
-            else *d = 0u;
+            const bool in = v < avail;  // past the end: a zero word (src stays a valid address)
+            cp_async4_fill(&at(v), in ? src + v : src, in ? 4u : 0u);
         }
         cp_async_commit();
         qnext++;
@@ -908,6 +914,9 @@ int launch_outlier_chunk_starts(const uint2 *outl, uint64_t m, uint64_t n, uint3
         return 0;
     }
     const uint64_t want = (m + 255) / 256;
+    // (a version reading each record once and taking the previous index from
+    // the neighbouring lane, with one block per 256 records, measured slower:
+    // 20.7 -> 24.5 us for 4.3e6 records)
     k_outlier_chunk_starts<<<(unsigned)std::min<uint64_t>(want, 4096), 256, 0, st>>>(outl, m, n, chunk, nchunk,
                                                                                       ostart, ctl);
     return 1;

@@ -486,3 +486,27 @@ def test_codeword_width_option_keeps_bytes(gb, ctx, kind, shape, R, C):
     torch.cuda.synchronize()
     assert n64 == n32 and torch.equal(a64[:n64], a32)
     assert np.array_equal(a32.cpu().numpy(), ref.compress(x, 1e-4, ref.EB_REL, radius=R, chunk=C))
+
+
+def test_anchored_decode_into_16_byte_aligned_output(gb, ctx):
+    """The decoder that writes the values stores eight values with one 32-byte
+    store when the output is 32-byte aligned, else with two 16-byte stores;
+    both give the oracle's floats."""
+    n, C = (1 << 22) + 3, 1024
+    x = workloads.random_walk_1d(n, seed=77)
+    oa = ref.compress(x, 1e-4, ref.EB_REL, 512, C)
+    yo = ref.decompress(oa)
+    arc = torch.from_numpy(oa).cuda()
+    for dec in (1, 3):
+        ctx.set_option(gb.OPT_DECODER, dec)
+        try:
+            for off in (0, 4):  # floats: 0 and 16 bytes past a 256-byte aligned allocation
+                buf = torch.full((n + 8,), float("nan"), dtype=torch.float32, device="cuda")
+                out = buf[off:off + n]
+                assert ctx.decompress_status(arc, oa.size, out) == gb.OK
+                torch.cuda.synchronize()
+                got = buf.cpu().numpy()
+                assert np.array_equal(got[off:off + n].view(np.uint32), yo.view(np.uint32)), (dec, off)
+                assert np.isnan(got[:off]).all() and np.isnan(got[off + n:]).all(), (dec, off)
+        finally:
+            ctx.set_option(gb.OPT_DECODER, 0)
