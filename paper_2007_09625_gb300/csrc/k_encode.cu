@@ -451,10 +451,13 @@ __device__ __forceinline__ void emit_outliers(const EncodeArgs &a, const Layout 
 // warps cost 0.146 of 0.338 ms at 2^28 points with 1.6% outliers: pack runs
 // three blocks per SM for its shared-memory staging, too few warps to cover
 // the residuals' random loads.)
-// PAIR (longest code at most 16 bits): two codewords are joined into one of
-// at most 32 bits before they enter the accumulator, so each pair needs one
-// shift-in and one full-word test.
-template <bool CW32, bool PAIR>
+// PAIR (longest code at most 16 bits, or with LONG at most 24): two
+// codewords are joined into one of at most 32 bits before they enter the
+// accumulator, so each pair needs one shift-in and one full-word test; with
+// LONG a pair longer than 32 bits together takes two shift-ins instead.
+// (Longest code 18 bits, 512^3 lognormal field at rel eb 1e-4: pack 0.244 ms
+// with one codeword per shift-in, 0.240 ms in pairs.)
+template <bool CW32, bool PAIR, bool LONG = false>
 __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW32> &tab, uint4 *slot, VGrid vg)
 {
     const uint32_t lane = threadIdx.x & 31;
@@ -556,6 +559,23 @@ __device__ void pack_units(const EncodeArgs &a, uint64_t nunits, const Table<CW3
                         for (int k = 0; k < 4; k++) {
                             const uint2 e0 = tab.split(v[k] & 0xFFFFu), e1 = tab.split(v[k] >> 16);
                             const uint32_t len = e0.y + e1.y;
+                            if (LONG && len > 32) {
+                                // two codes of up to 24 bits that do not fit one word together
+                                // (rare): one shift-in each
+                                acc = (acc << e0.y) | e0.x;
+                                nacc += e0.y;
+                                bool full_w = nacc >= 32;
+                                nacc -= full_w ? 32u : 0u;
+                                if (full_w && ok) lout[nw32] = (uint32_t)(acc >> nacc);
+                                nw32 += full_w ? 1u : 0u;
+                                acc = (acc << e1.y) | e1.x;
+                                nacc += e1.y;
+                                full_w = nacc >= 32;
+                                nacc -= full_w ? 32u : 0u;
+                                if (full_w && ok) lout[nw32] = (uint32_t)(acc >> nacc);
+                                nw32 += full_w ? 1u : 0u;
+                                continue;
+                            }
                             acc = (acc << len) | ((e0.x << e1.y) | e1.x);
                             nacc += len;
                             const bool full_w = nacc >= 32;
@@ -820,11 +840,11 @@ __device__ __forceinline__ void pack_body(const EncodeArgs &a, uint64_t nunits, 
     const bool w32 = !a.cw64_only && a.ctl->maxlen <= 24;
     // each call sees where its table lives, so shared-memory tables are read
     // with shared loads
-    const bool pair = w32 && a.ctl->maxlen <= 16;
+    const bool pair = w32;
     if (use_smem) {
         load_table(a, 1, s_tab, w32, pair);
-        if (pair) pack_units<true, true>(a, nunits, Table<true>{s_tab}, slot, vg);
-        else if (w32) pack_units<true, false>(a, nunits, Table<true>{s_tab}, slot, vg);
+        if (pair && a.ctl->maxlen <= 16) pack_units<true, true>(a, nunits, Table<true>{s_tab}, slot, vg);
+        else if (pair) pack_units<true, true, true>(a, nunits, Table<true>{s_tab}, slot, vg);
         else pack_units<false, false>(a, nunits, Table<false>{s_tab}, slot, vg);
     } else {
         if (w32) pack_units<true, false>(a, nunits, Table<true>{a.cw32}, slot, vg);
