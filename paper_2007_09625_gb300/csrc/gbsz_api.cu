@@ -14,6 +14,8 @@
 #include "common.cuh"
 #include "scan.cuh"
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <array>
 #include <atomic>
@@ -1505,6 +1507,18 @@ gbsz_status decompress_batch_grouped(gbsz_ctx *c, uint32_t count, const std::vec
 
 }  // namespace
 
+namespace {
+// An NVTX range named after the entry point, open for the duration of the
+// call (header-only NVTX 3: a no-op unless a profiler such as Nsight
+// Systems has attached its NVTX library).
+struct ApiRange {
+    explicit ApiRange(const char *name) { nvtxRangePushA(name); }
+    ~ApiRange() { nvtxRangePop(); }
+    ApiRange(const ApiRange &) = delete;
+    ApiRange &operator=(const ApiRange &) = delete;
+};
+}  // namespace
+
 extern "C" {
 
 const char *gbsz_status_str(gbsz_status s)
@@ -1638,6 +1652,7 @@ uint32_t gbsz_auto_chunk(const gbsz_params *p)
 gbsz_status gbsz_autotune(gbsz_ctx *c, const float *d_field, const gbsz_params *p, gbsz_params *out, float *ms,
                           void *stream)
 {
+    const ApiRange nvtx_range("gbsz_autotune");
     uint64_t n;
     if (!c || !d_field || !p || !out || !valid_params(p, &n)) return GBSZ_ERR_INVALID_ARG;
     DevGuard g(c->device);
@@ -1757,6 +1772,7 @@ size_t gbsz_compress_bound(const gbsz_params *p)
 gbsz_status gbsz_compress(gbsz_ctx *c, const float *d_field, const gbsz_params *pin, void *d_archive,
                           size_t capacity, size_t *out_bytes, void *stream)
 {
+    const ApiRange nvtx_range("gbsz_compress");
     if (!c || !out_bytes) return GBSZ_ERR_INVALID_ARG;
     *out_bytes = 0;
     gbsz_params p;
@@ -1825,6 +1841,7 @@ gbsz_status gbsz_archive_info(const void *h_archive, size_t bytes, gbsz_params *
 gbsz_status gbsz_decompress(gbsz_ctx *c, const void *d_archive, size_t bytes, float *d_field,
                             uint64_t capacity_elems, void *stream)
 {
+    const ApiRange nvtx_range("gbsz_decompress");
     if (!c || !d_archive || !d_field) return GBSZ_ERR_INVALID_ARG;
     if ((reinterpret_cast<uintptr_t>(d_archive) & 15) || (reinterpret_cast<uintptr_t>(d_field) & 15))
         return GBSZ_ERR_INVALID_ARG;
@@ -1882,6 +1899,7 @@ gbsz_status gbsz_compress_batch(gbsz_ctx *c, uint32_t count, const float *const 
                                 const gbsz_params *params, void *const *d_archives, const size_t *capacities,
                                 size_t *out_bytes, gbsz_status *statuses, void *stream)
 {
+    const ApiRange nvtx_range("gbsz_compress_batch");
     if (!c || !d_fields || !params || !d_archives || !capacities || !out_bytes || !statuses)
         return GBSZ_ERR_INVALID_ARG;
     if (count == 0) return GBSZ_OK;
@@ -1963,6 +1981,7 @@ gbsz_status gbsz_decompress_batch(gbsz_ctx *c, uint32_t count, const void *const
                                   float *const *d_fields, const uint64_t *capacities, gbsz_status *statuses,
                                   void *stream)
 {
+    const ApiRange nvtx_range("gbsz_decompress_batch");
     if (!c || !d_archives || !bytes || !d_fields || !capacities || !statuses) return GBSZ_ERR_INVALID_ARG;
     if (count == 0) return GBSZ_OK;
     DevGuard g(c->device);
@@ -2047,6 +2066,7 @@ gbsz_status gbsz_decompress_batch(gbsz_ctx *c, uint32_t count, const void *const
 gbsz_status gbsz_compress_host(gbsz_ctx *c, const float *h_field, const gbsz_params *p, void *h_archive,
                                size_t capacity, size_t *out_bytes, void *stream)
 {
+    const ApiRange nvtx_range("gbsz_compress_host");
     uint64_t n;
     if (!c || !h_field || !h_archive || !out_bytes || !valid_params(p, &n)) return GBSZ_ERR_INVALID_ARG;
     DevGuard g(c->device);
@@ -2067,6 +2087,7 @@ gbsz_status gbsz_compress_host(gbsz_ctx *c, const float *h_field, const gbsz_par
 gbsz_status gbsz_decompress_host(gbsz_ctx *c, const void *h_archive, size_t bytes, float *h_field,
                                  uint64_t capacity_elems, void *stream)
 {
+    const ApiRange nvtx_range("gbsz_decompress_host");
     if (!c || !h_archive || !h_field) return GBSZ_ERR_INVALID_ARG;
     Header h;
     gbsz_status s = parse_header(static_cast<const uint8_t *>(h_archive), bytes, &h);
@@ -2088,6 +2109,7 @@ gbsz_status gbsz_decompress_host(gbsz_ctx *c, const void *h_archive, size_t byte
 gbsz_status gbsz_decompress_host_async(gbsz_ctx *c, const void *h_archive, size_t bytes, float *h_field,
                                        uint64_t capacity_elems, void *stream)
 {
+    const ApiRange nvtx_range("gbsz_decompress_host_async");
     if (!c || !h_archive || !h_field || c->apending) return GBSZ_ERR_INVALID_ARG;
     Header h;
     gbsz_status s = parse_header(static_cast<const uint8_t *>(h_archive), bytes, &h);
@@ -2122,6 +2144,7 @@ gbsz_status gbsz_decompress_host_async(gbsz_ctx *c, const void *h_archive, size_
 
 gbsz_status gbsz_async_wait(gbsz_ctx *c)
 {
+    const ApiRange nvtx_range("gbsz_async_wait");
     if (!c) return GBSZ_ERR_INVALID_ARG;
     if (!c->apending) return GBSZ_OK;
     DevGuard g(c->device);
