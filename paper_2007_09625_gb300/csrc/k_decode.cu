@@ -321,6 +321,25 @@ __device__ __forceinline__ uint32_t ld_ft_pred(bool p, const uint16_t *addr, uin
     return v;
 }
 
+// the same from a copy of the complete table in shared memory
+__device__ __forceinline__ uint32_t ld_ft_pred_smem(bool p, const uint16_t *addr, uint32_t keep)
+{
+    uint32_t v = keep;
+    const uint32_t a = (uint32_t)__cvta_generic_to_shared(addr);
+    asm volatile(
+        "{\n\t.reg .pred q;\n\t"
+        "setp.ne.u32 q, %1, 0;\n\t"
+        "@q ld.shared.u16 %0, [%2];\n\t}"
+        : "+r"(v)
+        : "r"((uint32_t)p), "r"(a));
+    return v;
+}
+template <bool FT_SMEM>
+__device__ __forceinline__ uint32_t ld_ft(bool p, const uint16_t *addr, uint32_t keep)
+{
+    return FT_SMEM ? ld_ft_pred_smem(p, addr, keep) : ld_ft_pred(p, addr, keep);
+}
+
 // Two codes per step.  The level-1 entry of the window's top byte holds the
 // first code and, when it fits in the same byte, the second, as 8 bytes:
 // x = sym1 | sym2 << 16 (the two symbols as they are stored), y = len1 |
@@ -344,7 +363,9 @@ __device__ __forceinline__ uint2 ld_shared_pred64(bool p, const void *addr)
     return v;
 }
 
-// Returns the two symbols packed as stored (sym1 | sym2 << 16).
+// Returns the two symbols packed as stored (sym1 | sym2 << 16).  FT_SMEM: ft
+// is a copy of the complete table in shared memory.
+template <bool FT_SMEM = false>
 __device__ __forceinline__ uint32_t decode_two(Window &w, const Ring<kRingFast> &rg, const uint2 *l1,
                                                const uint16_t *ft, uint32_t shift, uint32_t &minlen, bool act1,
                                                bool act2)
@@ -357,7 +378,7 @@ __device__ __forceinline__ uint32_t decode_two(Window &w, const Ring<kRingFast> 
     uint32_t l1n = e.y & 0xFFu, l2n = e.y >> 8;
     const bool long1 = l1n == 0;
     if (__any_sync(0xffffffffu, long1)) {
-        const uint32_t f = ld_ft_pred(long1, ft + (c0 >> shift), 0u);
+        const uint32_t f = ld_ft<FT_SMEM>(long1, ft + (c0 >> shift), 0u);
         if (long1) {
             l1n = f & 15u;
             sw = f >> 4;
@@ -371,7 +392,7 @@ __device__ __forceinline__ uint32_t decode_two(Window &w, const Ring<kRingFast> 
         uint32_t l2b = e2.y & 0xFFu, s2b = e2.x & 0xFFFFu;
         const bool long2 = need2 && l2b == 0;
         if (__any_sync(0xffffffffu, long2)) {
-            const uint32_t f = ld_ft_pred(long2, ft + (cur2 >> shift), 0u);
+            const uint32_t f = ld_ft<FT_SMEM>(long2, ft + (cur2 >> shift), 0u);
             if (long2) {
                 l2b = f & 15u;
                 s2b = f >> 4;
@@ -390,11 +411,12 @@ __device__ __forceinline__ uint32_t decode_two(Window &w, const Ring<kRingFast> 
 }
 
 // single code (the odd last symbol of a chunk)
+template <bool FT_SMEM = false>
 __device__ __forceinline__ uint32_t decode_two_level(Window &w, const Ring<kRingFast> &rg, const uint2 *l1,
                                                      const uint16_t *ft, uint32_t shift, uint32_t &minlen,
                                                      bool active)
 {
-    return decode_two(w, rg, l1, ft, shift, minlen, active, false) & 0xFFFFu;
+    return decode_two<FT_SMEM>(w, rg, l1, ft, shift, minlen, active, false) & 0xFFFFu;
 }
 
 // One chunk of cnt symbols; the warp runs kend >= cnt symbol steps (GUARD:
@@ -620,7 +642,7 @@ __device__ __forceinline__ void residuals8(const DecodeArgs &a, const uint32_t (
 // running prequantized integer (from the chunk's anchor), each value is
 // fl(2eb * fl(q)) as in the separate reconstruction, and the eight values of
 // a batch leave in one 32-byte store.
-template <bool GUARD>
+template <bool GUARD, bool FT_SMEM>
 __device__ __forceinline__ void decode_chunk_values(const DecodeArgs &a, Ring<kRingFast> &rg, Window &w,
                                                     const uint2 *l1, const uint16_t *ft, uint32_t shift, uint64_t s0,
                                                     uint32_t cnt, uint32_t kend, uint32_t &q, OutlierCursor &oc,
@@ -635,11 +657,13 @@ __device__ __forceinline__ void decode_chunk_values(const DecodeArgs &a, Ring<kR
         if (k + kBatch <= kend) {
 #pragma unroll
             for (int j = 0; j < (int)kBatch; j += 2)
-                pw[j / 2] = decode_two(w, rg, l1, ft, shift, minlen, !GUARD || k + j < cnt, !GUARD || k + j + 1 < cnt);
+                pw[j / 2] = decode_two<FT_SMEM>(w, rg, l1, ft, shift, minlen, !GUARD || k + j < cnt,
+                                                !GUARD || k + j + 1 < cnt);
         } else {  // the warp's last, partial batch: one code at a time
 #pragma unroll
             for (int j = 0; j < (int)kBatch; j++) {
-                const uint32_t sy = k + j < kend ? decode_two_level(w, rg, l1, ft, shift, minlen, k + j < cnt) : 0u;
+                const uint32_t sy =
+                    k + j < kend ? decode_two_level<FT_SMEM>(w, rg, l1, ft, shift, minlen, k + j < cnt) : 0u;
                 pw[j / 2] = (j & 1) ? pw[j / 2] | (sy << 16) : sy;
             }
         }
@@ -666,15 +690,27 @@ __device__ __forceinline__ void decode_chunk_values(const DecodeArgs &a, Ring<kR
 // archives): every lane starts its chunk at the chunk's anchor and its first
 // outlier entry, and afterwards checks that it consumed exactly its bits and
 // its outlier entries and reached the next chunk's anchor.
+template <bool FT_SMEM>
 __device__ __forceinline__ void decode_fast_values_body(const DecodeArgs &a, VGrid vg)
 {
-    extern __shared__ uint32_t s_dyn[];  // rings, level-1 table (lane-replicated), staging slots
+    // rings, level-1 table (lane-replicated), staging slots, and with FT_SMEM
+    // the complete table (2^fast_bits 16-bit entries)
+    extern __shared__ uint32_t s_dyn[];
     uint2 *l1tab = reinterpret_cast<uint2 *>(s_dyn + blockDim.x * kRingFast);
     uint4 *s_stage = reinterpret_cast<uint4 *>(l1tab + (kL1Copies << kL1Bits));
+    const uint16_t *ft = static_cast<const uint16_t *>(a.lutf);
+    if (FT_SMEM) {
+        uint4 *s_ft = s_stage + 2 * blockDim.x;
+        // 2^fast_bits entries of 2 bytes in 16-byte pieces (at least one: the
+        // table's buffer holds 2^15 entries)
+        const uint4 *g_ft = static_cast<const uint4 *>(a.lutf);
+        const uint32_t pieces = ((1u << a.fast_bits) + 7) >> 3;
+        for (uint32_t i = threadIdx.x; i < pieces; i += blockDim.x) s_ft[i] = g_ft[i];
+        ft = reinterpret_cast<const uint16_t *>(s_ft);  // visible after build_level1's barriers
+    }
     build_level1(a, s_dyn, l1tab);
     if (a.ctl->error & DERR_CORRUPT) return;
     const uint32_t shift = 32 - a.fast_bits;
-    const uint16_t *ft = static_cast<const uint16_t *>(a.lutf);
     const uint32_t *stream = reinterpret_cast<const uint32_t *>(a.archive + a.off_stream);
     const uint32_t *bits_tab = reinterpret_cast<const uint32_t *>(a.archive + a.off_bits);
     uint32_t *warp_ring = s_dyn + (threadIdx.x >> 5) * kRingFast * 32;
@@ -706,12 +742,12 @@ __device__ __forceinline__ void decode_fast_values_body(const DecodeArgs &a, VGr
         Window w{0, 0, rg.at(0), rg.at(1), rg.at(2), rg.at(3)};
         uint32_t minlen = 15;
         if (__all_sync(0xffffffffu, cnt == a.chunk)) {
-            decode_chunk_values<false>(a, rg, w, l1, ft, shift, s0, cnt, cnt, q, oc, stg0, stg1, al32, bad, zeros,
-                                       minlen);
+            decode_chunk_values<false, FT_SMEM>(a, rg, w, l1, ft, shift, s0, cnt, cnt, q, oc, stg0, stg1, al32, bad,
+                                                zeros, minlen);
         } else {
             const uint32_t cmax = __reduce_max_sync(0xffffffffu, cnt);
-            decode_chunk_values<true>(a, rg, w, l1, ft, shift, s0, cnt, cmax, q, oc, stg0, stg1, al32, bad, zeros,
-                                      minlen);
+            decode_chunk_values<true, FT_SMEM>(a, rg, w, l1, ft, shift, s0, cnt, cmax, q, oc, stg0, stg1, al32, bad,
+                                               zeros, minlen);
         }
         cp_async_wait<0>();  // the ring is reused by the next chunk
         if (live) {
@@ -729,15 +765,17 @@ __device__ __forceinline__ void decode_fast_values_body(const DecodeArgs &a, VGr
 // most 1024), so that every SM and every scheduler gets the same number of
 // chunks to within one warp, or, for more chunks than that, as the persistent
 // 512-thread blocks of k_decode_fast (see launch_decode).
+template <bool FT_SMEM>
 __global__ void __launch_bounds__(kFastValuesMaxThreads, 1) k_decode_fast_values(const __grid_constant__ DecodeArgs a)
 {
-    decode_fast_values_body(a, vgrid_self());
+    decode_fast_values_body<FT_SMEM>(a, vgrid_self());
 }
 
 // rings, level-1 copies and the two staging slots of every thread
-constexpr size_t fast_values_smem(uint32_t threads)
+constexpr size_t fast_values_smem(uint32_t threads, uint32_t ft_bits = 0)
 {
-    return (size_t)threads * kRingFast * 4 + 8u * kL1Copies * (1u << kL1Bits) + 2u * threads * 16u;
+    return (size_t)threads * kRingFast * 4 + 8u * kL1Copies * (1u << kL1Bits) + 2u * threads * 16u +
+           (ft_bits ? ((2u << ft_bits) + 15u) / 16u * 16u : 0u);
 }
 
 // each chunk's first outlier (see launch_outlier_chunk_starts)
@@ -798,10 +836,13 @@ int launch_decode(const DecodeArgs &a, cudaStream_t st, int phase)
         const uint64_t sms = (uint64_t)(a.num_sms ? a.num_sms : 1);
         const uint64_t per_sm = ((a.nchunk + 31) / 32 + sms - 1) / sms;  // warps of chunks per SM
         if (per_sm * 32 <= (uint64_t)kFastValuesMaxThreads) {
+            // one block per SM leaves room for the complete table in shared
+            // memory, so codes longer than 8 bits are looked up there
             const uint32_t t = (uint32_t)per_sm * 32;
-            k_decode_fast_values<<<(unsigned)((a.nchunk + t - 1) / t), t, fast_values_smem(t), st>>>(a);
+            k_decode_fast_values<true>
+                <<<(unsigned)((a.nchunk + t - 1) / t), t, fast_values_smem(t, a.fast_bits), st>>>(a);
         } else {
-            k_decode_fast_values<<<g, kDecFastThreads, fast_values_smem(kDecFastThreads), st>>>(a);
+            k_decode_fast_values<false><<<g, kDecFastThreads, fast_values_smem(kDecFastThreads), st>>>(a);
         }
         return 1;
     }
@@ -832,8 +873,10 @@ void set_decode_smem(int dev)
     cudaFuncSetAttribute(k_decode<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     cudaFuncSetAttribute(k_decode_fast<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
     cudaFuncSetAttribute(k_decode_fast<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
-    cudaFuncSetAttribute(k_decode_fast_values, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)fast_values_smem(kFastValuesMaxThreads));
+    cudaFuncSetAttribute(k_decode_fast_values<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fast_values_smem(kFastValuesMaxThreads, kFastLutMax));
+    cudaFuncSetAttribute(k_decode_fast_values<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                         (int)fast_values_smem(kDecFastThreads));
     cudaFuncSetAttribute(k_decode_group<false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     cudaFuncSetAttribute(k_decode_group<false, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, most);
     cudaFuncSetAttribute(k_decode_group<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, most_fast);
