@@ -376,17 +376,22 @@ __device__ __forceinline__ uint32_t decode_two(Window &w, const Ring<kRingFast> 
     const uint2 e = l1[(c0 >> (32 - kL1Bits)) * kL1Copies];
     uint32_t sw = e.x;
     uint32_t l1n = e.y & 0xFFu, l2n = e.y >> 8;
-    const bool long1 = l1n == 0;
-    if (__any_sync(0xffffffffu, long1)) {
-        const uint32_t f = ld_ft<FT_SMEM>(long1, ft + (c0 >> shift), 0u);
-        if (long1) {
-            l1n = f & 15u;
-            sw = f >> 4;
-            l2n = 0;
+    // One vote for both rare paths: an entry without a second code (l2n = 0)
+    // covers a first code over 8 bits too (its entry is all zero).  The
+    // lengths of an entry with both codes are those of real codewords, so a
+    // pattern missing from the codebook (length 0) can only come out of this
+    // branch, and the smallest length is tracked here alone.
+    if (__any_sync(0xffffffffu, l2n == 0)) {
+        const bool long1 = l1n == 0;
+        if (__any_sync(0xffffffffu, long1)) {
+            const uint32_t f = ld_ft<FT_SMEM>(long1, ft + (c0 >> shift), 0u);
+            if (long1) {
+                l1n = f & 15u;
+                sw = f >> 4;
+                l2n = 0;
+            }
         }
-    }
-    const bool need2 = l2n == 0;
-    if (__any_sync(0xffffffffu, need2)) {
+        const bool need2 = l2n == 0;
         const uint32_t cur2 = __funnelshift_l(c1, c0, l1n);  // the bits after the first code (l1n < 16)
         const uint2 e2 = ld_shared_pred64(need2, l1 + (cur2 >> (32 - kL1Bits)) * kL1Copies);
         uint32_t l2b = e2.y & 0xFFu, s2b = e2.x & 0xFFFFu;
@@ -402,10 +407,10 @@ __device__ __forceinline__ uint32_t decode_two(Window &w, const Ring<kRingFast> 
             l2n = l2b;
             sw = (sw & 0xFFFFu) | (s2b << 16);
         }
+        minlen = min(minlen, min(act1 ? l1n : 15u, act2 ? l2n : 15u));
     }
     l1n = act1 ? l1n : 0u;
     l2n = act2 ? l2n : 0u;
-    minlen = min(minlen, min(act1 ? l1n : 15u, act2 ? l2n : 15u));
     step(w, nxt, l1n + l2n);
     return sw;
 }
