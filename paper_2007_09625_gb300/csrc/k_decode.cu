@@ -38,13 +38,8 @@ constexpr int kDecFastThreads = 512;
 constexpr int kFastValuesMaxThreads = 1024;  // k_decode_fast_values: one block per SM of up to 32 warps
 constexpr uint32_t kBatch = 8;       // symbols between refill checks
 
-__device__ __forceinline__ void cp_async4(uint32_t *dst, const uint32_t *src)
-{
-    const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(d), "l"(src) : "memory");
-}
-// the same with src_bytes (4 or 0) read and the rest of the word zero-filled:
-// no branch around words past the end of the stream
+// 4-byte cp.async of which src_bytes (4 or 0) are read and the rest of the
+// word zero-filled: no branch around words past the end of the stream
 __device__ __forceinline__ void cp_async4_fill(uint32_t *dst, const uint32_t *src, uint32_t src_bytes)
 {
     const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
@@ -365,17 +360,20 @@ __device__ __forceinline__ uint2 ld_shared_pred64(bool p, const void *addr)
 
 // Returns the two symbols packed as stored (sym1 | sym2 << 16).  FT_SMEM: ft
 // is a copy of the complete table in shared memory.
-template <bool FT_SMEM = false>
+// ZF: the level-1 entries also flag code-0 symbols (bit 16: the first code,
+// bit 17: the second), and zf returns those two flags.
+template <bool FT_SMEM = false, bool ZF = false>
 __device__ __forceinline__ uint32_t decode_two(Window &w, const Ring<kRingFast> &rg, const uint2 *l1,
                                                const uint16_t *ft, uint32_t shift, uint32_t &minlen, bool act1,
-                                               bool act2)
+                                               bool act2, uint32_t *zf = nullptr)
 {
     const uint32_t nxt = rg.at(w.v + 4);
     const uint32_t c0 = __funnelshift_l(w.lo, w.hi, w.bo);
     const uint32_t c1 = __funnelshift_l(w.q0, w.lo, w.bo);
     const uint2 e = l1[(c0 >> (32 - kL1Bits)) * kL1Copies];
     uint32_t sw = e.x;
-    uint32_t l1n = e.y & 0xFFu, l2n = e.y >> 8;
+    uint32_t l1n = e.y & 0xFFu, l2n = ZF ? (e.y >> 8) & 0xFFu : e.y >> 8;
+    if (ZF) *zf = e.y >> 16;
     // One vote for both rare paths: an entry without a second code (l2n = 0)
     // covers a first code over 8 bits too (its entry is all zero).  The
     // lengths of an entry with both codes are those of real codewords, so a
@@ -408,6 +406,7 @@ __device__ __forceinline__ uint32_t decode_two(Window &w, const Ring<kRingFast> 
             sw = (sw & 0xFFFFu) | (s2b << 16);
         }
         minlen = min(minlen, min(act1 ? l1n : 15u, act2 ? l2n : 15u));
+        if (ZF) *zf = ((sw & 0xFFFFu) == 0 ? 1u : 0u) | ((sw >> 16) == 0 ? 2u : 0u);
     }
     l1n = act1 ? l1n : 0u;
     l2n = act2 ? l2n : 0u;
@@ -416,12 +415,13 @@ __device__ __forceinline__ uint32_t decode_two(Window &w, const Ring<kRingFast> 
 }
 
 // single code (the odd last symbol of a chunk)
-template <bool FT_SMEM = false>
+template <bool FT_SMEM = false, bool ZF = false>
 __device__ __forceinline__ uint32_t decode_two_level(Window &w, const Ring<kRingFast> &rg, const uint2 *l1,
                                                      const uint16_t *ft, uint32_t shift, uint32_t &minlen,
                                                      bool active)
 {
-    return decode_two<FT_SMEM>(w, rg, l1, ft, shift, minlen, active, false) & 0xFFFFu;
+    uint32_t zf;
+    return decode_two<FT_SMEM, ZF>(w, rg, l1, ft, shift, minlen, active, false, &zf) & 0xFFFFu;
 }
 
 // One chunk of cnt symbols; the warp runs kend >= cnt symbol steps (GUARD:
@@ -491,6 +491,7 @@ __device__ __forceinline__ void decode_chunk(const DecodeArgs &a, Ring<kRingFast
 // Level 1 from the complete table: the code at the start of each byte if it
 // has at most 8 bits, and the code after it if that fits in the byte; built
 // once per block in the (not yet used) ring area, then copied per lane.
+template <bool ZF = false>
 __device__ __forceinline__ void build_level1(const DecodeArgs &a, uint32_t *s_dyn, uint2 *l1tab)
 {
     const uint32_t B = a.fast_bits;
@@ -505,11 +506,14 @@ __device__ __forceinline__ void build_level1(const DecodeArgs &a, uint32_t *s_dy
         const uint32_t la = f & 15u;
         uint2 e = make_uint2(0u, 0u);
         if (la >= 1 && la <= kL1Bits) {
-            e = make_uint2(f >> 4, la);
+            e = make_uint2(f >> 4, la | (ZF && (f >> 4) == 0 ? 1u << 16 : 0u));
             if (la < kL1Bits) {
                 const uint32_t g2 = ft_at((i << la) & 0xFFu);
                 const uint32_t lb = g2 & 15u;
-                if (lb >= 1 && lb <= kL1Bits - la) e = make_uint2((f >> 4) | ((g2 >> 4) << 16), la | (lb << 8));
+                if (lb >= 1 && lb <= kL1Bits - la)
+                    e = make_uint2((f >> 4) | ((g2 >> 4) << 16),
+                                   la | (lb << 8) | (ZF && (f >> 4) == 0 ? 1u << 16 : 0u) |
+                                       (ZF && (g2 >> 4) == 0 ? 1u << 17 : 0u));
             }
         }
         l1once[i] = e;
@@ -608,17 +612,16 @@ struct OutlierCursor {
 // slots in shared memory (the code-0 positions are only known at run time);
 // the branch around it is warp-uniform.
 __device__ __forceinline__ void residuals8(const DecodeArgs &a, const uint32_t (&pw)[4], uint32_t cnt8, uint64_t p0,
-                                           uint32_t (&d)[8], OutlierCursor &oc, uint4 *stg0, uint4 *stg1, bool &bad,
-                                           unsigned long long &zeros)
+                                           uint32_t zflags, uint32_t (&d)[8], OutlierCursor &oc, uint4 *stg0,
+                                           uint4 *stg1, bool &bad, unsigned long long &zeros)
 {
     const uint32_t R = a.radius;
-    uint32_t zm = 0;
+    // zflags: bit j set for a code-0 symbol j (from the decode tables)
+    const uint32_t zm = zflags & (cnt8 >= 8 ? 0xFFu : (1u << cnt8) - 1u);
 #pragma unroll
     for (int j = 0; j < 8; j++) {
         const uint32_t sy = (pw[j >> 1] >> ((j & 1) * 16)) & 0xFFFFu;
-        const bool live = (uint32_t)j < cnt8;
-        d[j] = live ? sy - R : 0u;
-        zm |= (live && sy == 0 ? 1u : 0u) << j;
+        d[j] = (uint32_t)j < cnt8 ? sy - R : 0u;
     }
     if (__any_sync(0xffffffffu, zm != 0)) {
         *stg0 = make_uint4(d[0], d[1], d[2], d[3]);
@@ -658,23 +661,27 @@ __device__ __forceinline__ void decode_chunk_values(const DecodeArgs &a, Ring<kR
     float *out = a.out + s0;
     for (uint32_t k = 0; k < kend; k += kBatch) {
         rg.refill(w.v);
-        uint32_t pw[kBatch / 2];
+        uint32_t pw[kBatch / 2], zfl = 0;
         if (k + kBatch <= kend) {
 #pragma unroll
-            for (int j = 0; j < (int)kBatch; j += 2)
-                pw[j / 2] = decode_two<FT_SMEM>(w, rg, l1, ft, shift, minlen, !GUARD || k + j < cnt,
-                                                !GUARD || k + j + 1 < cnt);
+            for (int j = 0; j < (int)kBatch; j += 2) {
+                uint32_t zf;
+                pw[j / 2] = decode_two<FT_SMEM, true>(w, rg, l1, ft, shift, minlen, !GUARD || k + j < cnt,
+                                                      !GUARD || k + j + 1 < cnt, &zf);
+                zfl |= zf << j;
+            }
         } else {  // the warp's last, partial batch: one code at a time
 #pragma unroll
             for (int j = 0; j < (int)kBatch; j++) {
                 const uint32_t sy =
-                    k + j < kend ? decode_two_level<FT_SMEM>(w, rg, l1, ft, shift, minlen, k + j < cnt) : 0u;
+                    k + j < kend ? decode_two_level<FT_SMEM, true>(w, rg, l1, ft, shift, minlen, k + j < cnt) : 1u;
                 pw[j / 2] = (j & 1) ? pw[j / 2] | (sy << 16) : sy;
+                zfl |= (sy == 0 ? 1u : 0u) << j;
             }
         }
         const uint32_t cnt8 = !GUARD || k + kBatch <= cnt ? kBatch : (k < cnt ? cnt - k : 0u);
         uint32_t d[8];
-        residuals8(a, pw, cnt8, s0 + k, d, oc, stg0, stg1, bad, zeros);
+        residuals8(a, pw, cnt8, s0 + k, zfl, d, oc, stg0, stg1, bad, zeros);
         float v[8];
 #pragma unroll
         for (int j = 0; j < 8; j++) {
@@ -713,7 +720,7 @@ __device__ __forceinline__ void decode_fast_values_body(const DecodeArgs &a, VGr
         for (uint32_t i = threadIdx.x; i < pieces; i += blockDim.x) s_ft[i] = g_ft[i];
         ft = reinterpret_cast<const uint16_t *>(s_ft);  // visible after build_level1's barriers
     }
-    build_level1(a, s_dyn, l1tab);
+    build_level1<true>(a, s_dyn, l1tab);
     if (a.ctl->error & DERR_CORRUPT) return;
     const uint32_t shift = 32 - a.fast_bits;
     const uint32_t *stream = reinterpret_cast<const uint32_t *>(a.archive + a.off_stream);
