@@ -109,7 +109,9 @@ struct Ring {
 // writing codes, in two 512-thread blocks per SM, measured 0.489 -> 0.506 ms
 // with it, and the general decoder on a 512^3 lognormal field at rel eb 1e-4,
 // whose codes average 7.8 bits, 0.405 -> 0.532 ms with K = 4: both keep
-// Ring.)  Before a batch at word v, every word requested in an
+// Ring.  One word a batch measured the same as two here; a copy of the
+// complete table in shared memory, which helps the fused decoder, made the
+// codes decoder slower too, 0.489 -> 0.503 ms, by taking L1 from its rings.)  Before a batch at word v, every word requested in an
 // earlier batch has landed (wait_group 1 leaves only this batch's pending);
 // a lane that drained to within v + AHEAD (it consumed more than K words a
 // batch for a while) refills the whole ring and waits for it.  Either way
