@@ -687,18 +687,33 @@ __device__ __forceinline__ void residuals8(const DecodeArgs &a, const uint32_t (
     if (__any_sync(0xffffffffu, zm != 0)) {
         *stg0 = make_uint4(d[0], d[1], d[2], d[3]);
         *stg1 = make_uint4(d[4], d[5], d[6], d[7]);
-        uint32_t mm = zm, t = 0;
-        while (mm) {
-            const uint32_t j = __ffs(mm) - 1;
-            mm &= mm - 1;
-            const uint2 e = t == 0 ? oc.o1 : t == 1 ? oc.o2 : oc.at(a, oc.op + t);
-            bad |= oc.op + t >= oc.oend || e.x != (uint32_t)(p0 + j);
-            reinterpret_cast<uint32_t *>(j < 4 ? stg0 : stg1)[j & 3] = e.y;
-            t++;
+        // the first two code-0 points take the two prefetched records without
+        // a loop; a third or more in one batch (rare) read theirs in a loop
+        const uint32_t nz = __popc(zm);
+        const uint32_t m1 = zm & (zm - 1u);
+        if (nz >= 1) {
+            const uint32_t j = __ffs(zm) - 1;
+            bad |= oc.op >= oc.oend || oc.o1.x != (uint32_t)(p0 + j);
+            reinterpret_cast<uint32_t *>(j < 4 ? stg0 : stg1)[j & 3] = oc.o1.y;
         }
-        if (t) {
-            oc.op += t;
-            zeros += t;
+        if (nz >= 2) {
+            const uint32_t j = __ffs(m1) - 1;
+            bad |= oc.op + 1 >= oc.oend || oc.o2.x != (uint32_t)(p0 + j);
+            reinterpret_cast<uint32_t *>(j < 4 ? stg0 : stg1)[j & 3] = oc.o2.y;
+        }
+        if (nz > 2) {
+            uint32_t mm = m1 & (m1 - 1u);
+            for (uint32_t t = 2; mm; t++) {
+                const uint32_t j = __ffs(mm) - 1;
+                mm &= mm - 1;
+                const uint2 e = oc.at(a, oc.op + t);
+                bad |= oc.op + t >= oc.oend || e.x != (uint32_t)(p0 + j);
+                reinterpret_cast<uint32_t *>(j < 4 ? stg0 : stg1)[j & 3] = e.y;
+            }
+        }
+        if (nz) {
+            oc.op += nz;
+            zeros += nz;
             oc.fetch(a);
         }
         const uint4 u0 = *stg0, u1 = *stg1;
