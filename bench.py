@@ -438,7 +438,7 @@ DRAM_TRAFFIC = {
     "dualquant_hist": (1749994325, ('k_quant.cu', 'common.cuh'), "46464c23b2bc0113"),
     "encode_count": (572855893, ('k_encode.cu', 'common.cuh', 'scan.cuh'), "eafb965bd833f037"),
     "encode_pack": (929418922, ('k_encode.cu', 'common.cuh', 'scan.cuh'), "eafb965bd833f037"),
-    "decode": (1248666709, ('k_decode.cu', 'common.cuh', 'scan.cuh'), "7d29f1c072600893"),
+    "decode": (1248666709, ('k_decode.cu', 'common.cuh', 'scan.cuh'), "362706e8664691c7"),
 }
 TRAFFIC_CONFIG = (28, 1e-4, 512, 2048)  # log2 n, rel eb, radius, chunk of the capture
 

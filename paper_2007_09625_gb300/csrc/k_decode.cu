@@ -1,21 +1,27 @@
 // k_decode.cu -- S7: Huffman decode (inflate, Sec. 3.3).
 //
 // Chunk word offsets are the exclusive prefix sum of ceil(bits/32) over the
-// archive's chunk table (three coalesced scan kernels).  Decoding is
+// archive's chunk table (one single-pass scan kernel).  Decoding is
 // sequential inside a chunk, as in the paper; one thread decodes one chunk.
-// Each thread keeps a 32-word ring of its chunk's stream in shared memory,
-// filled eight words at a time by cp.async (issued about two quarters before
-// the words are needed, so refills never stall the decode), and a bit window
-// of three registers (current word, next word, one look-ahead) advanced with
-// selects instead of branches.  A 4096-entry shared-memory table resolves
-// every code of at most 12 bits in one lookup; longer codes fall back to the
-// canonical per-length tables, also in shared memory.  Decoded codes leave in
-// 16-byte stores.  Every chunk must consume exactly its recorded bit count and
-// every code must exist in the codebook; anything else marks the archive
-// corrupt.  For 1D fields the decoder also accumulates the residual sum of
-// every 4096-point tile (in-cap codes only; outliers are added by the
-// scatter), which the reconstruction scans instead of making another pass
-// over the codes.
+// Each thread keeps a ring of its chunk's stream words in shared memory, fed
+// by cp.async ahead of the decode, and a bit window of four registers
+// advanced with selects instead of branches.  Three decoders:
+//   k_decode          any code length: a 4096-entry table resolves codes of
+//                     at most 12 bits, a second level those of 13-16 bits,
+//                     the canonical per-length tables the rest;
+//   k_decode_fast     codes of at most 15 bits: a lane-replicated table of
+//                     the window's top byte gives one or two codes per
+//                     lookup, the complete table the longer ones;
+//   k_decode_fast_values  the same decode for anchored 1D archives (every
+//                     chunk starts from its anchor) writing the values
+//                     fl(2eb * q) instead of the codes: the reconstruction
+//                     (Alg. 2) happens in the decoder.
+// Codes leave in 16-byte stores, values in 32-byte stores.  Every chunk must
+// consume exactly its recorded bit count and every code must exist in the
+// codebook; anything else marks the archive corrupt.  For 1D fields the code
+// decoders also accumulate the residual sum of every 512-point tile (in-cap
+// codes only; outliers are added by the reconstruction), which the separate
+// value pass scans instead of making another pass over the codes.
 #include "common.cuh"
 #include "scan.cuh"
 
