@@ -111,6 +111,29 @@ def test_archive_info_parses_oracle_archives(lib, oracle):
         gbsz.archive_info(a, a.size - 1)
 
 
+def test_archive_info_parses_anchored_archives(lib, oracle):
+    """Archives of 1D fields in chunks of at least 1024 symbols carry one
+    anchor per chunk between the chunk table and the outliers: the library's
+    host-side parser lays the sections out as the oracle wrote them (its total
+    size check passes only then), its compress bound covers them, and an
+    archive of the previous format version is refused by both."""
+    rng = np.random.default_rng(1)
+    x = np.cumsum(rng.normal(size=50001)).astype(np.float32)
+    for chunk in (512, 1024, 4096, 65536):
+        a = oracle.compress(x, 1e-4, oracle.EB_REL, radius=512, chunk=chunk)
+        p, n = gbsz.archive_info(a, a.size)
+        assert n == x.size and p.chunk == chunk and p.ndim == 1
+        nc = (x.size + chunk - 1) // chunk
+        assert oracle.sections(a)["nanchor"] == (nc if chunk >= 1024 else 0)
+        q = gbsz.make_params([x.size], 1e-4, gbsz.EB_REL, 512, chunk)
+        assert lib.gbsz_compress_bound(C.byref(q)) >= a.size
+        old = a.copy()
+        old[4:6] = np.frombuffer(np.uint16(1).tobytes(), np.uint8)  # format version 1
+        with pytest.raises(gbsz.GbszError):
+            gbsz.archive_info(old, old.size)
+        assert oracle.decompress_status(old) == oracle.ERR_CORRUPT
+
+
 def test_create_without_gpu_is_a_clean_error(lib):
     import torch
     if torch.cuda.is_available():
