@@ -284,8 +284,9 @@ def test_profiling_survives_graph_replay(gb, ctx):
 def test_grouped_batch_equals_slot_streams_and_oracle(gb, ctx):
     """One launch per stage for the whole batch: ranks 1-4, absolute and
     relative bounds, radii from 64 to 32768, chunks 64 to 8192, the per-block
-    mode, a field whose pointer is not 16-byte aligned; the archives equal
-    the slot-stream path's and the oracle's."""
+    mode, a field whose pointer is not 16-byte aligned (and whose 1D archive
+    carries chunk anchors); the archives equal the slot-stream path's and the
+    oracle's."""
     rng = np.random.default_rng(950)
     kinds = [("walk", (70001,)), ("sinus", (90, 131)), ("lognormal", (17, 23, 29)), ("walk", (1,)),
              ("grf", (200, 300)), ("sinus", (3, 4, 19, 21)), ("walk", (300007,)), ("lognormal", (40, 40, 41))]
@@ -306,7 +307,7 @@ def test_grouped_batch_equals_slot_streams_and_oracle(gb, ctx):
         mode = gb.EB_ABS if i % 3 == 2 else gb.EB_REL
         eb = 1e-3 if mode == gb.EB_ABS else [1e-4, 1e-3, 1e-2][i % 3]
         R = [512, 64, 32768, 512][i % 4]
-        C = [0, 64, 256, 8192][i % 4]
+        C = [0, 64, 256, 8192][i % 4] if i != 6 else 2048  # field 6: 1D in chunks of 2048, with chunk anchors
         params.append(gb.make_params(gb.field_dims(t), eb, mode, R, C, lblock=1 if i in (1, 4) else 0))
     torch.cuda.synchronize()
     results = {}
