@@ -510,3 +510,19 @@ def test_anchored_decode_into_16_byte_aligned_output(gb, ctx):
                 assert np.isnan(got[:off]).all() and np.isnan(got[off + n:]).all(), (dec, off)
         finally:
             ctx.set_option(gb.OPT_DECODER, 0)
+
+
+@pytest.mark.parametrize("kind,rel", [("sin", 1e-2), ("ramp", 1e-2)])
+def test_anchored_without_outliers_and_tiny_codebooks(gb, ctx, kind, rel):
+    """Anchored 1D archives with no outlier at all (the chunk starts come
+    from a zeroed table) and with codebooks of 1-3 bit codes (the complete
+    table that the decoder copies into shared memory has 2-8 entries),
+    through the decoder that writes the values and through the two-kernel
+    path."""
+    n = (1 << 20) + 17
+    t = np.arange(n, dtype=np.float64)
+    x = ((np.sin(t * 2e-4) + 0.5 * np.sin(t * 7e-5 + 1.0)) if kind == "sin" else t * 1e-3).astype(np.float32)
+    arc, nb, oa = compare_stages(gb, ctx, x, rel, ref.EB_REL, 512, 1024)
+    s_ = ref.sections(oa)
+    assert s_["m"] == 0 and s_["maxlen"] <= 3 and s_["nanchor"] == (n + 1023) // 1024
+    check_decompress(gb, ctx, arc, nb, oa, x, rel, ref.EB_REL)
